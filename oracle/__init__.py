@@ -1,0 +1,228 @@
+"""CPU oracle for the cellGPU SPV/AVM hot path (Sussman, arXiv 1702.02939).
+
+TEST INFRASTRUCTURE ONLY.  A plain, slow, obviously-correct C++ restatement of
+the method, loaded with ctypes.  Only tests/, ``__graft_entry__.smoke()`` and the
+CPU-baseline legs of ``bench.py`` may import it; the library never does.  It
+shares no code with the CUDA path.
+"""
+import ctypes as C
+import numpy as np
+
+from . import build as _build
+
+MAX_RING = 16
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(_build.build())
+        _declare(_lib)
+    return _lib
+
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_lp = C.POINTER(C.c_int64)
+_up = C.POINTER(C.c_uint32)
+
+
+def _declare(L):
+    L.cgo_grid_exponent.argtypes = [C.c_double, C.c_double]
+    L.cgo_grid_exponent.restype = C.c_int
+    L.cgo_snap_length.argtypes = [C.c_double, C.c_int]
+    L.cgo_snap_length.restype = C.c_double
+    L.cgo_snap_positions.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp]
+    L.cgo_philox.argtypes = [_up, _up, _up]
+    L.cgo_philox.restype = None
+    L.cgo_director_noise.argtypes = [C.c_uint64, C.c_int32, C.c_int64]
+    L.cgo_director_noise.restype = C.c_double
+    L.cgo_orient2d.argtypes = [_lp, _lp, _lp]
+    L.cgo_incircle.argtypes = [_lp, _lp, _lp, _lp]
+    L.cgo_incircle_sos.argtypes = [_lp, _lp, _lp, _lp, _lp]
+    L.cgo_delaunay_plain.argtypes = [C.c_int, _lp, _lp, C.c_int, _ip, _ip]
+    L.cgo_triangulate.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, C.c_int, _ip, _ip, _ip]
+    L.cgo_geometry.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _ip, _ip, _ip, C.c_int,
+                               _dp, _dp, _dp, _dp]
+    L.cgo_forces.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _ip, _ip, _ip, C.c_int,
+                             _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.cgo_integrate.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                C.c_uint64, C.c_int64]
+    L.cgo_spv_run.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp,
+                              C.c_uint64, C.c_int64, C.c_int64, _dp, _dp, _dp, _dp]
+    for name in ("cgo_snap_positions", "cgo_orient2d", "cgo_incircle", "cgo_incircle_sos",
+                 "cgo_delaunay_plain", "cgo_triangulate", "cgo_geometry", "cgo_forces",
+                 "cgo_integrate", "cgo_spv_run"):
+        getattr(L, name).restype = C.c_int
+    for extra in ("_declare_avm", "_declare_adjoint"):
+        fn = globals().get(extra)
+        if fn is not None:
+            fn(L)
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip)
+
+
+def _l(a):
+    return a.ctypes.data_as(_lp)
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise OracleError(f"{what} failed with code {rc}")
+
+
+def grid_exponent(Lx, Ly):
+    return lib().cgo_grid_exponent(float(Lx), float(Ly))
+
+
+def snap_length(L, q):
+    return lib().cgo_snap_length(float(L), int(q))
+
+
+def box(Lx, Ly=None):
+    """Box lengths snapped onto the position grid: (Lx, Ly, q)."""
+    Ly = Lx if Ly is None else Ly
+    q = grid_exponent(Lx, Ly)
+    return snap_length(Lx, q), snap_length(Ly, q), q
+
+
+def snap_positions(x, y, Lx, Ly):
+    x = np.array(x, dtype=np.float64, copy=True)
+    y = np.array(y, dtype=np.float64, copy=True)
+    _check(lib().cgo_snap_positions(len(x), Lx, Ly, _d(x), _d(y)), "snap")
+    return x, y
+
+
+def philox(ctr, key):
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_uint32 * 4)()
+    lib().cgo_philox(c, k, o)
+    return [int(v) for v in o]
+
+
+def director_noise(seed, tag, step):
+    return lib().cgo_director_noise(int(seed), int(tag), int(step))
+
+
+def _pt(p):
+    return (C.c_int64 * 2)(int(p[0]), int(p[1]))
+
+
+def orient2d(a, b, c):
+    return lib().cgo_orient2d(_pt(a), _pt(b), _pt(c))
+
+
+def incircle(a, b, c, d):
+    return lib().cgo_incircle(_pt(a), _pt(b), _pt(c), _pt(d))
+
+
+def incircle_sos(a, b, c, d, keys):
+    k = (C.c_int64 * 4)(*[int(v) for v in keys])
+    return lib().cgo_incircle_sos(_pt(a), _pt(b), _pt(c), _pt(d), k)
+
+
+def delaunay_plain(X, Y, max_ring=64):
+    X = np.ascontiguousarray(X, dtype=np.int64)
+    Y = np.ascontiguousarray(Y, dtype=np.int64)
+    m = len(X)
+    cnt = np.zeros(m, np.int32)
+    nbr = np.full(m * max_ring, -1, np.int32)
+    _check(lib().cgo_delaunay_plain(m, _l(X), _l(Y), max_ring, _i(cnt), _i(nbr)), "delaunay")
+    return cnt, nbr.reshape(m, max_ring)
+
+
+class Topology:
+    """Rings of a periodic Delaunay triangulation: neighbour tags, CCW from the
+    smallest tag, with the periodic image offset of each neighbour."""
+
+    def __init__(self, cnt, nbr, off):
+        self.cnt, self.nbr, self.off = cnt, nbr, off
+
+    def rings(self):
+        return [tuple(int(v) for v in self.nbr[i, :self.cnt[i]]) for i in range(len(self.cnt))]
+
+
+def triangulate(x, y, Lx, Ly):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    n = len(x)
+    cnt = np.zeros(n, np.int32)
+    nbr = np.full(n * MAX_RING, -1, np.int32)
+    off = np.zeros(n * MAX_RING * 2, np.int32)
+    _check(lib().cgo_triangulate(n, Lx, Ly, _d(x), _d(y), MAX_RING, _i(cnt), _i(nbr), _i(off)),
+           "triangulate")
+    return Topology(cnt, nbr.reshape(n, MAX_RING), off.reshape(n, MAX_RING, 2))
+
+
+def geometry(x, y, Lx, Ly, topo):
+    n = len(x)
+    A = np.zeros(n)
+    P = np.zeros(n)
+    hx = np.zeros(n * MAX_RING)
+    hy = np.zeros(n * MAX_RING)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    _check(lib().cgo_geometry(n, Lx, Ly, _d(x), _d(y), _i(topo.cnt), _i(topo.nbr), _i(topo.off),
+                              MAX_RING, _d(A), _d(P), _d(hx), _d(hy)), "geometry")
+    return A, P, hx.reshape(n, MAX_RING), hy.reshape(n, MAX_RING)
+
+
+def forces(x, y, Lx, Ly, topo, p0, A0=1.0, KA=1.0, KP=1.0):
+    n = len(x)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    p0 = np.ascontiguousarray(np.broadcast_to(np.asarray(p0, np.float64), (n,)))
+    mech = np.array([A0, KA, KP], np.float64)
+    Fx, Fy, A, P, E = np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(1)
+    _check(lib().cgo_forces(n, Lx, Ly, _d(x), _d(y), _i(topo.cnt), _i(topo.nbr), _i(topo.off),
+                            MAX_RING, _d(p0), _d(mech), _d(Fx), _d(Fy), _d(A), _d(P), _d(E)),
+           "forces")
+    return Fx, Fy, A, P, float(E[0])
+
+
+def energy(x, y, Lx, Ly, topo, p0, A0=1.0, KA=1.0, KP=1.0):
+    return forces(x, y, Lx, Ly, topo, p0, A0, KA, KP)[4]
+
+
+def integrate(x, y, theta, Fx, Fy, Lx, Ly, v0, mu, Dr, dt, seed, step):
+    n = len(x)
+    x = np.array(x, np.float64, copy=True)
+    y = np.array(y, np.float64, copy=True)
+    theta = np.array(theta, np.float64, copy=True)
+    Fx = np.ascontiguousarray(Fx, dtype=np.float64)
+    Fy = np.ascontiguousarray(Fy, dtype=np.float64)
+    v0 = np.ascontiguousarray(np.broadcast_to(np.asarray(v0, np.float64), (n,)))
+    par = np.array([mu, Dr, dt], np.float64)
+    _check(lib().cgo_integrate(n, Lx, Ly, _d(x), _d(y), _d(theta), _d(Fx), _d(Fy), _d(v0),
+                               _d(par), int(seed), int(step)), "integrate")
+    return x, y, theta
+
+
+def spv_run(x, y, theta, Lx, Ly, p0, v0, nsteps, seed, step0=0, A0=1.0, KA=1.0, KP=1.0, mu=1.0,
+            Dr=1.0, dt=0.01):
+    """nsteps oracle steps (each retriangulates from scratch). Returns the new
+    state and the forces/areas/perimeters evaluated at the last step's start."""
+    n = len(x)
+    x = np.array(x, np.float64, copy=True)
+    y = np.array(y, np.float64, copy=True)
+    theta = np.array(theta, np.float64, copy=True)
+    p0 = np.ascontiguousarray(np.broadcast_to(np.asarray(p0, np.float64), (n,)))
+    v0 = np.ascontiguousarray(np.broadcast_to(np.asarray(v0, np.float64), (n,)))
+    par = np.array([A0, KA, KP, mu, Dr, dt], np.float64)
+    Fx, Fy, A, P = np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n)
+    _check(lib().cgo_spv_run(n, Lx, Ly, _d(x), _d(y), _d(theta), _d(p0), _d(v0), _d(par),
+                             int(seed), int(step0), int(nsteps), _d(Fx), _d(Fy), _d(A), _d(P)),
+           "spv_run")
+    return x, y, theta, (Fx, Fy, A, P)

@@ -1,0 +1,388 @@
+// Oracle: self-propelled Voronoi (SPV) model, one plain CPU step at a time.
+// TEST INFRASTRUCTURE ONLY: used by tests/, the smoke check and the timed CPU
+// baseline of bench.py; never by the library.
+//
+// What is computed, with the passage of Sussman, arXiv 1702.02939 it follows:
+//  * periodic Delaunay triangulation from scratch (3x3 image tiling +
+//    Bowyer-Watson, exact predicates)                      -- Sec. 2.C.3
+//  * Voronoi vertices as circumcentres h = r_i + z/d       -- Eqs. A8-A12
+//  * areas A_i (shoelace) and perimeters P_i               -- Sec. 2.C.1
+//  * energy E = sum K_A (A_i - A0)^2 + K_P (P_i - P0_i)^2  -- Eq. 1 / A1
+//  * force sets dE_c/dh per (cell, vertex)                 -- Eqs. A3-A5
+//  * net force F_i = -sum_t (dh_t/dr_i)^T G_t              -- Eqs. A6, A7, A16
+//  * overdamped active update dr/dt = mu F + v0 n(theta),
+//    dtheta/dt = eta with variance 2 D_r (Euler-Maruyama)  -- Eq. 3, Sec. 2.C.3
+// Readings of garbled/silent passages (each also stated in the design notes):
+//  - Eq. 2 prints F = +grad E; Eq. A6 has the minus sign: F = -grad E.
+//  - Eq. A5 prints dP/dh = -(t_ij + t_ik); with t_ij = h_ijk - h_gij and
+//    t_ik = h_ikl - h_ijk the derivative of sum |t| is  t^_ij - t^_ik.
+//  - Eq. A14 must read  d(gamma d)/dr_i = -2 (r_ik.r_jk) r_ij - |r_ij|^2 r_jk,
+//    and Eq. A15 must read (1/d) dd/dr_i = (2/c) (r_jk,y, -r_jk,x) for c as
+//    defined in Eq. A8 (both re-derived; pinned by finite differences).
+//  - P0_i = p0_i * sqrt(A0) (p0 is the dimensionless target shape index).
+//  - positions are kept on the dyadic grid 2^-q, q = 50 - ceil(log2 max(Lx,Ly)),
+//    so coordinate differences are exact and predicates are decidable exactly.
+#include "internal.h"
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+namespace cgo {
+namespace {
+
+struct Geo {
+  int n = 0;
+  double Lx = 0, Ly = 0;
+  int max_ring = 16;
+  const double *x = nullptr, *y = nullptr;
+  const int32_t *cnt = nullptr, *nbr = nullptr, *off = nullptr;
+};
+
+inline int wrapi(int a, int n) { return ((a % n) + n) % n; }
+
+// Vector from cell i to the image of ring entry a of cell i (exact on the grid).
+inline void rel(const Geo& g, int i, int a, double& dx, double& dy) {
+  int j = g.nbr[i * g.max_ring + a];
+  int ox = g.off[(i * g.max_ring + a) * 2 + 0];
+  int oy = g.off[(i * g.max_ring + a) * 2 + 1];
+  dx = (g.x[j] - g.x[i]) + ox * g.Lx;
+  dy = (g.y[j] - g.y[i]) + oy * g.Ly;
+}
+
+// Circumcentre of (r_i, r_j, r_k) relative to r_i, written as in Eqs. A8-A12:
+//   c = r_ij x r_kj, d = 2c^2, beta d = -|r_ik|^2 (r_ij . r_jk),
+//   gamma d = |r_ij|^2 (r_ik . r_jk), z = beta d r_ij + gamma d r_ik, h - r_i = z/d.
+void circumcentre_rel(double rijx, double rijy, double rikx, double riky, double& hx, double& hy) {
+  double rjkx = rikx - rijx, rjky = riky - rijy;
+  double rkjx = -rjkx, rkjy = -rjky;
+  double c = rijx * rkjy - rijy * rkjx;
+  double d = 2.0 * c * c;
+  double betad = -(rikx * rikx + riky * riky) * (rijx * rjkx + rijy * rjky);
+  double gammad = (rijx * rijx + rijy * rijy) * (rikx * rjkx + riky * rjky);
+  double zx = betad * rijx + gammad * rikx;
+  double zy = betad * rijy + gammad * riky;
+  hx = zx / d;
+  hy = zy / d;
+}
+
+// Voronoi polygon of every cell (vertices relative to the cell), A and P.
+void polygons(const Geo& g, std::vector<double>& hx, std::vector<double>& hy, double* A,
+              double* P) {
+  hx.assign((size_t)g.n * g.max_ring, 0.0);
+  hy.assign((size_t)g.n * g.max_ring, 0.0);
+  for (int i = 0; i < g.n; ++i) {
+    int m = g.cnt[i];
+    for (int a = 0; a < m; ++a) {
+      double ax, ay, bx, by;
+      rel(g, i, a, ax, ay);
+      rel(g, i, (a + 1) % m, bx, by);
+      circumcentre_rel(ax, ay, bx, by, hx[i * g.max_ring + a], hy[i * g.max_ring + a]);
+    }
+    double area = 0.0, per = 0.0;
+    for (int a = 0; a < m; ++a) {
+      double x0 = hx[i * g.max_ring + a], y0 = hy[i * g.max_ring + a];
+      double x1 = hx[i * g.max_ring + (a + 1) % m], y1 = hy[i * g.max_ring + (a + 1) % m];
+      area += x0 * y1 - x1 * y0;
+      per += std::sqrt((x1 - x0) * (x1 - x0) + (y1 - y0) * (y1 - y0));
+    }
+    A[i] = 0.5 * area;
+    P[i] = per;
+  }
+}
+
+// Slot b of cell c's ring such that ring(c)[b] = (u, ou) and ring(c)[b+1] = (w, ow).
+int find_pair(const Geo& g, int c, int u, int oux, int ouy, int w, int owx, int owy) {
+  int m = g.cnt[c];
+  for (int b = 0; b < m; ++b) {
+    int e0 = c * g.max_ring + b, e1 = c * g.max_ring + (b + 1) % m;
+    if (g.nbr[e0] == u && g.off[2 * e0] == oux && g.off[2 * e0 + 1] == ouy && g.nbr[e1] == w &&
+        g.off[2 * e1] == owx && g.off[2 * e1 + 1] == owy)
+      return b;
+  }
+  return -1;
+}
+
+struct Mech {
+  double A0, KA, KP;
+  const double* p0;
+};
+
+// Forces on every cell (Eqs. A3-A7 and A13-A16 with the corrections above).
+int forces(const Geo& g, const Mech& mp, double* Fx, double* Fy, double* A, double* P,
+           double* energy) {
+  std::vector<double> hx, hy;
+  polygons(g, hx, hy, A, P);
+  const double sqA0 = std::sqrt(mp.A0);
+  double E = 0.0;
+  // force sets dE_c/dh at every vertex of every cell (Eq. A3 with A4, A5)
+  std::vector<double> sx((size_t)g.n * g.max_ring, 0.0), sy((size_t)g.n * g.max_ring, 0.0);
+  for (int c = 0; c < g.n; ++c) {
+    double P0 = mp.p0[c] * sqA0;
+    double ka = 2.0 * mp.KA * (A[c] - mp.A0);
+    double kp = 2.0 * mp.KP * (P[c] - P0);
+    E += mp.KA * (A[c] - mp.A0) * (A[c] - mp.A0) + mp.KP * (P[c] - P0) * (P[c] - P0);
+    int m = g.cnt[c];
+    for (int a = 0; a < m; ++a) {
+      int ip = c * g.max_ring + (a + m - 1) % m, ia = c * g.max_ring + a,
+          in = c * g.max_ring + (a + 1) % m;
+      double tinx = hx[ia] - hx[ip], tiny = hy[ia] - hy[ip];   // t_ij (incoming edge)
+      double toutx = hx[in] - hx[ia], touty = hy[in] - hy[ia];  // t_ik (outgoing edge)
+      // Eq. A4: dA/dh = 1/2 (l_ij n_ij + l_ik n_ik), outward normal l n = (t_y, -t_x)
+      double dAx = 0.5 * (tiny + touty), dAy = 0.5 * (-tinx - toutx);
+      // Eq. A5 (corrected): dP/dh = t^_ij - t^_ik
+      double lin = std::sqrt(tinx * tinx + tiny * tiny);
+      double lout = std::sqrt(toutx * toutx + touty * touty);
+      double dPx = tinx / lin - toutx / lout, dPy = tiny / lin - touty / lout;
+      sx[ia] = ka * dAx + kp * dPx;
+      sy[ia] = ka * dAy + kp * dPy;
+    }
+  }
+  if (energy) *energy = E;
+  // net force (Eqs. A6, A7): F_i = - sum_{t ni i} (dh_t/dr_i)^T G_t
+  for (int i = 0; i < g.n; ++i) {
+    int m = g.cnt[i];
+    double fx = 0.0, fy = 0.0;
+    for (int a = 0; a < m; ++a) {
+      int ea = i * g.max_ring + a, eb = i * g.max_ring + (a + 1) % m;
+      int j = g.nbr[ea], k = g.nbr[eb];
+      int ojx = g.off[2 * ea], ojy = g.off[2 * ea + 1];
+      int okx = g.off[2 * eb], oky = g.off[2 * eb + 1];
+      // triangle (i, j, k) appears as (j, k, i) around j and as (k, i, j) around k
+      int bj = find_pair(g, j, k, okx - ojx, oky - ojy, i, -ojx, -ojy);
+      int bk = find_pair(g, k, i, -okx, -oky, j, ojx - okx, ojy - oky);
+      if (bj < 0 || bk < 0) return -10;  // inconsistent rings
+      double Gx = sx[ea] + sx[j * g.max_ring + bj] + sx[k * g.max_ring + bk];
+      double Gy = sy[ea] + sy[j * g.max_ring + bj] + sy[k * g.max_ring + bk];
+      // Jacobian dh/dr_i (Eqs. A8-A16, corrected)
+      double rijx, rijy, rikx, riky;
+      rel(g, i, a, rijx, rijy);
+      rel(g, i, (a + 1) % m, rikx, riky);
+      double rjkx = rikx - rijx, rjky = riky - rijy;
+      double c = rijx * (-rjky) - rijy * (-rjkx);
+      double d = 2.0 * c * c;
+      double rij2 = rijx * rijx + rijy * rijy, rik2 = rikx * rikx + riky * riky;
+      double ij_jk = rijx * rjkx + rijy * rjky, ik_jk = rikx * rjkx + riky * rjky;
+      double betad = -rik2 * ij_jk, gammad = rij2 * ik_jk;
+      double zx = betad * rijx + gammad * rikx, zy = betad * rijy + gammad * riky;
+      double gbx = 2.0 * ij_jk * rikx + rik2 * rjkx, gby = 2.0 * ij_jk * riky + rik2 * rjky;
+      double ggx = -2.0 * ik_jk * rijx - rij2 * rjkx, ggy = -2.0 * ik_jk * rijy - rij2 * rjky;
+      double gdx = (2.0 / c) * rjky, gdy = (2.0 / c) * (-rjkx);
+      double J[2][2];
+      const double rv[2] = {rijx, rijy}, kv[2] = {rikx, riky}, zv[2] = {zx, zy};
+      const double gb[2] = {gbx, gby}, gg[2] = {ggx, ggy}, gd[2] = {gdx, gdy};
+      for (int al = 0; al < 2; ++al)
+        for (int be = 0; be < 2; ++be)
+          J[al][be] = (al == be ? 1.0 : 0.0) +
+                      (rv[al] * gb[be] + kv[al] * gg[be] - (al == be ? betad + gammad : 0.0) -
+                       zv[al] * gd[be]) / d;
+      fx -= J[0][0] * Gx + J[1][0] * Gy;
+      fy -= J[0][1] * Gx + J[1][1] * Gy;
+    }
+    Fx[i] = fx;
+    Fy[i] = fy;
+  }
+  return 0;
+}
+
+inline double snap_wrap(double v, double L, int q) {
+  double s = std::ldexp(std::rint(std::ldexp(v, q)), -q);
+  if (s >= L) s -= L;
+  else if (s < 0.0) s += L;
+  return s + 0.0;
+}
+
+int grid_exponent(double Lx, double Ly) {
+  double m = Lx > Ly ? Lx : Ly;
+  int ex;
+  double fr = std::frexp(m, &ex);  // m = fr * 2^ex, fr in [0.5, 1)
+  int e = (fr == 0.5) ? ex - 1 : ex;
+  return 50 - e;
+}
+
+// uniform in (0, 1]: (53 high bits of (hi:lo) + 1) * 2^-53
+inline double u53(uint32_t hi, uint32_t lo) {
+  uint64_t k = ((((uint64_t)hi) << 32) | lo) >> 11;
+  return std::ldexp((double)(k + 1), -53);
+}
+
+double director_noise(uint64_t seed, int32_t tag, int64_t step) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t ctr[4] = {(uint32_t)tag, (uint32_t)(uint64_t)step, (uint32_t)((uint64_t)step >> 32), 0u};
+  uint32_t out[4];
+  philox4x32_10(ctr, key, out);
+  double u1 = u53(out[0], out[1]), u2 = u53(out[2], out[3]);
+  // Box-Muller, cosine branch
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+int triangulate(int n, double Lx, double Ly, const double* x, const double* y, int max_ring,
+                int32_t* cnt, int32_t* nbr, int32_t* off) {
+  int q = grid_exponent(Lx, Ly);
+  int64_t LX = (int64_t)std::ldexp(Lx, q), LY = (int64_t)std::ldexp(Ly, q);
+  std::vector<Pt> pts;
+  std::vector<char> central;
+  pts.reserve((size_t)9 * n);
+  for (int oy = -1; oy <= 1; ++oy)
+    for (int ox = -1; ox <= 1; ++ox)
+      for (int i = 0; i < n; ++i) {
+        int64_t X = (int64_t)std::ldexp(x[i], q), Y = (int64_t)std::ldexp(y[i], q);
+        int img = (oy + 1) * 3 + (ox + 1);
+        pts.push_back(Pt{X + ox * LX, Y + oy * LY, i, ox, oy, (int64_t)i * 16 + img});
+        central.push_back(ox == 0 && oy == 0);
+      }
+  std::vector<Ring> rings;
+  int rc = bowyer_watson_rings(pts, central, rings);
+  if (rc) return rc;
+  for (size_t p = 0; p < pts.size(); ++p) {
+    if (!central[p]) continue;
+    int i = pts[p].tag;
+    const Ring& r = rings[p];
+    if ((int)r.tag.size() > max_ring) return -5;  // ring overflow
+    cnt[i] = (int32_t)r.tag.size();
+    for (int a = 0; a < max_ring; ++a) {
+      bool on = a < (int)r.tag.size();
+      nbr[i * max_ring + a] = on ? r.tag[a] : -1;
+      off[(i * max_ring + a) * 2 + 0] = on ? r.ox[a] : 0;
+      off[(i * max_ring + a) * 2 + 1] = on ? r.oy[a] : 0;
+    }
+  }
+  return 0;
+}
+
+}  // namespace
+}  // namespace cgo
+
+using namespace cgo;
+
+extern "C" {
+
+int cgo_grid_exponent(double Lx, double Ly) { return grid_exponent(Lx, Ly); }
+
+double cgo_snap_length(double L, int q) { return std::ldexp(std::rint(std::ldexp(L, q)), -q); }
+
+// Snaps positions onto the grid and wraps them into [0, L). Inputs must lie in [-L, 2L).
+int cgo_snap_positions(int n, double Lx, double Ly, double* x, double* y) {
+  int q = grid_exponent(Lx, Ly);
+  for (int i = 0; i < n; ++i) {
+    if (!(x[i] >= -Lx && x[i] < 2 * Lx && y[i] >= -Ly && y[i] < 2 * Ly)) return -1;
+    x[i] = snap_wrap(x[i], Lx, q);
+    y[i] = snap_wrap(y[i], Ly, q);
+  }
+  return 0;
+}
+
+void cgo_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  philox4x32_10(ctr, key, out);
+}
+
+double cgo_director_noise(uint64_t seed, int32_t tag, int64_t step) {
+  return director_noise(seed, tag, step);
+}
+
+static Pt mkpt(const int64_t* p, int64_t key) { return Pt{p[0], p[1], 0, 0, 0, key}; }
+
+int cgo_orient2d(const int64_t* a, const int64_t* b, const int64_t* c) {
+  return orient2d_exact(mkpt(a, 0), mkpt(b, 0), mkpt(c, 0));
+}
+
+int cgo_incircle(const int64_t* a, const int64_t* b, const int64_t* c, const int64_t* d) {
+  return incircle_exact(mkpt(a, 0), mkpt(b, 0), mkpt(c, 0), mkpt(d, 0));
+}
+
+int cgo_incircle_sos(const int64_t* a, const int64_t* b, const int64_t* c, const int64_t* d,
+                     const int64_t* keys) {
+  return incircle_sos(mkpt(a, keys[0]), mkpt(b, keys[1]), mkpt(c, keys[2]), mkpt(d, keys[3]));
+}
+
+// Delaunay triangulation of a plain (non-periodic) point set given in grid
+// units; rings of every interior point (CCW, starting at the smallest index);
+// hull points get cnt = 0.
+int cgo_delaunay_plain(int m, const int64_t* X, const int64_t* Y, int max_ring, int32_t* cnt,
+                       int32_t* nbr) {
+  std::vector<Pt> pts(m);
+  std::vector<char> central(m, 1);
+  for (int i = 0; i < m; ++i) pts[i] = Pt{X[i], Y[i], i, 0, 0, (int64_t)i};
+  std::vector<Ring> rings;
+  int rc = bowyer_watson_rings(pts, central, rings, true);
+  if (rc) return rc;
+  for (int i = 0; i < m; ++i) {
+    if ((int)rings[i].tag.size() > max_ring) return -5;
+    cnt[i] = (int32_t)rings[i].tag.size();
+    for (int a = 0; a < max_ring; ++a)
+      nbr[i * max_ring + a] = a < cnt[i] ? rings[i].tag[a] : -1;
+  }
+  return 0;
+}
+
+int cgo_triangulate(int n, double Lx, double Ly, const double* x, const double* y, int max_ring,
+                    int32_t* cnt, int32_t* nbr, int32_t* off) {
+  return triangulate(n, Lx, Ly, x, y, max_ring, cnt, nbr, off);
+}
+
+// Voronoi vertices (relative to each cell), areas and perimeters.
+int cgo_geometry(int n, double Lx, double Ly, const double* x, const double* y,
+                 const int32_t* cnt, const int32_t* nbr, const int32_t* off, int max_ring,
+                 double* A, double* P, double* hx, double* hy) {
+  Geo g{n, Lx, Ly, max_ring, x, y, cnt, nbr, off};
+  std::vector<double> vx, vy;
+  polygons(g, vx, vy, A, P);
+  if (hx) std::memcpy(hx, vx.data(), sizeof(double) * vx.size());
+  if (hy) std::memcpy(hy, vy.data(), sizeof(double) * vy.size());
+  return 0;
+}
+
+// mech = {A0, KA, KP}
+int cgo_forces(int n, double Lx, double Ly, const double* x, const double* y, const int32_t* cnt,
+               const int32_t* nbr, const int32_t* off, int max_ring, const double* p0,
+               const double* mech, double* Fx, double* Fy, double* A, double* P, double* E) {
+  Geo g{n, Lx, Ly, max_ring, x, y, cnt, nbr, off};
+  Mech mp{mech[0], mech[1], mech[2], p0};
+  return forces(g, mp, Fx, Fy, A, P, E);
+}
+
+// One Euler-Maruyama update (Eq. 3) from given forces; positions snapped/wrapped.
+// par = {mu, Dr, dt}
+int cgo_integrate(int n, double Lx, double Ly, double* x, double* y, double* theta,
+                  const double* Fx, const double* Fy, const double* v0, const double* par,
+                  uint64_t seed, int64_t step) {
+  int q = grid_exponent(Lx, Ly);
+  double mu = par[0], Dr = par[1], dt = par[2];
+  double s = std::sqrt(2.0 * Dr * dt);
+  for (int i = 0; i < n; ++i) {
+    double vx = mu * Fx[i] + v0[i] * std::cos(theta[i]);
+    double vy = mu * Fy[i] + v0[i] * std::sin(theta[i]);
+    double xn = x[i] + dt * vx, yn = y[i] + dt * vy;
+    x[i] = snap_wrap(xn, Lx, q);
+    y[i] = snap_wrap(yn, Ly, q);
+    theta[i] = theta[i] + s * director_noise(seed, i, step);
+  }
+  return 0;
+}
+
+// nsteps full oracle steps: triangulate from scratch, forces, update.
+// par = {A0, KA, KP, mu, Dr, dt}.  Final forces/areas/perimeters of the last
+// step's starting state are left in Fx, Fy, A, P (may be NULL).
+int cgo_spv_run(int n, double Lx, double Ly, double* x, double* y, double* theta,
+                const double* p0, const double* v0, const double* par, uint64_t seed,
+                int64_t step0, int64_t nsteps, double* Fx, double* Fy, double* A, double* P) {
+  const int R = 16;
+  std::vector<int32_t> cnt(n), nbr((size_t)n * R), off((size_t)n * R * 2);
+  std::vector<double> fx(n), fy(n), a(n), p(n);
+  Mech mp{par[0], par[1], par[2], p0};
+  double ipar[3] = {par[3], par[4], par[5]};
+  for (int64_t s = 0; s < nsteps; ++s) {
+    int rc = triangulate(n, Lx, Ly, x, y, R, cnt.data(), nbr.data(), off.data());
+    if (rc) return rc;
+    Geo g{n, Lx, Ly, R, x, y, cnt.data(), nbr.data(), off.data()};
+    rc = forces(g, mp, fx.data(), fy.data(), a.data(), p.data(), nullptr);
+    if (rc) return rc;
+    if (Fx) std::memcpy(Fx, fx.data(), sizeof(double) * n);
+    if (Fy) std::memcpy(Fy, fy.data(), sizeof(double) * n);
+    if (A) std::memcpy(A, a.data(), sizeof(double) * n);
+    if (P) std::memcpy(P, p.data(), sizeof(double) * n);
+    cgo_integrate(n, Lx, Ly, x, y, theta, fx.data(), fy.data(), v0, ipar, seed, step0 + s);
+  }
+  return 0;
+}
+
+}  // extern "C"
