@@ -1,0 +1,157 @@
+/* cellgb: GB300-native (sm_103a) self-propelled Voronoi (SPV) model.
+ *
+ * C ABI of libcellgb.so.  The model and every step follow D. M. Sussman,
+ * "cellGPU: massively parallel simulations of dynamic vertex models",
+ * arXiv 1702.02939 (cited below as "the paper"):
+ *   energy           E = sum_i K_A (A_i - A0)^2 + K_P (P_i - P0_i)^2     Eq. 1
+ *   force            F_i = -dE/dr_i (chain rule through the Voronoi
+ *                    vertices)                                          Eqs. 2, A6-A16
+ *   motion           dr_i/dt = mu F_i + v0_i n(theta_i),
+ *                    dtheta_i/dt = eta_i,  <eta eta> = 2 D_r            Eq. 3
+ *   topology         Delaunay triangulation of the cell positions in a
+ *                    periodic box, tested by the empty-circumcircle
+ *                    property after every move and repaired locally     Sec. 2.C.3-4
+ *
+ * Units and conventions
+ *   - Cells live in periodic boxes [0, Lx) x [0, Ly).  Positions are kept on
+ *     the dyadic grid 2^-q with q = 50 - ceil(log2(max(Lx, Ly))); box sides
+ *     are rounded to that grid at creation.  Moves are rounded to the grid
+ *     (error <= 2^-(q+1), about 1e-15 L) so that every topological decision
+ *     is exact.
+ *   - P0_i = p0_i * sqrt(A0): p0 is the dimensionless target shape index.
+ *   - One Euler-Maruyama step: positions move with theta(t), then
+ *     theta <- theta + sqrt(2 D_r dt) xi, xi a standard normal from
+ *     Philox4x32-10 keyed by (seed) with counter (cell index, step, 0).
+ *   - A context may hold several independent systems ("replicas"), each
+ *     with its own box, p0 and v0; their cells are concatenated in replica
+ *     order and cell indices below always refer to that user order.
+ *
+ * Memory and ownership
+ *   - The caller owns all device memory.  The library needs one device
+ *     workspace of cg_workspace_bytes() bytes, aligned to 256 bytes, that
+ *     must stay allocated and unused by anyone else until cg_destroy().
+ *   - The library owns only the opaque host context.
+ *   - Array arguments marked "any" may be host or device pointers (unified
+ *     addressing); pinned host memory gives the fastest transfers.
+ *   - All work runs on the CUDA stream given at creation.  Calls that return
+ *     data synchronize that stream before returning; cg_step() does not.
+ *
+ * Errors: every call returns CG_OK (0) or a negative CG_E* code.  Device
+ * kernels report errors through a status word that cg_sync() and every
+ * getter return; once set, it stays set.
+ */
+#ifndef CELLGB_H
+#define CELLGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CG_MAX_RING 16
+
+#define CG_OK 0
+#define CG_EINVAL (-1)          /* bad argument or position outside [-L, 2L) */
+#define CG_ECUDA (-2)           /* a CUDA runtime call failed */
+#define CG_ERING_OVERFLOW (-3)  /* a cell has more than CG_MAX_RING neighbours */
+#define CG_EREPAIR_CAP (-4)     /* topology not consistent after repair_cap rounds */
+#define CG_ETOPO_INCONSISTENT (-5) /* j in ring(i) but i not in ring(j) during forces */
+#define CG_ENONFINITE (-6)      /* a move produced a non-finite position */
+#define CG_EBOX_TOO_SMALL (-7)  /* Voronoi cell wider than the search box allows */
+#define CG_EDEGENERATE (-8)     /* coincident cells */
+#define CG_ECANDIDATES (-9)     /* too many repair candidates in one cell-list ring */
+
+typedef struct cg_ctx cg_ctx;
+
+/* One independent periodic system. */
+typedef struct cg_replica {
+  int32_t n;      /* cells, >= 16 */
+  double Lx, Ly;  /* box sides */
+  double p0;      /* default target shape index of its cells */
+  double v0;      /* default self-propulsion speed of its cells */
+} cg_replica;
+
+/* Parameters shared by all replicas (Eqs. 1 and 3 of the paper). */
+typedef struct cg_params {
+  double A0;           /* preferred area */
+  double KA, KP;       /* area and perimeter moduli */
+  double mu;           /* mobility */
+  double Dr;           /* rotational diffusion constant */
+  double dt;           /* time step */
+  uint64_t seed;       /* Philox key of the director noise */
+  int32_t repair_cap;  /* repair rounds per step, >= 1 (default 4) */
+  int32_t sort_every;  /* Hilbert re-sort period in steps; 0 = never */
+} cg_params;
+
+/* Counters accumulated on the device since creation. */
+typedef struct cg_counters {
+  int64_t steps;           /* steps taken (the Philox step counter) */
+  int64_t flagged_total;   /* cells flagged by the circumcircle test */
+  int64_t repaired_total;  /* cell repairs (all rounds) */
+  int32_t last_flagged;    /* flagged cells in the last step */
+  int32_t last_rounds;     /* repair rounds in the last step */
+  int32_t status;          /* device status word */
+  int32_t reserved;
+} cg_counters;
+
+/* Workspace size for R replicas. */
+int cg_workspace_bytes(int32_t R, const cg_replica* reps, size_t* bytes);
+
+/* Creates a context and triangulates every replica from scratch: each cell's
+ * Voronoi polygon is built by clipping with cell-list candidates, which is the
+ * GPU counterpart of the paper's CPU repair (Sec. 2.C.4) applied to all cells.
+ *   x, y, theta : any, n_total doubles each, replica-concatenated user order;
+ *                 positions must lie in [-L, 2L) and are wrapped into [0, L).
+ *   d_ws        : device workspace of ws_bytes >= cg_workspace_bytes().
+ *   stream      : cudaStream_t (may be 0).
+ * Synchronizes the stream; on error *out is NULL. */
+int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const double* x, const double* y,
+              const double* theta, void* d_ws, size_t ws_bytes, void* stream, cg_ctx** out);
+
+/* Advances every replica by nsteps time steps (Sec. 2.C: geometry, force
+ * sets, net force, move and rotate, circumcircle test, local repair).
+ * Asynchronous: enqueues work on the stream and returns.  Steps run as a
+ * captured CUDA graph without host synchronization. */
+int cg_step(cg_ctx* ctx, int64_t nsteps);
+
+/* Waits for the stream and returns the device status word. */
+int cg_sync(cg_ctx* ctx);
+
+/* State in user order (any pointers, n_total doubles each; NULL to skip). */
+int cg_get_state(cg_ctx* ctx, double* x, double* y, double* theta);
+/* Replaces the state and triangulates from scratch (as cg_create). */
+int cg_set_state(cg_ctx* ctx, const double* x, const double* y, const double* theta);
+
+/* Cell areas and perimeters at the current state (Sec. 2.C.1). */
+int cg_get_geometry(cg_ctx* ctx, double* A, double* P);
+/* Forces F = -dE/dr at the current state (Eqs. A6-A16); *energy (host, may
+ * be NULL) receives E of Eq. 1 summed over all replicas. */
+int cg_get_forces(cg_ctx* ctx, double* Fx, double* Fy, double* energy);
+/* Delaunay neighbours: cnt[i] and nbr[i*CG_MAX_RING + a] (cell indices, CCW,
+ * starting at the smallest index, -1 padded).  int32 arrays, any pointers. */
+int cg_get_neighbors(cg_ctx* ctx, int32_t* cnt, int32_t* nbr);
+
+/* Per-cell target shape index and self-propulsion speed (any pointers). */
+int cg_set_p0(cg_ctx* ctx, const double* p0);
+int cg_set_v0(cg_ctx* ctx, const double* v0);
+
+int cg_get_counters(cg_ctx* ctx, cg_counters* host_out);
+
+/* Total cells of the context. */
+int64_t cg_num_cells(const cg_ctx* ctx);
+
+/* Releases the host context (the workspace stays the caller's). */
+int cg_destroy(cg_ctx* ctx);
+
+/* Static description of a status code. */
+const char* cg_status_string(int status);
+/* Last error message of a context (static lifetime within the context). */
+const char* cg_last_error(const cg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CELLGB_H */

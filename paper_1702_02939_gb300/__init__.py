@@ -1,0 +1,265 @@
+"""cellgb: GB300-native self-propelled Voronoi (SPV) model.
+
+Thin Python binding of libcellgb.so (C ABI declared in include/cellgb.h).  The
+functions ``cg_*`` below carry the same names and arguments as the C entry
+points and only marshal pointers; all computation runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the CUDA stream.
+
+Model: Sussman, "cellGPU: massively parallel simulations of dynamic vertex
+models", arXiv 1702.02939 (energy Eq. 1, forces Eqs. A6-A16, motion Eq. 3,
+topology test and repair Sec. 2.C.3-4).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+MAX_RING = 16
+_LIB_PATH = _build.LIB
+_lib = None
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "ring overflow",
+          -4: "repair cap exceeded", -5: "inconsistent rings", -6: "non-finite position",
+          -7: "box too small", -8: "degenerate input", -9: "too many repair candidates"}
+
+
+class CellgbError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__(f"cellgb status {code} ({STATUS.get(code, '?')}) {msg}".strip())
+
+
+class cg_replica(C.Structure):
+    _fields_ = [("n", C.c_int32), ("Lx", C.c_double), ("Ly", C.c_double), ("p0", C.c_double),
+                ("v0", C.c_double)]
+
+
+class cg_params(C.Structure):
+    _fields_ = [("A0", C.c_double), ("KA", C.c_double), ("KP", C.c_double), ("mu", C.c_double),
+                ("Dr", C.c_double), ("dt", C.c_double), ("seed", C.c_uint64),
+                ("repair_cap", C.c_int32), ("sort_every", C.c_int32)]
+
+
+class cg_counters(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("flagged_total", C.c_int64), ("repaired_total", C.c_int64),
+                ("last_flagged", C.c_int32), ("last_rounds", C.c_int32), ("status", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+def lib():
+    """The loaded library.  Fails loudly if it was not built: there is no
+    fallback implementation."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"libcellgb.so not built ({_LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(_LIB_PATH)
+        vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+        L.cg_workspace_bytes.argtypes = [i32, C.POINTER(cg_replica), C.POINTER(C.c_size_t)]
+        L.cg_create.argtypes = [i32, C.POINTER(cg_replica), C.POINTER(cg_params), vp, vp, vp, vp, C.c_size_t,
+                                vp, C.POINTER(vp)]
+        L.cg_step.argtypes = [vp, i64]
+        L.cg_sync.argtypes = [vp]
+        L.cg_get_state.argtypes = [vp, vp, vp, vp]
+        L.cg_set_state.argtypes = [vp, vp, vp, vp]
+        L.cg_get_geometry.argtypes = [vp, vp, vp]
+        L.cg_get_forces.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
+        L.cg_get_neighbors.argtypes = [vp, vp, vp]
+        L.cg_set_p0.argtypes = [vp, vp]
+        L.cg_set_v0.argtypes = [vp, vp]
+        L.cg_get_counters.argtypes = [vp, C.POINTER(cg_counters)]
+        L.cg_num_cells.argtypes = [vp]
+        L.cg_num_cells.restype = i64
+        L.cg_destroy.argtypes = [vp]
+        L.cg_status_string.argtypes = [C.c_int]
+        L.cg_status_string.restype = C.c_char_p
+        L.cg_last_error.argtypes = [vp]
+        L.cg_last_error.restype = C.c_char_p
+        for name in ("cg_workspace_bytes", "cg_create", "cg_step", "cg_sync", "cg_get_state", "cg_set_state",
+                     "cg_get_geometry", "cg_get_forces", "cg_get_neighbors", "cg_set_p0", "cg_set_v0",
+                     "cg_get_counters", "cg_destroy"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers (argument marshalling only)
+# ---------------------------------------------------------------------------
+def _ptr(a):
+    """Raw address of a torch tensor or numpy array (contiguous)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return C.c_void_p(a.data_ptr())
+    assert a.flags["C_CONTIGUOUS"]
+    return C.c_void_p(a.ctypes.data)
+
+
+def _check(rc, ctx=None):
+    if rc != 0:
+        msg = lib().cg_last_error(ctx).decode() if ctx else ""
+        raise CellgbError(rc, msg)
+
+
+def _reps(replicas):
+    arr = (cg_replica * len(replicas))()
+    for k, r in enumerate(replicas):
+        arr[k] = cg_replica(int(r["n"]), float(r["Lx"]), float(r["Ly"]), float(r["p0"]), float(r["v0"]))
+    return arr
+
+
+def cg_workspace_bytes(replicas):
+    out = C.c_size_t(0)
+    _check(lib().cg_workspace_bytes(len(replicas), _reps(replicas), C.byref(out)))
+    return out.value
+
+
+def cg_create(replicas, params, x, y, theta, workspace, stream):
+    ctx = C.c_void_p()
+    _check(lib().cg_create(len(replicas), _reps(replicas), C.byref(params), _ptr(x), _ptr(y), _ptr(theta),
+                           _ptr(workspace), workspace.numel(), C.c_void_p(stream), C.byref(ctx)))
+    return ctx
+
+
+def cg_step(ctx, nsteps):
+    _check(lib().cg_step(ctx, int(nsteps)), ctx)
+
+
+def cg_sync(ctx):
+    _check(lib().cg_sync(ctx), ctx)
+
+
+def cg_get_state(ctx, x, y, theta):
+    _check(lib().cg_get_state(ctx, _ptr(x), _ptr(y), _ptr(theta)), ctx)
+
+
+def cg_set_state(ctx, x, y, theta):
+    _check(lib().cg_set_state(ctx, _ptr(x), _ptr(y), _ptr(theta)), ctx)
+
+
+def cg_get_geometry(ctx, A, P):
+    _check(lib().cg_get_geometry(ctx, _ptr(A), _ptr(P)), ctx)
+
+
+def cg_get_forces(ctx, Fx, Fy):
+    e = C.c_double(0.0)
+    _check(lib().cg_get_forces(ctx, _ptr(Fx), _ptr(Fy), C.byref(e)), ctx)
+    return e.value
+
+
+def cg_get_neighbors(ctx, cnt, nbr):
+    _check(lib().cg_get_neighbors(ctx, _ptr(cnt), _ptr(nbr)), ctx)
+
+
+def cg_set_p0(ctx, p0):
+    _check(lib().cg_set_p0(ctx, _ptr(p0)), ctx)
+
+
+def cg_set_v0(ctx, v0):
+    _check(lib().cg_set_v0(ctx, _ptr(v0)), ctx)
+
+
+def cg_get_counters(ctx):
+    c = cg_counters()
+    _check(lib().cg_get_counters(ctx, C.byref(c)), ctx)
+    return {k: getattr(c, k) for k, _ in cg_counters._fields_ if k != "reserved"}
+
+
+def cg_num_cells(ctx):
+    return int(lib().cg_num_cells(ctx))
+
+
+def cg_destroy(ctx):
+    if ctx:
+        lib().cg_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# Convenience object
+# ---------------------------------------------------------------------------
+class SPV:
+    """One or more independent periodic SPV systems advanced together.
+
+    replicas: list of dicts {n, Lx, Ly, p0, v0}; x, y, theta: arrays of the
+    concatenated cells (numpy, or torch tensors on any device).
+    """
+
+    def __init__(self, replicas, x, y, theta, A0=1.0, KA=1.0, KP=1.0, mu=1.0, Dr=1.0, dt=0.01, seed=0,
+                 repair_cap=4, sort_every=0, device="cuda"):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.replicas = [dict(r) for r in replicas]
+        self.params = cg_params(A0, KA, KP, mu, Dr, dt, int(seed), int(repair_cap), int(sort_every))
+        nbytes = cg_workspace_bytes(self.replicas)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.n = sum(int(r["n"]) for r in self.replicas)
+        self.stream = torch.cuda.current_stream(self.device).cuda_stream
+        xs, ys, ts = (self._as_input(v) for v in (x, y, theta))
+        self.ctx = cg_create(self.replicas, self.params, xs, ys, ts, self.workspace, self.stream)
+
+    def _as_input(self, v):
+        t = self.torch
+        if isinstance(v, t.Tensor):
+            return v.to(dtype=t.float64).contiguous()
+        return np.ascontiguousarray(v, dtype=np.float64)
+
+    def _out(self, n=None, dtype=None):
+        t = self.torch
+        return t.empty(self.n if n is None else n, dtype=dtype or t.float64, device=self.device)
+
+    def step(self, nsteps=1):
+        cg_step(self.ctx, nsteps)
+
+    def sync(self):
+        cg_sync(self.ctx)
+
+    def state(self):
+        x, y, th = self._out(), self._out(), self._out()
+        cg_get_state(self.ctx, x, y, th)
+        return x, y, th
+
+    def set_state(self, x, y, theta=None):
+        cg_set_state(self.ctx, self._as_input(x), self._as_input(y),
+                     None if theta is None else self._as_input(theta))
+
+    def geometry(self):
+        A, P = self._out(), self._out()
+        cg_get_geometry(self.ctx, A, P)
+        return A, P
+
+    def forces(self):
+        Fx, Fy = self._out(), self._out()
+        E = cg_get_forces(self.ctx, Fx, Fy)
+        return Fx, Fy, E
+
+    def neighbors(self):
+        t = self.torch
+        cnt = self._out(dtype=t.int32)
+        nbr = self._out(self.n * MAX_RING, dtype=t.int32)
+        cg_get_neighbors(self.ctx, cnt, nbr)
+        return cnt, nbr.view(self.n, MAX_RING)
+
+    def set_p0(self, p0):
+        cg_set_p0(self.ctx, self._as_input(p0))
+
+    def set_v0(self, v0):
+        cg_set_v0(self.ctx, self._as_input(v0))
+
+    def counters(self):
+        return cg_get_counters(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            cg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,627 @@
+// C ABI of libcellgb.so: context, workspace layout, step graph, getters.
+#include "../../include/cellgb.h"
+#include "cg_device.cuh"
+#include "cg_kernels.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace cgk;
+
+namespace {
+
+struct Layout {
+  size_t total = 0;
+  size_t take(size_t bytes) {
+    size_t off = total;
+    total += (bytes + 255) & ~(size_t)255;
+    return off;
+  }
+};
+
+struct Offsets {
+  size_t x, y, X, Y, theta, p0, v0, A, P, Fx, Fy, ecell, tmp, tmp2, scalar;
+  size_t tag, rep, cnt, nbr, old_cnt, old_nbr;
+  size_t fs, s, w;
+  size_t flags, list0, list1;
+  size_t bin_count, bin_start, partials, cell_bin, cell_rank, ids;
+  size_t reps, ctl;
+  size_t total;
+};
+
+constexpr int kScanChunkHost = 256 * 8;
+
+Offsets layout(int64_t N, int64_t NB, int R) {
+  Layout L;
+  Offsets o;
+  const size_t d = sizeof(double), i4 = sizeof(int), i8 = sizeof(long long);
+  o.x = L.take(2 * N * d);
+  o.y = L.take(2 * N * d);
+  o.X = L.take(2 * N * i8);
+  o.Y = L.take(2 * N * i8);
+  o.theta = L.take(N * d);
+  o.p0 = L.take(N * d);
+  o.v0 = L.take(N * d);
+  o.A = L.take(N * d);
+  o.P = L.take(N * d);
+  o.Fx = L.take(N * d);
+  o.Fy = L.take(N * d);
+  o.ecell = L.take(N * d);
+  o.tmp = L.take(N * d);
+  o.tmp2 = L.take(N * d);
+  o.scalar = L.take(4 * d);
+  o.tag = L.take(N * i4);
+  o.rep = L.take(N * i4);
+  o.cnt = L.take(N * i4);
+  o.nbr = L.take(N * CG_RING * i4);
+  o.old_cnt = L.take(N * i4);
+  o.old_nbr = L.take(N * CG_RING * i4);
+  o.fs = L.take(N * CG_RING * sizeof(double2));
+  o.s = L.take(N * CG_RING * sizeof(double2));
+  o.w = L.take(N * CG_RING * sizeof(double2));
+  o.flags = L.take(((N + 31) / 32) * 4);
+  o.list0 = L.take(N * i4);
+  o.list1 = L.take(N * i4);
+  o.bin_count = L.take(NB * i4);
+  o.bin_start = L.take((NB + 1) * i4);
+  o.partials = L.take(((NB + 1 + kScanChunkHost - 1) / kScanChunkHost + 1) * i4);
+  o.cell_bin = L.take(N * i4);
+  o.cell_rank = L.take(N * i4);
+  o.ids = L.take(N * i4);
+  o.reps = L.take(R * sizeof(Rep));
+  o.ctl = L.take(sizeof(Ctl));
+  o.total = L.total;
+  return o;
+}
+
+struct RepHost {
+  Rep r;
+};
+
+// Smallest e with 2^e >= v.
+int ceil_log2(double v) {
+  int ex;
+  double fr = std::frexp(v, &ex);
+  return (fr == 0.5) ? ex - 1 : ex;
+}
+
+bool build_reps(int R, const cg_replica* reps, std::vector<Rep>& out, int64_t& N, int64_t& NB, std::string& err) {
+  out.resize(R);
+  N = 0;
+  NB = 0;
+  for (int r = 0; r < R; ++r) {
+    const cg_replica& c = reps[r];
+    if (c.n < 16 || !(c.Lx > 0) || !(c.Ly > 0) || !std::isfinite(c.Lx) || !std::isfinite(c.Ly)) {
+      err = "replica " + std::to_string(r) + ": need n >= 16 and positive finite box";
+      return false;
+    }
+    Rep& p = out[r];
+    std::memset(&p, 0, sizeof(p));
+    const int e = ceil_log2(std::fmax(c.Lx, c.Ly));
+    p.q = 50 - e;
+    p.scale = std::ldexp(1.0, p.q);
+    p.inv_scale = std::ldexp(1.0, -p.q);
+    p.LX = (long long)std::rint(std::ldexp(c.Lx, p.q));
+    p.LY = (long long)std::rint(std::ldexp(c.Ly, p.q));
+    p.Lx = std::ldexp((double)p.LX, -p.q);
+    p.Ly = std::ldexp((double)p.LY, -p.q);
+    p.hLx = 0.5 * p.Lx;
+    p.hLy = 0.5 * p.Ly;
+    // bins of about one mean cell spacing, at least 9 per side
+    const double spacing = std::sqrt(p.Lx * p.Ly / c.n);
+    p.nbx = std::max(9, (int)std::floor(p.Lx / spacing));
+    p.nby = std::max(9, (int)std::floor(p.Ly / spacing));
+    p.bsx = p.Lx / p.nbx;
+    p.bsy = p.Ly / p.nby;
+    // initial repair square: half-width W = 2^ceil(log2(max(L)/4)) >= L/4
+    const int ew = ceil_log2(std::fmax(p.Lx, p.Ly) / 4.0);
+    p.W2 = (long long)std::ldexp(2.0, ew + p.q);
+    p.cell0 = (int)N;
+    p.ncell = c.n;
+    p.bin0 = (int)NB;
+    p.v0 = c.v0;
+    p.p0 = c.p0;
+    N += c.n;
+    NB += (int64_t)p.nbx * p.nby;
+    if (N > (int64_t)1 << 30 || NB > (int64_t)1 << 30) {
+      err = "too many cells or bins";
+      return false;
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+struct cg_ctx {
+  int R = 0;
+  int64_t N = 0, NB = 0;
+  cg_params par{};
+  std::vector<Rep> reps;
+  char* ws = nullptr;
+  Offsets off{};
+  cudaStream_t stream = nullptr;    // user stream
+  cudaStream_t capture = nullptr;   // private stream used for graph capture
+  cudaGraphExec_t step_exec = nullptr;
+  int graph_steps = 0;
+  std::string last_error;
+
+  template <class T>
+  T* at(size_t o) const { return reinterpret_cast<T*>(ws + o); }
+  Ctl* ctl() const { return at<Ctl>(off.ctl); }
+};
+
+namespace {
+
+int fail(cg_ctx* c, int code, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return code;
+}
+
+#define CG_CUDA(ctx, call)                                                                 \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(ctx, CG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+  } while (0)
+
+GeomArgs geom_args(cg_ctx* c) {
+  GeomArgs g;
+  g.n = (int)c->N;
+  g.reps = c->at<Rep>(c->off.reps);
+  g.rep = c->at<int>(c->off.rep);
+  g.ctl = c->ctl();
+  g.x = c->at<double>(c->off.x);
+  g.y = c->at<double>(c->off.y);
+  g.cnt = c->at<int>(c->off.cnt);
+  g.nbr = c->at<int>(c->off.nbr);
+  g.p0 = c->at<double>(c->off.p0);
+  g.A0 = c->par.A0;
+  g.sqrtA0 = std::sqrt(c->par.A0);
+  g.KA = c->par.KA;
+  g.KP = c->par.KP;
+  g.A = c->at<double>(c->off.A);
+  g.P = c->at<double>(c->off.P);
+  g.energy_out = nullptr;
+  g.fs = c->at<double2>(c->off.fs);
+  g.s = c->at<double2>(c->off.s);
+  g.w = c->at<double2>(c->off.w);
+  return g;
+}
+
+ForceArgs force_args(cg_ctx* c, int integrate) {
+  ForceArgs f;
+  f.n = (int)c->N;
+  f.reps = c->at<Rep>(c->off.reps);
+  f.rep = c->at<int>(c->off.rep);
+  f.ctl = c->ctl();
+  f.cnt = c->at<int>(c->off.cnt);
+  f.nbr = c->at<int>(c->off.nbr);
+  f.tag = c->at<int>(c->off.tag);
+  f.fs = c->at<double2>(c->off.fs);
+  f.s = c->at<double2>(c->off.s);
+  f.w = c->at<double2>(c->off.w);
+  f.Fx = c->at<double>(c->off.Fx);
+  f.Fy = c->at<double>(c->off.Fy);
+  f.integrate = integrate;
+  f.x = c->at<double>(c->off.x);
+  f.y = c->at<double>(c->off.y);
+  f.X = c->at<long long>(c->off.X);
+  f.Y = c->at<long long>(c->off.Y);
+  f.theta = c->at<double>(c->off.theta);
+  f.v0 = c->at<double>(c->off.v0);
+  f.mu = c->par.mu;
+  f.dt = c->par.dt;
+  f.noise_amp = std::sqrt(2.0 * c->par.Dr * c->par.dt);
+  f.seed = c->par.seed;
+  return f;
+}
+
+TestArgs test_args(cg_ctx* c) {
+  TestArgs t;
+  t.n = (int)c->N;
+  t.reps = c->at<Rep>(c->off.reps);
+  t.rep = c->at<int>(c->off.rep);
+  t.ctl = c->ctl();
+  t.X = c->at<long long>(c->off.X);
+  t.Y = c->at<long long>(c->off.Y);
+  t.cnt = c->at<int>(c->off.cnt);
+  t.nbr = c->at<int>(c->off.nbr);
+  t.tag = c->at<int>(c->off.tag);
+  t.flags = c->at<unsigned>(c->off.flags);
+  t.list = c->at<int>(c->off.list0);
+  return t;
+}
+
+CellListArgs cell_list_args(cg_ctx* c, int only_if_flagged) {
+  CellListArgs a;
+  a.n = (int)c->N;
+  a.nbins = (int)c->NB;
+  a.reps = c->at<Rep>(c->off.reps);
+  a.rep = c->at<int>(c->off.rep);
+  a.ctl = c->ctl();
+  a.x = c->at<double>(c->off.x);
+  a.y = c->at<double>(c->off.y);
+  a.bin_count = c->at<int>(c->off.bin_count);
+  a.bin_start = c->at<int>(c->off.bin_start);
+  a.cell_bin = c->at<int>(c->off.cell_bin);
+  a.cell_rank = c->at<int>(c->off.cell_rank);
+  a.ids = c->at<int>(c->off.ids);
+  a.scan_partials = c->at<int>(c->off.partials);
+  a.only_if_flagged = only_if_flagged;
+  return a;
+}
+
+RepairArgs repair_args(cg_ctx* c, int which_in, int all_cells) {
+  RepairArgs r;
+  r.n = (int)c->N;
+  r.reps = c->at<Rep>(c->off.reps);
+  r.rep = c->at<int>(c->off.rep);
+  r.ctl = c->ctl();
+  r.x = c->at<double>(c->off.x);
+  r.y = c->at<double>(c->off.y);
+  r.X = c->at<long long>(c->off.X);
+  r.Y = c->at<long long>(c->off.Y);
+  r.tag = c->at<int>(c->off.tag);
+  r.bin_start = c->at<int>(c->off.bin_start);
+  r.bin_partials = c->at<int>(c->off.partials);
+  r.ids = c->at<int>(c->off.ids);
+  r.cnt = c->at<int>(c->off.cnt);
+  r.nbr = c->at<int>(c->off.nbr);
+  r.old_cnt = c->at<int>(c->off.old_cnt);
+  r.old_nbr = c->at<int>(c->off.old_nbr);
+  r.flags = c->at<unsigned>(c->off.flags);
+  r.list_in = c->at<int>(which_in ? c->off.list1 : c->off.list0);
+  r.which_in = which_in;
+  r.all_cells = all_cells;
+  return r;
+}
+
+CheckArgs check_args(cg_ctx* c, int which_in, int last_round, int all_cells) {
+  CheckArgs k;
+  k.n = (int)c->N;
+  k.ctl = c->ctl();
+  k.cnt = c->at<int>(c->off.cnt);
+  k.nbr = c->at<int>(c->off.nbr);
+  k.old_cnt = c->at<int>(c->off.old_cnt);
+  k.old_nbr = c->at<int>(c->off.old_nbr);
+  k.flags = c->at<unsigned>(c->off.flags);
+  k.list_in = c->at<int>(which_in ? c->off.list1 : c->off.list0);
+  k.list_out = c->at<int>(which_in ? c->off.list0 : c->off.list1);
+  k.which_in = which_in;
+  k.which_out = which_in ^ 1;
+  k.last_round = last_round;
+  k.all_cells = all_cells;
+  return k;
+}
+
+int repair_grid(const cg_ctx* c) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms * 8;
+}
+
+// One time step, enqueued on stream st (also used for capture).
+void enqueue_step(cg_ctx* c, cudaStream_t st) {
+  launch_geom(geom_args(c), st);
+  launch_force(force_args(c, 1), st);
+  launch_begin_topology(c->ctl(), 1, st);
+  launch_test(test_args(c), st);
+  launch_cell_list(cell_list_args(c, 1), st);
+  const int cap = c->par.repair_cap > 0 ? c->par.repair_cap : 4;
+  const int grid = repair_grid(c);
+  for (int r = 0; r < cap; ++r) {
+    const int which = r & 1;
+    launch_repair(repair_args(c, which, 0), grid, st);
+    launch_check(check_args(c, which, r == cap - 1, 0), st);
+  }
+}
+
+// Full triangulation of the current positions (every cell repaired).
+int triangulate_all(cg_ctx* c) {
+  cudaStream_t st = c->stream;
+  CG_CUDA(c, cudaMemsetAsync(c->at<int>(c->off.cnt), 0, c->N * sizeof(int), st));
+  CG_CUDA(c, cudaMemsetAsync(c->at<int>(c->off.nbr), 0xff, c->N * CG_RING * sizeof(int), st));
+  CG_CUDA(c, cudaMemsetAsync(c->at<unsigned>(c->off.flags), 0, ((c->N + 31) / 32) * 4, st));
+  CG_CUDA(c, cudaMemsetAsync(c->at<int>(c->off.bin_count), 0, c->NB * sizeof(int), st));
+  launch_begin_topology(c->ctl(), 0, st);
+  launch_cell_list(cell_list_args(c, 0), st);
+  launch_repair(repair_args(c, 0, 1), repair_grid(c), st);
+  launch_check(check_args(c, 0, 1, 1), st);
+  launch_begin_topology(c->ctl(), 0, st);
+  CG_CUDA(c, cudaGetLastError());
+  return CG_OK;
+}
+
+int read_status(cg_ctx* c) {
+  Ctl h;
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  CG_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
+  if (h.status != 0) return fail(c, h.status, std::string("device status: ") + cg_status_string(h.status));
+  return CG_OK;
+}
+
+int load_positions(cg_ctx* c, const double* x, const double* y) {
+  cudaStream_t st = c->stream;
+  double* tx = c->at<double>(c->off.tmp);
+  double* ty = c->at<double>(c->off.tmp2);
+  CG_CUDA(c, cudaMemcpyAsync(tx, x, c->N * sizeof(double), cudaMemcpyDefault, st));
+  CG_CUDA(c, cudaMemcpyAsync(ty, y, c->N * sizeof(double), cudaMemcpyDefault, st));
+  // user order == storage order until the first sort; scatter through tags
+  double* sx = c->at<double>(c->off.A);  // staging in storage order
+  double* sy = c->at<double>(c->off.P);
+  launch_scatter_d((int)c->N, c->at<int>(c->off.tag), tx, sx, st);
+  launch_scatter_d((int)c->N, c->at<int>(c->off.tag), ty, sy, st);
+  Ctl h;
+  CG_CUDA(c, cudaMemcpyAsync(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  CG_CUDA(c, cudaStreamSynchronize(st));
+  const size_t cur = (size_t)h.cur;
+  launch_snap((int)c->N, c->at<Rep>(c->off.reps), c->at<int>(c->off.rep), sx, sy,
+              c->at<double>(c->off.x) + cur * c->N, c->at<double>(c->off.y) + cur * c->N,
+              c->at<long long>(c->off.X) + cur * c->N, c->at<long long>(c->off.Y) + cur * c->N, c->ctl(), st);
+  CG_CUDA(c, cudaGetLastError());
+  return CG_OK;
+}
+
+int build_graph(cg_ctx* c) {
+  if (c->step_exec) return CG_OK;
+  cudaGraph_t graph;
+  CG_CUDA(c, cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+  enqueue_step(c, c->capture);
+  cudaError_t e = cudaStreamEndCapture(c->capture, &graph);
+  if (e != cudaSuccess) return fail(c, CG_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->step_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(c, CG_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+  return CG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cg_workspace_bytes(int32_t R, const cg_replica* reps, size_t* bytes) {
+  if (R <= 0 || !reps || !bytes) return CG_EINVAL;
+  std::vector<Rep> r;
+  int64_t N, NB;
+  std::string err;
+  if (!build_reps(R, reps, r, N, NB, err)) return CG_EINVAL;
+  *bytes = layout(N, NB, R).total;
+  return CG_OK;
+}
+
+int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const double* x, const double* y,
+              const double* theta, void* d_ws, size_t ws_bytes, void* stream, cg_ctx** out) {
+  if (!out) return CG_EINVAL;
+  *out = nullptr;
+  if (R <= 0 || !reps || !params || !x || !y || !theta || !d_ws) return CG_EINVAL;
+  if (((uintptr_t)d_ws & 255) != 0) return CG_EINVAL;
+  if (!(params->dt > 0) || !(params->mu >= 0) || !(params->Dr >= 0) || !(params->A0 > 0)) return CG_EINVAL;
+  cg_ctx* c = new (std::nothrow) cg_ctx();
+  if (!c) return CG_EINVAL;
+  std::string err;
+  if (!build_reps(R, reps, c->reps, c->N, c->NB, err)) {
+    delete c;
+    return CG_EINVAL;
+  }
+  c->R = R;
+  c->par = *params;
+  if (c->par.repair_cap <= 0) c->par.repair_cap = 4;
+  c->off = layout(c->N, c->NB, R);
+  if (ws_bytes < c->off.total) {
+    delete c;
+    return CG_EINVAL;
+  }
+  c->ws = static_cast<char*>(d_ws);
+  c->stream = static_cast<cudaStream_t>(stream);
+  int rc = CG_OK;
+  do {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { rc = fail(c, CG_ECUDA, cudaGetErrorString(e)); break; }
+    cudaStream_t st = c->stream;
+    // replica table and per-cell constants
+    std::vector<int> tag(c->N), rep(c->N);
+    std::vector<double> p0(c->N), v0(c->N);
+    for (int r = 0; r < R; ++r)
+      for (int k = 0; k < c->reps[r].ncell; ++k) {
+        int i = c->reps[r].cell0 + k;
+        tag[i] = i;
+        rep[i] = r;
+        p0[i] = c->reps[r].p0;
+        v0[i] = c->reps[r].v0;
+      }
+    Ctl h;
+    std::memset(&h, 0, sizeof(h));
+#define TRY(call) do { cudaError_t e2 = (call); if (e2 != cudaSuccess) { rc = fail(c, CG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e2)); } } while (0)
+    TRY(cudaMemcpyAsync(c->at<Rep>(c->off.reps), c->reps.data(), R * sizeof(Rep), cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(c->at<int>(c->off.tag), tag.data(), c->N * sizeof(int), cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(c->at<int>(c->off.rep), rep.data(), c->N * sizeof(int), cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(c->at<double>(c->off.p0), p0.data(), c->N * sizeof(double), cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(c->at<double>(c->off.v0), v0.data(), c->N * sizeof(double), cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(c->ctl(), &h, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(c->at<double>(c->off.tmp), theta, c->N * sizeof(double), cudaMemcpyDefault, st));
+#undef TRY
+    if (rc) break;
+    launch_scatter_d((int)c->N, c->at<int>(c->off.tag), c->at<double>(c->off.tmp), c->at<double>(c->off.theta), st);
+    rc = load_positions(c, x, y);
+    if (rc) break;
+    rc = triangulate_all(c);
+    if (rc) break;
+    rc = read_status(c);
+    if (rc) break;
+    rc = build_graph(c);
+  } while (0);
+  if (rc) {
+    cg_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return CG_OK;
+}
+
+int cg_step(cg_ctx* c, int64_t nsteps) {
+  if (!c || nsteps < 0) return CG_EINVAL;
+  for (int64_t s = 0; s < nsteps; ++s) CG_CUDA(c, cudaGraphLaunch(c->step_exec, c->stream));
+  return CG_OK;
+}
+
+int cg_sync(cg_ctx* c) {
+  if (!c) return CG_EINVAL;
+  return read_status(c);
+}
+
+int cg_get_state(cg_ctx* c, double* x, double* y, double* theta) {
+  if (!c) return CG_EINVAL;
+  int rc = read_status(c);
+  if (rc) return rc;
+  Ctl h;
+  CG_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
+  const size_t cur = (size_t)h.cur;
+  cudaStream_t st = c->stream;
+  const int* tag = c->at<int>(c->off.tag);
+  double* tmp = c->at<double>(c->off.tmp);
+  const double* srcs[3] = {c->at<double>(c->off.x) + cur * c->N, c->at<double>(c->off.y) + cur * c->N,
+                           c->at<double>(c->off.theta)};
+  double* dsts[3] = {x, y, theta};
+  for (int k = 0; k < 3; ++k) {
+    if (!dsts[k]) continue;
+    launch_gather_d((int)c->N, tag, srcs[k], tmp, st);
+    CG_CUDA(c, cudaMemcpyAsync(dsts[k], tmp, c->N * sizeof(double), cudaMemcpyDefault, st));
+    CG_CUDA(c, cudaStreamSynchronize(st));
+  }
+  return read_status(c);
+}
+
+int cg_set_state(cg_ctx* c, const double* x, const double* y, const double* theta) {
+  if (!c || !x || !y) return CG_EINVAL;
+  int rc = read_status(c);
+  if (rc) return rc;
+  if (theta) {
+    CG_CUDA(c, cudaMemcpyAsync(c->at<double>(c->off.tmp), theta, c->N * sizeof(double), cudaMemcpyDefault,
+                               c->stream));
+    launch_scatter_d((int)c->N, c->at<int>(c->off.tag), c->at<double>(c->off.tmp), c->at<double>(c->off.theta),
+                     c->stream);
+  }
+  rc = load_positions(c, x, y);
+  if (rc) return rc;
+  rc = triangulate_all(c);
+  if (rc) return rc;
+  return read_status(c);
+}
+
+static int compute_forces(cg_ctx* c, int want_energy) {
+  GeomArgs g = geom_args(c);
+  if (want_energy) g.energy_out = c->at<double>(c->off.ecell);
+  launch_geom(g, c->stream);
+  launch_force(force_args(c, 0), c->stream);
+  if (want_energy) launch_reduce_sum((int)c->N, c->at<double>(c->off.ecell), c->at<double>(c->off.scalar), c->stream);
+  CG_CUDA(c, cudaGetLastError());
+  return CG_OK;
+}
+
+static int gather_out(cg_ctx* c, const double* src, double* dst) {
+  if (!dst) return CG_OK;
+  double* tmp = c->at<double>(c->off.tmp);
+  launch_gather_d((int)c->N, c->at<int>(c->off.tag), src, tmp, c->stream);
+  CG_CUDA(c, cudaMemcpyAsync(dst, tmp, c->N * sizeof(double), cudaMemcpyDefault, c->stream));
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CG_OK;
+}
+
+int cg_get_geometry(cg_ctx* c, double* A, double* P) {
+  if (!c) return CG_EINVAL;
+  int rc = compute_forces(c, 0);
+  if (!rc) rc = gather_out(c, c->at<double>(c->off.A), A);
+  if (!rc) rc = gather_out(c, c->at<double>(c->off.P), P);
+  if (rc) return rc;
+  return read_status(c);
+}
+
+int cg_get_forces(cg_ctx* c, double* Fx, double* Fy, double* energy) {
+  if (!c) return CG_EINVAL;
+  int rc = compute_forces(c, energy != nullptr);
+  if (!rc) rc = gather_out(c, c->at<double>(c->off.Fx), Fx);
+  if (!rc) rc = gather_out(c, c->at<double>(c->off.Fy), Fy);
+  if (rc) return rc;
+  if (energy) {
+    CG_CUDA(c, cudaMemcpyAsync(energy, c->at<double>(c->off.scalar), sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream));
+  }
+  return read_status(c);
+}
+
+int cg_get_neighbors(cg_ctx* c, int32_t* cnt, int32_t* nbr) {
+  if (!c || !cnt || !nbr) return CG_EINVAL;
+  int rc = read_status(c);
+  if (rc) return rc;
+  // stage in the old-ring scratch (free outside a step)
+  int* tc = c->at<int>(c->off.cell_bin);
+  int* tn = c->at<int>(c->off.old_nbr);
+  launch_gather_ring((int)c->N, c->at<int>(c->off.tag), c->at<int>(c->off.cnt), c->at<int>(c->off.nbr), tc, tn,
+                     c->stream);
+  CG_CUDA(c, cudaMemcpyAsync(cnt, tc, c->N * sizeof(int), cudaMemcpyDefault, c->stream));
+  CG_CUDA(c, cudaMemcpyAsync(nbr, tn, c->N * CG_RING * sizeof(int), cudaMemcpyDefault, c->stream));
+  return read_status(c);
+}
+
+static int set_percell(cg_ctx* c, const double* src, size_t off) {
+  if (!c || !src) return CG_EINVAL;
+  double* tmp = c->at<double>(c->off.tmp);
+  CG_CUDA(c, cudaMemcpyAsync(tmp, src, c->N * sizeof(double), cudaMemcpyDefault, c->stream));
+  launch_scatter_d((int)c->N, c->at<int>(c->off.tag), tmp, c->at<double>(off), c->stream);
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return read_status(c);
+}
+
+int cg_set_p0(cg_ctx* c, const double* p0) { return c ? set_percell(c, p0, c->off.p0) : CG_EINVAL; }
+int cg_set_v0(cg_ctx* c, const double* v0) { return c ? set_percell(c, v0, c->off.v0) : CG_EINVAL; }
+
+int cg_get_counters(cg_ctx* c, cg_counters* out) {
+  if (!c || !out) return CG_EINVAL;
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  Ctl h;
+  CG_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
+  out->steps = h.step;
+  out->flagged_total = h.flagged_total;
+  out->repaired_total = h.repaired_total;
+  out->last_flagged = h.last_flagged;
+  out->last_rounds = h.round_count;
+  out->status = h.status;
+  out->reserved = 0;
+  return CG_OK;
+}
+
+int64_t cg_num_cells(const cg_ctx* c) { return c ? c->N : -1; }
+
+int cg_destroy(cg_ctx* c) {
+  if (!c) return CG_EINVAL;
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  if (c->capture) cudaStreamDestroy(c->capture);
+  delete c;
+  return CG_OK;
+}
+
+const char* cg_status_string(int s) {
+  switch (s) {
+    case CG_OK: return "ok";
+    case CG_EINVAL: return "invalid argument";
+    case CG_ECUDA: return "CUDA runtime error";
+    case CG_ERING_OVERFLOW: return "ring overflow (more than 16 neighbours)";
+    case CG_EREPAIR_CAP: return "topology inconsistent after the repair cap";
+    case CG_ETOPO_INCONSISTENT: return "inconsistent neighbour rings";
+    case CG_ENONFINITE: return "non-finite position";
+    case CG_EBOX_TOO_SMALL: return "box too small for the Voronoi search";
+    case CG_EDEGENERATE: return "degenerate input (coincident cells)";
+    case CG_ECANDIDATES: return "too many repair candidates";
+    default: return "unknown status";
+  }
+}
+
+const char* cg_last_error(const cg_ctx* c) { return c ? c->last_error.c_str() : "null context"; }
+
+}  // extern "C"

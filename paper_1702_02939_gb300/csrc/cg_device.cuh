@@ -1,0 +1,233 @@
+// Device-side building blocks of the cellgb SPV path (sm_103a).
+//
+// Model: self-propelled Voronoi (SPV) model of Sussman, "cellGPU: massively
+// parallel simulations of dynamic vertex models", arXiv 1702.02939.
+//
+// Conventions shared by every kernel
+//  * Positions live on the dyadic grid 2^-q of their replica, q = 50 -
+//    ceil(log2 max(Lx, Ly)); x (double) and X = x 2^q (int64) hold the same
+//    value.  Minimum-image differences of grid values are exact, so every
+//    topological decision (orientation, in-circle) is made exactly: a single
+//    precision filter with a rigorous error bound, then exact integer
+//    arithmetic (128-bit products, 256-bit sums) when the filter is unsure.
+//  * Exactly cocircular quadruples are resolved by the lifting perturbation
+//    |p|^2 + eps_p with eps_p growing with the cell tag (a phantom repair
+//    generator counts as larger than every tag).
+//  * Rings are stored row-major, CG_RING int32 slots per cell, CCW.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define CG_RING 16
+
+namespace cgk {
+
+// Status codes (mirrors include/cellgb.h).
+enum : int {
+  kOK = 0,
+  kEINVAL = -1,
+  kECUDA = -2,
+  kERING = -3,
+  kEREPAIR_CAP = -4,
+  kETOPO = -5,
+  kENONFINITE = -6,
+  kEBOX = -7,
+  kEDEGEN = -8,
+  kECAND = -9,
+};
+
+// Per-replica constants.
+struct Rep {
+  double Lx, Ly, hLx, hLy;  // box and half box (on the grid)
+  double scale, inv_scale;  // 2^q and 2^-q
+  double bsx, bsy;          // cell-list bin size
+  long long LX, LY;         // box in grid units
+  long long W2;             // twice the initial repair half-width, grid units
+  int cell0, ncell;         // cell range
+  int nbx, nby, bin0;       // cell-list bins
+  int q;
+  double v0, p0;            // defaults for the replica's cells
+  int pad[2];
+};
+
+// Mutable device globals of one context.
+struct Ctl {
+  int status;        // first error code raised by any kernel (0 = OK)
+  int cur;           // which position buffer holds the current state
+  long long step;    // global step counter (Philox counter)
+  int count[2];      // flagged-list lengths (double-buffered)
+  int round_count;   // repair rounds used in the last step
+  int max_rounds;    // max over steps
+  long long flagged_total, repaired_total;
+  int last_flagged;
+  int pad;
+};
+
+__device__ __forceinline__ void raise_status(Ctl* ctl, int code) {
+  atomicCAS(&ctl->status, 0, code);
+}
+
+__device__ __forceinline__ double min_image(double d, double L, double hL) {
+  if (d > hL) d -= L;
+  else if (d < -hL) d += L;
+  return d;
+}
+__device__ __forceinline__ long long min_image_i(long long d, long long L) {
+  long long h = L >> 1;
+  if (d > h) d -= L;
+  else if (d < -h) d += L;
+  return d;
+}
+
+// ----------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11) and the director noise of Eq. 3.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// (53 high bits of hi:lo, plus one) * 2^-53, in (0, 1].
+__device__ __forceinline__ double unit53(unsigned hi, unsigned lo) {
+  unsigned long long k = ((((unsigned long long)hi) << 32) | lo) >> 11;
+  return (double)(k + 1ull) * 0x1.0p-53;
+}
+
+// Standard normal for (seed, cell tag, step), cosine branch of Box-Muller.
+__device__ __forceinline__ double director_noise(unsigned long long seed, int tag, long long step) {
+  uint4 r = philox_10(make_uint4((unsigned)tag, (unsigned)(unsigned long long)step,
+                                 (unsigned)((unsigned long long)step >> 32), 0u),
+                      make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+  double u1 = unit53(r.x, r.y), u2 = unit53(r.z, r.w);
+  return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
+// ----------------------------------------------------------------------------
+// Exact predicates on integer grid coordinates.
+// ----------------------------------------------------------------------------
+typedef __int128 s128;
+typedef unsigned __int128 u128;
+
+// 256-bit two's complement value as (hi, lo).
+struct W256 {
+  u128 hi, lo;
+};
+
+__device__ __forceinline__ W256 w256_neg(W256 v) {
+  W256 r;
+  r.lo = ~v.lo + 1;
+  r.hi = ~v.hi + (r.lo == 0 ? 1 : 0);
+  return r;
+}
+__device__ __forceinline__ W256 w256_add(W256 a, W256 b) {
+  W256 r;
+  r.lo = a.lo + b.lo;
+  r.hi = a.hi + b.hi + (r.lo < a.lo ? 1 : 0);
+  return r;
+}
+// Signed product of two 128-bit integers whose magnitudes are below 2^110.
+static __device__ __noinline__ W256 w256_mul(s128 a, s128 b) {
+  bool neg = (a < 0) != (b < 0);
+  u128 x = a < 0 ? (u128)(-a) : (u128)a;
+  u128 y = b < 0 ? (u128)(-b) : (u128)b;
+  unsigned long long x0 = (unsigned long long)x, x1 = (unsigned long long)(x >> 64);
+  unsigned long long y0 = (unsigned long long)y, y1 = (unsigned long long)(y >> 64);
+  u128 p00 = (u128)x0 * y0;
+  u128 mid = (u128)x0 * y1 + (u128)x1 * y0;  // < 2^127 for our operand sizes
+  u128 p11 = (u128)x1 * y1;
+  W256 r;
+  r.lo = p00 + (mid << 64);
+  u128 carry = (r.lo < p00) ? 1 : 0;
+  r.hi = p11 + (mid >> 64) + carry;
+  return neg ? w256_neg(r) : r;
+}
+__device__ __forceinline__ int w256_sign(W256 v) {
+  if (v.hi == 0 && v.lo == 0) return 0;
+  return ((long long)(unsigned long long)(v.hi >> 64) < 0) ? -1 : 1;
+}
+
+__device__ __forceinline__ int orient_exact(long long ax, long long ay, long long bx, long long by) {
+  s128 d = (s128)ax * by - (s128)ay * bx;
+  return (d > 0) - (d < 0);
+}
+
+// Sign of (b - a) x (c - a) for integer points, exact.
+__device__ __forceinline__ int orient3_exact(long long ax, long long ay, long long bx, long long by,
+                                             long long cx, long long cy) {
+  return orient_exact(bx - ax, by - ay, cx - ax, cy - ay);
+}
+
+// Exact sign of det[[a, |a|^2], [b, |b|^2], [c, |c|^2]] (rows relative to the
+// query point), for |coordinates| < 2^52.
+static __device__ __noinline__ int incircle_rows_exact(long long ax, long long ay, long long bx, long long by,
+                                                long long cx, long long cy) {
+  s128 la = (s128)ax * ax + (s128)ay * ay;
+  s128 lb = (s128)bx * bx + (s128)by * by;
+  s128 lc = (s128)cx * cx + (s128)cy * cy;
+  s128 xbc = (s128)bx * cy - (s128)by * cx;
+  s128 xca = (s128)cx * ay - (s128)cy * ax;
+  s128 xab = (s128)ax * by - (s128)ay * bx;
+  W256 s = w256_add(w256_add(w256_mul(la, xbc), w256_mul(lb, xca)), w256_mul(lc, xab));
+  return w256_sign(s);
+}
+
+// Orientation of (0, a, b), coordinates in grid units; sc = 2^-q (float).
+__device__ __forceinline__ int orient_sign(long long ax, long long ay, long long bx, long long by, float sc) {
+  float fax = (float)ax * sc, fay = (float)ay * sc, fbx = (float)bx * sc, fby = (float)by * sc;
+  float l = fax * fby, r = fay * fbx;
+  float det = l - r;
+  // conversion (2u per product) + product (u) + difference (u): <= 6u * (|l|+|r|)
+  float bound = 1.0e-6f * (fabsf(l) + fabsf(r));
+  if (bound > 1.0e-30f) {
+    if (det > bound) return 1;
+    if (det < -bound) return -1;
+  }
+  return orient_exact(ax, ay, bx, by);
+}
+
+// Lifting-perturbed in-circle of (p, q, r, s): > 0 iff s is inside the circle
+// through p, q, r (p, q, r counter-clockwise).  Integer grid coordinates with
+// a common origin; keys order the infinitesimal lifts.  Never returns 0 for
+// four distinct points.
+__device__ __forceinline__ int incircle_sign(long long px, long long py, long long qx, long long qy,
+                                             long long rx, long long ry, long long sx, long long sy,
+                                             int kp, int kq, int kr, int ks, float sc) {
+  long long ax = px - sx, ay = py - sy, bx = qx - sx, by = qy - sy, cx = rx - sx, cy = ry - sy;
+  float fax = (float)ax * sc, fay = (float)ay * sc, fbx = (float)bx * sc, fby = (float)by * sc;
+  float fcx = (float)cx * sc, fcy = (float)cy * sc;
+  float la = fax * fax + fay * fay, lb = fbx * fbx + fby * fby, lc = fcx * fcx + fcy * fcy;
+  float t1 = fbx * fcy, t2 = fby * fcx, t3 = fcx * fay, t4 = fcy * fax, t5 = fax * fby, t6 = fay * fbx;
+  float det = la * (t1 - t2) + lb * (t3 - t4) + lc * (t5 - t6);
+  float perm = la * (fabsf(t1) + fabsf(t2)) + lb * (fabsf(t3) + fabsf(t4)) + lc * (fabsf(t5) + fabsf(t6));
+  // input conversion (<= 4u per monomial) + evaluation (<= 10u): 2e-6 ~ 34u.
+  float bound = 2.0e-6f * perm;
+  if (bound > 1.0e-30f && bound < 1.0e30f) {
+    if (det > bound) return 1;
+    if (det < -bound) return -1;
+  }
+  int s = incircle_rows_exact(ax, ay, bx, by, cx, cy);
+  if (s != 0) return s;
+  // Tie: the highest-key point's lift decides (its cofactor is a non-zero
+  // orientation because no three of four distinct cocircular points are collinear).
+  int top = 0, kt = kp;
+  if (kq > kt) { top = 1; kt = kq; }
+  if (kr > kt) { top = 2; kt = kr; }
+  if (ks > kt) { top = 3; kt = ks; }
+  switch (top) {
+    case 0: return orient3_exact(qx, qy, rx, ry, sx, sy);
+    case 1: return orient3_exact(rx, ry, px, py, sx, sy);
+    case 2: return orient3_exact(px, py, qx, qy, sx, sy);
+    default: return -orient3_exact(px, py, qx, qy, rx, ry);
+  }
+}
+
+}  // namespace cgk

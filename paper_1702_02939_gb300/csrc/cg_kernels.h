@@ -1,0 +1,117 @@
+// Kernel argument blocks and host-side launchers of the cellgb library.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cgk {
+
+struct Rep;
+struct Ctl;
+
+constexpr int kGeomThreads = 64;
+constexpr int kForceThreads = 128;
+constexpr int kTestThreads = 128;
+constexpr int kRepairWarps = 4;  // warps per repair block
+constexpr int kCand = 64;        // candidate buffer per repair warp
+
+struct GeomArgs {
+  int n;
+  const Rep* reps;
+  const int* rep;
+  Ctl* ctl;
+  const double *x, *y;  // [2][n] position buffers
+  const int *cnt, *nbr;
+  const double* p0;
+  double A0, sqrtA0, KA, KP;
+  double *A, *P;
+  double* energy_out;   // per-cell energy or nullptr
+  double2 *fs, *s, *w;  // [CG_RING][n]
+};
+
+struct ForceArgs {
+  int n;
+  const Rep* reps;
+  const int* rep;
+  Ctl* ctl;
+  const int *cnt, *nbr, *tag;
+  const double2 *fs, *s, *w;
+  double *Fx, *Fy;
+  int integrate;
+  double *x, *y;       // [2][n]
+  long long *X, *Y;    // [2][n]
+  double* theta;
+  const double* v0;
+  double mu, dt, noise_amp;
+  unsigned long long seed;
+};
+
+struct TestArgs {
+  int n;
+  const Rep* reps;
+  const int* rep;
+  Ctl* ctl;
+  const long long *X, *Y;  // [2][n]
+  const int *cnt, *nbr, *tag;
+  unsigned* flags;
+  int* list;  // list 0
+};
+
+struct CellListArgs {
+  int n, nbins;
+  const Rep* reps;
+  const int* rep;
+  Ctl* ctl;
+  const double *x, *y;  // [2][n]
+  int *bin_count, *bin_start, *cell_bin, *cell_rank, *ids;
+  int* scan_partials;
+  int only_if_flagged;  // skip when nothing is flagged
+};
+
+struct RepairArgs {
+  int n;
+  const Rep* reps;
+  const int* rep;
+  Ctl* ctl;
+  const double *x, *y;     // [2][n]
+  const long long *X, *Y;  // [2][n]
+  const int* tag;
+  const int *bin_start, *bin_partials, *ids;
+  int *cnt, *nbr;
+  int *old_cnt, *old_nbr;
+  unsigned* flags;
+  const int* list_in;
+  int which_in;  // count index of list_in
+  int all_cells; // process cells 0..n-1 instead of the list
+};
+
+struct CheckArgs {
+  int n;
+  Ctl* ctl;
+  const int *cnt, *nbr, *old_cnt, *old_nbr;
+  unsigned* flags;
+  const int* list_in;
+  int* list_out;
+  int which_in, which_out;
+  int last_round;  // raise REPAIR_CAP if anything is flagged
+  int all_cells;
+};
+
+void launch_geom(const GeomArgs& a, cudaStream_t st);
+void launch_force(const ForceArgs& a, cudaStream_t st);
+void launch_begin_topology(Ctl* ctl, int flip, cudaStream_t st);
+void launch_test(const TestArgs& a, cudaStream_t st);
+void launch_cell_list(const CellListArgs& a, cudaStream_t st);
+void launch_repair(const RepairArgs& a, int grid_blocks, cudaStream_t st);
+void launch_check(const CheckArgs& a, cudaStream_t st);
+
+// state preparation and user-order transfers
+void launch_snap(int n, const Rep* reps, const int* rep, const double* xin, const double* yin, double* x,
+                 double* y, long long* X, long long* Y, Ctl* ctl, cudaStream_t st);
+void launch_gather_d(int n, const int* tag, const double* src, double* dst_user, cudaStream_t st);
+void launch_scatter_d(int n, const int* tag, const double* src_user, double* dst, cudaStream_t st);
+void launch_gather_ring(int n, const int* tag, const int* cnt, const int* nbr, int* cnt_user, int* nbr_user,
+                        cudaStream_t st);
+void launch_reduce_sum(int n, const double* v, double* out, cudaStream_t st);
+
+}  // namespace cgk

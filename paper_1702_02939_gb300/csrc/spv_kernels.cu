@@ -1,0 +1,304 @@
+// SPV step kernels: geometry + force sets, net force + update, Delaunay test.
+//
+// Sussman, arXiv 1702.02939:
+//  * geometry of every cell from the circumcentres of its Delaunay triangles
+//    (Sec. 2.C.1); areas, perimeters, E of Eq. 1
+//  * "force sets" dE_c/dh per (cell, vertex) (Sec. 2.C.2, Eqs. A3-A5) and the
+//    net force F_i = -sum_t (dh_t/dr_i)^T G_t (Eqs. A6-A7)
+//  * displacement by Eq. 3 and director rotation (Sec. 2.C.3)
+//  * empty-circumcircle test of the triangulation (Sec. 2.C.3)
+//
+// GB300 design notes: the path is bound by the FP64 pipe (about 1/74 of the
+// FP32 rate), so FP64 is spent only on the physics.  The Jacobian dh/dr_i is
+// used in its rank-one form J = w u^T / det (u = h - r_i, w = perp(r_k - r_j),
+// det = (r_j - r_i) x (r_k - r_i)), which follows from differentiating the
+// equidistance conditions |h - r_i| = |h - r_j| = |h - r_k| and equals the
+// matrix of Eq. A16.  All predicates run on the FP32/integer pipes.
+#include "cg_device.cuh"
+#include "cg_kernels.h"
+
+namespace cgk {
+
+// One thread per cell.  Writes A, P, force sets fs[a][i] = dE_i/dh_a, and the
+// per-slot Jacobian factors s[a][i] = u_a / det_a and w[a][i].
+__global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
+  __shared__ double sh_hx[CG_RING][kGeomThreads];
+  __shared__ double sh_hy[CG_RING][kGeomThreads];
+  __shared__ double sh_il[CG_RING][kGeomThreads];
+  const int t = threadIdx.x;
+  const int i = blockIdx.x * kGeomThreads + t;
+  if (i >= g.n) return;
+  const int cur = g.ctl->cur;
+  const double* __restrict__ x = g.x + (size_t)cur * g.n;
+  const double* __restrict__ y = g.y + (size_t)cur * g.n;
+  const Rep R = g.reps[g.rep[i]];
+  const double xi = x[i], yi = y[i];
+  const int m = g.cnt[i];
+  if (m < 3 || m > CG_RING) {
+    raise_status(g.ctl, kETOPO);
+    return;
+  }
+  const int* ring = g.nbr + (size_t)i * CG_RING;
+  const size_t N = (size_t)g.n;
+
+  int j0 = ring[0];
+  const double d0x = min_image(x[j0] - xi, R.Lx, R.hLx);
+  const double d0y = min_image(y[j0] - yi, R.Ly, R.hLy);
+  const double l0 = d0x * d0x + d0y * d0y;
+  double ax = d0x, ay = d0y, la = l0;
+  double hpx = 0.0, hpy = 0.0, h0x = 0.0, h0y = 0.0;
+  double area = 0.0, per = 0.0;
+  for (int a = 0; a < m; ++a) {
+    double bx, by, lb;
+    if (a + 1 < m) {
+      int j = ring[a + 1];
+      bx = min_image(x[j] - xi, R.Lx, R.hLx);
+      by = min_image(y[j] - yi, R.Ly, R.hLy);
+      lb = bx * bx + by * by;
+    } else {
+      bx = d0x; by = d0y; lb = l0;
+    }
+    const double det = ax * by - ay * bx;  // (r_j - r_i) x (r_k - r_i)
+    const double inv = 1.0 / det;
+    // circumcentre relative to r_i
+    const double hx = 0.5 * (by * la - ay * lb) * inv;
+    const double hy = 0.5 * (ax * lb - bx * la) * inv;
+    g.s[a * N + i] = make_double2(hx * inv, hy * inv);
+    g.w[a * N + i] = make_double2(by - ay, ax - bx);
+    sh_hx[a][t] = hx;
+    sh_hy[a][t] = hy;
+    if (a == 0) {
+      h0x = hx; h0y = hy;
+    } else {
+      area += hpx * hy - hx * hpy;
+      const double ex = hx - hpx, ey = hy - hpy;
+      const double l2 = ex * ex + ey * ey;
+      const double il = rsqrt(l2);
+      per += l2 * il;
+      sh_il[a][t] = il;
+    }
+    hpx = hx; hpy = hy;
+    ax = bx; ay = by; la = lb;
+  }
+  {  // closing edge h_{m-1} -> h_0 is the incoming edge of vertex 0
+    area += hpx * h0y - h0x * hpy;
+    const double ex = h0x - hpx, ey = h0y - hpy;
+    const double l2 = ex * ex + ey * ey;
+    const double il = rsqrt(l2);
+    per += l2 * il;
+    sh_il[0][t] = il;
+  }
+  const double A = 0.5 * area, P = per;
+  g.A[i] = A;
+  g.P[i] = P;
+  const double dA = A - g.A0, dP = P - g.p0[i] * g.sqrtA0;
+  if (g.energy_out) g.energy_out[i] = g.KA * dA * dA + g.KP * dP * dP;
+  const double ka = 2.0 * g.KA * dA, kp = 2.0 * g.KP * dP;
+  for (int a = 0; a < m; ++a) {
+    const int ap = (a == 0) ? m - 1 : a - 1;
+    const int an = (a + 1 == m) ? 0 : a + 1;
+    const double hx = sh_hx[a][t], hy = sh_hy[a][t];
+    const double px = sh_hx[ap][t], py = sh_hy[ap][t];
+    const double nx = sh_hx[an][t], ny = sh_hy[an][t];
+    // dA/dh = 1/2 perp(h_next - h_prev); dP/dh = e_in - e_out (unit edge vectors)
+    const double dAx = 0.5 * (ny - py), dAy = 0.5 * (px - nx);
+    const double ilin = sh_il[a][t], ilout = sh_il[an][t];
+    const double dPx = (hx - px) * ilin - (nx - hx) * ilout;
+    const double dPy = (hy - py) * ilin - (ny - hy) * ilout;
+    g.fs[a * N + i] = make_double2(ka * dAx + kp * dPx, ka * dAy + kp * dPy);
+  }
+}
+
+// Position of cell i in the ring of cell j, or -1.
+__device__ __forceinline__ int ring_pos(const int* __restrict__ nbr, const int* __restrict__ cnt, int j, int i) {
+  const int4* row = reinterpret_cast<const int4*>(nbr + (size_t)j * CG_RING);
+  const int mj = cnt[j];
+  int pos = -1;
+#pragma unroll
+  for (int q = 0; q < CG_RING / 4; ++q) {
+    if (4 * q >= mj) break;
+    int4 v = row[q];
+    if (v.x == i && 4 * q + 0 < mj) pos = 4 * q + 0;
+    if (v.y == i && 4 * q + 1 < mj) pos = 4 * q + 1;
+    if (v.z == i && 4 * q + 2 < mj) pos = 4 * q + 2;
+    if (v.w == i && 4 * q + 3 < mj) pos = 4 * q + 3;
+  }
+  return pos;
+}
+
+// One thread per cell: G_t = sum over the triangle's three cells of their force
+// sets, F_i = -sum_t s_t (w_t . G_t); then (optionally) the update of Eq. 3.
+__global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
+  const int i = blockIdx.x * kForceThreads + threadIdx.x;
+  if (i >= g.n) return;
+  const size_t N = (size_t)g.n;
+  const int m = g.cnt[i];
+  if (m < 3 || m > CG_RING) {
+    raise_status(g.ctl, kETOPO);
+    return;
+  }
+  const int* ring = g.nbr + (size_t)i * CG_RING;
+  int jfirst = ring[0];
+  int pfirst = ring_pos(g.nbr, g.cnt, jfirst, i);
+  int j = jfirst, pj = pfirst;
+  double fx = 0.0, fy = 0.0;
+  bool bad = pfirst < 0;
+  for (int a = 0; a < m; ++a) {
+    int k, pk;
+    if (a + 1 < m) {
+      k = ring[a + 1];
+      pk = ring_pos(g.nbr, g.cnt, k, i);
+      bad |= pk < 0;
+    } else {
+      k = jfirst;
+      pk = pfirst;
+    }
+    // triangle (i, j, k) is slot pj-1 around j and slot pk around k
+    const int mj = g.cnt[j];
+    const int bj = (pj <= 0) ? (mj > 0 ? mj - 1 : 0) : pj - 1;
+    const double2 f0 = g.fs[a * N + i];
+    const double2 f1 = g.fs[(size_t)bj * N + j];
+    const double2 f2 = g.fs[(size_t)(pk < 0 ? 0 : pk) * N + k];
+    const double Gx = f0.x + f1.x + f2.x, Gy = f0.y + f1.y + f2.y;
+    const double2 s = g.s[a * N + i], w = g.w[a * N + i];
+    const double c = w.x * Gx + w.y * Gy;
+    fx -= s.x * c;
+    fy -= s.y * c;
+    j = k;
+    pj = pk;
+  }
+  if (bad) raise_status(g.ctl, kETOPO);
+  g.Fx[i] = fx;
+  g.Fy[i] = fy;
+  if (!g.integrate) return;
+
+  // Eq. 3: r <- r + dt (mu F + v0 n(theta)), snapped to the grid and wrapped;
+  // theta <- theta + sqrt(2 D_r dt) xi.
+  const int cur = g.ctl->cur;
+  const Rep R = g.reps[g.rep[i]];
+  const double xi = g.x[(size_t)cur * N + i], yi = g.y[(size_t)cur * N + i];
+  const double th = g.theta[i];
+  double sn, cs;
+  sincos(th, &sn, &cs);
+  const double v0 = g.v0[i];
+  const double vx = g.mu * fx + v0 * cs, vy = g.mu * fy + v0 * sn;
+  const double xn = xi + g.dt * vx, yn = yi + g.dt * vy;
+  long long X, Y;
+  if (xn > -R.Lx && xn < 2.0 * R.Lx && yn > -R.Ly && yn < 2.0 * R.Ly) {  // also false for NaN
+    X = (long long)rint(xn * R.scale);
+    Y = (long long)rint(yn * R.scale);
+    if (X >= R.LX) X -= R.LX;
+    else if (X < 0) X += R.LX;
+    if (Y >= R.LY) Y -= R.LY;
+    else if (Y < 0) Y += R.LY;
+  } else {
+    raise_status(g.ctl, kENONFINITE);
+    X = (long long)rint(xi * R.scale);
+    Y = (long long)rint(yi * R.scale);
+  }
+  const int nxt = cur ^ 1;
+  g.x[(size_t)nxt * N + i] = (double)X * R.inv_scale;
+  g.y[(size_t)nxt * N + i] = (double)Y * R.inv_scale;
+  g.X[(size_t)nxt * N + i] = X;
+  g.Y[(size_t)nxt * N + i] = Y;
+  const long long step = g.ctl->step;
+  g.theta[i] = th + g.noise_amp * director_noise(g.seed, g.tag[i], step);
+}
+
+// Start of the topology phase of a step: the new positions become current,
+// the step counter advances and the flagged list is emptied.
+__global__ void k_begin_topology(Ctl* ctl, int flip) {
+  if (flip) {
+    ctl->cur ^= 1;
+    ctl->step += 1;
+  }
+  ctl->count[0] = 0;
+  ctl->count[1] = 0;
+  ctl->round_count = 0;
+}
+
+__device__ __forceinline__ void flag_cell(unsigned* flags, int* list, int* count, int c) {
+  const unsigned bit = 1u << (c & 31);
+  const unsigned old = atomicOr(&flags[c >> 5], bit);
+  if (!(old & bit)) list[atomicAdd(count, 1)] = c;
+}
+
+// One thread per cell: every edge (i, j_a) with i < j_a must be locally
+// Delaunay (the far vertex j_{a+1} outside the circle through i, j_{a-1}, j_a)
+// and every triangle owned by i (i its smallest index) positively oriented.
+// Failing quadruples/triangles flag all their cells.
+__global__ void __launch_bounds__(kTestThreads) k_test(TestArgs g) {
+  const int i = blockIdx.x * kTestThreads + threadIdx.x;
+  if (i >= g.n) return;
+  const size_t N = (size_t)g.n;
+  const int cur = g.ctl->cur;
+  const long long* __restrict__ X = g.X + (size_t)cur * N;
+  const long long* __restrict__ Y = g.Y + (size_t)cur * N;
+  const Rep R = g.reps[g.rep[i]];
+  const float sc = (float)R.inv_scale;
+  const long long Xi = X[i], Yi = Y[i];
+  const int m = g.cnt[i];
+  if (m < 3 || m > CG_RING) {
+    raise_status(g.ctl, kETOPO);
+    return;
+  }
+  const int* ring = g.nbr + (size_t)i * CG_RING;
+  const int ti = g.tag[i];
+  // sliding window over (j_{a-1}, j_a, j_{a+1})
+  int jp = ring[m - 1], ja = ring[0];
+  long long pX = min_image_i(X[jp] - Xi, R.LX), pY = min_image_i(Y[jp] - Yi, R.LY);
+  long long aX = min_image_i(X[ja] - Xi, R.LX), aY = min_image_i(Y[ja] - Yi, R.LY);
+  const long long fX = aX, fY = aY;
+  const int jfirst = ja;
+  int tp = g.tag[jp], ta = g.tag[ja];
+  for (int a = 0; a < m; ++a) {
+    int jn;
+    long long nX, nY;
+    if (a + 1 < m) {
+      jn = ring[a + 1];
+      nX = min_image_i(X[jn] - Xi, R.LX);
+      nY = min_image_i(Y[jn] - Yi, R.LY);
+    } else {
+      jn = jfirst; nX = fX; nY = fY;
+    }
+    const int tn = g.tag[jn];
+    if (i < ja) {
+      // triangle (i, j_{a-1}, j_a) CCW; j_{a+1} must be outside its circle
+      int s = incircle_sign(0, 0, pX, pY, aX, aY, nX, nY, ti, tp, ta, tn, sc);
+      if (s > 0) {
+        flag_cell(g.flags, g.list, &g.ctl->count[0], i);
+        flag_cell(g.flags, g.list, &g.ctl->count[0], jp);
+        flag_cell(g.flags, g.list, &g.ctl->count[0], ja);
+        flag_cell(g.flags, g.list, &g.ctl->count[0], jn);
+      }
+    }
+    if (i < ja && i < jn) {
+      if (orient_sign(aX, aY, nX, nY, sc) <= 0) {
+        flag_cell(g.flags, g.list, &g.ctl->count[0], i);
+        flag_cell(g.flags, g.list, &g.ctl->count[0], ja);
+        flag_cell(g.flags, g.list, &g.ctl->count[0], jn);
+      }
+    }
+    jp = ja; pX = aX; pY = aY; tp = ta;
+    ja = jn; aX = nX; aY = nY; ta = tn;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers
+// ---------------------------------------------------------------------------
+void launch_geom(const GeomArgs& a, cudaStream_t st) {
+  if (a.n <= 0) return;
+  k_geom<<<(a.n + kGeomThreads - 1) / kGeomThreads, kGeomThreads, 0, st>>>(a);
+}
+void launch_force(const ForceArgs& a, cudaStream_t st) {
+  if (a.n <= 0) return;
+  k_force<<<(a.n + kForceThreads - 1) / kForceThreads, kForceThreads, 0, st>>>(a);
+}
+void launch_begin_topology(Ctl* ctl, int flip, cudaStream_t st) { k_begin_topology<<<1, 1, 0, st>>>(ctl, flip); }
+void launch_test(const TestArgs& a, cudaStream_t st) {
+  if (a.n <= 0) return;
+  k_test<<<(a.n + kTestThreads - 1) / kTestThreads, kTestThreads, 0, st>>>(a);
+}
+
+}  // namespace cgk

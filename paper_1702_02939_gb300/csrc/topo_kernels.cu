@@ -1,0 +1,560 @@
+// Topology maintenance: cell list, local repair by Voronoi-cell clipping and
+// the ring-consistency check.
+//
+// The paper repairs flagged cells on the CPU: a candidate "Delaunay 1-ring"
+// from the locality lemma of Chen et al., reduced to the true neighbours with
+// CGAL (Sussman, arXiv 1702.02939, Sec. 2.C.4).  Here the repair stays on the
+// GPU: each flagged cell's Voronoi polygon is rebuilt by clipping a large
+// square with the bisectors of nearby cells taken from a periodic cell list,
+// nearest first.  A polygon vertex v_a (circumcentre of i, g_a, g_{a+1})
+// is cut away by candidate j exactly when j lies inside the circle through
+// (i, g_a, g_{a+1}), so every keep/drop decision is the exact, perturbed
+// in-circle predicate and the result is the exact Delaunay ring of i.  The
+// search stops once every unvisited cell is farther than twice the polygon's
+// circumradius (the security radius), which is the locality argument of the
+// paper in its simplest form.
+#include "cg_device.cuh"
+#include "cg_kernels.h"
+
+#include <climits>
+
+namespace cgk {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 8;
+constexpr int kScanChunk = kScanThreads * kScanPer;  // bins per scan block
+
+__device__ __forceinline__ void bin_of(const Rep& R, double x, double y, int& bx, int& by) {
+  bx = (int)(x / R.bsx);
+  by = (int)(y / R.bsy);
+  bx = bx < 0 ? 0 : (bx >= R.nbx ? R.nbx - 1 : bx);
+  by = by < 0 ? 0 : (by >= R.nby ? R.nby - 1 : by);
+}
+
+// bin_start is stored as a block-local exclusive prefix plus one offset per
+// scan block; the global start of bin b is their sum.
+__device__ __forceinline__ int bin_begin(const int* local, const int* partial, int b) {
+  return local[b] + partial[b / kScanChunk];
+}
+
+__global__ void k_bin_count(CellListArgs g) {
+  if (g.only_if_flagged && g.ctl->count[0] == 0) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  const int cur = g.ctl->cur;
+  const Rep R = g.reps[g.rep[i]];
+  int bx, by;
+  bin_of(R, g.x[(size_t)cur * g.n + i], g.y[(size_t)cur * g.n + i], bx, by);
+  const int b = R.bin0 + by * R.nbx + bx;
+  g.cell_bin[i] = b;
+  g.cell_rank[i] = atomicAdd(&g.bin_count[b], 1);
+}
+
+// Block-local exclusive scan of bin counts; block totals to scan_partials.
+__global__ void __launch_bounds__(kScanThreads) k_scan_local(CellListArgs g) {
+  if (g.only_if_flagged && g.ctl->count[0] == 0) return;
+  __shared__ int warp_tot[kScanThreads / 32];
+  const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+  int v[kScanPer];
+  int sum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    int b = base + k;
+    v[k] = (b < g.nbins) ? g.bin_count[b] : 0;
+    sum += v[k];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  int woff = 0;
+  for (int w = 0; w < wid; ++w) woff += warp_tot[w];
+  int run = woff + incl - sum;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    int b = base + k;
+    if (b < g.nbins) g.bin_start[b] = run;
+    else if (b == g.nbins) g.bin_start[b] = run;  // sentinel
+    run += v[k];
+  }
+  if (threadIdx.x == kScanThreads - 1) {
+    int tot = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) tot += warp_tot[w];
+    g.scan_partials[blockIdx.x] = tot;
+  }
+}
+
+// Exclusive scan of the block totals (one block); also records step statistics.
+__global__ void __launch_bounds__(1024) k_scan_partials(CellListArgs g, int nblocks) {
+  Ctl* ctl = g.ctl;
+  if (threadIdx.x == 0) {
+    int c = ctl->count[0];
+    ctl->last_flagged = c;
+    ctl->flagged_total += c;
+  }
+  if (g.only_if_flagged && ctl->count[0] == 0) return;
+  __shared__ int buf[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base <= nblocks; base += 1024) {
+    int idx = base + threadIdx.x;
+    int v = (idx < nblocks) ? g.scan_partials[idx] : 0;
+    buf[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      int t = (threadIdx.x >= o) ? buf[threadIdx.x - o] : 0;
+      __syncthreads();
+      buf[threadIdx.x] += t;
+      __syncthreads();
+    }
+    int excl = carry + buf[threadIdx.x] - v;
+    __syncthreads();
+    if (idx < nblocks) g.scan_partials[idx] = excl;
+    else if (idx == nblocks) g.scan_partials[idx] = excl;  // total
+    if (threadIdx.x == 1023) carry += buf[1023];
+    __syncthreads();
+  }
+}
+
+__global__ void k_bin_scatter(CellListArgs g) {
+  if (g.only_if_flagged && g.ctl->count[0] == 0) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  const int b = g.cell_bin[i];
+  g.ids[bin_begin(g.bin_start, g.scan_partials, b) + g.cell_rank[i]] = i;
+  g.bin_count[b] = 0;  // ready for the next build
+}
+
+void launch_cell_list(const CellListArgs& a, cudaStream_t st) {
+  if (a.n <= 0) return;
+  const int nblk = (a.nbins + 1 + kScanChunk - 1) / kScanChunk;
+  k_bin_count<<<(a.n + 255) / 256, 256, 0, st>>>(a);
+  k_scan_local<<<nblk, kScanThreads, 0, st>>>(a);
+  k_scan_partials<<<1, 1024, 0, st>>>(a, nblk);
+  k_bin_scatter<<<(a.n + 255) / 256, 256, 0, st>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// Repair: one warp per cell.
+// ---------------------------------------------------------------------------
+
+// Circumcentre of (0, a, b) in real units (for the security radius only).
+__device__ __forceinline__ void circ_rel(long long aX, long long aY, long long bX, long long bY, double inv_scale,
+                                         double& vx, double& vy) {
+  // exact determinant in grid units^2, then rounded
+  s128 D = (s128)aX * bY - (s128)aY * bX;
+  long long dhi = (long long)(D >> 64);
+  unsigned long long dlo = (unsigned long long)D;
+  double det = ((double)dhi * 0x1.0p64 + (double)dlo) * inv_scale * inv_scale;
+  double ax = (double)aX * inv_scale, ay = (double)aY * inv_scale;
+  double bx = (double)bX * inv_scale, by = (double)bY * inv_scale;
+  double la = ax * ax + ay * ay, lb = bx * bx + by * by;
+  if (det == 0.0) {
+    vx = vy = 1e300;
+    return;
+  }
+  double inv = 0.5 / det;
+  vx = (by * la - ay * lb) * inv;
+  vy = (ax * lb - bx * la) * inv;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// (dx, dy) of the idx-th bin on the Chebyshev ring k around the origin bin.
+__device__ __forceinline__ void ring_bin(int k, int idx, int& dx, int& dy) {
+  if (k == 0) { dx = 0; dy = 0; return; }
+  const int side = 2 * k;  // bins per side, walking CCW from (-k, -k)
+  const int s = idx / side, t = idx % side;
+  switch (s) {
+    case 0: dx = -k + t; dy = -k; break;
+    case 1: dx = k; dy = -k + t; break;
+    case 2: dx = k - t; dy = k; break;
+    default: dx = -k; dy = k - t; break;
+  }
+}
+
+struct Poly {
+  long long gX, gY;  // this lane's generator (grid units, relative to the cell)
+  int gid, gkey;     // generator cell index (phantoms < 0) and perturbation key
+  double vx, vy;     // vertex between this generator and the next
+  int m;             // generators in use (warp-uniform)
+  double R2;         // max |v|^2 (warp-uniform)
+  int err;
+};
+
+constexpr int kPhantomKey = INT_MAX - 8;
+constexpr double kSelfKey = 1e307;  // sort key of the cell itself
+constexpr double kPadKey = 1e308;   // sort key of unused buffer slots
+
+// Clip the polygon by the bisector of candidate j.
+__device__ __forceinline__ void clip(Poly& p, long long jX, long long jY, int jid, int jkey, int ikey, float sc,
+                                     double inv_scale, int lane) {
+  const int m = p.m;
+  const int nl = (lane + 1 == m) ? 0 : (lane + 1) % 32;
+  const long long nX = __shfl_sync(0xffffffffu, p.gX, nl);
+  const long long nY = __shfl_sync(0xffffffffu, p.gY, nl);
+  const int nkey = __shfl_sync(0xffffffffu, p.gkey, nl);
+  int rem = 0;
+  if (lane < m) rem = incircle_sign(0, 0, p.gX, p.gY, nX, nY, jX, jY, ikey, p.gkey, nkey, jkey, sc) > 0;
+  const unsigned mask = __ballot_sync(0xffffffffu, rem);
+  if (mask == 0) return;
+  const int r = __popc(mask);
+  if (r == m) { p.err = kEDEGEN; return; }
+  const int pl = (lane == 0) ? m - 1 : lane - 1;
+  const int prevrem = (mask >> pl) & 1;
+  const unsigned smask = __ballot_sync(0xffffffffu, lane < m && rem && !prevrem);
+  if (__popc(smask) != 1) { p.err = kEDEGEN; return; }
+  const int s = __ffs(smask) - 1;
+  const int e = (s + r - 1) % m;
+  const int m2 = m - r + 2;
+  if (m2 > 32) { p.err = kERING; return; }
+  const int src = (lane + e + 1) % m;
+  long long ngX = __shfl_sync(0xffffffffu, p.gX, src);
+  long long ngY = __shfl_sync(0xffffffffu, p.gY, src);
+  int ngid = __shfl_sync(0xffffffffu, p.gid, src);
+  int ngkey = __shfl_sync(0xffffffffu, p.gkey, src);
+  double nvx = __shfl_sync(0xffffffffu, p.vx, src);
+  double nvy = __shfl_sync(0xffffffffu, p.vy, src);
+  if (lane == m2 - 1) { ngX = jX; ngY = jY; ngid = jid; ngkey = jkey; }
+  p.gX = ngX; p.gY = ngY; p.gid = ngid; p.gkey = ngkey; p.vx = nvx; p.vy = nvy;
+  p.m = m2;
+  const int nl2 = (lane + 1 == m2) ? 0 : (lane + 1) % 32;
+  const long long n2X = __shfl_sync(0xffffffffu, p.gX, nl2);
+  const long long n2Y = __shfl_sync(0xffffffffu, p.gY, nl2);
+  if (lane == m2 - 2 || lane == m2 - 1) circ_rel(p.gX, p.gY, n2X, n2Y, inv_scale, p.vx, p.vy);
+  const double v2 = (lane < m2) ? p.vx * p.vx + p.vy * p.vy : 0.0;
+  p.R2 = warp_max(v2);
+}
+
+// Sort the warp's candidate buffer by squared distance (bitonic, 64 entries)
+// and clip with every candidate that can still reach the polygon.
+__device__ void process_candidates(Poly& p, int nbuf, int* s_id, long long* s_X, long long* s_Y, double* s_d2,
+                                   double* s_key, int* s_val, const int* tag, int ikey, float sc, double inv_scale,
+                                   int lane) {
+  if (nbuf == 0) return;
+  for (int q = lane; q < kCand; q += 32) {
+    s_key[q] = (q < nbuf) ? s_d2[q] : kPadKey;
+    s_val[q] = q;
+  }
+  __syncwarp();
+  for (int k = 2; k <= kCand; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int q = lane; q < kCand; q += 32) {
+        int partner = q ^ jj;
+        if (partner > q) {
+          bool up = (q & k) == 0;
+          double a = s_key[q], b = s_key[partner];
+          if ((a > b) == up) {
+            s_key[q] = b; s_key[partner] = a;
+            int t = s_val[q]; s_val[q] = s_val[partner]; s_val[partner] = t;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  for (int c = 0; c < nbuf; ++c) {
+    const double d2 = s_key[c];
+    if (d2 >= kSelfKey) break;  // the cell itself and padding sort last
+    // a cell can cut the polygon only if it is nearer than twice its circumradius
+    if (d2 > 4.0 * p.R2 * (1.0 + 1e-3)) break;
+    const int e = s_val[c];
+    const int jid = s_id[e];
+    clip(p, s_X[e], s_Y[e], jid, tag[jid], ikey, sc, inv_scale, lane);
+    if (p.err) break;
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
+  __shared__ int s_id[kRepairWarps][kCand];
+  __shared__ long long s_X[kRepairWarps][kCand], s_Y[kRepairWarps][kCand];
+  __shared__ double s_d2[kRepairWarps][kCand];
+  __shared__ double s_key[kRepairWarps][kCand];
+  __shared__ int s_val[kRepairWarps][kCand];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * kRepairWarps + wib, nw = gridDim.x * kRepairWarps;
+  const int total = g.all_cells ? g.n : g.ctl->count[g.which_in];
+  // the list this round's check fills must start empty
+  if (!g.all_cells && blockIdx.x == 0 && threadIdx.x == 0) g.ctl->count[g.which_in ^ 1] = 0;
+  if (total == 0) return;
+  const int cur = g.ctl->cur;
+  const size_t N = (size_t)g.n;
+  const long long* __restrict__ X = g.X + cur * N;
+  const long long* __restrict__ Y = g.Y + cur * N;
+  const double* __restrict__ x = g.x + cur * N;
+  const double* __restrict__ y = g.y + cur * N;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && !g.all_cells) {
+    atomicAdd(&g.ctl->round_count, 1);
+    atomicAdd((unsigned long long*)&g.ctl->repaired_total, (unsigned long long)total);
+  }
+
+  for (int item = gw; item < total; item += nw) {
+    const int i = g.all_cells ? item : g.list_in[item];
+    const Rep R = g.reps[g.rep[i]];
+    const long long Xi = X[i], Yi = Y[i];
+    const int ikey = g.tag[i];
+    const float sc = (float)R.inv_scale;
+    // keep the old ring for the consistency check
+    const int oc = g.cnt[i];
+    if (lane < CG_RING) g.old_nbr[(size_t)i * CG_RING + lane] = g.nbr[(size_t)i * CG_RING + lane];
+    if (lane == 0) g.old_cnt[i] = oc;
+
+    // initial polygon: the square of half-width W, cut out by four phantom
+    // generators at (+-2W, 0) and (0, +-2W)
+    Poly p;
+    p.m = 4;
+    p.err = 0;
+    p.gX = (lane == 0) ? R.W2 : (lane == 2 ? -R.W2 : 0);
+    p.gY = (lane == 1) ? R.W2 : (lane == 3 ? -R.W2 : 0);
+    p.gid = -1 - (lane & 3);
+    p.gkey = kPhantomKey + (lane & 3);
+    {
+      const int nl = (lane + 1) & 3;
+      const long long nX = __shfl_sync(0xffffffffu, p.gX, nl), nY = __shfl_sync(0xffffffffu, p.gY, nl);
+      circ_rel(p.gX, p.gY, nX, nY, R.inv_scale, p.vx, p.vy);
+      p.R2 = warp_max(lane < 4 ? p.vx * p.vx + p.vy * p.vy : 0.0);
+    }
+    int bxi, byi;
+    bin_of(R, x[i], y[i], bxi, byi);
+    const double bs = fmin(R.bsx, R.bsy);
+    const int kmax = min((R.nbx - 1) / 2, (R.nby - 1) / 2);
+    int nbuf = 0;
+    bool done = false;
+    for (int k = 0; k <= kmax && !done && !p.err; ++k) {
+      const int nring = (k == 0) ? 1 : 8 * k;
+      for (int base = 0; base < nring && !p.err; base += 32) {
+        const int idx = base + lane;
+        int start = 0, count = 0;
+        if (idx < nring) {
+          int dx, dy;
+          ring_bin(k, idx, dx, dy);
+          int bx = bxi + dx, by = byi + dy;
+          bx += (bx < 0) ? R.nbx : (bx >= R.nbx ? -R.nbx : 0);
+          by += (by < 0) ? R.nby : (by >= R.nby ? -R.nby : 0);
+          const int b = R.bin0 + by * R.nbx + bx;
+          start = bin_begin(g.bin_start, g.bin_partials, b);
+          count = bin_begin(g.bin_start, g.bin_partials, b + 1) - start;
+        }
+        int incl = count;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (nbuf + tot > kCand) {
+          process_candidates(p, nbuf, s_id[wib], s_X[wib], s_Y[wib], s_d2[wib], s_key[wib], s_val[wib], g.tag,
+                             ikey, sc, R.inv_scale, lane);
+          nbuf = 0;
+          if (tot > kCand) p.err = kECAND;
+        }
+        if (!p.err) {
+          int slot = nbuf + incl - count;
+          for (int t = 0; t < count; ++t) {
+            const int j = g.ids[start + t];
+            if (j == i) {
+              s_d2[wib][slot] = kSelfKey;  // never clips
+              s_id[wib][slot] = j;
+              s_X[wib][slot] = 0;
+              s_Y[wib][slot] = 0;
+            } else {
+              const long long dX = min_image_i(X[j] - Xi, R.LX), dY = min_image_i(Y[j] - Yi, R.LY);
+              const double dx = (double)dX * R.inv_scale, dy = (double)dY * R.inv_scale;
+              s_d2[wib][slot] = dx * dx + dy * dy;
+              s_id[wib][slot] = j;
+              s_X[wib][slot] = dX;
+              s_Y[wib][slot] = dY;
+            }
+            ++slot;
+          }
+          nbuf += tot;
+        }
+        __syncwarp();
+      }
+      if (p.err) break;
+      process_candidates(p, nbuf, s_id[wib], s_X[wib], s_Y[wib], s_d2[wib], s_key[wib], s_val[wib], g.tag, ikey,
+                         sc, R.inv_scale, lane);
+      nbuf = 0;
+      // every unvisited cell is farther than k*bs from cell i
+      const double reach = k * bs;
+      if (reach * reach > 4.0 * p.R2 * (1.0 + 1e-3)) done = true;
+    }
+    int err = p.err;
+    if (!err && !done) err = kEBOX;
+    if (!err) {
+      const unsigned ph = __ballot_sync(0xffffffffu, lane < p.m && p.gid < 0);
+      if (ph) err = kEBOX;
+      if (p.m > CG_RING) err = kERING;
+    }
+    if (err) {
+      if (lane == 0) raise_status(g.ctl, err);
+      continue;
+    }
+    // canonical CCW ring: start at the smallest tag
+    int kmin = (lane < p.m) ? p.gkey : INT_MAX;
+    int lmin = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int ok = __shfl_xor_sync(0xffffffffu, kmin, o);
+      const int ol = __shfl_xor_sync(0xffffffffu, lmin, o);
+      if (ok < kmin || (ok == kmin && ol < lmin)) { kmin = ok; lmin = ol; }
+    }
+    if (lane < p.m) {
+      const int slot = (lane - lmin + p.m) % p.m;
+      g.nbr[(size_t)i * CG_RING + slot] = p.gid;
+    } else if (lane < CG_RING) {
+      g.nbr[(size_t)i * CG_RING + lane] = -1;
+    }
+    if (lane == 0) {
+      g.cnt[i] = p.m;
+      atomicAnd(&g.flags[i >> 5], ~(1u << (i & 31)));
+    }
+  }
+}
+
+void launch_repair(const RepairArgs& a, int grid_blocks, cudaStream_t st) {
+  if (a.n <= 0) return;
+  k_repair<<<grid_blocks, kRepairWarps * 32, 0, st>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// Ring consistency after a repair round: j in ring(i) <=> i in ring(j).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool in_ring(const int* nbr, const int* cnt, int j, int i) {
+  const int mj = cnt[j];
+  const int* row = nbr + (size_t)j * CG_RING;
+  for (int a = 0; a < mj; ++a)
+    if (row[a] == i) return true;
+  return false;
+}
+
+__device__ __forceinline__ void flag_into(unsigned* flags, int* list, int* count, int c) {
+  const unsigned bit = 1u << (c & 31);
+  const unsigned old = atomicOr(&flags[c >> 5], bit);
+  if (!(old & bit)) list[atomicAdd(count, 1)] = c;
+}
+
+__global__ void k_check(CheckArgs g) {
+  const int total = g.all_cells ? g.n : g.ctl->count[g.which_in];
+  const int item = blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= total) return;
+  const int i = g.all_cells ? item : g.list_in[item];
+  int* count_out = &g.ctl->count[g.which_out];
+  const int m = g.cnt[i];
+  const int* row = g.nbr + (size_t)i * CG_RING;
+  bool bad = false;
+  for (int a = 0; a < m; ++a) {
+    const int j = row[a];
+    if (!in_ring(g.nbr, g.cnt, j, i)) {
+      flag_into(g.flags, g.list_out, count_out, j);
+      bad = true;
+    }
+  }
+  const int om = g.old_cnt[i];
+  const int* orow = g.old_nbr + (size_t)i * CG_RING;
+  for (int b = 0; b < om; ++b) {
+    const int j = orow[b];
+    if (j < 0 || j >= g.n) continue;
+    bool kept = false;
+    for (int a = 0; a < m; ++a) kept |= (row[a] == j);
+    if (!kept && in_ring(g.nbr, g.cnt, j, i)) {
+      flag_into(g.flags, g.list_out, count_out, j);
+      bad = true;
+    }
+  }
+  if (bad && g.last_round) raise_status(g.ctl, kEREPAIR_CAP);
+}
+
+void launch_check(const CheckArgs& a, cudaStream_t st) {
+  if (a.n <= 0) return;
+  // sized for the worst case; threads beyond the device-side count exit
+  k_check<<<(a.n + 255) / 256, 256, 0, st>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// State preparation and user-order transfers.
+// ---------------------------------------------------------------------------
+__global__ void k_snap(int n, const Rep* reps, const int* rep, const double* xin, const double* yin, double* x,
+                       double* y, long long* X, long long* Y, Ctl* ctl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Rep R = reps[rep[i]];
+  const double xv = xin[i], yv = yin[i];
+  if (!(xv >= -R.Lx && xv < 2.0 * R.Lx && yv >= -R.Ly && yv < 2.0 * R.Ly)) {
+    raise_status(ctl, kEINVAL);
+    x[i] = y[i] = 0.0;
+    X[i] = Y[i] = 0;
+    return;
+  }
+  long long Xv = (long long)rint(xv * R.scale), Yv = (long long)rint(yv * R.scale);
+  if (Xv >= R.LX) Xv -= R.LX; else if (Xv < 0) Xv += R.LX;
+  if (Yv >= R.LY) Yv -= R.LY; else if (Yv < 0) Yv += R.LY;
+  X[i] = Xv;
+  Y[i] = Yv;
+  x[i] = (double)Xv * R.inv_scale;
+  y[i] = (double)Yv * R.inv_scale;
+}
+
+void launch_snap(int n, const Rep* reps, const int* rep, const double* xin, const double* yin, double* x, double* y,
+                 long long* X, long long* Y, Ctl* ctl, cudaStream_t st) {
+  if (n <= 0) return;
+  k_snap<<<(n + 255) / 256, 256, 0, st>>>(n, reps, rep, xin, yin, x, y, X, Y, ctl);
+}
+
+__global__ void k_gather_d(int n, const int* tag, const double* src, double* dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[tag[i]] = src[i];
+}
+__global__ void k_scatter_d(int n, const int* tag, const double* src, double* dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[tag[i]];
+}
+__global__ void k_gather_ring(int n, const int* tag, const int* cnt, const int* nbr, int* cnt_u, int* nbr_u) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int t = tag[i], m = cnt[i];
+  cnt_u[t] = m;
+  for (int a = 0; a < CG_RING; ++a) {
+    const int j = (a < m) ? nbr[(size_t)i * CG_RING + a] : -1;
+    nbr_u[(size_t)t * CG_RING + a] = (j >= 0 && j < n) ? tag[j] : -1;
+  }
+}
+__global__ void __launch_bounds__(1024) k_reduce_sum(int n, const double* v, double* out) {
+  __shared__ double buf[1024];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 1024) s += v[i];
+  buf[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 512; o > 0; o >>= 1) {
+    if (threadIdx.x < o) buf[threadIdx.x] += buf[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = buf[0];
+}
+
+void launch_gather_d(int n, const int* tag, const double* src, double* dst_user, cudaStream_t st) {
+  if (n > 0) k_gather_d<<<(n + 255) / 256, 256, 0, st>>>(n, tag, src, dst_user);
+}
+void launch_scatter_d(int n, const int* tag, const double* src_user, double* dst, cudaStream_t st) {
+  if (n > 0) k_scatter_d<<<(n + 255) / 256, 256, 0, st>>>(n, tag, src_user, dst);
+}
+void launch_gather_ring(int n, const int* tag, const int* cnt, const int* nbr, int* cnt_user, int* nbr_user,
+                        cudaStream_t st) {
+  if (n > 0) k_gather_ring<<<(n + 255) / 256, 256, 0, st>>>(n, tag, cnt, nbr, cnt_user, nbr_user);
+}
+void launch_reduce_sum(int n, const double* v, double* out, cudaStream_t st) {
+  k_reduce_sum<<<1, 1024, 0, st>>>(n, v, out);
+}
+
+}  // namespace cgk

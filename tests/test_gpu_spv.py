@@ -1,0 +1,179 @@
+"""GPU parity of the SPV path against the CPU oracle, through the C ABI.
+
+Sussman, arXiv 1702.02939: topology (Sec. 2.C.3-4) must be bit-exact from the
+same state; forces (Eqs. A6-A16) within 1e-10 of max|F|; positions after one
+step (Eq. 3) within 1e-12 L.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1702_02939_gb300 as cg  # noqa: E402  (fails loudly if the library is missing)
+
+F_TOL = 1e-10
+X_TOL = 1e-12
+
+
+def make(n, iseed, p0=3.8, v0=0.05, L=None, **kw):
+    x, y, th, Lr = workloads.spv_uniform(n, iseed, L)
+    Lx, Ly, q = oracle.box(Lr)
+    xs, ys = oracle.snap_positions(x, y, Lx, Ly)
+    sim = cg.SPV([dict(n=n, Lx=Lr, Ly=Lr, p0=p0, v0=v0)], xs, ys, th, **kw)
+    return sim, xs, ys, th, Lx, Ly
+
+
+def wrapdiff(a, b, L):
+    return (a - b + L / 2) % L - L / 2
+
+
+def check_topology(sim, xs, ys, Lx, Ly):
+    cnt, nbr = sim.neighbors()
+    topo = oracle.triangulate(xs, ys, Lx, Ly)
+    np.testing.assert_array_equal(cnt.cpu().numpy(), topo.cnt)
+    np.testing.assert_array_equal(nbr.cpu().numpy(), topo.nbr)
+    # the library uses minimum-image neighbours: the oracle's image offsets must agree
+    n = len(xs)
+    for i in range(0, n, max(1, n // 500)):
+        for a in range(topo.cnt[i]):
+            j = topo.nbr[i, a]
+            dx = xs[j] + topo.off[i, a, 0] * Lx - xs[i]
+            dy = ys[j] + topo.off[i, a, 1] * Ly - ys[i]
+            assert abs(dx) < Lx / 2 and abs(dy) < Ly / 2
+    return topo
+
+
+@pytest.mark.parametrize("n,seed", [(64, 1), (400, 2), (1000, 3), (4096, 4)])
+def test_initial_triangulation_bit_exact(n, seed):
+    sim, xs, ys, th, Lx, Ly = make(n, seed)
+    check_topology(sim, xs, ys, Lx, Ly)
+    sim.close()
+
+
+@pytest.mark.parametrize("n,seed,p0", [(400, 5, 3.8), (4096, 6, 3.85), (1000, 7, 4.1)])
+def test_geometry_and_forces(n, seed, p0):
+    sim, xs, ys, th, Lx, Ly = make(n, seed, p0=p0)
+    topo = check_topology(sim, xs, ys, Lx, Ly)
+    A, P = sim.geometry()
+    Fx, Fy, E = sim.forces()
+    oFx, oFy, oA, oP, oE = oracle.forces(xs, ys, Lx, Ly, topo, p0)
+    np.testing.assert_allclose(A.cpu().numpy(), oA, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(P.cpu().numpy(), oP, rtol=1e-12, atol=1e-13)
+    scale = max(np.abs(oFx).max(), np.abs(oFy).max())
+    assert np.abs(Fx.cpu().numpy() - oFx).max() <= F_TOL * scale
+    assert np.abs(Fy.cpu().numpy() - oFy).max() <= F_TOL * scale
+    assert abs(E - oE) <= 1e-11 * abs(oE)
+    sim.close()
+
+
+@pytest.mark.parametrize("n,seed,v0", [(400, 8, 0.05), (4096, 9, 0.1)])
+def test_one_step(n, seed, v0):
+    sim, xs, ys, th, Lx, Ly = make(n, seed, p0=3.85, v0=v0, seed=17, dt=0.01)
+    sim.step(1)
+    gx, gy, gth = (t.cpu().numpy() for t in sim.state())
+    ox, oy, oth, _ = oracle.spv_run(xs, ys, th, Lx, Ly, 3.85, v0, 1, seed=17, dt=0.01)
+    assert np.abs(wrapdiff(gx, ox, Lx)).max() <= X_TOL * Lx
+    assert np.abs(wrapdiff(gy, oy, Ly)).max() <= X_TOL * Ly
+    np.testing.assert_allclose(gth, oth, rtol=0, atol=1e-12)
+    # topology after the step (test + repair) equals the exact triangulation
+    check_topology(sim, gx, gy, Lx, Ly)
+    sim.close()
+
+
+def test_many_steps_keep_exact_delaunay():
+    """200 steps of the N=400 workload (p0=3.8, v0=0.05): after every 50 steps
+    the maintained rings equal the oracle's triangulation from scratch."""
+    sim, xs, ys, th, Lx, Ly = make(400, 1, p0=3.8, v0=0.05, seed=1, dt=0.01)
+    for _ in range(4):
+        sim.step(50)
+        gx, gy, _ = (t.cpu().numpy() for t in sim.state())
+        check_topology(sim, gx, gy, Lx, Ly)
+    c = sim.counters()
+    assert c["steps"] == 200 and c["status"] == 0
+    sim.close()
+
+
+def test_fluid_regime_repairs():
+    """Fluid regime with fast cells: many neighbour changes per step."""
+    sim, xs, ys, th, Lx, Ly = make(2000, 12, p0=4.0, v0=1.0, seed=3, dt=0.02)
+    for _ in range(5):
+        sim.step(20)
+        gx, gy, _ = (t.cpu().numpy() for t in sim.state())
+        check_topology(sim, gx, gy, Lx, Ly)
+    c = sim.counters()
+    assert c["flagged_total"] > 0
+    sim.close()
+
+
+def test_square_lattice_tie_break_matches_oracle():
+    x, y, L = workloads.square_lattice(12)
+    Lx, Ly, q = oracle.box(L)
+    xs, ys = oracle.snap_positions(x, y, Lx, Ly)
+    sim = cg.SPV([dict(n=len(xs), Lx=L, Ly=L, p0=3.8, v0=0.0)], xs, ys, np.zeros(len(xs)))
+    check_topology(sim, xs, ys, Lx, Ly)
+    sim.close()
+
+
+def test_hexagonal_lattice_zero_force():
+    x, y, Lx, Ly = workloads.triangular_lattice(16, 16)
+    Lxs, Lys, q = oracle.box(Lx, Ly)
+    xs, ys = oracle.snap_positions(x, y, Lxs, Lys)
+    sim = cg.SPV([dict(n=len(xs), Lx=Lx, Ly=Ly, p0=3.9, v0=0.0)], xs, ys, np.zeros(len(xs)))
+    cnt, nbr = sim.neighbors()
+    assert set(cnt.cpu().numpy().tolist()) == {6}
+    Fx, Fy, E = sim.forces()
+    assert float(Fx.abs().max()) < 1e-12 and float(Fy.abs().max()) < 1e-12
+    A, P = sim.geometry()
+    np.testing.assert_allclose((P / A.sqrt()).cpu().numpy(), np.sqrt(8 * np.sqrt(3)), rtol=1e-12)
+    sim.close()
+
+
+def test_invalid_positions_raise():
+    n = 64
+    x, y, th, L = workloads.spv_uniform(n, 1)
+    x = x.copy()
+    x[3] = 5 * L
+    with pytest.raises(cg.CellgbError):
+        cg.SPV([dict(n=n, Lx=L, Ly=L, p0=3.8, v0=0.05)], x, y, th)
+
+
+def test_set_p0_v0_change_forces_and_motion():
+    sim, xs, ys, th, Lx, Ly = make(400, 21, p0=3.8, v0=0.0)
+    topo = oracle.triangulate(xs, ys, Lx, Ly)
+    p0 = np.random.default_rng(0).uniform(3.7, 3.9, 400)
+    sim.set_p0(p0)
+    Fx, Fy, E = sim.forces()
+    oFx, oFy, *_ = oracle.forces(xs, ys, Lx, Ly, topo, p0)
+    scale = max(np.abs(oFx).max(), np.abs(oFy).max())
+    assert np.abs(Fx.cpu().numpy() - oFx).max() <= F_TOL * scale
+    v0 = np.random.default_rng(1).uniform(0.0, 0.3, 400)
+    sim.set_v0(v0)
+    sim.step(1)
+    gx, gy, gth = (t.cpu().numpy() for t in sim.state())
+    ox, oy, oth, _ = oracle.spv_run(xs, ys, th, Lx, Ly, p0, v0, 1, seed=0, dt=0.01)
+    assert np.abs(wrapdiff(gx, ox, Lx)).max() <= X_TOL * Lx
+    sim.close()
+
+
+def test_full_size_workload():
+    """N = 262144, L = 512 (the benchmark workload): initial topology
+    bit-exact, forces within tolerance, and after 10 fluid-regime steps the
+    maintained topology equals the exact triangulation of the new positions."""
+    n = 262144
+    sim, xs, ys, th, Lx, Ly = make(n, 1, p0=3.85, v0=0.1, seed=1, dt=0.01)
+    topo = check_topology(sim, xs, ys, Lx, Ly)
+    Fx, Fy, E = sim.forces()
+    oFx, oFy, *_ = oracle.forces(xs, ys, Lx, Ly, topo, 3.85)
+    scale = max(np.abs(oFx).max(), np.abs(oFy).max())
+    assert np.abs(Fx.cpu().numpy() - oFx).max() <= F_TOL * scale
+    sim.step(10)
+    gx, gy, _ = (t.cpu().numpy() for t in sim.state())
+    check_topology(sim, gx, gy, Lx, Ly)
+    sim.close()
