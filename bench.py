@@ -1,0 +1,332 @@
+#!/usr/bin/env python3
+"""SPV benchmark: cell-steps/s of the self-propelled Voronoi step on GB300.
+
+Workload (Sussman, arXiv 1702.02939, SPV model of Sec. 2.C, fluid regime of
+Fig. 3): N = 262144 cells at unit density in a periodic box L = 512, uniform
+random positions and directors, p0 = 3.85, v0 = 0.1, A0 = K_A = K_P = mu =
+D_r = 1, dt = 0.01, FP64.  Warm-up steps double as equilibration; every timed
+step runs the whole hot path (geometry, force sets, net force, move, exact
+circumcircle test, local repair) and is timed alone with CUDA events, with L2
+flushed in between.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain restatement of the method used
+by the tests) on bounded spatial-window samples of the same workload.
+With N > 1 (torchrun), each rank advances its own independent replica
+(replicas only, weak scaling); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_CELLS = 262144
+P0, V0, DT = 3.85, 0.1, 0.01
+METRIC = "SPV cell-steps/s at N=262144 (FP64, 1 GB300)"
+UNIT = "cell-steps/s"
+WORKLOAD = "spv_fluid_N262144_L512_p0_3.85_v0_0.1_dt0.01_fp64"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+# Algorithmic FP64 floating-point operations per cell-step of each kernel
+# (fma = 2, add/mul/div/sqrt/rsqrt = 1, transcendental = 1), for the mean ring
+# size of 6 of a random Voronoi tessellation.  Derivation in the design notes.
+FLOPS_PER_CELL = {"geometry": 342.0, "force_move": 93.0}
+# Algorithmic bytes per cell-step of the whole step (state read + written once).
+BYTES_PER_CELL_STEP = 84.0
+# FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Dominant-kernel DRAM traffic per launch from the committed ncu capture
+# (profiles/k_geom_spv_N262144.md); None until captured for the current kernel.
+GEOM_DRAM_BYTES_PER_LAUNCH = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_CELLS)
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def hbm_peak():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(n, seed):
+    import oracle  # noqa: F401  (not used for inputs; see workloads)
+    import workloads
+
+    x, y, th, L = workloads.spv_uniform(n, seed)
+    return x, y, th, L
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [t.strip() for t in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernels_per_step(repair_cap):
+    # geometry, force+move, begin-topology, test, 4 cell-list kernels,
+    # repair_cap x (repair + check)
+    return 4 + 4 + 2 * repair_cap
+
+
+def cpu_baseline(x, y, th, L, seconds):
+    """The oracle as it stands: full periodic steps (retriangulation from
+    scratch, forces, update) of the same workload, single thread."""
+    import oracle
+
+    Lx, Ly, q = oracle.box(L)
+    xs, ys = oracle.snap_positions(x, y, Lx, Ly)
+    n = len(xs)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        xs, ys, th, _ = oracle.spv_run(xs, ys, th, Lx, Ly, P0, V0, 1, seed=1, step0=steps, dt=DT)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or steps >= 50:
+            break
+    return {"value": n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full oracle steps of the N={n} workload (periodic Bowyer-Watson "
+                      f"retriangulation + forces + update), {el:.1f} s, single thread"}
+
+
+def run_reference(args):
+    """CPU oracle arm: each step is one oracle step of a spatial window of the
+    N=262144 state, sized so that the whole run takes a few minutes."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+
+    x, y, th, L = workload(args.n, 1)
+    Lx, Ly, q = oracle.box(L)
+    xs, ys = oracle.snap_positions(x, y, Lx, Ly)
+    n = len(xs)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    # calibrate the window half-width for about `budget` seconds per step
+    hw = 8.0
+    for _ in range(6):
+        t0 = time.perf_counter()
+        oracle.spv_window_step(xs, ys, th, Lx, Ly, P0, V0, 1, 0, Lx / 2, Ly / 2, hw)
+        el = time.perf_counter() - t0
+        if el > 0.5 * budget or hw >= Lx / 2 - 8:
+            break
+        hw = min(hw * 2.0, Lx / 2 - 8)
+    scale = math.sqrt(max(budget / max(el, 1e-4), 0.05))
+    hw = float(min(max(4.0, hw * scale), Lx / 2 - 8))
+    rng = np.random.default_rng(0)
+    total_cells, total_t = 0, 0.0
+    for s in range(args.warmup + args.steps):
+        cx = float(oracle.snap_length(rng.uniform(0, Lx), q))
+        cy = float(oracle.snap_length(rng.uniform(0, Ly), q))
+        t0 = time.perf_counter()
+        xs, ys, th, k = oracle.spv_window_step(xs, ys, th, Lx, Ly, P0, V0, 1, s, cx, cy, hw)
+        el = time.perf_counter() - t0
+        if s >= args.warmup:
+            total_cells += k
+            total_t += el
+    value = total_cells / total_t
+    sample = (f"{args.steps} oracle steps of square windows (half-width {hw:.1f}, ~{total_cells // args.steps} "
+              f"cells updated each) of the N={n} state: exact triangulation of the window plus a 6-spacing "
+              f"margin, forces and update of its interior cells, single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n_cells": n, "box": Lx, "sample": "window"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_1702_02939_gb300 as cg
+
+    x, y, th, L = workload(args.n, 1 + rank)
+    repair_cap = 4
+    sim = cg.SPV([dict(n=args.n, Lx=L, Ly=L, p0=P0, v0=V0)], x, y, th, dt=DT, seed=1 + rank,
+                 repair_cap=repair_cap, device=f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+    # warm-up = equilibration steps
+    sim.step(args.warmup)
+    sim.sync()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush (256 MB > 129 MB L2) between timed steps
+        ev_s[k].record(stream)
+        sim.step(1)
+        ev_e[k].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    sim.sync()  # raises on any device error
+    ms = sum(ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps))
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    counters = sim.counters()
+    value = world * args.n * args.steps / (ms * 1e-3)
+
+    # per-kernel device times (eager launches, CUDA events on the same stream)
+    prof_steps = 20
+    ph = sim.profile(prof_steps)
+    dominant = max(("geometry", "force_move"), key=lambda k: ph[k])
+    dom_ms = ph[dominant] / prof_steps
+    achieved_tflops = FLOPS_PER_CELL[dominant] * args.n / (dom_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+                "traffic": GEOM_DRAM_BYTES_PER_LAUNCH if dominant == "geometry" else None,
+                "kernel": {"geometry": "k_geom", "force_move": "k_force"}[dominant],
+                "peak_source": "FP64 nominal from unit counts x 2.07 GHz (FP64 units, not tensor)"}
+    hbm_gbs, hbm_src = hbm_peak()
+    step_s = ms * 1e-3 / args.steps
+    hbm = {"achieved_gbs": BYTES_PER_CELL_STEP * args.n / step_s / 1e9, "peak_gbs": hbm_gbs,
+           "frac": BYTES_PER_CELL_STEP * args.n / step_s / 1e9 / hbm_gbs, "source": hbm_src,
+           "bytes_per_cell_step": BYTES_PER_CELL_STEP}
+
+    # end to end through the public API with pinned host buffers: every step
+    # uploads that step's per-cell v0 and reads back the positions
+    e2e = None
+    if not args.no_e2e:
+        hv0 = torch.full((args.n,), V0, dtype=torch.float64).pin_memory()
+        hx = torch.empty(args.n, dtype=torch.float64).pin_memory()
+        hy = torch.empty(args.n, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            cg.cg_set_v0(sim.ctx, hv0)
+            cg.cg_step(sim.ctx, 1)
+            cg.cg_get_state(sim.ctx, hx, hy, None)
+        el = time.perf_counter() - t0
+        e2e = {"value": world * args.n * args.e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": 8 * args.n,
+               "d2h_bytes_per_step": 16 * args.n}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(x, y, th, L, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_cells": args.n, "box": L, "p0": P0, "v0": V0, "dt": DT,
+                           "replicas_per_gpu": 1, "l2": "flushed between timed steps (256 MB write)",
+                           "repair_cap": repair_cap},
+                "clocks": clk, "e2e": e2e,
+                "gpu_launches": kernels_per_step(repair_cap) * args.steps,
+                "roofline": roofline, "hbm_roofline": hbm, "cpu_baseline": cpu,
+                "phase_ms_per_step": {k: v / prof_steps for k, v in ph.items()},
+                "counters": counters}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

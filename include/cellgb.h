@@ -116,6 +116,15 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
  * captured CUDA graph without host synchronization. */
 int cg_step(cg_ctx* ctx, int64_t nsteps);
 
+/* Per-phase device time of nsteps ordinary steps run eagerly (not as a
+ * graph), timed with CUDA events on the context's stream.  ms_out[k] receives
+ * the summed milliseconds of phase k (n_out >= CG_NUM_PHASES):
+ *   0 geometry + force sets, 1 net force + move, 2 circumcircle test,
+ *   3 cell-list build, 4 repair rounds (repair + consistency check).
+ * The steps advance the state exactly like cg_step(). */
+#define CG_NUM_PHASES 5
+int cg_profile_step(cg_ctx* ctx, int64_t nsteps, double* ms_out, int32_t n_out);
+
 /* Waits for the stream and returns the device status word. */
 int cg_sync(cg_ctx* ctx);
 

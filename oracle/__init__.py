@@ -51,6 +51,10 @@ def _declare(L):
                                 C.c_uint64, C.c_int64]
     L.cgo_spv_run.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp,
                               C.c_uint64, C.c_int64, C.c_int64, _dp, _dp, _dp, _dp]
+    L.cgo_spv_window_step.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp,
+                                      C.c_uint64, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                      C.c_double]
+    L.cgo_spv_window_step.restype = C.c_int
     for name in ("cgo_snap_positions", "cgo_orient2d", "cgo_incircle", "cgo_incircle_sos",
                  "cgo_delaunay_plain", "cgo_triangulate", "cgo_geometry", "cgo_forces",
                  "cgo_integrate", "cgo_spv_run"):
@@ -226,3 +230,21 @@ def spv_run(x, y, theta, Lx, Ly, p0, v0, nsteps, seed, step0=0, A0=1.0, KA=1.0, 
                              int(seed), int(step0), int(nsteps), _d(Fx), _d(Fy), _d(A), _d(P)),
            "spv_run")
     return x, y, theta, (Fx, Fy, A, P)
+
+
+def spv_window_step(x, y, theta, Lx, Ly, p0, v0, seed, step, cx, cy, hw, margin=6.0, A0=1.0, KA=1.0,
+                    KP=1.0, mu=1.0, Dr=1.0, dt=0.01):
+    """One oracle step for the cells within hw of (cx, cy) (in place on copies).
+    Returns (x, y, theta, number of updated cells)."""
+    n = len(x)
+    x = np.array(x, np.float64, copy=True)
+    y = np.array(y, np.float64, copy=True)
+    theta = np.array(theta, np.float64, copy=True)
+    p0 = np.ascontiguousarray(np.broadcast_to(np.asarray(p0, np.float64), (n,)))
+    v0 = np.ascontiguousarray(np.broadcast_to(np.asarray(v0, np.float64), (n,)))
+    par = np.array([A0, KA, KP, mu, Dr, dt], np.float64)
+    k = lib().cgo_spv_window_step(n, Lx, Ly, _d(x), _d(y), _d(theta), _d(p0), _d(v0), _d(par), int(seed),
+                                  int(step), float(cx), float(cy), float(hw), float(margin))
+    if k < 0:
+        raise OracleError(f"window step failed with code {k}")
+    return x, y, theta, k

@@ -109,7 +109,7 @@ struct Mech {
 
 // Forces on every cell (Eqs. A3-A7 and A13-A16 with the corrections above).
 int forces(const Geo& g, const Mech& mp, double* Fx, double* Fy, double* A, double* P,
-           double* energy) {
+           double* energy, const char* only = nullptr) {
   std::vector<double> hx, hy;
   polygons(g, hx, hy, A, P);
   const double sqA0 = std::sqrt(mp.A0);
@@ -140,6 +140,7 @@ int forces(const Geo& g, const Mech& mp, double* Fx, double* Fy, double* A, doub
   if (energy) *energy = E;
   // net force (Eqs. A6, A7): F_i = - sum_{t ni i} (dh_t/dr_i)^T G_t
   for (int i = 0; i < g.n; ++i) {
+    if (only && !only[i]) continue;
     int m = g.cnt[i];
     double fx = 0.0, fy = 0.0;
     for (int a = 0; a < m; ++a) {
@@ -383,6 +384,76 @@ int cgo_spv_run(int n, double Lx, double Ly, double* x, double* y, double* theta
     cgo_integrate(n, Lx, Ly, x, y, theta, fx.data(), fy.data(), v0, ipar, seed, step0 + s);
   }
   return 0;
+}
+
+// One oracle step restricted to a square window of the periodic system: the
+// cells within hw + margin of (cx, cy) are triangulated from scratch (plain
+// Bowyer-Watson), and the cells within hw of the centre get their exact force
+// and update (their rings and their neighbours' rings lie well inside the
+// triangulated patch when margin >= 6 mean spacings).  Used as a bounded
+// sample of a large workload for CPU timing.  (cx, cy) must lie on the grid.
+// Returns the number of updated (interior) cells, or a negative error code.
+int cgo_spv_window_step(int n, double Lx, double Ly, double* x, double* y, double* theta,
+                        const double* p0, const double* v0, const double* par, uint64_t seed,
+                        int64_t step, double cx, double cy, double hw, double margin) {
+  const int q = grid_exponent(Lx, Ly);
+  const int R = 16;
+  std::vector<int> ids;
+  std::vector<double> lx, ly;
+  for (int i = 0; i < n; ++i) {
+    double dx = x[i] - cx, dy = y[i] - cy;
+    if (dx >= 0.5 * Lx) dx -= Lx; else if (dx < -0.5 * Lx) dx += Lx;
+    if (dy >= 0.5 * Ly) dy -= Ly; else if (dy < -0.5 * Ly) dy += Ly;
+    if (std::fabs(dx) < hw + margin && std::fabs(dy) < hw + margin) {
+      ids.push_back(i);
+      lx.push_back(dx);
+      ly.push_back(dy);
+    }
+  }
+  const int m = (int)ids.size();
+  std::vector<Pt> pts(m);
+  std::vector<char> central(m, 1);
+  for (int k = 0; k < m; ++k)
+    pts[k] = Pt{(int64_t)std::ldexp(lx[k], q), (int64_t)std::ldexp(ly[k], q), ids[k], 0, 0,
+                (int64_t)ids[k] * 16};
+  std::vector<Ring> rings;
+  int rc = bowyer_watson_rings(pts, central, rings, true);
+  if (rc) return rc;
+  // local tags -> local indices
+  std::vector<int> local_of(n, -1);
+  for (int k = 0; k < m; ++k) local_of[ids[k]] = k;
+  std::vector<int32_t> cnt(m, 0), nbr((size_t)m * R, -1), off((size_t)m * R * 2, 0);
+  std::vector<char> interior(m, 0);
+  int n_int = 0;
+  const double valid = hw + margin - 3.0;
+  for (int k = 0; k < m; ++k) {
+    interior[k] = std::fabs(lx[k]) < hw && std::fabs(ly[k]) < hw;
+    n_int += interior[k];
+    if (!(std::fabs(lx[k]) < valid && std::fabs(ly[k]) < valid)) continue;
+    const Ring& r = rings[k];
+    if (r.tag.empty()) continue;
+    if ((int)r.tag.size() > R) return -5;
+    cnt[k] = (int32_t)r.tag.size();
+    for (size_t a = 0; a < r.tag.size(); ++a) nbr[(size_t)k * R + a] = local_of[r.tag[a]];
+  }
+  Geo g{m, 2.0 * Lx, 2.0 * Ly, R, lx.data(), ly.data(), cnt.data(), nbr.data(), off.data()};
+  std::vector<double> lp0(m), fx(m, 0.0), fy(m, 0.0), A(m), P(m);
+  for (int k = 0; k < m; ++k) lp0[k] = p0[ids[k]];
+  Mech mp{par[0], par[1], par[2], lp0.data()};
+  rc = forces(g, mp, fx.data(), fy.data(), A.data(), P.data(), nullptr, interior.data());
+  if (rc) return rc;
+  const double mu = par[3], Dr = par[4], dt = par[5];
+  const double s = std::sqrt(2.0 * Dr * dt);
+  for (int k = 0; k < m; ++k) {
+    if (!interior[k]) continue;
+    const int i = ids[k];
+    double vx = mu * fx[k] + v0[i] * std::cos(theta[i]);
+    double vy = mu * fy[k] + v0[i] * std::sin(theta[i]);
+    x[i] = snap_wrap(x[i] + dt * vx, Lx, q);
+    y[i] = snap_wrap(y[i] + dt * vy, Ly, q);
+    theta[i] = theta[i] + s * director_noise(seed, i, step);
+  }
+  return n_int;
 }
 
 }  // extern "C"

@@ -62,6 +62,7 @@ def lib():
                                 vp, C.POINTER(vp)]
         L.cg_step.argtypes = [vp, i64]
         L.cg_sync.argtypes = [vp]
+        L.cg_profile_step.argtypes = [vp, i64, C.POINTER(C.c_double), i32]
         L.cg_get_state.argtypes = [vp, vp, vp, vp]
         L.cg_set_state.argtypes = [vp, vp, vp, vp]
         L.cg_get_geometry.argtypes = [vp, vp, vp]
@@ -77,7 +78,7 @@ def lib():
         L.cg_status_string.restype = C.c_char_p
         L.cg_last_error.argtypes = [vp]
         L.cg_last_error.restype = C.c_char_p
-        for name in ("cg_workspace_bytes", "cg_create", "cg_step", "cg_sync", "cg_get_state", "cg_set_state",
+        for name in ("cg_workspace_bytes", "cg_create", "cg_step", "cg_sync", "cg_profile_step", "cg_get_state", "cg_set_state",
                      "cg_get_geometry", "cg_get_forces", "cg_get_neighbors", "cg_set_p0", "cg_set_v0",
                      "cg_get_counters", "cg_destroy"):
             getattr(L, name).restype = C.c_int
@@ -127,6 +128,15 @@ def cg_create(replicas, params, x, y, theta, workspace, stream):
 
 def cg_step(ctx, nsteps):
     _check(lib().cg_step(ctx, int(nsteps)), ctx)
+
+
+PHASES = ("geometry", "force_move", "test", "cell_list", "repair")
+
+
+def cg_profile_step(ctx, nsteps):
+    ms = (C.c_double * len(PHASES))()
+    _check(lib().cg_profile_step(ctx, int(nsteps), ms, len(PHASES)), ctx)
+    return {k: ms[i] for i, k in enumerate(PHASES)}
 
 
 def cg_sync(ctx):
@@ -217,6 +227,9 @@ class SPV:
 
     def sync(self):
         cg_sync(self.ctx)
+
+    def profile(self, nsteps):
+        return cg_profile_step(self.ctx, nsteps)
 
     def state(self):
         x, y, th = self._out(), self._out(), self._out()

@@ -470,6 +470,43 @@ int cg_step(cg_ctx* c, int64_t nsteps) {
   return CG_OK;
 }
 
+int cg_profile_step(cg_ctx* c, int64_t nsteps, double* ms_out, int32_t n_out) {
+  if (!c || !ms_out || n_out < CG_NUM_PHASES || nsteps < 0) return CG_EINVAL;
+  cudaStream_t st = c->stream;
+  cudaEvent_t ev[CG_NUM_PHASES + 1];
+  for (int k = 0; k <= CG_NUM_PHASES; ++k) CG_CUDA(c, cudaEventCreate(&ev[k]));
+  for (int k = 0; k < CG_NUM_PHASES; ++k) ms_out[k] = 0.0;
+  const int cap = c->par.repair_cap > 0 ? c->par.repair_cap : 4;
+  const int grid = repair_grid(c);
+  int rc = CG_OK;
+  for (int64_t s = 0; s < nsteps && !rc; ++s) {
+    cudaEventRecord(ev[0], st);
+    launch_geom(geom_args(c), st);
+    cudaEventRecord(ev[1], st);
+    launch_force(force_args(c, 1), st);
+    cudaEventRecord(ev[2], st);
+    launch_begin_topology(c->ctl(), 1, st);
+    launch_test(test_args(c), st);
+    cudaEventRecord(ev[3], st);
+    launch_cell_list(cell_list_args(c, 1), st);
+    cudaEventRecord(ev[4], st);
+    for (int r = 0; r < cap; ++r) {
+      launch_repair(repair_args(c, r & 1, 0), grid, st);
+      launch_check(check_args(c, r & 1, r == cap - 1, 0), st);
+    }
+    cudaEventRecord(ev[5], st);
+    if (cudaEventSynchronize(ev[5]) != cudaSuccess) { rc = fail(c, CG_ECUDA, "profile sync"); break; }
+    for (int k = 0; k < CG_NUM_PHASES; ++k) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      ms_out[k] += ms;
+    }
+  }
+  for (int k = 0; k <= CG_NUM_PHASES; ++k) cudaEventDestroy(ev[k]);
+  if (rc) return rc;
+  return read_status(c);
+}
+
 int cg_sync(cg_ctx* c) {
   if (!c) return CG_EINVAL;
   return read_status(c);

@@ -139,3 +139,16 @@ def test_single_step_update_formula():
     assert np.abs(dxm).max() <= 2.0 ** (-q) and np.abs(dym).max() <= 2.0 ** (-q)
     xi = np.array([oracle.director_noise(5, i, 3) for i in range(64)])
     np.testing.assert_allclose(th1, th + math.sqrt(2 * 1.0 * 0.01) * xi, rtol=0, atol=1e-15)
+
+
+def test_window_step_equals_full_step():
+    """The spatial-window step used to time bounded samples of a large
+    workload reproduces the full periodic step exactly for its interior cells."""
+    x, y, th, Lx, Ly = state(4096, 13)
+    x1, y1, th1, _ = oracle.spv_run(x, y, th, Lx, Ly, 3.85, 0.1, 1, seed=5, step0=2)
+    wx, wy, wth, k = oracle.spv_window_step(x, y, th, Lx, Ly, 3.85, 0.1, 5, 2, 32.0, 32.0, 12.0)
+    upd = np.nonzero((wx != x) | (wy != y) | (wth != th))[0]
+    assert k > 400 and len(upd) == k
+    np.testing.assert_array_equal(wx[upd], x1[upd])
+    np.testing.assert_array_equal(wy[upd], y1[upd])
+    np.testing.assert_array_equal(wth[upd], th1[upd])
