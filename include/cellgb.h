@@ -151,6 +151,29 @@ int cg_get_counters(cg_ctx* ctx, cg_counters* host_out);
 /* Total cells of the context. */
 int64_t cg_num_cells(const cg_ctx* ctx);
 
+/* Allocation-free triangulation, for callers that cannot call cudaMalloc
+ * (code running under a fixed device memory pool, inside another runtime's
+ * allocator or plugin hooks, or with all device memory reserved up front).
+ * The paper has no counterpart: this is a deployment variant of the
+ * from-scratch triangulation that cg_create performs.
+ *   n, Lx, Ly   : 16 <= n <= CG_NOALLOC_MAX_CELLS cells in a periodic box;
+ *                 n > CG_NOALLOC_MAX_CELLS (or a box needing more than
+ *                 2*CG_NOALLOC_MAX_CELLS cell-list bins) returns CG_EINVAL.
+ *   d_x, d_y    : device, n doubles each, positions in [-L, 2L).
+ *   d_cnt, d_nbr: device outputs, n and n*CG_MAX_RING int32: the Delaunay
+ *                 neighbours of every cell exactly as cg_get_neighbors()
+ *                 returns them for the same positions.
+ *   stream      : cudaStream_t (may be 0); the call synchronizes it.
+ * Scratch lives in a static device array of the library (about 3.7 MB, held
+ * by every GPU that loads the library until the process exits); the call
+ * makes no device allocation.  All calls share that array: calls whose GPU
+ * work overlaps race.  The first call on each device looks the array's address
+ * up and should come before any stream capture.  Returns CG_OK or a status
+ * code (the outputs are undefined on error). */
+#define CG_NOALLOC_MAX_CELLS 16384
+int cg_triangulate_noalloc(int32_t n, double Lx, double Ly, const double* d_x, const double* d_y,
+                           int32_t* d_cnt, int32_t* d_nbr, void* stream);
+
 /* Releases the host context (the workspace stays the caller's). */
 int cg_destroy(cg_ctx* ctx);
 

@@ -71,6 +71,8 @@ def lib():
         L.cg_set_p0.argtypes = [vp, vp]
         L.cg_set_v0.argtypes = [vp, vp]
         L.cg_get_counters.argtypes = [vp, C.POINTER(cg_counters)]
+        L.cg_triangulate_noalloc.argtypes = [i32, C.c_double, C.c_double, vp, vp, vp, vp, vp]
+        L.cg_triangulate_noalloc.restype = C.c_int
         L.cg_num_cells.argtypes = [vp]
         L.cg_num_cells.restype = i64
         L.cg_destroy.argtypes = [vp]
@@ -177,6 +179,19 @@ def cg_get_counters(ctx):
     c = cg_counters()
     _check(lib().cg_get_counters(ctx, C.byref(c)), ctx)
     return {k: getattr(c, k) for k, _ in cg_counters._fields_ if k != "reserved"}
+
+
+NOALLOC_MAX_CELLS = 16384
+
+
+def cg_triangulate_noalloc(n, Lx, Ly, x, y, cnt, nbr, stream):
+    """Delaunay rings of n cells without any device allocation (scratch is a
+    static array of the library, shared by all calls; at most
+    NOALLOC_MAX_CELLS cells).  x, y, cnt, nbr are device tensors."""
+    if n > NOALLOC_MAX_CELLS:
+        raise CellgbError(-1, f"n={n} exceeds the static scratch limit of {NOALLOC_MAX_CELLS} cells")
+    _check(lib().cg_triangulate_noalloc(int(n), float(Lx), float(Ly), _ptr(x), _ptr(y), _ptr(cnt), _ptr(nbr),
+                                        C.c_void_p(stream)))
 
 
 def cg_num_cells(ctx):
