@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=40)
+    ap.add_argument("--batched-warmup", type=int, default=50)
     return ap.parse_args()
 
 
@@ -158,6 +161,63 @@ def cpu_baseline(x, y, th, L, seconds):
     return {"value": n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{steps} full oracle steps of the N={n} workload (periodic Bowyer-Watson "
                       f"retriangulation + forces + update), {el:.1f} s, single thread"}
+
+
+def batched_comparison(args, device):
+    """512 independent replicas (N_r log-uniform on [256, 16384], p0 ~
+    U[3.6, 4.0], v0 ~ U[0.01, 0.5], L_r = sqrt(N_r)): all replicas in one
+    context (one graph launch per step for all of them) versus one context per
+    replica stepped in a loop (one graph launch per replica per step)."""
+    import numpy as np
+    import torch
+
+    import paper_1702_02939_gb300 as cg
+    import workloads
+
+    R = 512
+    sizes = workloads.replica_sizes(R, 7)
+    p0s, v0s = workloads.replica_params(R, 7)
+    reps, xs, ys, ths = [], [], [], []
+    for r in range(R):
+        x, y, th, L = workloads.spv_uniform(int(sizes[r]), 1000 + r)
+        reps.append(dict(n=int(sizes[r]), Lx=L, Ly=L, p0=float(p0s[r]), v0=float(v0s[r])))
+        xs.append(x); ys.append(y); ths.append(th)
+    total = int(sizes.sum())
+    stream = torch.cuda.current_stream()
+
+    def timed(step_fn, steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step_fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    fused = cg.SPV(reps, np.concatenate(xs), np.concatenate(ys), np.concatenate(ths), dt=DT, seed=7,
+                   device=device)
+    # equilibration: the random initial state relaxes large forces first
+    fused.step(args.batched_warmup)
+    ms_f = timed(lambda: fused.step(1), args.batched_steps)
+    fused.sync()
+    fused.close()
+    del fused
+    singles = [cg.SPV([reps[r]], xs[r], ys[r], ths[r], dt=DT, seed=7, device=device) for r in range(R)]
+    for sim in singles:
+        sim.step(args.batched_warmup)
+    steps_loop = max(3, args.batched_steps // 4)
+    ms_l = timed(lambda: [sim.step(1) for sim in singles], steps_loop)
+    for sim in singles:
+        sim.sync()
+        sim.close()
+    v_f = total * args.batched_steps / (ms_f * 1e-3)
+    v_l = total * steps_loop / (ms_l * 1e-3)
+    return {"workload": "spv_batched_R512_N256-16384_loguniform", "replicas": R, "cells": total,
+            "fused_cell_steps_per_s": v_f, "per_replica_loop_cell_steps_per_s": v_l, "fused_over_loop": v_f / v_l,
+            "fused_ms_per_step": ms_f / args.batched_steps, "loop_ms_per_step": ms_l / steps_loop,
+            "steps": [args.batched_steps, steps_loop], "warmup": args.batched_warmup}
 
 
 def run_reference(args):
@@ -301,6 +361,10 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(x, y, th, L, args.cpu_seconds)
+    sim.close()
+    batched = None
+    if rank == 0 and world == 1 and not args.no_batched:
+        batched = batched_comparison(args, f"cuda:{local}")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -313,9 +377,8 @@ def run_ours(args):
                 "gpu_launches": kernels_per_step(repair_cap) * args.steps,
                 "roofline": roofline, "hbm_roofline": hbm, "cpu_baseline": cpu,
                 "phase_ms_per_step": {k: v / prof_steps for k, v in ph.items()},
-                "counters": counters}
+                "counters": counters, "batched": batched}
         print(json.dumps(line), flush=True)
-    sim.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -185,11 +185,23 @@ int forces(const Geo& g, const Mech& mp, double* Fx, double* Fy, double* A, doub
   return 0;
 }
 
+// Periodic reduction of a finite coordinate (any move size): v' = fmod(v, L)
+// is exact, v' is rounded to the grid 2^-q, and the grid integer is wrapped
+// into [0, L 2^q).  Returns false for a non-finite v.
+inline bool snap_wrap_ok(double v, double L, int q, double& out) {
+  if (!std::isfinite(v)) return false;
+  double r = std::fmod(v, L);
+  double X = std::rint(std::ldexp(r, q));
+  double LX = std::ldexp(L, q);
+  if (X < 0.0) X += LX;
+  else if (X >= LX) X -= LX;
+  out = std::ldexp(X, -q) + 0.0;
+  return true;
+}
 inline double snap_wrap(double v, double L, int q) {
-  double s = std::ldexp(std::rint(std::ldexp(v, q)), -q);
-  if (s >= L) s -= L;
-  else if (s < 0.0) s += L;
-  return s + 0.0;
+  double out = 0.0;
+  snap_wrap_ok(v, L, q, out);
+  return out;
 }
 
 int grid_exponent(double Lx, double Ly) {
@@ -353,8 +365,7 @@ int cgo_integrate(int n, double Lx, double Ly, double* x, double* y, double* the
     double vx = mu * Fx[i] + v0[i] * std::cos(theta[i]);
     double vy = mu * Fy[i] + v0[i] * std::sin(theta[i]);
     double xn = x[i] + dt * vx, yn = y[i] + dt * vy;
-    x[i] = snap_wrap(xn, Lx, q);
-    y[i] = snap_wrap(yn, Ly, q);
+    if (!snap_wrap_ok(xn, Lx, q, x[i]) || !snap_wrap_ok(yn, Ly, q, y[i])) return -6;  // non-finite move
     theta[i] = theta[i] + s * director_noise(seed, i, step);
   }
   return 0;
@@ -381,7 +392,8 @@ int cgo_spv_run(int n, double Lx, double Ly, double* x, double* y, double* theta
     if (Fy) std::memcpy(Fy, fy.data(), sizeof(double) * n);
     if (A) std::memcpy(A, a.data(), sizeof(double) * n);
     if (P) std::memcpy(P, p.data(), sizeof(double) * n);
-    cgo_integrate(n, Lx, Ly, x, y, theta, fx.data(), fy.data(), v0, ipar, seed, step0 + s);
+    rc = cgo_integrate(n, Lx, Ly, x, y, theta, fx.data(), fy.data(), v0, ipar, seed, step0 + s);
+    if (rc) return rc;
   }
   return 0;
 }

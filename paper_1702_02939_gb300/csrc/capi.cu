@@ -24,6 +24,8 @@ struct Layout {
 };
 
 struct Offsets {
+  size_t key, rank, perm, key_count, key_start, key_partials, theta_alt, p0_alt, v0_alt, tag_alt, rep_alt,
+      cnt_alt, nbr_alt;
   size_t x, y, X, Y, theta, p0, v0, A, P, Fx, Fy, ecell, tmp, tmp2, scalar;
   size_t tag, rep, cnt, nbr, old_cnt, old_nbr;
   size_t fs, s, w;
@@ -35,10 +37,23 @@ struct Offsets {
 
 constexpr int kScanChunkHost = 256 * 8;
 
-Offsets layout(int64_t N, int64_t NB, int R) {
+Offsets layout(int64_t N, int64_t NB, int64_t NK, int R) {
   Layout L;
   Offsets o;
   const size_t d = sizeof(double), i4 = sizeof(int), i8 = sizeof(long long);
+  o.key = L.take(N * i4);
+  o.rank = L.take(N * i4);
+  o.perm = L.take(N * i4);
+  o.key_count = L.take(NK * i4);
+  o.key_start = L.take((NK + 1) * i4);
+  o.key_partials = L.take(((NK + 1 + kScanChunkHost - 1) / kScanChunkHost + 1) * i4);
+  o.theta_alt = L.take(N * d);
+  o.p0_alt = L.take(N * d);
+  o.v0_alt = L.take(N * d);
+  o.tag_alt = L.take(N * i4);
+  o.rep_alt = L.take(N * i4);
+  o.cnt_alt = L.take(N * i4);
+  o.nbr_alt = L.take(N * CG_RING * i4);
   o.x = L.take(2 * N * d);
   o.y = L.take(2 * N * d);
   o.X = L.take(2 * N * i8);
@@ -89,10 +104,12 @@ int ceil_log2(double v) {
   return (fr == 0.5) ? ex - 1 : ex;
 }
 
-bool build_reps(int R, const cg_replica* reps, std::vector<Rep>& out, int64_t& N, int64_t& NB, std::string& err) {
+bool build_reps(int R, const cg_replica* reps, std::vector<Rep>& out, int64_t& N, int64_t& NB, int64_t& NK,
+                std::string& err) {
   out.resize(R);
   N = 0;
   NB = 0;
+  NK = 0;
   for (int r = 0; r < R; ++r) {
     const cg_replica& c = reps[r];
     if (c.n < 16 || !(c.Lx > 0) || !(c.Ly > 0) || !std::isfinite(c.Lx) || !std::isfinite(c.Ly)) {
@@ -125,9 +142,13 @@ bool build_reps(int R, const cg_replica* reps, std::vector<Rep>& out, int64_t& N
     p.bin0 = (int)NB;
     p.v0 = c.v0;
     p.p0 = c.p0;
+    // Hilbert sort grid: the smallest power of two covering the bin grid
+    p.hord = std::max(1, ceil_log2((double)std::max(p.nbx, p.nby)));
+    p.hkey0 = (int)NK;
     N += c.n;
     NB += (int64_t)p.nbx * p.nby;
-    if (N > (int64_t)1 << 30 || NB > (int64_t)1 << 30) {
+    NK += (int64_t)1 << (2 * p.hord);
+    if (N > (int64_t)1 << 30 || NB > (int64_t)1 << 30 || NK > (int64_t)1 << 30 || p.hord > 15) {
       err = "too many cells or bins";
       return false;
     }
@@ -139,7 +160,8 @@ bool build_reps(int R, const cg_replica* reps, std::vector<Rep>& out, int64_t& N
 
 struct cg_ctx {
   int R = 0;
-  int64_t N = 0, NB = 0;
+  int64_t N = 0, NB = 0, NK = 0;
+  int64_t host_step = 0;  // steps enqueued (decides when to re-sort)
   cg_params par{};
   std::vector<Rep> reps;
   char* ws = nullptr;
@@ -299,6 +321,39 @@ CheckArgs check_args(cg_ctx* c, int which_in, int last_round, int all_cells) {
   return k;
 }
 
+SortArgs sort_args(cg_ctx* c) {
+  SortArgs a;
+  a.n = (int)c->N;
+  a.nkeys = (int)c->NK;
+  a.reps = c->at<Rep>(c->off.reps);
+  a.ctl = c->ctl();
+  a.x = c->at<double>(c->off.x);
+  a.y = c->at<double>(c->off.y);
+  a.X = c->at<long long>(c->off.X);
+  a.Y = c->at<long long>(c->off.Y);
+  a.theta = c->at<double>(c->off.theta);
+  a.p0 = c->at<double>(c->off.p0);
+  a.v0 = c->at<double>(c->off.v0);
+  a.tag = c->at<int>(c->off.tag);
+  a.rep = c->at<int>(c->off.rep);
+  a.cnt = c->at<int>(c->off.cnt);
+  a.nbr = c->at<int>(c->off.nbr);
+  a.key = c->at<int>(c->off.key);
+  a.rank = c->at<int>(c->off.rank);
+  a.perm = c->at<int>(c->off.perm);
+  a.key_count = c->at<int>(c->off.key_count);
+  a.key_start = c->at<int>(c->off.key_start);
+  a.key_partials = c->at<int>(c->off.key_partials);
+  a.theta_alt = c->at<double>(c->off.theta_alt);
+  a.p0_alt = c->at<double>(c->off.p0_alt);
+  a.v0_alt = c->at<double>(c->off.v0_alt);
+  a.tag_alt = c->at<int>(c->off.tag_alt);
+  a.rep_alt = c->at<int>(c->off.rep_alt);
+  a.cnt_alt = c->at<int>(c->off.cnt_alt);
+  a.nbr_alt = c->at<int>(c->off.nbr_alt);
+  return a;
+}
+
 int repair_grid(const cg_ctx* c) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
@@ -388,10 +443,10 @@ extern "C" {
 int cg_workspace_bytes(int32_t R, const cg_replica* reps, size_t* bytes) {
   if (R <= 0 || !reps || !bytes) return CG_EINVAL;
   std::vector<Rep> r;
-  int64_t N, NB;
+  int64_t N, NB, NK;
   std::string err;
-  if (!build_reps(R, reps, r, N, NB, err)) return CG_EINVAL;
-  *bytes = layout(N, NB, R).total;
+  if (!build_reps(R, reps, r, N, NB, NK, err)) return CG_EINVAL;
+  *bytes = layout(N, NB, NK, R).total;
   return CG_OK;
 }
 
@@ -405,14 +460,14 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
   cg_ctx* c = new (std::nothrow) cg_ctx();
   if (!c) return CG_EINVAL;
   std::string err;
-  if (!build_reps(R, reps, c->reps, c->N, c->NB, err)) {
+  if (!build_reps(R, reps, c->reps, c->N, c->NB, c->NK, err)) {
     delete c;
     return CG_EINVAL;
   }
   c->R = R;
   c->par = *params;
   if (c->par.repair_cap <= 0) c->par.repair_cap = 4;
-  c->off = layout(c->N, c->NB, R);
+  c->off = layout(c->N, c->NB, c->NK, R);
   if (ws_bytes < c->off.total) {
     delete c;
     return CG_EINVAL;
@@ -444,12 +499,15 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
     TRY(cudaMemcpyAsync(c->at<double>(c->off.p0), p0.data(), c->N * sizeof(double), cudaMemcpyHostToDevice, st));
     TRY(cudaMemcpyAsync(c->at<double>(c->off.v0), v0.data(), c->N * sizeof(double), cudaMemcpyHostToDevice, st));
     TRY(cudaMemcpyAsync(c->ctl(), &h, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    TRY(cudaMemsetAsync(c->at<int>(c->off.key_count), 0, c->NK * sizeof(int), st));
+    TRY(cudaMemsetAsync(c->at<int>(c->off.cnt), 0, c->N * sizeof(int), st));
     TRY(cudaMemcpyAsync(c->at<double>(c->off.tmp), theta, c->N * sizeof(double), cudaMemcpyDefault, st));
 #undef TRY
     if (rc) break;
     launch_scatter_d((int)c->N, c->at<int>(c->off.tag), c->at<double>(c->off.tmp), c->at<double>(c->off.theta), st);
     rc = load_positions(c, x, y);
     if (rc) break;
+    launch_sort(sort_args(c), st);  // spatial order before the first triangulation
     rc = triangulate_all(c);
     if (rc) break;
     rc = read_status(c);
@@ -466,7 +524,12 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
 
 int cg_step(cg_ctx* c, int64_t nsteps) {
   if (!c || nsteps < 0) return CG_EINVAL;
-  for (int64_t s = 0; s < nsteps; ++s) CG_CUDA(c, cudaGraphLaunch(c->step_exec, c->stream));
+  for (int64_t s = 0; s < nsteps; ++s) {
+    if (c->par.sort_every > 0 && c->host_step > 0 && c->host_step % c->par.sort_every == 0)
+      launch_sort(sort_args(c), c->stream);
+    CG_CUDA(c, cudaGraphLaunch(c->step_exec, c->stream));
+    ++c->host_step;
+  }
   return CG_OK;
 }
 

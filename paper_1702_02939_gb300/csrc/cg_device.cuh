@@ -47,7 +47,8 @@ struct Rep {
   int nbx, nby, bin0;       // cell-list bins
   int q;
   double v0, p0;            // defaults for the replica's cells
-  int pad[2];
+  int hord;                 // Hilbert curve order of the replica's sort grid
+  int hkey0;                // first sort key of the replica
 };
 
 // Mutable device globals of one context.
@@ -62,6 +63,13 @@ struct Ctl {
   int last_flagged;
   int pad;
 };
+
+// Bins per block of the block-local scans; the global start of bin b is the
+// block-local exclusive prefix plus one offset per scan block.
+constexpr int kScanChunk = 256 * 8;
+__device__ __forceinline__ int bin_begin(const int* local, const int* partial, int b) {
+  return local[b] + partial[b / kScanChunk];
+}
 
 __device__ __forceinline__ void raise_status(Ctl* ctl, int code) {
   atomicCAS(&ctl->status, 0, code);

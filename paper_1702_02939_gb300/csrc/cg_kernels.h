@@ -103,6 +103,8 @@ void launch_begin_topology(Ctl* ctl, int flip, cudaStream_t st);
 void launch_test(const TestArgs& a, cudaStream_t st);
 void launch_cell_list(const CellListArgs& a, cudaStream_t st);
 void launch_repair(const RepairArgs& a, int grid_blocks, cudaStream_t st);
+// exclusive scan of a.bin_count[0..nbins) into (a.bin_start, a.scan_partials)
+void launch_scan(const CellListArgs& a, cudaStream_t st);
 void launch_check(const CheckArgs& a, cudaStream_t st);
 
 // state preparation and user-order transfers
@@ -113,5 +115,22 @@ void launch_scatter_d(int n, const int* tag, const double* src_user, double* dst
 void launch_gather_ring(int n, const int* tag, const int* cnt, const int* nbr, int* cnt_user, int* nbr_user,
                         cudaStream_t st);
 void launch_reduce_sum(int n, const double* v, double* out, cudaStream_t st);
+
+// Hilbert re-sort of all per-cell state (sort_kernels.cu)
+struct SortArgs {
+  int n, nkeys;
+  const Rep* reps;
+  Ctl* ctl;
+  double *x, *y;        // [2][n]; the permuted state goes to the other buffer
+  long long *X, *Y;     // [2][n]
+  double *theta, *p0, *v0;
+  int *tag, *rep, *cnt, *nbr;
+  // scratch
+  int *key, *rank, *perm;
+  int *key_count, *key_start, *key_partials;
+  double *theta_alt, *p0_alt, *v0_alt;
+  int *tag_alt, *rep_alt, *cnt_alt, *nbr_alt;
+};
+void launch_sort(const SortArgs& a, cudaStream_t st);
 
 }  // namespace cgk

@@ -109,6 +109,21 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
   }
 }
 
+// Periodic reduction of a finite coordinate: v' = fmod(v, L) (exact), rounded
+// to the grid, then wrapped into [0, L) in integer grid units.  For v in
+// [-L, 2L) fmod is a single exact subtraction or nothing.
+__device__ __forceinline__ long long wrap_to_grid(double v, double L, double scale, long long LI) {
+  double r;
+  if (v >= 0.0 && v < L) r = v;
+  else if (v >= L && v < 2.0 * L) r = v - L;
+  else if (v < 0.0 && v >= -L) r = v;
+  else r = fmod(v, L);
+  long long X = (long long)rint(r * scale);
+  if (X < 0) X += LI;
+  else if (X >= LI) X -= LI;
+  return X;
+}
+
 // Position of cell i in the ring of cell j, or -1.
 __device__ __forceinline__ int ring_pos(const int* __restrict__ nbr, const int* __restrict__ cnt, int j, int i) {
   const int4* row = reinterpret_cast<const int4*>(nbr + (size_t)j * CG_RING);
@@ -172,7 +187,7 @@ __global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
   g.Fy[i] = fy;
   if (!g.integrate) return;
 
-  // Eq. 3: r <- r + dt (mu F + v0 n(theta)), snapped to the grid and wrapped;
+  // Eq. 3: r <- r + dt (mu F + v0 n(theta)), rounded to the grid and wrapped;
   // theta <- theta + sqrt(2 D_r dt) xi.
   const int cur = g.ctl->cur;
   const Rep R = g.reps[g.rep[i]];
@@ -184,13 +199,9 @@ __global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
   const double vx = g.mu * fx + v0 * cs, vy = g.mu * fy + v0 * sn;
   const double xn = xi + g.dt * vx, yn = yi + g.dt * vy;
   long long X, Y;
-  if (xn > -R.Lx && xn < 2.0 * R.Lx && yn > -R.Ly && yn < 2.0 * R.Ly) {  // also false for NaN
-    X = (long long)rint(xn * R.scale);
-    Y = (long long)rint(yn * R.scale);
-    if (X >= R.LX) X -= R.LX;
-    else if (X < 0) X += R.LX;
-    if (Y >= R.LY) Y -= R.LY;
-    else if (Y < 0) Y += R.LY;
+  if (isfinite(xn) && isfinite(yn)) {
+    X = wrap_to_grid(xn, R.Lx, R.scale, R.LX);
+    Y = wrap_to_grid(yn, R.Ly, R.scale, R.LY);
   } else {
     raise_status(g.ctl, kENONFINITE);
     X = (long long)rint(xi * R.scale);

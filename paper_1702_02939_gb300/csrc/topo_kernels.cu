@@ -22,19 +22,13 @@ namespace cgk {
 
 constexpr int kScanThreads = 256;
 constexpr int kScanPer = 8;
-constexpr int kScanChunk = kScanThreads * kScanPer;  // bins per scan block
+static_assert(kScanChunk == kScanThreads * kScanPer, "scan block size");
 
 __device__ __forceinline__ void bin_of(const Rep& R, double x, double y, int& bx, int& by) {
   bx = (int)(x / R.bsx);
   by = (int)(y / R.bsy);
   bx = bx < 0 ? 0 : (bx >= R.nbx ? R.nbx - 1 : bx);
   by = by < 0 ? 0 : (by >= R.nby ? R.nby - 1 : by);
-}
-
-// bin_start is stored as a block-local exclusive prefix plus one offset per
-// scan block; the global start of bin b is their sum.
-__device__ __forceinline__ int bin_begin(const int* local, const int* partial, int b) {
-  return local[b] + partial[b / kScanChunk];
 }
 
 __global__ void k_bin_count(CellListArgs g) {
@@ -92,7 +86,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_local(CellListArgs g) {
 // Exclusive scan of the block totals (one block); also records step statistics.
 __global__ void __launch_bounds__(1024) k_scan_partials(CellListArgs g, int nblocks) {
   Ctl* ctl = g.ctl;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && g.only_if_flagged) {  // per-step build: record statistics
     int c = ctl->count[0];
     ctl->last_flagged = c;
     ctl->flagged_total += c;
@@ -138,6 +132,12 @@ void launch_cell_list(const CellListArgs& a, cudaStream_t st) {
   k_scan_local<<<nblk, kScanThreads, 0, st>>>(a);
   k_scan_partials<<<1, 1024, 0, st>>>(a, nblk);
   k_bin_scatter<<<(a.n + 255) / 256, 256, 0, st>>>(a);
+}
+
+void launch_scan(const CellListArgs& a, cudaStream_t st) {
+  const int nblk = (a.nbins + 1 + kScanChunk - 1) / kScanChunk;
+  k_scan_local<<<nblk, kScanThreads, 0, st>>>(a);
+  k_scan_partials<<<1, 1024, 0, st>>>(a, nblk);
 }
 
 // ---------------------------------------------------------------------------

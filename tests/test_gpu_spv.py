@@ -177,3 +177,86 @@ def test_full_size_workload():
     gx, gy, _ = (t.cpu().numpy() for t in sim.state())
     check_topology(sim, gx, gy, Lx, Ly)
     sim.close()
+
+
+def test_hilbert_resort_leaves_results_bit_identical():
+    """Re-sorting the storage order (Sec. 2.B) must not change any result:
+    rings are canonical by cell index and every sum runs in ring order."""
+    n, Lr = 2000, None
+    x, y, th, L = workloads.spv_uniform(n, 41)
+    Lx, Ly, q = oracle.box(L)
+    xs, ys = oracle.snap_positions(x, y, Lx, Ly)
+    a = cg.SPV([dict(n=n, Lx=L, Ly=L, p0=3.9, v0=0.3)], xs, ys, th, seed=2, sort_every=0)
+    b = cg.SPV([dict(n=n, Lx=L, Ly=L, p0=3.9, v0=0.3)], xs, ys, th, seed=2, sort_every=7)
+    a.step(60)
+    b.step(60)
+    for ta, tb in zip(a.state(), b.state()):
+        assert torch.equal(ta, tb)
+    for ta, tb in zip(a.neighbors(), b.neighbors()):
+        assert torch.equal(ta, tb)
+    fa, fb = a.forces(), b.forces()
+    assert torch.equal(fa[0], fb[0]) and torch.equal(fa[1], fb[1])
+    gx, gy, _ = (t.cpu().numpy() for t in b.state())
+    check_topology(b, gx, gy, Lx, Ly)
+    a.close()
+    b.close()
+
+
+def test_batched_replicas_match_per_replica_oracle():
+    """Several independent systems of uneven size, box, p0 and v0 in one
+    context: each replica equals the oracle run on that replica alone."""
+    specs = [(300, 0.0, 3.7, 0.05), (1000, 5.0, 3.95, 0.3), (4096, 0.0, 3.85, 0.1), (700, 2.0, 4.05, 0.5)]
+    reps, xs_all, ys_all, th_all, boxes = [], [], [], [], []
+    for k, (n, extra, p0, v0) in enumerate(specs):
+        x, y, th, L = workloads.spv_uniform(n, 50 + k, None if not extra else (n ** 0.5 + extra))
+        Lx, Ly, q = oracle.box(L)
+        xs, ys = oracle.snap_positions(x, y, Lx, Ly)
+        reps.append(dict(n=n, Lx=L, Ly=L, p0=p0, v0=v0))
+        xs_all.append(xs); ys_all.append(ys); th_all.append(th); boxes.append((Lx, Ly))
+    sim = cg.SPV(reps, np.concatenate(xs_all), np.concatenate(ys_all), np.concatenate(th_all), seed=9)
+    cnt, nbr = (t.cpu().numpy() for t in sim.neighbors())
+    Fx, Fy, E = sim.forces()
+    Fx, Fy = Fx.cpu().numpy(), Fy.cpu().numpy()
+    sim.step(1)
+    gx, gy, gth = (t.cpu().numpy() for t in sim.state())
+    off = 0
+    for k, (n, extra, p0, v0) in enumerate(specs):
+        Lx, Ly = boxes[k]
+        sl = slice(off, off + n)
+        topo = oracle.triangulate(xs_all[k], ys_all[k], Lx, Ly)
+        np.testing.assert_array_equal(cnt[sl], topo.cnt)
+        local = np.where(nbr[sl] >= 0, nbr[sl] - off, -1)
+        np.testing.assert_array_equal(local, topo.nbr)
+        oFx, oFy, *_ = oracle.forces(xs_all[k], ys_all[k], Lx, Ly, topo, p0)
+        scale = max(np.abs(oFx).max(), np.abs(oFy).max())
+        assert np.abs(Fx[sl] - oFx).max() <= F_TOL * scale
+        assert np.abs(Fy[sl] - oFy).max() <= F_TOL * scale
+        # noise counters use the global cell index of the concatenated system
+        ox, oy, oth = oracle.integrate(xs_all[k], ys_all[k], th_all[k], oFx, oFy, Lx, Ly, v0, 1.0, 1.0, 0.01,
+                                       9, 0)
+        assert np.abs(wrapdiff(gx[sl], ox, Lx)).max() <= X_TOL * Lx
+        off += n
+    sim.close()
+
+
+def test_large_force_move_wraps_and_repairs():
+    """Two nearly coincident cells feel a very large force; the move of several
+    box lengths is wrapped modulo L exactly as in the oracle and the topology
+    is repaired to the exact triangulation."""
+    n = 256
+    x, y, th, L = workloads.spv_uniform(n, 77)
+    x = x.copy(); y = y.copy()
+    x[1] = x[0] + 1e-5
+    y[1] = y[0] + 2e-5
+    Lx, Ly, q = oracle.box(L)
+    xs, ys = oracle.snap_positions(x, y, Lx, Ly)
+    sim = cg.SPV([dict(n=n, Lx=L, Ly=L, p0=3.8, v0=0.1)], xs, ys, th, seed=4, dt=0.01)
+    Fx, Fy, E = sim.forces()
+    assert float(Fx.abs().max()) * 0.01 > L  # the step moves a cell farther than the box
+    sim.step(1)
+    gx, gy, gth = (t.cpu().numpy() for t in sim.state())
+    ox, oy, oth, _ = oracle.spv_run(xs, ys, th, Lx, Ly, 3.8, 0.1, 1, seed=4, dt=0.01)
+    assert np.abs(wrapdiff(gx, ox, Lx)).max() <= 1e-9 * Lx
+    assert np.abs(wrapdiff(gy, oy, Ly)).max() <= 1e-9 * Ly
+    check_topology(sim, gx, gy, Lx, Ly)
+    sim.close()
