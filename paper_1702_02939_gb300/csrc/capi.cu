@@ -128,12 +128,15 @@ bool build_reps(int R, const cg_replica* reps, std::vector<Rep>& out, int64_t& N
     p.Ly = std::ldexp((double)p.LY, -p.q);
     p.hLx = 0.5 * p.Lx;
     p.hLy = 0.5 * p.Ly;
-    // bins of about one mean cell spacing, at least 9 per side
+    // cell-list bins 2^bshift grid units wide (about one mean spacing, at least
+    // 9 per side); the last bin of each row absorbs the remainder of the box
     const double spacing = std::sqrt(p.Lx * p.Ly / c.n);
-    p.nbx = std::max(9, (int)std::floor(p.Lx / spacing));
-    p.nby = std::max(9, (int)std::floor(p.Ly / spacing));
-    p.bsx = p.Lx / p.nbx;
-    p.bsy = p.Ly / p.nby;
+    int bshift = (int)std::lround(std::log2(spacing)) + p.q;
+    while (bshift > 0 && ((p.LX >> bshift) < 9 || (p.LY >> bshift) < 9)) --bshift;
+    p.bshift = bshift;
+    p.nbx = (int)(p.LX >> bshift);
+    p.nby = (int)(p.LY >> bshift);
+    p.bsx = p.bsy = std::ldexp(1.0, bshift - p.q);
     // initial repair square: half-width W = 2^ceil(log2(max(L)/4)) >= L/4
     const int ew = ceil_log2(std::fmax(p.Lx, p.Ly) / 4.0);
     p.W2 = (long long)std::ldexp(2.0, ew + p.q);
@@ -144,6 +147,7 @@ bool build_reps(int R, const cg_replica* reps, std::vector<Rep>& out, int64_t& N
     p.p0 = c.p0;
     // Hilbert sort grid: the smallest power of two covering the bin grid
     p.hord = std::max(1, ceil_log2((double)std::max(p.nbx, p.nby)));
+    p.hshift = std::max(0, ceil_log2((double)std::max(p.LX, p.LY)) - p.hord);
     p.hkey0 = (int)NK;
     N += c.n;
     NB += (int64_t)p.nbx * p.nby;
@@ -197,8 +201,8 @@ GeomArgs geom_args(cg_ctx* c) {
   g.reps = c->at<Rep>(c->off.reps);
   g.rep = c->at<int>(c->off.rep);
   g.ctl = c->ctl();
-  g.x = c->at<double>(c->off.x);
-  g.y = c->at<double>(c->off.y);
+  g.X = c->at<long long>(c->off.X);
+  g.Y = c->at<long long>(c->off.Y);
   g.cnt = c->at<int>(c->off.cnt);
   g.nbr = c->at<int>(c->off.nbr);
   g.p0 = c->at<double>(c->off.p0);
@@ -266,8 +270,8 @@ CellListArgs cell_list_args(cg_ctx* c, int only_if_flagged) {
   a.reps = c->at<Rep>(c->off.reps);
   a.rep = c->at<int>(c->off.rep);
   a.ctl = c->ctl();
-  a.x = c->at<double>(c->off.x);
-  a.y = c->at<double>(c->off.y);
+  a.X = c->at<long long>(c->off.X);
+  a.Y = c->at<long long>(c->off.Y);
   a.bin_count = c->at<int>(c->off.bin_count);
   a.bin_start = c->at<int>(c->off.bin_start);
   a.cell_bin = c->at<int>(c->off.cell_bin);
@@ -354,12 +358,19 @@ SortArgs sort_args(cg_ctx* c) {
   return a;
 }
 
-int repair_grid(const cg_ctx* c) {
+int sm_count() {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms * 8;
+  return sms;
 }
+// Per-step repair rounds handle a few hundred flagged cells: a modest
+// persistent grid (warps loop over the list) keeps empty rounds cheap.
+int repair_grid(const cg_ctx*) { return sm_count() * 4; }
+int check_grid(const cg_ctx*) { return sm_count() * 2; }
+// Full triangulation: one warp per cell over every cell.
+int repair_grid_all(const cg_ctx*) { return sm_count() * 16; }
+int check_grid_all(const cg_ctx* c) { return (int)((c->N + 255) / 256); }
 
 // One time step, enqueued on stream st (also used for capture).
 void enqueue_step(cg_ctx* c, cudaStream_t st) {
@@ -373,7 +384,7 @@ void enqueue_step(cg_ctx* c, cudaStream_t st) {
   for (int r = 0; r < cap; ++r) {
     const int which = r & 1;
     launch_repair(repair_args(c, which, 0), grid, st);
-    launch_check(check_args(c, which, r == cap - 1, 0), st);
+    launch_check(check_args(c, which, r == cap - 1, 0), check_grid(c), st);
   }
 }
 
@@ -386,8 +397,8 @@ int triangulate_all(cg_ctx* c) {
   CG_CUDA(c, cudaMemsetAsync(c->at<int>(c->off.bin_count), 0, c->NB * sizeof(int), st));
   launch_begin_topology(c->ctl(), 0, st);
   launch_cell_list(cell_list_args(c, 0), st);
-  launch_repair(repair_args(c, 0, 1), repair_grid(c), st);
-  launch_check(check_args(c, 0, 1, 1), st);
+  launch_repair(repair_args(c, 0, 1), repair_grid_all(c), st);
+  launch_check(check_args(c, 0, 1, 1), check_grid_all(c), st);
   launch_begin_topology(c->ctl(), 0, st);
   CG_CUDA(c, cudaGetLastError());
   return CG_OK;
@@ -555,7 +566,7 @@ int cg_profile_step(cg_ctx* c, int64_t nsteps, double* ms_out, int32_t n_out) {
     cudaEventRecord(ev[4], st);
     for (int r = 0; r < cap; ++r) {
       launch_repair(repair_args(c, r & 1, 0), grid, st);
-      launch_check(check_args(c, r & 1, r == cap - 1, 0), st);
+      launch_check(check_args(c, r & 1, r == cap - 1, 0), check_grid(c), st);
     }
     cudaEventRecord(ev[5], st);
     if (cudaEventSynchronize(ev[5]) != cudaSuccess) { rc = fail(c, CG_ECUDA, "profile sync"); break; }

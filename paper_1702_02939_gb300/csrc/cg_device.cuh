@@ -40,7 +40,7 @@ enum : int {
 struct Rep {
   double Lx, Ly, hLx, hLy;  // box and half box (on the grid)
   double scale, inv_scale;  // 2^q and 2^-q
-  double bsx, bsy;          // cell-list bin size
+  double bsx, bsy;          // cell-list bin size (the last bin of a row is wider)
   long long LX, LY;         // box in grid units
   long long W2;             // twice the initial repair half-width, grid units
   int cell0, ncell;         // cell range
@@ -49,7 +49,17 @@ struct Rep {
   double v0, p0;            // defaults for the replica's cells
   int hord;                 // Hilbert curve order of the replica's sort grid
   int hkey0;                // first sort key of the replica
+  int bshift;               // cell-list bin width = 2^bshift grid units
+  int hshift;               // Hilbert grid cell = 2^hshift grid units
 };
+
+// Cell-list bin of a position in grid units (integer only: every bin is
+// 2^bshift grid units wide, the last bin of a row absorbs the remainder).
+__device__ __forceinline__ void bin_of_grid(const Rep& R, long long X, long long Y, int& bx, int& by) {
+  long long b = X >> R.bshift, c = Y >> R.bshift;
+  bx = (int)(b < R.nbx ? b : R.nbx - 1);
+  by = (int)(c < R.nby ? c : R.nby - 1);
+}
 
 // Mutable device globals of one context.
 struct Ctl {
@@ -188,12 +198,28 @@ static __device__ __noinline__ int incircle_rows_exact(long long ax, long long a
   return w256_sign(s);
 }
 
+// v * sc as a float for |v| < 2^51, without 64-bit conversion instructions
+// (which issue on the FP64 pipe of this GPU): |v| is split into 22-bit chunks,
+// each converted exactly by adding it to the bit pattern of 1.5 * 2^23 and
+// subtracting 1.5 * 2^23; two FMAs recombine them.  Relative error <= 2u + u^2
+// (u = 2^-24); sc must be a power of two.
+__device__ __forceinline__ float i2f_scaled(long long v, float sc) {
+  const bool neg = v < 0;
+  const unsigned long long a = neg ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int c0 = (int)(a & 0x3FFFFFull), c1 = (int)((a >> 22) & 0x3FFFFFull), c2 = (int)(a >> 44);
+  const float f0 = __int_as_float(0x4B400000 + c0) - 12582912.0f;
+  const float f1 = __int_as_float(0x4B400000 + c1) - 12582912.0f;
+  const float f2 = __int_as_float(0x4B400000 + c2) - 12582912.0f;
+  const float f = fmaf(f2, 0x1p44f, fmaf(f1, 0x1p22f, f0)) * sc;
+  return neg ? -f : f;
+}
+
 // Orientation of (0, a, b), coordinates in grid units; sc = 2^-q (float).
 __device__ __forceinline__ int orient_sign(long long ax, long long ay, long long bx, long long by, float sc) {
-  float fax = (float)ax * sc, fay = (float)ay * sc, fbx = (float)bx * sc, fby = (float)by * sc;
+  float fax = i2f_scaled(ax, sc), fay = i2f_scaled(ay, sc), fbx = i2f_scaled(bx, sc), fby = i2f_scaled(by, sc);
   float l = fax * fby, r = fay * fbx;
   float det = l - r;
-  // conversion (2u per product) + product (u) + difference (u): <= 6u * (|l|+|r|)
+  // conversion (<= 4u per product) + product (u) + difference (u): <= 6u * (|l|+|r|)
   float bound = 1.0e-6f * (fabsf(l) + fabsf(r));
   if (bound > 1.0e-30f) {
     if (det > bound) return 1;
@@ -210,13 +236,13 @@ __device__ __forceinline__ int incircle_sign(long long px, long long py, long lo
                                              long long rx, long long ry, long long sx, long long sy,
                                              int kp, int kq, int kr, int ks, float sc) {
   long long ax = px - sx, ay = py - sy, bx = qx - sx, by = qy - sy, cx = rx - sx, cy = ry - sy;
-  float fax = (float)ax * sc, fay = (float)ay * sc, fbx = (float)bx * sc, fby = (float)by * sc;
-  float fcx = (float)cx * sc, fcy = (float)cy * sc;
+  float fax = i2f_scaled(ax, sc), fay = i2f_scaled(ay, sc), fbx = i2f_scaled(bx, sc), fby = i2f_scaled(by, sc);
+  float fcx = i2f_scaled(cx, sc), fcy = i2f_scaled(cy, sc);
   float la = fax * fax + fay * fay, lb = fbx * fbx + fby * fby, lc = fcx * fcx + fcy * fcy;
   float t1 = fbx * fcy, t2 = fby * fcx, t3 = fcx * fay, t4 = fcy * fax, t5 = fax * fby, t6 = fay * fbx;
   float det = la * (t1 - t2) + lb * (t3 - t4) + lc * (t5 - t6);
   float perm = la * (fabsf(t1) + fabsf(t2)) + lb * (fabsf(t3) + fabsf(t4)) + lc * (fabsf(t5) + fabsf(t6));
-  // input conversion (<= 4u per monomial) + evaluation (<= 10u): 2e-6 ~ 34u.
+  // input conversion (<= 8u per degree-4 monomial) + evaluation (<= 10u): 2e-6 ~ 34u.
   float bound = 2.0e-6f * perm;
   if (bound > 1.0e-30f && bound < 1.0e30f) {
     if (det > bound) return 1;

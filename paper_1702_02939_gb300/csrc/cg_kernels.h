@@ -20,7 +20,7 @@ struct GeomArgs {
   const Rep* reps;
   const int* rep;
   Ctl* ctl;
-  const double *x, *y;  // [2][n] position buffers
+  const long long *X, *Y;  // [2][n] grid coordinates
   const int *cnt, *nbr;
   const double* p0;
   double A0, sqrtA0, KA, KP;
@@ -62,7 +62,7 @@ struct CellListArgs {
   const Rep* reps;
   const int* rep;
   Ctl* ctl;
-  const double *x, *y;  // [2][n]
+  const long long *X, *Y;  // [2][n] grid coordinates
   int *bin_count, *bin_start, *cell_bin, *cell_rank, *ids;
   int* scan_partials;
   int only_if_flagged;  // skip when nothing is flagged
@@ -105,7 +105,7 @@ void launch_cell_list(const CellListArgs& a, cudaStream_t st);
 void launch_repair(const RepairArgs& a, int grid_blocks, cudaStream_t st);
 // exclusive scan of a.bin_count[0..nbins) into (a.bin_start, a.scan_partials)
 void launch_scan(const CellListArgs& a, cudaStream_t st);
-void launch_check(const CheckArgs& a, cudaStream_t st);
+void launch_check(const CheckArgs& a, int grid_blocks, cudaStream_t st);
 
 // state preparation and user-order transfers
 void launch_snap(int n, const Rep* reps, const int* rep, const double* xin, const double* yin, double* x,

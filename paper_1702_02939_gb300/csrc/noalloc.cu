@@ -32,7 +32,7 @@ using namespace cgk;
 namespace {
 
 constexpr int kMaxCells = CG_NOALLOC_MAX_CELLS;
-constexpr int kMaxBins = 2 * CG_NOALLOC_MAX_CELLS;
+constexpr int kMaxBins = 4 * CG_NOALLOC_MAX_CELLS;
 constexpr int kScanChunk = 256 * 8;  // bins per scan block of the cell-list kernels
 constexpr int kMaxPartials = (kMaxBins + 1 + kScanChunk - 1) / kScanChunk + 1;
 
@@ -105,12 +105,16 @@ bool make_rep(int n, double Lx, double Ly, Rep& p) {
   p.Ly = std::ldexp((double)p.LY, -p.q);
   p.hLx = 0.5 * p.Lx;
   p.hLy = 0.5 * p.Ly;
+  // cell-list bins 2^bshift grid units wide (about one mean spacing, at least
+  // 9 per side); the last bin of each row absorbs the remainder of the box
   const double spacing = std::sqrt(p.Lx * p.Ly / n);
-  p.nbx = std::max(9, (int)std::floor(p.Lx / spacing));
-  p.nby = std::max(9, (int)std::floor(p.Ly / spacing));
+  int bshift = (int)std::lround(std::log2(spacing)) + p.q;
+  while (bshift > 0 && ((p.LX >> bshift) < 9 || (p.LY >> bshift) < 9)) --bshift;
+  p.bshift = bshift;
+  p.nbx = (int)(p.LX >> bshift);
+  p.nby = (int)(p.LY >> bshift);
+  p.bsx = p.bsy = std::ldexp(1.0, bshift - p.q);
   if ((long long)p.nbx * p.nby > kMaxBins) return false;
-  p.bsx = p.Lx / p.nbx;
-  p.bsy = p.Ly / p.nby;
   const int ew = ceil_log2(std::fmax(p.Lx, p.Ly) / 4.0);
   p.W2 = (long long)std::ldexp(2.0, ew + p.q);
   p.cell0 = 0;
@@ -168,8 +172,8 @@ extern "C" int cg_triangulate_noalloc(int32_t n, double Lx, double Ly, const dou
   cl.reps = d_rep;
   cl.rep = repi;
   cl.ctl = ctl;
-  cl.x = x;
-  cl.y = y;
+  cl.X = X;
+  cl.Y = Y;
   cl.bin_count = reinterpret_cast<int*>(base + kOffBinCount);
   cl.bin_start = reinterpret_cast<int*>(base + kOffBinStart);
   cl.cell_bin = reinterpret_cast<int*>(base + kOffCellBin);
@@ -219,7 +223,7 @@ extern "C" int cg_triangulate_noalloc(int32_t n, double Lx, double Ly, const dou
   ck.which_out = 1;
   ck.last_round = 1;
   ck.all_cells = 1;
-  launch_check(ck, st);
+  launch_check(ck, (n + 255) / 256, st);
 
   launch_gather_ring(n, tag, cnt, nbr, d_cnt, d_nbr, st);
   if (cudaGetLastError() != cudaSuccess) return CG_ECUDA;

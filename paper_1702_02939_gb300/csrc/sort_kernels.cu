@@ -41,8 +41,8 @@ __global__ void k_sort_keys(SortArgs g) {
   const int cur = g.ctl->cur;
   const Rep R = g.reps[g.rep[i]];
   const unsigned side = 1u << R.hord;
-  unsigned gx = (unsigned)(g.x[(size_t)cur * g.n + i] / R.Lx * side);
-  unsigned gy = (unsigned)(g.y[(size_t)cur * g.n + i] / R.Ly * side);
+  unsigned gx = (unsigned)(g.X[(size_t)cur * g.n + i] >> R.hshift);
+  unsigned gy = (unsigned)(g.Y[(size_t)cur * g.n + i] >> R.hshift);
   gx = gx >= side ? side - 1 : gx;
   gy = gy >= side ? side - 1 : gy;
   const int key = R.hkey0 + (int)hilbert_index(R.hord, gx, gy);

@@ -19,31 +19,55 @@
 
 namespace cgk {
 
+// Exact int64 -> double for |v| < 2^51: v added to the bit pattern of 1.5 * 2^52
+// (integer pipe) lands in [2^52, 2^53) where doubles are spaced by one; one
+// FP64 subtraction removes the offset.
+__device__ __forceinline__ double i2d_exact(long long v) {
+  return __longlong_as_double(0x4338000000000000LL + v) - 0x1.8p52;
+}
+
+// 1/d to ~1 ulp: hardware reciprocal approximation refined by two Newton steps
+// (each squares the relative error), 4 FP64 FMAs instead of an IEEE division.
+__device__ __forceinline__ double fast_rcp(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
 // One thread per cell.  Writes A, P, force sets fs[a][i] = dE_i/dh_a, and the
 // per-slot Jacobian factors s[a][i] = u_a / det_a and w[a][i].
+//
+// The geometry runs in grid units (coordinates x 2^q): relative positions come
+// exactly from the int64 grid coordinates, and the powers of two cancel in the
+// force (u/det scales as 2^q, w as 2^-q) or fold into one factor per cell
+// (A x 2^-2q, P x 2^-q, dA/dh x 2^-q).
 __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
   __shared__ double sh_hx[CG_RING][kGeomThreads];
   __shared__ double sh_hy[CG_RING][kGeomThreads];
-  __shared__ double sh_il[CG_RING][kGeomThreads];
+  __shared__ double sh_ex[CG_RING][kGeomThreads];  // unit vector of the edge ending at vertex a
+  __shared__ double sh_ey[CG_RING][kGeomThreads];
   const int t = threadIdx.x;
   const int i = blockIdx.x * kGeomThreads + t;
   if (i >= g.n) return;
+  const size_t N = (size_t)g.n;
   const int cur = g.ctl->cur;
-  const double* __restrict__ x = g.x + (size_t)cur * g.n;
-  const double* __restrict__ y = g.y + (size_t)cur * g.n;
+  const long long* __restrict__ X = g.X + (size_t)cur * N;
+  const long long* __restrict__ Y = g.Y + (size_t)cur * N;
   const Rep R = g.reps[g.rep[i]];
-  const double xi = x[i], yi = y[i];
+  const long long Xi = X[i], Yi = Y[i];
   const int m = g.cnt[i];
   if (m < 3 || m > CG_RING) {
     raise_status(g.ctl, kETOPO);
     return;
   }
   const int* ring = g.nbr + (size_t)i * CG_RING;
-  const size_t N = (size_t)g.n;
 
-  int j0 = ring[0];
-  const double d0x = min_image(x[j0] - xi, R.Lx, R.hLx);
-  const double d0y = min_image(y[j0] - yi, R.Ly, R.hLy);
+  const int j0 = ring[0];
+  const double d0x = i2d_exact(min_image_i(X[j0] - Xi, R.LX));
+  const double d0y = i2d_exact(min_image_i(Y[j0] - Yi, R.LY));
   const double l0 = d0x * d0x + d0y * d0y;
   double ax = d0x, ay = d0y, la = l0;
   double hpx = 0.0, hpy = 0.0, h0x = 0.0, h0y = 0.0;
@@ -51,19 +75,20 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
   for (int a = 0; a < m; ++a) {
     double bx, by, lb;
     if (a + 1 < m) {
-      int j = ring[a + 1];
-      bx = min_image(x[j] - xi, R.Lx, R.hLx);
-      by = min_image(y[j] - yi, R.Ly, R.hLy);
+      const int j = ring[a + 1];
+      bx = i2d_exact(min_image_i(X[j] - Xi, R.LX));
+      by = i2d_exact(min_image_i(Y[j] - Yi, R.LY));
       lb = bx * bx + by * by;
     } else {
       bx = d0x; by = d0y; lb = l0;
     }
     const double det = ax * by - ay * bx;  // (r_j - r_i) x (r_k - r_i)
-    const double inv = 1.0 / det;
+    const double r = fast_rcp(det);
+    const double hr = 0.5 * r;
     // circumcentre relative to r_i
-    const double hx = 0.5 * (by * la - ay * lb) * inv;
-    const double hy = 0.5 * (ax * lb - bx * la) * inv;
-    g.s[a * N + i] = make_double2(hx * inv, hy * inv);
+    const double hx = (by * la - ay * lb) * hr;
+    const double hy = (ax * lb - bx * la) * hr;
+    g.s[a * N + i] = make_double2(hx * r, hy * r);
     g.w[a * N + i] = make_double2(by - ay, ax - bx);
     sh_hx[a][t] = hx;
     sh_hy[a][t] = hy;
@@ -75,7 +100,8 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
       const double l2 = ex * ex + ey * ey;
       const double il = rsqrt(l2);
       per += l2 * il;
-      sh_il[a][t] = il;
+      sh_ex[a][t] = ex * il;
+      sh_ey[a][t] = ey * il;
     }
     hpx = hx; hpy = hy;
     ax = bx; ay = by; la = lb;
@@ -86,26 +112,24 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
     const double l2 = ex * ex + ey * ey;
     const double il = rsqrt(l2);
     per += l2 * il;
-    sh_il[0][t] = il;
+    sh_ex[0][t] = ex * il;
+    sh_ey[0][t] = ey * il;
   }
-  const double A = 0.5 * area, P = per;
+  const double sc = R.inv_scale;
+  const double A = 0.5 * area * sc * sc, P = per * sc;
   g.A[i] = A;
   g.P[i] = P;
   const double dA = A - g.A0, dP = P - g.p0[i] * g.sqrtA0;
   if (g.energy_out) g.energy_out[i] = g.KA * dA * dA + g.KP * dP * dP;
-  const double ka = 2.0 * g.KA * dA, kp = 2.0 * g.KP * dP;
+  // dA/dh = 1/2 perp(h_next - h_prev) (the 1/2 and the grid scale fold into ka);
+  // dP/dh = e_in - e_out (unit edge vectors)
+  const double ka = g.KA * dA * sc, kp = 2.0 * g.KP * dP;
   for (int a = 0; a < m; ++a) {
     const int ap = (a == 0) ? m - 1 : a - 1;
     const int an = (a + 1 == m) ? 0 : a + 1;
-    const double hx = sh_hx[a][t], hy = sh_hy[a][t];
-    const double px = sh_hx[ap][t], py = sh_hy[ap][t];
-    const double nx = sh_hx[an][t], ny = sh_hy[an][t];
-    // dA/dh = 1/2 perp(h_next - h_prev); dP/dh = e_in - e_out (unit edge vectors)
-    const double dAx = 0.5 * (ny - py), dAy = 0.5 * (px - nx);
-    const double ilin = sh_il[a][t], ilout = sh_il[an][t];
-    const double dPx = (hx - px) * ilin - (nx - hx) * ilout;
-    const double dPy = (hy - py) * ilin - (ny - hy) * ilout;
-    g.fs[a * N + i] = make_double2(ka * dAx + kp * dPx, ka * dAy + kp * dPy);
+    const double gx = sh_hy[an][t] - sh_hy[ap][t], gy = sh_hx[ap][t] - sh_hx[an][t];
+    const double dPx = sh_ex[a][t] - sh_ex[an][t], dPy = sh_ey[a][t] - sh_ey[an][t];
+    g.fs[a * N + i] = make_double2(fma(ka, gx, kp * dPx), fma(ka, gy, kp * dPy));
   }
 }
 

@@ -24,13 +24,6 @@ constexpr int kScanThreads = 256;
 constexpr int kScanPer = 8;
 static_assert(kScanChunk == kScanThreads * kScanPer, "scan block size");
 
-__device__ __forceinline__ void bin_of(const Rep& R, double x, double y, int& bx, int& by) {
-  bx = (int)(x / R.bsx);
-  by = (int)(y / R.bsy);
-  bx = bx < 0 ? 0 : (bx >= R.nbx ? R.nbx - 1 : bx);
-  by = by < 0 ? 0 : (by >= R.nby ? R.nby - 1 : by);
-}
-
 __global__ void k_bin_count(CellListArgs g) {
   if (g.only_if_flagged && g.ctl->count[0] == 0) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -38,7 +31,7 @@ __global__ void k_bin_count(CellListArgs g) {
   const int cur = g.ctl->cur;
   const Rep R = g.reps[g.rep[i]];
   int bx, by;
-  bin_of(R, g.x[(size_t)cur * g.n + i], g.y[(size_t)cur * g.n + i], bx, by);
+  bin_of_grid(R, g.X[(size_t)cur * g.n + i], g.Y[(size_t)cur * g.n + i], bx, by);
   const int b = R.bin0 + by * R.nbx + bx;
   g.cell_bin[i] = b;
   g.cell_rank[i] = atomicAdd(&g.bin_count[b], 1);
@@ -144,29 +137,52 @@ void launch_scan(const CellListArgs& a, cudaStream_t st) {
 // Repair: one warp per cell.
 // ---------------------------------------------------------------------------
 
-// Circumcentre of (0, a, b) in real units (for the security radius only).
-__device__ __forceinline__ void circ_rel(long long aX, long long aY, long long bX, long long bY, double inv_scale,
-                                         double& vx, double& vy) {
-  // exact determinant in grid units^2, then rounded
-  s128 D = (s128)aX * bY - (s128)aY * bX;
-  long long dhi = (long long)(D >> 64);
-  unsigned long long dlo = (unsigned long long)D;
-  double det = ((double)dhi * 0x1.0p64 + (double)dlo) * inv_scale * inv_scale;
-  double ax = (double)aX * inv_scale, ay = (double)aY * inv_scale;
-  double bx = (double)bX * inv_scale, by = (double)bY * inv_scale;
-  double la = ax * ax + ay * ay, lb = bx * bx + by * by;
-  if (det == 0.0) {
-    vx = vy = 1e300;
-    return;
-  }
-  double inv = 0.5 / det;
-  vx = (by * la - ay * lb) * inv;
-  vy = (ax * lb - bx * la) * inv;
+// Upper bound on |v|^2 for the polygon vertex v = circumcentre of (0, a, b)
+// (real units; a, b in grid units).  Used only for the security radius, so it
+// may over-estimate but never under-estimate.  Single precision with a
+// first-order error bound: inputs carry relative error <= 2u (u = 2^-24, see
+// i2f_scaled), the determinant is accepted when its error bound is below 1/64
+// of it; otherwise (nearly collinear generators) the vertex is recomputed in
+// double precision from the exact integer determinant.
+__device__ __noinline__ float vertex_r2_fp64(long long aX, long long aY, long long bX, long long bY, double inv_scale) {
+  const s128 D = (s128)aX * bY - (s128)aY * bX;
+  const long long dhi = (long long)(D >> 64);
+  const unsigned long long dlo = (unsigned long long)D;
+  const double det = ((double)dhi * 0x1.0p64 + (double)dlo) * inv_scale * inv_scale;
+  if (det == 0.0) return 3.0e38f;
+  const double ax = (double)aX * inv_scale, ay = (double)aY * inv_scale;
+  const double bx = (double)bX * inv_scale, by = (double)bY * inv_scale;
+  const double la = ax * ax + ay * ay, lb = bx * bx + by * by;
+  const double inv = 0.5 / det;
+  const double vx = (by * la - ay * lb) * inv, vy = (ax * lb - bx * la) * inv;
+  const double r2 = (vx * vx + vy * vy) * (1.0 + 1e-9);
+  return r2 < 3.0e38 ? (float)r2 * 1.000001f : 3.0e38f;
 }
 
-__device__ __forceinline__ double warp_max(double v) {
+__device__ __forceinline__ float vertex_r2_bound(long long aX, long long aY, long long bX, long long bY, float sc,
+                                                 double inv_scale) {
+  const float u = 0x1p-24f;
+  const float ax = i2f_scaled(aX, sc), ay = i2f_scaled(aY, sc), bx = i2f_scaled(bX, sc), by = i2f_scaled(bY, sc);
+  const float p1 = ax * by, p2 = ay * bx;
+  const float det = p1 - p2;
+  const float edet = 8.0f * u * (fabsf(p1) + fabsf(p2));
+  if (!(fabsf(det) > 64.0f * edet) || !(fabsf(det) > 1e-30f)) return vertex_r2_fp64(aX, aY, bX, bY, inv_scale);
+  const float la = ax * ax + ay * ay, lb = bx * bx + by * by;
+  const float n1 = by * la, n2 = ay * lb, n3 = ax * lb, n4 = bx * la;
+  const float hinv = 0.5f / det;
+  const float hx = (n1 - n2) * hinv, hy = (n3 - n4) * hinv;
+  // numerator: 6u from the inputs of the degree-3 terms + 4u from evaluation
+  const float ad = fabsf(det);
+  const float rel = edet / ad;  // <= 1/64
+  const float dhx = (10.0f * u * (fabsf(n1) + fabsf(n2)) * 0.5f / ad + fabsf(hx) * rel) * 1.05f;
+  const float dhy = (10.0f * u * (fabsf(n3) + fabsf(n4)) * 0.5f / ad + fabsf(hy) * rel) * 1.05f;
+  const float r = sqrtf(hx * hx + hy * hy) * (1.0f + 4.0f * u) + sqrtf(dhx * dhx + dhy * dhy);
+  return r * r * (1.0f + 8.0f * u);
+}
+
+__device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
@@ -186,15 +202,15 @@ __device__ __forceinline__ void ring_bin(int k, int idx, int& dx, int& dy) {
 struct Poly {
   long long gX, gY;  // this lane's generator (grid units, relative to the cell)
   int gid, gkey;     // generator cell index (phantoms < 0) and perturbation key
-  double vx, vy;     // vertex between this generator and the next
+  float r2;          // upper bound of |v|^2, v = vertex between this generator and the next
   int m;             // generators in use (warp-uniform)
-  double R2;         // max |v|^2 (warp-uniform)
+  float R2;          // max over the polygon of r2 (warp-uniform)
   int err;
 };
 
 constexpr int kPhantomKey = INT_MAX - 8;
-constexpr double kSelfKey = 1e307;  // sort key of the cell itself
-constexpr double kPadKey = 1e308;   // sort key of unused buffer slots
+constexpr float kSelfKey = 1e37f;  // sort key of the cell itself
+constexpr float kPadKey = 3e38f;   // sort key of unused buffer slots
 
 // Clip the polygon by the bisector of candidate j.
 __device__ __forceinline__ void clip(Poly& p, long long jX, long long jY, int jid, int jkey, int ikey, float sc,
@@ -223,23 +239,21 @@ __device__ __forceinline__ void clip(Poly& p, long long jX, long long jY, int ji
   long long ngY = __shfl_sync(0xffffffffu, p.gY, src);
   int ngid = __shfl_sync(0xffffffffu, p.gid, src);
   int ngkey = __shfl_sync(0xffffffffu, p.gkey, src);
-  double nvx = __shfl_sync(0xffffffffu, p.vx, src);
-  double nvy = __shfl_sync(0xffffffffu, p.vy, src);
+  float nr2 = __shfl_sync(0xffffffffu, p.r2, src);
   if (lane == m2 - 1) { ngX = jX; ngY = jY; ngid = jid; ngkey = jkey; }
-  p.gX = ngX; p.gY = ngY; p.gid = ngid; p.gkey = ngkey; p.vx = nvx; p.vy = nvy;
+  p.gX = ngX; p.gY = ngY; p.gid = ngid; p.gkey = ngkey; p.r2 = nr2;
   p.m = m2;
   const int nl2 = (lane + 1 == m2) ? 0 : (lane + 1) % 32;
   const long long n2X = __shfl_sync(0xffffffffu, p.gX, nl2);
   const long long n2Y = __shfl_sync(0xffffffffu, p.gY, nl2);
-  if (lane == m2 - 2 || lane == m2 - 1) circ_rel(p.gX, p.gY, n2X, n2Y, inv_scale, p.vx, p.vy);
-  const double v2 = (lane < m2) ? p.vx * p.vx + p.vy * p.vy : 0.0;
-  p.R2 = warp_max(v2);
+  if (lane == m2 - 2 || lane == m2 - 1) p.r2 = vertex_r2_bound(p.gX, p.gY, n2X, n2Y, sc, inv_scale);
+  p.R2 = warp_max(lane < m2 ? p.r2 : 0.0f);
 }
 
 // Sort the warp's candidate buffer by squared distance (bitonic, 64 entries)
 // and clip with every candidate that can still reach the polygon.
-__device__ void process_candidates(Poly& p, int nbuf, int* s_id, long long* s_X, long long* s_Y, double* s_d2,
-                                   double* s_key, int* s_val, const int* tag, int ikey, float sc, double inv_scale,
+__device__ void process_candidates(Poly& p, int nbuf, int* s_id, long long* s_X, long long* s_Y, float* s_d2,
+                                   float* s_key, int* s_val, const int* tag, int ikey, float sc, double inv_scale,
                                    int lane) {
   if (nbuf == 0) return;
   for (int q = lane; q < kCand; q += 32) {
@@ -250,13 +264,13 @@ __device__ void process_candidates(Poly& p, int nbuf, int* s_id, long long* s_X,
   for (int k = 2; k <= kCand; k <<= 1) {
     for (int jj = k >> 1; jj > 0; jj >>= 1) {
       for (int q = lane; q < kCand; q += 32) {
-        int partner = q ^ jj;
+        const int partner = q ^ jj;
         if (partner > q) {
-          bool up = (q & k) == 0;
-          double a = s_key[q], b = s_key[partner];
+          const bool up = (q & k) == 0;
+          const float a = s_key[q], b = s_key[partner];
           if ((a > b) == up) {
             s_key[q] = b; s_key[partner] = a;
-            int t = s_val[q]; s_val[q] = s_val[partner]; s_val[partner] = t;
+            const int t = s_val[q]; s_val[q] = s_val[partner]; s_val[partner] = t;
           }
         }
       }
@@ -264,10 +278,11 @@ __device__ void process_candidates(Poly& p, int nbuf, int* s_id, long long* s_X,
     }
   }
   for (int c = 0; c < nbuf; ++c) {
-    const double d2 = s_key[c];
+    const float d2 = s_key[c];
     if (d2 >= kSelfKey) break;  // the cell itself and padding sort last
     // a cell can cut the polygon only if it is nearer than twice its circumradius
-    if (d2 > 4.0 * p.R2 * (1.0 + 1e-3)) break;
+    // (d2 carries a relative error below 1e-6; the margin is 1e-3)
+    if (d2 > 4.0f * p.R2 * (1.0f + 1e-3f)) break;
     const int e = s_val[c];
     const int jid = s_id[e];
     clip(p, s_X[e], s_Y[e], jid, tag[jid], ikey, sc, inv_scale, lane);
@@ -279,8 +294,8 @@ __device__ void process_candidates(Poly& p, int nbuf, int* s_id, long long* s_X,
 __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
   __shared__ int s_id[kRepairWarps][kCand];
   __shared__ long long s_X[kRepairWarps][kCand], s_Y[kRepairWarps][kCand];
-  __shared__ double s_d2[kRepairWarps][kCand];
-  __shared__ double s_key[kRepairWarps][kCand];
+  __shared__ float s_d2[kRepairWarps][kCand];
+  __shared__ float s_key[kRepairWarps][kCand];
   __shared__ int s_val[kRepairWarps][kCand];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gw = blockIdx.x * kRepairWarps + wib, nw = gridDim.x * kRepairWarps;
@@ -292,8 +307,6 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
   const size_t N = (size_t)g.n;
   const long long* __restrict__ X = g.X + cur * N;
   const long long* __restrict__ Y = g.Y + cur * N;
-  const double* __restrict__ x = g.x + cur * N;
-  const double* __restrict__ y = g.y + cur * N;
   if (blockIdx.x == 0 && threadIdx.x == 0 && !g.all_cells) {
     atomicAdd(&g.ctl->round_count, 1);
     atomicAdd((unsigned long long*)&g.ctl->repaired_total, (unsigned long long)total);
@@ -310,8 +323,8 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
     if (lane < CG_RING) g.old_nbr[(size_t)i * CG_RING + lane] = g.nbr[(size_t)i * CG_RING + lane];
     if (lane == 0) g.old_cnt[i] = oc;
 
-    // initial polygon: the square of half-width W, cut out by four phantom
-    // generators at (+-2W, 0) and (0, +-2W)
+    // initial polygon: the square of half-width W (vertices (+-W, +-W)), cut
+    // out by four phantom generators at (+-2W, 0) and (0, +-2W)
     Poly p;
     p.m = 4;
     p.err = 0;
@@ -320,14 +333,13 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
     p.gid = -1 - (lane & 3);
     p.gkey = kPhantomKey + (lane & 3);
     {
-      const int nl = (lane + 1) & 3;
-      const long long nX = __shfl_sync(0xffffffffu, p.gX, nl), nY = __shfl_sync(0xffffffffu, p.gY, nl);
-      circ_rel(p.gX, p.gY, nX, nY, R.inv_scale, p.vx, p.vy);
-      p.R2 = warp_max(lane < 4 ? p.vx * p.vx + p.vy * p.vy : 0.0);
+      const float W = 0.5f * i2f_scaled(R.W2, sc);  // power of two: exact
+      p.r2 = 2.0f * W * W;
+      p.R2 = p.r2;
     }
     int bxi, byi;
-    bin_of(R, x[i], y[i], bxi, byi);
-    const double bs = fmin(R.bsx, R.bsy);
+    bin_of_grid(R, Xi, Yi, bxi, byi);
+    const float bs = (float)R.bsx;  // every bin is at least this wide
     const int kmax = min((R.nbx - 1) / 2, (R.nby - 1) / 2);
     int nbuf = 0;
     bool done = false;
@@ -370,7 +382,7 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
               s_Y[wib][slot] = 0;
             } else {
               const long long dX = min_image_i(X[j] - Xi, R.LX), dY = min_image_i(Y[j] - Yi, R.LY);
-              const double dx = (double)dX * R.inv_scale, dy = (double)dY * R.inv_scale;
+              const float dx = i2f_scaled(dX, sc), dy = i2f_scaled(dY, sc);
               s_d2[wib][slot] = dx * dx + dy * dy;
               s_id[wib][slot] = j;
               s_X[wib][slot] = dX;
@@ -383,12 +395,14 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
         __syncwarp();
       }
       if (p.err) break;
+      // rings 0..2 are gathered into one batch before clipping
+      if (k < 2 && k < kmax) continue;
       process_candidates(p, nbuf, s_id[wib], s_X[wib], s_Y[wib], s_d2[wib], s_key[wib], s_val[wib], g.tag, ikey,
                          sc, R.inv_scale, lane);
       nbuf = 0;
       // every unvisited cell is farther than k*bs from cell i
-      const double reach = k * bs;
-      if (reach * reach > 4.0 * p.R2 * (1.0 + 1e-3)) done = true;
+      const float reach = k * bs;
+      if (reach * reach > 4.0f * p.R2 * (1.0f + 1e-3f)) done = true;
     }
     int err = p.err;
     if (!err && !done) err = kEBOX;
@@ -447,39 +461,38 @@ __device__ __forceinline__ void flag_into(unsigned* flags, int* list, int* count
 
 __global__ void k_check(CheckArgs g) {
   const int total = g.all_cells ? g.n : g.ctl->count[g.which_in];
-  const int item = blockIdx.x * blockDim.x + threadIdx.x;
-  if (item >= total) return;
-  const int i = g.all_cells ? item : g.list_in[item];
   int* count_out = &g.ctl->count[g.which_out];
-  const int m = g.cnt[i];
-  const int* row = g.nbr + (size_t)i * CG_RING;
-  bool bad = false;
-  for (int a = 0; a < m; ++a) {
-    const int j = row[a];
-    if (!in_ring(g.nbr, g.cnt, j, i)) {
-      flag_into(g.flags, g.list_out, count_out, j);
-      bad = true;
+  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
+    const int i = g.all_cells ? item : g.list_in[item];
+    const int m = g.cnt[i];
+    const int* row = g.nbr + (size_t)i * CG_RING;
+    bool bad = false;
+    for (int a = 0; a < m; ++a) {
+      const int j = row[a];
+      if (!in_ring(g.nbr, g.cnt, j, i)) {
+        flag_into(g.flags, g.list_out, count_out, j);
+        bad = true;
+      }
     }
-  }
-  const int om = g.old_cnt[i];
-  const int* orow = g.old_nbr + (size_t)i * CG_RING;
-  for (int b = 0; b < om; ++b) {
-    const int j = orow[b];
-    if (j < 0 || j >= g.n) continue;
-    bool kept = false;
-    for (int a = 0; a < m; ++a) kept |= (row[a] == j);
-    if (!kept && in_ring(g.nbr, g.cnt, j, i)) {
-      flag_into(g.flags, g.list_out, count_out, j);
-      bad = true;
+    const int om = g.old_cnt[i];
+    const int* orow = g.old_nbr + (size_t)i * CG_RING;
+    for (int b = 0; b < om; ++b) {
+      const int j = orow[b];
+      if (j < 0 || j >= g.n) continue;
+      bool kept = false;
+      for (int a = 0; a < m; ++a) kept |= (row[a] == j);
+      if (!kept && in_ring(g.nbr, g.cnt, j, i)) {
+        flag_into(g.flags, g.list_out, count_out, j);
+        bad = true;
+      }
     }
+    if (bad && g.last_round) raise_status(g.ctl, kEREPAIR_CAP);
   }
-  if (bad && g.last_round) raise_status(g.ctl, kEREPAIR_CAP);
 }
 
-void launch_check(const CheckArgs& a, cudaStream_t st) {
+void launch_check(const CheckArgs& a, int grid_blocks, cudaStream_t st) {
   if (a.n <= 0) return;
-  // sized for the worst case; threads beyond the device-side count exit
-  k_check<<<(a.n + 255) / 256, 256, 0, st>>>(a);
+  k_check<<<grid_blocks, 256, 0, st>>>(a);
 }
 
 // ---------------------------------------------------------------------------
