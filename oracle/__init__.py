@@ -248,3 +248,59 @@ def spv_window_step(x, y, theta, Lx, Ly, p0, v0, seed, step, cx, cy, hw, margin=
     if k < 0:
         raise OracleError(f"window step failed with code {k}")
     return x, y, theta, k
+
+
+def _declare_adjoint(L):
+    L.cgo_hvp.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _ip, _ip, _ip, C.c_int, _dp, _dp, _dp, _dp,
+                          _dp, _dp, _dp, _dp]
+    L.cgo_hvp.restype = C.c_int
+    L.cgo_geom_grad.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _ip, _ip, _ip, C.c_int, _dp, _dp, _dp,
+                                _dp]
+    L.cgo_geom_grad.restype = C.c_int
+    L.cgo_spv_backward.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp, C.c_uint64,
+                                   C.c_int64, C.c_int64, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                   _dp, _dp]
+    L.cgo_spv_backward.restype = C.c_int
+
+
+def _f64(a, n):
+    return np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), (n,)))
+
+
+def hvp(x, y, Lx, Ly, topo, p0, vx, vy, A0=1.0, KA=1.0, KP=1.0):
+    """H v (Hessian of E times v) and dA/dv, dP/dv on the given topology."""
+    n = len(x)
+    x, y, vx, vy, p0 = _f64(x, n), _f64(y, n), _f64(vx, n), _f64(vy, n), _f64(p0, n)
+    mech = np.array([A0, KA, KP], np.float64)
+    Hx, Hy, Ad, Pd = np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n)
+    _check(lib().cgo_hvp(n, Lx, Ly, _d(x), _d(y), _i(topo.cnt), _i(topo.nbr), _i(topo.off), MAX_RING, _d(p0),
+                         _d(mech), _d(vx), _d(vy), _d(Hx), _d(Hy), _d(Ad), _d(Pd)), "hvp")
+    return Hx, Hy, Ad, Pd
+
+
+def geom_grad(x, y, Lx, Ly, topo, cA, cP):
+    """Gradient of sum_c (cA_c A_c + cP_c P_c) with respect to the positions."""
+    n = len(x)
+    x, y, cA, cP = _f64(x, n), _f64(y, n), _f64(cA, n), _f64(cP, n)
+    gx, gy = np.zeros(n), np.zeros(n)
+    _check(lib().cgo_geom_grad(n, Lx, Ly, _d(x), _d(y), _i(topo.cnt), _i(topo.nbr), _i(topo.off), MAX_RING,
+                               _d(cA), _d(cP), _d(gx), _d(gy)), "geom_grad")
+    return gx, gy
+
+
+def spv_backward(x0, y0, theta0, Lx, Ly, p0, v0, nsteps, seed, gxT, gyT, gAT, gPT, step0=0, A0=1.0, KA=1.0,
+                 KP=1.0, mu=1.0, Dr=1.0, dt=0.01):
+    """Forward run plus reverse pass.  Returns dict with the final state
+    (x, y, A, P) and the cotangents gx0, gy0, gp0, gv0 (per cell), gKA, gKP."""
+    n = len(x0)
+    x0, y0, th, p0, v0 = _f64(x0, n), _f64(y0, n), _f64(theta0, n), _f64(p0, n), _f64(v0, n)
+    gxT, gyT, gAT, gPT = _f64(gxT, n), _f64(gyT, n), _f64(gAT, n), _f64(gPT, n)
+    par = np.array([A0, KA, KP, mu, Dr, dt], np.float64)
+    out = {k: np.zeros(n) for k in ("x", "y", "A", "P", "gx0", "gy0", "gp0", "gv0")}
+    gK = np.zeros(2)
+    _check(lib().cgo_spv_backward(n, Lx, Ly, _d(x0), _d(y0), _d(th), _d(p0), _d(v0), _d(par), int(seed), int(step0),
+                                  int(nsteps), _d(gxT), _d(gyT), _d(gAT), _d(gPT), _d(out["x"]), _d(out["y"]),
+                                  _d(out["A"]), _d(out["P"]), _d(out["gx0"]), _d(out["gy0"]), _d(out["gp0"]),
+                                  _d(out["gv0"]), _d(gK)), "spv_backward")
+    out["gKA"], out["gKP"] = float(gK[0]), float(gK[1])
+    return out

@@ -23,6 +23,7 @@
 //  - positions are kept on the dyadic grid 2^-q, q = 50 - ceil(log2 max(Lx,Ly)),
 //    so coordinate differences are exact and predicates are decidable exactly.
 #include "internal.h"
+#include "spv_core.h"
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -30,160 +31,8 @@
 namespace cgo {
 namespace {
 
-struct Geo {
-  int n = 0;
-  double Lx = 0, Ly = 0;
-  int max_ring = 16;
-  const double *x = nullptr, *y = nullptr;
-  const int32_t *cnt = nullptr, *nbr = nullptr, *off = nullptr;
-};
-
-inline int wrapi(int a, int n) { return ((a % n) + n) % n; }
-
-// Vector from cell i to the image of ring entry a of cell i (exact on the grid).
-inline void rel(const Geo& g, int i, int a, double& dx, double& dy) {
-  int j = g.nbr[i * g.max_ring + a];
-  int ox = g.off[(i * g.max_ring + a) * 2 + 0];
-  int oy = g.off[(i * g.max_ring + a) * 2 + 1];
-  dx = (g.x[j] - g.x[i]) + ox * g.Lx;
-  dy = (g.y[j] - g.y[i]) + oy * g.Ly;
-}
-
-// Circumcentre of (r_i, r_j, r_k) relative to r_i, written as in Eqs. A8-A12:
-//   c = r_ij x r_kj, d = 2c^2, beta d = -|r_ik|^2 (r_ij . r_jk),
-//   gamma d = |r_ij|^2 (r_ik . r_jk), z = beta d r_ij + gamma d r_ik, h - r_i = z/d.
-void circumcentre_rel(double rijx, double rijy, double rikx, double riky, double& hx, double& hy) {
-  double rjkx = rikx - rijx, rjky = riky - rijy;
-  double rkjx = -rjkx, rkjy = -rjky;
-  double c = rijx * rkjy - rijy * rkjx;
-  double d = 2.0 * c * c;
-  double betad = -(rikx * rikx + riky * riky) * (rijx * rjkx + rijy * rjky);
-  double gammad = (rijx * rijx + rijy * rijy) * (rikx * rjkx + riky * rjky);
-  double zx = betad * rijx + gammad * rikx;
-  double zy = betad * rijy + gammad * riky;
-  hx = zx / d;
-  hy = zy / d;
-}
-
-// Voronoi polygon of every cell (vertices relative to the cell), A and P.
-void polygons(const Geo& g, std::vector<double>& hx, std::vector<double>& hy, double* A,
-              double* P) {
-  hx.assign((size_t)g.n * g.max_ring, 0.0);
-  hy.assign((size_t)g.n * g.max_ring, 0.0);
-  for (int i = 0; i < g.n; ++i) {
-    int m = g.cnt[i];
-    for (int a = 0; a < m; ++a) {
-      double ax, ay, bx, by;
-      rel(g, i, a, ax, ay);
-      rel(g, i, (a + 1) % m, bx, by);
-      circumcentre_rel(ax, ay, bx, by, hx[i * g.max_ring + a], hy[i * g.max_ring + a]);
-    }
-    double area = 0.0, per = 0.0;
-    for (int a = 0; a < m; ++a) {
-      double x0 = hx[i * g.max_ring + a], y0 = hy[i * g.max_ring + a];
-      double x1 = hx[i * g.max_ring + (a + 1) % m], y1 = hy[i * g.max_ring + (a + 1) % m];
-      area += x0 * y1 - x1 * y0;
-      per += std::sqrt((x1 - x0) * (x1 - x0) + (y1 - y0) * (y1 - y0));
-    }
-    A[i] = 0.5 * area;
-    P[i] = per;
-  }
-}
-
-// Slot b of cell c's ring such that ring(c)[b] = (u, ou) and ring(c)[b+1] = (w, ow).
-int find_pair(const Geo& g, int c, int u, int oux, int ouy, int w, int owx, int owy) {
-  int m = g.cnt[c];
-  for (int b = 0; b < m; ++b) {
-    int e0 = c * g.max_ring + b, e1 = c * g.max_ring + (b + 1) % m;
-    if (g.nbr[e0] == u && g.off[2 * e0] == oux && g.off[2 * e0 + 1] == ouy && g.nbr[e1] == w &&
-        g.off[2 * e1] == owx && g.off[2 * e1 + 1] == owy)
-      return b;
-  }
-  return -1;
-}
-
-struct Mech {
-  double A0, KA, KP;
-  const double* p0;
-};
-
-// Forces on every cell (Eqs. A3-A7 and A13-A16 with the corrections above).
-int forces(const Geo& g, const Mech& mp, double* Fx, double* Fy, double* A, double* P,
-           double* energy, const char* only = nullptr) {
-  std::vector<double> hx, hy;
-  polygons(g, hx, hy, A, P);
-  const double sqA0 = std::sqrt(mp.A0);
-  double E = 0.0;
-  // force sets dE_c/dh at every vertex of every cell (Eq. A3 with A4, A5)
-  std::vector<double> sx((size_t)g.n * g.max_ring, 0.0), sy((size_t)g.n * g.max_ring, 0.0);
-  for (int c = 0; c < g.n; ++c) {
-    double P0 = mp.p0[c] * sqA0;
-    double ka = 2.0 * mp.KA * (A[c] - mp.A0);
-    double kp = 2.0 * mp.KP * (P[c] - P0);
-    E += mp.KA * (A[c] - mp.A0) * (A[c] - mp.A0) + mp.KP * (P[c] - P0) * (P[c] - P0);
-    int m = g.cnt[c];
-    for (int a = 0; a < m; ++a) {
-      int ip = c * g.max_ring + (a + m - 1) % m, ia = c * g.max_ring + a,
-          in = c * g.max_ring + (a + 1) % m;
-      double tinx = hx[ia] - hx[ip], tiny = hy[ia] - hy[ip];   // t_ij (incoming edge)
-      double toutx = hx[in] - hx[ia], touty = hy[in] - hy[ia];  // t_ik (outgoing edge)
-      // Eq. A4: dA/dh = 1/2 (l_ij n_ij + l_ik n_ik), outward normal l n = (t_y, -t_x)
-      double dAx = 0.5 * (tiny + touty), dAy = 0.5 * (-tinx - toutx);
-      // Eq. A5 (corrected): dP/dh = t^_ij - t^_ik
-      double lin = std::sqrt(tinx * tinx + tiny * tiny);
-      double lout = std::sqrt(toutx * toutx + touty * touty);
-      double dPx = tinx / lin - toutx / lout, dPy = tiny / lin - touty / lout;
-      sx[ia] = ka * dAx + kp * dPx;
-      sy[ia] = ka * dAy + kp * dPy;
-    }
-  }
-  if (energy) *energy = E;
-  // net force (Eqs. A6, A7): F_i = - sum_{t ni i} (dh_t/dr_i)^T G_t
-  for (int i = 0; i < g.n; ++i) {
-    if (only && !only[i]) continue;
-    int m = g.cnt[i];
-    double fx = 0.0, fy = 0.0;
-    for (int a = 0; a < m; ++a) {
-      int ea = i * g.max_ring + a, eb = i * g.max_ring + (a + 1) % m;
-      int j = g.nbr[ea], k = g.nbr[eb];
-      int ojx = g.off[2 * ea], ojy = g.off[2 * ea + 1];
-      int okx = g.off[2 * eb], oky = g.off[2 * eb + 1];
-      // triangle (i, j, k) appears as (j, k, i) around j and as (k, i, j) around k
-      int bj = find_pair(g, j, k, okx - ojx, oky - ojy, i, -ojx, -ojy);
-      int bk = find_pair(g, k, i, -okx, -oky, j, ojx - okx, ojy - oky);
-      if (bj < 0 || bk < 0) return -10;  // inconsistent rings
-      double Gx = sx[ea] + sx[j * g.max_ring + bj] + sx[k * g.max_ring + bk];
-      double Gy = sy[ea] + sy[j * g.max_ring + bj] + sy[k * g.max_ring + bk];
-      // Jacobian dh/dr_i (Eqs. A8-A16, corrected)
-      double rijx, rijy, rikx, riky;
-      rel(g, i, a, rijx, rijy);
-      rel(g, i, (a + 1) % m, rikx, riky);
-      double rjkx = rikx - rijx, rjky = riky - rijy;
-      double c = rijx * (-rjky) - rijy * (-rjkx);
-      double d = 2.0 * c * c;
-      double rij2 = rijx * rijx + rijy * rijy, rik2 = rikx * rikx + riky * riky;
-      double ij_jk = rijx * rjkx + rijy * rjky, ik_jk = rikx * rjkx + riky * rjky;
-      double betad = -rik2 * ij_jk, gammad = rij2 * ik_jk;
-      double zx = betad * rijx + gammad * rikx, zy = betad * rijy + gammad * riky;
-      double gbx = 2.0 * ij_jk * rikx + rik2 * rjkx, gby = 2.0 * ij_jk * riky + rik2 * rjky;
-      double ggx = -2.0 * ik_jk * rijx - rij2 * rjkx, ggy = -2.0 * ik_jk * rijy - rij2 * rjky;
-      double gdx = (2.0 / c) * rjky, gdy = (2.0 / c) * (-rjkx);
-      double J[2][2];
-      const double rv[2] = {rijx, rijy}, kv[2] = {rikx, riky}, zv[2] = {zx, zy};
-      const double gb[2] = {gbx, gby}, gg[2] = {ggx, ggy}, gd[2] = {gdx, gdy};
-      for (int al = 0; al < 2; ++al)
-        for (int be = 0; be < 2; ++be)
-          J[al][be] = (al == be ? 1.0 : 0.0) +
-                      (rv[al] * gb[be] + kv[al] * gg[be] - (al == be ? betad + gammad : 0.0) -
-                       zv[al] * gd[be]) / d;
-      fx -= J[0][0] * Gx + J[1][0] * Gy;
-      fy -= J[0][1] * Gx + J[1][1] * Gy;
-    }
-    Fx[i] = fx;
-    Fy[i] = fy;
-  }
-  return 0;
-}
+using Geo = GeoT<double>;
+using Mech = MechT<double>;
 
 // Periodic reduction of a finite coordinate (any move size): v' = fmod(v, L)
 // is exact, v' is rounded to the grid 2^-q, and the grid integer is wrapped
@@ -338,7 +187,7 @@ int cgo_geometry(int n, double Lx, double Ly, const double* x, const double* y,
                  double* A, double* P, double* hx, double* hy) {
   Geo g{n, Lx, Ly, max_ring, x, y, cnt, nbr, off};
   std::vector<double> vx, vy;
-  polygons(g, vx, vy, A, P);
+  polygons_t(g, vx, vy, A, P);
   if (hx) std::memcpy(hx, vx.data(), sizeof(double) * vx.size());
   if (hy) std::memcpy(hy, vy.data(), sizeof(double) * vy.size());
   return 0;
@@ -350,7 +199,7 @@ int cgo_forces(int n, double Lx, double Ly, const double* x, const double* y, co
                const double* mech, double* Fx, double* Fy, double* A, double* P, double* E) {
   Geo g{n, Lx, Ly, max_ring, x, y, cnt, nbr, off};
   Mech mp{mech[0], mech[1], mech[2], p0};
-  return forces(g, mp, Fx, Fy, A, P, E);
+  return forces_t(g, mp, Fx, Fy, A, P, E);
 }
 
 // One Euler-Maruyama update (Eq. 3) from given forces; positions snapped/wrapped.
@@ -386,7 +235,7 @@ int cgo_spv_run(int n, double Lx, double Ly, double* x, double* y, double* theta
     int rc = triangulate(n, Lx, Ly, x, y, R, cnt.data(), nbr.data(), off.data());
     if (rc) return rc;
     Geo g{n, Lx, Ly, R, x, y, cnt.data(), nbr.data(), off.data()};
-    rc = forces(g, mp, fx.data(), fy.data(), a.data(), p.data(), nullptr);
+    rc = forces_t(g, mp, fx.data(), fy.data(), a.data(), p.data(), (double*)nullptr);
     if (rc) return rc;
     if (Fx) std::memcpy(Fx, fx.data(), sizeof(double) * n);
     if (Fy) std::memcpy(Fy, fy.data(), sizeof(double) * n);
@@ -452,7 +301,7 @@ int cgo_spv_window_step(int n, double Lx, double Ly, double* x, double* y, doubl
   std::vector<double> lp0(m), fx(m, 0.0), fy(m, 0.0), A(m), P(m);
   for (int k = 0; k < m; ++k) lp0[k] = p0[ids[k]];
   Mech mp{par[0], par[1], par[2], lp0.data()};
-  rc = forces(g, mp, fx.data(), fy.data(), A.data(), P.data(), nullptr, interior.data());
+  rc = forces_t(g, mp, fx.data(), fy.data(), A.data(), P.data(), (double*)nullptr, interior.data());
   if (rc) return rc;
   const double mu = par[3], Dr = par[4], dt = par[5];
   const double s = std::sqrt(2.0 * Dr * dt);
