@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=40)
     ap.add_argument("--batched-warmup", type=int, default=50)
+    ap.add_argument("--bwd-steps", type=int, default=1000)
+    ap.add_argument("--no-backward", action="store_true")
     return ap.parse_args()
 
 
@@ -220,6 +222,46 @@ def batched_comparison(args, device):
             "steps": [args.batched_steps, steps_loop], "warmup": args.batched_warmup}
 
 
+def backward_cost(args, device):
+    """Differentiable run: N = 4096, 1000 steps, checkpoint every 50, loss =
+    mean over cells of (A (P/sqrt(A) - 3.95))^2 at the final state, per-cell p0
+    ~ U[3.7, 3.9].  Times the checkpointed forward run and the reverse pass
+    (which recomputes every segment) with CUDA events."""
+    import numpy as np
+    import torch
+
+    import paper_1702_02939_gb300 as cg
+    import workloads
+
+    n, K, every = 4096, args.bwd_steps, 50
+    x, y, th, L = workloads.spv_uniform(n, 3)
+    sim = cg.SPV([dict(n=n, Lx=L, Ly=L, p0=3.8, v0=0.1)], x, y, th, dt=DT, seed=11, device=device)
+    sim.set_p0(np.random.default_rng(5).uniform(3.7, 3.9, n))
+    sim.step(20)
+    sim.sync()
+    stream = torch.cuda.current_stream()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(stream)
+    bw = sim.run_checkpointed(K, every)
+    e[1].record(stream)
+    A, P = sim.geometry()
+    r = P * A.sqrt() - 3.95 * A
+    gA = 2.0 * r * (P / (2.0 * A.sqrt()) - 3.95) / n
+    gP = 2.0 * r * A.sqrt() / n
+    z = torch.zeros(n, dtype=torch.float64, device=device)
+    torch.cuda.synchronize()
+    e1b = torch.cuda.Event(enable_timing=True)
+    e1b.record(stream)
+    out = sim.backward(bw, K, every, z, z, gA, gP)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e[0].elapsed_time(e[1])
+    bwd_ms = e1b.elapsed_time(e[2])
+    sim.close()
+    return {"workload": "spv_grad_N4096_steps%d_ckpt%d" % (K, every), "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+            "backward_over_forward": bwd_ms / fwd_ms, "grad_KA": out[4], "grad_KP": out[5]}
+
+
 def run_reference(args):
     """CPU oracle arm: each step is one oracle step of a spatial window of the
     N=262144 state, sized so that the whole run takes a few minutes."""
@@ -365,6 +407,9 @@ def run_ours(args):
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
         batched = batched_comparison(args, f"cuda:{local}")
+    backward = None
+    if rank == 0 and world == 1 and not args.no_backward:
+        backward = backward_cost(args, f"cuda:{local}")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -377,7 +422,7 @@ def run_ours(args):
                 "gpu_launches": kernels_per_step(repair_cap) * args.steps,
                 "roofline": roofline, "hbm_roofline": hbm, "cpu_baseline": cpu,
                 "phase_ms_per_step": {k: v / prof_steps for k, v in ph.items()},
-                "counters": counters, "batched": batched}
+                "counters": counters, "batched": batched, "backward": backward}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

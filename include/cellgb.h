@@ -148,6 +148,41 @@ int cg_set_v0(cg_ctx* ctx, const double* v0);
 
 int cg_get_counters(cg_ctx* ctx, cg_counters* host_out);
 
+/* ---- Differentiation (backward pass) ------------------------------------
+ * With the director noise replayed from the seed, one step of Eq. 3 is the
+ * map r' = r + dt (mu F(r) + v0 n(theta)) whose transposed Jacobian is
+ * I - dt mu H, H the Hessian of E (Eq. 1).  The reverse pass below runs
+ * g_t = g_{t+1} - dt mu H(r_t) g_{t+1} over a checkpointed run, with H g
+ * computed as a forward-mode derivative of the forces (Eqs. A6-A16) on the
+ * frozen topology of each step.  Gradients are exact on windows without
+ * neighbour changes.  Cell re-sorting is suspended during these calls.
+ * They need a second caller-owned device buffer of cg_backward_bytes(). */
+
+/* Size of the backward buffer for a run of nsteps with a checkpoint every
+ * ckpt_every steps (one saved state per checkpoint plus one segment). */
+int cg_backward_bytes(const cg_ctx* ctx, int64_t nsteps, int32_t ckpt_every, size_t* bytes);
+/* Moduli K_A, K_P (Eq. 1); recaptures the step graph.  Synchronizes. */
+int cg_set_moduli(cg_ctx* ctx, double KA, double KP);
+/* Sets the Philox step counter (the noise of the next step uses it). */
+int cg_set_step(cg_ctx* ctx, int64_t step);
+/* nsteps steps from the current state, saving checkpoints into d_bw
+ * (device, >= cg_backward_bytes, 256-byte aligned).  Synchronizes. */
+int cg_run_checkpointed(cg_ctx* ctx, int64_t nsteps, int32_t ckpt_every, void* d_bw, size_t bytes);
+/* Reverse pass of the run saved by cg_run_checkpointed (same nsteps,
+ * ckpt_every, d_bw).  Inputs (any pointers, n doubles each, user order):
+ * cotangents of the final positions (gxT, gyT), areas (gAT) and perimeters
+ * (gPT).  Outputs (any pointers or NULL): cotangents of the initial
+ * positions (gx0, gy0), per-cell p0 (gp0) and v0 (gv0), and h_gK[2] (host)
+ * for (K_A, K_P).  Leaves the context in the final state.  Synchronizes. */
+int cg_backward(cg_ctx* ctx, int64_t nsteps, int32_t ckpt_every, void* d_bw, size_t bytes, const double* gxT,
+                const double* gyT, const double* gAT, const double* gPT, double* gx0, double* gy0, double* gp0,
+                double* gv0, double* h_gK);
+/* H v at the current state, and the derivatives of the areas and perimeters
+ * along v (Adot, Pdot; may be NULL).  d_bw: a buffer of at least
+ * cg_backward_bytes(ctx, 1, 1).  Any pointers, user order.  Synchronizes. */
+int cg_hvp(cg_ctx* ctx, const double* vx, const double* vy, double* hvx, double* hvy, double* Adot, double* Pdot,
+           void* d_bw, size_t bytes);
+
 /* Total cells of the context. */
 int64_t cg_num_cells(const cg_ctx* ctx);
 

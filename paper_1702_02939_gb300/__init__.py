@@ -71,6 +71,15 @@ def lib():
         L.cg_set_p0.argtypes = [vp, vp]
         L.cg_set_v0.argtypes = [vp, vp]
         L.cg_get_counters.argtypes = [vp, C.POINTER(cg_counters)]
+        L.cg_backward_bytes.argtypes = [vp, i64, i32, C.POINTER(C.c_size_t)]
+        L.cg_set_moduli.argtypes = [vp, C.c_double, C.c_double]
+        L.cg_set_step.argtypes = [vp, i64]
+        L.cg_run_checkpointed.argtypes = [vp, i64, i32, vp, C.c_size_t]
+        L.cg_backward.argtypes = [vp, i64, i32, vp, C.c_size_t, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.cg_hvp.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, C.c_size_t]
+        for name in ("cg_backward_bytes", "cg_set_moduli", "cg_set_step", "cg_run_checkpointed", "cg_backward",
+                     "cg_hvp"):
+            getattr(L, name).restype = C.c_int
         L.cg_triangulate_noalloc.argtypes = [i32, C.c_double, C.c_double, vp, vp, vp, vp, vp]
         L.cg_triangulate_noalloc.restype = C.c_int
         L.cg_num_cells.argtypes = [vp]
@@ -181,6 +190,36 @@ def cg_get_counters(ctx):
     return {k: getattr(c, k) for k, _ in cg_counters._fields_ if k != "reserved"}
 
 
+def cg_backward_bytes(ctx, nsteps, ckpt_every):
+    out = C.c_size_t(0)
+    _check(lib().cg_backward_bytes(ctx, int(nsteps), int(ckpt_every), C.byref(out)), ctx)
+    return out.value
+
+
+def cg_set_moduli(ctx, KA, KP):
+    _check(lib().cg_set_moduli(ctx, float(KA), float(KP)), ctx)
+
+
+def cg_set_step(ctx, step):
+    _check(lib().cg_set_step(ctx, int(step)), ctx)
+
+
+def cg_run_checkpointed(ctx, nsteps, ckpt_every, bw):
+    _check(lib().cg_run_checkpointed(ctx, int(nsteps), int(ckpt_every), _ptr(bw), bw.numel()), ctx)
+
+
+def cg_backward(ctx, nsteps, ckpt_every, bw, gxT, gyT, gAT, gPT, gx0, gy0, gp0, gv0):
+    gK = (C.c_double * 2)()
+    _check(lib().cg_backward(ctx, int(nsteps), int(ckpt_every), _ptr(bw), bw.numel(), _ptr(gxT), _ptr(gyT),
+                             _ptr(gAT), _ptr(gPT), _ptr(gx0), _ptr(gy0), _ptr(gp0), _ptr(gv0), gK), ctx)
+    return float(gK[0]), float(gK[1])
+
+
+def cg_hvp(ctx, vx, vy, hvx, hvy, Adot, Pdot, bw):
+    _check(lib().cg_hvp(ctx, _ptr(vx), _ptr(vy), _ptr(hvx), _ptr(hvy), _ptr(Adot), _ptr(Pdot), _ptr(bw),
+                        bw.numel()), ctx)
+
+
 NOALLOC_MAX_CELLS = 16384
 
 
@@ -281,6 +320,35 @@ class SPV:
     def counters(self):
         return cg_get_counters(self.ctx)
 
+    def set_moduli(self, KA, KP):
+        cg_set_moduli(self.ctx, KA, KP)
+
+    def set_step(self, step):
+        cg_set_step(self.ctx, step)
+
+    def _bwd_buffer(self, nsteps, ckpt_every):
+        nbytes = cg_backward_bytes(self.ctx, nsteps, ckpt_every)
+        return self.torch.empty(nbytes, dtype=self.torch.uint8, device=self.device)
+
+    def hvp(self, vx, vy):
+        """(H v, dA/dv, dP/dv) at the current state."""
+        bw = self._bwd_buffer(1, 1)
+        out = [self._out() for _ in range(4)]
+        cg_hvp(self.ctx, self._as_input(vx), self._as_input(vy), *out, bw)
+        return tuple(out)
+
+    def run_checkpointed(self, nsteps, ckpt_every):
+        bw = self._bwd_buffer(nsteps, ckpt_every)
+        cg_run_checkpointed(self.ctx, nsteps, ckpt_every, bw)
+        return bw
+
+    def backward(self, bw, nsteps, ckpt_every, gxT, gyT, gAT, gPT):
+        """Cotangents (gx0, gy0, gp0, gv0, gKA, gKP) of a checkpointed run."""
+        out = [self._out() for _ in range(4)]
+        gKA, gKP = cg_backward(self.ctx, nsteps, ckpt_every, bw, *(self._as_input(g) for g in (gxT, gyT, gAT, gPT)),
+                               *out)
+        return (*out, gKA, gKP)
+
     def close(self):
         if getattr(self, "ctx", None):
             cg_destroy(self.ctx)
@@ -291,3 +359,43 @@ class SPV:
             self.close()
         except Exception:
             pass
+
+
+def _autograd_function():
+    import torch
+
+    class SPVRunFunction(torch.autograd.Function):
+        """Differentiable SPV run: (x0, y0, p0, v0, KA, KP) -> (x, y, A, P) after
+        nsteps steps of Eq. 3 with the director noise fixed by the seed.  The
+        backward is the library's checkpointed reverse pass (H g products on
+        the frozen topology of each step), exact on windows without neighbour
+        changes.  p0 is per cell; v0, KA, KP are scalars (tensors)."""
+
+        @staticmethod
+        def forward(fctx, x0, y0, p0, v0, KA, KP, sim, theta0, nsteps, ckpt_every, step0):
+            n = sim.n
+            sim.set_moduli(float(KA), float(KP))
+            sim.set_p0(p0.detach())
+            sim.set_v0(torch.full((n,), float(v0), dtype=torch.float64, device=sim.device))
+            sim.set_state(x0.detach(), y0.detach(), theta0)
+            sim.set_step(step0)
+            bw = sim.run_checkpointed(nsteps, ckpt_every)
+            x, y, _ = sim.state()
+            A, P = sim.geometry()
+            fctx.sim, fctx.bw, fctx.nsteps, fctx.every = sim, bw, nsteps, ckpt_every
+            return x, y, A, P
+
+        @staticmethod
+        def backward(fctx, gx, gy, gA, gP):
+            sim = fctx.sim
+            z = lambda g: torch.zeros(sim.n, dtype=torch.float64, device=sim.device) if g is None else g.contiguous()
+            gx0, gy0, gp0, gv0, gKA, gKP = sim.backward(fctx.bw, fctx.nsteps, fctx.every, z(gx), z(gy), z(gA), z(gP))
+            t = lambda v: torch.tensor(v, dtype=torch.float64)
+            return gx0, gy0, gp0, gv0.sum().cpu(), t(gKA), t(gKP), None, None, None, None, None
+
+    return SPVRunFunction
+
+
+def spv_run_differentiable(sim, x0, y0, p0, v0, KA, KP, theta0, nsteps, ckpt_every=50, step0=0):
+    """Differentiable nsteps-step SPV run; returns final (x, y, A, P)."""
+    return _autograd_function().apply(x0, y0, p0, v0, KA, KP, sim, theta0, nsteps, ckpt_every, step0)

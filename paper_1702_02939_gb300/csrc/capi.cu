@@ -3,6 +3,7 @@
 #include "cg_device.cuh"
 #include "cg_kernels.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -447,6 +448,109 @@ int build_graph(cg_ctx* c) {
   return CG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Backward pass: checkpointed forward run and reverse accumulation.
+// ---------------------------------------------------------------------------
+struct BwdLayout {
+  size_t snap_bytes = 0;                 // one state snapshot
+  size_t snaps = 0, seg = 0;             // checkpoints (+ final state), segment states
+  size_t v, fsd, sd, wd, gp0, gv0, gKA, gKP, cA, cP, gx, gy, F, red;
+  size_t total = 0;
+};
+
+BwdLayout bwd_layout(int64_t N, int64_t nsteps, int32_t every) {
+  BwdLayout b;
+  Layout L;
+  const size_t d = sizeof(double), i4 = sizeof(int);
+  Layout s;
+  s.take(N * d); s.take(N * d); s.take(N * d);           // x, y, theta
+  s.take(N * 8); s.take(N * 8);                          // X, Y
+  s.take(N * i4); s.take(N * CG_RING * i4);              // cnt, nbr
+  s.take(sizeof(Ctl));
+  b.snap_bytes = s.total;
+  const int64_t nck = (nsteps + every - 1) / every;
+  b.snaps = L.take((size_t)(nck + 1) * b.snap_bytes);
+  b.seg = L.take((size_t)every * b.snap_bytes);
+  b.v = L.take(N * sizeof(double2));
+  b.fsd = L.take(N * CG_RING * sizeof(double2));
+  b.sd = L.take(N * CG_RING * sizeof(double2));
+  b.wd = L.take(N * CG_RING * sizeof(double2));
+  b.gp0 = L.take(N * d);
+  b.gv0 = L.take(N * d);
+  b.gKA = L.take(N * d);
+  b.gKP = L.take(N * d);
+  b.cA = L.take(N * d);
+  b.cP = L.take(N * d);
+  b.gx = L.take(N * d);
+  b.gy = L.take(N * d);
+  b.F = L.take(N * sizeof(double2));
+  b.red = L.take(4 * d);
+  b.total = L.total;
+  return b;
+}
+
+Snapshot snapshot_at(char* base, size_t N) {
+  Snapshot s;
+  Layout L;
+  const size_t d = sizeof(double), i4 = sizeof(int);
+  s.x = reinterpret_cast<double*>(base + L.take(N * d));
+  s.y = reinterpret_cast<double*>(base + L.take(N * d));
+  s.theta = reinterpret_cast<double*>(base + L.take(N * d));
+  s.X = reinterpret_cast<long long*>(base + L.take(N * 8));
+  s.Y = reinterpret_cast<long long*>(base + L.take(N * 8));
+  s.cnt = reinterpret_cast<int*>(base + L.take(N * i4));
+  s.nbr = reinterpret_cast<int*>(base + L.take(N * CG_RING * i4));
+  s.ctl = reinterpret_cast<Ctl*>(base + L.take(sizeof(Ctl)));
+  return s;
+}
+
+void snapshot(cg_ctx* c, int save, const Snapshot& s) {
+  launch_snapshot((int)c->N, save, c->ctl(), c->at<double>(c->off.x), c->at<double>(c->off.y),
+                  c->at<long long>(c->off.X), c->at<long long>(c->off.Y), c->at<double>(c->off.theta),
+                  c->at<int>(c->off.cnt), c->at<int>(c->off.nbr), s, c->stream);
+}
+
+JvpArgs jvp_args(cg_ctx* c, char* bw, const BwdLayout& b) {
+  JvpArgs a;
+  a.n = (int)c->N;
+  a.reps = c->at<Rep>(c->off.reps);
+  a.rep = c->at<int>(c->off.rep);
+  a.ctl = c->ctl();
+  a.X = c->at<long long>(c->off.X);
+  a.Y = c->at<long long>(c->off.Y);
+  a.cnt = c->at<int>(c->off.cnt);
+  a.nbr = c->at<int>(c->off.nbr);
+  a.p0 = c->at<double>(c->off.p0);
+  a.theta = c->at<double>(c->off.theta);
+  a.A0 = c->par.A0;
+  a.sqrtA0 = std::sqrt(c->par.A0);
+  a.KA = c->par.KA;
+  a.KP = c->par.KP;
+  a.dt = c->par.dt;
+  a.dtmu = c->par.dt * c->par.mu;
+  a.coefA = a.coefP = nullptr;
+  a.v = reinterpret_cast<double2*>(bw + b.v);
+  a.A = a.P = nullptr;
+  a.Adot = a.Pdot = nullptr;
+  a.fs = c->at<double2>(c->off.fs);
+  a.s = c->at<double2>(c->off.s);
+  a.w = c->at<double2>(c->off.w);
+  a.fsd = reinterpret_cast<double2*>(bw + b.fsd);
+  a.sd = reinterpret_cast<double2*>(bw + b.sd);
+  a.wd = reinterpret_cast<double2*>(bw + b.wd);
+  a.gp0 = a.gv0 = a.gKA = a.gKP = nullptr;
+  a.F = a.Hv = nullptr;
+  a.update = 0;
+  return a;
+}
+
+int check_bwd(cg_ctx* c, int64_t nsteps, int32_t every, void* d_bw, size_t bytes, BwdLayout& b) {
+  if (!c || nsteps < 1 || every < 1 || !d_bw || ((uintptr_t)d_bw & 255)) return CG_EINVAL;
+  b = bwd_layout(c->N, nsteps, every);
+  if (bytes < b.total) return CG_EINVAL;
+  return CG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -705,6 +809,177 @@ int cg_get_counters(cg_ctx* c, cg_counters* out) {
   out->status = h.status;
   out->reserved = 0;
   return CG_OK;
+}
+
+
+int cg_backward_bytes(const cg_ctx* c, int64_t nsteps, int32_t ckpt_every, size_t* bytes) {
+  if (!c || nsteps < 1 || ckpt_every < 1 || !bytes) return CG_EINVAL;
+  *bytes = bwd_layout(c->N, nsteps, ckpt_every).total;
+  return CG_OK;
+}
+
+int cg_set_moduli(cg_ctx* c, double KA, double KP) {
+  if (!c || !std::isfinite(KA) || !std::isfinite(KP)) return CG_EINVAL;
+  int rc = read_status(c);
+  if (rc) return rc;
+  c->par.KA = KA;
+  c->par.KP = KP;
+  if (c->step_exec) {  // kernel parameters are baked into the graph: capture again
+    cudaGraphExecDestroy(c->step_exec);
+    c->step_exec = nullptr;
+  }
+  return build_graph(c);
+}
+
+int cg_set_step(cg_ctx* c, int64_t step) {
+  if (!c || step < 0) return CG_EINVAL;
+  int rc = read_status(c);
+  if (rc) return rc;
+  Ctl h;
+  CG_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
+  h.step = step;
+  CG_CUDA(c, cudaMemcpy(c->ctl(), &h, sizeof(Ctl), cudaMemcpyHostToDevice));
+  return CG_OK;
+}
+
+int cg_run_checkpointed(cg_ctx* c, int64_t nsteps, int32_t ckpt_every, void* d_bw, size_t bytes) {
+  BwdLayout b;
+  int rc = check_bwd(c, nsteps, ckpt_every, d_bw, bytes, b);
+  if (rc) return rc;
+  rc = read_status(c);
+  if (rc) return rc;
+  char* bw = static_cast<char*>(d_bw);
+  const int64_t nck = (nsteps + ckpt_every - 1) / ckpt_every;
+  for (int64_t t = 0; t < nsteps; ++t) {
+    if (t % ckpt_every == 0) snapshot(c, 1, snapshot_at(bw + b.snaps + (t / ckpt_every) * b.snap_bytes, c->N));
+    CG_CUDA(c, cudaGraphLaunch(c->step_exec, c->stream));
+  }
+  snapshot(c, 1, snapshot_at(bw + b.snaps + nck * b.snap_bytes, c->N));
+  CG_CUDA(c, cudaGetLastError());
+  return read_status(c);
+}
+
+int cg_backward(cg_ctx* c, int64_t nsteps, int32_t ckpt_every, void* d_bw, size_t bytes, const double* gxT,
+                const double* gyT, const double* gAT, const double* gPT, double* gx0, double* gy0, double* gp0,
+                double* gv0, double* h_gK) {
+  BwdLayout b;
+  int rc = check_bwd(c, nsteps, ckpt_every, d_bw, bytes, b);
+  if (rc) return rc;
+  if (!gxT || !gyT || !gAT || !gPT) return CG_EINVAL;
+  rc = read_status(c);
+  if (rc) return rc;
+  char* bw = static_cast<char*>(d_bw);
+  cudaStream_t st = c->stream;
+  const int n = (int)c->N;
+  const int* tag = c->at<int>(c->off.tag);
+  const int64_t nck = (nsteps + ckpt_every - 1) / ckpt_every;
+  const Snapshot fin = snapshot_at(bw + b.snaps + nck * b.snap_bytes, c->N);
+  snapshot(c, 0, fin);
+  // cotangents of the final state, in storage order
+  double* tmp = c->at<double>(c->off.tmp);
+  const double* srcs[4] = {gxT, gyT, gAT, gPT};
+  double* dsts[4] = {reinterpret_cast<double*>(bw + b.gx), reinterpret_cast<double*>(bw + b.gy),
+                     reinterpret_cast<double*>(bw + b.cA), reinterpret_cast<double*>(bw + b.cP)};
+  for (int k = 0; k < 4; ++k) {
+    CG_CUDA(c, cudaMemcpyAsync(tmp, srcs[k], c->N * sizeof(double), cudaMemcpyDefault, st));
+    launch_scatter_d(n, tag, tmp, dsts[k], st);
+  }
+  JvpArgs a = jvp_args(c, bw, b);
+  CG_CUDA(c, cudaMemsetAsync(a.v, 0, c->N * sizeof(double2), st));
+  {
+    JvpArgs f = a;
+    f.coefA = dsts[2];
+    f.coefP = dsts[3];
+    f.F = reinterpret_cast<double2*>(bw + b.F);
+    launch_geom_jvp(f, st);
+    launch_force_jvp(f, st);
+    launch_combine_final(n, dsts[0], dsts[1], f.F, a.v, st);
+  }
+  for (size_t off : {b.gp0, b.gv0, b.gKA, b.gKP}) CG_CUDA(c, cudaMemsetAsync(bw + off, 0, c->N * sizeof(double), st));
+  a.gp0 = reinterpret_cast<double*>(bw + b.gp0);
+  a.gv0 = reinterpret_cast<double*>(bw + b.gv0);
+  a.gKA = reinterpret_cast<double*>(bw + b.gKA);
+  a.gKP = reinterpret_cast<double*>(bw + b.gKP);
+  a.update = 1;
+  for (int64_t ck = nck - 1; ck >= 0; --ck) {
+    const int64_t t0 = ck * ckpt_every, t1 = std::min<int64_t>(t0 + ckpt_every, nsteps);
+    snapshot(c, 0, snapshot_at(bw + b.snaps + ck * b.snap_bytes, c->N));
+    for (int64_t t = t0; t < t1; ++t) {  // recompute the segment, keeping every step's input state
+      snapshot(c, 1, snapshot_at(bw + b.seg + (t - t0) * b.snap_bytes, c->N));
+      if (t + 1 < t1) CG_CUDA(c, cudaGraphLaunch(c->step_exec, st));
+    }
+    for (int64_t t = t1 - 1; t >= t0; --t) {
+      snapshot(c, 0, snapshot_at(bw + b.seg + (t - t0) * b.snap_bytes, c->N));
+      launch_geom_jvp(a, st);
+      launch_force_jvp(a, st);
+    }
+  }
+  snapshot(c, 0, fin);  // leave the context in the final state
+  // results in user order
+  double2* v = a.v;
+  double* vx = reinterpret_cast<double*>(bw + b.gx);
+  double* vy = reinterpret_cast<double*>(bw + b.gy);
+  CG_CUDA(c, cudaMemcpy2DAsync(vx, sizeof(double), v, sizeof(double2), sizeof(double), c->N, cudaMemcpyDeviceToDevice, st));
+  CG_CUDA(c, cudaMemcpy2DAsync(vy, sizeof(double), reinterpret_cast<double*>(v) + 1, sizeof(double2), sizeof(double), c->N,
+                               cudaMemcpyDeviceToDevice, st));
+  const double* outs_src[4] = {vx, vy, a.gp0, a.gv0};
+  double* outs_dst[4] = {gx0, gy0, gp0, gv0};
+  for (int k = 0; k < 4; ++k) {
+    if (!outs_dst[k]) continue;
+    launch_gather_d(n, tag, outs_src[k], tmp, st);
+    CG_CUDA(c, cudaMemcpyAsync(outs_dst[k], tmp, c->N * sizeof(double), cudaMemcpyDefault, st));
+  }
+  if (h_gK) {
+    double* red = reinterpret_cast<double*>(bw + b.red);
+    launch_reduce2(n, a.gKA, a.gKP, red, st);
+    CG_CUDA(c, cudaMemcpyAsync(h_gK, red, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  CG_CUDA(c, cudaGetLastError());
+  return read_status(c);
+}
+
+int cg_hvp(cg_ctx* c, const double* vx, const double* vy, double* hvx, double* hvy, double* Adot, double* Pdot,
+           void* d_bw, size_t bytes) {
+  BwdLayout b;
+  int rc = check_bwd(c, 1, 1, d_bw, bytes, b);
+  if (rc) return rc;
+  if (!vx || !vy) return CG_EINVAL;
+  rc = read_status(c);
+  if (rc) return rc;
+  char* bw = static_cast<char*>(d_bw);
+  cudaStream_t st = c->stream;
+  const int n = (int)c->N;
+  const int* tag = c->at<int>(c->off.tag);
+  double* tmp = c->at<double>(c->off.tmp);
+  double* sx = reinterpret_cast<double*>(bw + b.gx);
+  double* sy = reinterpret_cast<double*>(bw + b.gy);
+  CG_CUDA(c, cudaMemcpyAsync(tmp, vx, c->N * sizeof(double), cudaMemcpyDefault, st));
+  launch_scatter_d(n, tag, tmp, sx, st);
+  CG_CUDA(c, cudaMemcpyAsync(tmp, vy, c->N * sizeof(double), cudaMemcpyDefault, st));
+  launch_scatter_d(n, tag, tmp, sy, st);
+  JvpArgs a = jvp_args(c, bw, b);
+  CG_CUDA(c, cudaMemcpy2DAsync(a.v, sizeof(double2), sx, sizeof(double), sizeof(double), c->N, cudaMemcpyDeviceToDevice, st));
+  CG_CUDA(c, cudaMemcpy2DAsync(reinterpret_cast<double*>(a.v) + 1, sizeof(double2), sy, sizeof(double), sizeof(double), c->N,
+                               cudaMemcpyDeviceToDevice, st));
+  double* Ad = reinterpret_cast<double*>(bw + b.gKA);
+  double* Pd = reinterpret_cast<double*>(bw + b.gKP);
+  a.Adot = Ad;
+  a.Pdot = Pd;
+  a.Hv = reinterpret_cast<double2*>(bw + b.F);
+  launch_geom_jvp(a, st);
+  launch_force_jvp(a, st);
+  CG_CUDA(c, cudaMemcpy2DAsync(sx, sizeof(double), a.Hv, sizeof(double2), sizeof(double), c->N, cudaMemcpyDeviceToDevice, st));
+  CG_CUDA(c, cudaMemcpy2DAsync(sy, sizeof(double), reinterpret_cast<double*>(a.Hv) + 1, sizeof(double2), sizeof(double), c->N,
+                               cudaMemcpyDeviceToDevice, st));
+  const double* srcs[4] = {sx, sy, Ad, Pd};
+  double* dsts[4] = {hvx, hvy, Adot, Pdot};
+  for (int k = 0; k < 4; ++k) {
+    if (!dsts[k]) continue;
+    launch_gather_d(n, tag, srcs[k], tmp, st);
+    CG_CUDA(c, cudaMemcpyAsync(dsts[k], tmp, c->N * sizeof(double), cudaMemcpyDefault, st));
+  }
+  CG_CUDA(c, cudaGetLastError());
+  return read_status(c);
 }
 
 int64_t cg_num_cells(const cg_ctx* c) { return c ? c->N : -1; }

@@ -133,4 +133,37 @@ struct SortArgs {
 };
 void launch_sort(const SortArgs& a, cudaStream_t st);
 
+// Backward pass (adjoint_kernels.cu)
+struct JvpArgs {
+  int n;
+  const Rep* reps;
+  const int* rep;
+  Ctl* ctl;
+  const long long *X, *Y;  // [2][n]
+  const int *cnt, *nbr;
+  const double* p0;
+  const double* theta;
+  double A0, sqrtA0, KA, KP, dt, dtmu;
+  const double *coefA, *coefP;  // loss coefficients instead of 2K(A-A0), 2K(P-P0), or null
+  double2* v;                   // tangent / running cotangent per cell
+  double *A, *P;                // optional outputs
+  double *Adot, *Pdot;          // optional outputs: tangents of A and P along v
+  double2 *fs, *fsd, *s, *sd, *w, *wd;  // [CG_RING][n]
+  double *gp0, *gv0, *gKA, *gKP;        // per-cell accumulators, or null
+  double2 *F, *Hv;                      // optional outputs of k_force_jvp
+  int update;                           // v <- v - dt mu H v
+};
+struct Snapshot {
+  double *x, *y, *theta;
+  long long *X, *Y;
+  int *cnt, *nbr;
+  Ctl* ctl;
+};
+void launch_snapshot(int n, int save, Ctl* ctl, double* x, double* y, long long* X, long long* Y, double* theta,
+                     int* cnt, int* nbr, const Snapshot& s, cudaStream_t st);
+void launch_geom_jvp(const JvpArgs& a, cudaStream_t st);
+void launch_force_jvp(const JvpArgs& a, cudaStream_t st);
+void launch_combine_final(int n, const double* gx, const double* gy, const double2* F, double2* g, cudaStream_t st);
+void launch_reduce2(int n, const double* a, const double* b, double* out, cudaStream_t st);
+
 }  // namespace cgk
