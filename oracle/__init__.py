@@ -59,6 +59,15 @@ def _declare(L):
                  "cgo_delaunay_plain", "cgo_triangulate", "cgo_geometry", "cgo_forces",
                  "cgo_integrate", "cgo_spv_run"):
         getattr(L, name).restype = C.c_int
+    L.cgo_avm_build.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp, _ip, _ip, _ip, _ip]
+    L.cgo_avm_forces.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _ip, _ip, _ip, _ip, _dp, _dp,
+                                 _dp, _dp, _dp, _dp, _dp]
+    L.cgo_avm_t1.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _ip, _ip, _ip, _ip, C.c_double,
+                             C.c_double, C.c_int, _ip]
+    L.cgo_avm_step.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _ip, _ip, _ip, _ip, _dp, _dp,
+                               _dp, C.c_uint64, C.c_int64, C.c_int, _ip]
+    for name in ("cgo_avm_build", "cgo_avm_forces", "cgo_avm_t1", "cgo_avm_step"):
+        getattr(L, name).restype = C.c_int
     for extra in ("_declare_avm", "_declare_adjoint"):
         fn = globals().get(extra)
         if fn is not None:
@@ -304,3 +313,73 @@ def spv_backward(x0, y0, theta0, Lx, Ly, p0, v0, nsteps, seed, gxT, gyT, gAT, gP
                                   _d(out["gv0"]), _d(gK)), "spv_backward")
     out["gKA"], out["gKP"] = float(gK[0]), float(gK[1])
     return out
+
+
+class AvmNet:
+    """Vertex network of the active vertex model: vertex positions (hx, hy),
+    per-vertex cells and neighbours (vc, vn: V x 3, CCW, edge v-vn[k] between
+    vc[k] and vc[k+1]) and per-cell CCW vertex lists (cc, cv)."""
+
+    def __init__(self, n, Lx, Ly, hx, hy, vc, vn, cc, cv):
+        self.n, self.Lx, self.Ly = n, Lx, Ly
+        self.hx, self.hy, self.vc, self.vn, self.cc, self.cv = hx, hy, vc, vn, cc, cv
+
+    @property
+    def V(self):
+        return len(self.hx)
+
+    def copy(self):
+        return AvmNet(self.n, self.Lx, self.Ly, *(a.copy() for a in (self.hx, self.hy, self.vc, self.vn, self.cc,
+                                                                      self.cv)))
+
+    def _args(self):
+        return (self.n, self.V, self.Lx, self.Ly, _d(self.hx), _d(self.hy), _i(self.vc), _i(self.vn), _i(self.cc),
+                _i(self.cv))
+
+
+def avm_build(x, y, Lx, Ly):
+    """Voronoi tessellation of the seed positions as a vertex network."""
+    n = len(x)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    hx, hy = np.zeros(2 * n), np.zeros(2 * n)
+    vc, vn = np.zeros(6 * n, np.int32), np.zeros(6 * n, np.int32)
+    cc, cv = np.zeros(n, np.int32), np.full(n * MAX_RING, -1, np.int32)
+    _check(lib().cgo_avm_build(n, Lx, Ly, _d(x), _d(y), _d(hx), _d(hy), _i(vc), _i(vn), _i(cc), _i(cv)), "avm_build")
+    return AvmNet(n, Lx, Ly, hx, hy, vc, vn, cc, cv)
+
+
+def avm_forces(net, p0, A0=1.0, KA=1.0, KP=1.0):
+    p0 = np.ascontiguousarray(np.broadcast_to(np.asarray(p0, np.float64), (net.n,)))
+    mech = np.array([A0, KA, KP], np.float64)
+    Fx, Fy, A, P, E = np.zeros(net.V), np.zeros(net.V), np.zeros(net.n), np.zeros(net.n), np.zeros(1)
+    _check(lib().cgo_avm_forces(*net._args(), _d(p0), _d(mech), _d(Fx), _d(Fy), _d(A), _d(P), _d(E)), "avm_forces")
+    return Fx, Fy, A, P, float(E[0])
+
+
+def avm_t1(net, thr, newlen=None, cap=16, allow_cap=False):
+    """T1 passes on a copy of the network; returns (new network, transitions).
+    With allow_cap, hitting the pass cap returns the partial result."""
+    net = net.copy()
+    newlen = 1.5 * thr if newlen is None else newlen
+    applied = np.zeros(1, np.int32)
+    rc = lib().cgo_avm_t1(*net._args(), float(thr), float(newlen), int(cap), _i(applied))
+    if not (allow_cap and rc == -8):
+        _check(rc, "avm_t1")
+    return net, int(applied[0])
+
+
+def avm_step(net, theta, p0, v0, seed, step, A0=1.0, KA=1.0, KP=1.0, mu=1.0, Dr=1.0, dt=0.01, thr=0.04, newlen=None,
+             cap=16):
+    """One AVM step on copies: returns (network, theta, transitions)."""
+    net = net.copy()
+    theta = np.array(theta, np.float64, copy=True)
+    p0 = np.ascontiguousarray(np.broadcast_to(np.asarray(p0, np.float64), (net.n,)))
+    v0 = np.ascontiguousarray(np.broadcast_to(np.asarray(v0, np.float64), (net.n,)))
+    newlen = 1.5 * thr if newlen is None else newlen
+    par = np.array([A0, KA, KP, mu, Dr, dt, thr, newlen], np.float64)
+    applied = np.zeros(1, np.int32)
+    _check(lib().cgo_avm_step(net.n, net.V, net.Lx, net.Ly, _d(net.hx), _d(net.hy), _d(theta), _i(net.vc),
+                              _i(net.vn), _i(net.cc), _i(net.cv), _d(p0), _d(v0), _d(par), int(seed), int(step),
+                              int(cap), _i(applied)), "avm_step")
+    return net, theta, int(applied[0])

@@ -1,0 +1,355 @@
+// Oracle: active vertex model (AVM). TEST INFRASTRUCTURE ONLY.
+//
+// Sussman, arXiv 1702.02939, Sec. 2.D and Eq. 4:
+//  * degrees of freedom: the vertices h_v of a degree-3 network (2N vertices
+//    for N cells); here the initial network is the Voronoi tessellation of
+//    cell seed positions (the circumcentres of the Delaunay triangles);
+//  * energy of Eq. 1 from the polygon areas and perimeters;
+//  * vertex force F_v = -(dE_i + dE_j + dE_k)/dh_v over the vertex's three
+//    cells (Eq. A2) with dA/dh, dP/dh of Eqs. A4, A5 (A5 corrected);
+//  * motion dh_v/dt = mu F_v + (v0 / 3) sum_{cells c of v} n(theta_c) (Eq. 4, n = 3),
+//    then the directors rotate (a separate update, Sec. 2.D);
+//  * T1 transitions (Fig. 1): an edge shorter than a threshold is rotated by
+//    90 degrees about its midpoint and the neighbours are exchanged; at most
+//    one transition per cell per pass, passes repeated until none is called
+//    for (Sec. 2.D).
+// Conventions (shared definitions with the library, each written separately):
+//  * vertex v stores its cells (c0, c1, c2) counter-clockwise around it and
+//    its neighbours (n0, n1, n2), where the edge v-n_k separates c_k and c_{k+1};
+//  * cell vertex lists are counter-clockwise;
+//  * vertex ids: the Delaunay triangles of each cell o whose smallest cell is
+//    o, in o's ring order, numbered consecutively in increasing o;
+//  * T1 candidates: edges (v, n_s) with v < n_s and squared length below the
+//    squared threshold (products and sums rounded separately, no fused
+//    multiply-add); edge id = 3 v + s; for the edge, i = c_s, k = c_{s+1}
+//    (the cells that share it), j = c_{s+2}, l = the third cell of n_s;
+//    a transition needs |i|, |k| > 3 vertices and |j|, |l| < 16;
+//    a candidate applies in a pass when its edge id is the smallest among the
+//    candidates touching each of i, j, k, l;
+//  * the rotated edge gets length 1.5 x threshold; v becomes the endpoint on
+//    cell i's side (cells j, i, l; neighbours A_ll, A_lr, n_s), n_s the one
+//    on cell k's side (cells k, j, l; neighbours A_ul, v, A_ur).
+#include "internal.h"
+
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+extern "C" int cgo_triangulate(int n, double Lx, double Ly, const double* x, const double* y, int max_ring,
+                               int32_t* cnt, int32_t* nbr, int32_t* off);
+extern "C" double cgo_director_noise(uint64_t seed, int32_t tag, int64_t step);
+
+namespace cgo {
+namespace {
+
+constexpr int kR = 16;
+
+inline double mimg(double d, double L) {
+  if (d > 0.5 * L) d -= L;
+  else if (d < -0.5 * L) d += L;
+  return d;
+}
+inline double wrapL(double v, double L) {
+  double r = std::fmod(v, L);
+  if (r < 0.0) r += L;
+  if (r >= L) r -= L;
+  return r + 0.0;
+}
+
+struct Net {
+  int N, V;
+  double Lx, Ly;
+  double* hx;
+  double* hy;
+  int32_t *vc, *vn, *cc, *cv;
+};
+
+// Squared edge length, every product and sum rounded on its own.
+double edge_len2(const Net& g, int v, int w) {
+  volatile double dx = mimg(g.hx[w] - g.hx[v], g.Lx);
+  volatile double dy = mimg(g.hy[w] - g.hy[v], g.Ly);
+  volatile double a = dx * dx;
+  volatile double b = dy * dy;
+  return a + b;
+}
+
+void polygon_geometry(const Net& g, int c, double& A, double& P) {
+  int m = g.cc[c];
+  int v0 = g.cv[c * kR];
+  std::vector<double> px(m), py(m);
+  for (int a = 0; a < m; ++a) {
+    int v = g.cv[c * kR + a];
+    px[a] = mimg(g.hx[v] - g.hx[v0], g.Lx);
+    py[a] = mimg(g.hy[v] - g.hy[v0], g.Ly);
+  }
+  double area = 0.0, per = 0.0;
+  for (int a = 0; a < m; ++a) {
+    int b = (a + 1) % m;
+    area += px[a] * py[b] - px[b] * py[a];
+    per += std::sqrt((px[b] - px[a]) * (px[b] - px[a]) + (py[b] - py[a]) * (py[b] - py[a]));
+  }
+  A = 0.5 * area;
+  P = per;
+}
+
+// F_v = -sum_c dE_c/dh_v, accumulated cell by cell over each cell's vertex list.
+void vertex_forces(const Net& g, const double* p0, double A0, double KA, double KP, double* Fx, double* Fy,
+                   double* A, double* P, double* energy) {
+  const double sqA0 = std::sqrt(A0);
+  double E = 0.0;
+  for (int v = 0; v < g.V; ++v) Fx[v] = Fy[v] = 0.0;
+  for (int c = 0; c < g.N; ++c) {
+    polygon_geometry(g, c, A[c], P[c]);
+    double P0 = p0[c] * sqA0;
+    E += KA * (A[c] - A0) * (A[c] - A0) + KP * (P[c] - P0) * (P[c] - P0);
+    double ka = 2.0 * KA * (A[c] - A0), kp = 2.0 * KP * (P[c] - P0);
+    int m = g.cc[c];
+    for (int a = 0; a < m; ++a) {
+      int vp = g.cv[c * kR + (a + m - 1) % m], v = g.cv[c * kR + a], vn = g.cv[c * kR + (a + 1) % m];
+      double tinx = mimg(g.hx[v] - g.hx[vp], g.Lx), tiny = mimg(g.hy[v] - g.hy[vp], g.Ly);    // t_ij
+      double toutx = mimg(g.hx[vn] - g.hx[v], g.Lx), touty = mimg(g.hy[vn] - g.hy[v], g.Ly);  // t_ik
+      // Eq. A4 with outward normals l n = (t_y, -t_x); Eq. A5 (corrected)
+      double dAx = 0.5 * (tiny + touty), dAy = 0.5 * (-tinx - toutx);
+      double lin = std::sqrt(tinx * tinx + tiny * tiny), lout = std::sqrt(toutx * toutx + touty * touty);
+      double dPx = tinx / lin - toutx / lout, dPy = tiny / lin - touty / lout;
+      Fx[v] -= ka * dAx + kp * dPx;
+      Fy[v] -= ka * dAy + kp * dPy;
+    }
+  }
+  if (energy) *energy = E;
+}
+
+int slot_of(const int32_t* arr, int v, int val) {
+  for (int s = 0; s < 3; ++s)
+    if (arr[3 * v + s] == val) return s;
+  return -1;
+}
+
+void remove_vertex(Net& g, int c, int v) {
+  int m = g.cc[c], w = 0;
+  for (int a = 0; a < m; ++a)
+    if (g.cv[c * kR + a] != v) g.cv[c * kR + w++] = g.cv[c * kR + a];
+  for (int a = w; a < kR; ++a) g.cv[c * kR + a] = -1;
+  g.cc[c] = w;
+}
+
+void insert_after(Net& g, int c, int after, int v) {
+  int m = g.cc[c];
+  int pos = -1;
+  for (int a = 0; a < m; ++a)
+    if (g.cv[c * kR + a] == after) pos = a;
+  for (int a = m; a > pos + 1; --a) g.cv[c * kR + a] = g.cv[c * kR + a - 1];
+  g.cv[c * kR + pos + 1] = v;
+  g.cc[c] = m + 1;
+}
+
+struct Cand {
+  int v, s, w, i, j, k, l, id;
+};
+
+// One T1 pass; returns the number of transitions applied, or -1 on a broken network.
+int t1_pass(Net& g, double thr, double newlen, int* remaining) {
+  std::vector<Cand> cands;
+  const double thr2 = thr * thr;
+  for (int v = 0; v < g.V; ++v) {
+    for (int s = 0; s < 3; ++s) {
+      int w = g.vn[3 * v + s];
+      if (w <= v) continue;
+      if (!(edge_len2(g, v, w) < thr2)) continue;
+      int i = g.vc[3 * v + s], k = g.vc[3 * v + (s + 1) % 3], j = g.vc[3 * v + (s + 2) % 3];
+      int l = -1;
+      for (int t = 0; t < 3; ++t) {
+        int c = g.vc[3 * w + t];
+        if (c != i && c != k) l = c;
+      }
+      if (l < 0) return -1;
+      if (g.cc[i] <= 3 || g.cc[k] <= 3 || g.cc[j] >= kR || g.cc[l] >= kR) continue;
+      cands.push_back(Cand{v, s, w, i, j, k, l, 3 * v + s});
+    }
+  }
+  *remaining = (int)cands.size();
+  if (cands.empty()) return 0;
+  std::vector<int> lock(g.N, INT_MAX);
+  for (const Cand& c : cands)
+    for (int cell : {c.i, c.j, c.k, c.l}) lock[cell] = std::min(lock[cell], c.id);
+  int applied = 0;
+  for (const Cand& c : cands) {
+    if (lock[c.i] != c.id || lock[c.j] != c.id || lock[c.k] != c.id || lock[c.l] != c.id) continue;
+    const int v1 = c.v, v2 = c.w, a = c.s;
+    const int Aul = g.vn[3 * v1 + (a + 1) % 3], All = g.vn[3 * v1 + (a + 2) % 3];
+    const int b = slot_of(g.vn, v2, v1);
+    if (b < 0 || g.vc[3 * v2 + b] != c.k || g.vc[3 * v2 + (b + 1) % 3] != c.i) return -1;
+    const int Alr = g.vn[3 * v2 + (b + 1) % 3], Aur = g.vn[3 * v2 + (b + 2) % 3];
+    // geometry: rotate the edge by 90 degrees about its midpoint
+    double ex = mimg(g.hx[v2] - g.hx[v1], g.Lx), ey = mimg(g.hy[v2] - g.hy[v1], g.Ly);
+    double mx = g.hx[v1] + 0.5 * ex, my = g.hy[v1] + 0.5 * ey;
+    double len = std::sqrt(ex * ex + ey * ey);
+    double px = -ey / len * 0.5 * newlen, py = ex / len * 0.5 * newlen;
+    g.hx[v1] = wrapL(mx - px, g.Lx);
+    g.hy[v1] = wrapL(my - py, g.Ly);
+    g.hx[v2] = wrapL(mx + px, g.Lx);
+    g.hy[v2] = wrapL(my + py, g.Ly);
+    // topology
+    int* c1 = g.vc + 3 * v1;
+    int* n1 = g.vn + 3 * v1;
+    int* c2 = g.vc + 3 * v2;
+    int* n2 = g.vn + 3 * v2;
+    c1[0] = c.j; c1[1] = c.i; c1[2] = c.l;
+    n1[0] = All; n1[1] = Alr; n1[2] = v2;
+    c2[0] = c.k; c2[1] = c.j; c2[2] = c.l;
+    n2[0] = Aul; n2[1] = v1; n2[2] = Aur;
+    int su = slot_of(g.vn, Aul, v1);
+    int sl = slot_of(g.vn, Alr, v2);
+    if (su < 0 || sl < 0) return -1;
+    g.vn[3 * Aul + su] = v2;
+    g.vn[3 * Alr + sl] = v1;
+    remove_vertex(g, c.i, v2);
+    remove_vertex(g, c.k, v1);
+    insert_after(g, c.j, v1, v2);
+    insert_after(g, c.l, v2, v1);
+    ++applied;
+  }
+  return applied;
+}
+
+}  // namespace
+}  // namespace cgo
+
+using namespace cgo;
+
+extern "C" {
+
+// Initial vertex network: the Voronoi tessellation of cell seed positions.
+// Outputs: V = 2n vertices (hx, hy), vc/vn [V*3], cc [n], cv [n*16].
+int cgo_avm_build(int n, double Lx, double Ly, const double* x, const double* y, double* hx, double* hy,
+                  int32_t* vc, int32_t* vn, int32_t* cc, int32_t* cv) {
+  std::vector<int32_t> cnt(n), nbr((size_t)n * kR), off((size_t)n * kR * 2);
+  int rc = cgo_triangulate(n, Lx, Ly, x, y, kR, cnt.data(), nbr.data(), off.data());
+  if (rc) return rc;
+  // vertex id of (cell, slot): owner = smallest cell of the triangle
+  std::vector<int> base(n + 1, 0);
+  for (int o = 0; o < n; ++o) {
+    int owned = 0;
+    for (int b = 0; b < cnt[o]; ++b) {
+      int j = nbr[o * kR + b], k = nbr[o * kR + (b + 1) % cnt[o]];
+      owned += (o < j && o < k);
+    }
+    base[o + 1] = base[o] + owned;
+  }
+  if (base[n] != 2 * n) return -20;
+  auto owned_rank = [&](int o, int b) {
+    int r = 0;
+    for (int t = 0; t < b; ++t) {
+      int j = nbr[o * kR + t], k = nbr[o * kR + (t + 1) % cnt[o]];
+      r += (o < j && o < k);
+    }
+    return r;
+  };
+  // find slot of the triangle (c, u, w) in c's ring: ring[b] = u, ring[b+1] = w
+  auto slot_pair = [&](int c, int u, int w) {
+    for (int b = 0; b < cnt[c]; ++b)
+      if (nbr[c * kR + b] == u && nbr[c * kR + (b + 1) % cnt[c]] == w) return b;
+    return -1;
+  };
+  auto vid = [&](int c, int a) {  // vertex of triangle (c, ring[a], ring[a+1])
+    int j = nbr[c * kR + a], k = nbr[c * kR + (a + 1) % cnt[c]];
+    if (c < j && c < k) return base[c] + owned_rank(c, a);
+    int o, b;
+    if (j < k) { o = j; b = slot_pair(j, k, c); }   // seen from j: (j, k, c)
+    else { o = k; b = slot_pair(k, c, j); }         // seen from k: (k, c, j)
+    if (b < 0) return -1;
+    return base[o] + owned_rank(o, b);
+  };
+  for (int c = 0; c < n; ++c) {
+    cc[c] = cnt[c];
+    for (int a = 0; a < kR; ++a) cv[c * kR + a] = a < cnt[c] ? vid(c, a) : -1;
+    for (int a = 0; a < cnt[c]; ++a)
+      if (cv[c * kR + a] < 0) return -21;
+  }
+  for (int o = 0; o < n; ++o) {
+    int m = cnt[o];
+    for (int b = 0; b < m; ++b) {
+      int j = nbr[o * kR + b], k = nbr[o * kR + (b + 1) % m];
+      if (!(o < j && o < k)) continue;
+      int v = base[o] + owned_rank(o, b);
+      vc[3 * v + 0] = o; vc[3 * v + 1] = j; vc[3 * v + 2] = k;
+      vn[3 * v + 0] = cv[o * kR + (b + m - 1) % m];                // across edge (o, j)
+      int p = slot_pair(j, k, o);                                  // (j, k, o) in j's ring
+      int mj = cnt[j];
+      vn[3 * v + 1] = cv[j * kR + (p + mj - 1) % mj];              // across edge (j, k)
+      vn[3 * v + 2] = cv[o * kR + (b + 1) % m];                    // across edge (k, o)
+      // position: circumcentre of (o, j, k) with the periodic offsets of the ring
+      double ax = (x[j] - x[o]) + off[(o * kR + b) * 2] * Lx, ay = (y[j] - y[o]) + off[(o * kR + b) * 2 + 1] * Ly;
+      int b1 = (b + 1) % m;
+      double bx = (x[k] - x[o]) + off[(o * kR + b1) * 2] * Lx, by = (y[k] - y[o]) + off[(o * kR + b1) * 2 + 1] * Ly;
+      double d = 2.0 * (ax * by - ay * bx);
+      double la = ax * ax + ay * ay, lb = bx * bx + by * by;
+      hx[v] = wrapL(x[o] + (by * la - ay * lb) / d, Lx);
+      hy[v] = wrapL(y[o] + (ax * lb - bx * la) / d, Ly);
+    }
+  }
+  return 0;
+}
+
+int cgo_avm_forces(int n, int V, double Lx, double Ly, double* hx, double* hy, int32_t* vc, int32_t* vn,
+                   int32_t* cc, int32_t* cv, const double* p0, const double* mech, double* Fx, double* Fy, double* A,
+                   double* P, double* E) {
+  Net g{n, V, Lx, Ly, hx, hy, vc, vn, cc, cv};
+  vertex_forces(g, p0, mech[0], mech[1], mech[2], Fx, Fy, A, P, E);
+  return 0;
+}
+
+// T1 passes until a pass finds no eligible candidate (at most cap passes);
+// *applied = transitions made.  Returns -8 when candidates remain after cap.
+int cgo_avm_t1(int n, int V, double Lx, double Ly, double* hx, double* hy, int32_t* vc, int32_t* vn, int32_t* cc,
+               int32_t* cv, double thr, double newlen, int cap, int32_t* applied) {
+  Net g{n, V, Lx, Ly, hx, hy, vc, vn, cc, cv};
+  int total = 0;
+  for (int r = 0; r <= cap; ++r) {
+    int rem = 0;
+    int a = (r < cap) ? t1_pass(g, thr, newlen, &rem) : 0;
+    if (r == cap) {  // count what is left without applying
+      Net h = g;
+      std::vector<double> sx(hx, hx + V), sy(hy, hy + V);
+      std::vector<int32_t> svc(vc, vc + 3 * V), svn(vn, vn + 3 * V), scc(cc, cc + n), scv(cv, cv + n * kR);
+      h.hx = sx.data(); h.hy = sy.data(); h.vc = svc.data(); h.vn = svn.data(); h.cc = scc.data(); h.cv = scv.data();
+      t1_pass(h, thr, newlen, &rem);
+      *applied = total;
+      return rem ? -8 : 0;
+    }
+    if (a < 0) return -22;
+    total += a;
+    if (rem == 0) break;
+  }
+  *applied = total;
+  return 0;
+}
+
+// One AVM step: vertex move (Eq. 4), director rotation, T1 passes.
+// par = {A0, KA, KP, mu, Dr, dt, thr, newlen}; v0 per cell.
+int cgo_avm_step(int n, int V, double Lx, double Ly, double* hx, double* hy, double* theta, int32_t* vc, int32_t* vn,
+                 int32_t* cc, int32_t* cv, const double* p0, const double* v0, const double* par, uint64_t seed,
+                 int64_t step, int cap, int32_t* applied) {
+  Net g{n, V, Lx, Ly, hx, hy, vc, vn, cc, cv};
+  std::vector<double> Fx(V), Fy(V), A(n), P(n);
+  vertex_forces(g, p0, par[0], par[1], par[2], Fx.data(), Fy.data(), A.data(), P.data(), nullptr);
+  const double mu = par[3], Dr = par[4], dt = par[5];
+  std::vector<double> nx(n), ny(n);
+  for (int c = 0; c < n; ++c) {
+    nx[c] = v0[c] * std::cos(theta[c]);
+    ny[c] = v0[c] * std::sin(theta[c]);
+  }
+  for (int v = 0; v < V; ++v) {
+    // Eq. 4 with n = 3 cells per vertex (per-cell speeds v0_c)
+    double ax = (nx[vc[3 * v]] + nx[vc[3 * v + 1]] + nx[vc[3 * v + 2]]) / 3.0;
+    double ay = (ny[vc[3 * v]] + ny[vc[3 * v + 1]] + ny[vc[3 * v + 2]]) / 3.0;
+    hx[v] = wrapL(hx[v] + dt * (mu * Fx[v] + ax), Lx);
+    hy[v] = wrapL(hy[v] + dt * (mu * Fy[v] + ay), Ly);
+  }
+  const double s = std::sqrt(2.0 * Dr * dt);
+  for (int c = 0; c < n; ++c) theta[c] = theta[c] + s * cgo_director_noise(seed, c, step);
+  return cgo_avm_t1(n, V, Lx, Ly, hx, hy, vc, vn, cc, cv, par[6], par[7], cap, applied);
+}
+
+}  // extern "C"
