@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--batched-warmup", type=int, default=50)
     ap.add_argument("--bwd-steps", type=int, default=1000)
     ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--no-avm", action="store_true")
+    ap.add_argument("--avm-steps", type=int, default=500)
     return ap.parse_args()
 
 
@@ -262,6 +264,62 @@ def backward_cost(args, device):
             "backward_over_forward": bwd_ms / fwd_ms, "grad_KA": out[4], "grad_KP": out[5]}
 
 
+def avm_throughput(args, device):
+    """Active vertex model (Sec. 2.D, Eq. 4, Fig. 1): N = 65536 cells (V =
+    131072 vertices) from the Voronoi tessellation of uniform random seeds in
+    L = 256, p0 = 3.8, v0 = 0.1, T1 threshold 0.04, dt = 0.01, FP64.  100
+    equilibration steps, then each step (geometry, vertex force and move,
+    directors, T1 passes) timed alone with CUDA events, L2 flushed in between.
+    The oracle's AVM step on the same state is timed beside it (one thread)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1702_02939_gb300 as cg
+    import workloads
+
+    n, thr, p0, v0 = 65536, 0.04, 3.8, 0.1
+    x, y, th, L = workloads.spv_uniform(n, 21)
+    sim = cg.AVM(n, L, L, x, y, th, p0=p0, v0=v0, dt=DT, t1_threshold=thr, seed=21, device=device)
+    sim.step(100)
+    sim.sync()
+    c0 = sim.counters()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+    K = args.avm_steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(stream)
+        sim.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    sim.sync()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    c1 = sim.counters()
+    # oracle on the same kind of state (its own network build), a few steps
+    Lx, Ly, q = oracle.box(L)
+    xs, ys = oracle.snap_positions(x, y, Lx, Ly)
+    net = oracle.avm_build(xs, ys, Lx, Ly)
+    oth, steps, t0 = th, 0, time.perf_counter()
+    while True:
+        net, oth, _ = oracle.avm_step(net, oth, p0, v0, seed=21, step=steps, dt=DT, thr=thr)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > 5.0 or steps >= 200:
+            break
+    sim.close()
+    V = 2 * n
+    return {"workload": "avm_N65536_L256_p0_3.8_v0_0.1_thr0.04_dt0.01_fp64", "unit": "vertex-steps/s",
+            "vertex_steps_per_s": V * K / (ms * 1e-3), "cell_steps_per_s": n * K / (ms * 1e-3),
+            "ms_per_step": ms / K, "steps": K, "warmup": 100, "l2": "flushed between timed steps",
+            "t1_per_step": (c1["t1_total"] - c0["t1_total"]) / K,
+            "t1_passes_per_step": (c1["t1_passes"] - c0["t1_passes"]) / K,
+            "cpu_oracle": {"value": V * steps / el, "unit": "vertex-steps/s", "cores": 1, "kind": "oracle",
+                           "sample": f"{steps} oracle AVM steps of the same N={n} network, {el:.1f} s"}}
+
+
 def run_reference(args):
     """CPU oracle arm: each step is one oracle step of a spatial window of the
     N=262144 state, sized so that the whole run takes a few minutes."""
@@ -410,6 +468,9 @@ def run_ours(args):
     backward = None
     if rank == 0 and world == 1 and not args.no_backward:
         backward = backward_cost(args, f"cuda:{local}")
+    avm = None
+    if rank == 0 and world == 1 and not args.no_avm:
+        avm = avm_throughput(args, f"cuda:{local}")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -422,7 +483,7 @@ def run_ours(args):
                 "gpu_launches": kernels_per_step(repair_cap) * args.steps,
                 "roofline": roofline, "hbm_roofline": hbm, "cpu_baseline": cpu,
                 "phase_ms_per_step": {k: v / prof_steps for k, v in ph.items()},
-                "counters": counters, "batched": batched, "backward": backward}
+                "counters": counters, "batched": batched, "backward": backward, "avm": avm}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

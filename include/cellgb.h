@@ -62,6 +62,7 @@ extern "C" {
 #define CG_EBOX_TOO_SMALL (-7)  /* Voronoi cell wider than the search box allows */
 #define CG_EDEGENERATE (-8)     /* coincident cells */
 #define CG_ECANDIDATES (-9)     /* too many repair candidates in one cell-list ring */
+#define CG_ET1_CAP (-10)        /* AVM: T1 candidates left after t1_cap passes */
 
 typedef struct cg_ctx cg_ctx;
 
@@ -208,6 +209,93 @@ int64_t cg_num_cells(const cg_ctx* ctx);
 #define CG_NOALLOC_MAX_CELLS 16384
 int cg_triangulate_noalloc(int32_t n, double Lx, double Ly, const double* d_x, const double* d_y,
                            int32_t* d_cnt, int32_t* d_nbr, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Active vertex model (AVM), Sec. 2.D and Eq. 4 of the paper.
+ *
+ * The degrees of freedom are the 2N vertices of a degree-3 network; the
+ * initial network is the Voronoi tessellation of N seed positions (the
+ * circumcentres of their exact periodic Delaunay triangulation).  One step:
+ * the energy of Eq. 1 per polygon, the vertex force F_v = -dE/dh_v (Eq. A2
+ * with Eqs. A4 and A5), the move dh_v = dt (mu F_v + (1/3) sum over the three
+ * cells c of v of v0_c n(theta_c)) (Eq. 4), the director rotation
+ * theta_c += sqrt(2 D_r dt) xi (Philox4x32-10, counter (c, step)), then T1
+ * passes (Fig. 1) until no edge is shorter than the threshold.
+ *
+ * Layout (all int32 / double, vertex v, cell c):
+ *   hx, hy [V]        vertex positions in [0, L)
+ *   vc [3V], vn [3V]  cells and neighbours of v, counter-clockwise: the edge
+ *                     v - vn[3v+k] separates cells vc[3v+k] and vc[3v+k+1]
+ *   cc [N], cv [N*CG_MAX_RING]  vertex count and counter-clockwise vertex
+ *                     list of each cell (unused slots -1)
+ * Vertex ids of the initial network: the Delaunay triangles owned by their
+ * smallest cell, in that cell's ring order, numbered in increasing cell.
+ *
+ * T1 rule: an edge (v, vn[3v+s]) with v < vn[3v+s] and squared length (each
+ * product and the sum rounded separately) below t1_threshold^2 is a
+ * candidate with id 3v+s; its cells are i = vc[3v+s], k = vc[3v+s+1] (they
+ * share the edge), j = vc[3v+s+2] and l (the third cell of the other end).
+ * It needs more than 3 vertices on i and k and fewer than CG_MAX_RING on j
+ * and l.  In a pass a candidate applies when its id is the smallest among the
+ * candidates touching each of i, j, k, l; the edge is rotated by 90 degrees
+ * about its midpoint to length t1_length and i, k lose the edge to j, l.
+ * After t1_cap passes with transitions a last pass only counts candidates:
+ * any left set CG_ET1_CAP.
+ * ------------------------------------------------------------------------ */
+typedef struct cg_avm_ctx cg_avm_ctx;
+
+typedef struct cg_avm_params {
+  double A0;            /* preferred area */
+  double KA, KP;        /* area and perimeter moduli */
+  double mu;            /* mobility */
+  double Dr;            /* rotational diffusion constant */
+  double dt;            /* time step */
+  double t1_threshold;  /* edges shorter than this undergo a T1 transition (0: none) */
+  double t1_length;     /* length of the rotated edge; 0 = 1.5 t1_threshold */
+  uint64_t seed;        /* Philox key of the director noise */
+  int32_t t1_cap;       /* T1 passes with transitions per step; 0 = 16 */
+  int32_t reserved;
+} cg_avm_params;
+
+/* Workspace size for an N-cell network in an Lx x Ly box. */
+int cg_avm_workspace_bytes(int32_t n, double Lx, double Ly, size_t* bytes);
+/* Builds the Voronoi network of the seeds x, y (n doubles each, host or
+ * device, in [-L, 2L), snapped to the position grid as cg_create does) with
+ * directors theta, per-cell shape index p0 and speed v0.  d_ws: device,
+ * >= cg_avm_workspace_bytes, 256-byte aligned, the caller's until
+ * cg_avm_destroy.  stream: cudaStream_t (may be 0).  Synchronizes. */
+int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const cg_avm_params* params,
+                  const double* x, const double* y, const double* theta, void* d_ws, size_t ws_bytes, void* stream,
+                  cg_avm_ctx** out);
+/* Enqueues nsteps steps (one CUDA graph launch each); does not synchronize. */
+int cg_avm_step(cg_avm_ctx* ctx, int64_t nsteps);
+/* Waits for the stream and returns the device status. */
+int cg_avm_sync(cg_avm_ctx* ctx);
+/* Vertex positions [V] and directors [N]; any pointer may be NULL.  Host or
+ * device pointers.  Synchronizes. */
+int cg_avm_get_state(cg_avm_ctx* ctx, double* hx, double* hy, double* theta);
+/* Network (layout above); any pointer may be NULL.  Synchronizes. */
+int cg_avm_get_topology(cg_avm_ctx* ctx, int32_t* vc, int32_t* vn, int32_t* cc, int32_t* cv);
+/* Replaces positions (required) and, where not NULL, directors and network
+ * arrays, which must describe a valid network of the same N.  Synchronizes. */
+int cg_avm_set_state(cg_avm_ctx* ctx, const double* hx, const double* hy, const double* theta, const int32_t* vc,
+                     const int32_t* vn, const int32_t* cc, const int32_t* cv);
+/* Polygon areas and perimeters [N] of the current state.  Synchronizes. */
+int cg_avm_get_geometry(cg_avm_ctx* ctx, double* A, double* P);
+/* Vertex forces [V] and, if energy != NULL, the total energy of Eq. 1.
+ * Synchronizes. */
+int cg_avm_get_forces(cg_avm_ctx* ctx, double* Fx, double* Fy, double* energy);
+/* T1 passes on the current state, without a move.  Synchronizes. */
+int cg_avm_t1(cg_avm_ctx* ctx);
+/* Per-cell shape index and speed, N doubles (host or device).  Synchronizes. */
+int cg_avm_set_p0(cg_avm_ctx* ctx, const double* p0);
+int cg_avm_set_v0(cg_avm_ctx* ctx, const double* v0);
+/* Counters: steps, repaired_total = T1 transitions made, last_rounds = T1
+ * passes that ran (both since creation), status. */
+int cg_avm_get_counters(cg_avm_ctx* ctx, cg_counters* host_out);
+/* Releases the host context (the workspace stays the caller's). */
+int cg_avm_destroy(cg_avm_ctx* ctx);
+const char* cg_avm_last_error(const cg_avm_ctx* ctx);
 
 /* Releases the host context (the workspace stays the caller's). */
 int cg_destroy(cg_ctx* ctx);

@@ -22,7 +22,8 @@ _lib = None
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "ring overflow",
           -4: "repair cap exceeded", -5: "inconsistent rings", -6: "non-finite position",
-          -7: "box too small", -8: "degenerate input", -9: "too many repair candidates"}
+          -7: "box too small", -8: "degenerate input", -9: "too many repair candidates",
+          -10: "T1 candidates left after the pass cap"}
 
 
 class CellgbError(RuntimeError):
@@ -40,6 +41,13 @@ class cg_params(C.Structure):
     _fields_ = [("A0", C.c_double), ("KA", C.c_double), ("KP", C.c_double), ("mu", C.c_double),
                 ("Dr", C.c_double), ("dt", C.c_double), ("seed", C.c_uint64),
                 ("repair_cap", C.c_int32), ("sort_every", C.c_int32)]
+
+
+class cg_avm_params(C.Structure):
+    _fields_ = [("A0", C.c_double), ("KA", C.c_double), ("KP", C.c_double), ("mu", C.c_double),
+                ("Dr", C.c_double), ("dt", C.c_double), ("t1_threshold", C.c_double),
+                ("t1_length", C.c_double), ("seed", C.c_uint64), ("t1_cap", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class cg_counters(C.Structure):
@@ -92,6 +100,28 @@ def lib():
         for name in ("cg_workspace_bytes", "cg_create", "cg_step", "cg_sync", "cg_profile_step", "cg_get_state", "cg_set_state",
                      "cg_get_geometry", "cg_get_forces", "cg_get_neighbors", "cg_set_p0", "cg_set_v0",
                      "cg_get_counters", "cg_destroy"):
+            getattr(L, name).restype = C.c_int
+        # active vertex model
+        L.cg_avm_workspace_bytes.argtypes = [i32, C.c_double, C.c_double, C.POINTER(C.c_size_t)]
+        L.cg_avm_create.argtypes = [i32, C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(cg_avm_params),
+                                    vp, vp, vp, vp, C.c_size_t, vp, C.POINTER(vp)]
+        L.cg_avm_step.argtypes = [vp, i64]
+        L.cg_avm_sync.argtypes = [vp]
+        L.cg_avm_get_state.argtypes = [vp, vp, vp, vp]
+        L.cg_avm_get_topology.argtypes = [vp, vp, vp, vp, vp]
+        L.cg_avm_set_state.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        L.cg_avm_get_geometry.argtypes = [vp, vp, vp]
+        L.cg_avm_get_forces.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
+        L.cg_avm_t1.argtypes = [vp]
+        L.cg_avm_set_p0.argtypes = [vp, vp]
+        L.cg_avm_set_v0.argtypes = [vp, vp]
+        L.cg_avm_get_counters.argtypes = [vp, C.POINTER(cg_counters)]
+        L.cg_avm_destroy.argtypes = [vp]
+        L.cg_avm_last_error.argtypes = [vp]
+        L.cg_avm_last_error.restype = C.c_char_p
+        for name in ("cg_avm_workspace_bytes", "cg_avm_create", "cg_avm_step", "cg_avm_sync", "cg_avm_get_state",
+                     "cg_avm_get_topology", "cg_avm_set_state", "cg_avm_get_geometry", "cg_avm_get_forces",
+                     "cg_avm_t1", "cg_avm_set_p0", "cg_avm_set_v0", "cg_avm_get_counters", "cg_avm_destroy"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -399,3 +429,161 @@ def _autograd_function():
 def spv_run_differentiable(sim, x0, y0, p0, v0, KA, KP, theta0, nsteps, ckpt_every=50, step0=0):
     """Differentiable nsteps-step SPV run; returns final (x, y, A, P)."""
     return _autograd_function().apply(x0, y0, p0, v0, KA, KP, sim, theta0, nsteps, ckpt_every, step0)
+
+
+# ---------------------------------------------------------------------------
+# Active vertex model (Sec. 2.D, Eq. 4, Fig. 1): C-named wrappers
+# ---------------------------------------------------------------------------
+def _check_avm(rc, ctx=None):
+    if rc != 0:
+        msg = lib().cg_avm_last_error(ctx).decode() if ctx else ""
+        raise CellgbError(rc, msg)
+
+
+def cg_avm_workspace_bytes(n, Lx, Ly):
+    out = C.c_size_t(0)
+    _check_avm(lib().cg_avm_workspace_bytes(int(n), float(Lx), float(Ly), C.byref(out)))
+    return out.value
+
+
+def cg_avm_create(n, Lx, Ly, p0, v0, params, x, y, theta, workspace, stream):
+    ctx = C.c_void_p()
+    _check_avm(lib().cg_avm_create(int(n), float(Lx), float(Ly), float(p0), float(v0), C.byref(params), _ptr(x),
+                                   _ptr(y), _ptr(theta), _ptr(workspace), workspace.numel(), C.c_void_p(stream),
+                                   C.byref(ctx)))
+    return ctx
+
+
+def cg_avm_step(ctx, nsteps):
+    _check_avm(lib().cg_avm_step(ctx, int(nsteps)), ctx)
+
+
+def cg_avm_sync(ctx):
+    _check_avm(lib().cg_avm_sync(ctx), ctx)
+
+
+def cg_avm_get_state(ctx, hx, hy, theta):
+    _check_avm(lib().cg_avm_get_state(ctx, _ptr(hx), _ptr(hy), _ptr(theta)), ctx)
+
+
+def cg_avm_get_topology(ctx, vc, vn, cc, cv):
+    _check_avm(lib().cg_avm_get_topology(ctx, _ptr(vc), _ptr(vn), _ptr(cc), _ptr(cv)), ctx)
+
+
+def cg_avm_set_state(ctx, hx, hy, theta, vc, vn, cc, cv):
+    _check_avm(lib().cg_avm_set_state(ctx, _ptr(hx), _ptr(hy), _ptr(theta), _ptr(vc), _ptr(vn), _ptr(cc),
+                                      _ptr(cv)), ctx)
+
+
+def cg_avm_get_geometry(ctx, A, P):
+    _check_avm(lib().cg_avm_get_geometry(ctx, _ptr(A), _ptr(P)), ctx)
+
+
+def cg_avm_get_forces(ctx, Fx, Fy):
+    E = C.c_double(0.0)
+    _check_avm(lib().cg_avm_get_forces(ctx, _ptr(Fx), _ptr(Fy), C.byref(E)), ctx)
+    return E.value
+
+
+def cg_avm_t1(ctx):
+    _check_avm(lib().cg_avm_t1(ctx), ctx)
+
+
+def cg_avm_set_p0(ctx, p0):
+    _check_avm(lib().cg_avm_set_p0(ctx, _ptr(p0)), ctx)
+
+
+def cg_avm_set_v0(ctx, v0):
+    _check_avm(lib().cg_avm_set_v0(ctx, _ptr(v0)), ctx)
+
+
+def cg_avm_get_counters(ctx):
+    c = cg_counters()
+    _check_avm(lib().cg_avm_get_counters(ctx, C.byref(c)), ctx)
+    return {"steps": c.steps, "t1_total": c.repaired_total, "t1_passes": c.last_rounds, "status": c.status}
+
+
+def cg_avm_destroy(ctx):
+    if ctx:
+        lib().cg_avm_destroy(ctx)
+
+
+class AVM:
+    """A periodic active vertex model started from the Voronoi tessellation of
+    seed positions x, y (numpy, or torch tensors on any device)."""
+
+    def __init__(self, n, Lx, Ly, x, y, theta, p0=3.8, v0=0.1, A0=1.0, KA=1.0, KP=1.0, mu=1.0, Dr=1.0, dt=0.01,
+                 t1_threshold=0.04, t1_length=0.0, seed=0, t1_cap=16, device="cuda"):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.n, self.V = int(n), 2 * int(n)
+        self.params = cg_avm_params(A0, KA, KP, mu, Dr, dt, t1_threshold, t1_length, int(seed), int(t1_cap), 0)
+        nbytes = cg_avm_workspace_bytes(n, Lx, Ly)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = torch.cuda.current_stream(self.device).cuda_stream
+        xs, ys, ts = (self._as_input(v) for v in (x, y, theta))
+        self.ctx = cg_avm_create(n, Lx, Ly, p0, v0, self.params, xs, ys, ts, self.workspace, self.stream)
+
+    def _as_input(self, v, dtype=None):
+        t = self.torch
+        if isinstance(v, t.Tensor):
+            return v.to(dtype=dtype or t.float64).contiguous()
+        return np.ascontiguousarray(v, dtype=np.int32 if dtype is t.int32 else np.float64)
+
+    def _out(self, n, dtype=None):
+        t = self.torch
+        return t.empty(n, dtype=dtype or t.float64, device=self.device)
+
+    def step(self, nsteps=1):
+        cg_avm_step(self.ctx, nsteps)
+
+    def sync(self):
+        cg_avm_sync(self.ctx)
+
+    def state(self):
+        hx, hy, th = self._out(self.V), self._out(self.V), self._out(self.n)
+        cg_avm_get_state(self.ctx, hx, hy, th)
+        return hx, hy, th
+
+    def topology(self):
+        """(vc [V,3], vn [V,3], cc [N], cv [N, MAX_RING]) as int32 tensors."""
+        t = self.torch
+        vc, vn = self._out(3 * self.V, t.int32), self._out(3 * self.V, t.int32)
+        cc, cv = self._out(self.n, t.int32), self._out(self.n * MAX_RING, t.int32)
+        cg_avm_get_topology(self.ctx, vc, vn, cc, cv)
+        return vc.view(self.V, 3), vn.view(self.V, 3), cc, cv.view(self.n, MAX_RING)
+
+    def set_state(self, hx, hy, theta=None, vc=None, vn=None, cc=None, cv=None):
+        t = self.torch
+        ints = [None if a is None else self._as_input(a, t.int32) for a in (vc, vn, cc, cv)]
+        cg_avm_set_state(self.ctx, self._as_input(hx), self._as_input(hy),
+                         None if theta is None else self._as_input(theta), *ints)
+
+    def geometry(self):
+        A, P = self._out(self.n), self._out(self.n)
+        cg_avm_get_geometry(self.ctx, A, P)
+        return A, P
+
+    def forces(self):
+        Fx, Fy = self._out(self.V), self._out(self.V)
+        E = cg_avm_get_forces(self.ctx, Fx, Fy)
+        return Fx, Fy, E
+
+    def t1(self):
+        cg_avm_t1(self.ctx)
+
+    def set_p0(self, p0):
+        cg_avm_set_p0(self.ctx, self._as_input(p0))
+
+    def set_v0(self, v0):
+        cg_avm_set_v0(self.ctx, self._as_input(v0))
+
+    def counters(self):
+        return cg_avm_get_counters(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            self.torch.cuda.synchronize(self.device)
+            cg_avm_destroy(self.ctx)
+            self.ctx = None

@@ -1,0 +1,458 @@
+// C ABI of the active vertex model (AVM) mode of libcellgb.so.
+#include "../../include/cellgb.h"
+#include "cg_device.cuh"
+#include "cg_kernels.h"
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace cgk;
+
+namespace {
+
+struct Lay {
+  size_t total = 0;
+  size_t take(size_t b) {
+    size_t o = total;
+    total += (b + 255) & ~(size_t)255;
+    return o;
+  }
+};
+
+struct AvmOff {
+  size_t spv, spv_bytes;
+  size_t hx, hy, vc, vn, cc, cv, theta, p0, v0, A, P, ka, kp, energy, act, Fx, Fy, lock, cand, done;
+  size_t owned, base_local, base_partial, xs, ys, cnt, nbr, scalar, ctl;
+  size_t total;
+};
+
+AvmOff avm_layout(int64_t n, size_t spv_bytes) {
+  Lay L;
+  AvmOff o;
+  const int64_t V = 2 * n;
+  const size_t d = sizeof(double), i4 = sizeof(int);
+  o.spv_bytes = spv_bytes;
+  o.spv = L.take(spv_bytes);
+  o.hx = L.take(2 * V * d);
+  o.hy = L.take(2 * V * d);
+  o.vc = L.take(3 * V * i4);
+  o.vn = L.take(3 * V * i4);
+  o.cc = L.take(n * i4);
+  o.cv = L.take(n * CG_RING * i4);
+  o.theta = L.take(n * d);
+  o.p0 = L.take(n * d);
+  o.v0 = L.take(n * d);
+  o.A = L.take(n * d);
+  o.P = L.take(n * d);
+  o.ka = L.take(n * d);
+  o.kp = L.take(n * d);
+  o.energy = L.take(n * d);
+  o.act = L.take(n * 2 * d);
+  o.Fx = L.take(V * d);
+  o.Fy = L.take(V * d);
+  o.lock = L.take(n * sizeof(unsigned long long));
+  o.cand = L.take(3 * V * sizeof(int4));
+  o.done = L.take(2 * sizeof(unsigned int));
+  o.owned = L.take(n * i4);
+  o.base_local = L.take((n + 1) * i4);
+  o.base_partial = L.take(((n + 1 + kScanChunk - 1) / kScanChunk + 1) * i4);
+  o.xs = L.take(n * d);
+  o.ys = L.take(n * d);
+  o.cnt = L.take(n * i4);
+  o.nbr = L.take(n * CG_RING * i4);
+  o.scalar = L.take(4 * d);
+  o.ctl = L.take(sizeof(Ctl));
+  o.total = L.total;
+  return o;
+}
+
+}  // namespace
+
+struct cg_avm_ctx {
+  int n = 0, V = 0;
+  double Lx = 0, Ly = 0;
+  cg_avm_params par{};
+  char* ws = nullptr;
+  AvmOff off{};
+  cudaStream_t stream = nullptr, capture = nullptr;
+  cudaGraphExec_t exec = nullptr;     // one step
+  cudaGraphExec_t t1_exec = nullptr;  // T1 passes alone
+  bool broken = false;  // a device status was seen: no further steps
+  std::string last_error;
+  template <class T>
+  T* at(size_t o) const { return reinterpret_cast<T*>(ws + o); }
+  Ctl* ctl() const { return at<Ctl>(off.ctl); }
+};
+
+namespace {
+
+int afail(cg_avm_ctx* c, int code, const std::string& m) {
+  if (c) c->last_error = m;
+  return code;
+}
+
+#define AV_CUDA(ctx, call)                                                              \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return afail(ctx, CG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+int cap_of(const cg_avm_ctx* c) { return c->par.t1_cap > 0 ? c->par.t1_cap : 16; }
+
+AvmArgs avm_args(cg_avm_ctx* c) {
+  AvmArgs a;
+  a.n = c->n;
+  a.V = c->V;
+  a.ctl = c->ctl();
+  a.Lx = c->Lx;
+  a.Ly = c->Ly;
+  a.hx = c->at<double>(c->off.hx);
+  a.hy = c->at<double>(c->off.hy);
+  a.vc = c->at<int>(c->off.vc);
+  a.vn = c->at<int>(c->off.vn);
+  a.cc = c->at<int>(c->off.cc);
+  a.cv = c->at<int>(c->off.cv);
+  a.theta = c->at<double>(c->off.theta);
+  a.p0 = c->at<double>(c->off.p0);
+  a.v0 = c->at<double>(c->off.v0);
+  a.A0 = c->par.A0;
+  a.sqrtA0 = std::sqrt(c->par.A0);
+  a.KA = c->par.KA;
+  a.KP = c->par.KP;
+  a.mu = c->par.mu;
+  a.dt = c->par.dt;
+  a.noise_amp = std::sqrt(2.0 * c->par.Dr * c->par.dt);
+  a.seed = c->par.seed;
+  a.A = c->at<double>(c->off.A);
+  a.P = c->at<double>(c->off.P);
+  a.ka = c->at<double>(c->off.ka);
+  a.kp = c->at<double>(c->off.kp);
+  a.energy = nullptr;
+  a.act = c->at<double2>(c->off.act);
+  a.Fx = c->at<double>(c->off.Fx);
+  a.Fy = c->at<double>(c->off.Fy);
+  a.move = 1;
+  a.thr2 = c->par.t1_threshold * c->par.t1_threshold;
+  a.t1_len = c->par.t1_length > 0 ? c->par.t1_length : 1.5 * c->par.t1_threshold;
+  a.t1_cap = cap_of(c);
+  a.lock = c->at<unsigned long long>(c->off.lock);
+  a.cand = c->at<int4>(c->off.cand);
+  a.done = c->at<unsigned int>(c->off.done);
+  a.loop = 0;
+  return a;
+}
+
+int avm_status(cg_avm_ctx* c) {
+  AV_CUDA(c, cudaStreamSynchronize(c->stream));
+  Ctl h;
+  AV_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
+  if (h.status) {
+    c->broken = true;
+    return afail(c, h.status, std::string("device status: ") + cg_status_string(h.status));
+  }
+  return CG_OK;
+}
+
+// A graph of `prefix` (captured) followed by a while node whose body is one
+// T1 pass; the loop handle starts at 1 on every launch, the pass's first
+// kernel sets it to 0 and its closing block back to 1 when another pass is due.
+template <class Prefix>
+int loop_graph(cg_avm_ctx* c, Prefix prefix, cudaGraphExec_t* out) {
+  if (*out) {
+    cudaGraphExecDestroy(*out);
+    *out = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  AV_CUDA(c, cudaGraphCreate(&g, 0));
+  int rc = CG_OK;
+  do {
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) { rc = CG_ECUDA; break; }
+    AvmArgs a = avm_args(c);
+    a.loop = h;
+    if (cudaStreamBeginCaptureToGraph(c->capture, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess) { rc = CG_ECUDA; break; }
+    prefix(a, c->capture);
+    cudaGraph_t captured = g;
+    if (cudaStreamEndCapture(c->capture, &captured) != cudaSuccess) { rc = CG_ECUDA; break; }
+    // the captured prefix is a chain: its one node without dependents
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    cudaGraphNode_t leaf = nullptr;
+    for (cudaGraphNode_t node : nodes) {
+      size_t nd = 0;
+      cudaGraphNodeGetDependentNodes(node, nullptr, nullptr, &nd);
+      if (nd == 0) leaf = node;
+    }
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t loop;
+    if (cudaGraphAddNode(&loop, g, leaf ? &leaf : nullptr, nullptr, leaf ? 1 : 0, &p) != cudaSuccess) {
+      rc = CG_ECUDA;
+      break;
+    }
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(c->capture, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess) { rc = CG_ECUDA; break; }
+    launch_avm_t1_pass(a, c->capture);
+    if (cudaStreamEndCapture(c->capture, &body) != cudaSuccess) { rc = CG_ECUDA; break; }
+    if (cudaGraphInstantiate(out, g, 0) != cudaSuccess) { rc = CG_ECUDA; break; }
+  } while (0);
+  cudaGraphDestroy(g);
+  if (rc) {
+    cudaGetLastError();
+    return afail(c, rc, "building the T1 loop graph failed");
+  }
+  return CG_OK;
+}
+
+int avm_graphs(cg_avm_ctx* c) {
+  int rc = loop_graph(c, [](const AvmArgs& a, cudaStream_t st) { launch_avm_move(a, st); }, &c->exec);
+  if (rc) return rc;
+  return loop_graph(c, [](const AvmArgs& a, cudaStream_t st) { launch_avm_begin_t1(a.ctl, st); }, &c->t1_exec);
+}
+
+int copy_in(cg_avm_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (!src) return CG_OK;
+  AV_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+  return CG_OK;
+}
+
+int copy_out(cg_avm_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (!dst) return CG_OK;
+  AV_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+  return CG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cg_avm_workspace_bytes(int32_t n, double Lx, double Ly, size_t* bytes) {
+  if (!bytes || n < 16) return CG_EINVAL;
+  cg_replica r{n, Lx, Ly, 3.8, 0.0};
+  size_t spv = 0;
+  int rc = cg_workspace_bytes(1, &r, &spv);
+  if (rc) return rc;
+  *bytes = avm_layout(n, spv).total;
+  return CG_OK;
+}
+
+int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const cg_avm_params* par, const double* x,
+                  const double* y, const double* theta, void* d_ws, size_t ws_bytes, void* stream, cg_avm_ctx** out) {
+  if (!out) return CG_EINVAL;
+  *out = nullptr;
+  if (!par || !x || !y || !theta || !d_ws || ((uintptr_t)d_ws & 255) || n < 16) return CG_EINVAL;
+  if (!(par->dt > 0) || !(par->A0 > 0) || !(par->t1_threshold >= 0)) return CG_EINVAL;
+  size_t need = 0;
+  int rc = cg_avm_workspace_bytes(n, Lx, Ly, &need);
+  if (rc) return rc;
+  if (ws_bytes < need) return CG_EINVAL;
+  cg_avm_ctx* c = new (std::nothrow) cg_avm_ctx();
+  if (!c) return CG_EINVAL;
+  c->n = n;
+  c->V = 2 * n;
+  c->par = *par;
+  c->ws = static_cast<char*>(d_ws);
+  c->stream = static_cast<cudaStream_t>(stream);
+  cg_replica r{n, Lx, Ly, p0, v0};
+  size_t spv_bytes = 0;
+  cg_workspace_bytes(1, &r, &spv_bytes);
+  c->off = avm_layout(n, spv_bytes);
+  do {
+    if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) { rc = CG_ECUDA; break; }
+    // exact Delaunay triangulation of the seeds (temporary SPV context)
+    cg_params sp{};
+    sp.A0 = par->A0; sp.KA = 1.0; sp.KP = 1.0; sp.mu = 1.0; sp.Dr = 0.0; sp.dt = 0.01; sp.seed = 0;
+    sp.repair_cap = 4; sp.sort_every = 0;
+    cg_ctx* spv = nullptr;
+    rc = cg_create(1, &r, &sp, x, y, theta, c->ws + c->off.spv, spv_bytes, stream, &spv);
+    if (rc) { c->last_error = "triangulation of the seeds failed"; break; }
+    rc = cg_get_neighbors(spv, c->at<int>(c->off.cnt), c->at<int>(c->off.nbr));
+    if (!rc) rc = cg_get_state(spv, c->at<double>(c->off.xs), c->at<double>(c->off.ys), nullptr);
+    // box rounded to the position grid 2^-q, as the seeds are
+    if (!rc) {
+      int ex;
+      const double fr = std::frexp(std::fmax(Lx, Ly), &ex);
+      const int q = 50 - ((fr == 0.5) ? ex - 1 : ex);
+      c->Lx = std::ldexp(std::rint(std::ldexp(Lx, q)), -q);
+      c->Ly = std::ldexp(std::rint(std::ldexp(Ly, q)), -q);
+    }
+    cg_destroy(spv);
+    if (rc) break;
+    cudaStream_t st = c->stream;
+    Ctl h;
+    std::memset(&h, 0, sizeof(h));
+    if (cudaMemcpyAsync(c->ctl(), &h, sizeof(Ctl), cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = CG_ECUDA; break; }
+    AvmBuildArgs b;
+    b.n = n;
+    b.ctl = c->ctl();
+    b.Lx = c->Lx;
+    b.Ly = c->Ly;
+    b.x = c->at<double>(c->off.xs);
+    b.y = c->at<double>(c->off.ys);
+    b.cnt = c->at<int>(c->off.cnt);
+    b.nbr = c->at<int>(c->off.nbr);
+    b.owned = c->at<int>(c->off.owned);
+    b.base_local = c->at<int>(c->off.base_local);
+    b.base_partial = c->at<int>(c->off.base_partial);
+    b.vc = c->at<int>(c->off.vc);
+    b.vn = c->at<int>(c->off.vn);
+    b.cc = c->at<int>(c->off.cc);
+    b.cv = c->at<int>(c->off.cv);
+    b.hx = c->at<double>(c->off.hx);
+    b.hy = c->at<double>(c->off.hy);
+    launch_avm_build(b, st);
+    launch_avm_validate(avm_args(c), st);
+    rc = copy_in(c, c->at<double>(c->off.theta), theta, n * sizeof(double));
+    if (rc) break;
+    launch_fill_d(n, p0, c->at<double>(c->off.p0), st);
+    launch_fill_d(n, v0, c->at<double>(c->off.v0), st);
+    launch_fill_u64(n, ~0ull, c->at<unsigned long long>(c->off.lock), st);
+    if (cudaMemsetAsync(c->at<unsigned int>(c->off.done), 0, 2 * sizeof(unsigned int), st) != cudaSuccess) {
+      rc = CG_ECUDA;
+      break;
+    }
+    rc = avm_status(c);
+    if (rc) break;
+    rc = avm_graphs(c);
+  } while (0);
+  if (rc) {
+    cg_avm_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return CG_OK;
+}
+
+int cg_avm_step(cg_avm_ctx* c, int64_t nsteps) {
+  if (!c || nsteps < 0) return CG_EINVAL;
+  if (c->broken) return afail(c, CG_EINVAL, "context holds a device error: " + c->last_error);
+  for (int64_t s = 0; s < nsteps; ++s) AV_CUDA(c, cudaGraphLaunch(c->exec, c->stream));
+  return CG_OK;
+}
+
+int cg_avm_sync(cg_avm_ctx* c) { return c ? avm_status(c) : CG_EINVAL; }
+
+int cg_avm_get_state(cg_avm_ctx* c, double* hx, double* hy, double* theta) {
+  if (!c) return CG_EINVAL;
+  int rc = avm_status(c);
+  if (rc) return rc;
+  Ctl h;
+  AV_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
+  const size_t V = c->V;
+  if ((rc = copy_out(c, hx, c->at<double>(c->off.hx) + h.cur * V, V * sizeof(double)))) return rc;
+  if ((rc = copy_out(c, hy, c->at<double>(c->off.hy) + h.cur * V, V * sizeof(double)))) return rc;
+  if ((rc = copy_out(c, theta, c->at<double>(c->off.theta), c->n * sizeof(double)))) return rc;
+  return avm_status(c);
+}
+
+int cg_avm_get_topology(cg_avm_ctx* c, int32_t* vc, int32_t* vn, int32_t* cc, int32_t* cv) {
+  if (!c) return CG_EINVAL;
+  int rc = avm_status(c);
+  if (rc) return rc;
+  if ((rc = copy_out(c, vc, c->at<int>(c->off.vc), 3 * (size_t)c->V * sizeof(int)))) return rc;
+  if ((rc = copy_out(c, vn, c->at<int>(c->off.vn), 3 * (size_t)c->V * sizeof(int)))) return rc;
+  if ((rc = copy_out(c, cc, c->at<int>(c->off.cc), (size_t)c->n * sizeof(int)))) return rc;
+  if ((rc = copy_out(c, cv, c->at<int>(c->off.cv), (size_t)c->n * CG_RING * sizeof(int)))) return rc;
+  return avm_status(c);
+}
+
+int cg_avm_set_state(cg_avm_ctx* c, const double* hx, const double* hy, const double* theta, const int32_t* vc,
+                     const int32_t* vn, const int32_t* cc, const int32_t* cv) {
+  if (!c || !hx || !hy) return CG_EINVAL;
+  int rc = avm_status(c);
+  if (rc) return rc;
+  Ctl h;
+  AV_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
+  const size_t V = c->V;
+  if ((rc = copy_in(c, c->at<double>(c->off.hx) + h.cur * V, hx, V * sizeof(double)))) return rc;
+  if ((rc = copy_in(c, c->at<double>(c->off.hy) + h.cur * V, hy, V * sizeof(double)))) return rc;
+  if ((rc = copy_in(c, c->at<double>(c->off.theta), theta, c->n * sizeof(double)))) return rc;
+  if ((rc = copy_in(c, c->at<int>(c->off.vc), vc, 3 * V * sizeof(int)))) return rc;
+  if ((rc = copy_in(c, c->at<int>(c->off.vn), vn, 3 * V * sizeof(int)))) return rc;
+  if ((rc = copy_in(c, c->at<int>(c->off.cc), cc, c->n * sizeof(int)))) return rc;
+  if ((rc = copy_in(c, c->at<int>(c->off.cv), cv, c->n * CG_RING * sizeof(int)))) return rc;
+  launch_avm_validate(avm_args(c), c->stream);
+  return avm_status(c);
+}
+
+int cg_avm_get_geometry(cg_avm_ctx* c, double* A, double* P) {
+  if (!c) return CG_EINVAL;
+  launch_avm_forces(avm_args(c), c->stream);
+  int rc;
+  if ((rc = copy_out(c, A, c->at<double>(c->off.A), c->n * sizeof(double)))) return rc;
+  if ((rc = copy_out(c, P, c->at<double>(c->off.P), c->n * sizeof(double)))) return rc;
+  return avm_status(c);
+}
+
+int cg_avm_get_forces(cg_avm_ctx* c, double* Fx, double* Fy, double* energy) {
+  if (!c) return CG_EINVAL;
+  AvmArgs a = avm_args(c);
+  a.energy = c->at<double>(c->off.energy);
+  launch_avm_forces(a, c->stream);
+  int rc;
+  if ((rc = copy_out(c, Fx, c->at<double>(c->off.Fx), c->V * sizeof(double)))) return rc;
+  if ((rc = copy_out(c, Fy, c->at<double>(c->off.Fy), c->V * sizeof(double)))) return rc;
+  if (energy) {
+    launch_reduce_sum(c->n, a.energy, c->at<double>(c->off.scalar), c->stream);
+    AV_CUDA(c, cudaMemcpyAsync(energy, c->at<double>(c->off.scalar), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  return avm_status(c);
+}
+
+int cg_avm_t1(cg_avm_ctx* c) {
+  if (!c) return CG_EINVAL;
+  int rc = avm_status(c);
+  if (rc) return rc;
+  if (c->broken) return afail(c, CG_EINVAL, "context holds a device error: " + c->last_error);
+  AV_CUDA(c, cudaGraphLaunch(c->t1_exec, c->stream));
+  return avm_status(c);
+}
+
+int cg_avm_set_p0(cg_avm_ctx* c, const double* p0) {
+  if (!c || !p0) return CG_EINVAL;
+  int rc = copy_in(c, c->at<double>(c->off.p0), p0, c->n * sizeof(double));
+  return rc ? rc : avm_status(c);
+}
+
+int cg_avm_set_v0(cg_avm_ctx* c, const double* v0) {
+  if (!c || !v0) return CG_EINVAL;
+  int rc = copy_in(c, c->at<double>(c->off.v0), v0, c->n * sizeof(double));
+  return rc ? rc : avm_status(c);
+}
+
+int cg_avm_get_counters(cg_avm_ctx* c, cg_counters* out) {
+  if (!c || !out) return CG_EINVAL;
+  AV_CUDA(c, cudaStreamSynchronize(c->stream));
+  Ctl h;
+  AV_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
+  out->steps = h.step;
+  out->flagged_total = 0;
+  out->repaired_total = h.repaired_total;  // T1 transitions
+  out->last_flagged = 0;
+  out->last_rounds = h.round_count;        // T1 passes
+  out->status = h.status;
+  out->reserved = 0;
+  return CG_OK;
+}
+
+int cg_avm_destroy(cg_avm_ctx* c) {
+  if (!c) return CG_EINVAL;
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->t1_exec) cudaGraphExecDestroy(c->t1_exec);
+  if (c->capture) cudaStreamDestroy(c->capture);
+  delete c;
+  return CG_OK;
+}
+
+const char* cg_avm_last_error(const cg_avm_ctx* c) { return c ? c->last_error.c_str() : "null context"; }
+
+}  // extern "C"

@@ -1,0 +1,493 @@
+// Active vertex model (AVM) kernels (Sussman, arXiv 1702.02939, Sec. 2.D,
+// Eq. 4, Fig. 1).
+//
+// State: vertex positions (two buffers), per-vertex cells and neighbours
+// (vc, vn: counter-clockwise, the edge v-vn[k] separates vc[k] and vc[k+1]),
+// per-cell counter-clockwise vertex lists (cc, cv), directors theta.
+// One step: polygon geometry per cell; vertex force and move per vertex
+// (Eq. 4 with the activity averaged over the vertex's three cells); director
+// rotation per cell; then T1 passes: edges shorter than the threshold propose
+// a transition and take an atomic-min lock (edge id) on their four cells;
+// an edge whose id holds all four locks rotates by 90 degrees about its
+// midpoint and exchanges neighbours; passes repeat until none is proposed.
+#include "cg_device.cuh"
+#include "cg_kernels.h"
+
+namespace cgk {
+
+__device__ __forceinline__ double mimg_d(double d, double L) {
+  if (d > 0.5 * L) d -= L;
+  else if (d < -0.5 * L) d += L;
+  return d;
+}
+__device__ __forceinline__ double wrap_d(double v, double L) {
+  if (v >= 0.0 && v < L) return v;
+  if (v >= L && v < 2.0 * L) return v - L;
+  if (v < 0.0 && v >= -L) {
+    const double r = v + L;
+    return r >= L ? 0.0 : r;
+  }
+  double r = fmod(v, L);
+  if (r < 0.0) r += L;
+  return r >= L ? 0.0 : r;
+}
+
+// ---------------------------------------------------------------------------
+// Building the Voronoi network from a Delaunay triangulation (rings in user
+// order).  Vertex ids: the triangles owned by each cell (its smallest cell),
+// in ring order, numbered consecutively in increasing cell index.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool owns(const int* nbr, const int* cnt, int o, int b) {
+  const int m = cnt[o];
+  const int j = nbr[o * CG_RING + b], k = nbr[o * CG_RING + (b + 1) % m];
+  return o < j && o < k;
+}
+
+__global__ void k_avm_count_owned(AvmBuildArgs g) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= g.n) return;
+  int c = 0;
+  for (int b = 0; b < g.cnt[o]; ++b) c += owns(g.nbr, g.cnt, o, b);
+  g.owned[o] = c;
+}
+
+__device__ __forceinline__ int owned_rank(const AvmBuildArgs& g, int o, int b) {
+  int r = 0;
+  for (int t = 0; t < b; ++t) r += owns(g.nbr, g.cnt, o, t);
+  return bin_begin(g.base_local, g.base_partial, o) + r;
+}
+
+__device__ __forceinline__ int slot_pair(const AvmBuildArgs& g, int c, int u, int w) {
+  const int m = g.cnt[c];
+  for (int b = 0; b < m; ++b)
+    if (g.nbr[c * CG_RING + b] == u && g.nbr[c * CG_RING + (b + 1) % m] == w) return b;
+  return -1;
+}
+
+__global__ void k_avm_cell_lists(AvmBuildArgs g) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.n) return;
+  const int m = g.cnt[c];
+  g.cc[c] = m;
+  for (int a = 0; a < CG_RING; ++a) {
+    int vid = -1;
+    if (a < m) {
+      const int j = g.nbr[c * CG_RING + a], k = g.nbr[c * CG_RING + (a + 1) % m];
+      if (c < j && c < k) {
+        vid = owned_rank(g, c, a);
+      } else {
+        int o, b;
+        if (j < k) { o = j; b = slot_pair(g, j, k, c); }
+        else { o = k; b = slot_pair(g, k, c, j); }
+        vid = b < 0 ? -1 : owned_rank(g, o, b);
+      }
+      if (vid >= 2 * g.n) vid = -1;
+      if (vid < 0) raise_status(g.ctl, kETOPO);
+    }
+    g.cv[c * CG_RING + a] = vid;
+  }
+}
+
+__global__ void k_avm_vertices(AvmBuildArgs g) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= g.n) return;
+  const int m = g.cnt[o];
+  for (int b = 0; b < m; ++b) {
+    if (!owns(g.nbr, g.cnt, o, b)) continue;
+    const int j = g.nbr[o * CG_RING + b], k = g.nbr[o * CG_RING + (b + 1) % m];
+    const int v = g.cv[o * CG_RING + b];
+    if (v < 0) continue;
+    g.vc[3 * v + 0] = o; g.vc[3 * v + 1] = j; g.vc[3 * v + 2] = k;
+    g.vn[3 * v + 0] = g.cv[o * CG_RING + (b + m - 1) % m];  // across the edge o-j
+    const int p = slot_pair(g, j, k, o);                     // (j, k, o) around j
+    const int mj = g.cnt[j];
+    if (p < 0) raise_status(g.ctl, kETOPO);
+    g.vn[3 * v + 1] = p < 0 ? -1 : g.cv[j * CG_RING + (p + mj - 1) % mj];  // across j-k
+    g.vn[3 * v + 2] = g.cv[o * CG_RING + (b + 1) % m];      // across k-o
+    // circumcentre of (o, j, k), minimum-image offsets from o
+    const double ax = mimg_d(g.x[j] - g.x[o], g.Lx), ay = mimg_d(g.y[j] - g.y[o], g.Ly);
+    const double bx = mimg_d(g.x[k] - g.x[o], g.Lx), by = mimg_d(g.y[k] - g.y[o], g.Ly);
+    const double d = 2.0 * (ax * by - ay * bx);
+    const double la = ax * ax + ay * ay, lb = bx * bx + by * by;
+    g.hx[v] = wrap_d(g.x[o] + (by * la - ay * lb) / d, g.Lx);
+    g.hy[v] = wrap_d(g.y[o] + (ax * lb - bx * la) / d, g.Ly);
+  }
+}
+
+void launch_avm_build(const AvmBuildArgs& a, cudaStream_t st) {
+  const int blocks = (a.n + 127) / 128;
+  k_avm_count_owned<<<blocks, 128, 0, st>>>(a);
+  CellListArgs sc{};
+  sc.n = a.n;
+  sc.nbins = a.n;
+  sc.ctl = a.ctl;
+  sc.bin_count = a.owned;
+  sc.bin_start = a.base_local;
+  sc.scan_partials = a.base_partial;
+  sc.only_if_flagged = 0;
+  launch_scan(sc, st);
+  k_avm_cell_lists<<<blocks, 128, 0, st>>>(a);
+  k_avm_vertices<<<blocks, 128, 0, st>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// Step kernels.
+// ---------------------------------------------------------------------------
+// True in exactly one block of the grid: the last one to get here.  Every
+// thread of every block must call it; each block's global writes are fenced
+// before it counts itself, and the last block fences again before reading.
+// The last block resets the counter for the next launch.
+__device__ __forceinline__ bool last_block(unsigned int* done) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(done, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    if (threadIdx.x == 0) *done = 0u;
+  }
+  return s_last;
+}
+
+// Per cell: area and perimeter of the polygon, the force coefficients
+// ka = 2 K_A (A - A0) and kp = 2 K_P (P - P0), and, when stepping, the
+// self-propulsion v0 n(theta) of the current director followed by the
+// director update theta <- theta + sqrt(2 D_r dt) xi (Philox, counter
+// (cell, step)).
+__global__ void k_avm_cells(AvmArgs g) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.n) return;
+  const size_t V = (size_t)g.V;
+  const int cur = g.ctl->cur;
+  const double* hx = g.hx + cur * V;
+  const double* hy = g.hy + cur * V;
+  const int m = g.cc[c];
+  if (m < 3 || m > CG_RING) {
+    raise_status(g.ctl, kETOPO);
+    return;
+  }
+  const int* row = g.cv + (size_t)c * CG_RING;
+  for (int a = 0; a < m; ++a)
+    if ((unsigned)row[a] >= (unsigned)g.V) {
+      raise_status(g.ctl, kETOPO);
+      return;
+    }
+  const int v0 = row[0];
+  const double x0 = hx[v0], y0 = hy[v0];
+  double px = 0.0, py = 0.0, area = 0.0, per = 0.0;
+  for (int a = 1; a <= m; ++a) {
+    double qx = 0.0, qy = 0.0;
+    if (a < m) {
+      const int v = row[a];
+      qx = mimg_d(hx[v] - x0, g.Lx);
+      qy = mimg_d(hy[v] - y0, g.Ly);
+    }
+    area += px * qy - qx * py;
+    per += sqrt((qx - px) * (qx - px) + (qy - py) * (qy - py));
+    px = qx;
+    py = qy;
+  }
+  const double A = 0.5 * area, P = per;
+  g.A[c] = A;
+  g.P[c] = P;
+  const double dA = A - g.A0, dP = P - g.p0[c] * g.sqrtA0;
+  g.ka[c] = 2.0 * g.KA * dA;
+  g.kp[c] = 2.0 * g.KP * dP;
+  if (g.energy) g.energy[c] = g.KA * dA * dA + g.KP * dP * dP;
+  if (g.move) {
+    const double th = g.theta[c];
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    g.act[c] = make_double2(g.v0[c] * cs, g.v0[c] * sn);
+    g.theta[c] = th + g.noise_amp * director_noise(g.seed, c, g.ctl->step);
+  }
+}
+
+// Per vertex: F_v = -sum_k [ka_k 1/2 perp(u_{k-1} - u_k) - kp_k (u^_k + u^_{k-1})]
+// with u_k = h(n_k) - h(v); then, when stepping, the move of Eq. 4 into the
+// other position buffer.  The last block switches buffers, advances the step
+// counter and opens the step's T1 passes.
+__global__ void k_avm_force_move(AvmArgs g) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t V = (size_t)g.V;
+  const int cur = g.ctl->cur;
+  bool ok = v < g.V;
+  if (ok)
+    for (int k = 0; k < 3; ++k)
+      if ((unsigned)g.vn[3 * v + k] >= (unsigned)g.V || (unsigned)g.vc[3 * v + k] >= (unsigned)g.n) {
+        raise_status(g.ctl, kETOPO);
+        ok = false;
+        break;
+      }
+  if (ok) {
+    const double* hx = g.hx + cur * V;
+    const double* hy = g.hy + cur * V;
+    const double xv = hx[v], yv = hy[v];
+    double ux[3], uy[3], nx[3], ny[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int w = g.vn[3 * v + k];
+      ux[k] = mimg_d(hx[w] - xv, g.Lx);
+      uy[k] = mimg_d(hy[w] - yv, g.Ly);
+      const double il = rsqrt(ux[k] * ux[k] + uy[k] * uy[k]);
+      nx[k] = ux[k] * il;
+      ny[k] = uy[k] * il;
+    }
+    double fx = 0.0, fy = 0.0, ax = 0.0, ay = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int km = (k + 2) % 3;
+      const int c = g.vc[3 * v + k];
+      const double ka = g.ka[c], kp = g.kp[c];
+      const double dx = ux[km] - ux[k], dy = uy[km] - uy[k];
+      // dE_c/dh = ka/2 perp(h_next - h_prev) + kp (t^_in - t^_out), perp(d) = (d_y, -d_x)
+      fx -= 0.5 * ka * dy - kp * (nx[k] + nx[km]);
+      fy -= -0.5 * ka * dx - kp * (ny[k] + ny[km]);
+      if (g.move) {
+        const double2 a = g.act[c];
+        ax += a.x;
+        ay += a.y;
+      }
+    }
+    g.Fx[v] = fx;
+    g.Fy[v] = fy;
+    if (g.move) {
+      const int nxt = cur ^ 1;
+      const double mx = xv + g.dt * (g.mu * fx + ax / 3.0), my = yv + g.dt * (g.mu * fy + ay / 3.0);
+      if (!isfinite(mx) || !isfinite(my)) raise_status(g.ctl, kENONFINITE);
+      g.hx[nxt * V + v] = wrap_d(mx, g.Lx);
+      g.hy[nxt * V + v] = wrap_d(my, g.Ly);
+    }
+  }
+  if (!g.move) return;  // uniform over the grid
+  if (last_block(g.done) && threadIdx.x == 0) {
+    Ctl* ctl = g.ctl;
+    ctl->cur = cur ^ 1;
+    ctl->step += 1;
+    ctl->last_flagged = 0;  // T1 passes run in this step
+  }
+}
+
+// Opens T1 passes on the current state without a move.
+__global__ void k_avm_begin_t1(Ctl* ctl) {
+  ctl->last_flagged = 0;
+  ctl->count[1] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// T1 passes: the body of a conditional (while) graph node.  Candidate edges
+// take an atomic minimum of a 64-bit key on their four cells; the high word
+// 0xffffffff - pass number makes every key of this pass smaller than any
+// left over from earlier passes, so the locks never need clearing.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long lock_key(int stamp, int e) {
+  return ((unsigned long long)(0xffffffffu - (unsigned)stamp) << 32) | (unsigned)e;
+}
+
+__device__ __forceinline__ double len2_rn(double dx, double dy) {
+  // products and sum rounded separately (no fused multiply-add)
+  return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+}
+
+__global__ void k_t1_propose(AvmArgs g) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  // stop the loop unless the closing kernel of this pass asks for another
+  if (v == 0) cudaGraphSetConditional(g.loop, 0);
+  if (v >= g.V) return;
+  const size_t V = (size_t)g.V;
+  const int cur = g.ctl->cur;
+  const int stamp = g.ctl->round_count;
+  const double* hx = g.hx + cur * V;
+  const double* hy = g.hy + cur * V;
+  for (int s = 0; s < 3; ++s) {
+    const int e = 3 * v + s;
+    g.cand[e] = make_int4(-1, -1, -1, -1);
+    const int w = g.vn[e];
+    if (w <= v) continue;
+    if (w >= g.V) {
+      raise_status(g.ctl, kETOPO);
+      continue;
+    }
+    const double dx = mimg_d(hx[w] - hx[v], g.Lx), dy = mimg_d(hy[w] - hy[v], g.Ly);
+    if (!(len2_rn(dx, dy) < g.thr2)) continue;
+    const int i = g.vc[e], k = g.vc[3 * v + (s + 1) % 3], j = g.vc[3 * v + (s + 2) % 3];
+    int l = -1;
+    for (int t = 0; t < 3; ++t) {
+      const int c = g.vc[3 * w + t];
+      if (c != i && c != k) l = c;
+    }
+    if (l < 0) {
+      raise_status(g.ctl, kETOPO);
+      continue;
+    }
+    if (g.cc[i] <= 3 || g.cc[k] <= 3 || g.cc[j] >= CG_RING || g.cc[l] >= CG_RING) continue;
+    g.cand[e] = make_int4(i, j, k, l);
+    const unsigned long long key = lock_key(stamp, e);
+    atomicMin(&g.lock[i], key);
+    atomicMin(&g.lock[j], key);
+    atomicMin(&g.lock[k], key);
+    atomicMin(&g.lock[l], key);
+    atomicAdd(&g.ctl->count[1], 1);
+  }
+}
+
+__device__ __forceinline__ int slot3(const int* a, int v, int val) {
+  for (int s = 0; s < 3; ++s)
+    if (a[3 * v + s] == val) return s;
+  return -1;
+}
+
+__device__ void remove_from_cell(int* cc, int* cv, int c, int v) {
+  const int m = cc[c];
+  int* row = cv + (size_t)c * CG_RING;
+  int w = 0;
+  for (int a = 0; a < m; ++a)
+    if (row[a] != v) row[w++] = row[a];
+  for (int a = w; a < CG_RING; ++a) row[a] = -1;
+  cc[c] = w;
+}
+
+__device__ void insert_in_cell(int* cc, int* cv, int c, int after, int v) {
+  const int m = cc[c];
+  int* row = cv + (size_t)c * CG_RING;
+  int pos = -1;
+  for (int a = 0; a < m; ++a)
+    if (row[a] == after) pos = a;
+  for (int a = m; a > pos + 1; --a) row[a] = row[a - 1];
+  row[pos + 1] = v;
+  cc[c] = m + 1;
+}
+
+__device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd) {
+  Ctl* ctl = g.ctl;
+  const size_t V = (size_t)g.V;
+  double* hx = g.hx + ctl->cur * V;
+  double* hy = g.hy + ctl->cur * V;
+  const int e = 3 * v1 + a;
+  const int i = cd.x, j = cd.y, k = cd.z, l = cd.w;
+  const int v2 = g.vn[e];
+  const int Aul = g.vn[3 * v1 + (a + 1) % 3], All = g.vn[3 * v1 + (a + 2) % 3];
+  const int b = slot3(g.vn, v2, v1);
+  if (b < 0 || g.vc[3 * v2 + b] != k || g.vc[3 * v2 + (b + 1) % 3] != i) {
+    raise_status(ctl, kETOPO);
+    return;
+  }
+  const int Alr = g.vn[3 * v2 + (b + 1) % 3], Aur = g.vn[3 * v2 + (b + 2) % 3];
+  const int su = slot3(g.vn, Aul, v1), sl = slot3(g.vn, Alr, v2);
+  if (su < 0 || sl < 0) {
+    raise_status(ctl, kETOPO);
+    return;
+  }
+  // rotate the edge by 90 degrees about its midpoint, new length t1_len
+  const double ex = mimg_d(hx[v2] - hx[v1], g.Lx), ey = mimg_d(hy[v2] - hy[v1], g.Ly);
+  const double mx = hx[v1] + 0.5 * ex, my = hy[v1] + 0.5 * ey;
+  const double len = sqrt(ex * ex + ey * ey);
+  const double px = -ey / len * 0.5 * g.t1_len, py = ex / len * 0.5 * g.t1_len;
+  hx[v1] = wrap_d(mx - px, g.Lx);
+  hy[v1] = wrap_d(my - py, g.Ly);
+  hx[v2] = wrap_d(mx + px, g.Lx);
+  hy[v2] = wrap_d(my + py, g.Ly);
+  // neighbour exchange (Fig. 1): v1 -> cells (j, i, l), v2 -> cells (k, j, l)
+  g.vc[3 * v1 + 0] = j; g.vc[3 * v1 + 1] = i; g.vc[3 * v1 + 2] = l;
+  g.vn[3 * v1 + 0] = All; g.vn[3 * v1 + 1] = Alr; g.vn[3 * v1 + 2] = v2;
+  g.vc[3 * v2 + 0] = k; g.vc[3 * v2 + 1] = j; g.vc[3 * v2 + 2] = l;
+  g.vn[3 * v2 + 0] = Aul; g.vn[3 * v2 + 1] = v1; g.vn[3 * v2 + 2] = Aur;
+  g.vn[3 * Aul + su] = v2;
+  g.vn[3 * Alr + sl] = v1;
+  remove_from_cell(g.cc, g.cv, i, v2);
+  remove_from_cell(g.cc, g.cv, k, v1);
+  insert_in_cell(g.cc, g.cv, j, v1, v2);
+  insert_in_cell(g.cc, g.cv, l, v2, v1);
+  atomicAdd((unsigned long long*)&ctl->repaired_total, 1ull);
+}
+
+// Applies the candidates that hold all four locks (passes 0 .. t1_cap-1; pass
+// t1_cap only counts).  The last block closes the pass: another pass runs
+// while this one proposed something and the cap is not reached; candidates
+// at the counting pass raise the T1-cap status.
+__global__ void k_t1_apply(AvmArgs g) {
+  Ctl* ctl = g.ctl;
+  const int v1 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int pass = ctl->last_flagged;
+  const int proposed = *(volatile int*)&ctl->count[1];
+  if (proposed > 0 && pass < g.t1_cap && v1 < g.V) {
+    const int stamp = ctl->round_count;
+    for (int a = 0; a < 3; ++a) {
+      const int e = 3 * v1 + a;
+      const int4 cd = g.cand[e];
+      if (cd.x < 0) continue;
+      const unsigned long long key = lock_key(stamp, e);
+      if (g.lock[cd.x] != key || g.lock[cd.y] != key || g.lock[cd.z] != key || g.lock[cd.w] != key) continue;
+      apply_t1(g, v1, a, cd);
+    }
+  }
+  if (last_block(g.done + 1) && threadIdx.x == 0) {
+    ctl->count[1] = 0;
+    ctl->round_count += 1;
+    ctl->last_flagged = pass + 1;
+    if (pass >= g.t1_cap && proposed > 0) atomicCAS(&ctl->status, 0, (int)kET1CAP);
+    if (proposed > 0 && pass < g.t1_cap && ctl->status == 0) cudaGraphSetConditional(g.loop, 1);
+  }
+}
+
+// Index ranges of a network handed in from outside: vc in [0, n), vn in
+// [0, V), 3 <= cc <= CG_RING, cv[a] in [0, V) for a < cc.
+__global__ void k_avm_validate(AvmArgs g) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad = false;
+  if (t < g.V)
+    for (int k = 0; k < 3; ++k)
+      bad |= (unsigned)g.vc[3 * t + k] >= (unsigned)g.n || (unsigned)g.vn[3 * t + k] >= (unsigned)g.V;
+  if (t < g.n) {
+    const int m = g.cc[t];
+    if (m < 3 || m > CG_RING) bad = true;
+    else
+      for (int a = 0; a < m; ++a) bad |= (unsigned)g.cv[(size_t)t * CG_RING + a] >= (unsigned)g.V;
+  }
+  if (bad) raise_status(g.ctl, kEINVAL);
+}
+
+__global__ void k_fill_d(int n, double v, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = v;
+}
+__global__ void k_fill_u64(int n, unsigned long long v, unsigned long long* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+constexpr int kAvmThreads = 128;
+static inline int blocks_of(int n) { return (n + kAvmThreads - 1) / kAvmThreads; }
+
+void launch_avm_move(const AvmArgs& a, cudaStream_t st) {
+  AvmArgs m = a;
+  m.move = 1;
+  k_avm_cells<<<blocks_of(a.n), kAvmThreads, 0, st>>>(m);
+  k_avm_force_move<<<blocks_of(a.V), kAvmThreads, 0, st>>>(m);
+}
+void launch_avm_begin_t1(Ctl* ctl, cudaStream_t st) { k_avm_begin_t1<<<1, 1, 0, st>>>(ctl); }
+void launch_avm_t1_pass(const AvmArgs& a, cudaStream_t st) {
+  k_t1_propose<<<blocks_of(a.V), kAvmThreads, 0, st>>>(a);
+  k_t1_apply<<<blocks_of(a.V), kAvmThreads, 0, st>>>(a);
+}
+void launch_avm_forces(const AvmArgs& a, cudaStream_t st) {
+  AvmArgs f = a;
+  f.move = 0;
+  k_avm_cells<<<blocks_of(a.n), kAvmThreads, 0, st>>>(f);
+  k_avm_force_move<<<blocks_of(a.V), kAvmThreads, 0, st>>>(f);
+}
+void launch_avm_validate(const AvmArgs& a, cudaStream_t st) {
+  k_avm_validate<<<blocks_of(a.V), kAvmThreads, 0, st>>>(a);
+}
+void launch_fill_d(int n, double v, double* out, cudaStream_t st) {
+  if (n > 0) k_fill_d<<<(n + 255) / 256, 256, 0, st>>>(n, v, out);
+}
+void launch_fill_u64(int n, unsigned long long v, unsigned long long* out, cudaStream_t st) {
+  if (n > 0) k_fill_u64<<<(n + 255) / 256, 256, 0, st>>>(n, v, out);
+}
+
+}  // namespace cgk

@@ -1004,6 +1004,7 @@ const char* cg_status_string(int s) {
     case CG_EBOX_TOO_SMALL: return "box too small for the Voronoi search";
     case CG_EDEGENERATE: return "degenerate input (coincident cells)";
     case CG_ECANDIDATES: return "too many repair candidates";
+    case CG_ET1_CAP: return "T1 candidates left after the pass cap";
     default: return "unknown status";
   }
 }

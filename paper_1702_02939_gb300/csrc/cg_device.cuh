@@ -34,6 +34,7 @@ enum : int {
   kEBOX = -7,
   kEDEGEN = -8,
   kECAND = -9,
+  kET1CAP = -10,
 };
 
 // Per-replica constants.

@@ -166,4 +166,45 @@ void launch_force_jvp(const JvpArgs& a, cudaStream_t st);
 void launch_combine_final(int n, const double* gx, const double* gy, const double2* F, double2* g, cudaStream_t st);
 void launch_reduce2(int n, const double* a, const double* b, double* out, cudaStream_t st);
 
+// Active vertex model (avm_kernels.cu)
+struct AvmBuildArgs {
+  int n;
+  Ctl* ctl;
+  double Lx, Ly;
+  const double *x, *y;     // seed positions (user order)
+  const int *cnt, *nbr;    // Delaunay rings (user order)
+  int *owned, *base_local, *base_partial;
+  int *vc, *vn, *cc, *cv;
+  double *hx, *hy;         // first position buffer
+};
+struct AvmArgs {
+  int n, V;
+  Ctl* ctl;
+  double Lx, Ly;
+  double *hx, *hy;         // [2][V]
+  int *vc, *vn, *cc, *cv;
+  double* theta;
+  const double *p0, *v0;
+  double A0, sqrtA0, KA, KP, mu, dt, noise_amp;
+  unsigned long long seed;
+  double *A, *P, *ka, *kp, *energy;
+  double2* act;            // [n] v0 n(theta) of the step's directors
+  double *Fx, *Fy;
+  int move;
+  double thr2, t1_len;
+  int t1_cap;
+  unsigned long long* lock;  // [n] pass-stamped T1 locks
+  int4* cand;                // [3V] proposed transitions (cells i, j, k, l)
+  unsigned int* done;        // [2] last-block counters (force/move, T1 apply)
+  cudaGraphConditionalHandle loop;  // while-node handle of the T1 passes
+};
+void launch_avm_build(const AvmBuildArgs& a, cudaStream_t st);
+void launch_avm_move(const AvmArgs& a, cudaStream_t st);
+void launch_avm_begin_t1(Ctl* ctl, cudaStream_t st);
+void launch_avm_t1_pass(const AvmArgs& a, cudaStream_t st);
+void launch_avm_forces(const AvmArgs& a, cudaStream_t st);
+void launch_avm_validate(const AvmArgs& a, cudaStream_t st);
+void launch_fill_d(int n, double v, double* out, cudaStream_t st);
+void launch_fill_u64(int n, unsigned long long v, unsigned long long* out, cudaStream_t st);
+
 }  // namespace cgk

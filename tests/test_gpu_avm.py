@@ -1,0 +1,226 @@
+"""GPU active vertex model (AVM) against the oracle.
+
+Sussman, arXiv 1702.02939, Sec. 2.D: vertex forces (Eqs. A2-A5), motion
+(Eq. 4), T1 transitions (Fig. 1).  The network built from the seeds, the T1
+decisions and every list of the network must be bit-exact; forces within
+1e-10 max|F|; positions within 1e-12 L per step.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1702_02939_gb300 as cg  # noqa: E402
+
+F_TOL = 1e-10
+X_TOL = 1e-12
+R = oracle.MAX_RING
+
+
+def seeds(n, iseed, L=None):
+    x, y, th, Lr = workloads.spv_uniform(n, iseed, L)
+    Lx, Ly, q = oracle.box(Lr)
+    xs, ys = oracle.snap_positions(x, y, Lx, Ly)
+    return xs, ys, th, Lr, Lx, Ly
+
+
+def make(n, iseed, L=None, **kw):
+    xs, ys, th, Lr, Lx, Ly = seeds(n, iseed, L)
+    sim = cg.AVM(n, Lr, Lr, xs, ys, th, **kw)
+    return sim, xs, ys, th, Lx, Ly
+
+
+def wrapdiff(a, b, L):
+    return (a - b + L / 2) % L - L / 2
+
+
+def gpu_net(sim, Lx, Ly):
+    hx, hy, th = (t.cpu().numpy() for t in sim.state())
+    vc, vn, cc, cv = (t.cpu().numpy() for t in sim.topology())
+    return oracle.AvmNet(sim.n, Lx, Ly, hx, hy, vc.reshape(-1), vn.reshape(-1), cc, cv.reshape(-1)), th
+
+
+def assert_same_network(g, o, tol=X_TOL):
+    np.testing.assert_array_equal(g.vc, o.vc)
+    np.testing.assert_array_equal(g.vn, o.vn)
+    np.testing.assert_array_equal(g.cc, o.cc)
+    np.testing.assert_array_equal(g.cv, o.cv)
+    assert np.abs(wrapdiff(g.hx, o.hx, o.Lx)).max() <= tol * o.Lx
+    assert np.abs(wrapdiff(g.hy, o.hy, o.Ly)).max() <= tol * o.Ly
+
+
+def load(sim, net, theta=None):
+    sim.set_state(net.hx, net.hy, theta, net.vc, net.vn, net.cc, net.cv)
+
+
+def test_smallest_box_is_refused_cleanly():
+    """16 cells at unit density (L = 4): a Voronoi cell can be wider than the
+    cell-list search of the seed triangulation covers in so small a box; the
+    library reports CG_EBOX_TOO_SMALL instead of a wrong network."""
+    with pytest.raises(cg.CellgbError) as e:
+        make(16, 1)
+    assert e.value.code == -7
+
+
+@pytest.mark.parametrize("n,iseed", [(64, 2), (400, 3), (4096, 4)])
+def test_network_build_matches_oracle(n, iseed):
+    sim, xs, ys, th, Lx, Ly = make(n, iseed)
+    g, gth = gpu_net(sim, Lx, Ly)
+    assert_same_network(g, oracle.avm_build(xs, ys, Lx, Ly))
+    np.testing.assert_array_equal(gth, th)
+    sim.close()
+
+
+@pytest.mark.parametrize("p0,KA,KP", [(3.8, 1.0, 1.0), (4.1, 0.5, 2.0)])
+def test_forces_match_oracle(p0, KA, KP):
+    n = 1000
+    sim, xs, ys, th, Lx, Ly = make(n, 5, p0=p0, KA=KA, KP=KP)
+    net = oracle.avm_build(xs, ys, Lx, Ly)
+    load(sim, net)  # identical positions on both sides
+    Fx, Fy, E = sim.forces()
+    A, P = (t.cpu().numpy() for t in sim.geometry())
+    oFx, oFy, oA, oP, oE = oracle.avm_forces(net, p0, KA=KA, KP=KP)
+    scale = max(np.abs(oFx).max(), np.abs(oFy).max())
+    assert np.abs(Fx.cpu().numpy() - oFx).max() <= F_TOL * scale
+    assert np.abs(Fy.cpu().numpy() - oFy).max() <= F_TOL * scale
+    np.testing.assert_allclose(A, oA, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(P, oP, rtol=1e-12, atol=1e-13)
+    assert abs(E - oE) <= 1e-11 * abs(oE)
+    sim.close()
+
+
+def test_per_cell_p0_and_v0():
+    n = 400
+    sim, xs, ys, th, Lx, Ly = make(n, 6, t1_threshold=0.0)
+    rng = np.random.default_rng(2)
+    p0 = rng.uniform(3.6, 4.0, n)
+    v0 = rng.uniform(0.0, 0.3, n)
+    net = oracle.avm_build(xs, ys, Lx, Ly)
+    load(sim, net, th)
+    sim.set_p0(p0)
+    sim.set_v0(v0)
+    Fx, Fy, _ = sim.forces()
+    oFx, oFy, *_ = oracle.avm_forces(net, p0)
+    scale = max(np.abs(oFx).max(), np.abs(oFy).max())
+    assert np.abs(Fx.cpu().numpy() - oFx).max() <= F_TOL * scale
+    sim.step(1)
+    g, gth = gpu_net(sim, Lx, Ly)
+    o, oth, _ = oracle.avm_step(net, th, p0, v0, seed=0, step=0, thr=0.0)
+    assert_same_network(g, o)
+    np.testing.assert_allclose(gth, oth, rtol=0, atol=1e-13)
+    sim.close()
+
+
+@pytest.mark.parametrize("thr", [0.04, 0.1, 0.2])
+def test_t1_passes_match_oracle(thr):
+    """Same network on both sides, then T1 passes only: the winners of every
+    pass (smallest edge id on each of the four cells) and the rewired lists
+    must agree exactly; thr = 0.2 gives many conflicting candidates."""
+    n = 2000
+    sim, xs, ys, th, Lx, Ly = make(n, 7, t1_threshold=thr)
+    net = oracle.avm_build(xs, ys, Lx, Ly)
+    o, k = oracle.avm_t1(net, thr)
+    assert k > 0
+    load(sim, net)
+    sim.t1()
+    g, _ = gpu_net(sim, Lx, Ly)
+    assert_same_network(g, o)
+    c = sim.counters()
+    assert c["t1_total"] == k and c["status"] == 0
+    sim.close()
+
+
+def test_t1_cap_status():
+    """Candidates left after t1_cap passes raise the T1-cap status on the host."""
+    n = 2000
+    sim, xs, ys, th, Lx, Ly = make(n, 7, t1_threshold=0.3, t1_cap=1)
+    net = oracle.avm_build(xs, ys, Lx, Ly)
+    with pytest.raises(oracle.OracleError):
+        oracle.avm_t1(net, 0.3, cap=1)  # the oracle reports the same situation
+    load(sim, net)
+    with pytest.raises(cg.CellgbError) as e:
+        sim.t1()
+    assert e.value.code == -10
+    sim.close()
+
+
+@pytest.mark.parametrize("n,iseed,thr,steps", [(400, 8, 0.04, 1), (2000, 9, 0.1, 1), (2000, 10, 0.1, 5)])
+def test_steps_match_oracle(n, iseed, thr, steps):
+    p0, v0, dt = 3.8, 0.1, 0.01
+    sim, xs, ys, th, Lx, Ly = make(n, iseed, p0=p0, v0=v0, dt=dt, t1_threshold=thr, seed=11)
+    net = oracle.avm_build(xs, ys, Lx, Ly)
+    load(sim, net, th)
+    sim.step(steps)
+    g, gth = gpu_net(sim, Lx, Ly)
+    o, oth, total = net, th, 0
+    for s in range(steps):
+        o, oth, k = oracle.avm_step(o, oth, p0, v0, seed=11, step=s, dt=dt, thr=thr)
+        total += k
+    assert total > 0
+    assert_same_network(g, o, tol=X_TOL * steps)
+    np.testing.assert_allclose(gth, oth, rtol=0, atol=1e-13 * steps)
+    c = sim.counters()
+    assert c["steps"] == steps and c["t1_total"] == total
+    sim.close()
+
+
+def check_network_valid(sim, Lx, Ly, p0):
+    """Properties that hold at any size: degree 3, symmetric neighbour lists,
+    cell lists consistent with vertex lists, areas positive and tiling the box."""
+    g, _ = gpu_net(sim, Lx, Ly)
+    V, n = g.V, g.n
+    vc, vn = g.vc.reshape(V, 3), g.vn.reshape(V, 3)
+    assert np.all(np.bincount(g.vn, minlength=V) == 3)
+    for s in range(3):
+        w = vn[:, s]
+        assert np.all((vn[w] == np.arange(V)[:, None]).any(1))
+    assert int(g.cc.sum()) == 3 * V
+    cv = g.cv.reshape(n, R)
+    for c in range(0, n, max(1, n // 300)):
+        for a in range(g.cc[c]):
+            assert c in vc[cv[c, a]]
+    A, P = (t.cpu().numpy() for t in sim.geometry())
+    assert np.all(A > 0)
+    assert abs(A.sum() - Lx * Ly) <= 1e-9 * Lx * Ly
+    return g
+
+
+def test_long_run_keeps_a_valid_network():
+    n = 4096
+    sim, xs, ys, th, Lx, Ly = make(n, 12, p0=3.8, v0=0.1, t1_threshold=0.04, seed=3)
+    sim.step(300)
+    sim.sync()
+    check_network_valid(sim, Lx, Ly, 3.8)
+    assert sim.counters()["t1_total"] > 0
+    sim.close()
+
+
+def test_full_size_workload():
+    """N = 65536, L = 256 (the benchmark workload): network build bit-exact,
+    forces within tolerance, one step (move, directors, T1) exact, then 50
+    more steps keep a valid network."""
+    n, p0, v0, thr = 65536, 3.8, 0.1, 0.04
+    sim, xs, ys, th, Lx, Ly = make(n, 1, p0=p0, v0=v0, t1_threshold=thr, seed=1)
+    net = oracle.avm_build(xs, ys, Lx, Ly)
+    g, _ = gpu_net(sim, Lx, Ly)
+    assert_same_network(g, net)
+    load(sim, net, th)
+    Fx, Fy, _ = sim.forces()
+    oFx, oFy, *_ = oracle.avm_forces(net, p0)
+    scale = max(np.abs(oFx).max(), np.abs(oFy).max())
+    assert np.abs(Fx.cpu().numpy() - oFx).max() <= F_TOL * scale
+    sim.step(1)
+    g, gth = gpu_net(sim, Lx, Ly)
+    o, oth, k = oracle.avm_step(net, th, p0, v0, seed=1, step=0, thr=thr)
+    assert k > 0
+    assert_same_network(g, o)
+    sim.step(50)
+    check_network_valid(sim, Lx, Ly, p0)
+    sim.close()
