@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-avm", action="store_true")
     ap.add_argument("--avm-steps", type=int, default=500)
+    ap.add_argument("--avm-warmup", type=int, default=100)
+    ap.add_argument("--avm-profile-steps", type=int, default=20)
+    ap.add_argument("--avm-only", action="store_true",
+                    help="run only the AVM section and print its JSON object (a diagnostic, not the bench line)")
     return ap.parse_args()
 
 
@@ -270,7 +274,8 @@ def avm_throughput(args, device):
     L = 256, p0 = 3.8, v0 = 0.1, T1 threshold 0.04, dt = 0.01, FP64.  100
     equilibration steps, then each step (geometry, vertex force and move,
     directors, T1 passes) timed alone with CUDA events, L2 flushed in between.
-    The oracle's AVM step on the same state is timed beside it (one thread)."""
+    The oracle's AVM step from the initial network of the same seeds is timed
+    beside it (one thread)."""
     import numpy as np
     import torch
 
@@ -281,12 +286,12 @@ def avm_throughput(args, device):
     n, thr, p0, v0 = 65536, 0.04, 3.8, 0.1
     x, y, th, L = workloads.spv_uniform(n, 21)
     sim = cg.AVM(n, L, L, x, y, th, p0=p0, v0=v0, dt=DT, t1_threshold=thr, seed=21, device=device)
-    sim.step(100)
+    sim.step(args.avm_warmup)
     sim.sync()
     c0 = sim.counters()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
-    K = args.avm_steps
+    K = args.avm_steps  # 0: eager profiled steps only (no graph launch)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     torch.cuda.synchronize()
     for k in range(K):
@@ -298,6 +303,8 @@ def avm_throughput(args, device):
     sim.sync()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     c1 = sim.counters()
+    prof_steps = max(1, args.avm_profile_steps)
+    ph = sim.profile(prof_steps)
     # oracle on the same kind of state (its own network build), a few steps
     Lx, Ly, q = oracle.box(L)
     xs, ys = oracle.snap_positions(x, y, Lx, Ly)
@@ -311,11 +318,16 @@ def avm_throughput(args, device):
             break
     sim.close()
     V = 2 * n
+    Kd = max(K, 1)
     return {"workload": "avm_N65536_L256_p0_3.8_v0_0.1_thr0.04_dt0.01_fp64", "unit": "vertex-steps/s",
-            "vertex_steps_per_s": V * K / (ms * 1e-3), "cell_steps_per_s": n * K / (ms * 1e-3),
-            "ms_per_step": ms / K, "steps": K, "warmup": 100, "l2": "flushed between timed steps",
-            "t1_per_step": (c1["t1_total"] - c0["t1_total"]) / K,
-            "t1_passes_per_step": (c1["t1_passes"] - c0["t1_passes"]) / K,
+            "vertex_steps_per_s": V * K / (ms * 1e-3) if K else None,
+            "cell_steps_per_s": n * K / (ms * 1e-3) if K else None,
+            "ms_per_step": ms / Kd if K else None, "steps": K, "warmup": args.avm_warmup, "l2": "flushed between timed steps",
+            "t1_per_step": (c1["t1_total"] - c0["t1_total"]) / Kd,
+            "t1_passes_per_step": (c1["t1_passes"] - c0["t1_passes"]) / Kd,
+            "phase_ms_per_step": {"cells": ph["cells_ms"] / prof_steps, "vertices": ph["vertices_ms"] / prof_steps,
+                                  "t1_passes": ph["t1_ms"] / prof_steps,
+                                  "t1_passes_count": ph["t1_passes"] / prof_steps},
             "cpu_oracle": {"value": V * steps / el, "unit": "vertex-steps/s", "cores": 1, "kind": "oracle",
                            "sample": f"{steps} oracle AVM steps of the same N={n} network, {el:.1f} s"}}
 
@@ -425,7 +437,7 @@ def run_ours(args):
     value = world * args.n * args.steps / (ms * 1e-3)
 
     # per-kernel device times (eager launches, CUDA events on the same stream)
-    prof_steps = 20
+    prof_steps = max(1, args.avm_profile_steps)
     ph = sim.profile(prof_steps)
     dominant = max(("geometry", "force_move"), key=lambda k: ph[k])
     dom_ms = ph[dominant] / prof_steps
@@ -491,6 +503,12 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.avm_only:
+        import __graft_entry__
+
+        __graft_entry__.build()
+        print(json.dumps(avm_throughput(args, "cuda:0")), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

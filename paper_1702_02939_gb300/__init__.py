@@ -107,6 +107,7 @@ def lib():
                                     vp, vp, vp, vp, C.c_size_t, vp, C.POINTER(vp)]
         L.cg_avm_step.argtypes = [vp, i64]
         L.cg_avm_sync.argtypes = [vp]
+        L.cg_avm_profile_step.argtypes = [vp, i64, C.POINTER(C.c_double), i32]
         L.cg_avm_get_state.argtypes = [vp, vp, vp, vp]
         L.cg_avm_get_topology.argtypes = [vp, vp, vp, vp, vp]
         L.cg_avm_set_state.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
@@ -121,7 +122,8 @@ def lib():
         L.cg_avm_last_error.restype = C.c_char_p
         for name in ("cg_avm_workspace_bytes", "cg_avm_create", "cg_avm_step", "cg_avm_sync", "cg_avm_get_state",
                      "cg_avm_get_topology", "cg_avm_set_state", "cg_avm_get_geometry", "cg_avm_get_forces",
-                     "cg_avm_t1", "cg_avm_set_p0", "cg_avm_set_v0", "cg_avm_get_counters", "cg_avm_destroy"):
+                     "cg_avm_t1", "cg_avm_set_p0", "cg_avm_set_v0", "cg_avm_get_counters", "cg_avm_destroy",
+                     "cg_avm_profile_step"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -458,6 +460,12 @@ def cg_avm_step(ctx, nsteps):
     _check_avm(lib().cg_avm_step(ctx, int(nsteps)), ctx)
 
 
+def cg_avm_profile_step(ctx, nsteps):
+    out = (C.c_double * 4)()
+    _check_avm(lib().cg_avm_profile_step(ctx, int(nsteps), out, 4), ctx)
+    return {"cells_ms": out[0], "vertices_ms": out[1], "t1_ms": out[2], "t1_passes": out[3]}
+
+
 def cg_avm_sync(ctx):
     _check_avm(lib().cg_avm_sync(ctx), ctx)
 
@@ -540,6 +548,9 @@ class AVM:
 
     def sync(self):
         cg_avm_sync(self.ctx)
+
+    def profile(self, nsteps):
+        return cg_avm_profile_step(self.ctx, nsteps)
 
     def state(self):
         hx, hy, th = self._out(self.V), self._out(self.V), self._out(self.n)

@@ -3,6 +3,7 @@
 #include "cg_device.cuh"
 #include "cg_kernels.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -24,7 +25,7 @@ struct Lay {
 
 struct AvmOff {
   size_t spv, spv_bytes;
-  size_t hx, hy, vc, vn, cc, cv, theta, p0, v0, A, P, ka, kp, energy, act, Fx, Fy, lock, cand, done;
+  size_t hx, hy, hf, vc, vn, cc, cv, theta, p0, v0, A, P, ka, kp, energy, act, Fx, Fy, lock, cand_e, cand, done;
   size_t owned, base_local, base_partial, xs, ys, cnt, nbr, scalar, ctl;
   size_t total;
 };
@@ -38,6 +39,7 @@ AvmOff avm_layout(int64_t n, size_t spv_bytes) {
   o.spv = L.take(spv_bytes);
   o.hx = L.take(2 * V * d);
   o.hy = L.take(2 * V * d);
+  o.hf = L.take(V * sizeof(float2));
   o.vc = L.take(3 * V * i4);
   o.vn = L.take(3 * V * i4);
   o.cc = L.take(n * i4);
@@ -54,7 +56,8 @@ AvmOff avm_layout(int64_t n, size_t spv_bytes) {
   o.Fx = L.take(V * d);
   o.Fy = L.take(V * d);
   o.lock = L.take(n * sizeof(unsigned long long));
-  o.cand = L.take(3 * V * sizeof(int4));
+  o.cand_e = L.take((3 * V / 2 + 1) * i4);  // at most one entry per edge
+  o.cand = L.take((3 * V / 2 + 1) * sizeof(int4));
   o.done = L.take(2 * sizeof(unsigned int));
   o.owned = L.take(n * i4);
   o.base_local = L.take((n + 1) * i4);
@@ -80,6 +83,7 @@ struct cg_avm_ctx {
   cudaStream_t stream = nullptr, capture = nullptr;
   cudaGraphExec_t exec = nullptr;     // one step
   cudaGraphExec_t t1_exec = nullptr;  // T1 passes alone
+  int sms = 0;
   bool broken = false;  // a device status was seen: no further steps
   std::string last_error;
   template <class T>
@@ -102,6 +106,33 @@ int afail(cg_avm_ctx* c, int code, const std::string& m) {
 
 int cap_of(const cg_avm_ctx* c) { return c->par.t1_cap > 0 ? c->par.t1_cap : 16; }
 
+Axis axis(double L) {
+  Axis a;
+  a.L = L;
+  const double h = 0.5 * L;
+  std::memcpy(&a.L_bits, &L, sizeof(double));
+  std::memcpy(&a.half_bits, &h, sizeof(double));
+  return a;
+}
+
+// FP32 squared lengths certainly below / above thr^2.  A float copy of a
+// position in [0, L) is off by at most L 2^-24, the float difference and its
+// periodic correction add 3 L 2^-24 more, so each component of the float edge
+// vector is within delta = 5 L 2^-24 of the exact one and its length within
+// sqrt(2) delta; the margin doubles that, and the factors (1 +- 2^-20) cover
+// the rounding of the float squared length.
+void t1_bounds(double thr, double L, float& lo, float& hi) {
+  const double m = 2.0 * std::sqrt(2.0) * 5.0 * L * std::ldexp(1.0, -24);
+  const double h = (thr + m) * (1.0 + std::ldexp(1.0, -20));
+  hi = std::nextafter((float)(h * h), INFINITY);
+  if (thr > m) {
+    const double l = (thr - m) * (1.0 - std::ldexp(1.0, -20));
+    lo = std::nextafter((float)(l * l), 0.0f);
+  } else {
+    lo = 0.0f;
+  }
+}
+
 AvmArgs avm_args(cg_avm_ctx* c) {
   AvmArgs a;
   a.n = c->n;
@@ -109,6 +140,10 @@ AvmArgs avm_args(cg_avm_ctx* c) {
   a.ctl = c->ctl();
   a.Lx = c->Lx;
   a.Ly = c->Ly;
+  a.ax = axis(c->Lx);
+  a.ay = axis(c->Ly);
+  a.Lxf = (float)c->Lx;
+  a.Lyf = (float)c->Ly;
   a.hx = c->at<double>(c->off.hx);
   a.hy = c->at<double>(c->off.hy);
   a.vc = c->at<int>(c->off.vc);
@@ -137,8 +172,12 @@ AvmArgs avm_args(cg_avm_ctx* c) {
   a.move = 1;
   a.thr2 = c->par.t1_threshold * c->par.t1_threshold;
   a.t1_len = c->par.t1_length > 0 ? c->par.t1_length : 1.5 * c->par.t1_threshold;
+  t1_bounds(c->par.t1_threshold, std::fmax(c->Lx, c->Ly), a.t2lo, a.t2hi);
+  a.hf = c->at<float2>(c->off.hf);
   a.t1_cap = cap_of(c);
+  a.apply_blocks = std::max(1, std::min((c->V + 127) / 128, 2 * std::max(c->sms, 1)));
   a.lock = c->at<unsigned long long>(c->off.lock);
+  a.cand_e = c->at<int>(c->off.cand_e);
   a.cand = c->at<int4>(c->off.cand);
   a.done = c->at<unsigned int>(c->off.done);
   a.loop = 0;
@@ -268,6 +307,9 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
   c->off = avm_layout(n, spv_bytes);
   do {
     if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) { rc = CG_ECUDA; break; }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) { rc = CG_ECUDA; break; }
     // exact Delaunay triangulation of the seeds (temporary SPV context)
     cg_params sp{};
     sp.A0 = par->A0; sp.KA = 1.0; sp.KP = 1.0; sp.mu = 1.0; sp.Dr = 0.0; sp.dt = 0.01; sp.seed = 0;
@@ -311,6 +353,7 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
     b.hy = c->at<double>(c->off.hy);
     launch_avm_build(b, st);
     launch_avm_validate(avm_args(c), st);
+    launch_avm_shadow(avm_args(c), st);
     rc = copy_in(c, c->at<double>(c->off.theta), theta, n * sizeof(double));
     if (rc) break;
     launch_fill_d(n, p0, c->at<double>(c->off.p0), st);
@@ -337,6 +380,45 @@ int cg_avm_step(cg_avm_ctx* c, int64_t nsteps) {
   if (c->broken) return afail(c, CG_EINVAL, "context holds a device error: " + c->last_error);
   for (int64_t s = 0; s < nsteps; ++s) AV_CUDA(c, cudaGraphLaunch(c->exec, c->stream));
   return CG_OK;
+}
+
+int cg_avm_profile_step(cg_avm_ctx* c, int64_t nsteps, double* ms_out, int32_t n_out) {
+  if (!c || !ms_out || n_out < CG_AVM_NUM_PHASES || nsteps < 0) return CG_EINVAL;
+  int rc = avm_status(c);
+  if (rc) return rc;
+  cudaStream_t st = c->stream;
+  cudaEvent_t ev[3];
+  for (int k = 0; k < 3; ++k) AV_CUDA(c, cudaEventCreate(&ev[k]));
+  for (int k = 0; k < CG_AVM_NUM_PHASES; ++k) ms_out[k] = 0.0;
+  AvmArgs a = avm_args(c);  // loop handle 0: the pass control is read back here
+  float ms = 0.f;
+  for (int64_t s = 0; s < nsteps && !rc; ++s) {
+    cudaEventRecord(ev[0], st);
+    launch_avm_move(a, st, 1);
+    cudaEventRecord(ev[1], st);
+    launch_avm_move(a, st, 2);
+    cudaEventRecord(ev[2], st);
+    if (cudaEventSynchronize(ev[2]) != cudaSuccess) { rc = afail(c, CG_ECUDA, "profile sync"); break; }
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    ms_out[0] += ms;
+    cudaEventElapsedTime(&ms, ev[1], ev[2]);
+    ms_out[1] += ms;
+    for (int pass = 0; pass <= cap_of(c) + 1; ++pass) {
+      cudaEventRecord(ev[0], st);
+      launch_avm_t1_pass(a, st);
+      cudaEventRecord(ev[1], st);
+      Ctl h;
+      if (cudaMemcpyAsync(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) { rc = afail(c, CG_ECUDA, "profile sync"); break; }
+      cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      ms_out[2] += ms;
+      ms_out[3] += 1.0;
+      if (!h.pad || h.status) break;
+    }
+  }
+  for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[k]);
+  if (rc) return rc;
+  return avm_status(c);
 }
 
 int cg_avm_sync(cg_avm_ctx* c) { return c ? avm_status(c) : CG_EINVAL; }
@@ -381,6 +463,7 @@ int cg_avm_set_state(cg_avm_ctx* c, const double* hx, const double* hy, const do
   if ((rc = copy_in(c, c->at<int>(c->off.cc), cc, c->n * sizeof(int)))) return rc;
   if ((rc = copy_in(c, c->at<int>(c->off.cv), cv, c->n * CG_RING * sizeof(int)))) return rc;
   launch_avm_validate(avm_args(c), c->stream);
+  launch_avm_shadow(avm_args(c), c->stream);
   return avm_status(c);
 }
 

@@ -20,6 +20,18 @@ __device__ __forceinline__ double mimg_d(double d, double L) {
   else if (d < -0.5 * L) d += L;
   return d;
 }
+// The same minimum image with the |d| > L/2 test on the integer pipe
+// (non-negative doubles order like their bit patterns); the correction itself
+// is rare.  Equal to mimg_d for every input.
+__device__ __forceinline__ double mimg_a(double d, const Axis& a) {
+  if (((unsigned long long)__double_as_longlong(d) & 0x7fffffffffffffffull) > a.half_bits)
+    d = d > 0.0 ? d - a.L : d + a.L;
+  return d;
+}
+__device__ __forceinline__ float mimg_f(float d, float L) {
+  if (fabsf(d) > 0.5f * L) d = d > 0.0f ? d - L : d + L;
+  return d;
+}
 __device__ __forceinline__ double wrap_d(double v, double L) {
   if (v >= 0.0 && v < L) return v;
   if (v >= L && v < 2.0 * L) return v - L;
@@ -30,6 +42,13 @@ __device__ __forceinline__ double wrap_d(double v, double L) {
   double r = fmod(v, L);
   if (r < 0.0) r += L;
   return r >= L ? 0.0 : r;
+}
+
+// Reduction into [0, L) with the common case (already inside; +0 included)
+// decided on the integer pipe.
+__device__ __forceinline__ double wrap_a(double v, const Axis& a) {
+  if ((unsigned long long)__double_as_longlong(v) < a.L_bits) return v;
+  return wrap_d(v, a.L);
 }
 
 // ---------------------------------------------------------------------------
@@ -180,8 +199,8 @@ __global__ void k_avm_cells(AvmArgs g) {
     double qx = 0.0, qy = 0.0;
     if (a < m) {
       const int v = row[a];
-      qx = mimg_d(hx[v] - x0, g.Lx);
-      qy = mimg_d(hy[v] - y0, g.Ly);
+      qx = mimg_a(hx[v] - x0, g.ax);
+      qy = mimg_a(hy[v] - y0, g.ay);
     }
     area += px * qy - qx * py;
     per += sqrt((qx - px) * (qx - px) + (qy - py) * (qy - py));
@@ -228,8 +247,8 @@ __global__ void k_avm_force_move(AvmArgs g) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const int w = g.vn[3 * v + k];
-      ux[k] = mimg_d(hx[w] - xv, g.Lx);
-      uy[k] = mimg_d(hy[w] - yv, g.Ly);
+      ux[k] = mimg_a(hx[w] - xv, g.ax);
+      uy[k] = mimg_a(hy[w] - yv, g.ay);
       const double il = rsqrt(ux[k] * ux[k] + uy[k] * uy[k]);
       nx[k] = ux[k] * il;
       ny[k] = uy[k] * il;
@@ -256,8 +275,10 @@ __global__ void k_avm_force_move(AvmArgs g) {
       const int nxt = cur ^ 1;
       const double mx = xv + g.dt * (g.mu * fx + ax / 3.0), my = yv + g.dt * (g.mu * fy + ay / 3.0);
       if (!isfinite(mx) || !isfinite(my)) raise_status(g.ctl, kENONFINITE);
-      g.hx[nxt * V + v] = wrap_d(mx, g.Lx);
-      g.hy[nxt * V + v] = wrap_d(my, g.Ly);
+      const double wx = wrap_a(mx, g.ax), wy = wrap_a(my, g.ay);
+      g.hx[nxt * V + v] = wx;
+      g.hy[nxt * V + v] = wy;
+      g.hf[v] = make_float2((float)wx, (float)wy);
     }
   }
   if (!g.move) return;  // uniform over the grid
@@ -266,6 +287,7 @@ __global__ void k_avm_force_move(AvmArgs g) {
     ctl->cur = cur ^ 1;
     ctl->step += 1;
     ctl->last_flagged = 0;  // T1 passes run in this step
+    ctl->pad = 1;
   }
 }
 
@@ -273,6 +295,7 @@ __global__ void k_avm_force_move(AvmArgs g) {
 __global__ void k_avm_begin_t1(Ctl* ctl) {
   ctl->last_flagged = 0;
   ctl->count[1] = 0;
+  ctl->pad = 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -290,27 +313,37 @@ __device__ __forceinline__ double len2_rn(double dx, double dy) {
   return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
 }
 
+// One thread per vertex v, its edges (v, w) with w > v.  The squared length
+// is first bounded in FP32 from the float copies of the positions; only edges
+// within the error band of the threshold are decided in FP64 in the fixed
+// rounding order.  Candidates go to a compact list.
 __global__ void k_t1_propose(AvmArgs g) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   // stop the loop unless the closing kernel of this pass asks for another
-  if (v == 0) cudaGraphSetConditional(g.loop, 0);
+  if (v == 0 && g.loop) cudaGraphSetConditional(g.loop, 0);
   if (v >= g.V) return;
   const size_t V = (size_t)g.V;
-  const int cur = g.ctl->cur;
+  const float2 pv = g.hf[v];
   const int stamp = g.ctl->round_count;
-  const double* hx = g.hx + cur * V;
-  const double* hy = g.hy + cur * V;
   for (int s = 0; s < 3; ++s) {
     const int e = 3 * v + s;
-    g.cand[e] = make_int4(-1, -1, -1, -1);
     const int w = g.vn[e];
     if (w <= v) continue;
     if (w >= g.V) {
       raise_status(g.ctl, kETOPO);
       continue;
     }
-    const double dx = mimg_d(hx[w] - hx[v], g.Lx), dy = mimg_d(hy[w] - hy[v], g.Ly);
-    if (!(len2_rn(dx, dy) < g.thr2)) continue;
+    const float2 pw = g.hf[w];
+    const float fx = mimg_f(pw.x - pv.x, g.Lxf), fy = mimg_f(pw.y - pv.y, g.Lyf);
+    const float l2 = fx * fx + fy * fy;
+    if (l2 > g.t2hi) continue;
+    if (!(l2 < g.t2lo)) {
+      const int cur = g.ctl->cur;
+      const double* hx = g.hx + cur * V;
+      const double* hy = g.hy + cur * V;
+      const double dx = mimg_a(hx[w] - hx[v], g.ax), dy = mimg_a(hy[w] - hy[v], g.ay);
+      if (!(len2_rn(dx, dy) < g.thr2)) continue;
+    }
     const int i = g.vc[e], k = g.vc[3 * v + (s + 1) % 3], j = g.vc[3 * v + (s + 2) % 3];
     int l = -1;
     for (int t = 0; t < 3; ++t) {
@@ -322,13 +355,14 @@ __global__ void k_t1_propose(AvmArgs g) {
       continue;
     }
     if (g.cc[i] <= 3 || g.cc[k] <= 3 || g.cc[j] >= CG_RING || g.cc[l] >= CG_RING) continue;
-    g.cand[e] = make_int4(i, j, k, l);
     const unsigned long long key = lock_key(stamp, e);
     atomicMin(&g.lock[i], key);
     atomicMin(&g.lock[j], key);
     atomicMin(&g.lock[k], key);
     atomicMin(&g.lock[l], key);
-    atomicAdd(&g.ctl->count[1], 1);
+    const int slot = atomicAdd(&g.ctl->count[1], 1);
+    g.cand_e[slot] = e;
+    g.cand[slot] = make_int4(i, j, k, l);
   }
 }
 
@@ -359,6 +393,62 @@ __device__ void insert_in_cell(int* cc, int* cv, int c, int after, int v) {
   cc[c] = m + 1;
 }
 
+// A cell's vertex list held in registers: four 16-byte loads, edits by
+// compile-time-indexed selects, four 16-byte stores.  Slots past the count
+// hold -1, as after the in-memory edits above.
+struct Row {
+  int r[CG_RING];
+};
+__device__ __forceinline__ Row load_row(const int* cv, int c) {
+  Row w;
+  const int4* p = reinterpret_cast<const int4*>(cv + (size_t)c * CG_RING);
+#pragma unroll
+  for (int q = 0; q < CG_RING / 4; ++q) {
+    const int4 t = p[q];
+    w.r[4 * q] = t.x; w.r[4 * q + 1] = t.y; w.r[4 * q + 2] = t.z; w.r[4 * q + 3] = t.w;
+  }
+  return w;
+}
+__device__ __forceinline__ void store_row(int* cv, int c, const Row& w) {
+  int4* p = reinterpret_cast<int4*>(cv + (size_t)c * CG_RING);
+#pragma unroll
+  for (int q = 0; q < CG_RING / 4; ++q)
+    p[q] = make_int4(w.r[4 * q], w.r[4 * q + 1], w.r[4 * q + 2], w.r[4 * q + 3]);
+}
+// Removes every occurrence of v among the first m entries; returns the count.
+__device__ __forceinline__ int row_remove(Row& w, int m, int v) {
+  Row o;
+  int n = 0;
+#pragma unroll
+  for (int a = 0; a < CG_RING; ++a) o.r[a] = -1;
+#pragma unroll
+  for (int a = 0; a < CG_RING; ++a) {
+    const bool keep = a < m && w.r[a] != v;
+#pragma unroll
+    for (int b = 0; b <= a; ++b)
+      if (keep && n == b) o.r[b] = w.r[a];
+    n += keep;
+  }
+  w = o;
+  return n;
+}
+// Inserts v after the last occurrence of `after` among the first m entries
+// (at the front if absent); returns the new count.
+__device__ __forceinline__ int row_insert(Row& w, int m, int after, int v) {
+  int p = -1;
+#pragma unroll
+  for (int a = 0; a < CG_RING; ++a)
+    if (a < m && w.r[a] == after) p = a;
+  Row o;
+#pragma unroll
+  for (int a = 0; a < CG_RING; ++a) {
+    const int prev = a > 0 ? w.r[a - 1] : -1;
+    o.r[a] = (a <= p) ? w.r[a] : (a == p + 1) ? v : (a <= m) ? prev : w.r[a];
+  }
+  w = o;
+  return m + 1;
+}
+
 __device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd) {
   Ctl* ctl = g.ctl;
   const size_t V = (size_t)g.V;
@@ -366,28 +456,48 @@ __device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd) {
   double* hy = g.hy + ctl->cur * V;
   const int e = 3 * v1 + a;
   const int i = cd.x, j = cd.y, k = cd.z, l = cd.w;
+  // independent loads first: the lists of v1 and of the four cells
   const int v2 = g.vn[e];
   const int Aul = g.vn[3 * v1 + (a + 1) % 3], All = g.vn[3 * v1 + (a + 2) % 3];
-  const int b = slot3(g.vn, v2, v1);
-  if (b < 0 || g.vc[3 * v2 + b] != k || g.vc[3 * v2 + (b + 1) % 3] != i) {
+  const bool distinct = i != j && i != k && i != l && j != k && j != l && k != l;
+  Row ri, rk, rj, rl;
+  int mi = 0, mk = 0, mj = 0, ml = 0;
+  if (distinct) {
+    ri = load_row(g.cv, i); rk = load_row(g.cv, k); rj = load_row(g.cv, j); rl = load_row(g.cv, l);
+    mi = g.cc[i]; mk = g.cc[k]; mj = g.cc[j]; ml = g.cc[l];
+  }
+  int n2[3], c2[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    n2[t] = g.vn[3 * v2 + t];
+    c2[t] = g.vc[3 * v2 + t];
+  }
+  const double x1 = hx[v1], y1 = hy[v1], x2 = hx[v2], y2 = hy[v2];
+  int b = -1;
+#pragma unroll
+  for (int t = 2; t >= 0; --t)
+    if (n2[t] == v1) b = t;
+  if (b < 0 || c2[b] != k || c2[(b + 1) % 3] != i) {
     raise_status(ctl, kETOPO);
     return;
   }
-  const int Alr = g.vn[3 * v2 + (b + 1) % 3], Aur = g.vn[3 * v2 + (b + 2) % 3];
+  const int Alr = n2[(b + 1) % 3], Aur = n2[(b + 2) % 3];
   const int su = slot3(g.vn, Aul, v1), sl = slot3(g.vn, Alr, v2);
   if (su < 0 || sl < 0) {
     raise_status(ctl, kETOPO);
     return;
   }
   // rotate the edge by 90 degrees about its midpoint, new length t1_len
-  const double ex = mimg_d(hx[v2] - hx[v1], g.Lx), ey = mimg_d(hy[v2] - hy[v1], g.Ly);
-  const double mx = hx[v1] + 0.5 * ex, my = hy[v1] + 0.5 * ey;
+  const double ex = mimg_a(x2 - x1, g.ax), ey = mimg_a(y2 - y1, g.ay);
+  const double mx = x1 + 0.5 * ex, my = y1 + 0.5 * ey;
   const double len = sqrt(ex * ex + ey * ey);
   const double px = -ey / len * 0.5 * g.t1_len, py = ex / len * 0.5 * g.t1_len;
-  hx[v1] = wrap_d(mx - px, g.Lx);
-  hy[v1] = wrap_d(my - py, g.Ly);
-  hx[v2] = wrap_d(mx + px, g.Lx);
-  hy[v2] = wrap_d(my + py, g.Ly);
+  const double nx1 = wrap_a(mx - px, g.ax), ny1 = wrap_a(my - py, g.ay);
+  const double nx2 = wrap_a(mx + px, g.ax), ny2 = wrap_a(my + py, g.ay);
+  hx[v1] = nx1; hy[v1] = ny1;
+  hx[v2] = nx2; hy[v2] = ny2;
+  g.hf[v1] = make_float2((float)nx1, (float)ny1);
+  g.hf[v2] = make_float2((float)nx2, (float)ny2);
   // neighbour exchange (Fig. 1): v1 -> cells (j, i, l), v2 -> cells (k, j, l)
   g.vc[3 * v1 + 0] = j; g.vc[3 * v1 + 1] = i; g.vc[3 * v1 + 2] = l;
   g.vn[3 * v1 + 0] = All; g.vn[3 * v1 + 1] = Alr; g.vn[3 * v1 + 2] = v2;
@@ -395,31 +505,37 @@ __device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd) {
   g.vn[3 * v2 + 0] = Aul; g.vn[3 * v2 + 1] = v1; g.vn[3 * v2 + 2] = Aur;
   g.vn[3 * Aul + su] = v2;
   g.vn[3 * Alr + sl] = v1;
-  remove_from_cell(g.cc, g.cv, i, v2);
-  remove_from_cell(g.cc, g.cv, k, v1);
-  insert_in_cell(g.cc, g.cv, j, v1, v2);
-  insert_in_cell(g.cc, g.cv, l, v2, v1);
+  if (distinct) {
+    g.cc[i] = row_remove(ri, mi, v2);
+    g.cc[k] = row_remove(rk, mk, v1);
+    g.cc[j] = row_insert(rj, mj, v1, v2);
+    g.cc[l] = row_insert(rl, ml, v2, v1);
+    store_row(g.cv, i, ri); store_row(g.cv, k, rk); store_row(g.cv, j, rj); store_row(g.cv, l, rl);
+  } else {  // a degenerate network: the edits in order, in memory
+    remove_from_cell(g.cc, g.cv, i, v2);
+    remove_from_cell(g.cc, g.cv, k, v1);
+    insert_in_cell(g.cc, g.cv, j, v1, v2);
+    insert_in_cell(g.cc, g.cv, l, v2, v1);
+  }
   atomicAdd((unsigned long long*)&ctl->repaired_total, 1ull);
 }
 
-// Applies the candidates that hold all four locks (passes 0 .. t1_cap-1; pass
-// t1_cap only counts).  The last block closes the pass: another pass runs
-// while this one proposed something and the cap is not reached; candidates
-// at the counting pass raise the T1-cap status.
+// Applies the listed candidates that hold all four locks (passes 0 ..
+// t1_cap-1; pass t1_cap only counts).  The last block closes the pass:
+// another pass runs while this one proposed something and the cap is not
+// reached; candidates at the counting pass raise the T1-cap status.
 __global__ void k_t1_apply(AvmArgs g) {
   Ctl* ctl = g.ctl;
-  const int v1 = blockIdx.x * blockDim.x + threadIdx.x;
   const int pass = ctl->last_flagged;
   const int proposed = *(volatile int*)&ctl->count[1];
-  if (proposed > 0 && pass < g.t1_cap && v1 < g.V) {
+  if (pass < g.t1_cap) {
     const int stamp = ctl->round_count;
-    for (int a = 0; a < 3; ++a) {
-      const int e = 3 * v1 + a;
-      const int4 cd = g.cand[e];
-      if (cd.x < 0) continue;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < proposed; t += gridDim.x * blockDim.x) {
+      const int e = g.cand_e[t];
+      const int4 cd = g.cand[t];
       const unsigned long long key = lock_key(stamp, e);
       if (g.lock[cd.x] != key || g.lock[cd.y] != key || g.lock[cd.z] != key || g.lock[cd.w] != key) continue;
-      apply_t1(g, v1, a, cd);
+      apply_t1(g, e / 3, e % 3, cd);
     }
   }
   if (last_block(g.done + 1) && threadIdx.x == 0) {
@@ -427,8 +543,19 @@ __global__ void k_t1_apply(AvmArgs g) {
     ctl->round_count += 1;
     ctl->last_flagged = pass + 1;
     if (pass >= g.t1_cap && proposed > 0) atomicCAS(&ctl->status, 0, (int)kET1CAP);
-    if (proposed > 0 && pass < g.t1_cap && ctl->status == 0) cudaGraphSetConditional(g.loop, 1);
+    const int more = proposed > 0 && pass < g.t1_cap && ctl->status == 0;
+    ctl->pad = more;  // read by the host when the passes run outside a graph
+    if (more && g.loop) cudaGraphSetConditional(g.loop, 1);
   }
+}
+
+// Float copies of the current positions (after the network or the positions
+// were replaced from outside).
+__global__ void k_avm_shadow(AvmArgs g) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= g.V) return;
+  const size_t off = (size_t)g.ctl->cur * g.V;
+  g.hf[v] = make_float2((float)g.hx[off + v], (float)g.hy[off + v]);
 }
 
 // Index ranges of a network handed in from outside: vc in [0, n), vn in
@@ -463,16 +590,19 @@ __global__ void k_fill_u64(int n, unsigned long long v, unsigned long long* out)
 constexpr int kAvmThreads = 128;
 static inline int blocks_of(int n) { return (n + kAvmThreads - 1) / kAvmThreads; }
 
-void launch_avm_move(const AvmArgs& a, cudaStream_t st) {
+void launch_avm_move(const AvmArgs& a, cudaStream_t st, int part) {
   AvmArgs m = a;
   m.move = 1;
-  k_avm_cells<<<blocks_of(a.n), kAvmThreads, 0, st>>>(m);
-  k_avm_force_move<<<blocks_of(a.V), kAvmThreads, 0, st>>>(m);
+  if (part != 2) k_avm_cells<<<blocks_of(a.n), kAvmThreads, 0, st>>>(m);
+  if (part != 1) k_avm_force_move<<<blocks_of(a.V), kAvmThreads, 0, st>>>(m);
 }
 void launch_avm_begin_t1(Ctl* ctl, cudaStream_t st) { k_avm_begin_t1<<<1, 1, 0, st>>>(ctl); }
 void launch_avm_t1_pass(const AvmArgs& a, cudaStream_t st) {
   k_t1_propose<<<blocks_of(a.V), kAvmThreads, 0, st>>>(a);
-  k_t1_apply<<<blocks_of(a.V), kAvmThreads, 0, st>>>(a);
+  k_t1_apply<<<a.apply_blocks, kAvmThreads, 0, st>>>(a);
+}
+void launch_avm_shadow(const AvmArgs& a, cudaStream_t st) {
+  k_avm_shadow<<<blocks_of(a.V), kAvmThreads, 0, st>>>(a);
 }
 void launch_avm_forces(const AvmArgs& a, cudaStream_t st) {
   AvmArgs f = a;

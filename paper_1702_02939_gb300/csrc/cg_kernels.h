@@ -177,10 +177,17 @@ struct AvmBuildArgs {
   int *vc, *vn, *cc, *cv;
   double *hx, *hy;         // first position buffer
 };
+// One periodic axis: the length and the bit patterns of L and L/2.
+struct Axis {
+  double L;
+  unsigned long long L_bits, half_bits;
+};
 struct AvmArgs {
   int n, V;
   Ctl* ctl;
   double Lx, Ly;
+  Axis ax, ay;
+  float Lxf, Lyf;           // lengths for the FP32 T1 filter
   double *hx, *hy;         // [2][V]
   int *vc, *vn, *cc, *cv;
   double* theta;
@@ -192,18 +199,23 @@ struct AvmArgs {
   double *Fx, *Fy;
   int move;
   double thr2, t1_len;
-  int t1_cap;
+  float t2lo, t2hi;          // FP32 squared lengths certainly below / above thr2
+  float2* hf;                // [V] float copies of the current positions
+  int t1_cap, apply_blocks;
   unsigned long long* lock;  // [n] pass-stamped T1 locks
-  int4* cand;                // [3V] proposed transitions (cells i, j, k, l)
+  int* cand_e;               // [3V/2] proposed edges (ids), compacted
+  int4* cand;                // [3V/2] their cells (i, j, k, l)
   unsigned int* done;        // [2] last-block counters (force/move, T1 apply)
   cudaGraphConditionalHandle loop;  // while-node handle of the T1 passes
 };
 void launch_avm_build(const AvmBuildArgs& a, cudaStream_t st);
-void launch_avm_move(const AvmArgs& a, cudaStream_t st);
+// part: 0 both kernels, 1 the per-cell kernel only, 2 the per-vertex kernel only
+void launch_avm_move(const AvmArgs& a, cudaStream_t st, int part = 0);
 void launch_avm_begin_t1(Ctl* ctl, cudaStream_t st);
 void launch_avm_t1_pass(const AvmArgs& a, cudaStream_t st);
 void launch_avm_forces(const AvmArgs& a, cudaStream_t st);
 void launch_avm_validate(const AvmArgs& a, cudaStream_t st);
+void launch_avm_shadow(const AvmArgs& a, cudaStream_t st);
 void launch_fill_d(int n, double v, double* out, cudaStream_t st);
 void launch_fill_u64(int n, unsigned long long v, unsigned long long* out, cudaStream_t st);
 

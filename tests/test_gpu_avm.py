@@ -137,6 +137,43 @@ def test_t1_passes_match_oracle(thr):
     sim.close()
 
 
+def edge_lengths(net):
+    """(v, w, |h_w - h_v|) for every edge v < w, the squared length rounded as
+    the T1 rule states (each product and the sum on its own)."""
+    vn = net.vn.reshape(-1, 3)
+    out = []
+    for v in range(net.V):
+        for s in range(3):
+            w = int(vn[v, s])
+            if w <= v:
+                continue
+            dx = (net.hx[w] - net.hx[v] + net.Lx / 2) % net.Lx - net.Lx / 2
+            dy = (net.hy[w] - net.hy[v] + net.Ly / 2) % net.Ly - net.Ly / 2
+            out.append((v, w, np.sqrt(dx * dx + dy * dy)))
+    return out
+
+
+@pytest.mark.parametrize("side", [-1, +1])
+def test_t1_threshold_at_an_edge_length(side):
+    """Thresholds one ulp either side of existing edge lengths put those edges
+    inside the band where the FP32 length filter defers to FP64: the decisions
+    and the resulting networks must still equal the oracle's."""
+    n = 2000
+    xs, ys, th, Lr, Lx, Ly = seeds(n, 14)
+    net = oracle.avm_build(xs, ys, Lx, Ly)
+    lengths = sorted(l for _, _, l in edge_lengths(net) if 0.05 < l < 0.12)
+    for l in lengths[:: max(1, len(lengths) // 3)][:3]:
+        thr = float(np.nextafter(l, np.inf if side > 0 else 0.0))
+        sim = cg.AVM(n, Lr, Lr, xs, ys, th, t1_threshold=thr)
+        load(sim, net)
+        o, k = oracle.avm_t1(net, thr)
+        sim.t1()
+        g, _ = gpu_net(sim, Lx, Ly)
+        assert_same_network(g, o)
+        assert sim.counters()["t1_total"] == k
+        sim.close()
+
+
 def test_t1_cap_status():
     """Candidates left after t1_cap passes raise the T1-cap status on the host."""
     n = 2000
@@ -169,6 +206,25 @@ def test_steps_match_oracle(n, iseed, thr, steps):
     c = sim.counters()
     assert c["steps"] == steps and c["t1_total"] == total
     sim.close()
+
+
+def test_profiled_steps_equal_graph_steps():
+    """The eagerly launched, host-controlled steps of the profiler advance the
+    state bit-identically to the graph steps with the conditional T1 loop."""
+    n = 2000
+    a, xs, ys, th, Lx, Ly = make(n, 13, t1_threshold=0.1, seed=5)
+    b, *_ = make(n, 13, t1_threshold=0.1, seed=5)
+    a.step(6)
+    ph = b.profile(6)
+    assert ph["t1_passes"] >= 6
+    ga, tha = gpu_net(a, Lx, Ly)
+    gb, thb = gpu_net(b, Lx, Ly)
+    for f in ("hx", "hy", "vc", "vn", "cc", "cv"):
+        np.testing.assert_array_equal(getattr(ga, f), getattr(gb, f))
+    np.testing.assert_array_equal(tha, thb)
+    assert a.counters() == b.counters()
+    a.close()
+    b.close()
 
 
 def check_network_valid(sim, Lx, Ly, p0):
@@ -224,3 +280,33 @@ def test_full_size_workload():
     sim.step(50)
     check_network_valid(sim, Lx, Ly, p0)
     sim.close()
+
+
+def test_long_run_ensemble_statistics_match_oracle():
+    """Long AVM runs (N = 400, p0 = 3.8, v0 = 0.1, T1 threshold 0.04, 1000
+    steps, eight seeds): the ensemble mean shape index agrees within 1% and
+    the vertex mean-squared displacement within its seed-to-seed standard
+    error."""
+    n, K, p0, v0, thr = 400, 1000, 3.8, 0.1, 0.04
+    qg, qo, mg, mo = [], [], [], []
+    for s in range(8):
+        sim, xs, ys, th, Lx, Ly = make(n, 200 + s, p0=p0, v0=v0, t1_threshold=thr, seed=s)
+        net = oracle.avm_build(xs, ys, Lx, Ly)
+        load(sim, net, th)
+        sim.step(K)
+        g, _ = gpu_net(sim, Lx, Ly)
+        A, P = (t.cpu().numpy() for t in sim.geometry())
+        sim.close()
+        o, oth = net, th
+        for k in range(K):
+            o, oth, _ = oracle.avm_step(o, oth, p0, v0, seed=s, step=k, thr=thr)
+        _, _, oA, oP, _ = oracle.avm_forces(o, p0)
+        qg.append((P / np.sqrt(A)).mean())
+        qo.append((oP / np.sqrt(oA)).mean())
+        mg.append((wrapdiff(g.hx, net.hx, Lx) ** 2 + wrapdiff(g.hy, net.hy, Ly) ** 2).mean())
+        mo.append((wrapdiff(o.hx, net.hx, Lx) ** 2 + wrapdiff(o.hy, net.hy, Ly) ** 2).mean())
+    qg, qo, mg, mo = (np.asarray(v) for v in (qg, qo, mg, mo))
+    se = max(mg.std(ddof=1), mo.std(ddof=1)) / np.sqrt(len(mg))
+    print(f"q: gpu {qg.mean():.6f} oracle {qo.mean():.6f}; MSD: gpu {mg.mean():.6f} oracle {mo.mean():.6f} se {se:.2e}")
+    assert abs(qg.mean() - qo.mean()) <= 0.01 * qo.mean()
+    assert abs(mg.mean() - mo.mean()) <= se

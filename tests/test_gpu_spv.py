@@ -260,3 +260,36 @@ def test_large_force_move_wraps_and_repairs():
     assert np.abs(wrapdiff(gy, oy, Ly)).max() <= 1e-9 * Ly
     check_topology(sim, gx, gy, Lx, Ly)
     sim.close()
+
+
+def ensemble(values):
+    v = np.asarray(values, np.float64)
+    return v.mean(), v.std(ddof=1) / np.sqrt(len(v))
+
+
+def test_long_run_ensemble_statistics_match_oracle():
+    """Long runs (N = 400, p0 = 3.85, v0 = 0.1, 600 steps of dt = 0.01, eight
+    seeds): the ensemble mean shape index q = P / sqrt(A) agrees within 1% and
+    the mean-squared displacement within its seed-to-seed standard error.
+    Trajectories are compared only through these statistics."""
+    n, K, p0, v0 = 400, 600, 3.85, 0.1
+    qg, qo, mg, mo = [], [], [], []
+    for s in range(8):
+        sim, xs, ys, th, Lx, Ly = make(n, 100 + s, p0=p0, v0=v0, seed=s, dt=0.01)
+        sim.step(K)
+        gx, gy, _ = (t.cpu().numpy() for t in sim.state())
+        A, P = (t.cpu().numpy() for t in sim.geometry())
+        sim.close()
+        ox, oy, _, _ = oracle.spv_run(xs, ys, th, Lx, Ly, p0, v0, K, seed=s, dt=0.01)
+        oA, oP, _, _ = oracle.geometry(ox, oy, Lx, Ly, oracle.triangulate(ox, oy, Lx, Ly))
+        qg.append((P / np.sqrt(A)).mean())
+        qo.append((oP / np.sqrt(oA)).mean())
+        mg.append((wrapdiff(gx, xs, Lx) ** 2 + wrapdiff(gy, ys, Ly) ** 2).mean())
+        mo.append((wrapdiff(ox, xs, Lx) ** 2 + wrapdiff(oy, ys, Ly) ** 2).mean())
+    Qg, _ = ensemble(qg)
+    Qo, _ = ensemble(qo)
+    Mg, seg = ensemble(mg)
+    Mo, seo = ensemble(mo)
+    print(f"q: gpu {Qg:.6f} oracle {Qo:.6f}; MSD: gpu {Mg:.6f} +- {seg:.2e} oracle {Mo:.6f} +- {seo:.2e}")
+    assert abs(Qg - Qo) <= 0.01 * Qo
+    assert abs(Mg - Mo) <= max(seg, seo)
