@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--avm-steps", type=int, default=500)
     ap.add_argument("--avm-warmup", type=int, default=100)
     ap.add_argument("--avm-profile-steps", type=int, default=20)
+    ap.add_argument("--eager", action="store_true",
+                    help="launch every kernel of the step eagerly instead of replaying the step graph "
+                         "(same kernels and results; for kernel-level profilers)")
     ap.add_argument("--avm-only", action="store_true",
                     help="run only the AVM section and print its JSON object (a diagnostic, not the bench line)")
     return ap.parse_args()
@@ -145,10 +148,10 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def kernels_per_step(repair_cap):
-    # geometry, force+move, begin-topology, test, 4 cell-list kernels,
-    # repair_cap x (repair + check)
-    return 4 + 4 + 2 * repair_cap
+def kernels_launched(steps, loop_iterations):
+    # per step: geometry, force+move, begin-topology, test, 4 cell-list
+    # kernels; per iteration of the repair-round loop node: repair + check
+    return 8 * steps + 2 * loop_iterations
 
 
 def cpu_baseline(x, y, th, L, seconds):
@@ -303,6 +306,7 @@ def avm_throughput(args, device):
     sim.sync()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     c1 = sim.counters()
+    launches = 2 * K + 2 * (c1["loop_total"] - c0["loop_total"])
     prof_steps = max(1, args.avm_profile_steps)
     ph = sim.profile(prof_steps)
     # oracle on the same kind of state (its own network build), a few steps
@@ -323,6 +327,7 @@ def avm_throughput(args, device):
             "vertex_steps_per_s": V * K / (ms * 1e-3) if K else None,
             "cell_steps_per_s": n * K / (ms * 1e-3) if K else None,
             "ms_per_step": ms / Kd if K else None, "steps": K, "warmup": args.avm_warmup, "l2": "flushed between timed steps",
+            "gpu_launches": launches,
             "t1_per_step": (c1["t1_total"] - c0["t1_total"]) / Kd,
             "t1_passes_per_step": (c1["t1_passes"] - c0["t1_passes"]) / Kd,
             "phase_ms_per_step": {"cells": ph["cells_ms"] / prof_steps, "vertices": ph["vertices_ms"] / prof_steps,
@@ -406,13 +411,15 @@ def run_ours(args):
     sim = cg.SPV([dict(n=args.n, Lx=L, Ly=L, p0=P0, v0=V0)], x, y, th, dt=DT, seed=1 + rank,
                  repair_cap=repair_cap, device=f"cuda:{local}")
     stream = torch.cuda.current_stream()
+    advance = sim.profile if args.eager else sim.step
     # warm-up = equilibration steps
-    sim.step(args.warmup)
+    advance(args.warmup)
     sim.sync()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
+    loops0 = sim.counters()["loop_total"]
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -421,7 +428,7 @@ def run_ours(args):
     for k in range(args.steps):
         flush.zero_()  # L2 flush (256 MB > 129 MB L2) between timed steps
         ev_s[k].record(stream)
-        sim.step(1)
+        advance(1)
         ev_e[k].record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -490,9 +497,10 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n_cells": args.n, "box": L, "p0": P0, "v0": V0, "dt": DT,
                            "replicas_per_gpu": 1, "l2": "flushed between timed steps (256 MB write)",
-                           "repair_cap": repair_cap},
+                           "repair_cap": repair_cap, "launch": "eager" if args.eager else "graph"},
                 "clocks": clk, "e2e": e2e,
-                "gpu_launches": kernels_per_step(repair_cap) * args.steps,
+                "gpu_launches": (kernels_launched(args.steps, args.steps * repair_cap) if args.eager
+                                 else kernels_launched(args.steps, counters["loop_total"] - loops0)),
                 "roofline": roofline, "hbm_roofline": hbm, "cpu_baseline": cpu,
                 "phase_ms_per_step": {k: v / prof_steps for k, v in ph.items()},
                 "counters": counters, "batched": batched, "backward": backward, "avm": avm}

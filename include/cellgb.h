@@ -95,6 +95,8 @@ typedef struct cg_counters {
   int32_t last_rounds;     /* repair rounds in the last step */
   int32_t status;          /* device status word */
   int32_t reserved;
+  int64_t loop_total;      /* iterations of the step graph's loop node (repair
+                              rounds; T1 passes for the AVM) since creation */
 } cg_counters;
 
 /* Workspace size for R replicas. */

@@ -53,7 +53,7 @@ class cg_avm_params(C.Structure):
 class cg_counters(C.Structure):
     _fields_ = [("steps", C.c_int64), ("flagged_total", C.c_int64), ("repaired_total", C.c_int64),
                 ("last_flagged", C.c_int32), ("last_rounds", C.c_int32), ("status", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("loop_total", C.c_int64)]
 
 
 def lib():
@@ -508,7 +508,8 @@ def cg_avm_set_v0(ctx, v0):
 def cg_avm_get_counters(ctx):
     c = cg_counters()
     _check_avm(lib().cg_avm_get_counters(ctx, C.byref(c)), ctx)
-    return {"steps": c.steps, "t1_total": c.repaired_total, "t1_passes": c.last_rounds, "status": c.status}
+    return {"steps": c.steps, "t1_total": c.repaired_total, "t1_passes": c.last_rounds, "status": c.status,
+            "loop_total": c.loop_total}
 
 
 def cg_avm_destroy(ctx):

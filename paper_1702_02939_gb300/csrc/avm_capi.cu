@@ -2,6 +2,7 @@
 #include "../../include/cellgb.h"
 #include "cg_device.cuh"
 #include "cg_kernels.h"
+#include "cg_graph.h"
 
 #include <algorithm>
 #include <cmath>
@@ -196,58 +197,29 @@ int avm_status(cg_avm_ctx* c) {
 }
 
 // A graph of `prefix` (captured) followed by a while node whose body is one
-// T1 pass; the loop handle starts at 1 on every launch, the pass's first
-// kernel sets it to 0 and its closing block back to 1 when another pass is due.
+// T1 pass (the pass's first kernel clears the handle, its closing block sets
+// it again when another pass is due).
 template <class Prefix>
 int loop_graph(cg_avm_ctx* c, Prefix prefix, cudaGraphExec_t* out) {
   if (*out) {
     cudaGraphExecDestroy(*out);
     *out = nullptr;
   }
-  cudaGraph_t g = nullptr;
-  AV_CUDA(c, cudaGraphCreate(&g, 0));
-  int rc = CG_OK;
-  do {
-    cudaGraphConditionalHandle h;
-    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) { rc = CG_ECUDA; break; }
-    AvmArgs a = avm_args(c);
-    a.loop = h;
-    if (cudaStreamBeginCaptureToGraph(c->capture, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
-        cudaSuccess) { rc = CG_ECUDA; break; }
-    prefix(a, c->capture);
-    cudaGraph_t captured = g;
-    if (cudaStreamEndCapture(c->capture, &captured) != cudaSuccess) { rc = CG_ECUDA; break; }
-    // the captured prefix is a chain: its one node without dependents
-    size_t nn = 0;
-    cudaGraphGetNodes(g, nullptr, &nn);
-    std::vector<cudaGraphNode_t> nodes(nn);
-    cudaGraphGetNodes(g, nodes.data(), &nn);
-    cudaGraphNode_t leaf = nullptr;
-    for (cudaGraphNode_t node : nodes) {
-      size_t nd = 0;
-      cudaGraphNodeGetDependentNodes(node, nullptr, nullptr, &nd);
-      if (nd == 0) leaf = node;
-    }
-    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
-    p.conditional.handle = h;
-    p.conditional.type = cudaGraphCondTypeWhile;
-    p.conditional.size = 1;
-    cudaGraphNode_t loop;
-    if (cudaGraphAddNode(&loop, g, leaf ? &leaf : nullptr, nullptr, leaf ? 1 : 0, &p) != cudaSuccess) {
-      rc = CG_ECUDA;
-      break;
-    }
-    cudaGraph_t body = p.conditional.phGraph_out[0];
-    if (cudaStreamBeginCaptureToGraph(c->capture, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
-        cudaSuccess) { rc = CG_ECUDA; break; }
-    launch_avm_t1_pass(a, c->capture);
-    if (cudaStreamEndCapture(c->capture, &body) != cudaSuccess) { rc = CG_ECUDA; break; }
-    if (cudaGraphInstantiate(out, g, 0) != cudaSuccess) { rc = CG_ECUDA; break; }
-  } while (0);
-  cudaGraphDestroy(g);
-  if (rc) {
+  AvmArgs a = avm_args(c);
+  cudaError_t e = build_loop_graph(
+      c->capture,
+      [&](cudaGraphConditionalHandle h, cudaStream_t st) {
+        a.loop = h;
+        prefix(a, st);
+      },
+      [&](cudaGraphConditionalHandle h, cudaStream_t st) {
+        a.loop = h;
+        launch_avm_t1_pass(a, st);
+      },
+      out);
+  if (e != cudaSuccess) {
     cudaGetLastError();
-    return afail(c, rc, "building the T1 loop graph failed");
+    return afail(c, CG_ECUDA, std::string("building the T1 loop graph: ") + cudaGetErrorString(e));
   }
   return CG_OK;
 }
@@ -524,6 +496,7 @@ int cg_avm_get_counters(cg_avm_ctx* c, cg_counters* out) {
   out->last_rounds = h.round_count;        // T1 passes
   out->status = h.status;
   out->reserved = 0;
+  out->loop_total = h.loop_total;
   return CG_OK;
 }
 

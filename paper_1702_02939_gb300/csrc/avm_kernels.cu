@@ -152,23 +152,6 @@ void launch_avm_build(const AvmBuildArgs& a, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // Step kernels.
 // ---------------------------------------------------------------------------
-// True in exactly one block of the grid: the last one to get here.  Every
-// thread of every block must call it; each block's global writes are fenced
-// before it counts itself, and the last block fences again before reading.
-// The last block resets the counter for the next launch.
-__device__ __forceinline__ bool last_block(unsigned int* done) {
-  __shared__ bool s_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(done, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    if (threadIdx.x == 0) *done = 0u;
-  }
-  return s_last;
-}
-
 // Per cell: area and perimeter of the polygon, the force coefficients
 // ka = 2 K_A (A - A0) and kp = 2 K_P (P - P0), and, when stepping, the
 // self-propulsion v0 n(theta) of the current director followed by the
@@ -541,6 +524,7 @@ __global__ void k_t1_apply(AvmArgs g) {
   if (last_block(g.done + 1) && threadIdx.x == 0) {
     ctl->count[1] = 0;
     ctl->round_count += 1;
+    ctl->loop_total += 1;
     ctl->last_flagged = pass + 1;
     if (pass >= g.t1_cap && proposed > 0) atomicCAS(&ctl->status, 0, (int)kET1CAP);
     const int more = proposed > 0 && pass < g.t1_cap && ctl->status == 0;

@@ -2,6 +2,7 @@
 #include "../../include/cellgb.h"
 #include "cg_device.cuh"
 #include "cg_kernels.h"
+#include "cg_graph.h"
 
 #include <algorithm>
 #include <cmath>
@@ -305,6 +306,9 @@ RepairArgs repair_args(cg_ctx* c, int which_in, int all_cells) {
   r.list_in = c->at<int>(which_in ? c->off.list1 : c->off.list0);
   r.which_in = which_in;
   r.all_cells = all_cells;
+  r.dyn = 0;
+  r.lists[0] = r.lists[1] = nullptr;
+  r.loop = 0;
   return r;
 }
 
@@ -323,6 +327,10 @@ CheckArgs check_args(cg_ctx* c, int which_in, int last_round, int all_cells) {
   k.which_out = which_in ^ 1;
   k.last_round = last_round;
   k.all_cells = all_cells;
+  k.dyn = 0;
+  k.cap = 0;
+  k.lists[0] = k.lists[1] = nullptr;
+  k.loop = 0;
   return k;
 }
 
@@ -374,19 +382,32 @@ int repair_grid_all(const cg_ctx*) { return sm_count() * 16; }
 int check_grid_all(const cg_ctx* c) { return (int)((c->N + 255) / 256); }
 
 // One time step, enqueued on stream st (also used for capture).
-void enqueue_step(cg_ctx* c, cudaStream_t st) {
+// One step up to the repair rounds: geometry, forces and move, circumcircle
+// test, cell list.
+void enqueue_step_prefix(cg_ctx* c, cudaStream_t st) {
   launch_geom(geom_args(c), st);
   launch_force(force_args(c, 1), st);
   launch_begin_topology(c->ctl(), 1, st);
   launch_test(test_args(c), st);
   launch_cell_list(cell_list_args(c, 1), st);
-  const int cap = c->par.repair_cap > 0 ? c->par.repair_cap : 4;
-  const int grid = repair_grid(c);
-  for (int r = 0; r < cap; ++r) {
-    const int which = r & 1;
-    launch_repair(repair_args(c, which, 0), grid, st);
-    launch_check(check_args(c, which, r == cap - 1, 0), check_grid(c), st);
-  }
+}
+
+// One repair round (repair + consistency check) for a conditional loop node:
+// the round counter in the control word picks the lists.
+void enqueue_repair_round(cg_ctx* c, cudaGraphConditionalHandle h, cudaStream_t st) {
+  RepairArgs r = repair_args(c, 0, 0);
+  r.dyn = 1;
+  r.lists[0] = c->at<int>(c->off.list0);
+  r.lists[1] = c->at<int>(c->off.list1);
+  r.loop = h;
+  CheckArgs k = check_args(c, 0, 0, 0);
+  k.dyn = 1;
+  k.cap = c->par.repair_cap > 0 ? c->par.repair_cap : 4;
+  k.lists[0] = c->at<int>(c->off.list0);
+  k.lists[1] = c->at<int>(c->off.list1);
+  k.loop = h;
+  launch_repair(r, repair_grid(c), st);
+  launch_check(k, check_grid(c), st);
 }
 
 // Full triangulation of the current positions (every cell repaired).
@@ -435,16 +456,18 @@ int load_positions(cg_ctx* c, const double* x, const double* y) {
   return CG_OK;
 }
 
+// One step as a graph: the prefix, then the repair rounds as a conditional
+// while node that stops at the first round leaving no cell flagged.
 int build_graph(cg_ctx* c) {
   if (c->step_exec) return CG_OK;
-  cudaGraph_t graph;
-  CG_CUDA(c, cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
-  enqueue_step(c, c->capture);
-  cudaError_t e = cudaStreamEndCapture(c->capture, &graph);
-  if (e != cudaSuccess) return fail(c, CG_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&c->step_exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return fail(c, CG_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+  cudaError_t e = build_loop_graph(
+      c->capture, [&](cudaGraphConditionalHandle, cudaStream_t st) { enqueue_step_prefix(c, st); },
+      [&](cudaGraphConditionalHandle h, cudaStream_t st) { enqueue_repair_round(c, h, st); }, &c->step_exec);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->step_exec = nullptr;
+    return fail(c, CG_ECUDA, std::string("step graph: ") + cudaGetErrorString(e));
+  }
   return CG_OK;
 }
 
@@ -808,6 +831,7 @@ int cg_get_counters(cg_ctx* c, cg_counters* out) {
   out->last_rounds = h.round_count;
   out->status = h.status;
   out->reserved = 0;
+  out->loop_total = h.loop_total;
   return CG_OK;
 }
 

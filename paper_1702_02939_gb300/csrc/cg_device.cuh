@@ -73,7 +73,27 @@ struct Ctl {
   long long flagged_total, repaired_total;
   int last_flagged;
   int pad;
+  unsigned int done;  // last-block counter of the repair-round check
+  int pad2;
+  long long loop_total;  // iterations of the repair-round (or T1-pass) loop node
 };
+
+// True in exactly one block of the grid: the last one to get here.  Every
+// thread of every block must call it; each block's global writes are fenced
+// before it counts itself, and the last block fences again before reading.
+// The last block resets the counter for the next launch.
+__device__ __forceinline__ bool last_block(unsigned int* done) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(done, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    if (threadIdx.x == 0) *done = 0u;
+  }
+  return s_last;
+}
 
 // Bins per block of the block-local scans; the global start of bin b is the
 // block-local exclusive prefix plus one offset per scan block.

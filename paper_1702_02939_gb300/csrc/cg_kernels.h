@@ -83,6 +83,11 @@ struct RepairArgs {
   const int* list_in;
   int which_in;  // count index of list_in
   int all_cells; // process cells 0..n-1 instead of the list
+  // Rounds inside a conditional (while) graph node: the input list is
+  // lists[round & 1] with the round counter read from the control word.
+  int dyn;
+  const int* lists[2];
+  cudaGraphConditionalHandle loop;
 };
 
 struct CheckArgs {
@@ -95,6 +100,12 @@ struct CheckArgs {
   int which_in, which_out;
   int last_round;  // raise REPAIR_CAP if anything is flagged
   int all_cells;
+  // Rounds inside a conditional (while) graph node (see RepairArgs): the last
+  // block counts the round, raises REPAIR_CAP after `cap` rounds with work
+  // and asks for another round while cells are left flagged.
+  int dyn, cap;
+  int* lists[2];
+  cudaGraphConditionalHandle loop;
 };
 
 void launch_geom(const GeomArgs& a, cudaStream_t st);

@@ -299,21 +299,25 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
   __shared__ int s_val[kRepairWarps][kCand];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gw = blockIdx.x * kRepairWarps + wib, nw = gridDim.x * kRepairWarps;
-  const int total = g.all_cells ? g.n : g.ctl->count[g.which_in];
+  // stop the round loop unless this round's check asks for another
+  if (g.dyn && g.loop && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(g.loop, 0);
+  const int which_in = g.dyn ? (g.ctl->round_count & 1) : g.which_in;
+  const int* list_in = g.dyn ? (which_in ? g.lists[1] : g.lists[0]) : g.list_in;
+  const int total = g.all_cells ? g.n : g.ctl->count[which_in];
   // the list this round's check fills must start empty
-  if (!g.all_cells && blockIdx.x == 0 && threadIdx.x == 0) g.ctl->count[g.which_in ^ 1] = 0;
+  if (!g.all_cells && blockIdx.x == 0 && threadIdx.x == 0) g.ctl->count[which_in ^ 1] = 0;
   if (total == 0) return;
   const int cur = g.ctl->cur;
   const size_t N = (size_t)g.n;
   const long long* __restrict__ X = g.X + cur * N;
   const long long* __restrict__ Y = g.Y + cur * N;
   if (blockIdx.x == 0 && threadIdx.x == 0 && !g.all_cells) {
-    atomicAdd(&g.ctl->round_count, 1);
+    if (!g.dyn) atomicAdd(&g.ctl->round_count, 1);  // counted by the check otherwise
     atomicAdd((unsigned long long*)&g.ctl->repaired_total, (unsigned long long)total);
   }
 
   for (int item = gw; item < total; item += nw) {
-    const int i = g.all_cells ? item : g.list_in[item];
+    const int i = g.all_cells ? item : list_in[item];
     const Rep R = g.reps[g.rep[i]];
     const long long Xi = X[i], Yi = Y[i];
     const int ikey = g.tag[i];
@@ -460,17 +464,21 @@ __device__ __forceinline__ void flag_into(unsigned* flags, int* list, int* count
 }
 
 __global__ void k_check(CheckArgs g) {
-  const int total = g.all_cells ? g.n : g.ctl->count[g.which_in];
-  int* count_out = &g.ctl->count[g.which_out];
+  const int which_in = g.dyn ? (g.ctl->round_count & 1) : g.which_in;
+  const int which_out = which_in ^ 1;
+  const int* list_in = g.dyn ? (which_in ? g.lists[1] : g.lists[0]) : g.list_in;
+  int* list_out = g.dyn ? (which_out ? g.lists[1] : g.lists[0]) : g.list_out;
+  const int total = g.all_cells ? g.n : g.ctl->count[which_in];
+  int* count_out = &g.ctl->count[which_out];
   for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
-    const int i = g.all_cells ? item : g.list_in[item];
+    const int i = g.all_cells ? item : list_in[item];
     const int m = g.cnt[i];
     const int* row = g.nbr + (size_t)i * CG_RING;
     bool bad = false;
     for (int a = 0; a < m; ++a) {
       const int j = row[a];
       if (!in_ring(g.nbr, g.cnt, j, i)) {
-        flag_into(g.flags, g.list_out, count_out, j);
+        flag_into(g.flags, list_out, count_out, j);
         bad = true;
       }
     }
@@ -482,11 +490,23 @@ __global__ void k_check(CheckArgs g) {
       bool kept = false;
       for (int a = 0; a < m; ++a) kept |= (row[a] == j);
       if (!kept && in_ring(g.nbr, g.cnt, j, i)) {
-        flag_into(g.flags, g.list_out, count_out, j);
+        flag_into(g.flags, list_out, count_out, j);
         bad = true;
       }
     }
-    if (bad && g.last_round) raise_status(g.ctl, kEREPAIR_CAP);
+    if (bad && g.last_round && !g.dyn) raise_status(g.ctl, kEREPAIR_CAP);
+  }
+  if (!g.dyn) return;  // uniform over the grid
+  if (last_block(&g.ctl->done) && threadIdx.x == 0) {
+    Ctl* ctl = g.ctl;
+    const int produced = *(volatile int*)count_out;
+    const int r = ctl->round_count + (total > 0 ? 1 : 0);
+    ctl->round_count = r;
+    ctl->loop_total += 1;
+    if (produced > 0) {
+      if (r >= g.cap) atomicCAS(&ctl->status, 0, (int)kEREPAIR_CAP);
+      else if (g.loop) cudaGraphSetConditional(g.loop, 1);
+    }
   }
 }
 

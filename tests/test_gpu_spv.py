@@ -293,3 +293,36 @@ def test_long_run_ensemble_statistics_match_oracle():
     print(f"q: gpu {Qg:.6f} oracle {Qo:.6f}; MSD: gpu {Mg:.6f} +- {seg:.2e} oracle {Mo:.6f} +- {seo:.2e}")
     assert abs(Qg - Qo) <= 0.01 * Qo
     assert abs(Mg - Mo) <= max(seg, seo)
+
+
+def test_profiled_steps_equal_graph_steps():
+    """cg_profile_step (eager launches, repair rounds unrolled to the cap)
+    advances the state bit-identically to the graph step, whose repair rounds
+    run in a conditional loop node that stops at the first clean round."""
+    n = 4096
+    a, xs, ys, th, Lx, Ly = make(n, 31, p0=3.85, v0=0.1, seed=2)
+    b, *_ = make(n, 31, p0=3.85, v0=0.1, seed=2)
+    a.step(25)
+    b.profile(25)
+    for ta, tb in zip(a.state(), b.state()):
+        assert torch.equal(ta, tb)
+    for ta, tb in zip(a.neighbors(), b.neighbors()):
+        assert torch.equal(ta, tb)
+    ca, cb = a.counters(), b.counters()
+    for k in ("steps", "flagged_total", "repaired_total", "status"):
+        assert ca[k] == cb[k]
+    # the loop ran at least one round per step, and at most the cap
+    assert 25 <= ca["loop_total"] <= 25 * 4
+    a.close()
+    b.close()
+
+
+def test_repair_cap_status():
+    """From a random state the first step needs more than one repair round:
+    with repair_cap = 1 the loop stops and the host sees CG_EREPAIR_CAP."""
+    sim, *_ = make(4096, 32, p0=3.85, v0=0.1, repair_cap=1)
+    with pytest.raises(cg.CellgbError) as e:
+        sim.step(1)
+        sim.sync()
+    assert e.value.code == -4
+    sim.close()
