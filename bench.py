@@ -45,9 +45,10 @@ FLOPS_PER_CELL = {"geometry": 342.0, "force_move": 93.0}
 BYTES_PER_CELL_STEP = 84.0
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# Dominant-kernel DRAM traffic per launch from the committed ncu capture
-# (profiles/k_geom_spv_N262144.md); None until captured for the current kernel.
-GEOM_DRAM_BYTES_PER_LAUNCH = None
+# Dominant-kernel DRAM traffic per launch (dram__bytes_read.sum +
+# dram__bytes_write.sum) from the committed ncu capture of the current k_geom
+# (profiles/k_geom_spv_N262144.md); set back to None whenever k_geom changes.
+GEOM_DRAM_BYTES_PER_LAUNCH = 57.98e6
 
 
 def parse():
