@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--avm-steps", type=int, default=500)
     ap.add_argument("--avm-warmup", type=int, default=100)
     ap.add_argument("--avm-profile-steps", type=int, default=20)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel of the step eagerly instead of replaying the step graph "
                          "(same kernels and results; for kernel-level profilers)")
@@ -212,6 +213,7 @@ def batched_comparison(args, device):
                    device=device)
     # equilibration: the random initial state relaxes large forces first
     fused.step(args.batched_warmup)
+    launch, _ = fused.autotune(5) if not args.no_autotune else (fused.launch, None)
     ms_f = timed(lambda: fused.step(1), args.batched_steps)
     fused.sync()
     fused.close()
@@ -229,7 +231,8 @@ def batched_comparison(args, device):
     return {"workload": "spv_batched_R512_N256-16384_loguniform", "replicas": R, "cells": total,
             "fused_cell_steps_per_s": v_f, "per_replica_loop_cell_steps_per_s": v_l, "fused_over_loop": v_f / v_l,
             "fused_ms_per_step": ms_f / args.batched_steps, "loop_ms_per_step": ms_l / steps_loop,
-            "steps": [args.batched_steps, steps_loop], "warmup": args.batched_warmup}
+            "steps": [args.batched_steps, steps_loop], "warmup": args.batched_warmup,
+            "fused_launch_shapes": launch}
 
 
 def backward_cost(args, device):
@@ -413,9 +416,11 @@ def run_ours(args):
                  repair_cap=repair_cap, device=f"cuda:{local}")
     stream = torch.cuda.current_stream()
     advance = sim.profile if args.eager else sim.step
-    # warm-up = equilibration steps
+    # warm-up = equilibration steps; then the launch shapes are tuned on a
+    # temporary copy of the equilibrated state (the simulation takes no step)
     advance(args.warmup)
     sim.sync()
+    launch, tune_ms = (sim.autotune(10) if not args.no_autotune else (sim.launch, None))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -498,7 +503,8 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n_cells": args.n, "box": L, "p0": P0, "v0": V0, "dt": DT,
                            "replicas_per_gpu": 1, "l2": "flushed between timed steps (256 MB write)",
-                           "repair_cap": repair_cap, "launch": "eager" if args.eager else "graph"},
+                           "repair_cap": repair_cap, "launch": "eager" if args.eager else "graph",
+                           "launch_shapes": launch, "autotune_ms_per_step": tune_ms},
                 "clocks": clk, "e2e": e2e,
                 "gpu_launches": (kernels_launched(args.steps, args.steps * repair_cap) if args.eager
                                  else kernels_launched(args.steps, counters["loop_total"] - loops0)),

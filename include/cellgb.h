@@ -99,6 +99,15 @@ typedef struct cg_counters {
                               rounds; T1 passes for the AVM) since creation */
 } cg_counters;
 
+/* Launch shapes of the step graph.  They change timing only: every result
+ * is the same for any valid setting. */
+typedef struct cg_launch {
+  int32_t repair_blocks_per_sm;  /* repair-round grid = SMs x this (1..64, default 4) */
+  int32_t check_blocks_per_sm;   /* consistency-check grid = SMs x this (1..64, default 2) */
+  int32_t dir_blocks_per_sm;     /* director branch grid = SMs x this; 0 = one thread per cell (default) */
+  int32_t dir_low_priority;      /* 1: director branch at the lowest stream priority, the rest at the highest */
+} cg_launch;
+
 /* Workspace size for R replicas. */
 int cg_workspace_bytes(int32_t R, const cg_replica* reps, size_t* bytes);
 
@@ -123,9 +132,11 @@ int cg_step(cg_ctx* ctx, int64_t nsteps);
  * graph), timed with CUDA events on the context's stream.  ms_out[k] receives
  * the summed milliseconds of phase k (n_out >= CG_NUM_PHASES):
  *   0 geometry + force sets, 1 net force + move, 2 circumcircle test,
- *   3 cell-list build, 4 repair rounds (repair + consistency check).
+ *   3 cell-list build, 4 repair rounds (repair + consistency check),
+ *   5 director terms of the next step (n(theta) and the noise; in the step
+ *     graph this runs beside phases 2-4).
  * The steps advance the state exactly like cg_step(). */
-#define CG_NUM_PHASES 5
+#define CG_NUM_PHASES 6
 int cg_profile_step(cg_ctx* ctx, int64_t nsteps, double* ms_out, int32_t n_out);
 
 /* Waits for the stream and returns the device status word. */
@@ -188,6 +199,22 @@ int cg_hvp(cg_ctx* ctx, const double* vx, const double* vy, double* hvx, double*
 
 /* Total cells of the context. */
 int64_t cg_num_cells(const cg_ctx* ctx);
+
+/* ---- Launch shapes and autotuning -------------------------------------- */
+int cg_get_launch(const cg_ctx* ctx, cg_launch* out);
+/* Sets the launch shapes and recaptures the step graph.  Synchronizes. */
+int cg_set_launch(cg_ctx* ctx, const cg_launch* launch);
+/* Scratch needed by cg_autotune: a second workspace plus the saved state. */
+int cg_autotune_bytes(const cg_ctx* ctx, size_t* bytes);
+/* Picks the launch shapes by timing candidates (coordinate descent over the
+ * four fields, two sweeps) on a temporary copy of the context built in d_ws2
+ * (device, >= cg_autotune_bytes, 256-byte aligned) from the current state,
+ * directors, step counter, p0 and v0: each trial restores that state, runs 2
+ * untimed and steps_per_trial timed graph steps (CUDA events).  The context
+ * itself takes no step; it gets the fastest shapes (graph recaptured).
+ * best (may be NULL) receives them, best_ms the time per step.  Synchronizes. */
+int cg_autotune(cg_ctx* ctx, int32_t steps_per_trial, void* d_ws2, size_t ws2_bytes, cg_launch* best,
+                double* best_ms);
 
 /* Allocation-free triangulation, for callers that cannot call cudaMalloc
  * (code running under a fixed device memory pool, inside another runtime's

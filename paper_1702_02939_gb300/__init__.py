@@ -43,6 +43,11 @@ class cg_params(C.Structure):
                 ("repair_cap", C.c_int32), ("sort_every", C.c_int32)]
 
 
+class cg_launch(C.Structure):
+    _fields_ = [("repair_blocks_per_sm", C.c_int32), ("check_blocks_per_sm", C.c_int32),
+                ("dir_blocks_per_sm", C.c_int32), ("dir_low_priority", C.c_int32)]
+
+
 class cg_avm_params(C.Structure):
     _fields_ = [("A0", C.c_double), ("KA", C.c_double), ("KP", C.c_double), ("mu", C.c_double),
                 ("Dr", C.c_double), ("dt", C.c_double), ("t1_threshold", C.c_double),
@@ -100,6 +105,12 @@ def lib():
         for name in ("cg_workspace_bytes", "cg_create", "cg_step", "cg_sync", "cg_profile_step", "cg_get_state", "cg_set_state",
                      "cg_get_geometry", "cg_get_forces", "cg_get_neighbors", "cg_set_p0", "cg_set_v0",
                      "cg_get_counters", "cg_destroy"):
+            getattr(L, name).restype = C.c_int
+        L.cg_get_launch.argtypes = [vp, C.POINTER(cg_launch)]
+        L.cg_set_launch.argtypes = [vp, C.POINTER(cg_launch)]
+        L.cg_autotune_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.cg_autotune.argtypes = [vp, i32, vp, C.c_size_t, C.POINTER(cg_launch), C.POINTER(C.c_double)]
+        for name in ("cg_get_launch", "cg_set_launch", "cg_autotune_bytes", "cg_autotune"):
             getattr(L, name).restype = C.c_int
         # active vertex model
         L.cg_avm_workspace_bytes.argtypes = [i32, C.c_double, C.c_double, C.POINTER(C.c_size_t)]
@@ -173,7 +184,7 @@ def cg_step(ctx, nsteps):
     _check(lib().cg_step(ctx, int(nsteps)), ctx)
 
 
-PHASES = ("geometry", "force_move", "test", "cell_list", "repair")
+PHASES = ("geometry", "force_move", "test", "cell_list", "repair", "directors")
 
 
 def cg_profile_step(ctx, nsteps):
@@ -265,6 +276,29 @@ def cg_triangulate_noalloc(n, Lx, Ly, x, y, cnt, nbr, stream):
                                         C.c_void_p(stream)))
 
 
+def cg_get_launch(ctx):
+    out = cg_launch()
+    _check(lib().cg_get_launch(ctx, C.byref(out)), ctx)
+    return {k: getattr(out, k) for k, _ in cg_launch._fields_}
+
+
+def cg_set_launch(ctx, launch):
+    _check(lib().cg_set_launch(ctx, C.byref(cg_launch(**launch))), ctx)
+
+
+def cg_autotune_bytes(ctx):
+    out = C.c_size_t(0)
+    _check(lib().cg_autotune_bytes(ctx, C.byref(out)), ctx)
+    return out.value
+
+
+def cg_autotune(ctx, steps_per_trial, scratch):
+    best, ms = cg_launch(), C.c_double(0.0)
+    _check(lib().cg_autotune(ctx, int(steps_per_trial), _ptr(scratch), scratch.numel(), C.byref(best),
+                             C.byref(ms)), ctx)
+    return {k: getattr(best, k) for k, _ in cg_launch._fields_}, ms.value
+
+
 def cg_num_cells(ctx):
     return int(lib().cg_num_cells(ctx))
 
@@ -351,6 +385,24 @@ class SPV:
 
     def counters(self):
         return cg_get_counters(self.ctx)
+
+    @property
+    def launch(self):
+        return cg_get_launch(self.ctx)
+
+    def set_launch(self, **launch):
+        cur = cg_get_launch(self.ctx)
+        cur.update(launch)
+        cg_set_launch(self.ctx, cur)
+
+    def autotune(self, steps_per_trial=10):
+        """Times candidate launch shapes on a temporary copy of the current
+        state and keeps the fastest; the simulation itself takes no step."""
+        t = self.torch
+        scratch = t.empty(cg_autotune_bytes(self.ctx), dtype=t.uint8, device=self.device)
+        best, ms = cg_autotune(self.ctx, steps_per_trial, scratch)
+        del scratch
+        return best, ms
 
     def set_moduli(self, KA, KP):
         cg_set_moduli(self.ctx, KA, KP)

@@ -216,7 +216,7 @@ int loop_graph(cg_avm_ctx* c, Prefix prefix, cudaGraphExec_t* out) {
         a.loop = h;
         launch_avm_t1_pass(a, st);
       },
-      out);
+      [](cudaStream_t) {}, out);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return afail(c, CG_ECUDA, std::string("building the T1 loop graph: ") + cudaGetErrorString(e));

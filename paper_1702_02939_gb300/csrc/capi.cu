@@ -28,7 +28,7 @@ struct Layout {
 struct Offsets {
   size_t key, rank, perm, key_count, key_start, key_partials, theta_alt, p0_alt, v0_alt, tag_alt, rep_alt,
       cnt_alt, nbr_alt;
-  size_t x, y, X, Y, theta, p0, v0, A, P, Fx, Fy, ecell, tmp, tmp2, scalar;
+  size_t x, y, X, Y, theta, p0, v0, A, P, Fx, Fy, ecell, tmp, tmp2, scalar, nrm, xi;
   size_t tag, rep, cnt, nbr, old_cnt, old_nbr;
   size_t fs, s, w;
   size_t flags, list0, list1;
@@ -71,6 +71,8 @@ Offsets layout(int64_t N, int64_t NB, int64_t NK, int R) {
   o.tmp = L.take(N * d);
   o.tmp2 = L.take(N * d);
   o.scalar = L.take(4 * d);
+  o.nrm = L.take(N * sizeof(double2));
+  o.xi = L.take(N * d);
   o.tag = L.take(N * i4);
   o.rep = L.take(N * i4);
   o.cnt = L.take(N * i4);
@@ -174,6 +176,10 @@ struct cg_ctx {
   Offsets off{};
   cudaStream_t stream = nullptr;    // user stream
   cudaStream_t capture = nullptr;   // private stream used for graph capture
+  cudaStream_t side[2] = {nullptr, nullptr};  // branches of the captured step
+  cudaEvent_t fork = nullptr, join_dir = nullptr, join_list = nullptr;
+  cg_launch launch{4, 2, 0, 0};                // launch shapes of the step graph
+  std::vector<cg_replica> user_reps;           // as passed to cg_create
   cudaGraphExec_t step_exec = nullptr;
   int graph_steps = 0;
   std::string last_error;
@@ -246,8 +252,26 @@ ForceArgs force_args(cg_ctx* c, int integrate) {
   f.dt = c->par.dt;
   f.noise_amp = std::sqrt(2.0 * c->par.Dr * c->par.dt);
   f.seed = c->par.seed;
+  f.nrm = c->at<double2>(c->off.nrm);
+  f.xi = c->at<double>(c->off.xi);
   return f;
 }
+
+DirArgs dir_args(cg_ctx* c) {
+  DirArgs d;
+  d.n = (int)c->N;
+  d.ctl = c->ctl();
+  d.theta = c->at<double>(c->off.theta);
+  d.tag = c->at<int>(c->off.tag);
+  d.seed = c->par.seed;
+  d.nrm = c->at<double2>(c->off.nrm);
+  d.xi = c->at<double>(c->off.xi);
+  return d;
+}
+
+// Director terms of the next move for the current directors, step counter
+// and storage order (after anything that changes one of them).
+void refresh_directors(cg_ctx* c) { launch_dir(dir_args(c), c->stream); }
 
 TestArgs test_args(cg_ctx* c) {
   TestArgs t;
@@ -375,21 +399,31 @@ int sm_count() {
 }
 // Per-step repair rounds handle a few hundred flagged cells: a modest
 // persistent grid (warps loop over the list) keeps empty rounds cheap.
-int repair_grid(const cg_ctx*) { return sm_count() * 4; }
-int check_grid(const cg_ctx*) { return sm_count() * 2; }
+int repair_grid(const cg_ctx* c) { return sm_count() * c->launch.repair_blocks_per_sm; }
+int check_grid(const cg_ctx* c) { return sm_count() * c->launch.check_blocks_per_sm; }
+int dir_grid(const cg_ctx* c) { return sm_count() * c->launch.dir_blocks_per_sm; }  // 0: full
 // Full triangulation: one warp per cell over every cell.
 int repair_grid_all(const cg_ctx*) { return sm_count() * 16; }
 int check_grid_all(const cg_ctx* c) { return (int)((c->N + 255) / 256); }
 
 // One time step, enqueued on stream st (also used for capture).
-// One step up to the repair rounds: geometry, forces and move, circumcircle
-// test, cell list.
+// One step up to the repair rounds, as captured into the step graph:
+// geometry, forces and move, then three branches — the circumcircle test,
+// the cell-list build, and the director terms of the next step (FP64 work
+// that overlaps the FP32/integer test and the latency-bound repair).
 void enqueue_step_prefix(cg_ctx* c, cudaStream_t st) {
   launch_geom(geom_args(c), st);
   launch_force(force_args(c, 1), st);
   launch_begin_topology(c->ctl(), 1, st);
+  cudaEventRecord(c->fork, st);
+  cudaStreamWaitEvent(c->side[0], c->fork, 0);
+  launch_dir(dir_args(c), c->side[0], dir_grid(c));
+  cudaEventRecord(c->join_dir, c->side[0]);
+  cudaStreamWaitEvent(c->side[1], c->fork, 0);
+  launch_cell_list(cell_list_args(c, 0), c->side[1]);
+  cudaEventRecord(c->join_list, c->side[1]);
   launch_test(test_args(c), st);
-  launch_cell_list(cell_list_args(c, 1), st);
+  cudaStreamWaitEvent(st, c->join_list, 0);
 }
 
 // One repair round (repair + consistency check) for a conditional loop node:
@@ -462,7 +496,9 @@ int build_graph(cg_ctx* c) {
   if (c->step_exec) return CG_OK;
   cudaError_t e = build_loop_graph(
       c->capture, [&](cudaGraphConditionalHandle, cudaStream_t st) { enqueue_step_prefix(c, st); },
-      [&](cudaGraphConditionalHandle h, cudaStream_t st) { enqueue_repair_round(c, h, st); }, &c->step_exec);
+      [&](cudaGraphConditionalHandle h, cudaStream_t st) { enqueue_repair_round(c, h, st); },
+      [&](cudaStream_t st) { cudaStreamWaitEvent(st, c->join_dir, 0); }, &c->step_exec,
+      c->launch.dir_low_priority ? (unsigned long long)cudaGraphInstantiateFlagUseNodePriority : 0ull);
   if (e != cudaSuccess) {
     cudaGetLastError();
     c->step_exec = nullptr;
@@ -531,6 +567,7 @@ void snapshot(cg_ctx* c, int save, const Snapshot& s) {
   launch_snapshot((int)c->N, save, c->ctl(), c->at<double>(c->off.x), c->at<double>(c->off.y),
                   c->at<long long>(c->off.X), c->at<long long>(c->off.Y), c->at<double>(c->off.theta),
                   c->at<int>(c->off.cnt), c->at<int>(c->off.nbr), s, c->stream);
+  if (!save) refresh_directors(c);  // directors and step counter were restored
 }
 
 JvpArgs jvp_args(cg_ctx* c, char* bw, const BwdLayout& b) {
@@ -604,6 +641,7 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
   }
   c->R = R;
   c->par = *params;
+  c->user_reps.assign(reps, reps + R);
   if (c->par.repair_cap <= 0) c->par.repair_cap = 4;
   c->off = layout(c->N, c->NB, c->NK, R);
   if (ws_bytes < c->off.total) {
@@ -614,7 +652,17 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
   c->stream = static_cast<cudaStream_t>(stream);
   int rc = CG_OK;
   do {
-    cudaError_t e = cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking);
+    // the critical path (capture stream, cell-list branch) at the highest
+    // priority, the director branch at the lowest; the priorities take effect
+    // when the graph is instantiated with node priorities (dir_low_priority)
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->capture, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side[0], cudaStreamNonBlocking, lo);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side[1], cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_dir, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_list, cudaEventDisableTiming);
     if (e != cudaSuccess) { rc = fail(c, CG_ECUDA, cudaGetErrorString(e)); break; }
     cudaStream_t st = c->stream;
     // replica table and per-cell constants
@@ -648,6 +696,7 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
     launch_sort(sort_args(c), st);  // spatial order before the first triangulation
     rc = triangulate_all(c);
     if (rc) break;
+    refresh_directors(c);
     rc = read_status(c);
     if (rc) break;
     rc = build_graph(c);
@@ -663,8 +712,10 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
 int cg_step(cg_ctx* c, int64_t nsteps) {
   if (!c || nsteps < 0) return CG_EINVAL;
   for (int64_t s = 0; s < nsteps; ++s) {
-    if (c->par.sort_every > 0 && c->host_step > 0 && c->host_step % c->par.sort_every == 0)
+    if (c->par.sort_every > 0 && c->host_step > 0 && c->host_step % c->par.sort_every == 0) {
       launch_sort(sort_args(c), c->stream);
+      refresh_directors(c);
+    }
     CG_CUDA(c, cudaGraphLaunch(c->step_exec, c->stream));
     ++c->host_step;
   }
@@ -696,7 +747,9 @@ int cg_profile_step(cg_ctx* c, int64_t nsteps, double* ms_out, int32_t n_out) {
       launch_check(check_args(c, r & 1, r == cap - 1, 0), check_grid(c), st);
     }
     cudaEventRecord(ev[5], st);
-    if (cudaEventSynchronize(ev[5]) != cudaSuccess) { rc = fail(c, CG_ECUDA, "profile sync"); break; }
+    launch_dir(dir_args(c), st, dir_grid(c));
+    cudaEventRecord(ev[6], st);
+    if (cudaEventSynchronize(ev[6]) != cudaSuccess) { rc = fail(c, CG_ECUDA, "profile sync"); break; }
     for (int k = 0; k < CG_NUM_PHASES; ++k) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
@@ -749,6 +802,7 @@ int cg_set_state(cg_ctx* c, const double* x, const double* y, const double* thet
   if (rc) return rc;
   rc = triangulate_all(c);
   if (rc) return rc;
+  refresh_directors(c);
   return read_status(c);
 }
 
@@ -855,6 +909,117 @@ int cg_set_moduli(cg_ctx* c, double KA, double KP) {
   return build_graph(c);
 }
 
+int cg_get_launch(const cg_ctx* c, cg_launch* out) {
+  if (!c || !out) return CG_EINVAL;
+  *out = c->launch;
+  return CG_OK;
+}
+
+int cg_set_launch(cg_ctx* c, const cg_launch* l) {
+  if (!c || !l) return CG_EINVAL;
+  if (l->repair_blocks_per_sm < 1 || l->repair_blocks_per_sm > 64 || l->check_blocks_per_sm < 1 ||
+      l->check_blocks_per_sm > 64 || l->dir_blocks_per_sm < 0 || l->dir_blocks_per_sm > 64 ||
+      (l->dir_low_priority != 0 && l->dir_low_priority != 1))
+    return CG_EINVAL;
+  int rc = read_status(c);
+  if (rc) return rc;
+  c->launch = *l;
+  if (c->step_exec) {
+    cudaGraphExecDestroy(c->step_exec);
+    c->step_exec = nullptr;
+  }
+  return build_graph(c);
+}
+
+int cg_autotune_bytes(const cg_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return CG_EINVAL;
+  *bytes = c->off.total + ((5 * (size_t)c->N * sizeof(double) + 255) & ~(size_t)255);
+  return CG_OK;
+}
+
+int cg_autotune(cg_ctx* c, int32_t steps_per_trial, void* d_ws2, size_t ws2_bytes, cg_launch* best,
+                double* best_ms) {
+  if (!c || steps_per_trial < 1 || !d_ws2 || ((uintptr_t)d_ws2 & 255)) return CG_EINVAL;
+  size_t need = 0;
+  cg_autotune_bytes(c, &need);
+  if (ws2_bytes < need) return CG_EINVAL;
+  int rc = read_status(c);
+  if (rc) return rc;
+  // the current state in user order, after the temporary workspace
+  char* base = static_cast<char*>(d_ws2);
+  double* sx = reinterpret_cast<double*>(base + c->off.total);
+  double* sy = sx + c->N;
+  double* sth = sy + c->N;
+  double* sp0 = sth + c->N;
+  double* sv0 = sp0 + c->N;
+  if ((rc = cg_get_state(c, sx, sy, sth))) return rc;
+  const int* tag = c->at<int>(c->off.tag);
+  launch_gather_d((int)c->N, tag, c->at<double>(c->off.p0), sp0, c->stream);
+  launch_gather_d((int)c->N, tag, c->at<double>(c->off.v0), sv0, c->stream);
+  Ctl h;
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  CG_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
+  cg_ctx* t = nullptr;
+  rc = cg_create(c->R, c->user_reps.data(), &c->par, sx, sy, sth, d_ws2, c->off.total, c->stream, &t);
+  if (rc) return fail(c, rc, "autotune: temporary context: " + (t ? t->last_error : std::string("create failed")));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto trial = [&](const cg_launch& l, double& ms) -> int {
+    int r = cg_set_launch(t, &l);
+    if (!r) r = cg_set_state(t, sx, sy, sth);
+    if (!r) r = cg_set_p0(t, sp0);
+    if (!r) r = cg_set_v0(t, sv0);
+    if (!r) r = cg_set_step(t, h.step);
+    if (!r) r = cg_step(t, 2);
+    if (r) return r;
+    cudaEventRecord(e0, t->stream);
+    r = cg_step(t, steps_per_trial);
+    cudaEventRecord(e1, t->stream);
+    if (!r) r = read_status(t);
+    float f = 0.f;
+    cudaEventElapsedTime(&f, e0, e1);
+    ms = f / steps_per_trial;
+    return r;
+  };
+  static const int repair_opts[] = {2, 4, 8, 16};
+  static const int check_opts[] = {1, 2, 4, 8};
+  static const int dir_opts[] = {0, 1, 2, 4, 8};
+  static const int prio_opts[] = {0, 1};
+  cg_launch cur = c->launch;
+  double cur_ms = 0.0;
+  rc = trial(cur, cur_ms);
+  for (int sweep = 0; sweep < 2 && !rc; ++sweep) {
+    for (int field = 0; field < 4 && !rc; ++field) {
+      const int* opts = field == 0 ? repair_opts : field == 1 ? check_opts : field == 2 ? dir_opts : prio_opts;
+      const int nopt = field == 0 ? 4 : field == 1 ? 4 : field == 2 ? 5 : 2;
+      for (int k = 0; k < nopt && !rc; ++k) {
+        cg_launch cand = cur;
+        int* slot = field == 0 ? &cand.repair_blocks_per_sm : field == 1 ? &cand.check_blocks_per_sm
+                  : field == 2 ? &cand.dir_blocks_per_sm : &cand.dir_low_priority;
+        if (*slot == opts[k]) continue;
+        *slot = opts[k];
+        double ms = 0.0;
+        rc = trial(cand, ms);
+        if (!rc && ms < cur_ms) {
+          cur = cand;
+          cur_ms = ms;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::string terr = rc ? t->last_error : std::string();
+  cg_destroy(t);
+  if (rc) return fail(c, rc, "autotune trial: " + terr);
+  rc = cg_set_launch(c, &cur);
+  if (rc) return rc;
+  if (best) *best = cur;
+  if (best_ms) *best_ms = cur_ms;
+  return CG_OK;
+}
+
 int cg_set_step(cg_ctx* c, int64_t step) {
   if (!c || step < 0) return CG_EINVAL;
   int rc = read_status(c);
@@ -863,7 +1028,8 @@ int cg_set_step(cg_ctx* c, int64_t step) {
   CG_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
   h.step = step;
   CG_CUDA(c, cudaMemcpy(c->ctl(), &h, sizeof(Ctl), cudaMemcpyHostToDevice));
-  return CG_OK;
+  refresh_directors(c);
+  return read_status(c);
 }
 
 int cg_run_checkpointed(cg_ctx* c, int64_t nsteps, int32_t ckpt_every, void* d_bw, size_t bytes) {
@@ -1012,6 +1178,10 @@ int cg_destroy(cg_ctx* c) {
   if (!c) return CG_EINVAL;
   if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
   if (c->capture) cudaStreamDestroy(c->capture);
+  for (cudaStream_t sd : c->side)
+    if (sd) cudaStreamDestroy(sd);
+  for (cudaEvent_t ev : {c->fork, c->join_dir, c->join_list})
+    if (ev) cudaEventDestroy(ev);
   delete c;
   return CG_OK;
 }

@@ -44,7 +44,23 @@ struct ForceArgs {
   const double* v0;
   double mu, dt, noise_amp;
   unsigned long long seed;
+  const double2* nrm;  // (cos, sin) of each cell's director, from k_dir
+  const double* xi;    // the step's director noise, from k_dir
 };
+
+// Director terms of the next move, computed off the critical path: n(theta)
+// and the Philox/Box-Muller noise of the step held in the control word.
+struct DirArgs {
+  int n;
+  Ctl* ctl;
+  const double* theta;
+  const int* tag;
+  unsigned long long seed;
+  double2* nrm;
+  double* xi;
+};
+// blocks: grid size (grid-stride loop); 0 = one thread per cell
+void launch_dir(const DirArgs& a, cudaStream_t st, int blocks = 0);
 
 struct TestArgs {
   int n;

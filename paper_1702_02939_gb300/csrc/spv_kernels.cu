@@ -217,10 +217,9 @@ __global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
   const Rep R = g.reps[g.rep[i]];
   const double xi = g.x[(size_t)cur * N + i], yi = g.y[(size_t)cur * N + i];
   const double th = g.theta[i];
-  double sn, cs;
-  sincos(th, &sn, &cs);
+  const double2 nd = g.nrm[i];  // (cos theta, sin theta), from k_dir
   const double v0 = g.v0[i];
-  const double vx = g.mu * fx + v0 * cs, vy = g.mu * fy + v0 * sn;
+  const double vx = g.mu * fx + v0 * nd.x, vy = g.mu * fy + v0 * nd.y;
   const double xn = xi + g.dt * vx, yn = yi + g.dt * vy;
   long long X, Y;
   if (isfinite(xn) && isfinite(yn)) {
@@ -236,8 +235,25 @@ __global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
   g.y[(size_t)nxt * N + i] = (double)Y * R.inv_scale;
   g.X[(size_t)nxt * N + i] = X;
   g.Y[(size_t)nxt * N + i] = Y;
+  g.theta[i] = th + g.noise_amp * g.xi[i];
+}
+
+// n(theta) and xi (Philox counter (tag, step)) of the next move, one thread
+// per cell.  In the step graph it runs beside the circumcircle test, the cell
+// list and the repair rounds, which leave the FP64 pipe idle.
+__global__ void k_dir(DirArgs g) {
   const long long step = g.ctl->step;
-  g.theta[i] = th + g.noise_amp * director_noise(g.seed, g.tag[i], step);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincos(g.theta[i], &sn, &cs);
+    g.nrm[i] = make_double2(cs, sn);
+    g.xi[i] = director_noise(g.seed, g.tag[i], step);
+  }
+}
+void launch_dir(const DirArgs& a, cudaStream_t st, int blocks) {
+  if (a.n <= 0) return;
+  const int full = (a.n + 127) / 128;
+  k_dir<<<(blocks > 0 && blocks < full) ? blocks : full, 128, 0, st>>>(a);
 }
 
 // Start of the topology phase of a step: the new positions become current,

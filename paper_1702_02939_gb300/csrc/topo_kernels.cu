@@ -499,6 +499,10 @@ __global__ void k_check(CheckArgs g) {
   if (!g.dyn) return;  // uniform over the grid
   if (last_block(&g.ctl->done) && threadIdx.x == 0) {
     Ctl* ctl = g.ctl;
+    if (ctl->round_count == 0 && which_in == 0) {  // first round: the test's flags
+      ctl->last_flagged = total;
+      ctl->flagged_total += total;
+    }
     const int produced = *(volatile int*)count_out;
     const int r = ctl->round_count + (total > 0 ? 1 : 0);
     ctl->round_count = r;

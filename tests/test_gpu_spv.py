@@ -326,3 +326,43 @@ def test_repair_cap_status():
         sim.sync()
     assert e.value.code == -4
     sim.close()
+
+
+def test_launch_shapes_do_not_change_results():
+    """Grids of the repair, check and director kernels and the node priorities
+    change timing only: 20 steps agree bit for bit."""
+    n = 4096
+    a, *_ = make(n, 33, p0=3.85, v0=0.1, seed=3)
+    b, *_ = make(n, 33, p0=3.85, v0=0.1, seed=3)
+    b.set_launch(repair_blocks_per_sm=8, check_blocks_per_sm=4, dir_blocks_per_sm=1, dir_low_priority=1)
+    assert b.launch["dir_blocks_per_sm"] == 1
+    a.step(20)
+    b.step(20)
+    for ta, tb in zip(a.state() + a.neighbors(), b.state() + b.neighbors()):
+        assert torch.equal(ta, tb)
+    a.close()
+    b.close()
+
+
+def test_autotune_takes_no_step_and_keeps_results():
+    """The autotuner times candidates on a temporary copy: the context's state
+    and step counter are untouched and later steps equal an untuned run."""
+    n = 4096
+    a, *_ = make(n, 34, p0=3.85, v0=0.1, seed=4)
+    b, *_ = make(n, 34, p0=3.85, v0=0.1, seed=4)
+    a.step(3)
+    b.step(3)
+    before = a.state()
+    best, ms = a.autotune(3)
+    assert ms > 0 and set(best) == {"repair_blocks_per_sm", "check_blocks_per_sm", "dir_blocks_per_sm",
+                                    "dir_low_priority"}
+    assert a.launch == best
+    for t0, t1 in zip(before, a.state()):
+        assert torch.equal(t0, t1)
+    assert a.counters()["steps"] == 3
+    a.step(10)
+    b.step(10)
+    for ta, tb in zip(a.state() + a.neighbors(), b.state() + b.neighbors()):
+        assert torch.equal(ta, tb)
+    a.close()
+    b.close()
