@@ -150,10 +150,11 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def kernels_launched(steps, loop_iterations):
-    # per step: geometry, force+move, begin-topology, test, 4 cell-list
-    # kernels; per iteration of the repair-round loop node: repair + check
-    return 8 * steps + 2 * loop_iterations
+def kernels_launched(steps, loop_iterations, eager=False):
+    # per step: force+move, begin-topology, test, 4 cell-list kernels,
+    # directors, geometry of the new state, and (graph only) the geometry
+    # fix-up of repaired cells; per repair round: repair + check
+    return (9 if eager else 10) * steps + 2 * loop_iterations
 
 
 def cpu_baseline(x, y, th, L, seconds):
@@ -506,7 +507,7 @@ def run_ours(args):
                            "repair_cap": repair_cap, "launch": "eager" if args.eager else "graph",
                            "launch_shapes": launch, "autotune_ms_per_step": tune_ms},
                 "clocks": clk, "e2e": e2e,
-                "gpu_launches": (kernels_launched(args.steps, args.steps * repair_cap) if args.eager
+                "gpu_launches": (kernels_launched(args.steps, args.steps * repair_cap, eager=True) if args.eager
                                  else kernels_launched(args.steps, counters["loop_total"] - loops0)),
                 "roofline": roofline, "hbm_roofline": hbm, "cpu_baseline": cpu,
                 "phase_ms_per_step": {k: v / prof_steps for k, v in ph.items()},

@@ -135,7 +135,7 @@ void t1_bounds(double thr, double L, float& lo, float& hi) {
 }
 
 AvmArgs avm_args(cg_avm_ctx* c) {
-  AvmArgs a;
+  AvmArgs a{};  // every field starts zero or null
   a.n = c->n;
   a.V = c->V;
   a.ctl = c->ctl();
@@ -305,7 +305,7 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
     Ctl h;
     std::memset(&h, 0, sizeof(h));
     if (cudaMemcpyAsync(c->ctl(), &h, sizeof(Ctl), cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = CG_ECUDA; break; }
-    AvmBuildArgs b;
+    AvmBuildArgs b{};  // every field starts zero or null
     b.n = n;
     b.ctl = c->ctl();
     b.Lx = c->Lx;

@@ -31,7 +31,7 @@ struct Offsets {
   size_t x, y, X, Y, theta, p0, v0, A, P, Fx, Fy, ecell, tmp, tmp2, scalar, nrm, xi;
   size_t tag, rep, cnt, nbr, old_cnt, old_nbr;
   size_t fs, s, w;
-  size_t flags, list0, list1;
+  size_t flags, list0, list1, dirty_list, dirty_bits;
   size_t bin_count, bin_start, partials, cell_bin, cell_rank, ids;
   size_t reps, ctl;
   size_t total;
@@ -85,6 +85,8 @@ Offsets layout(int64_t N, int64_t NB, int64_t NK, int R) {
   o.flags = L.take(((N + 31) / 32) * 4);
   o.list0 = L.take(N * i4);
   o.list1 = L.take(N * i4);
+  o.dirty_list = L.take(N * i4);
+  o.dirty_bits = L.take(((N + 31) / 32) * 4);
   o.bin_count = L.take(NB * i4);
   o.bin_start = L.take((NB + 1) * i4);
   o.partials = L.take(((NB + 1 + kScanChunkHost - 1) / kScanChunkHost + 1) * i4);
@@ -178,7 +180,7 @@ struct cg_ctx {
   cudaStream_t capture = nullptr;   // private stream used for graph capture
   cudaStream_t side[2] = {nullptr, nullptr};  // branches of the captured step
   cudaEvent_t fork = nullptr, join_dir = nullptr, join_list = nullptr;
-  cg_launch launch{4, 2, 0, 0};                // launch shapes of the step graph
+  cg_launch launch{4, 2, 2, 1, 4, 0};          // launch shapes of the step graph
   std::vector<cg_replica> user_reps;           // as passed to cg_create
   cudaGraphExec_t step_exec = nullptr;
   int graph_steps = 0;
@@ -204,7 +206,7 @@ int fail(cg_ctx* c, int code, const std::string& msg) {
   } while (0)
 
 GeomArgs geom_args(cg_ctx* c) {
-  GeomArgs g;
+  GeomArgs g{};  // every field starts zero or null
   g.n = (int)c->N;
   g.reps = c->at<Rep>(c->off.reps);
   g.rep = c->at<int>(c->off.rep);
@@ -224,11 +226,15 @@ GeomArgs geom_args(cg_ctx* c) {
   g.fs = c->at<double2>(c->off.fs);
   g.s = c->at<double2>(c->off.s);
   g.w = c->at<double2>(c->off.w);
+  g.list = nullptr;
+  g.list_count = nullptr;
+  g.list_bits = nullptr;
+  g.tolerant = 0;
   return g;
 }
 
 ForceArgs force_args(cg_ctx* c, int integrate) {
-  ForceArgs f;
+  ForceArgs f{};  // every field starts zero or null
   f.n = (int)c->N;
   f.reps = c->at<Rep>(c->off.reps);
   f.rep = c->at<int>(c->off.rep);
@@ -258,7 +264,7 @@ ForceArgs force_args(cg_ctx* c, int integrate) {
 }
 
 DirArgs dir_args(cg_ctx* c) {
-  DirArgs d;
+  DirArgs d{};  // every field starts zero or null
   d.n = (int)c->N;
   d.ctl = c->ctl();
   d.theta = c->at<double>(c->off.theta);
@@ -274,7 +280,7 @@ DirArgs dir_args(cg_ctx* c) {
 void refresh_directors(cg_ctx* c) { launch_dir(dir_args(c), c->stream); }
 
 TestArgs test_args(cg_ctx* c) {
-  TestArgs t;
+  TestArgs t{};  // every field starts zero or null
   t.n = (int)c->N;
   t.reps = c->at<Rep>(c->off.reps);
   t.rep = c->at<int>(c->off.rep);
@@ -290,7 +296,7 @@ TestArgs test_args(cg_ctx* c) {
 }
 
 CellListArgs cell_list_args(cg_ctx* c, int only_if_flagged) {
-  CellListArgs a;
+  CellListArgs a{};  // every field starts zero or null
   a.n = (int)c->N;
   a.nbins = (int)c->NB;
   a.reps = c->at<Rep>(c->off.reps);
@@ -309,7 +315,7 @@ CellListArgs cell_list_args(cg_ctx* c, int only_if_flagged) {
 }
 
 RepairArgs repair_args(cg_ctx* c, int which_in, int all_cells) {
-  RepairArgs r;
+  RepairArgs r{};  // every field starts zero or null
   r.n = (int)c->N;
   r.reps = c->at<Rep>(c->off.reps);
   r.rep = c->at<int>(c->off.rep);
@@ -333,11 +339,13 @@ RepairArgs repair_args(cg_ctx* c, int which_in, int all_cells) {
   r.dyn = 0;
   r.lists[0] = r.lists[1] = nullptr;
   r.loop = 0;
+  r.dirty_list = nullptr;
+  r.dirty_bits = nullptr;
   return r;
 }
 
 CheckArgs check_args(cg_ctx* c, int which_in, int last_round, int all_cells) {
-  CheckArgs k;
+  CheckArgs k{};  // every field starts zero or null
   k.n = (int)c->N;
   k.ctl = c->ctl();
   k.cnt = c->at<int>(c->off.cnt);
@@ -359,7 +367,7 @@ CheckArgs check_args(cg_ctx* c, int which_in, int last_round, int all_cells) {
 }
 
 SortArgs sort_args(cg_ctx* c) {
-  SortArgs a;
+  SortArgs a{};  // every field starts zero or null
   a.n = (int)c->N;
   a.nkeys = (int)c->NK;
   a.reps = c->at<Rep>(c->off.reps);
@@ -401,23 +409,30 @@ int sm_count() {
 // persistent grid (warps loop over the list) keeps empty rounds cheap.
 int repair_grid(const cg_ctx* c) { return sm_count() * c->launch.repair_blocks_per_sm; }
 int check_grid(const cg_ctx* c) { return sm_count() * c->launch.check_blocks_per_sm; }
-int dir_grid(const cg_ctx* c) { return sm_count() * c->launch.dir_blocks_per_sm; }  // 0: full
+int dir_grid(const cg_ctx* c) { return sm_count() * c->launch.dir_blocks_per_sm; }    // 0: full
+int geom_grid(const cg_ctx* c) { return sm_count() * c->launch.geom_blocks_per_sm; }  // 0: full
 // Full triangulation: one warp per cell over every cell.
 int repair_grid_all(const cg_ctx*) { return sm_count() * 16; }
 int check_grid_all(const cg_ctx* c) { return (int)((c->N + 255) / 256); }
 
 // One time step, enqueued on stream st (also used for capture).
-// One step up to the repair rounds, as captured into the step graph:
-// geometry, forces and move, then three branches — the circumcircle test,
-// the cell-list build, and the director terms of the next step (FP64 work
-// that overlaps the FP32/integer test and the latency-bound repair).
+// One step up to the repair rounds, as captured into the step graph.  The
+// geometry and force sets of the current positions and rings are valid when
+// the step starts (they are computed at the end of the previous step, or by
+// prime_geometry): forces and move, then branches — the circumcircle test,
+// the cell-list build, and, at low priority, the director terms of the next
+// step followed by the geometry of the new positions, which overlaps the
+// latency-bound repair rounds (rings rewritten meanwhile are recomputed by
+// the fix-up after the rounds).
 void enqueue_step_prefix(cg_ctx* c, cudaStream_t st) {
-  launch_geom(geom_args(c), st);
   launch_force(force_args(c, 1), st);
   launch_begin_topology(c->ctl(), 1, st);
   cudaEventRecord(c->fork, st);
   cudaStreamWaitEvent(c->side[0], c->fork, 0);
   launch_dir(dir_args(c), c->side[0], dir_grid(c));
+  GeomArgs g = geom_args(c);
+  g.tolerant = 1;
+  launch_geom(g, c->side[0], geom_grid(c));
   cudaEventRecord(c->join_dir, c->side[0]);
   cudaStreamWaitEvent(c->side[1], c->fork, 0);
   launch_cell_list(cell_list_args(c, 0), c->side[1]);
@@ -425,6 +440,21 @@ void enqueue_step_prefix(cg_ctx* c, cudaStream_t st) {
   launch_test(test_args(c), st);
   cudaStreamWaitEvent(st, c->join_list, 0);
 }
+
+// After the repair rounds and the concurrent geometry: the geometry of every
+// cell whose ring a round rewrote.
+void enqueue_step_suffix(cg_ctx* c, cudaStream_t st) {
+  cudaStreamWaitEvent(st, c->join_dir, 0);
+  GeomArgs g = geom_args(c);
+  g.list = c->at<int>(c->off.dirty_list);
+  g.list_count = &c->ctl()->dirty_count;
+  g.list_bits = c->at<unsigned>(c->off.dirty_bits);
+  launch_geom(g, st, sm_count() * 2);
+}
+
+// Geometry and force sets of the current positions and rings (before the
+// first step and after anything outside a step changes their inputs).
+void prime_geometry(cg_ctx* c) { launch_geom(geom_args(c), c->stream); }
 
 // One repair round (repair + consistency check) for a conditional loop node:
 // the round counter in the control word picks the lists.
@@ -434,6 +464,8 @@ void enqueue_repair_round(cg_ctx* c, cudaGraphConditionalHandle h, cudaStream_t 
   r.lists[0] = c->at<int>(c->off.list0);
   r.lists[1] = c->at<int>(c->off.list1);
   r.loop = h;
+  r.dirty_list = c->at<int>(c->off.dirty_list);
+  r.dirty_bits = c->at<unsigned>(c->off.dirty_bits);
   CheckArgs k = check_args(c, 0, 0, 0);
   k.dyn = 1;
   k.cap = c->par.repair_cap > 0 ? c->par.repair_cap : 4;
@@ -497,7 +529,7 @@ int build_graph(cg_ctx* c) {
   cudaError_t e = build_loop_graph(
       c->capture, [&](cudaGraphConditionalHandle, cudaStream_t st) { enqueue_step_prefix(c, st); },
       [&](cudaGraphConditionalHandle h, cudaStream_t st) { enqueue_repair_round(c, h, st); },
-      [&](cudaStream_t st) { cudaStreamWaitEvent(st, c->join_dir, 0); }, &c->step_exec,
+      [&](cudaStream_t st) { enqueue_step_suffix(c, st); }, &c->step_exec,
       c->launch.dir_low_priority ? (unsigned long long)cudaGraphInstantiateFlagUseNodePriority : 0ull);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -567,11 +599,14 @@ void snapshot(cg_ctx* c, int save, const Snapshot& s) {
   launch_snapshot((int)c->N, save, c->ctl(), c->at<double>(c->off.x), c->at<double>(c->off.y),
                   c->at<long long>(c->off.X), c->at<long long>(c->off.Y), c->at<double>(c->off.theta),
                   c->at<int>(c->off.cnt), c->at<int>(c->off.nbr), s, c->stream);
-  if (!save) refresh_directors(c);  // directors and step counter were restored
+  if (!save) {  // positions, rings, directors and step counter were restored
+    refresh_directors(c);
+    prime_geometry(c);
+  }
 }
 
 JvpArgs jvp_args(cg_ctx* c, char* bw, const BwdLayout& b) {
-  JvpArgs a;
+  JvpArgs a{};  // every field starts zero or null
   a.n = (int)c->N;
   a.reps = c->at<Rep>(c->off.reps);
   a.rep = c->at<int>(c->off.rep);
@@ -694,9 +729,14 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
     rc = load_positions(c, x, y);
     if (rc) break;
     launch_sort(sort_args(c), st);  // spatial order before the first triangulation
+    if (cudaMemsetAsync(c->at<unsigned>(c->off.dirty_bits), 0, ((c->N + 31) / 32) * 4, st) != cudaSuccess) {
+      rc = fail(c, CG_ECUDA, "clearing the dirty bitmap");
+      break;
+    }
     rc = triangulate_all(c);
     if (rc) break;
     refresh_directors(c);
+    prime_geometry(c);
     rc = read_status(c);
     if (rc) break;
     rc = build_graph(c);
@@ -715,6 +755,7 @@ int cg_step(cg_ctx* c, int64_t nsteps) {
     if (c->par.sort_every > 0 && c->host_step > 0 && c->host_step % c->par.sort_every == 0) {
       launch_sort(sort_args(c), c->stream);
       refresh_directors(c);
+      prime_geometry(c);
     }
     CG_CUDA(c, cudaGraphLaunch(c->step_exec, c->stream));
     ++c->host_step;
@@ -731,29 +772,31 @@ int cg_profile_step(cg_ctx* c, int64_t nsteps, double* ms_out, int32_t n_out) {
   const int cap = c->par.repair_cap > 0 ? c->par.repair_cap : 4;
   const int grid = repair_grid(c);
   int rc = CG_OK;
+  // the order of the graph step: the geometry of the new state comes last
+  static const int kPhaseOfInterval[CG_NUM_PHASES] = {1, 2, 3, 4, 5, 0};
   for (int64_t s = 0; s < nsteps && !rc; ++s) {
     cudaEventRecord(ev[0], st);
-    launch_geom(geom_args(c), st);
-    cudaEventRecord(ev[1], st);
     launch_force(force_args(c, 1), st);
-    cudaEventRecord(ev[2], st);
+    cudaEventRecord(ev[1], st);
     launch_begin_topology(c->ctl(), 1, st);
     launch_test(test_args(c), st);
-    cudaEventRecord(ev[3], st);
+    cudaEventRecord(ev[2], st);
     launch_cell_list(cell_list_args(c, 1), st);
-    cudaEventRecord(ev[4], st);
+    cudaEventRecord(ev[3], st);
     for (int r = 0; r < cap; ++r) {
       launch_repair(repair_args(c, r & 1, 0), grid, st);
       launch_check(check_args(c, r & 1, r == cap - 1, 0), check_grid(c), st);
     }
-    cudaEventRecord(ev[5], st);
+    cudaEventRecord(ev[4], st);
     launch_dir(dir_args(c), st, dir_grid(c));
+    cudaEventRecord(ev[5], st);
+    launch_geom(geom_args(c), st);
     cudaEventRecord(ev[6], st);
     if (cudaEventSynchronize(ev[6]) != cudaSuccess) { rc = fail(c, CG_ECUDA, "profile sync"); break; }
     for (int k = 0; k < CG_NUM_PHASES; ++k) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
-      ms_out[k] += ms;
+      ms_out[kPhaseOfInterval[k]] += ms;
     }
   }
   for (int k = 0; k <= CG_NUM_PHASES; ++k) cudaEventDestroy(ev[k]);
@@ -803,6 +846,7 @@ int cg_set_state(cg_ctx* c, const double* x, const double* y, const double* thet
   rc = triangulate_all(c);
   if (rc) return rc;
   refresh_directors(c);
+  prime_geometry(c);
   return read_status(c);
 }
 
@@ -870,7 +914,13 @@ static int set_percell(cg_ctx* c, const double* src, size_t off) {
   return read_status(c);
 }
 
-int cg_set_p0(cg_ctx* c, const double* p0) { return c ? set_percell(c, p0, c->off.p0) : CG_EINVAL; }
+int cg_set_p0(cg_ctx* c, const double* p0) {
+  if (!c) return CG_EINVAL;
+  int rc = set_percell(c, p0, c->off.p0);
+  if (rc) return rc;
+  prime_geometry(c);  // the force sets depend on p0
+  return read_status(c);
+}
 int cg_set_v0(cg_ctx* c, const double* v0) { return c ? set_percell(c, v0, c->off.v0) : CG_EINVAL; }
 
 int cg_get_counters(cg_ctx* c, cg_counters* out) {
@@ -906,7 +956,10 @@ int cg_set_moduli(cg_ctx* c, double KA, double KP) {
     cudaGraphExecDestroy(c->step_exec);
     c->step_exec = nullptr;
   }
-  return build_graph(c);
+  rc = build_graph(c);
+  if (rc) return rc;
+  prime_geometry(c);  // the force sets depend on the moduli
+  return read_status(c);
 }
 
 int cg_get_launch(const cg_ctx* c, cg_launch* out) {
@@ -919,7 +972,8 @@ int cg_set_launch(cg_ctx* c, const cg_launch* l) {
   if (!c || !l) return CG_EINVAL;
   if (l->repair_blocks_per_sm < 1 || l->repair_blocks_per_sm > 64 || l->check_blocks_per_sm < 1 ||
       l->check_blocks_per_sm > 64 || l->dir_blocks_per_sm < 0 || l->dir_blocks_per_sm > 64 ||
-      (l->dir_low_priority != 0 && l->dir_low_priority != 1))
+      (l->dir_low_priority != 0 && l->dir_low_priority != 1) || l->geom_blocks_per_sm < 0 ||
+      l->geom_blocks_per_sm > 64 || l->reserved != 0)
     return CG_EINVAL;
   int rc = read_status(c);
   if (rc) return rc;
@@ -986,17 +1040,20 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, void* d_ws2, size_t ws2_byte
   static const int check_opts[] = {1, 2, 4, 8};
   static const int dir_opts[] = {0, 1, 2, 4, 8};
   static const int prio_opts[] = {0, 1};
+  static const int geom_opts[] = {0, 2, 4, 8};
   cg_launch cur = c->launch;
   double cur_ms = 0.0;
   rc = trial(cur, cur_ms);
   for (int sweep = 0; sweep < 2 && !rc; ++sweep) {
-    for (int field = 0; field < 4 && !rc; ++field) {
-      const int* opts = field == 0 ? repair_opts : field == 1 ? check_opts : field == 2 ? dir_opts : prio_opts;
-      const int nopt = field == 0 ? 4 : field == 1 ? 4 : field == 2 ? 5 : 2;
+    for (int field = 0; field < 5 && !rc; ++field) {
+      const int* opts = field == 0 ? repair_opts : field == 1 ? check_opts : field == 2 ? dir_opts
+                      : field == 3 ? prio_opts : geom_opts;
+      const int nopt = field == 0 ? 4 : field == 1 ? 4 : field == 2 ? 5 : field == 3 ? 2 : 4;
       for (int k = 0; k < nopt && !rc; ++k) {
         cg_launch cand = cur;
         int* slot = field == 0 ? &cand.repair_blocks_per_sm : field == 1 ? &cand.check_blocks_per_sm
-                  : field == 2 ? &cand.dir_blocks_per_sm : &cand.dir_low_priority;
+                  : field == 2 ? &cand.dir_blocks_per_sm : field == 3 ? &cand.dir_low_priority
+                  : &cand.geom_blocks_per_sm;
         if (*slot == opts[k]) continue;
         *slot = opts[k];
         double ms = 0.0;

@@ -74,7 +74,7 @@ struct Ctl {
   int last_flagged;
   int pad;
   unsigned int done;  // last-block counter of the repair-round check
-  int pad2;
+  int dirty_count;    // cells whose ring a repair round rewrote in this step
   long long loop_total;  // iterations of the repair-round (or T1-pass) loop node
 };
 

@@ -27,6 +27,14 @@ struct GeomArgs {
   double *A, *P;
   double* energy_out;   // per-cell energy or nullptr
   double2 *fs, *s, *w;  // [CG_RING][n]
+  // Cells to process: list[0 .. *list_count) if list is set, else all.
+  const int* list;
+  const int* list_count;
+  unsigned* list_bits;  // bit of each listed cell, cleared once processed
+  // Rings may be rewritten concurrently (the pass beside the repair rounds):
+  // out-of-range entries are skipped and no status is raised; every cell whose
+  // ring changes is processed again afterwards.
+  int tolerant;
 };
 
 struct ForceArgs {
@@ -104,6 +112,10 @@ struct RepairArgs {
   int dyn;
   const int* lists[2];
   cudaGraphConditionalHandle loop;
+  // Cells whose ring a per-step round rewrites, each once per step (bitmap
+  // dirty_bits, list dirty_list, count in the control word); null: not kept.
+  int* dirty_list;
+  unsigned* dirty_bits;
 };
 
 struct CheckArgs {
@@ -124,7 +136,8 @@ struct CheckArgs {
   cudaGraphConditionalHandle loop;
 };
 
-void launch_geom(const GeomArgs& a, cudaStream_t st);
+// blocks: grid size (grid-stride loop); 0 = one thread per cell (or per list entry bound n)
+void launch_geom(const GeomArgs& a, cudaStream_t st, int blocks = 0);
 void launch_force(const ForceArgs& a, cudaStream_t st);
 void launch_begin_topology(Ctl* ctl, int flip, cudaStream_t st);
 void launch_test(const TestArgs& a, cudaStream_t st);

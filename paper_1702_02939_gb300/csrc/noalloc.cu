@@ -166,7 +166,7 @@ extern "C" int cg_triangulate_noalloc(int32_t n, double Lx, double Ly, const dou
   k_noalloc_index<<<(n + 255) / 256, 256, 0, st>>>(n, tag, repi);
   launch_snap(n, d_rep, repi, d_x, d_y, x, y, X, Y, ctl, st);
 
-  CellListArgs cl;
+  CellListArgs cl{};  // every field starts zero or null
   cl.n = n;
   cl.nbins = nbins;
   cl.reps = d_rep;
@@ -183,7 +183,7 @@ extern "C" int cg_triangulate_noalloc(int32_t n, double Lx, double Ly, const dou
   cl.only_if_flagged = 0;
   launch_cell_list(cl, st);
 
-  RepairArgs ra;
+  RepairArgs ra{};  // every field starts zero or null
   ra.n = n;
   ra.reps = d_rep;
   ra.rep = repi;
@@ -209,7 +209,7 @@ extern "C" int cg_triangulate_noalloc(int32_t n, double Lx, double Ly, const dou
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   launch_repair(ra, sms * 8, st);
 
-  CheckArgs ck;
+  CheckArgs ck{};  // every field starts zero or null
   ck.n = n;
   ck.ctl = ctl;
   ck.cnt = cnt;

@@ -50,86 +50,95 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
   __shared__ double sh_ex[CG_RING][kGeomThreads];  // unit vector of the edge ending at vertex a
   __shared__ double sh_ey[CG_RING][kGeomThreads];
   const int t = threadIdx.x;
-  const int i = blockIdx.x * kGeomThreads + t;
-  if (i >= g.n) return;
   const size_t N = (size_t)g.n;
   const int cur = g.ctl->cur;
   const long long* __restrict__ X = g.X + (size_t)cur * N;
   const long long* __restrict__ Y = g.Y + (size_t)cur * N;
-  const Rep R = g.reps[g.rep[i]];
-  const long long Xi = X[i], Yi = Y[i];
-  const int m = g.cnt[i];
-  if (m < 3 || m > CG_RING) {
-    raise_status(g.ctl, kETOPO);
-    return;
-  }
-  const int* ring = g.nbr + (size_t)i * CG_RING;
-
-  const int j0 = ring[0];
-  const double d0x = i2d_exact(min_image_i(X[j0] - Xi, R.LX));
-  const double d0y = i2d_exact(min_image_i(Y[j0] - Yi, R.LY));
-  const double l0 = d0x * d0x + d0y * d0y;
-  double ax = d0x, ay = d0y, la = l0;
-  double hpx = 0.0, hpy = 0.0, h0x = 0.0, h0y = 0.0;
-  double area = 0.0, per = 0.0;
-  for (int a = 0; a < m; ++a) {
-    double bx, by, lb;
-    if (a + 1 < m) {
-      const int j = ring[a + 1];
-      bx = i2d_exact(min_image_i(X[j] - Xi, R.LX));
-      by = i2d_exact(min_image_i(Y[j] - Yi, R.LY));
-      lb = bx * bx + by * by;
-    } else {
-      bx = d0x; by = d0y; lb = l0;
+  const int total = g.list ? *g.list_count : g.n;
+  for (int item = blockIdx.x * kGeomThreads + t; item < total; item += gridDim.x * kGeomThreads) {
+    const int i = g.list ? g.list[item] : item;
+    if (g.list_bits) atomicAnd(&g.list_bits[i >> 5], ~(1u << (i & 31)));
+    const Rep R = g.reps[g.rep[i]];
+    const long long Xi = X[i], Yi = Y[i];
+    const int m = g.cnt[i];
+    if (m < 3 || m > CG_RING) {
+      if (!g.tolerant) raise_status(g.ctl, kETOPO);
+      continue;
     }
-    const double det = ax * by - ay * bx;  // (r_j - r_i) x (r_k - r_i)
-    const double r = fast_rcp(det);
-    const double hr = 0.5 * r;
-    // circumcentre relative to r_i
-    const double hx = (by * la - ay * lb) * hr;
-    const double hy = (ax * lb - bx * la) * hr;
-    g.s[a * N + i] = make_double2(hx * r, hy * r);
-    g.w[a * N + i] = make_double2(by - ay, ax - bx);
-    sh_hx[a][t] = hx;
-    sh_hy[a][t] = hy;
-    if (a == 0) {
-      h0x = hx; h0y = hy;
-    } else {
-      area += hpx * hy - hx * hpy;
-      const double ex = hx - hpx, ey = hy - hpy;
+    const int* ring = g.nbr + (size_t)i * CG_RING;
+    // a ring being rewritten concurrently may hold -1 entries: read the cell
+    // itself there (the result is discarded and computed again)
+    auto nb = [&](int a) {
+      const int j = ring[a];
+      return ((unsigned)j < (unsigned)g.n) ? j : i;
+    };
+
+    const int j0 = nb(0);
+    const double d0x = i2d_exact(min_image_i(X[j0] - Xi, R.LX));
+    const double d0y = i2d_exact(min_image_i(Y[j0] - Yi, R.LY));
+    const double l0 = d0x * d0x + d0y * d0y;
+    double ax = d0x, ay = d0y, la = l0;
+    double hpx = 0.0, hpy = 0.0, h0x = 0.0, h0y = 0.0;
+    double area = 0.0, per = 0.0;
+    for (int a = 0; a < m; ++a) {
+      double bx, by, lb;
+      if (a + 1 < m) {
+        const int j = nb(a + 1);
+        bx = i2d_exact(min_image_i(X[j] - Xi, R.LX));
+        by = i2d_exact(min_image_i(Y[j] - Yi, R.LY));
+        lb = bx * bx + by * by;
+      } else {
+        bx = d0x; by = d0y; lb = l0;
+      }
+      const double det = ax * by - ay * bx;  // (r_j - r_i) x (r_k - r_i)
+      const double r = fast_rcp(det);
+      const double hr = 0.5 * r;
+      // circumcentre relative to r_i
+      const double hx = (by * la - ay * lb) * hr;
+      const double hy = (ax * lb - bx * la) * hr;
+      g.s[a * N + i] = make_double2(hx * r, hy * r);
+      g.w[a * N + i] = make_double2(by - ay, ax - bx);
+      sh_hx[a][t] = hx;
+      sh_hy[a][t] = hy;
+      if (a == 0) {
+        h0x = hx; h0y = hy;
+      } else {
+        area += hpx * hy - hx * hpy;
+        const double ex = hx - hpx, ey = hy - hpy;
+        const double l2 = ex * ex + ey * ey;
+        const double il = rsqrt(l2);
+        per += l2 * il;
+        sh_ex[a][t] = ex * il;
+        sh_ey[a][t] = ey * il;
+      }
+      hpx = hx; hpy = hy;
+      ax = bx; ay = by; la = lb;
+    }
+    {  // closing edge h_{m-1} -> h_0 is the incoming edge of vertex 0
+      area += hpx * h0y - h0x * hpy;
+      const double ex = h0x - hpx, ey = h0y - hpy;
       const double l2 = ex * ex + ey * ey;
       const double il = rsqrt(l2);
       per += l2 * il;
-      sh_ex[a][t] = ex * il;
-      sh_ey[a][t] = ey * il;
+      sh_ex[0][t] = ex * il;
+      sh_ey[0][t] = ey * il;
     }
-    hpx = hx; hpy = hy;
-    ax = bx; ay = by; la = lb;
-  }
-  {  // closing edge h_{m-1} -> h_0 is the incoming edge of vertex 0
-    area += hpx * h0y - h0x * hpy;
-    const double ex = h0x - hpx, ey = h0y - hpy;
-    const double l2 = ex * ex + ey * ey;
-    const double il = rsqrt(l2);
-    per += l2 * il;
-    sh_ex[0][t] = ex * il;
-    sh_ey[0][t] = ey * il;
-  }
-  const double sc = R.inv_scale;
-  const double A = 0.5 * area * sc * sc, P = per * sc;
-  g.A[i] = A;
-  g.P[i] = P;
-  const double dA = A - g.A0, dP = P - g.p0[i] * g.sqrtA0;
-  if (g.energy_out) g.energy_out[i] = g.KA * dA * dA + g.KP * dP * dP;
-  // dA/dh = 1/2 perp(h_next - h_prev) (the 1/2 and the grid scale fold into ka);
-  // dP/dh = e_in - e_out (unit edge vectors)
-  const double ka = g.KA * dA * sc, kp = 2.0 * g.KP * dP;
-  for (int a = 0; a < m; ++a) {
-    const int ap = (a == 0) ? m - 1 : a - 1;
-    const int an = (a + 1 == m) ? 0 : a + 1;
-    const double gx = sh_hy[an][t] - sh_hy[ap][t], gy = sh_hx[ap][t] - sh_hx[an][t];
-    const double dPx = sh_ex[a][t] - sh_ex[an][t], dPy = sh_ey[a][t] - sh_ey[an][t];
-    g.fs[a * N + i] = make_double2(fma(ka, gx, kp * dPx), fma(ka, gy, kp * dPy));
+    const double sc = R.inv_scale;
+    const double A = 0.5 * area * sc * sc, P = per * sc;
+    g.A[i] = A;
+    g.P[i] = P;
+    const double dA = A - g.A0, dP = P - g.p0[i] * g.sqrtA0;
+    if (g.energy_out) g.energy_out[i] = g.KA * dA * dA + g.KP * dP * dP;
+    // dA/dh = 1/2 perp(h_next - h_prev) (the 1/2 and the grid scale fold into ka);
+    // dP/dh = e_in - e_out (unit edge vectors)
+    const double ka = g.KA * dA * sc, kp = 2.0 * g.KP * dP;
+    for (int a = 0; a < m; ++a) {
+      const int ap = (a == 0) ? m - 1 : a - 1;
+      const int an = (a + 1 == m) ? 0 : a + 1;
+      const double gx = sh_hy[an][t] - sh_hy[ap][t], gy = sh_hx[ap][t] - sh_hx[an][t];
+      const double dPx = sh_ex[a][t] - sh_ex[an][t], dPy = sh_ey[a][t] - sh_ey[an][t];
+      g.fs[a * N + i] = make_double2(fma(ka, gx, kp * dPx), fma(ka, gy, kp * dPy));
+    }
   }
 }
 
@@ -266,6 +275,7 @@ __global__ void k_begin_topology(Ctl* ctl, int flip) {
   ctl->count[0] = 0;
   ctl->count[1] = 0;
   ctl->round_count = 0;
+  ctl->dirty_count = 0;
 }
 
 __device__ __forceinline__ void flag_cell(unsigned* flags, int* list, int* count, int c) {
@@ -338,9 +348,10 @@ __global__ void __launch_bounds__(kTestThreads) k_test(TestArgs g) {
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
-void launch_geom(const GeomArgs& a, cudaStream_t st) {
+void launch_geom(const GeomArgs& a, cudaStream_t st, int blocks) {
   if (a.n <= 0) return;
-  k_geom<<<(a.n + kGeomThreads - 1) / kGeomThreads, kGeomThreads, 0, st>>>(a);
+  const int full = (a.n + kGeomThreads - 1) / kGeomThreads;
+  k_geom<<<(blocks > 0 && blocks < full) ? blocks : full, kGeomThreads, 0, st>>>(a);
 }
 void launch_force(const ForceArgs& a, cudaStream_t st) {
   if (a.n <= 0) return;

@@ -437,6 +437,10 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
     if (lane == 0) {
       g.cnt[i] = p.m;
       atomicAnd(&g.flags[i >> 5], ~(1u << (i & 31)));
+      if (g.dirty_list && !g.all_cells) {
+        const unsigned bit = 1u << (i & 31);
+        if (!(atomicOr(&g.dirty_bits[i >> 5], bit) & bit)) g.dirty_list[atomicAdd(&g.ctl->dirty_count, 1)] = i;
+      }
     }
   }
 }
