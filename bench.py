@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel of the step eagerly instead of replaying the step graph "
                          "(same kernels and results; for kernel-level profilers)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="time per step against N (solid and fluid regimes) and against p0, GPU and CPU "
+                         "oracle; prints one JSON object (a study, not the bench line)")
     ap.add_argument("--avm-only", action="store_true",
                     help="run only the AVM section and print its JSON object (a diagnostic, not the bench line)")
     return ap.parse_args()
@@ -87,6 +90,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value, world, device):
+    """The largest value over all ranks (timed regions are reported as the
+    slowest rank's); one rank returns its own value."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world, cells_per_rank, steps, ms):
+    """Whole-job throughput: every rank advances its own system of
+    cells_per_rank cells for `steps` steps in `ms` milliseconds (max over ranks)."""
+    return world * cells_per_rank * steps / (ms * 1e-3)
+
+
 def hbm_peak():
     try:
         with open(MEASURED_PEAKS) as f:
@@ -96,7 +118,6 @@ def hbm_peak():
 
 
 def workload(n, seed):
-    import oracle  # noqa: F401  (not used for inputs; see workloads)
     import workloads
 
     x, y, th, L = workloads.spv_uniform(n, seed)
@@ -342,6 +363,72 @@ def avm_throughput(args, device):
                            "sample": f"{steps} oracle AVM steps of the same N={n} network, {el:.1f} s"}}
 
 
+def sweep(args):
+    """Time per step against system size and shape index, in the regimes of
+    the paper's SPV timing figures: the solid regime (p0 = 3.8, v0 = 0.01,
+    dt = 0.05; Fig. 2) and the fluid regime of the benchmark (p0 = 3.85,
+    v0 = 0.1, dt = 0.01), N = 1024 ... 1048576; then p0 = 3.8 ... 4.0 at
+    N = 65536, v0 = 0.1 (Fig. 3).  GPU: 100 warm-up steps, then 200 graph
+    steps timed with CUDA events (default launch shapes).  CPU: the oracle's
+    full periodic step, single thread, timed on the same state for N up to
+    262144 (1 to 5 steps)."""
+    import torch
+
+    import __graft_entry__
+    import oracle
+    import paper_1702_02939_gb300 as cg
+    import workloads
+
+    __graft_entry__.build()
+    stream = torch.cuda.current_stream()
+
+    def gpu_time(n, p0, v0, dt, seed):
+        x, y, th, L = workloads.spv_uniform(n, seed)
+        sim = cg.SPV([dict(n=n, Lx=L, Ly=L, p0=p0, v0=v0)], x, y, th, dt=dt, seed=seed)
+        sim.step(100)
+        c0 = sim.counters()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(200)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sim.sync()
+        c1 = sim.counters()
+        ms = e0.elapsed_time(e1) / 200
+        xs, ys, ths = (t.cpu().numpy() for t in sim.state())
+        sim.close()
+        return ms, (c1["flagged_total"] - c0["flagged_total"]) / 200, (xs, ys, ths, L)
+
+    def cpu_time(state, p0, v0, dt):
+        xs, ys, ths, L = state
+        Lx, Ly, q = oracle.box(L)
+        xs, ys = oracle.snap_positions(xs, ys, Lx, Ly)
+        steps, t0 = 0, time.perf_counter()
+        while True:
+            xs, ys, ths, _ = oracle.spv_run(xs, ys, ths, Lx, Ly, p0, v0, 1, seed=1, step0=steps, dt=dt)
+            steps += 1
+            el = time.perf_counter() - t0
+            if el > 3.0 or steps >= 5:
+                return 1e3 * el / steps
+
+    rows = []
+    regimes = {"solid": (3.8, 0.01, 0.05), "fluid": (3.85, 0.1, 0.01)}
+    for name, (p0, v0, dt) in regimes.items():
+        for n in (1024, 4096, 16384, 65536, 262144, 1048576):
+            ms, flagged, state = gpu_time(n, p0, v0, dt, 5)
+            cms = cpu_time(state, p0, v0, dt) if n <= 262144 else None
+            rows.append({"regime": name, "n": n, "p0": p0, "v0": v0, "dt": dt, "gpu_ms_per_step": ms,
+                         "cpu_oracle_ms_per_step": cms, "speedup": (cms / ms) if cms else None,
+                         "flagged_per_step": flagged})
+    for p0 in (3.8, 3.85, 3.9, 4.0):
+        ms, flagged, state = gpu_time(65536, p0, 0.1, 0.01, 6)
+        cms = cpu_time(state, p0, 0.1, 0.01)
+        rows.append({"regime": "p0 scan", "n": 65536, "p0": p0, "v0": 0.1, "dt": 0.01, "gpu_ms_per_step": ms,
+                     "cpu_oracle_ms_per_step": cms, "speedup": cms / ms, "flagged_per_step": flagged})
+    print(json.dumps({"study": "SPV time per step vs N and p0 (GB300, FP64)", "rows": rows}), flush=True)
+
+
 def run_reference(args):
     """CPU oracle arm: each step is one oracle step of a spatial window of the
     N=262144 state, sized so that the whole run takes a few minutes."""
@@ -442,13 +529,9 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     sim.sync()  # raises on any device error
-    ms = sum(ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps))
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)), world, "cuda")
     counters = sim.counters()
-    value = world * args.n * args.steps / (ms * 1e-3)
+    value = weak_scaling_value(world, args.n, args.steps, ms)
 
     # per-kernel device times (eager launches, CUDA events on the same stream)
     prof_steps = max(1, args.avm_profile_steps)
@@ -480,9 +563,9 @@ def run_ours(args):
             cg.cg_set_v0(sim.ctx, hv0)
             cg.cg_step(sim.ctx, 1)
             cg.cg_get_state(sim.ctx, hx, hy, None)
-        el = time.perf_counter() - t0
-        e2e = {"value": world * args.n * args.e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": 8 * args.n,
-               "d2h_bytes_per_step": 16 * args.n}
+        el = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+        e2e = {"value": weak_scaling_value(world, args.n, args.e2e_steps, 1e3 * el), "unit": UNIT,
+               "h2d_bytes_per_step": 8 * args.n, "d2h_bytes_per_step": 16 * args.n}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -519,6 +602,9 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.sweep:
+        sweep(args)
+        return
     if args.avm_only:
         import __graft_entry__
 
