@@ -20,6 +20,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -48,7 +49,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # Dominant-kernel DRAM traffic per launch (dram__bytes_read.sum +
 # dram__bytes_write.sum) from the committed ncu capture of the current k_geom
 # (profiles/k_geom_spv_N262144.md); set back to None whenever k_geom changes.
-GEOM_DRAM_BYTES_PER_LAUNCH = 56.31e6
+GEOM_DRAM_BYTES_PER_LAUNCH = None
 
 
 def parse():
@@ -68,6 +69,8 @@ def parse():
     ap.add_argument("--bwd-steps", type=int, default=1000)
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-avm", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--fp32-steps", type=int, default=500)
     ap.add_argument("--avm-steps", type=int, default=500)
     ap.add_argument("--avm-warmup", type=int, default=100)
     ap.add_argument("--avm-profile-steps", type=int, default=20)
@@ -178,6 +181,21 @@ def kernels_launched(steps, loop_iterations, eager=False):
     return (9 if eager else 10) * steps + 2 * loop_iterations
 
 
+def host_cpu():
+    """Logical CPUs and model of the host the oracle runs on."""
+    model = platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "processor name"):
+                    model = f"{platform.machine()} {line.split(':', 1)[1].strip()}"
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
 def cpu_baseline(x, y, th, L, seconds):
     """The oracle as it stands: full periodic steps (retriangulation from
     scratch, forces, update) of the same workload, single thread."""
@@ -193,7 +211,7 @@ def cpu_baseline(x, y, th, L, seconds):
         el = time.perf_counter() - t0
         if el >= seconds or steps >= 50:
             break
-    return {"value": n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": n * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": f"{steps} full oracle steps of the N={n} workload (periodic Bowyer-Watson "
                       f"retriangulation + forces + update), {el:.1f} s, single thread"}
 
@@ -295,6 +313,50 @@ def backward_cost(args, device):
     sim.close()
     return {"workload": "spv_grad_N4096_steps%d_ckpt%d" % (K, every), "forward_ms": fwd_ms, "backward_ms": bwd_ms,
             "backward_over_forward": bwd_ms / fwd_ms, "grad_KA": out[4], "grad_KP": out[5]}
+
+
+def fp32_throughput(args, device):
+    """The same SPV workload with single-precision physics (cg_params.precision
+    = 1: FP32 geometry, forces and director terms; positions on the exact grid
+    and exact topology): 100 FP64 warm-up steps (the random initial state's
+    largest forces overflow FP32), 10 FP32 steps, autotuned launch shapes, then
+    each graph step timed alone with CUDA events, L2 flushed in between."""
+    import torch
+
+    import paper_1702_02939_gb300 as cg
+
+    # the random initial state holds nearly coincident cells whose forces
+    # overflow FP32; it is relaxed with FP64 steps first
+    x, y, th, L = workload(args.n, 1)
+    relax = cg.SPV([dict(n=args.n, Lx=L, Ly=L, p0=P0, v0=V0)], x, y, th, dt=DT, seed=1, device=device)
+    relax.step(args.warmup)
+    x, y, th = relax.state()
+    relax.close()
+    del relax
+    sim = cg.SPV([dict(n=args.n, Lx=L, Ly=L, p0=P0, v0=V0)], x, y, th, dt=DT, seed=1, precision="f32",
+                 device=device)
+    sim.set_step(args.warmup)
+    sim.step(10)
+    sim.sync()
+    launch, _ = sim.autotune(10) if not args.no_autotune else (sim.launch, None)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+    K = args.fp32_steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(stream)
+        sim.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    sim.sync()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / K
+    ph = sim.profile(20)
+    sim.close()
+    return {"workload": WORKLOAD.replace("fp64", "fp32"), "unit": UNIT, "dtype": "f32 physics, int64 grid, exact topology",
+            "cell_steps_per_s": args.n / (ms * 1e-3), "ms_per_step": ms, "steps": K, "warmup": args.warmup,
+            "launch_shapes": launch, "phase_ms_per_step": {k: v / 20 for k, v in ph.items()}}
 
 
 def avm_throughput(args, device):
@@ -487,7 +549,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / max(timed, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "n_cells": n, "box": Lx, "sample": "window"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -593,6 +656,9 @@ def run_ours(args):
     avm = None
     if rank == 0 and world == 1 and not args.no_avm:
         avm = avm_throughput(args, f"cuda:{local}")
+    fp32 = None
+    if rank == 0 and world == 1 and not args.no_fp32:
+        fp32 = fp32_throughput(args, f"cuda:{local}")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -607,7 +673,7 @@ def run_ours(args):
                                  else kernels_launched(args.steps, counters["loop_total"] - loops0)),
                 "roofline": roofline, "hbm_roofline": hbm, "cpu_baseline": cpu,
                 "phase_ms_per_step": {k: v / prof_steps for k, v in ph.items()},
-                "counters": counters, "batched": batched, "backward": backward, "avm": avm}
+                "counters": counters, "batched": batched, "backward": backward, "avm": avm, "fp32": fp32}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

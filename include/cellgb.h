@@ -84,6 +84,10 @@ typedef struct cg_params {
   uint64_t seed;       /* Philox key of the director noise */
   int32_t repair_cap;  /* repair rounds per step, >= 1 (default 4) */
   int32_t sort_every;  /* Hilbert re-sort period in steps; 0 = never */
+  int32_t precision;   /* 0: FP64 physics (default); 1: FP32 geometry, forces and
+                          director terms (positions stay on the exact grid and every
+                          topological decision stays exact; no backward pass) */
+  int32_t reserved;    /* 0 */
 } cg_params;
 
 /* Counters accumulated on the device since creation. */

@@ -40,7 +40,8 @@ class cg_replica(C.Structure):
 class cg_params(C.Structure):
     _fields_ = [("A0", C.c_double), ("KA", C.c_double), ("KP", C.c_double), ("mu", C.c_double),
                 ("Dr", C.c_double), ("dt", C.c_double), ("seed", C.c_uint64),
-                ("repair_cap", C.c_int32), ("sort_every", C.c_int32)]
+                ("repair_cap", C.c_int32), ("sort_every", C.c_int32), ("precision", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class cg_launch(C.Structure):
@@ -320,12 +321,15 @@ class SPV:
     """
 
     def __init__(self, replicas, x, y, theta, A0=1.0, KA=1.0, KP=1.0, mu=1.0, Dr=1.0, dt=0.01, seed=0,
-                 repair_cap=4, sort_every=0, device="cuda"):
+                 repair_cap=4, sort_every=0, precision="f64", device="cuda"):
         import torch
         self.torch = torch
         self.device = torch.device(device)
         self.replicas = [dict(r) for r in replicas]
-        self.params = cg_params(A0, KA, KP, mu, Dr, dt, int(seed), int(repair_cap), int(sort_every))
+        if precision not in ("f64", "f32"):
+            raise ValueError("precision is 'f64' or 'f32'")
+        self.params = cg_params(A0, KA, KP, mu, Dr, dt, int(seed), int(repair_cap), int(sort_every),
+                                1 if precision == "f32" else 0, 0)
         nbytes = cg_workspace_bytes(self.replicas)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.n = sum(int(r["n"]) for r in self.replicas)

@@ -7,8 +7,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcellgb.so")
-SOURCES = ["capi.cu", "spv_kernels.cu", "topo_kernels.cu", "sort_kernels.cu", "adjoint_kernels.cu", "noalloc.cu",
-           "avm_kernels.cu", "avm_capi.cu"]
+SOURCES = ["capi.cu", "spv_kernels.cu", "spv_kernels_f32.cu", "topo_kernels.cu", "sort_kernels.cu",
+           "adjoint_kernels.cu", "noalloc.cu", "avm_kernels.cu", "avm_capi.cu"]
 HEADERS = ["cg_device.cuh", "cg_kernels.h", "cg_graph.h"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -275,9 +275,24 @@ DirArgs dir_args(cg_ctx* c) {
   return d;
 }
 
+// Kernels of the chosen precision (cg_params.precision).
+bool fp32(const cg_ctx* c) { return c->par.precision == 1; }
+void run_geom(const cg_ctx* c, const GeomArgs& a, cudaStream_t st, int blocks = 0) {
+  if (fp32(c)) launch_geom_f32(a, st, blocks);
+  else launch_geom(a, st, blocks);
+}
+void run_force(const cg_ctx* c, const ForceArgs& a, cudaStream_t st) {
+  if (fp32(c)) launch_force_f32(a, st);
+  else launch_force(a, st);
+}
+void run_dir(const cg_ctx* c, const DirArgs& a, cudaStream_t st, int blocks = 0) {
+  if (fp32(c)) launch_dir_f32(a, st, blocks);
+  else launch_dir(a, st, blocks);
+}
+
 // Director terms of the next move for the current directors, step counter
 // and storage order (after anything that changes one of them).
-void refresh_directors(cg_ctx* c) { launch_dir(dir_args(c), c->stream); }
+void refresh_directors(cg_ctx* c) { run_dir(c, dir_args(c), c->stream); }
 
 TestArgs test_args(cg_ctx* c) {
   TestArgs t{};  // every field starts zero or null
@@ -425,14 +440,14 @@ int check_grid_all(const cg_ctx* c) { return (int)((c->N + 255) / 256); }
 // latency-bound repair rounds (rings rewritten meanwhile are recomputed by
 // the fix-up after the rounds).
 void enqueue_step_prefix(cg_ctx* c, cudaStream_t st) {
-  launch_force(force_args(c, 1), st);
+  run_force(c, force_args(c, 1), st);
   launch_begin_topology(c->ctl(), 1, st);
   cudaEventRecord(c->fork, st);
   cudaStreamWaitEvent(c->side[0], c->fork, 0);
-  launch_dir(dir_args(c), c->side[0], dir_grid(c));
+  run_dir(c, dir_args(c), c->side[0], dir_grid(c));
   GeomArgs g = geom_args(c);
   g.tolerant = 1;
-  launch_geom(g, c->side[0], geom_grid(c));
+  run_geom(c, g, c->side[0], geom_grid(c));
   cudaEventRecord(c->join_dir, c->side[0]);
   cudaStreamWaitEvent(c->side[1], c->fork, 0);
   launch_cell_list(cell_list_args(c, 0), c->side[1]);
@@ -449,12 +464,12 @@ void enqueue_step_suffix(cg_ctx* c, cudaStream_t st) {
   g.list = c->at<int>(c->off.dirty_list);
   g.list_count = &c->ctl()->dirty_count;
   g.list_bits = c->at<unsigned>(c->off.dirty_bits);
-  launch_geom(g, st, sm_count() * 2);
+  run_geom(c, g, st, sm_count() * 2);
 }
 
 // Geometry and force sets of the current positions and rings (before the
 // first step and after anything outside a step changes their inputs).
-void prime_geometry(cg_ctx* c) { launch_geom(geom_args(c), c->stream); }
+void prime_geometry(cg_ctx* c) { run_geom(c, geom_args(c), c->stream); }
 
 // One repair round (repair + consistency check) for a conditional loop node:
 // the round counter in the control word picks the lists.
@@ -641,6 +656,7 @@ JvpArgs jvp_args(cg_ctx* c, char* bw, const BwdLayout& b) {
 
 int check_bwd(cg_ctx* c, int64_t nsteps, int32_t every, void* d_bw, size_t bytes, BwdLayout& b) {
   if (!c || nsteps < 1 || every < 1 || !d_bw || ((uintptr_t)d_bw & 255)) return CG_EINVAL;
+  if (fp32(c)) return fail(c, CG_EINVAL, "the backward pass runs in double precision only");
   b = bwd_layout(c->N, nsteps, every);
   if (bytes < b.total) return CG_EINVAL;
   return CG_OK;
@@ -678,6 +694,10 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
   c->par = *params;
   c->user_reps.assign(reps, reps + R);
   if (c->par.repair_cap <= 0) c->par.repair_cap = 4;
+  if ((c->par.precision != 0 && c->par.precision != 1) || c->par.reserved != 0) {
+    delete c;
+    return CG_EINVAL;
+  }
   c->off = layout(c->N, c->NB, c->NK, R);
   if (ws_bytes < c->off.total) {
     delete c;
@@ -776,7 +796,7 @@ int cg_profile_step(cg_ctx* c, int64_t nsteps, double* ms_out, int32_t n_out) {
   static const int kPhaseOfInterval[CG_NUM_PHASES] = {1, 2, 3, 4, 5, 0};
   for (int64_t s = 0; s < nsteps && !rc; ++s) {
     cudaEventRecord(ev[0], st);
-    launch_force(force_args(c, 1), st);
+    run_force(c, force_args(c, 1), st);
     cudaEventRecord(ev[1], st);
     launch_begin_topology(c->ctl(), 1, st);
     launch_test(test_args(c), st);
@@ -788,9 +808,9 @@ int cg_profile_step(cg_ctx* c, int64_t nsteps, double* ms_out, int32_t n_out) {
       launch_check(check_args(c, r & 1, r == cap - 1, 0), check_grid(c), st);
     }
     cudaEventRecord(ev[4], st);
-    launch_dir(dir_args(c), st, dir_grid(c));
+    run_dir(c, dir_args(c), st, dir_grid(c));
     cudaEventRecord(ev[5], st);
-    launch_geom(geom_args(c), st);
+    run_geom(c, geom_args(c), st);
     cudaEventRecord(ev[6], st);
     if (cudaEventSynchronize(ev[6]) != cudaSuccess) { rc = fail(c, CG_ECUDA, "profile sync"); break; }
     for (int k = 0; k < CG_NUM_PHASES; ++k) {
@@ -853,8 +873,8 @@ int cg_set_state(cg_ctx* c, const double* x, const double* y, const double* thet
 static int compute_forces(cg_ctx* c, int want_energy) {
   GeomArgs g = geom_args(c);
   if (want_energy) g.energy_out = c->at<double>(c->off.ecell);
-  launch_geom(g, c->stream);
-  launch_force(force_args(c, 0), c->stream);
+  run_geom(c, g, c->stream);
+  run_force(c, force_args(c, 0), c->stream);
   if (want_energy) launch_reduce_sum((int)c->N, c->at<double>(c->off.ecell), c->at<double>(c->off.scalar), c->stream);
   CG_CUDA(c, cudaGetLastError());
   return CG_OK;

@@ -285,4 +285,39 @@ __device__ __forceinline__ int incircle_sign(long long px, long long py, long lo
   }
 }
 
+// ----------------------------------------------------------------------------
+// Shared by the FP64 and FP32 step kernels.
+// ----------------------------------------------------------------------------
+// Periodic reduction of a finite coordinate: v' = fmod(v, L) (exact), rounded
+// to the grid, then wrapped into [0, L) in integer grid units.  For v in
+// [-L, 2L) fmod is a single exact subtraction or nothing.
+__device__ __forceinline__ long long wrap_to_grid(double v, double L, double scale, long long LI) {
+  double r;
+  if (v >= 0.0 && v < L) r = v;
+  else if (v >= L && v < 2.0 * L) r = v - L;
+  else if (v < 0.0 && v >= -L) r = v;
+  else r = fmod(v, L);
+  long long X = (long long)rint(r * scale);
+  if (X < 0) X += LI;
+  else if (X >= LI) X -= LI;
+  return X;
+}
+
+// Position of cell i in the ring of cell j, or -1.
+__device__ __forceinline__ int ring_pos(const int* __restrict__ nbr, const int* __restrict__ cnt, int j, int i) {
+  const int4* row = reinterpret_cast<const int4*>(nbr + (size_t)j * CG_RING);
+  const int mj = cnt[j];
+  int pos = -1;
+#pragma unroll
+  for (int q = 0; q < CG_RING / 4; ++q) {
+    if (4 * q >= mj) break;
+    int4 v = row[q];
+    if (v.x == i && 4 * q + 0 < mj) pos = 4 * q + 0;
+    if (v.y == i && 4 * q + 1 < mj) pos = 4 * q + 1;
+    if (v.z == i && 4 * q + 2 < mj) pos = 4 * q + 2;
+    if (v.w == i && 4 * q + 3 < mj) pos = 4 * q + 3;
+  }
+  return pos;
+}
+
 }  // namespace cgk

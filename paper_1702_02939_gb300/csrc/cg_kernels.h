@@ -138,6 +138,10 @@ struct CheckArgs {
 
 // blocks: grid size (grid-stride loop); 0 = one thread per cell (or per list entry bound n)
 void launch_geom(const GeomArgs& a, cudaStream_t st, int blocks = 0);
+// Single-precision variants (spv_kernels_f32.cu); same arguments.
+void launch_geom_f32(const GeomArgs& a, cudaStream_t st, int blocks = 0);
+void launch_force_f32(const ForceArgs& a, cudaStream_t st);
+void launch_dir_f32(const DirArgs& a, cudaStream_t st, int blocks = 0);
 void launch_force(const ForceArgs& a, cudaStream_t st);
 void launch_begin_topology(Ctl* ctl, int flip, cudaStream_t st);
 void launch_test(const TestArgs& a, cudaStream_t st);

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
         area += hpx * hy - hx * hpy;
         const double ex = hx - hpx, ey = hy - hpy;
         const double l2 = ex * ex + ey * ey;
-        const double il = rsqrt(l2);
+        const double il = (__double_as_longlong(l2) > 0) ? rsqrt(l2) : 0.0;  // zero-length edge: no direction
         per += l2 * il;
         sh_ex[a][t] = ex * il;
         sh_ey[a][t] = ey * il;
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
       area += hpx * h0y - h0x * hpy;
       const double ex = h0x - hpx, ey = h0y - hpy;
       const double l2 = ex * ex + ey * ey;
-      const double il = rsqrt(l2);
+      const double il = (__double_as_longlong(l2) > 0) ? rsqrt(l2) : 0.0;  // zero-length edge: no direction
       per += l2 * il;
       sh_ex[0][t] = ex * il;
       sh_ey[0][t] = ey * il;
@@ -140,38 +140,6 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
       g.fs[a * N + i] = make_double2(fma(ka, gx, kp * dPx), fma(ka, gy, kp * dPy));
     }
   }
-}
-
-// Periodic reduction of a finite coordinate: v' = fmod(v, L) (exact), rounded
-// to the grid, then wrapped into [0, L) in integer grid units.  For v in
-// [-L, 2L) fmod is a single exact subtraction or nothing.
-__device__ __forceinline__ long long wrap_to_grid(double v, double L, double scale, long long LI) {
-  double r;
-  if (v >= 0.0 && v < L) r = v;
-  else if (v >= L && v < 2.0 * L) r = v - L;
-  else if (v < 0.0 && v >= -L) r = v;
-  else r = fmod(v, L);
-  long long X = (long long)rint(r * scale);
-  if (X < 0) X += LI;
-  else if (X >= LI) X -= LI;
-  return X;
-}
-
-// Position of cell i in the ring of cell j, or -1.
-__device__ __forceinline__ int ring_pos(const int* __restrict__ nbr, const int* __restrict__ cnt, int j, int i) {
-  const int4* row = reinterpret_cast<const int4*>(nbr + (size_t)j * CG_RING);
-  const int mj = cnt[j];
-  int pos = -1;
-#pragma unroll
-  for (int q = 0; q < CG_RING / 4; ++q) {
-    if (4 * q >= mj) break;
-    int4 v = row[q];
-    if (v.x == i && 4 * q + 0 < mj) pos = 4 * q + 0;
-    if (v.y == i && 4 * q + 1 < mj) pos = 4 * q + 1;
-    if (v.z == i && 4 * q + 2 < mj) pos = 4 * q + 2;
-    if (v.w == i && 4 * q + 3 < mj) pos = 4 * q + 3;
-  }
-  return pos;
 }
 
 // One thread per cell: G_t = sum over the triangle's three cells of their force

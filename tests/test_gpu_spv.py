@@ -367,3 +367,74 @@ def test_autotune_takes_no_step_and_keeps_results():
         assert torch.equal(ta, tb)
     a.close()
     b.close()
+
+
+# FP32 mode (single-precision physics, exact topology).  Bounds from the
+# arithmetic: every FP32 operation rounds with relative error u = 2^-24; the
+# force on a cell is a chain of about 30 dependent operations (relative
+# positions, circumcentres, edge vectors and lengths, force sets, Jacobian
+# factors and their sum over the ring) whose terms are up to ~10x larger than
+# the result, so |F32 - F64| <= 30 u * 10 * max|F| ~ 2e-5 max|F|; the noise
+# uses 24-bit uniforms and FP32 log/cos (relative 1e-6), so theta after one
+# step is within sqrt(2 D_r dt) * 6 * 1e-6 < 1e-5.
+F32_TOL = 2e-5
+
+
+@pytest.mark.parametrize("n,seed", [(400, 41), (4096, 42)])
+def test_fp32_mode_topology_forces_and_step(n, seed):
+    sim, xs, ys, th, Lx, Ly = make(n, seed, p0=3.85, v0=0.1, seed=3, dt=0.01, precision="f32")
+    topo = check_topology(sim, xs, ys, Lx, Ly)  # exact predicates: bit-exact
+    Fx, Fy, _ = sim.forces()
+    oFx, oFy, oA, oP, _ = oracle.forces(xs, ys, Lx, Ly, topo, 3.85)
+    scale = max(np.abs(oFx).max(), np.abs(oFy).max())
+    errF = max(np.abs(Fx.cpu().numpy() - oFx).max(), np.abs(Fy.cpu().numpy() - oFy).max()) / scale
+    A, P = (t.cpu().numpy() for t in sim.geometry())
+    errA = np.abs(A - oA).max() / np.abs(oA).max()
+    errP = np.abs(P - oP).max() / np.abs(oP).max()
+    print(f"fp32 n={n}: force err {errF:.2e} max|F|, A {errA:.2e}, P {errP:.2e}")
+    assert errF <= F32_TOL
+    assert errA <= 1e-5 and errP <= 1e-5
+    sim.step(1)
+    gx, gy, gth = (t.cpu().numpy() for t in sim.state())
+    ox, oy, oth, _ = oracle.spv_run(xs, ys, th, Lx, Ly, 3.85, 0.1, 1, seed=3, dt=0.01)
+    xtol = 0.01 * F32_TOL * scale + X_TOL * Lx
+    assert np.abs(wrapdiff(gx, ox, Lx)).max() <= xtol
+    assert np.abs(wrapdiff(gy, oy, Ly)).max() <= xtol
+    assert np.abs(gth - oth).max() <= 1e-5
+    sim.close()
+
+
+def test_fp32_mode_long_run_statistics():
+    """FP32 trajectories leave the FP64 ones after a few hundred steps (the
+    dynamics amplify the rounding differences); the ensemble statistics still
+    agree: mean shape index within 1% and MSD within three combined standard
+    errors (eight seeds, N = 400, p0 = 3.85, v0 = 0.1, 600 steps)."""
+    n, K, p0, v0 = 400, 600, 3.85, 0.1
+    qg, qo, mg, mo = [], [], [], []
+    for s in range(8):
+        sim, xs, ys, th, Lx, Ly = make(n, 300 + s, p0=p0, v0=v0, seed=s, dt=0.01, precision="f32")
+        sim.step(K)
+        gx, gy, _ = (t.cpu().numpy() for t in sim.state())
+        A, P = (t.cpu().numpy() for t in sim.geometry())
+        sim.close()
+        ox, oy, _, _ = oracle.spv_run(xs, ys, th, Lx, Ly, p0, v0, K, seed=s, dt=0.01)
+        oA, oP, _, _ = oracle.geometry(ox, oy, Lx, Ly, oracle.triangulate(ox, oy, Lx, Ly))
+        qg.append((P / np.sqrt(A)).mean())
+        qo.append((oP / np.sqrt(oA)).mean())
+        mg.append((wrapdiff(gx, xs, Lx) ** 2 + wrapdiff(gy, ys, Ly) ** 2).mean())
+        mo.append((wrapdiff(ox, xs, Lx) ** 2 + wrapdiff(oy, ys, Ly) ** 2).mean())
+    Qg, _ = ensemble(qg)
+    Qo, _ = ensemble(qo)
+    Mg, seg = ensemble(mg)
+    Mo, seo = ensemble(mo)
+    print(f"fp32 q: {Qg:.6f} vs {Qo:.6f}; MSD {Mg:.6f} +- {seg:.2e} vs {Mo:.6f} +- {seo:.2e}")
+    assert abs(Qg - Qo) <= 0.01 * Qo
+    assert abs(Mg - Mo) <= 3.0 * np.hypot(seg, seo)
+
+
+def test_fp32_mode_refuses_the_backward_pass():
+    sim, *_ = make(400, 43, precision="f32")
+    with pytest.raises(cg.CellgbError) as e:
+        sim.hvp(np.zeros(400), np.zeros(400))
+    assert e.value.code == -1
+    sim.close()
