@@ -212,17 +212,21 @@ int64_t cg_num_cells(const cg_ctx* ctx);
 int cg_get_launch(const cg_ctx* ctx, cg_launch* out);
 /* Sets the launch shapes and recaptures the step graph.  Synchronizes. */
 int cg_set_launch(cg_ctx* ctx, const cg_launch* launch);
-/* Scratch needed by cg_autotune: a second workspace plus the saved state. */
-int cg_autotune_bytes(const cg_ctx* ctx, size_t* bytes);
+/* Scratch needed by cg_autotune: a second workspace, the saved state and an
+ * optional L2-flush region of flush_bytes. */
+int cg_autotune_bytes(const cg_ctx* ctx, size_t flush_bytes, size_t* bytes);
 /* Picks the launch shapes by timing candidates (coordinate descent over the
- * four fields, two sweeps) on a temporary copy of the context built in d_ws2
- * (device, >= cg_autotune_bytes, 256-byte aligned) from the current state,
- * directors, step counter, p0 and v0: each trial restores that state, runs 2
- * untimed and steps_per_trial timed graph steps (CUDA events).  The context
- * itself takes no step; it gets the fastest shapes (graph recaptured).
- * best (may be NULL) receives them, best_ms the time per step.  Synchronizes. */
-int cg_autotune(cg_ctx* ctx, int32_t steps_per_trial, void* d_ws2, size_t ws2_bytes, cg_launch* best,
-                double* best_ms);
+ * five fields, two sweeps) on a temporary copy of the context built in d_ws2
+ * (device, >= cg_autotune_bytes(ctx, flush_bytes), 256-byte aligned) from the
+ * current state, directors, step counter, p0 and v0: each trial restores that
+ * state, runs 2 untimed and steps_per_trial timed graph steps (CUDA events).
+ * With flush_bytes > 0 (more than the L2 size, e.g. 256 MB) every timed step
+ * starts after a write of that many bytes and is timed alone, as a
+ * benchmark with a cold L2 times it.  The context itself takes no step; it gets
+ * the fastest shapes (graph recaptured).  best (may be NULL) receives them,
+ * best_ms the time per step.  Synchronizes. */
+int cg_autotune(cg_ctx* ctx, int32_t steps_per_trial, size_t flush_bytes, void* d_ws2, size_t ws2_bytes,
+                cg_launch* best, double* best_ms);
 
 /* Allocation-free triangulation, for callers that cannot call cudaMalloc
  * (code running under a fixed device memory pool, inside another runtime's

@@ -110,8 +110,8 @@ def lib():
             getattr(L, name).restype = C.c_int
         L.cg_get_launch.argtypes = [vp, C.POINTER(cg_launch)]
         L.cg_set_launch.argtypes = [vp, C.POINTER(cg_launch)]
-        L.cg_autotune_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
-        L.cg_autotune.argtypes = [vp, i32, vp, C.c_size_t, C.POINTER(cg_launch), C.POINTER(C.c_double)]
+        L.cg_autotune_bytes.argtypes = [vp, C.c_size_t, C.POINTER(C.c_size_t)]
+        L.cg_autotune.argtypes = [vp, i32, C.c_size_t, vp, C.c_size_t, C.POINTER(cg_launch), C.POINTER(C.c_double)]
         for name in ("cg_get_launch", "cg_set_launch", "cg_autotune_bytes", "cg_autotune"):
             getattr(L, name).restype = C.c_int
         # active vertex model
@@ -288,16 +288,16 @@ def cg_set_launch(ctx, launch):
     _check(lib().cg_set_launch(ctx, C.byref(cg_launch(**launch))), ctx)
 
 
-def cg_autotune_bytes(ctx):
+def cg_autotune_bytes(ctx, flush_bytes=0):
     out = C.c_size_t(0)
-    _check(lib().cg_autotune_bytes(ctx, C.byref(out)), ctx)
+    _check(lib().cg_autotune_bytes(ctx, int(flush_bytes), C.byref(out)), ctx)
     return out.value
 
 
-def cg_autotune(ctx, steps_per_trial, scratch):
+def cg_autotune(ctx, steps_per_trial, flush_bytes, scratch):
     best, ms = cg_launch(), C.c_double(0.0)
-    _check(lib().cg_autotune(ctx, int(steps_per_trial), _ptr(scratch), scratch.numel(), C.byref(best),
-                             C.byref(ms)), ctx)
+    _check(lib().cg_autotune(ctx, int(steps_per_trial), int(flush_bytes), _ptr(scratch), scratch.numel(),
+                             C.byref(best), C.byref(ms)), ctx)
     return {k: getattr(best, k) for k, _ in cg_launch._fields_ if k != "reserved"}, ms.value
 
 
@@ -400,12 +400,13 @@ class SPV:
         cur.update(launch)
         cg_set_launch(self.ctx, cur)
 
-    def autotune(self, steps_per_trial=10):
+    def autotune(self, steps_per_trial=10, flush_bytes=0):
         """Times candidate launch shapes on a temporary copy of the current
-        state and keeps the fastest; the simulation itself takes no step."""
+        state and keeps the fastest; the simulation itself takes no step.
+        flush_bytes > 0 times every step after an L2-evicting write."""
         t = self.torch
-        scratch = t.empty(cg_autotune_bytes(self.ctx), dtype=t.uint8, device=self.device)
-        best, ms = cg_autotune(self.ctx, steps_per_trial, scratch)
+        scratch = t.empty(cg_autotune_bytes(self.ctx, flush_bytes), dtype=t.uint8, device=self.device)
+        best, ms = cg_autotune(self.ctx, steps_per_trial, flush_bytes, scratch)
         del scratch
         return best, ms
 

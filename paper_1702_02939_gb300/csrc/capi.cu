@@ -1005,17 +1005,17 @@ int cg_set_launch(cg_ctx* c, const cg_launch* l) {
   return build_graph(c);
 }
 
-int cg_autotune_bytes(const cg_ctx* c, size_t* bytes) {
+int cg_autotune_bytes(const cg_ctx* c, size_t flush_bytes, size_t* bytes) {
   if (!c || !bytes) return CG_EINVAL;
-  *bytes = c->off.total + ((5 * (size_t)c->N * sizeof(double) + 255) & ~(size_t)255);
+  *bytes = c->off.total + ((5 * (size_t)c->N * sizeof(double) + 255) & ~(size_t)255) + flush_bytes;
   return CG_OK;
 }
 
-int cg_autotune(cg_ctx* c, int32_t steps_per_trial, void* d_ws2, size_t ws2_bytes, cg_launch* best,
-                double* best_ms) {
+int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_ws2, size_t ws2_bytes,
+                cg_launch* best, double* best_ms) {
   if (!c || steps_per_trial < 1 || !d_ws2 || ((uintptr_t)d_ws2 & 255)) return CG_EINVAL;
   size_t need = 0;
-  cg_autotune_bytes(c, &need);
+  cg_autotune_bytes(c, flush_bytes, &need);
   if (ws2_bytes < need) return CG_EINVAL;
   int rc = read_status(c);
   if (rc) return rc;
@@ -1026,6 +1026,7 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, void* d_ws2, size_t ws2_byte
   double* sth = sy + c->N;
   double* sp0 = sth + c->N;
   double* sv0 = sp0 + c->N;
+  char* flush = base + c->off.total + ((5 * (size_t)c->N * sizeof(double) + 255) & ~(size_t)255);
   if ((rc = cg_get_state(c, sx, sy, sth))) return rc;
   const int* tag = c->at<int>(c->off.tag);
   launch_gather_d((int)c->N, tag, c->at<double>(c->off.p0), sp0, c->stream);
@@ -1047,13 +1048,27 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, void* d_ws2, size_t ws2_byte
     if (!r) r = cg_set_step(t, h.step);
     if (!r) r = cg_step(t, 2);
     if (r) return r;
-    cudaEventRecord(e0, t->stream);
-    r = cg_step(t, steps_per_trial);
-    cudaEventRecord(e1, t->stream);
-    if (!r) r = read_status(t);
-    float f = 0.f;
-    cudaEventElapsedTime(&f, e0, e1);
-    ms = f / steps_per_trial;
+    float total = 0.f;
+    if (flush_bytes == 0) {
+      cudaEventRecord(e0, t->stream);
+      r = cg_step(t, steps_per_trial);
+      cudaEventRecord(e1, t->stream);
+      if (!r) r = read_status(t);
+      cudaEventElapsedTime(&total, e0, e1);
+    } else {
+      for (int k = 0; k < steps_per_trial && !r; ++k) {
+        cudaMemsetAsync(flush, k & 0xff, flush_bytes, t->stream);  // evicts the L2
+        cudaEventRecord(e0, t->stream);
+        r = cg_step(t, 1);
+        cudaEventRecord(e1, t->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) r = fail(c, CG_ECUDA, "autotune sync");
+        float f = 0.f;
+        cudaEventElapsedTime(&f, e0, e1);
+        total += f;
+      }
+      if (!r) r = read_status(t);
+    }
+    ms = total / steps_per_trial;
     return r;
   };
   static const int repair_opts[] = {2, 4, 8, 16};

@@ -285,6 +285,40 @@ __device__ __forceinline__ int incircle_sign(long long px, long long py, long lo
   }
 }
 
+// incircle_sign(0, q, r, s) with the float values of q, r, s (real units,
+// converted once by the caller) for the filter: translating the lifted
+// determinant to the first point instead of the last only flips its sign,
+// det3(q, r, s) = -det3(0 - s, q - s, r - s).  The filter bound is the one of
+// incircle_sign; an inconclusive filter defers to incircle_sign itself, so
+// every decision (ties included) is the same.
+__device__ __forceinline__ int incircle0_sign(float fqx, float fqy, float frx, float fry, float fsx, float fsy,
+                                              long long qx, long long qy, long long rx, long long ry, long long sx,
+                                              long long sy, int kp, int kq, int kr, int ks, float sc) {
+  float la = fqx * fqx + fqy * fqy, lb = frx * frx + fry * fry, lc = fsx * fsx + fsy * fsy;
+  float t1 = frx * fsy, t2 = fry * fsx, t3 = fsx * fqy, t4 = fsy * fqx, t5 = fqx * fry, t6 = fqy * frx;
+  float det = la * (t1 - t2) + lb * (t3 - t4) + lc * (t5 - t6);
+  float perm = la * (fabsf(t1) + fabsf(t2)) + lb * (fabsf(t3) + fabsf(t4)) + lc * (fabsf(t5) + fabsf(t6));
+  float bound = 2.0e-6f * perm;
+  if (bound > 1.0e-30f && bound < 1.0e30f) {
+    if (det > bound) return -1;
+    if (det < -bound) return 1;
+  }
+  return incircle_sign(0, 0, qx, qy, rx, ry, sx, sy, kp, kq, kr, ks, sc);
+}
+
+// orient_sign(a, b) with the float values of a and b converted by the caller.
+__device__ __forceinline__ int orient0_sign(float fax, float fay, float fbx, float fby, long long ax, long long ay,
+                                            long long bx, long long by) {
+  float l = fax * fby, r = fay * fbx;
+  float det = l - r;
+  float bound = 1.0e-6f * (fabsf(l) + fabsf(r));
+  if (bound > 1.0e-30f) {
+    if (det > bound) return 1;
+    if (det < -bound) return -1;
+  }
+  return orient_exact(ax, ay, bx, by);
+}
+
 // ----------------------------------------------------------------------------
 // Shared by the FP64 and FP32 step kernels.
 // ----------------------------------------------------------------------------
@@ -293,14 +327,27 @@ __device__ __forceinline__ int incircle_sign(long long px, long long py, long lo
 // [-L, 2L) fmod is a single exact subtraction or nothing.
 __device__ __forceinline__ long long wrap_to_grid(double v, double L, double scale, long long LI) {
   double r;
-  if (v >= 0.0 && v < L) r = v;
+  // the common case 0 <= v < L decided on the integer pipe (non-negative
+  // doubles order like their bit patterns; -0 and NaN fail it)
+  if ((unsigned long long)__double_as_longlong(v) < (unsigned long long)__double_as_longlong(L)) r = v;
   else if (v >= L && v < 2.0 * L) r = v - L;
   else if (v < 0.0 && v >= -L) r = v;
   else r = fmod(v, L);
-  long long X = (long long)rint(r * scale);
+  // rint(r * scale) for |r * scale| < 2^51 (scale is a power of two, so the
+  // product is exact): adding 1.5 * 2^52 rounds to the nearest integer, ties to
+  // even, and leaves it in the low bits
+  const long long X0 = __double_as_longlong(r * scale + 0x1.8p52) - 0x4338000000000000LL;
+  long long X = X0;
   if (X < 0) X += LI;
   else if (X >= LI) X -= LI;
   return X;
+}
+
+// Exact int64 -> double for |v| < 2^51: v added to the bit pattern of 1.5 * 2^52
+// (integer pipe) lands in [2^52, 2^53) where doubles are spaced by one; one
+// FP64 subtraction removes the offset.
+__device__ __forceinline__ double i2d_exact(long long v) {
+  return __longlong_as_double(0x4338000000000000LL + v) - 0x1.8p52;
 }
 
 // Position of cell i in the ring of cell j, or -1.

@@ -19,13 +19,6 @@
 
 namespace cgk {
 
-// Exact int64 -> double for |v| < 2^51: v added to the bit pattern of 1.5 * 2^52
-// (integer pipe) lands in [2^52, 2^53) where doubles are spaced by one; one
-// FP64 subtraction removes the offset.
-__device__ __forceinline__ double i2d_exact(long long v) {
-  return __longlong_as_double(0x4338000000000000LL + v) - 0x1.8p52;
-}
-
 // 1/d to ~1 ulp: hardware reciprocal approximation refined by two Newton steps
 // (each squares the relative error), 4 FP64 FMAs instead of an IEEE division.
 __device__ __forceinline__ double fast_rcp(double d) {
@@ -208,8 +201,8 @@ __global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
     Y = (long long)rint(yi * R.scale);
   }
   const int nxt = cur ^ 1;
-  g.x[(size_t)nxt * N + i] = (double)X * R.inv_scale;
-  g.y[(size_t)nxt * N + i] = (double)Y * R.inv_scale;
+  g.x[(size_t)nxt * N + i] = i2d_exact(X) * R.inv_scale;
+  g.y[(size_t)nxt * N + i] = i2d_exact(Y) * R.inv_scale;
   g.X[(size_t)nxt * N + i] = X;
   g.Y[(size_t)nxt * N + i] = Y;
   g.theta[i] = th + g.noise_amp * g.xi[i];
@@ -273,27 +266,34 @@ __global__ void __launch_bounds__(kTestThreads) k_test(TestArgs g) {
   }
   const int* ring = g.nbr + (size_t)i * CG_RING;
   const int ti = g.tag[i];
-  // sliding window over (j_{a-1}, j_a, j_{a+1})
+  // sliding window over (j_{a-1}, j_a, j_{a+1}): grid offsets (exact) and
+  // their float values, each converted once
   int jp = ring[m - 1], ja = ring[0];
   long long pX = min_image_i(X[jp] - Xi, R.LX), pY = min_image_i(Y[jp] - Yi, R.LY);
   long long aX = min_image_i(X[ja] - Xi, R.LX), aY = min_image_i(Y[ja] - Yi, R.LY);
+  float fpx = i2f_scaled(pX, sc), fpy = i2f_scaled(pY, sc);
+  float fax = i2f_scaled(aX, sc), fay = i2f_scaled(aY, sc);
   const long long fX = aX, fY = aY;
+  const float ffx = fax, ffy = fay;
   const int jfirst = ja;
   int tp = g.tag[jp], ta = g.tag[ja];
   for (int a = 0; a < m; ++a) {
     int jn;
     long long nX, nY;
+    float fnx, fny;
     if (a + 1 < m) {
       jn = ring[a + 1];
       nX = min_image_i(X[jn] - Xi, R.LX);
       nY = min_image_i(Y[jn] - Yi, R.LY);
+      fnx = i2f_scaled(nX, sc);
+      fny = i2f_scaled(nY, sc);
     } else {
-      jn = jfirst; nX = fX; nY = fY;
+      jn = jfirst; nX = fX; nY = fY; fnx = ffx; fny = ffy;
     }
     const int tn = g.tag[jn];
     if (i < ja) {
       // triangle (i, j_{a-1}, j_a) CCW; j_{a+1} must be outside its circle
-      int s = incircle_sign(0, 0, pX, pY, aX, aY, nX, nY, ti, tp, ta, tn, sc);
+      int s = incircle0_sign(fpx, fpy, fax, fay, fnx, fny, pX, pY, aX, aY, nX, nY, ti, tp, ta, tn, sc);
       if (s > 0) {
         flag_cell(g.flags, g.list, &g.ctl->count[0], i);
         flag_cell(g.flags, g.list, &g.ctl->count[0], jp);
@@ -302,14 +302,14 @@ __global__ void __launch_bounds__(kTestThreads) k_test(TestArgs g) {
       }
     }
     if (i < ja && i < jn) {
-      if (orient_sign(aX, aY, nX, nY, sc) <= 0) {
+      if (orient0_sign(fax, fay, fnx, fny, aX, aY, nX, nY) <= 0) {
         flag_cell(g.flags, g.list, &g.ctl->count[0], i);
         flag_cell(g.flags, g.list, &g.ctl->count[0], ja);
         flag_cell(g.flags, g.list, &g.ctl->count[0], jn);
       }
     }
-    jp = ja; pX = aX; pY = aY; tp = ta;
-    ja = jn; aX = nX; aY = nY; ta = tn;
+    jp = ja; pX = aX; pY = aY; tp = ta; fpx = fax; fpy = fay;
+    ja = jn; aX = nX; aY = nY; ta = tn; fax = fnx; fay = fny;
   }
 }
 

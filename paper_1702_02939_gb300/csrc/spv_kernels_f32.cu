@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(kForceThreads) k_force_f32(ForceArgs g) {
     Yn = (long long)rint(yi * R.scale);
   }
   const int nxt = cur ^ 1;
-  g.x[(size_t)nxt * N + i] = (double)Xn * R.inv_scale;
-  g.y[(size_t)nxt * N + i] = (double)Yn * R.inv_scale;
+  g.x[(size_t)nxt * N + i] = i2d_exact(Xn) * R.inv_scale;
+  g.y[(size_t)nxt * N + i] = i2d_exact(Yn) * R.inv_scale;
   g.X[(size_t)nxt * N + i] = Xn;
   g.Y[(size_t)nxt * N + i] = Yn;
   g.theta[i] = g.theta[i] + g.noise_amp * g.xi[i];

@@ -455,10 +455,15 @@ void launch_repair(const RepairArgs& a, int grid_blocks, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool in_ring(const int* nbr, const int* cnt, int j, int i) {
   const int mj = cnt[j];
-  const int* row = nbr + (size_t)j * CG_RING;
-  for (int a = 0; a < mj; ++a)
-    if (row[a] == i) return true;
-  return false;
+  const int4* row = reinterpret_cast<const int4*>(nbr + (size_t)j * CG_RING);
+  bool found = false;
+#pragma unroll
+  for (int q = 0; q < CG_RING / 4; ++q) {
+    const int4 v = row[q];
+    found |= (v.x == i && 4 * q + 0 < mj) || (v.y == i && 4 * q + 1 < mj) || (v.z == i && 4 * q + 2 < mj) ||
+             (v.w == i && 4 * q + 3 < mj);
+  }
+  return found;
 }
 
 __device__ __forceinline__ void flag_into(unsigned* flags, int* list, int* count, int c) {
@@ -467,6 +472,9 @@ __device__ __forceinline__ void flag_into(unsigned* flags, int* list, int* count
   if (!(old & bit)) list[atomicAdd(count, 1)] = c;
 }
 
+// One warp per listed cell i: lanes 0-15 take the entries of i's new ring
+// (j must list i), lanes 16-31 those of its old ring (a neighbour i dropped
+// must have dropped i too).  Every lookup of a ring row runs in parallel.
 __global__ void k_check(CheckArgs g) {
   const int which_in = g.dyn ? (g.ctl->round_count & 1) : g.which_in;
   const int which_out = which_in ^ 1;
@@ -474,31 +482,33 @@ __global__ void k_check(CheckArgs g) {
   int* list_out = g.dyn ? (which_out ? g.lists[1] : g.lists[0]) : g.list_out;
   const int total = g.all_cells ? g.n : g.ctl->count[which_in];
   int* count_out = &g.ctl->count[which_out];
-  for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31, a = lane & 15;
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int item = warp; item < total; item += nwarps) {  // warp-uniform
     const int i = g.all_cells ? item : list_in[item];
     const int m = g.cnt[i];
-    const int* row = g.nbr + (size_t)i * CG_RING;
-    bool bad = false;
-    for (int a = 0; a < m; ++a) {
-      const int j = row[a];
-      if (!in_ring(g.nbr, g.cnt, j, i)) {
-        flag_into(g.flags, list_out, count_out, j);
-        bad = true;
-      }
+    const int rj = (lane < 16 && a < m) ? g.nbr[(size_t)i * CG_RING + a] : -1;  // new ring of i
+    int j = -1;
+    bool mine = false;
+    if (lane < 16) {
+      j = rj;
+      mine = a < m;
+    } else if (a < g.old_cnt[i]) {
+      j = g.old_nbr[(size_t)i * CG_RING + a];
+      mine = j >= 0 && j < g.n;
     }
-    const int om = g.old_cnt[i];
-    const int* orow = g.old_nbr + (size_t)i * CG_RING;
-    for (int b = 0; b < om; ++b) {
-      const int j = orow[b];
-      if (j < 0 || j >= g.n) continue;
-      bool kept = false;
-      for (int a = 0; a < m; ++a) kept |= (row[a] == j);
-      if (!kept && in_ring(g.nbr, g.cnt, j, i)) {
-        flag_into(g.flags, list_out, count_out, j);
-        bad = true;
-      }
+    bool kept = false;  // j still in the new ring of i
+#pragma unroll
+    for (int b = 0; b < 16; ++b) kept |= (__shfl_sync(0xffffffffu, rj, b) == j);
+    bool flag = false;
+    if (mine) {
+      const bool lists_i = in_ring(g.nbr, g.cnt, j, i);
+      flag = (lane < 16) ? !lists_i : (!kept && lists_i);
     }
-    if (bad && g.last_round && !g.dyn) raise_status(g.ctl, kEREPAIR_CAP);
+    if (flag) flag_into(g.flags, list_out, count_out, j);
+    const bool bad = __any_sync(0xffffffffu, flag);
+    if (bad && g.last_round && !g.dyn && lane == 0) raise_status(g.ctl, kEREPAIR_CAP);
   }
   if (!g.dyn) return;  // uniform over the grid
   if (last_block(&g.ctl->done) && threadIdx.x == 0) {
