@@ -147,7 +147,8 @@ __device__ __forceinline__ double director_noise(unsigned long long seed, int ta
                                  (unsigned)((unsigned long long)step >> 32), 0u),
                       make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
   double u1 = unit53(r.x, r.y), u2 = unit53(r.z, r.w);
-  return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+  // cos(2 pi u2) as cospi(2 u2): 2 u2 is exact and the reduction by pi is exact
+  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
 }
 
 // ----------------------------------------------------------------------------
