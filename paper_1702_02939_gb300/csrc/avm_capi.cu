@@ -262,6 +262,8 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
   *out = nullptr;
   if (!par || !x || !y || !theta || !d_ws || ((uintptr_t)d_ws & 255) || n < 16) return CG_EINVAL;
   if (!(par->dt > 0) || !(par->A0 > 0) || !(par->t1_threshold >= 0)) return CG_EINVAL;
+  for (double v : {par->A0, par->KA, par->KP, par->mu, par->Dr, par->dt, par->t1_threshold, par->t1_length, p0, v0})
+    if (!std::isfinite(v)) return CG_EINVAL;
   size_t need = 0;
   int rc = cg_avm_workspace_bytes(n, Lx, Ly, &need);
   if (rc) return rc;
@@ -328,6 +330,7 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
     launch_avm_shadow(avm_args(c), st);
     rc = copy_in(c, c->at<double>(c->off.theta), theta, n * sizeof(double));
     if (rc) break;
+    launch_check_finite(n, c->at<double>(c->off.theta), c->ctl(), st);
     launch_fill_d(n, p0, c->at<double>(c->off.p0), st);
     launch_fill_d(n, v0, c->at<double>(c->off.v0), st);
     launch_fill_u64(n, ~0ull, c->at<unsigned long long>(c->off.lock), st);
@@ -430,6 +433,9 @@ int cg_avm_set_state(cg_avm_ctx* c, const double* hx, const double* hy, const do
   if ((rc = copy_in(c, c->at<double>(c->off.hx) + h.cur * V, hx, V * sizeof(double)))) return rc;
   if ((rc = copy_in(c, c->at<double>(c->off.hy) + h.cur * V, hy, V * sizeof(double)))) return rc;
   if ((rc = copy_in(c, c->at<double>(c->off.theta), theta, c->n * sizeof(double)))) return rc;
+  if (theta) launch_check_finite(c->n, c->at<double>(c->off.theta), c->ctl(), c->stream);
+  launch_check_finite(c->V, c->at<double>(c->off.hx) + h.cur * V, c->ctl(), c->stream);
+  launch_check_finite(c->V, c->at<double>(c->off.hy) + h.cur * V, c->ctl(), c->stream);
   if ((rc = copy_in(c, c->at<int>(c->off.vc), vc, 3 * V * sizeof(int)))) return rc;
   if ((rc = copy_in(c, c->at<int>(c->off.vn), vn, 3 * V * sizeof(int)))) return rc;
   if ((rc = copy_in(c, c->at<int>(c->off.cc), cc, c->n * sizeof(int)))) return rc;
@@ -475,13 +481,17 @@ int cg_avm_t1(cg_avm_ctx* c) {
 int cg_avm_set_p0(cg_avm_ctx* c, const double* p0) {
   if (!c || !p0) return CG_EINVAL;
   int rc = copy_in(c, c->at<double>(c->off.p0), p0, c->n * sizeof(double));
-  return rc ? rc : avm_status(c);
+  if (rc) return rc;
+  launch_check_finite(c->n, c->at<double>(c->off.p0), c->ctl(), c->stream);
+  return avm_status(c);
 }
 
 int cg_avm_set_v0(cg_avm_ctx* c, const double* v0) {
   if (!c || !v0) return CG_EINVAL;
   int rc = copy_in(c, c->at<double>(c->off.v0), v0, c->n * sizeof(double));
-  return rc ? rc : avm_status(c);
+  if (rc) return rc;
+  launch_check_finite(c->n, c->at<double>(c->off.v0), c->ctl(), c->stream);
+  return avm_status(c);
 }
 
 int cg_avm_get_counters(cg_avm_ctx* c, cg_counters* out) {

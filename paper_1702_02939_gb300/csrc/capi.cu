@@ -683,6 +683,8 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
   if (R <= 0 || !reps || !params || !x || !y || !theta || !d_ws) return CG_EINVAL;
   if (((uintptr_t)d_ws & 255) != 0) return CG_EINVAL;
   if (!(params->dt > 0) || !(params->mu >= 0) || !(params->Dr >= 0) || !(params->A0 > 0)) return CG_EINVAL;
+  for (double v : {params->A0, params->KA, params->KP, params->mu, params->Dr, params->dt})
+    if (!std::isfinite(v)) return CG_EINVAL;
   cg_ctx* c = new (std::nothrow) cg_ctx();
   if (!c) return CG_EINVAL;
   std::string err;
@@ -746,6 +748,7 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
 #undef TRY
     if (rc) break;
     launch_scatter_d((int)c->N, c->at<int>(c->off.tag), c->at<double>(c->off.tmp), c->at<double>(c->off.theta), st);
+    launch_check_finite((int)c->N, c->at<double>(c->off.theta), c->ctl(), st);
     rc = load_positions(c, x, y);
     if (rc) break;
     launch_sort(sort_args(c), st);  // spatial order before the first triangulation
@@ -860,6 +863,7 @@ int cg_set_state(cg_ctx* c, const double* x, const double* y, const double* thet
                                c->stream));
     launch_scatter_d((int)c->N, c->at<int>(c->off.tag), c->at<double>(c->off.tmp), c->at<double>(c->off.theta),
                      c->stream);
+    launch_check_finite((int)c->N, c->at<double>(c->off.theta), c->ctl(), c->stream);
   }
   rc = load_positions(c, x, y);
   if (rc) return rc;
@@ -930,6 +934,7 @@ static int set_percell(cg_ctx* c, const double* src, size_t off) {
   double* tmp = c->at<double>(c->off.tmp);
   CG_CUDA(c, cudaMemcpyAsync(tmp, src, c->N * sizeof(double), cudaMemcpyDefault, c->stream));
   launch_scatter_d((int)c->N, c->at<int>(c->off.tag), tmp, c->at<double>(off), c->stream);
+  launch_check_finite((int)c->N, c->at<double>(off), c->ctl(), c->stream);
   CG_CUDA(c, cudaStreamSynchronize(c->stream));
   return read_status(c);
 }

@@ -155,6 +155,7 @@ void launch_check(const CheckArgs& a, int grid_blocks, cudaStream_t st);
 void launch_snap(int n, const Rep* reps, const int* rep, const double* xin, const double* yin, double* x,
                  double* y, long long* X, long long* Y, Ctl* ctl, cudaStream_t st);
 void launch_gather_d(int n, const int* tag, const double* src, double* dst_user, cudaStream_t st);
+void launch_check_finite(int n, const double* v, Ctl* ctl, cudaStream_t st);
 void launch_scatter_d(int n, const int* tag, const double* src_user, double* dst, cudaStream_t st);
 void launch_gather_ring(int n, const int* tag, const int* cnt, const int* nbr, int* cnt_user, int* nbr_user,
                         cudaStream_t st);

@@ -563,6 +563,15 @@ void launch_snap(int n, const Rep* reps, const int* rep, const double* xin, cons
   k_snap<<<(n + 255) / 256, 256, 0, st>>>(n, reps, rep, xin, yin, x, y, X, Y, ctl);
 }
 
+// Inputs handed in from outside must be finite (directors, p0, v0).
+__global__ void k_check_finite(int n, const double* v, Ctl* ctl) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !isfinite(v[i])) raise_status(ctl, kEINVAL);
+}
+void launch_check_finite(int n, const double* v, Ctl* ctl, cudaStream_t st) {
+  if (n > 0) k_check_finite<<<(n + 255) / 256, 256, 0, st>>>(n, v, ctl);
+}
+
 __global__ void k_gather_d(int n, const int* tag, const double* src, double* dst) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[tag[i]] = src[i];

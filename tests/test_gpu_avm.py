@@ -310,3 +310,26 @@ def test_long_run_ensemble_statistics_match_oracle():
     print(f"q: gpu {qg.mean():.6f} oracle {qo.mean():.6f}; MSD: gpu {mg.mean():.6f} oracle {mo.mean():.6f} se {se:.2e}")
     assert abs(qg.mean() - qo.mean()) <= 0.01 * qo.mean()
     assert abs(mg.mean() - mo.mean()) <= se
+
+
+def test_corrupted_network_is_refused():
+    """A network handed in with an out-of-range neighbour or a non-finite
+    position is refused with CG_EINVAL before any step uses it."""
+    n = 400
+    sim, xs, ys, th, Lx, Ly = make(n, 15)
+    net = oracle.avm_build(xs, ys, Lx, Ly)
+    vn = net.vn.copy()
+    vn[10] = 10 * net.V
+    with pytest.raises(cg.CellgbError) as e:
+        sim.set_state(net.hx, net.hy, th, net.vc, vn, net.cc, net.cv)
+    assert e.value.code == -1
+    with pytest.raises(cg.CellgbError):
+        sim.step(1)  # the context keeps the error: no step runs on it
+    sim.close()
+    sim, *_ = make(n, 15)
+    hx = net.hx.copy()
+    hx[3] = float("nan")
+    with pytest.raises(cg.CellgbError) as e:
+        sim.set_state(hx, net.hy, th, net.vc, net.vn, net.cc, net.cv)
+    assert e.value.code == -1
+    sim.close()

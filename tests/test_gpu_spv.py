@@ -438,3 +438,53 @@ def test_fp32_mode_refuses_the_backward_pass():
         sim.hvp(np.zeros(400), np.zeros(400))
     assert e.value.code == -1
     sim.close()
+
+
+def test_host_side_fault_injection_gives_clean_errors():
+    """Faults injected on the host come back as status codes, never as a
+    GPU fault: non-finite parameters or directors at creation, a non-finite
+    p0 later, a box too small for the Voronoi search."""
+    n = 64
+    x, y, th, L = workloads.spv_uniform(n, 2)
+    rep = [dict(n=n, Lx=L, Ly=L, p0=3.8, v0=0.05)]
+    with pytest.raises(cg.CellgbError) as e:
+        cg.SPV(rep, x, y, th, KA=float("nan"))
+    assert e.value.code == -1
+    bad = th.copy()
+    bad[5] = float("inf")
+    with pytest.raises(cg.CellgbError) as e:
+        cg.SPV(rep, x, y, bad)
+    assert e.value.code == -1
+    sim = cg.SPV(rep, x, y, th)
+    p0 = np.full(n, 3.8)
+    p0[7] = float("nan")
+    with pytest.raises(cg.CellgbError) as e:
+        sim.set_p0(p0)
+    assert e.value.code == -1
+    sim.close()
+    x16, y16, th16, L16 = workloads.spv_uniform(16, 1)
+    with pytest.raises(cg.CellgbError) as e:
+        cg.SPV([dict(n=16, Lx=L16, Ly=L16, p0=3.8, v0=0.05)], x16, y16, th16)
+    assert e.value.code == -7
+
+
+def test_checkpoint_and_resume_is_bit_identical():
+    """A run saved after 15 steps (positions, directors, p0, v0, step counter)
+    and resumed in a fresh context continues exactly like the uninterrupted
+    run: Philox noise is counter based and the topology is rebuilt exactly."""
+    n = 4096
+    a, xs, ys, th, Lx, Ly = make(n, 35, p0=3.85, v0=0.1, seed=9)
+    p0 = np.random.default_rng(4).uniform(3.7, 4.0, n)
+    a.set_p0(p0)
+    a.step(15)
+    x15, y15, th15 = a.state()
+    b = cg.SPV([dict(n=n, Lx=Lx, Ly=Ly, p0=3.85, v0=0.1)], x15, y15, th15, seed=9)
+    b.set_p0(p0)
+    b.set_step(15)
+    a.step(25)
+    b.step(25)
+    for ta, tb in zip(a.state() + a.neighbors(), b.state() + b.neighbors()):
+        assert torch.equal(ta, tb)
+    assert a.counters()["steps"] == b.counters()["steps"] == 40
+    a.close()
+    b.close()
