@@ -489,7 +489,53 @@ def sweep(args):
         cms = cpu_time(state, p0, 0.1, 0.01)
         rows.append({"regime": "p0 scan", "n": 65536, "p0": p0, "v0": 0.1, "dt": 0.01, "gpu_ms_per_step": ms,
                      "cpu_oracle_ms_per_step": cms, "speedup": cms / ms, "flagged_per_step": flagged})
-    print(json.dumps({"study": "SPV time per step vs N and p0 (GB300, FP64)", "rows": rows}), flush=True)
+    # Hilbert re-sort period (Sec. 2.B), fluid regime at N = 262144
+    sort_rows = []
+    for every in (0, 10, 50, 200):
+        x, y, th, L = workloads.spv_uniform(262144, 5)
+        sim = cg.SPV([dict(n=262144, Lx=L, Ly=L, p0=3.85, v0=0.1)], x, y, th, dt=0.01, seed=5, sort_every=every)
+        sim.step(100)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(400)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sim.sync()
+        sim.close()
+        sort_rows.append({"sort_every": every, "gpu_ms_per_step": e0.elapsed_time(e1) / 400})
+    # AVM time per step against N (Fig. 4), GPU and the AVM oracle
+    avm_rows = []
+    for n in (4096, 16384, 65536, 262144, 1048576):
+        x, y, th, L = workloads.spv_uniform(n, 7)
+        sim = cg.AVM(n, L, L, x, y, th, p0=3.8, v0=0.1, dt=0.01, t1_threshold=0.04, seed=7)
+        sim.step(50)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(200)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sim.sync()
+        sim.close()
+        gms = e0.elapsed_time(e1) / 200
+        cms = None
+        if n <= 262144:
+            Lx, Ly, q = oracle.box(L)
+            xs, ys = oracle.snap_positions(x, y, Lx, Ly)
+            net = oracle.avm_build(xs, ys, Lx, Ly)
+            oth, k, t0 = th, 0, time.perf_counter()
+            while True:
+                net, oth, _ = oracle.avm_step(net, oth, 3.8, 0.1, seed=7, step=k, thr=0.04)
+                k += 1
+                el = time.perf_counter() - t0
+                if el > 2.0 or k >= 50:
+                    break
+            cms = 1e3 * el / k
+        avm_rows.append({"n": n, "vertices": 2 * n, "gpu_ms_per_step": gms, "cpu_oracle_ms_per_step": cms,
+                         "ratio": (cms / gms) if cms else None})
+    print(json.dumps({"study": "SPV time per step vs N and p0, Hilbert re-sort period, AVM vs N (GB300, FP64)",
+                      "rows": rows, "sort_rows": sort_rows, "avm_rows": avm_rows}), flush=True)
 
 
 def run_reference(args):
