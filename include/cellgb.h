@@ -107,12 +107,12 @@ typedef struct cg_counters {
  * is the same for any valid setting. */
 typedef struct cg_launch {
   int32_t repair_blocks_per_sm;  /* repair-round grid = SMs x this (1..64, default 4) */
-  int32_t check_blocks_per_sm;   /* consistency-check grid = SMs x this (1..64, default 2) */
+  int32_t check_blocks_per_sm;   /* consistency-check grid = SMs x this (1..64, default 4) */
   int32_t dir_blocks_per_sm;     /* director branch grid = SMs x this; 0 = one thread per cell (default 2) */
   int32_t dir_low_priority;      /* 1: the low-priority branch (directors, next geometry) at the lowest
                                     stream priority, the rest at the highest (default 1) */
   int32_t geom_blocks_per_sm;    /* grid of the geometry pass beside the repair rounds = SMs x this;
-                                    0 = one thread per cell (default 4) */
+                                    0 = one thread per cell (default) */
   int32_t reserved;              /* 0 */
 } cg_launch;
 

@@ -180,7 +180,7 @@ struct cg_ctx {
   cudaStream_t capture = nullptr;   // private stream used for graph capture
   cudaStream_t side[2] = {nullptr, nullptr};  // branches of the captured step
   cudaEvent_t fork = nullptr, join_dir = nullptr, join_list = nullptr;
-  cg_launch launch{4, 2, 2, 1, 4, 0};          // launch shapes of the step graph
+  cg_launch launch{4, 4, 2, 1, 0, 0};          // launch shapes of the step graph
   std::vector<cg_replica> user_reps;           // as passed to cg_create
   cudaGraphExec_t step_exec = nullptr;
   int graph_steps = 0;
