@@ -333,3 +333,21 @@ def test_corrupted_network_is_refused():
         sim.set_state(hx, net.hy, th, net.vc, net.vn, net.cc, net.cv)
     assert e.value.code == -1
     sim.close()
+
+
+def test_rectangular_box():
+    """AVM in a 40 x 10 box: network build and one step equal the oracle."""
+    n, Lxr, Lyr = 400, 40.0, 10.0
+    x, y, th = workloads.spv_uniform_rect(n, 16, Lxr, Lyr)
+    Lx, Ly, q = oracle.box(Lxr, Lyr)
+    xs, ys = oracle.snap_positions(x, y, Lx, Ly)
+    sim = cg.AVM(n, Lxr, Lyr, xs, ys, th, t1_threshold=0.1, seed=3)
+    net = oracle.avm_build(xs, ys, Lx, Ly)
+    g, _ = gpu_net(sim, Lx, Ly)
+    assert_same_network(g, net)
+    load(sim, net, th)
+    sim.step(1)
+    g, gth = gpu_net(sim, Lx, Ly)
+    o, oth, _ = oracle.avm_step(net, th, 3.8, 0.1, seed=3, step=0, thr=0.1)
+    assert_same_network(g, o)
+    sim.close()

@@ -488,3 +488,29 @@ def test_checkpoint_and_resume_is_bit_identical():
     assert a.counters()["steps"] == b.counters()["steps"] == 40
     a.close()
     b.close()
+
+
+def test_rectangular_box():
+    """Lx != Ly (aspect 2.5): the minimum image and the cell list work per
+    axis; topology bit-exact, forces and one step within tolerance, and after
+    20 steps the maintained topology is the exact triangulation."""
+    n, Lxr, Lyr = 1000, 50.0, 20.0
+    x, y, th = workloads.spv_uniform_rect(n, 44, Lxr, Lyr)
+    Lx, Ly, q = oracle.box(Lxr, Lyr)
+    xs, ys = oracle.snap_positions(x, y, Lx, Ly)
+    sim = cg.SPV([dict(n=n, Lx=Lxr, Ly=Lyr, p0=3.85, v0=0.1)], xs, ys, th, seed=6)
+    topo = check_topology(sim, xs, ys, Lx, Ly)
+    Fx, Fy, _ = sim.forces()
+    oFx, oFy, *_ = oracle.forces(xs, ys, Lx, Ly, topo, 3.85)
+    scale = max(np.abs(oFx).max(), np.abs(oFy).max())
+    assert np.abs(Fx.cpu().numpy() - oFx).max() <= F_TOL * scale
+    assert np.abs(Fy.cpu().numpy() - oFy).max() <= F_TOL * scale
+    sim.step(1)
+    gx, gy, _ = (t.cpu().numpy() for t in sim.state())
+    ox, oy, _, _ = oracle.spv_run(xs, ys, th, Lx, Ly, 3.85, 0.1, 1, seed=6)
+    assert np.abs(wrapdiff(gx, ox, Lx)).max() <= X_TOL * Lx
+    assert np.abs(wrapdiff(gy, oy, Ly)).max() <= X_TOL * Ly
+    sim.step(20)
+    gx, gy, _ = (t.cpu().numpy() for t in sim.state())
+    check_topology(sim, gx, gy, Lx, Ly)
+    sim.close()

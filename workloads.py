@@ -24,6 +24,16 @@ def spv_uniform(n, seed, L=None):
     return x, y, theta, L
 
 
+def spv_uniform_rect(n, seed, Lx, Ly):
+    """Uniform random positions in [0, Lx) x [0, Ly) and directors uniform in
+    [0, 2 pi)."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0.0, Lx, n)
+    y = rng.uniform(0.0, Ly, n)
+    theta = rng.uniform(0.0, 2.0 * math.pi, n)
+    return x, y, theta
+
+
 def triangular_lattice(m_cols, m_rows, a=1.0, jitter=0.0, seed=0):
     """Regular triangular lattice (hexagonal Voronoi cells) of spacing a in a
     periodic box Lx = m_cols a, Ly = m_rows a sqrt(3)/2 (m_rows even)."""
