@@ -272,6 +272,14 @@ DirArgs dir_args(cg_ctx* c) {
   d.seed = c->par.seed;
   d.nrm = c->at<double2>(c->off.nrm);
   d.xi = c->at<double>(c->off.xi);
+  d.advance = 0;
+  d.noise_amp = std::sqrt(2.0 * c->par.Dr * c->par.dt);
+  return d;
+}
+
+DirArgs dir_args_step(cg_ctx* c) {
+  DirArgs d = dir_args(c);
+  d.advance = 1;
   return d;
 }
 
@@ -290,9 +298,6 @@ void run_dir(const cg_ctx* c, const DirArgs& a, cudaStream_t st, int blocks = 0)
   else launch_dir(a, st, blocks);
 }
 
-// Director terms of the next move for the current directors, step counter
-// and storage order (after anything that changes one of them).
-void refresh_directors(cg_ctx* c) { run_dir(c, dir_args(c), c->stream); }
 
 TestArgs test_args(cg_ctx* c) {
   TestArgs t{};  // every field starts zero or null
@@ -431,20 +436,20 @@ int repair_grid_all(const cg_ctx*) { return sm_count() * 16; }
 int check_grid_all(const cg_ctx* c) { return (int)((c->N + 255) / 256); }
 
 // One time step, enqueued on stream st (also used for capture).
-// One step up to the repair rounds, as captured into the step graph.  The
-// geometry and force sets of the current positions and rings are valid when
-// the step starts (they are computed at the end of the previous step, or by
-// prime_geometry): forces and move, then branches — the circumcircle test,
-// the cell-list build, and, at low priority, the director terms of the next
-// step followed by the geometry of the new positions, which overlaps the
-// latency-bound repair rounds (rings rewritten meanwhile are recomputed by
-// the fix-up after the rounds).
+// One step as captured into the step graph.  When a step starts, the move of
+// Eq. 3 from the current state is already computed (the "pending move", in
+// the other position buffer): the step makes it current, then runs three
+// branches — the circumcircle test, the cell-list build, and, at low
+// priority, the director terms (rotation by the previous noise, n(theta),
+// new noise) followed by the geometry and force sets of the new positions,
+// which overlaps the latency-bound repair rounds (rings rewritten meanwhile
+// are recomputed by the fix-up after the rounds) — and ends with the forces
+// and the next pending move, while the force sets are still in L2.
 void enqueue_step_prefix(cg_ctx* c, cudaStream_t st) {
-  run_force(c, force_args(c, 1), st);
   launch_begin_topology(c->ctl(), 1, st);
   cudaEventRecord(c->fork, st);
   cudaStreamWaitEvent(c->side[0], c->fork, 0);
-  run_dir(c, dir_args(c), c->side[0], dir_grid(c));
+  run_dir(c, dir_args_step(c), c->side[0], dir_grid(c));
   GeomArgs g = geom_args(c);
   g.tolerant = 1;
   run_geom(c, g, c->side[0], geom_grid(c));
@@ -457,7 +462,7 @@ void enqueue_step_prefix(cg_ctx* c, cudaStream_t st) {
 }
 
 // After the repair rounds and the concurrent geometry: the geometry of every
-// cell whose ring a round rewrote.
+// cell whose ring a round rewrote, then the forces and the next pending move.
 void enqueue_step_suffix(cg_ctx* c, cudaStream_t st) {
   cudaStreamWaitEvent(st, c->join_dir, 0);
   GeomArgs g = geom_args(c);
@@ -465,11 +470,17 @@ void enqueue_step_suffix(cg_ctx* c, cudaStream_t st) {
   g.list_count = &c->ctl()->dirty_count;
   g.list_bits = c->at<unsigned>(c->off.dirty_bits);
   run_geom(c, g, st, sm_count() * 2);
+  run_force(c, force_args(c, 1), st);
 }
 
-// Geometry and force sets of the current positions and rings (before the
-// first step and after anything outside a step changes their inputs).
-void prime_geometry(cg_ctx* c) { run_geom(c, geom_args(c), c->stream); }
+// Director terms, geometry, force sets and the pending move of the current
+// state (before the first step and after anything outside a step changes the
+// positions, directors, step counter, storage order, p0, v0 or the moduli).
+void prime(cg_ctx* c) {
+  run_dir(c, dir_args(c), c->stream);
+  run_geom(c, geom_args(c), c->stream);
+  run_force(c, force_args(c, 1), c->stream);
+}
 
 // One repair round (repair + consistency check) for a conditional loop node:
 // the round counter in the control word picks the lists.
@@ -615,8 +626,7 @@ void snapshot(cg_ctx* c, int save, const Snapshot& s) {
                   c->at<long long>(c->off.X), c->at<long long>(c->off.Y), c->at<double>(c->off.theta),
                   c->at<int>(c->off.cnt), c->at<int>(c->off.nbr), s, c->stream);
   if (!save) {  // positions, rings, directors and step counter were restored
-    refresh_directors(c);
-    prime_geometry(c);
+    prime(c);
   }
 }
 
@@ -758,8 +768,7 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
     }
     rc = triangulate_all(c);
     if (rc) break;
-    refresh_directors(c);
-    prime_geometry(c);
+    prime(c);
     rc = read_status(c);
     if (rc) break;
     rc = build_graph(c);
@@ -777,8 +786,7 @@ int cg_step(cg_ctx* c, int64_t nsteps) {
   for (int64_t s = 0; s < nsteps; ++s) {
     if (c->par.sort_every > 0 && c->host_step > 0 && c->host_step % c->par.sort_every == 0) {
       launch_sort(sort_args(c), c->stream);
-      refresh_directors(c);
-      prime_geometry(c);
+      prime(c);
     }
     CG_CUDA(c, cudaGraphLaunch(c->step_exec, c->stream));
     ++c->host_step;
@@ -795,25 +803,26 @@ int cg_profile_step(cg_ctx* c, int64_t nsteps, double* ms_out, int32_t n_out) {
   const int cap = c->par.repair_cap > 0 ? c->par.repair_cap : 4;
   const int grid = repair_grid(c);
   int rc = CG_OK;
-  // the order of the graph step: the geometry of the new state comes last
-  static const int kPhaseOfInterval[CG_NUM_PHASES] = {1, 2, 3, 4, 5, 0};
+  // the order of the graph step: the pending move becomes current, then the
+  // test, cell list, rounds, director terms, geometry, and the next move
+  static const int kPhaseOfInterval[CG_NUM_PHASES] = {2, 3, 4, 5, 0, 1};
   for (int64_t s = 0; s < nsteps && !rc; ++s) {
     cudaEventRecord(ev[0], st);
-    run_force(c, force_args(c, 1), st);
-    cudaEventRecord(ev[1], st);
     launch_begin_topology(c->ctl(), 1, st);
     launch_test(test_args(c), st);
-    cudaEventRecord(ev[2], st);
+    cudaEventRecord(ev[1], st);
     launch_cell_list(cell_list_args(c, 1), st);
-    cudaEventRecord(ev[3], st);
+    cudaEventRecord(ev[2], st);
     for (int r = 0; r < cap; ++r) {
       launch_repair(repair_args(c, r & 1, 0), grid, st);
       launch_check(check_args(c, r & 1, r == cap - 1, 0), check_grid(c), st);
     }
+    cudaEventRecord(ev[3], st);
+    run_dir(c, dir_args_step(c), st, dir_grid(c));
     cudaEventRecord(ev[4], st);
-    run_dir(c, dir_args(c), st, dir_grid(c));
-    cudaEventRecord(ev[5], st);
     run_geom(c, geom_args(c), st);
+    cudaEventRecord(ev[5], st);
+    run_force(c, force_args(c, 1), st);
     cudaEventRecord(ev[6], st);
     if (cudaEventSynchronize(ev[6]) != cudaSuccess) { rc = fail(c, CG_ECUDA, "profile sync"); break; }
     for (int k = 0; k < CG_NUM_PHASES; ++k) {
@@ -869,8 +878,7 @@ int cg_set_state(cg_ctx* c, const double* x, const double* y, const double* thet
   if (rc) return rc;
   rc = triangulate_all(c);
   if (rc) return rc;
-  refresh_directors(c);
-  prime_geometry(c);
+  prime(c);
   return read_status(c);
 }
 
@@ -943,10 +951,16 @@ int cg_set_p0(cg_ctx* c, const double* p0) {
   if (!c) return CG_EINVAL;
   int rc = set_percell(c, p0, c->off.p0);
   if (rc) return rc;
-  prime_geometry(c);  // the force sets depend on p0
+  prime(c);  // the force sets and the pending move depend on p0
   return read_status(c);
 }
-int cg_set_v0(cg_ctx* c, const double* v0) { return c ? set_percell(c, v0, c->off.v0) : CG_EINVAL; }
+int cg_set_v0(cg_ctx* c, const double* v0) {
+  if (!c) return CG_EINVAL;
+  int rc = set_percell(c, v0, c->off.v0);
+  if (rc) return rc;
+  prime(c);  // the pending move depends on v0
+  return read_status(c);
+}
 
 int cg_get_counters(cg_ctx* c, cg_counters* out) {
   if (!c || !out) return CG_EINVAL;
@@ -983,7 +997,7 @@ int cg_set_moduli(cg_ctx* c, double KA, double KP) {
   }
   rc = build_graph(c);
   if (rc) return rc;
-  prime_geometry(c);  // the force sets depend on the moduli
+  prime(c);  // the force sets and the pending move depend on the moduli
   return read_status(c);
 }
 
@@ -1045,7 +1059,7 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  auto trial = [&](const cg_launch& l, double& ms) -> int {
+  auto trial = [&](const cg_launch& l, int steps, double& ms) -> int {
     int r = cg_set_launch(t, &l);
     if (!r) r = cg_set_state(t, sx, sy, sth);
     if (!r) r = cg_set_p0(t, sp0);
@@ -1056,12 +1070,12 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
     float total = 0.f;
     if (flush_bytes == 0) {
       cudaEventRecord(e0, t->stream);
-      r = cg_step(t, steps_per_trial);
+      r = cg_step(t, steps);
       cudaEventRecord(e1, t->stream);
       if (!r) r = read_status(t);
       cudaEventElapsedTime(&total, e0, e1);
     } else {
-      for (int k = 0; k < steps_per_trial && !r; ++k) {
+      for (int k = 0; k < steps && !r; ++k) {
         cudaMemsetAsync(flush, k & 0xff, flush_bytes, t->stream);  // evicts the L2
         cudaEventRecord(e0, t->stream);
         r = cg_step(t, 1);
@@ -1073,7 +1087,7 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
       }
       if (!r) r = read_status(t);
     }
-    ms = total / steps_per_trial;
+    ms = total / steps;
     return r;
   };
   static const int repair_opts[] = {2, 4, 8, 16};
@@ -1081,9 +1095,10 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
   static const int dir_opts[] = {0, 1, 2, 4, 8};
   static const int prio_opts[] = {0, 1};
   static const int geom_opts[] = {0, 2, 4, 8};
-  cg_launch cur = c->launch;
+  const cg_launch start = c->launch;
+  cg_launch cur = start;
   double cur_ms = 0.0;
-  rc = trial(cur, cur_ms);
+  rc = trial(cur, steps_per_trial, cur_ms);
   for (int sweep = 0; sweep < 2 && !rc; ++sweep) {
     for (int field = 0; field < 5 && !rc; ++field) {
       const int* opts = field == 0 ? repair_opts : field == 1 ? check_opts : field == 2 ? dir_opts
@@ -1097,11 +1112,31 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
         if (*slot == opts[k]) continue;
         *slot = opts[k];
         double ms = 0.0;
-        rc = trial(cand, ms);
+        rc = trial(cand, steps_per_trial, ms);
         if (!rc && ms < cur_ms) {
           cur = cand;
           cur_ms = ms;
         }
+      }
+    }
+  }
+  // short trials are noisy: the winner must beat the starting shapes again in
+  // two longer, interleaved trials each (best of two)
+  if (!rc && std::memcmp(&cur, &start, sizeof(cg_launch)) != 0) {
+    double best_cur = 1e30, best_start = 1e30;
+    for (int rep = 0; rep < 2 && !rc; ++rep) {
+      double ms = 0.0;
+      rc = trial(start, 3 * steps_per_trial, ms);
+      if (!rc) best_start = std::min(best_start, ms);
+      if (!rc) rc = trial(cur, 3 * steps_per_trial, ms);
+      if (!rc) best_cur = std::min(best_cur, ms);
+    }
+    if (!rc) {
+      if (best_start <= best_cur) {
+        cur = start;
+        cur_ms = best_start;
+      } else {
+        cur_ms = best_cur;
       }
     }
   }
@@ -1125,7 +1160,7 @@ int cg_set_step(cg_ctx* c, int64_t step) {
   CG_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
   h.step = step;
   CG_CUDA(c, cudaMemcpy(c->ctl(), &h, sizeof(Ctl), cudaMemcpyHostToDevice));
-  refresh_directors(c);
+  prime(c);  // the noise of the pending move depends on the step counter
   return read_status(c);
 }
 

@@ -61,11 +61,16 @@ struct ForceArgs {
 struct DirArgs {
   int n;
   Ctl* ctl;
-  const double* theta;
+  double* theta;
   const int* tag;
   unsigned long long seed;
   double2* nrm;
   double* xi;
+  // 1 in a step: first rotate every director by the noise of the previous
+  // step, theta <- theta + noise_amp * xi (Eq. 3); 0 when the terms are only
+  // refreshed for the current directors
+  int advance;
+  double noise_amp;
 };
 // blocks: grid size (grid-stride loop); 0 = one thread per cell
 void launch_dir(const DirArgs& a, cudaStream_t st, int blocks = 0);

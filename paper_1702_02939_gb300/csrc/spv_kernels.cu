@@ -181,12 +181,13 @@ __global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
   g.Fy[i] = fy;
   if (!g.integrate) return;
 
-  // Eq. 3: r <- r + dt (mu F + v0 n(theta)), rounded to the grid and wrapped;
-  // theta <- theta + sqrt(2 D_r dt) xi.
+  // Eq. 3: r <- r + dt (mu F + v0 n(theta)), rounded to the grid and wrapped
+  // into the other position buffer; the director rotation
+  // theta <- theta + sqrt(2 D_r dt) xi follows at the start of the next step
+  // (k_dir), so the state between steps is (r, theta) of one time.
   const int cur = g.ctl->cur;
   const Rep R = g.reps[g.rep[i]];
   const double xi = g.x[(size_t)cur * N + i], yi = g.y[(size_t)cur * N + i];
-  const double th = g.theta[i];
   const double2 nd = g.nrm[i];  // (cos theta, sin theta), from k_dir
   const double v0 = g.v0[i];
   const double vx = g.mu * fx + v0 * nd.x, vy = g.mu * fy + v0 * nd.y;
@@ -205,17 +206,23 @@ __global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
   g.y[(size_t)nxt * N + i] = i2d_exact(Y) * R.inv_scale;
   g.X[(size_t)nxt * N + i] = X;
   g.Y[(size_t)nxt * N + i] = Y;
-  g.theta[i] = th + g.noise_amp * g.xi[i];
 }
 
-// n(theta) and xi (Philox counter (tag, step)) of the next move, one thread
-// per cell.  In the step graph it runs beside the circumcircle test, the cell
-// list and the repair rounds, which leave the FP64 pipe idle.
+// Director terms of a step: with `advance`, first the rotation of the
+// previous step theta <- theta + sqrt(2 D_r dt) xi; then n(theta) and the
+// noise xi of this step (Philox counter (tag, step)), grid-stride over cells.
+// In the step graph it runs beside the circumcircle test, the cell list and
+// the repair rounds, which leave the FP64 pipe idle.
 __global__ void k_dir(DirArgs g) {
   const long long step = g.ctl->step;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
+    double th = g.theta[i];
+    if (g.advance) {
+      th = th + g.noise_amp * g.xi[i];
+      g.theta[i] = th;
+    }
     double sn, cs;
-    sincos(g.theta[i], &sn, &cs);
+    sincos(th, &sn, &cs);
     g.nrm[i] = make_double2(cs, sn);
     g.xi[i] = director_noise(g.seed, g.tag[i], step);
   }

@@ -222,7 +222,6 @@ __global__ void __launch_bounds__(kForceThreads) k_force_f32(ForceArgs g) {
   g.y[(size_t)nxt * N + i] = i2d_exact(Yn) * R.inv_scale;
   g.X[(size_t)nxt * N + i] = Xn;
   g.Y[(size_t)nxt * N + i] = Yn;
-  g.theta[i] = g.theta[i] + g.noise_amp * g.xi[i];
 }
 
 // Director terms in FP32: n(theta) of the float director, and the noise from
@@ -232,8 +231,13 @@ __global__ void k_dir_f32(DirArgs g) {
   const long long step = g.ctl->step;
   const uint2 key = make_uint2((unsigned)g.seed, (unsigned)(g.seed >> 32));
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
+    double th = g.theta[i];
+    if (g.advance) {
+      th = th + g.noise_amp * g.xi[i];
+      g.theta[i] = th;
+    }
     float sn, cs;
-    sincosf((float)g.theta[i], &sn, &cs);
+    sincosf((float)th, &sn, &cs);
     g.nrm[i] = make_double2(cs, sn);
     const uint4 r = philox_10(make_uint4((unsigned)g.tag[i], (unsigned)(unsigned long long)step,
                                          (unsigned)((unsigned long long)step >> 32), 0u),
