@@ -476,10 +476,11 @@ void enqueue_step_suffix(cg_ctx* c, cudaStream_t st) {
 // Director terms, geometry, force sets and the pending move of the current
 // state (before the first step and after anything outside a step changes the
 // positions, directors, step counter, storage order, p0, v0 or the moduli).
-void prime(cg_ctx* c) {
-  run_dir(c, dir_args(c), c->stream);
-  run_geom(c, geom_args(c), c->stream);
-  run_force(c, force_args(c, 1), c->stream);
+enum : int { kPrimeDir = 1, kPrimeGeom = 2, kPrimeMove = 4, kPrimeAll = 7 };
+void prime(cg_ctx* c, int what = kPrimeAll) {
+  if (what & kPrimeDir) run_dir(c, dir_args(c), c->stream);
+  if (what & kPrimeGeom) run_geom(c, geom_args(c), c->stream);
+  if (what & kPrimeMove) run_force(c, force_args(c, 1), c->stream);
 }
 
 // One repair round (repair + consistency check) for a conditional loop node:
@@ -951,14 +952,14 @@ int cg_set_p0(cg_ctx* c, const double* p0) {
   if (!c) return CG_EINVAL;
   int rc = set_percell(c, p0, c->off.p0);
   if (rc) return rc;
-  prime(c);  // the force sets and the pending move depend on p0
+  prime(c, kPrimeGeom | kPrimeMove);  // the force sets and the pending move depend on p0
   return read_status(c);
 }
 int cg_set_v0(cg_ctx* c, const double* v0) {
   if (!c) return CG_EINVAL;
   int rc = set_percell(c, v0, c->off.v0);
   if (rc) return rc;
-  prime(c);  // the pending move depends on v0
+  prime(c, kPrimeMove);  // only the pending move depends on v0
   return read_status(c);
 }
 
@@ -997,7 +998,7 @@ int cg_set_moduli(cg_ctx* c, double KA, double KP) {
   }
   rc = build_graph(c);
   if (rc) return rc;
-  prime(c);  // the force sets and the pending move depend on the moduli
+  prime(c, kPrimeGeom | kPrimeMove);  // the force sets and the pending move depend on the moduli
   return read_status(c);
 }
 
@@ -1160,7 +1161,7 @@ int cg_set_step(cg_ctx* c, int64_t step) {
   CG_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
   h.step = step;
   CG_CUDA(c, cudaMemcpy(c->ctl(), &h, sizeof(Ctl), cudaMemcpyHostToDevice));
-  prime(c);  // the noise of the pending move depends on the step counter
+  prime(c, kPrimeDir | kPrimeMove);  // the noise of the pending move depends on the step counter
   return read_status(c);
 }
 

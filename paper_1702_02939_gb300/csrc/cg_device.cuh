@@ -106,11 +106,6 @@ __device__ __forceinline__ void raise_status(Ctl* ctl, int code) {
   atomicCAS(&ctl->status, 0, code);
 }
 
-__device__ __forceinline__ double min_image(double d, double L, double hL) {
-  if (d > hL) d -= L;
-  else if (d < -hL) d += L;
-  return d;
-}
 __device__ __forceinline__ long long min_image_i(long long d, long long L) {
   long long h = L >> 1;
   if (d > h) d -= L;
