@@ -622,13 +622,14 @@ Snapshot snapshot_at(char* base, size_t N) {
   return s;
 }
 
-void snapshot(cg_ctx* c, int save, const Snapshot& s) {
+// Saves (save = 1) or restores the state; a restore recomputes what the next
+// use needs (`after_restore`: kPrime* flags; the tangent kernels of the
+// reverse pass compute their own geometry and need none).
+void snapshot(cg_ctx* c, int save, const Snapshot& s, int after_restore = kPrimeAll) {
   launch_snapshot((int)c->N, save, c->ctl(), c->at<double>(c->off.x), c->at<double>(c->off.y),
                   c->at<long long>(c->off.X), c->at<long long>(c->off.Y), c->at<double>(c->off.theta),
                   c->at<int>(c->off.cnt), c->at<int>(c->off.nbr), s, c->stream);
-  if (!save) {  // positions, rings, directors and step counter were restored
-    prime(c);
-  }
+  if (!save && after_restore) prime(c, after_restore);
 }
 
 JvpArgs jvp_args(cg_ctx* c, char* bw, const BwdLayout& b) {
@@ -1197,7 +1198,7 @@ int cg_backward(cg_ctx* c, int64_t nsteps, int32_t ckpt_every, void* d_bw, size_
   const int* tag = c->at<int>(c->off.tag);
   const int64_t nck = (nsteps + ckpt_every - 1) / ckpt_every;
   const Snapshot fin = snapshot_at(bw + b.snaps + nck * b.snap_bytes, c->N);
-  snapshot(c, 0, fin);
+  snapshot(c, 0, fin, 0);  // the tangent kernels compute their own geometry
   // cotangents of the final state, in storage order
   double* tmp = c->at<double>(c->off.tmp);
   const double* srcs[4] = {gxT, gyT, gAT, gPT};
@@ -1231,8 +1232,8 @@ int cg_backward(cg_ctx* c, int64_t nsteps, int32_t ckpt_every, void* d_bw, size_
       snapshot(c, 1, snapshot_at(bw + b.seg + (t - t0) * b.snap_bytes, c->N));
       if (t + 1 < t1) CG_CUDA(c, cudaGraphLaunch(c->step_exec, st));
     }
-    for (int64_t t = t1 - 1; t >= t0; --t) {
-      snapshot(c, 0, snapshot_at(bw + b.seg + (t - t0) * b.snap_bytes, c->N));
+    for (int64_t t = t1 - 1; t >= t0; --t) {  // the tangent kernels compute their own geometry
+      snapshot(c, 0, snapshot_at(bw + b.seg + (t - t0) * b.snap_bytes, c->N), 0);
       launch_geom_jvp(a, st);
       launch_force_jvp(a, st);
     }
