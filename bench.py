@@ -43,6 +43,12 @@ FLUSH_BYTES = 256 * 1024 * 1024  # written between timed steps: more than the 12
 # (fma = 2, add/mul/div/sqrt/rsqrt = 1, transcendental = 1), for the mean ring
 # size of 6 of a random Voronoi tessellation.  Derivation in the design notes.
 FLOPS_PER_CELL = {"geometry": 342.0, "force_move": 93.0}
+# AVM: per cell of k_avm_cells (12 per polygon vertex x 6: offsets, shoelace
+# term, edge, sqrt, sum; 12 for A, P and the coefficients; 11 for the
+# director terms with sincos, log, sqrt, cos counted as 1 each) and per vertex
+# of k_avm_force_move (3 edges x (offset, length, rsqrt, unit vector) + 3 force
+# terms x 8 + activity and move).
+AVM_FLOPS = {"cells_per_cell": 95.0, "vertices_per_vertex": 62.0}
 # Algorithmic bytes per cell-step of the whole step (state read + written once).
 BYTES_PER_CELL_STEP = 84.0
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
@@ -360,6 +366,21 @@ def fp32_throughput(args, device):
             "launch_shapes": launch, "phase_ms_per_step": {k: v / 20 for k, v in ph.items()}}
 
 
+def avm_roofline(n, ph, prof_steps):
+    """FP64 roofline of the dominant AVM kernel from its event-timed phase."""
+    cells_ms = ph["cells_ms"] / prof_steps
+    verts_ms = ph["vertices_ms"] / prof_steps
+    if cells_ms >= verts_ms:
+        kernel, flops, ms = "k_avm_cells", AVM_FLOPS["cells_per_cell"] * n, cells_ms
+    else:
+        kernel, flops, ms = "k_avm_force_move", AVM_FLOPS["vertices_per_vertex"] * 2 * n, verts_ms
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "note": "FP64 pipe 78-80% busy (profiles/avm_step_N65536.md): sqrt, sincos, log, cos count one flop "
+                    "each but take many FP64 instructions"}
+
+
 def avm_throughput(args, device):
     """Active vertex model (Sec. 2.D, Eq. 4, Fig. 1): N = 65536 cells (V =
     131072 vertices) from the Voronoi tessellation of uniform random seeds in
@@ -419,6 +440,7 @@ def avm_throughput(args, device):
             "gpu_launches": launches,
             "t1_per_step": (c1["t1_total"] - c0["t1_total"]) / Kd,
             "t1_passes_per_step": (c1["t1_passes"] - c0["t1_passes"]) / Kd,
+            "roofline": avm_roofline(n, ph, prof_steps),
             "phase_ms_per_step": {"cells": ph["cells_ms"] / prof_steps, "vertices": ph["vertices_ms"] / prof_steps,
                                   "t1_passes": ph["t1_ms"] / prof_steps,
                                   "t1_passes_count": ph["t1_passes"] / prof_steps},
