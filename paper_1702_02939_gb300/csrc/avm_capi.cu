@@ -224,10 +224,24 @@ int loop_graph(cg_avm_ctx* c, Prefix prefix, cudaGraphExec_t* out) {
   return CG_OK;
 }
 
+// The first T1 pass of a step runs as plain graph nodes before the while
+// node (every step has one); the node then runs only the further passes.
 int avm_graphs(cg_avm_ctx* c) {
-  int rc = loop_graph(c, [](const AvmArgs& a, cudaStream_t st) { launch_avm_move(a, st); }, &c->exec);
+  int rc = loop_graph(
+      c,
+      [](const AvmArgs& a, cudaStream_t st) {
+        launch_avm_move(a, st);
+        launch_avm_t1_pass(a, st);
+      },
+      &c->exec);
   if (rc) return rc;
-  return loop_graph(c, [](const AvmArgs& a, cudaStream_t st) { launch_avm_begin_t1(a.ctl, st); }, &c->t1_exec);
+  return loop_graph(
+      c,
+      [](const AvmArgs& a, cudaStream_t st) {
+        launch_avm_begin_t1(a.ctl, st);
+        launch_avm_t1_pass(a, st);
+      },
+      &c->t1_exec);
 }
 
 int copy_in(cg_avm_ctx* c, void* dst, const void* src, size_t bytes) {
