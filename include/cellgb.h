@@ -113,7 +113,8 @@ typedef struct cg_launch {
                                     stream priority, the rest at the highest (default 1) */
   int32_t geom_blocks_per_sm;    /* grid of the geometry pass beside the repair rounds = SMs x this;
                                     0 = one thread per cell (default) */
-  int32_t reserved;              /* 0 */
+  int32_t test_blocks_per_sm;    /* grid of the circumcircle test = SMs x this (default 8), a
+                                    grid-stride loop over cells; 0 = one thread per cell */
 } cg_launch;
 
 /* Workspace size for R replicas. */
@@ -216,7 +217,7 @@ int cg_set_launch(cg_ctx* ctx, const cg_launch* launch);
  * optional L2-flush region of flush_bytes. */
 int cg_autotune_bytes(const cg_ctx* ctx, size_t flush_bytes, size_t* bytes);
 /* Picks the launch shapes by timing candidates (coordinate descent over the
- * five fields, two sweeps; the winner is confirmed against the starting shapes
+ * six fields, two sweeps; the winner is confirmed against the starting shapes
  * in longer trials) on a temporary copy of the context built in d_ws2
  * (device, >= cg_autotune_bytes(ctx, flush_bytes), 256-byte aligned) from the
  * current state, directors, step counter, p0 and v0: each trial restores that

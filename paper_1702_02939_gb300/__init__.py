@@ -47,7 +47,7 @@ class cg_params(C.Structure):
 class cg_launch(C.Structure):
     _fields_ = [("repair_blocks_per_sm", C.c_int32), ("check_blocks_per_sm", C.c_int32),
                 ("dir_blocks_per_sm", C.c_int32), ("dir_low_priority", C.c_int32),
-                ("geom_blocks_per_sm", C.c_int32), ("reserved", C.c_int32)]
+                ("geom_blocks_per_sm", C.c_int32), ("test_blocks_per_sm", C.c_int32)]
 
 
 class cg_avm_params(C.Structure):
@@ -281,7 +281,7 @@ def cg_triangulate_noalloc(n, Lx, Ly, x, y, cnt, nbr, stream):
 def cg_get_launch(ctx):
     out = cg_launch()
     _check(lib().cg_get_launch(ctx, C.byref(out)), ctx)
-    return {k: getattr(out, k) for k, _ in cg_launch._fields_ if k != "reserved"}
+    return {k: getattr(out, k) for k, _ in cg_launch._fields_}
 
 
 def cg_set_launch(ctx, launch):
@@ -298,7 +298,7 @@ def cg_autotune(ctx, steps_per_trial, flush_bytes, scratch):
     best, ms = cg_launch(), C.c_double(0.0)
     _check(lib().cg_autotune(ctx, int(steps_per_trial), int(flush_bytes), _ptr(scratch), scratch.numel(),
                              C.byref(best), C.byref(ms)), ctx)
-    return {k: getattr(best, k) for k, _ in cg_launch._fields_ if k != "reserved"}, ms.value
+    return {k: getattr(best, k) for k, _ in cg_launch._fields_}, ms.value
 
 
 def cg_num_cells(ctx):

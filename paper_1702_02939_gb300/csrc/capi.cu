@@ -180,7 +180,7 @@ struct cg_ctx {
   cudaStream_t capture = nullptr;   // private stream used for graph capture
   cudaStream_t side[2] = {nullptr, nullptr};  // branches of the captured step
   cudaEvent_t fork = nullptr, join_dir = nullptr, join_list = nullptr;
-  cg_launch launch{4, 4, 2, 1, 0, 0};          // launch shapes of the step graph
+  cg_launch launch{4, 4, 2, 1, 0, 8};          // launch shapes of the step graph
   std::vector<cg_replica> user_reps;           // as passed to cg_create
   cudaGraphExec_t step_exec = nullptr;
   int graph_steps = 0;
@@ -431,6 +431,7 @@ int repair_grid(const cg_ctx* c) { return sm_count() * c->launch.repair_blocks_p
 int check_grid(const cg_ctx* c) { return sm_count() * c->launch.check_blocks_per_sm; }
 int dir_grid(const cg_ctx* c) { return sm_count() * c->launch.dir_blocks_per_sm; }    // 0: full
 int geom_grid(const cg_ctx* c) { return sm_count() * c->launch.geom_blocks_per_sm; }  // 0: full
+int test_grid(const cg_ctx* c) { return sm_count() * c->launch.test_blocks_per_sm; }  // 0: full
 // Full triangulation: one warp per cell over every cell.
 int repair_grid_all(const cg_ctx*) { return sm_count() * 16; }
 int check_grid_all(const cg_ctx* c) { return (int)((c->N + 255) / 256); }
@@ -457,7 +458,7 @@ void enqueue_step_prefix(cg_ctx* c, cudaStream_t st) {
   cudaStreamWaitEvent(c->side[1], c->fork, 0);
   launch_cell_list(cell_list_args(c, 0), c->side[1]);
   cudaEventRecord(c->join_list, c->side[1]);
-  launch_test(test_args(c), st);
+  launch_test(test_args(c), st, test_grid(c));
   cudaStreamWaitEvent(st, c->join_list, 0);
 }
 
@@ -1014,7 +1015,7 @@ int cg_set_launch(cg_ctx* c, const cg_launch* l) {
   if (l->repair_blocks_per_sm < 1 || l->repair_blocks_per_sm > 64 || l->check_blocks_per_sm < 1 ||
       l->check_blocks_per_sm > 64 || l->dir_blocks_per_sm < 0 || l->dir_blocks_per_sm > 64 ||
       (l->dir_low_priority != 0 && l->dir_low_priority != 1) || l->geom_blocks_per_sm < 0 ||
-      l->geom_blocks_per_sm > 64 || l->reserved != 0)
+      l->geom_blocks_per_sm > 64 || l->test_blocks_per_sm < 0 || l->test_blocks_per_sm > 64)
     return CG_EINVAL;
   int rc = read_status(c);
   if (rc) return rc;
@@ -1097,20 +1098,21 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
   static const int dir_opts[] = {0, 1, 2, 4, 8};
   static const int prio_opts[] = {0, 1};
   static const int geom_opts[] = {0, 2, 4, 8};
+  static const int test_opts[] = {0, 2, 4, 8};
   const cg_launch start = c->launch;
   cg_launch cur = start;
   double cur_ms = 0.0;
   rc = trial(cur, steps_per_trial, cur_ms);
   for (int sweep = 0; sweep < 2 && !rc; ++sweep) {
-    for (int field = 0; field < 5 && !rc; ++field) {
+    for (int field = 0; field < 6 && !rc; ++field) {
       const int* opts = field == 0 ? repair_opts : field == 1 ? check_opts : field == 2 ? dir_opts
-                      : field == 3 ? prio_opts : geom_opts;
+                      : field == 3 ? prio_opts : field == 4 ? geom_opts : test_opts;
       const int nopt = field == 0 ? 4 : field == 1 ? 4 : field == 2 ? 5 : field == 3 ? 2 : 4;
       for (int k = 0; k < nopt && !rc; ++k) {
         cg_launch cand = cur;
         int* slot = field == 0 ? &cand.repair_blocks_per_sm : field == 1 ? &cand.check_blocks_per_sm
                   : field == 2 ? &cand.dir_blocks_per_sm : field == 3 ? &cand.dir_low_priority
-                  : &cand.geom_blocks_per_sm;
+                  : field == 4 ? &cand.geom_blocks_per_sm : &cand.test_blocks_per_sm;
         if (*slot == opts[k]) continue;
         *slot = opts[k];
         double ms = 0.0;

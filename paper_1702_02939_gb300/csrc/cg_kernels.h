@@ -149,7 +149,7 @@ void launch_force_f32(const ForceArgs& a, cudaStream_t st);
 void launch_dir_f32(const DirArgs& a, cudaStream_t st, int blocks = 0);
 void launch_force(const ForceArgs& a, cudaStream_t st);
 void launch_begin_topology(Ctl* ctl, int flip, cudaStream_t st);
-void launch_test(const TestArgs& a, cudaStream_t st);
+void launch_test(const TestArgs& a, cudaStream_t st, int blocks = 0);
 void launch_cell_list(const CellListArgs& a, cudaStream_t st);
 void launch_repair(const RepairArgs& a, int grid_blocks, cudaStream_t st);
 // exclusive scan of a.bin_count[0..nbins) into (a.bin_start, a.scan_partials)

@@ -256,13 +256,8 @@ __device__ __forceinline__ void flag_cell(unsigned* flags, int* list, int* count
 // Delaunay (the far vertex j_{a+1} outside the circle through i, j_{a-1}, j_a)
 // and every triangle owned by i (i its smallest index) positively oriented.
 // Failing quadruples/triangles flag all their cells.
-__global__ void __launch_bounds__(kTestThreads) k_test(TestArgs g) {
-  const int i = blockIdx.x * kTestThreads + threadIdx.x;
-  if (i >= g.n) return;
-  const size_t N = (size_t)g.n;
-  const int cur = g.ctl->cur;
-  const long long* __restrict__ X = g.X + (size_t)cur * N;
-  const long long* __restrict__ Y = g.Y + (size_t)cur * N;
+__device__ __forceinline__ void test_cell(const TestArgs& g, int i, const long long* __restrict__ X,
+                                          const long long* __restrict__ Y) {
   const Rep R = g.reps[g.rep[i]];
   const float sc = (float)R.inv_scale;
   const long long Xi = X[i], Yi = Y[i];
@@ -320,6 +315,16 @@ __global__ void __launch_bounds__(kTestThreads) k_test(TestArgs g) {
   }
 }
 
+// Grid-stride over cells (a smaller grid leaves room on every SM for the
+// FP64 branch that runs beside the test).
+__global__ void __launch_bounds__(kTestThreads) k_test(TestArgs g) {
+  const size_t N = (size_t)g.n;
+  const int cur = g.ctl->cur;
+  const long long* __restrict__ X = g.X + (size_t)cur * N;
+  const long long* __restrict__ Y = g.Y + (size_t)cur * N;
+  for (int i = blockIdx.x * kTestThreads + threadIdx.x; i < g.n; i += gridDim.x * kTestThreads) test_cell(g, i, X, Y);
+}
+
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
@@ -333,9 +338,10 @@ void launch_force(const ForceArgs& a, cudaStream_t st) {
   k_force<<<(a.n + kForceThreads - 1) / kForceThreads, kForceThreads, 0, st>>>(a);
 }
 void launch_begin_topology(Ctl* ctl, int flip, cudaStream_t st) { k_begin_topology<<<1, 1, 0, st>>>(ctl, flip); }
-void launch_test(const TestArgs& a, cudaStream_t st) {
+void launch_test(const TestArgs& a, cudaStream_t st, int blocks) {
   if (a.n <= 0) return;
-  k_test<<<(a.n + kTestThreads - 1) / kTestThreads, kTestThreads, 0, st>>>(a);
+  const int full = (a.n + kTestThreads - 1) / kTestThreads;
+  k_test<<<(blocks > 0 && blocks < full) ? blocks : full, kTestThreads, 0, st>>>(a);
 }
 
 }  // namespace cgk

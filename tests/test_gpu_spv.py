@@ -335,7 +335,7 @@ def test_launch_shapes_do_not_change_results():
     a, *_ = make(n, 33, p0=3.85, v0=0.1, seed=3)
     b, *_ = make(n, 33, p0=3.85, v0=0.1, seed=3)
     b.set_launch(repair_blocks_per_sm=8, check_blocks_per_sm=4, dir_blocks_per_sm=1, dir_low_priority=1,
-                 geom_blocks_per_sm=2)
+                 geom_blocks_per_sm=2, test_blocks_per_sm=2)
     assert b.launch["dir_blocks_per_sm"] == 1
     a.step(20)
     b.step(20)
@@ -356,7 +356,7 @@ def test_autotune_takes_no_step_and_keeps_results():
     before = a.state()
     best, ms = a.autotune(3)
     assert ms > 0 and set(best) == {"repair_blocks_per_sm", "check_blocks_per_sm", "dir_blocks_per_sm",
-                                    "dir_low_priority", "geom_blocks_per_sm"}
+                                    "dir_low_priority", "geom_blocks_per_sm", "test_blocks_per_sm"}
     assert a.launch == best
     for t0, t1 in zip(before, a.state()):
         assert torch.equal(t0, t1)
