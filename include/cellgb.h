@@ -171,6 +171,16 @@ int cg_set_v0(cg_ctx* ctx, const double* v0);
 
 int cg_get_counters(cg_ctx* ctx, cg_counters* host_out);
 
+/* Director terms of Eq. 3 as the FP64 step evaluates them (Sec. 2.C.3): for
+ * n angles theta[i] and noise keys tag[i] (a cell's global index in the
+ * concatenated system) writes cos theta[i], sin theta[i] and the standard
+ * normal xi(seed, tag[i], step) of the context's seed (Box-Muller on
+ * Philox4x32-10).  Device pointers, n elements each; enqueued on the
+ * context's stream without synchronizing.  CG_EINVAL for n < 0 or a NULL
+ * pointer with n > 0. */
+int cg_director_terms(cg_ctx* ctx, int32_t n, const double* d_theta, const int32_t* d_tag, int64_t step,
+                      double* d_cos, double* d_sin, double* d_xi);
+
 /* ---- Differentiation (backward pass) ------------------------------------
  * With the director noise replayed from the seed, one step of Eq. 3 is the
  * map r' = r + dt (mu F(r) + v0 n(theta)) whose transposed Jacobian is

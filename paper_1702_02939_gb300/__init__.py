@@ -86,6 +86,7 @@ def lib():
         L.cg_set_p0.argtypes = [vp, vp]
         L.cg_set_v0.argtypes = [vp, vp]
         L.cg_get_counters.argtypes = [vp, C.POINTER(cg_counters)]
+        L.cg_director_terms.argtypes = [vp, i32, vp, vp, i64, vp, vp, vp]
         L.cg_backward_bytes.argtypes = [vp, i64, i32, C.POINTER(C.c_size_t)]
         L.cg_set_moduli.argtypes = [vp, C.c_double, C.c_double]
         L.cg_set_step.argtypes = [vp, i64]
@@ -233,6 +234,11 @@ def cg_get_counters(ctx):
     c = cg_counters()
     _check(lib().cg_get_counters(ctx, C.byref(c)), ctx)
     return {k: getattr(c, k) for k, _ in cg_counters._fields_ if k != "reserved"}
+
+
+def cg_director_terms(ctx, n, theta, tag, step, cs, sn, xi):
+    _check(lib().cg_director_terms(ctx, int(n), _ptr(theta), _ptr(tag), int(step), _ptr(cs), _ptr(sn), _ptr(xi)),
+           ctx)
 
 
 def cg_backward_bytes(ctx, nsteps, ckpt_every):
@@ -390,6 +396,20 @@ class SPV:
 
     def counters(self):
         return cg_get_counters(self.ctx)
+
+    def director_terms(self, theta, tag, step):
+        """(cos theta, sin theta, xi(seed, tag, step)) as the FP64 step
+        evaluates them, for device tensors theta (float64) and tag (int32)."""
+        t = self.torch
+        theta = theta.to(device=self.device, dtype=t.float64).contiguous()
+        tag = tag.to(device=self.device, dtype=t.int32).contiguous()
+        n = theta.numel()
+        if tag.numel() != n:
+            raise ValueError("theta and tag differ in length")
+        cs, sn, xi = self._out(n), self._out(n), self._out(n)
+        cg_director_terms(self.ctx, n, theta, tag, step, cs, sn, xi)
+        self.sync()
+        return cs, sn, xi
 
     @property
     def launch(self):

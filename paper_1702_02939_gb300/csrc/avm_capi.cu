@@ -27,7 +27,7 @@ struct Lay {
 struct AvmOff {
   size_t spv, spv_bytes;
   size_t hx, hy, hf, vc, vn, cc, cv, theta, p0, v0, A, P, ka, kp, energy, act, Fx, Fy, lock, cand_e, cand, done;
-  size_t owned, base_local, base_partial, xs, ys, cnt, nbr, scalar, ctl;
+  size_t owned, base_local, base_partial, xs, ys, cnt, nbr, scalar, ctl, dir_tab;
   size_t total;
 };
 
@@ -69,6 +69,7 @@ AvmOff avm_layout(int64_t n, size_t spv_bytes) {
   o.nbr = L.take(n * CG_RING * i4);
   o.scalar = L.take(4 * d);
   o.ctl = L.take(sizeof(Ctl));
+  o.dir_tab = L.take(kDirTabEntries * sizeof(double2));
   o.total = L.total;
   return o;
 }
@@ -162,6 +163,7 @@ AvmArgs avm_args(cg_avm_ctx* c) {
   a.dt = c->par.dt;
   a.noise_amp = std::sqrt(2.0 * c->par.Dr * c->par.dt);
   a.seed = c->par.seed;
+  a.tab = c->at<double2>(c->off.dir_tab);
   a.A = c->at<double>(c->off.A);
   a.P = c->at<double>(c->off.P);
   a.ka = c->at<double>(c->off.ka);
@@ -345,6 +347,7 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
     rc = copy_in(c, c->at<double>(c->off.theta), theta, n * sizeof(double));
     if (rc) break;
     launch_check_finite(n, c->at<double>(c->off.theta), c->ctl(), st);
+    launch_init_dir_tables(c->at<double2>(c->off.dir_tab), st);
     launch_fill_d(n, p0, c->at<double>(c->off.p0), st);
     launch_fill_d(n, v0, c->at<double>(c->off.v0), st);
     launch_fill_u64(n, ~0ull, c->at<unsigned long long>(c->off.lock), st);

@@ -200,9 +200,9 @@ __global__ void k_avm_cells(AvmArgs g) {
   if (g.move) {
     const double th = g.theta[c];
     double sn, cs;
-    sincos(th, &sn, &cs);
+    dm_sincos(th, g.tab, sn, cs);
     g.act[c] = make_double2(g.v0[c] * cs, g.v0[c] * sn);
-    g.theta[c] = th + g.noise_amp * director_noise(g.seed, c, g.ctl->step);
+    g.theta[c] = th + g.noise_amp * director_noise(g.seed, c, g.ctl->step, g.tab);
   }
 }
 

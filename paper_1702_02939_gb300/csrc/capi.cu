@@ -33,7 +33,7 @@ struct Offsets {
   size_t fs, s, w;
   size_t flags, list0, list1, dirty_list, dirty_bits;
   size_t bin_count, bin_start, partials, cell_bin, cell_rank, ids;
-  size_t reps, ctl;
+  size_t reps, ctl, dir_tab;
   size_t total;
 };
 
@@ -95,6 +95,7 @@ Offsets layout(int64_t N, int64_t NB, int64_t NK, int R) {
   o.ids = L.take(N * i4);
   o.reps = L.take(R * sizeof(Rep));
   o.ctl = L.take(sizeof(Ctl));
+  o.dir_tab = L.take(kDirTabEntries * sizeof(double2));
   o.total = L.total;
   return o;
 }
@@ -274,6 +275,7 @@ DirArgs dir_args(cg_ctx* c) {
   d.xi = c->at<double>(c->off.xi);
   d.advance = 0;
   d.noise_amp = std::sqrt(2.0 * c->par.Dr * c->par.dt);
+  d.tab = c->at<double2>(c->off.dir_tab);
   return d;
 }
 
@@ -760,6 +762,7 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
     TRY(cudaMemcpyAsync(c->at<double>(c->off.tmp), theta, c->N * sizeof(double), cudaMemcpyDefault, st));
 #undef TRY
     if (rc) break;
+    launch_init_dir_tables(c->at<double2>(c->off.dir_tab), st);
     launch_scatter_d((int)c->N, c->at<int>(c->off.tag), c->at<double>(c->off.tmp), c->at<double>(c->off.theta), st);
     launch_check_finite((int)c->N, c->at<double>(c->off.theta), c->ctl(), st);
     rc = load_positions(c, x, y);
@@ -978,6 +981,17 @@ int cg_get_counters(cg_ctx* c, cg_counters* out) {
   out->status = h.status;
   out->reserved = 0;
   out->loop_total = h.loop_total;
+  return CG_OK;
+}
+
+
+int cg_director_terms(cg_ctx* c, int32_t n, const double* theta, const int32_t* tag, int64_t step, double* cs,
+                      double* sn, double* xi) {
+  if (!c || n < 0) return CG_EINVAL;
+  if (n == 0) return CG_OK;
+  if (!theta || !tag || !cs || !sn || !xi) return CG_EINVAL;
+  launch_dir_terms(n, theta, tag, c->par.seed, step, c->at<double2>(c->off.dir_tab), cs, sn, xi, c->stream);
+  CG_CUDA(c, cudaGetLastError());
   return CG_OK;
 }
 

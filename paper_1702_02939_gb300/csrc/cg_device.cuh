@@ -18,6 +18,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "dir_math.cuh"
+
 #define CG_RING 16
 
 namespace cgk {
@@ -136,14 +138,17 @@ __device__ __forceinline__ double unit53(unsigned hi, unsigned lo) {
   return (double)(k + 1ull) * 0x1.0p-53;
 }
 
-// Standard normal for (seed, cell tag, step), cosine branch of Box-Muller.
-__device__ __forceinline__ double director_noise(unsigned long long seed, int tag, long long step) {
+// Standard normal for (seed, cell tag, step), cosine branch of Box-Muller,
+// with the table-driven ln and cos(pi .) of dir_math.cuh (tab: the 512-entry
+// director table).
+__device__ __forceinline__ double director_noise(unsigned long long seed, int tag, long long step,
+                                                 const double2* __restrict__ tab) {
   uint4 r = philox_10(make_uint4((unsigned)tag, (unsigned)(unsigned long long)step,
                                  (unsigned)((unsigned long long)step >> 32), 0u),
                       make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
   double u1 = unit53(r.x, r.y), u2 = unit53(r.z, r.w);
-  // cos(2 pi u2) as cospi(2 u2): 2 u2 is exact and the reduction by pi is exact
-  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  // cos(2 pi u2) as cos(pi t), t = 2 u2 exact
+  return sqrt(-2.0 * dm_log(u1, tab)) * dm_cospi(2.0 * u2, tab);
 }
 
 // ----------------------------------------------------------------------------

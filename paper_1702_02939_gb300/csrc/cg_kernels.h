@@ -71,9 +71,15 @@ struct DirArgs {
   // refreshed for the current directors
   int advance;
   double noise_amp;
+  const double2* tab;  // director table (dir_math.cuh), filled by launch_init_dir_tables
 };
 // blocks: grid size (grid-stride loop); 0 = one thread per cell
 void launch_dir(const DirArgs& a, cudaStream_t st, int blocks = 0);
+// Fills the kDirTabEntries-entry director table.
+void launch_init_dir_tables(double2* tab, cudaStream_t st);
+// cos, sin of n angles and the noise xi(seed, tag[i], step) (FP64 path).
+void launch_dir_terms(int n, const double* theta, const int* tag, unsigned long long seed, long long step,
+                      const double2* tab, double* cs, double* sn, double* xi, cudaStream_t st);
 
 struct TestArgs {
   int n;
@@ -244,6 +250,7 @@ struct AvmArgs {
   const double *p0, *v0;
   double A0, sqrtA0, KA, KP, mu, dt, noise_amp;
   unsigned long long seed;
+  const double2* tab;      // director table (dir_math.cuh)
   double *A, *P, *ka, *kp, *energy;
   double2* act;            // [n] v0 n(theta) of the step's directors
   double *Fx, *Fy;

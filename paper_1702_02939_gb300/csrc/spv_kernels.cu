@@ -16,6 +16,7 @@
 // matrix of Eq. A16.  All predicates run on the FP32/integer pipes.
 #include "cg_device.cuh"
 #include "cg_kernels.h"
+#include <algorithm>
 
 namespace cgk {
 
@@ -222,15 +223,49 @@ __global__ void k_dir(DirArgs g) {
       g.theta[i] = th;
     }
     double sn, cs;
-    sincos(th, &sn, &cs);
+    dm_sincos(th, g.tab, sn, cs);
     g.nrm[i] = make_double2(cs, sn);
-    g.xi[i] = director_noise(g.seed, g.tag[i], step);
+    g.xi[i] = director_noise(g.seed, g.tag[i], step, g.tab);
   }
 }
 void launch_dir(const DirArgs& a, cudaStream_t st, int blocks) {
   if (a.n <= 0) return;
   const int full = (a.n + 127) / 128;
   k_dir<<<(blocks > 0 && blocks < full) ? blocks : full, 128, 0, st>>>(a);
+}
+
+// Table of dir_math.cuh: (sin, cos)(j pi/128) from CUDA's sinpi/cospi (exact
+// at multiples of pi/2), then per logarithm interval j the reciprocal of its
+// centre and minus its logarithm (exactly 1 and 0 for the interval around 1).
+__global__ void k_init_dir_tables(double2* tab) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < 256) {
+    tab[j] = make_double2(sinpi(j / 128.0), cospi(j / 128.0));
+  } else if (j < kDirTabEntries) {
+    const int i = j - 256;
+    const double inv =
+        (i == kLogOne) ? 1.0 : 1.0 / __longlong_as_double(kLogOff + ((long long)i << 44) + (1LL << 43));
+    tab[j] = make_double2(inv, -log(inv));
+  }
+}
+void launch_init_dir_tables(double2* tab, cudaStream_t st) { k_init_dir_tables<<<kDirTabEntries / 128, 128, 0, st>>>(tab); }
+
+__global__ void k_dir_terms(int n, const double* __restrict__ theta, const int* __restrict__ tag,
+                            unsigned long long seed, long long step, const double2* __restrict__ tab,
+                            double* cs, double* sn, double* xi) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double s, c;
+    dm_sincos(theta[i], tab, s, c);
+    cs[i] = c;
+    sn[i] = s;
+    xi[i] = director_noise(seed, tag[i], step, tab);
+  }
+}
+void launch_dir_terms(int n, const double* theta, const int* tag, unsigned long long seed, long long step,
+                      const double2* tab, double* cs, double* sn, double* xi, cudaStream_t st) {
+  if (n <= 0) return;
+  const int blocks = (int)std::min<long long>((n + 127) / 128, 152LL * 16);
+  k_dir_terms<<<blocks, 128, 0, st>>>(n, theta, tag, seed, step, tab, cs, sn, xi);
 }
 
 // Start of the topology phase of a step: the new positions become current,

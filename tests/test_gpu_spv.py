@@ -514,3 +514,47 @@ def test_rectangular_box():
     gx, gy, _ = (t.cpu().numpy() for t in sim.state())
     check_topology(sim, gx, gy, Lx, Ly)
     sim.close()
+
+
+def test_director_terms_match_libm_and_oracle():
+    """n(theta) and the Box-Muller noise of Eq. 3 as the FP64 step evaluates
+    them (table-driven sin, cos and ln) against numpy's sin/cos and the
+    oracle's noise.  Angles include the table points j pi/128 and their
+    neighbourhoods, multiples of pi/2, tiny and large |theta|, and |theta| >=
+    2^20 (evaluated by CUDA's sincos)."""
+    sim, *_ = make(64, 41, seed=123)
+    rng = np.random.default_rng(17)
+    parts = [
+        rng.uniform(-50.0, 50.0, 40000),
+        rng.uniform(-2e5, 2e5, 20000),
+        np.arange(-3000, 3000) * (np.pi / 128),
+        np.arange(-3000, 3000) * (np.pi / 128) + rng.uniform(-1e-9, 1e-9, 6000),
+        np.arange(-200, 200) * (np.pi / 2),
+        rng.uniform(-1e-6, 1e-6, 2000),
+        np.array([0.0, -0.0, 2.0 ** -1074, 2.0 ** 20 - 1e-6, 2.0 ** 20, -(2.0 ** 20), 3e7, -1e9]),
+    ]
+    th = np.concatenate(parts)
+    n = len(th)
+    tag = rng.integers(0, 2 ** 31 - 1, n, dtype=np.int64).astype(np.int32)
+    step = 987654321
+    cs, sn, xi = sim.director_terms(torch.from_numpy(th), torch.from_numpy(tag), step)
+    cs, sn, xi = cs.cpu().numpy(), sn.cpu().numpy(), xi.cpu().numpy()
+    ulp = 2.0 ** -53
+    # libm is within 1 ulp, the table method within 4 units of 2^-53 (absolute)
+    assert np.max(np.abs(cs - np.cos(th))) <= 6 * ulp
+    assert np.max(np.abs(sn - np.sin(th))) <= 6 * ulp
+    assert np.max(np.abs(cs * cs + sn * sn - 1.0)) <= 8 * ulp
+    # exact where the angle is exactly 0
+    assert cs[-8] == 1.0 and sn[-8] == 0.0 and sn[-7] == 0.0
+    # xi = R cos(2 pi u2), R = sqrt(-2 ln u1).  The oracle rounds 2 pi u2 before
+    # its cosine (absolute error up to ~7 units of 2^-53 in the cosine), the
+    # table method is within 4; both round ln, sqrt and the product.
+    for k in range(0, n, 7):
+        ref = oracle.director_noise(123, int(tag[k]), step)
+        r = oracle.philox([int(tag[k]), step & 0xFFFFFFFF, step >> 32, 0], [123, 0])
+        u1 = ((((r[0] << 32) | r[1]) >> 11) + 1) * 2.0 ** -53
+        R = np.sqrt(-2.0 * np.log(u1))
+        assert abs(xi[k] - ref) <= ulp * (16 * R + 8 * abs(ref)), (k, xi[k], ref, R)
+    # the noise is a standard normal
+    assert abs(xi.mean()) < 0.02 and abs(xi.std() - 1.0) < 0.02
+    sim.close()
