@@ -137,6 +137,22 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
  * captured CUDA graph without host synchronization. */
 int cg_step(cg_ctx* ctx, int64_t nsteps);
 
+/* nsteps steps (as cg_step) with per-step I/O overlapped with the steps'
+ * kernels.  Before step k (0-based) the per-cell v0 of that step is taken
+ * from v0 + k*v0_stride (n_total doubles, user order; NULL keeps v0) exactly
+ * as cg_set_v0 would set it; after step k the positions are written to
+ * x + k*out_stride and y + k*out_stride (n_total doubles each, user order;
+ * NULL skips).  Strides count doubles; 0 reuses one buffer for every step.
+ * Pointers may be host (page-locked, for the copies to overlap) or device.
+ * The copies run on two private streams through double-buffered staging in
+ * the workspace, so step k's upload and step k-1's download overlap the
+ * kernels; the results are bit-identical to cg_set_v0, cg_step(1),
+ * cg_get_state per step.  Synchronizes before returning and returns the
+ * device status (a non-finite v0 sets CG_EINVAL; the steps after it still
+ * run). */
+int cg_run_io(cg_ctx* ctx, int64_t nsteps, const double* v0, int64_t v0_stride, double* x, double* y,
+              int64_t out_stride);
+
 /* Per-phase device time of nsteps ordinary steps run eagerly (not as a
  * graph), timed with CUDA events on the context's stream.  ms_out[k] receives
  * the summed milliseconds of phase k (n_out >= CG_NUM_PHASES):

@@ -76,6 +76,7 @@ def lib():
         L.cg_create.argtypes = [i32, C.POINTER(cg_replica), C.POINTER(cg_params), vp, vp, vp, vp, C.c_size_t,
                                 vp, C.POINTER(vp)]
         L.cg_step.argtypes = [vp, i64]
+        L.cg_run_io.argtypes = [vp, i64, vp, i64, vp, vp, i64]
         L.cg_sync.argtypes = [vp]
         L.cg_profile_step.argtypes = [vp, i64, C.POINTER(C.c_double), i32]
         L.cg_get_state.argtypes = [vp, vp, vp, vp]
@@ -236,6 +237,10 @@ def cg_get_counters(ctx):
     return {k: getattr(c, k) for k, _ in cg_counters._fields_ if k != "reserved"}
 
 
+def cg_run_io(ctx, nsteps, v0, v0_stride, x, y, out_stride):
+    _check(lib().cg_run_io(ctx, int(nsteps), _ptr(v0), int(v0_stride), _ptr(x), _ptr(y), int(out_stride)), ctx)
+
+
 def cg_director_terms(ctx, n, theta, tag, step, cs, sn, xi):
     _check(lib().cg_director_terms(ctx, int(n), _ptr(theta), _ptr(tag), int(step), _ptr(cs), _ptr(sn), _ptr(xi)),
            ctx)
@@ -361,6 +366,13 @@ class SPV:
 
     def profile(self, nsteps):
         return cg_profile_step(self.ctx, nsteps)
+
+    def run_io(self, nsteps, v0=None, x=None, y=None, v0_stride=0, out_stride=0):
+        """nsteps steps with per-step I/O overlapped with the kernels: v0 of
+        step k from v0[k * v0_stride:], positions after step k into
+        x[k * out_stride:], y[k * out_stride:] (contiguous float64 tensors or
+        arrays, host memory page-locked for overlap, or None)."""
+        cg_run_io(self.ctx, nsteps, v0, v0_stride, x, y, out_stride)
 
     def state(self):
         x, y, th = self._out(), self._out(), self._out()

@@ -34,6 +34,7 @@ struct Offsets {
   size_t flags, list0, list1, dirty_list, dirty_bits;
   size_t bin_count, bin_start, partials, cell_bin, cell_rank, ids;
   size_t reps, ctl, dir_tab;
+  size_t io_v0, io_xy;  // staging of cg_run_io: [2][n] v0, [2][2][n] positions
   size_t total;
 };
 
@@ -96,6 +97,8 @@ Offsets layout(int64_t N, int64_t NB, int64_t NK, int R) {
   o.reps = L.take(R * sizeof(Rep));
   o.ctl = L.take(sizeof(Ctl));
   o.dir_tab = L.take(kDirTabEntries * sizeof(double2));
+  o.io_v0 = L.take(2 * N * d);
+  o.io_xy = L.take(4 * N * d);
   o.total = L.total;
   return o;
 }
@@ -181,6 +184,9 @@ struct cg_ctx {
   cudaStream_t capture = nullptr;   // private stream used for graph capture
   cudaStream_t side[2] = {nullptr, nullptr};  // branches of the captured step
   cudaEvent_t fork = nullptr, join_dir = nullptr, join_list = nullptr;
+  // cg_run_io: copy streams and the events that order the double-buffered staging
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t in_ready[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_free[2] = {};
   cg_launch launch{4, 4, 2, 1, 0, 8};          // launch shapes of the step graph
   std::vector<cg_replica> user_reps;           // as passed to cg_create
   cudaGraphExec_t step_exec = nullptr;
@@ -735,6 +741,11 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_dir, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_list, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking);
+    for (int b = 0; b < 2; ++b)
+      for (cudaEvent_t* ev : {&c->in_ready[b], &c->in_free[b], &c->out_ready[b], &c->out_free[b]})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) { rc = fail(c, CG_ECUDA, cudaGetErrorString(e)); break; }
     cudaStream_t st = c->stream;
     // replica table and per-cell constants
@@ -798,6 +809,52 @@ int cg_step(cg_ctx* c, int64_t nsteps) {
     ++c->host_step;
   }
   return CG_OK;
+}
+
+int cg_run_io(cg_ctx* c, int64_t nsteps, const double* v0, int64_t v0_stride, double* x, double* y,
+              int64_t out_stride) {
+  if (!c || nsteps < 0 || v0_stride < 0 || out_stride < 0) return CG_EINVAL;
+  int rc = read_status(c);
+  if (rc) return rc;
+  const size_t N = (size_t)c->N;
+  const int n = (int)c->N;
+  cudaStream_t st = c->stream;
+  const int* tag = c->at<int>(c->off.tag);
+  for (int64_t k = 0; k < nsteps; ++k) {
+    const int b = (int)(k & 1);
+    if (v0) {
+      // H2D into staging b once the scatter that last read it is done
+      double* in = c->at<double>(c->off.io_v0) + b * N;
+      CG_CUDA(c, cudaStreamWaitEvent(c->h2d, c->in_free[b], 0));
+      CG_CUDA(c, cudaMemcpyAsync(in, v0 + k * v0_stride, N * sizeof(double), cudaMemcpyDefault, c->h2d));
+      CG_CUDA(c, cudaEventRecord(c->in_ready[b], c->h2d));
+      CG_CUDA(c, cudaStreamWaitEvent(st, c->in_ready[b], 0));
+      launch_scatter_d(n, tag, in, c->at<double>(c->off.v0), st);
+      CG_CUDA(c, cudaEventRecord(c->in_free[b], st));
+      launch_check_finite(n, c->at<double>(c->off.v0), c->ctl(), st);
+      run_force(c, force_args(c, 2), st);  // the pending move with this step's v0 (as cg_set_v0)
+    }
+    if (c->par.sort_every > 0 && c->host_step > 0 && c->host_step % c->par.sort_every == 0) {
+      launch_sort(sort_args(c), st);
+      prime(c);
+    }
+    CG_CUDA(c, cudaGraphLaunch(c->step_exec, st));
+    ++c->host_step;
+    if (x || y) {
+      // positions of this step into staging b once its previous D2H is done
+      double* out = c->at<double>(c->off.io_xy) + 2 * b * N;
+      CG_CUDA(c, cudaStreamWaitEvent(st, c->out_free[b], 0));
+      launch_gather_cur_xy(n, tag, c->at<double>(c->off.x), c->at<double>(c->off.y), c->ctl(), out, out + N, st);
+      CG_CUDA(c, cudaEventRecord(c->out_ready[b], st));
+      CG_CUDA(c, cudaStreamWaitEvent(c->d2h, c->out_ready[b], 0));
+      if (x) CG_CUDA(c, cudaMemcpyAsync(x + k * out_stride, out, N * sizeof(double), cudaMemcpyDefault, c->d2h));
+      if (y) CG_CUDA(c, cudaMemcpyAsync(y + k * out_stride, out + N, N * sizeof(double), cudaMemcpyDefault, c->d2h));
+      CG_CUDA(c, cudaEventRecord(c->out_free[b], c->d2h));
+    }
+  }
+  CG_CUDA(c, cudaStreamSynchronize(c->h2d));
+  CG_CUDA(c, cudaStreamSynchronize(c->d2h));
+  return read_status(c);
 }
 
 int cg_profile_step(cg_ctx* c, int64_t nsteps, double* ms_out, int32_t n_out) {
@@ -964,7 +1021,9 @@ int cg_set_v0(cg_ctx* c, const double* v0) {
   if (!c) return CG_EINVAL;
   int rc = set_percell(c, v0, c->off.v0);
   if (rc) return rc;
-  prime(c, kPrimeMove);  // only the pending move depends on v0
+  // only the pending move depends on v0; the forces of the current
+  // positions are stored, so the move is redone from them
+  run_force(c, force_args(c, 2), c->stream);
   return read_status(c);
 }
 
@@ -1332,6 +1391,11 @@ int cg_destroy(cg_ctx* c) {
     if (sd) cudaStreamDestroy(sd);
   for (cudaEvent_t ev : {c->fork, c->join_dir, c->join_list})
     if (ev) cudaEventDestroy(ev);
+  for (cudaStream_t sc : {c->h2d, c->d2h})
+    if (sc) cudaStreamDestroy(sc);
+  for (int b = 0; b < 2; ++b)
+    for (cudaEvent_t ev : {c->in_ready[b], c->in_free[b], c->out_ready[b], c->out_free[b]})
+      if (ev) cudaEventDestroy(ev);
   delete c;
   return CG_OK;
 }

@@ -45,7 +45,7 @@ struct ForceArgs {
   const int *cnt, *nbr, *tag;
   const double2 *fs, *s, *w;
   double *Fx, *Fy;
-  int integrate;
+  int integrate;       // 0 forces, 1 forces + move of Eq. 3, 2 the move from the stored Fx, Fy
   double *x, *y;       // [2][n]
   long long *X, *Y;    // [2][n]
   double* theta;
@@ -168,6 +168,9 @@ void launch_snap(int n, const Rep* reps, const int* rep, const double* xin, cons
 void launch_gather_d(int n, const int* tag, const double* src, double* dst_user, cudaStream_t st);
 void launch_check_finite(int n, const double* v, Ctl* ctl, cudaStream_t st);
 void launch_scatter_d(int n, const int* tag, const double* src_user, double* dst, cudaStream_t st);
+// current positions (x2, y2: [2][n], buffer ctl->cur) into user order
+void launch_gather_cur_xy(int n, const int* tag, const double* x2, const double* y2, const Ctl* ctl,
+                          double* dst_x, double* dst_y, cudaStream_t st);
 void launch_gather_ring(int n, const int* tag, const int* cnt, const int* nbr, int* cnt_user, int* nbr_user,
                         cudaStream_t st);
 void launch_reduce_sum(int n, const double* v, double* out, cudaStream_t st);

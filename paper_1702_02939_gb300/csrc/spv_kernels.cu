@@ -136,16 +136,15 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
   }
 }
 
-// One thread per cell: G_t = sum over the triangle's three cells of their force
-// sets, F_i = -sum_t s_t (w_t . G_t); then (optionally) the update of Eq. 3.
-__global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
-  const int i = blockIdx.x * kForceThreads + threadIdx.x;
-  if (i >= g.n) return;
+// Net force on cell i: G_t = sum over the triangle's three cells of their
+// force sets, F_i = -sum_t s_t (w_t . G_t).  False (status raised) for a
+// malformed ring.
+__device__ __forceinline__ bool net_force(const ForceArgs& g, int i, double& fx_out, double& fy_out) {
   const size_t N = (size_t)g.n;
   const int m = g.cnt[i];
   if (m < 3 || m > CG_RING) {
     raise_status(g.ctl, kETOPO);
-    return;
+    return false;
   }
   const int* ring = g.nbr + (size_t)i * CG_RING;
   int jfirst = ring[0];
@@ -178,9 +177,28 @@ __global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
     pj = pk;
   }
   if (bad) raise_status(g.ctl, kETOPO);
-  g.Fx[i] = fx;
-  g.Fy[i] = fy;
-  if (!g.integrate) return;
+  fx_out = fx;
+  fy_out = fy;
+  return true;
+}
+
+// One thread per cell: the net force (integrate 0 or 1) and the update of
+// Eq. 3 (integrate 1), or the update alone from the stored forces of the
+// current positions (integrate 2: after a change of v0).
+__global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
+  const int i = blockIdx.x * kForceThreads + threadIdx.x;
+  if (i >= g.n) return;
+  const size_t N = (size_t)g.n;
+  double fx, fy;
+  if (g.integrate == 2) {
+    fx = g.Fx[i];
+    fy = g.Fy[i];
+  } else {
+    if (!net_force(g, i, fx, fy)) return;
+    g.Fx[i] = fx;
+    g.Fy[i] = fy;
+    if (!g.integrate) return;
+  }
 
   // Eq. 3: r <- r + dt (mu F + v0 n(theta)), rounded to the grid and wrapped
   // into the other position buffer; the director rotation

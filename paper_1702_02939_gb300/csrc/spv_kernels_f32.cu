@@ -153,11 +153,9 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom_f32(GeomArgs g) {
   }
 }
 
-// One thread per cell: net force in FP32 from the float force sets; the move
-// of Eq. 3 is accumulated in FP64 and rounded to the grid as in k_force.
-__global__ void __launch_bounds__(kForceThreads) k_force_f32(ForceArgs g) {
-  const int i = blockIdx.x * kForceThreads + threadIdx.x;
-  if (i >= g.n) return;
+// Net force on cell i in FP32 from the float force sets (false, status
+// raised, for a malformed ring).
+__device__ __forceinline__ bool net_force_f32(const ForceArgs& g, int i, float& fx_out, float& fy_out) {
   const size_t N = (size_t)g.n;
   const float2* fs = as_f2(g.fs);
   const float2* sv = as_f2(g.s);
@@ -165,7 +163,7 @@ __global__ void __launch_bounds__(kForceThreads) k_force_f32(ForceArgs g) {
   const int m = g.cnt[i];
   if (m < 3 || m > CG_RING) {
     raise_status(g.ctl, kETOPO);
-    return;
+    return false;
   }
   const int* ring = g.nbr + (size_t)i * CG_RING;
   int jfirst = ring[0];
@@ -197,9 +195,28 @@ __global__ void __launch_bounds__(kForceThreads) k_force_f32(ForceArgs g) {
     pj = pk;
   }
   if (bad) raise_status(g.ctl, kETOPO);
-  g.Fx[i] = fx;
-  g.Fy[i] = fy;
-  if (!g.integrate) return;
+  fx_out = fx;
+  fy_out = fy;
+  return true;
+}
+
+// One thread per cell: the net force and, as in k_force, the move of Eq. 3
+// accumulated in FP64 and rounded to the grid (integrate 2: the move alone
+// from the stored forces, which hold the FP32 values exactly).
+__global__ void __launch_bounds__(kForceThreads) k_force_f32(ForceArgs g) {
+  const int i = blockIdx.x * kForceThreads + threadIdx.x;
+  if (i >= g.n) return;
+  const size_t N = (size_t)g.n;
+  float fx, fy;
+  if (g.integrate == 2) {
+    fx = (float)g.Fx[i];
+    fy = (float)g.Fy[i];
+  } else {
+    if (!net_force_f32(g, i, fx, fy)) return;
+    g.Fx[i] = fx;
+    g.Fy[i] = fy;
+    if (!g.integrate) return;
+  }
 
   const int cur = g.ctl->cur;
   const Rep R = g.reps[g.rep[i]];

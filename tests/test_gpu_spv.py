@@ -558,3 +558,51 @@ def test_director_terms_match_libm_and_oracle():
     # the noise is a standard normal
     assert abs(xi.mean()) < 0.02 and abs(xi.std() - 1.0) < 0.02
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_run_io_is_bit_identical_to_set_step_get(precision):
+    """cg_run_io (uploads overlapped with the steps, double-buffered staging)
+    gives the same positions, bit for bit, as cg_set_v0, cg_step(1),
+    cg_get_state per step; with a per-step v0 and per-step outputs, and with
+    v0 kept and one output buffer reused."""
+    n, K = 1000, 7
+    a, *_ = make(n, 51, p0=3.85, v0=0.1, seed=8, dt=0.01, precision=precision)
+    b, *_ = make(n, 51, p0=3.85, v0=0.1, seed=8, dt=0.01, precision=precision)
+    rng = np.random.default_rng(5)
+    v0 = rng.uniform(0.0, 0.3, (K, n))
+    ref_x, ref_y = [], []
+    for k in range(K):
+        a.set_v0(v0[k])
+        a.step(1)
+        x, y, _ = a.state()
+        ref_x.append(x.cpu().numpy())
+        ref_y.append(y.cpu().numpy())
+    hv0 = torch.from_numpy(v0.ravel().copy()).pin_memory()
+    hx = torch.empty(K * n, dtype=torch.float64).pin_memory()
+    hy = torch.empty(K * n, dtype=torch.float64).pin_memory()
+    b.run_io(K, v0=hv0, x=hx, y=hy, v0_stride=n, out_stride=n)
+    for k in range(K):
+        np.testing.assert_array_equal(hx[k * n:(k + 1) * n].numpy(), ref_x[k])
+        np.testing.assert_array_equal(hy[k * n:(k + 1) * n].numpy(), ref_y[k])
+    # v0 kept, one reused output buffer (device tensors this time)
+    a.step(3)
+    dx = torch.empty(n, dtype=torch.float64, device="cuda")
+    dy = torch.empty(n, dtype=torch.float64, device="cuda")
+    b.run_io(3, x=dx, y=dy)
+    x, y, th = a.state()
+    assert torch.equal(dx, x) and torch.equal(dy, y)
+    for t0, t1 in zip(a.state(), b.state()):
+        assert torch.equal(t0, t1)
+    a.close()
+    b.close()
+
+
+def test_run_io_refuses_a_non_finite_v0():
+    sim, *_ = make(400, 52, seed=2)
+    bad = np.full(400, 0.05)
+    bad[17] = np.nan
+    with pytest.raises(cg.CellgbError) as e:
+        sim.run_io(2, v0=bad)
+    assert e.value.code == -1  # CG_EINVAL
+    sim.close()
