@@ -296,10 +296,20 @@ __device__ __forceinline__ double len2_rn(double dx, double dy) {
   return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
 }
 
+// FP32 squared length of edge (v, w), v < w, from the float copies of the
+// positions, in a fixed rounding order (the proposal's filter and the
+// apply kernel's look-ahead see the same value).
+__device__ __forceinline__ float t1_len2_f(const AvmArgs& g, float2 pv, float2 pw) {
+  const float fx = mimg_f(pw.x - pv.x, g.Lxf), fy = mimg_f(pw.y - pv.y, g.Lyf);
+  return __fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy));
+}
+
 // One thread per vertex v, its edges (v, w) with w > v.  The squared length
 // is first bounded in FP32 from the float copies of the positions; only edges
 // within the error band of the threshold are decided in FP64 in the fixed
-// rounding order.  Candidates go to a compact list.
+// rounding order.  Candidates go to a compact list.  A short edge that its
+// cells' vertex counts keep from flipping marks the pass as possibly leaving
+// work (another flip may change those counts).
 __global__ void k_t1_propose(AvmArgs g) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   // stop the loop unless the closing kernel of this pass asks for another
@@ -316,9 +326,7 @@ __global__ void k_t1_propose(AvmArgs g) {
       raise_status(g.ctl, kETOPO);
       continue;
     }
-    const float2 pw = g.hf[w];
-    const float fx = mimg_f(pw.x - pv.x, g.Lxf), fy = mimg_f(pw.y - pv.y, g.Lyf);
-    const float l2 = fx * fx + fy * fy;
+    const float l2 = t1_len2_f(g, pv, g.hf[w]);
     if (l2 > g.t2hi) continue;
     if (!(l2 < g.t2lo)) {
       const int cur = g.ctl->cur;
@@ -337,7 +345,10 @@ __global__ void k_t1_propose(AvmArgs g) {
       raise_status(g.ctl, kETOPO);
       continue;
     }
-    if (g.cc[i] <= 3 || g.cc[k] <= 3 || g.cc[j] >= CG_RING || g.cc[l] >= CG_RING) continue;
+    if (g.cc[i] <= 3 || g.cc[k] <= 3 || g.cc[j] >= CG_RING || g.cc[l] >= CG_RING) {
+      g.ctl->t1_more = 1;
+      continue;
+    }
     const unsigned long long key = lock_key(stamp, e);
     atomicMin(&g.lock[i], key);
     atomicMin(&g.lock[j], key);
@@ -479,8 +490,32 @@ __device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd) {
   const double nx2 = wrap_a(mx + px, g.ax), ny2 = wrap_a(my + py, g.ay);
   hx[v1] = nx1; hy[v1] = ny1;
   hx[v2] = nx2; hy[v2] = ny2;
-  g.hf[v1] = make_float2((float)nx1, (float)ny1);
-  g.hf[v2] = make_float2((float)nx2, (float)ny2);
+  const float2 f1 = make_float2((float)nx1, (float)ny1), f2 = make_float2((float)nx2, (float)ny2);
+  g.hf[v1] = f1;
+  g.hf[v2] = f2;
+  // Look-ahead: the flip moved only v1 and v2, and no other flip of this pass
+  // moves a vertex adjacent to them (it would need one of this flip's locked
+  // cells), so the edges at v1 and v2 are the only ones whose length changed.
+  // If none of them passes the proposal's FP32 bound, the next pass finds no
+  // new candidate here.
+  {
+    const int a1[3] = {All, Alr, v2}, a2[2] = {Aul, Aur};
+    bool near = false;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const int w = a1[t];
+      near |= (w == v2) ? t1_len2_f(g, v1 < v2 ? f1 : f2, v1 < v2 ? f2 : f1) <= g.t2hi
+                        : t1_len2_f(g, v1 < w ? f1 : g.hf[w], v1 < w ? g.hf[w] : f1) <= g.t2hi;
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int w = a2[t];
+      near |= t1_len2_f(g, v2 < w ? f2 : g.hf[w], v2 < w ? g.hf[w] : f2) <= g.t2hi;
+    }
+    // (a degenerate network, with a cell on both sides of an edge, takes the
+    // next pass regardless)
+    if (near || !distinct) ctl->t1_more = 1;
+  }
   // neighbour exchange (Fig. 1): v1 -> cells (j, i, l), v2 -> cells (k, j, l)
   g.vc[3 * v1 + 0] = j; g.vc[3 * v1 + 1] = i; g.vc[3 * v1 + 2] = l;
   g.vn[3 * v1 + 0] = All; g.vn[3 * v1 + 1] = Alr; g.vn[3 * v1 + 2] = v2;
@@ -505,8 +540,11 @@ __device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd) {
 
 // Applies the listed candidates that hold all four locks (passes 0 ..
 // t1_cap-1; pass t1_cap only counts).  The last block closes the pass:
-// another pass runs while this one proposed something and the cap is not
-// reached; candidates at the counting pass raise the T1-cap status.
+// another pass runs while this one may have left work (a candidate that lost
+// a lock, an edge at a moved vertex within the FP32 bound of the threshold,
+// or a short edge its cells kept from flipping) and the cap is not reached;
+// candidates at the counting pass raise the T1-cap status.  Without such
+// work the next pass would propose nothing, so it is skipped.
 __global__ void k_t1_apply(AvmArgs g) {
   Ctl* ctl = g.ctl;
   const int pass = ctl->last_flagged;
@@ -517,7 +555,10 @@ __global__ void k_t1_apply(AvmArgs g) {
       const int e = g.cand_e[t];
       const int4 cd = g.cand[t];
       const unsigned long long key = lock_key(stamp, e);
-      if (g.lock[cd.x] != key || g.lock[cd.y] != key || g.lock[cd.z] != key || g.lock[cd.w] != key) continue;
+      if (g.lock[cd.x] != key || g.lock[cd.y] != key || g.lock[cd.z] != key || g.lock[cd.w] != key) {
+        ctl->t1_more = 1;
+        continue;
+      }
       apply_t1(g, e / 3, e % 3, cd);
     }
   }
@@ -527,7 +568,8 @@ __global__ void k_t1_apply(AvmArgs g) {
     ctl->loop_total += 1;
     ctl->last_flagged = pass + 1;
     if (pass >= g.t1_cap && proposed > 0) atomicCAS(&ctl->status, 0, (int)kET1CAP);
-    const int more = proposed > 0 && pass < g.t1_cap && ctl->status == 0;
+    const int more = proposed > 0 && ctl->t1_more && pass < g.t1_cap && ctl->status == 0;
+    ctl->t1_more = 0;
     ctl->pad = more;  // read by the host when the passes run outside a graph
     if (more && g.loop) cudaGraphSetConditional(g.loop, 1);
   }
