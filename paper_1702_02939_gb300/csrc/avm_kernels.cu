@@ -615,12 +615,18 @@ __global__ void k_fill_u64(int n, unsigned long long v, unsigned long long* out)
 // ---------------------------------------------------------------------------
 constexpr int kAvmThreads = 128;
 static inline int blocks_of(int n) { return (n + kAvmThreads - 1) / kAvmThreads; }
+// The FP64 step kernels in smaller blocks: 65536 cells make only ~3.4 blocks
+// of 128 per SM, and the SMs given one block more set the kernel's time
+// (measured best: 64 threads for the cells, 32 for the vertices).
+constexpr int kAvmCellThreads = 64, kAvmVertexThreads = 32;
+static inline int cell_blocks_of(int n) { return (n + kAvmCellThreads - 1) / kAvmCellThreads; }
+static inline int vertex_blocks_of(int n) { return (n + kAvmVertexThreads - 1) / kAvmVertexThreads; }
 
 void launch_avm_move(const AvmArgs& a, cudaStream_t st, int part) {
   AvmArgs m = a;
   m.move = 1;
-  if (part != 2) k_avm_cells<<<blocks_of(a.n), kAvmThreads, 0, st>>>(m);
-  if (part != 1) k_avm_force_move<<<blocks_of(a.V), kAvmThreads, 0, st>>>(m);
+  if (part != 2) k_avm_cells<<<cell_blocks_of(a.n), kAvmCellThreads, 0, st>>>(m);
+  if (part != 1) k_avm_force_move<<<vertex_blocks_of(a.V), kAvmVertexThreads, 0, st>>>(m);
 }
 void launch_avm_begin_t1(Ctl* ctl, cudaStream_t st) { k_avm_begin_t1<<<1, 1, 0, st>>>(ctl); }
 void launch_avm_t1_pass(const AvmArgs& a, cudaStream_t st) {
@@ -633,8 +639,8 @@ void launch_avm_shadow(const AvmArgs& a, cudaStream_t st) {
 void launch_avm_forces(const AvmArgs& a, cudaStream_t st) {
   AvmArgs f = a;
   f.move = 0;
-  k_avm_cells<<<blocks_of(a.n), kAvmThreads, 0, st>>>(f);
-  k_avm_force_move<<<blocks_of(a.V), kAvmThreads, 0, st>>>(f);
+  k_avm_cells<<<cell_blocks_of(a.n), kAvmCellThreads, 0, st>>>(f);
+  k_avm_force_move<<<vertex_blocks_of(a.V), kAvmVertexThreads, 0, st>>>(f);
 }
 void launch_avm_validate(const AvmArgs& a, cudaStream_t st) {
   k_avm_validate<<<blocks_of(a.V), kAvmThreads, 0, st>>>(a);
