@@ -1170,7 +1170,7 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
   static const int check_opts[] = {1, 2, 4, 8};
   static const int dir_opts[] = {0, 1, 2, 4, 8};
   static const int prio_opts[] = {0, 1};
-  static const int geom_opts[] = {0, 2, 4, 8};
+  static const int geom_opts[] = {0, 4, 8, 16};
   static const int test_opts[] = {0, 2, 4, 8};
   const cg_launch start = c->launch;
   cg_launch cur = start;
