@@ -164,8 +164,10 @@ def test_set_p0_v0_change_forces_and_motion():
 
 def test_full_size_workload():
     """N = 262144, L = 512 (the benchmark workload): initial topology
-    bit-exact, forces within tolerance, and after 10 fluid-regime steps the
-    maintained topology equals the exact triangulation of the new positions."""
+    bit-exact, forces within tolerance, positions and directors after one
+    graph step within tolerance of the oracle's step, and after 10
+    fluid-regime steps the maintained topology equals the exact
+    triangulation of the new positions."""
     n = 262144
     sim, xs, ys, th, Lx, Ly = make(n, 1, p0=3.85, v0=0.1, seed=1, dt=0.01)
     topo = check_topology(sim, xs, ys, Lx, Ly)
@@ -173,7 +175,14 @@ def test_full_size_workload():
     oFx, oFy, *_ = oracle.forces(xs, ys, Lx, Ly, topo, 3.85)
     scale = max(np.abs(oFx).max(), np.abs(oFy).max())
     assert np.abs(Fx.cpu().numpy() - oFx).max() <= F_TOL * scale
-    sim.step(10)
+    assert np.abs(Fy.cpu().numpy() - oFy).max() <= F_TOL * scale
+    sim.step(1)
+    gx, gy, gth = (t.cpu().numpy() for t in sim.state())
+    ox, oy, oth, _ = oracle.spv_run(xs, ys, th, Lx, Ly, 3.85, 0.1, 1, seed=1, dt=0.01)
+    assert np.abs(wrapdiff(gx, ox, Lx)).max() <= X_TOL * Lx
+    assert np.abs(wrapdiff(gy, oy, Ly)).max() <= X_TOL * Ly
+    np.testing.assert_allclose(gth, oth, rtol=0, atol=1e-12)
+    sim.step(9)
     gx, gy, _ = (t.cpu().numpy() for t in sim.state())
     check_topology(sim, gx, gy, Lx, Ly)
     sim.close()
