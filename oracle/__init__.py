@@ -61,11 +61,11 @@ def _declare(L):
         getattr(L, name).restype = C.c_int
     L.cgo_avm_build.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp, _ip, _ip, _ip, _ip]
     L.cgo_avm_forces.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _ip, _ip, _ip, _ip, _dp, _dp,
-                                 _dp, _dp, _dp, _dp, _dp]
+                                 _dp, _dp, _dp, _dp, _dp, _dp]
     L.cgo_avm_t1.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _ip, _ip, _ip, _ip, C.c_double,
-                             C.c_double, C.c_int, _ip]
+                             C.c_double, C.c_double, C.c_int, _ip]
     L.cgo_avm_step.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _ip, _ip, _ip, _ip, _dp, _dp,
-                               _dp, C.c_uint64, C.c_int64, C.c_int, _ip]
+                               _dp, _dp, C.c_uint64, C.c_int64, C.c_int, _ip]
     for name in ("cgo_avm_build", "cgo_avm_forces", "cgo_avm_t1", "cgo_avm_step"):
         getattr(L, name).restype = C.c_int
     for extra in ("_declare_avm", "_declare_adjoint"):
@@ -349,37 +349,53 @@ def avm_build(x, y, Lx, Ly):
     return AvmNet(n, Lx, Ly, hx, hy, vc, vn, cc, cv)
 
 
+def _cells(net, v):
+    return np.ascontiguousarray(np.broadcast_to(np.asarray(v, np.float64), (net.n,)))
+
+
 def avm_forces(net, p0, A0=1.0, KA=1.0, KP=1.0):
-    p0 = np.ascontiguousarray(np.broadcast_to(np.asarray(p0, np.float64), (net.n,)))
-    mech = np.array([A0, KA, KP], np.float64)
+    """Vertex forces, areas, perimeters and energy; p0 and A0 scalars or per
+    cell (P0_c = p0_c sqrt(A0_c)); removed cells (cc = 0) contribute nothing."""
+    p0, a0 = _cells(net, p0), _cells(net, A0)
+    mech = np.array([KA, KP], np.float64)
     Fx, Fy, A, P, E = np.zeros(net.V), np.zeros(net.V), np.zeros(net.n), np.zeros(net.n), np.zeros(1)
-    _check(lib().cgo_avm_forces(*net._args(), _d(p0), _d(mech), _d(Fx), _d(Fy), _d(A), _d(P), _d(E)), "avm_forces")
+    _check(lib().cgo_avm_forces(*net._args(), _d(p0), _d(a0), _d(mech), _d(Fx), _d(Fy), _d(A), _d(P), _d(E)),
+           "avm_forces")
     return Fx, Fy, A, P, float(E[0])
 
 
-def avm_t1(net, thr, newlen=None, cap=16, allow_cap=False):
-    """T1 passes on a copy of the network; returns (new network, transitions).
-    With allow_cap, hitting the pass cap returns the partial result."""
+def avm_transitions(net, thr, newlen=None, t2_area=0.0, cap=16, allow_cap=False):
+    """T1 (and, with t2_area > 0, T2) passes on a copy of the network; returns
+    (new network, T1s, T2s).  With allow_cap, hitting the pass cap returns
+    the partial result."""
     net = net.copy()
     newlen = 1.5 * thr if newlen is None else newlen
-    applied = np.zeros(1, np.int32)
-    rc = lib().cgo_avm_t1(*net._args(), float(thr), float(newlen), int(cap), _i(applied))
+    applied = np.zeros(2, np.int32)
+    rc = lib().cgo_avm_t1(*net._args(), float(thr), float(newlen), float(t2_area), int(cap), _i(applied))
     if not (allow_cap and rc == -8):
         _check(rc, "avm_t1")
-    return net, int(applied[0])
+    return net, int(applied[0]), int(applied[1])
+
+
+def avm_t1(net, thr, newlen=None, cap=16, allow_cap=False):
+    """T1 passes on a copy of the network; returns (new network, transitions)."""
+    net, t1, _ = avm_transitions(net, thr, newlen, 0.0, cap, allow_cap)
+    return net, t1
 
 
 def avm_step(net, theta, p0, v0, seed, step, A0=1.0, KA=1.0, KP=1.0, mu=1.0, Dr=1.0, dt=0.01, thr=0.04, newlen=None,
-             cap=16):
-    """One AVM step on copies: returns (network, theta, transitions)."""
+             cap=16, t2_area=0.0, counts=False):
+    """One AVM step on copies: returns (network, theta, T1s), or with counts
+    (network, theta, T1s, T2s).  p0, v0, A0: scalars or per cell."""
     net = net.copy()
     theta = np.array(theta, np.float64, copy=True)
-    p0 = np.ascontiguousarray(np.broadcast_to(np.asarray(p0, np.float64), (net.n,)))
-    v0 = np.ascontiguousarray(np.broadcast_to(np.asarray(v0, np.float64), (net.n,)))
+    p0, v0, a0 = _cells(net, p0), _cells(net, v0), _cells(net, A0)
     newlen = 1.5 * thr if newlen is None else newlen
-    par = np.array([A0, KA, KP, mu, Dr, dt, thr, newlen], np.float64)
-    applied = np.zeros(1, np.int32)
+    par = np.array([KA, KP, mu, Dr, dt, thr, newlen, t2_area], np.float64)
+    applied = np.zeros(2, np.int32)
     _check(lib().cgo_avm_step(net.n, net.V, net.Lx, net.Ly, _d(net.hx), _d(net.hy), _d(theta), _i(net.vc),
-                              _i(net.vn), _i(net.cc), _i(net.cv), _d(p0), _d(v0), _d(par), int(seed), int(step),
-                              int(cap), _i(applied)), "avm_step")
+                              _i(net.vn), _i(net.cc), _i(net.cv), _d(p0), _d(v0), _d(a0), _d(par), int(seed),
+                              int(step), int(cap), _i(applied)), "avm_step")
+    if counts:
+        return net, theta, int(applied[0]), int(applied[1])
     return net, theta, int(applied[0])

@@ -12,7 +12,12 @@
 //  * T1 transitions (Fig. 1): an edge shorter than a threshold is rotated by
 //    90 degrees about its midpoint and the neighbours are exchanged; at most
 //    one transition per cell per pass, passes repeated until none is called
-//    for (Sec. 2.D).
+//    for (Sec. 2.D);
+//  * T2 transitions (cell removal, named in Sec. 2.A; the paper's code has
+//    only T1s): a triangular cell whose area is below a threshold is removed
+//    and its three vertices merge into one at their centroid; per-cell
+//    preferred areas A0_c (a dying cell gets a small A0_c) drive the cell
+//    down to it.
 // Conventions (shared definitions with the library, each written separately):
 //  * vertex v stores its cells (c0, c1, c2) counter-clockwise around it and
 //    its neighbours (n0, n1, n2), where the edge v-n_k separates c_k and c_{k+1};
@@ -28,7 +33,20 @@
 //    candidates touching each of i, j, k, l;
 //  * the rotated edge gets length 1.5 x threshold; v becomes the endpoint on
 //    cell i's side (cells j, i, l; neighbours A_ll, A_lr, n_s), n_s the one
-//    on cell k's side (cells k, j, l; neighbours A_ul, v, A_ur).
+//    on cell k's side (cells k, j, l; neighbours A_ul, v, A_ur);
+//  * T2 candidates: cells c with exactly 3 vertices (v0, v1, v2 = its list)
+//    and d < 2 x threshold_T2, d = px1 py2 - px2 py1 (each product and the
+//    difference rounded separately; p = minimum-image offsets from v0), id
+//    3V + c; its cells are c and the three cells across its edges, which must
+//    be distinct with more than 3 vertices each; the three outer vertices
+//    must be distinct; the same lock rule as T1 (smallest id among the
+//    candidates touching each cell);
+//  * a T2 keeps the smallest of the three vertex ids at the centroid
+//    v0 + (p1 + p2)/3 (wrapped); the other two become free (vc, vn = -1),
+//    the cell is emptied (cc = 0, cv = -1); around the kept vertex the
+//    outer edges keep their order; each neighbour cell loses one vertex;
+//  * free vertices and empty cells take no part in forces, moves or
+//    transitions (their positions stay); P0_c = p0_c sqrt(A0_c).
 #include "internal.h"
 
 #include <climits>
@@ -65,6 +83,8 @@ struct Net {
   int32_t *vc, *vn, *cc, *cv;
 };
 
+inline bool vertex_free(const Net& g, int v) { return g.vc[3 * v] < 0; }
+
 // Squared edge length, every product and sum rounded on its own.
 double edge_len2(const Net& g, int v, int w) {
   volatile double dx = mimg(g.hx[w] - g.hx[v], g.Lx);
@@ -76,6 +96,10 @@ double edge_len2(const Net& g, int v, int w) {
 
 void polygon_geometry(const Net& g, int c, double& A, double& P) {
   int m = g.cc[c];
+  if (m == 0) {  // removed by a T2
+    A = P = 0.0;
+    return;
+  }
   int v0 = g.cv[c * kR];
   std::vector<double> px(m), py(m);
   for (int a = 0; a < m; ++a) {
@@ -94,17 +118,17 @@ void polygon_geometry(const Net& g, int c, double& A, double& P) {
 }
 
 // F_v = -sum_c dE_c/dh_v, accumulated cell by cell over each cell's vertex list.
-void vertex_forces(const Net& g, const double* p0, double A0, double KA, double KP, double* Fx, double* Fy,
-                   double* A, double* P, double* energy) {
-  const double sqA0 = std::sqrt(A0);
+void vertex_forces(const Net& g, const double* p0, const double* a0, double KA, double KP, double* Fx,
+                   double* Fy, double* A, double* P, double* energy) {
   double E = 0.0;
   for (int v = 0; v < g.V; ++v) Fx[v] = Fy[v] = 0.0;
   for (int c = 0; c < g.N; ++c) {
     polygon_geometry(g, c, A[c], P[c]);
-    double P0 = p0[c] * sqA0;
+    int m = g.cc[c];
+    if (m == 0) continue;
+    const double A0 = a0[c], P0 = p0[c] * std::sqrt(A0);
     E += KA * (A[c] - A0) * (A[c] - A0) + KP * (P[c] - P0) * (P[c] - P0);
     double ka = 2.0 * KA * (A[c] - A0), kp = 2.0 * KP * (P[c] - P0);
-    int m = g.cc[c];
     for (int a = 0; a < m; ++a) {
       int vp = g.cv[c * kR + (a + m - 1) % m], v = g.cv[c * kR + a], vn = g.cv[c * kR + (a + 1) % m];
       double tinx = mimg(g.hx[v] - g.hx[vp], g.Lx), tiny = mimg(g.hy[v] - g.hy[vp], g.Ly);    // t_ij
@@ -148,11 +172,131 @@ struct Cand {
   int v, s, w, i, j, k, l, id;
 };
 
-// One T1 pass; returns the number of transitions applied, or -1 on a broken network.
-int t1_pass(Net& g, double thr, double newlen, int* remaining) {
+// A T2 candidate: the triangular cell c, its vertices v[3] (its list), the
+// cells nb[a] across its edges (v[a], v[a+1]), the outer vertices w[a] of
+// v[a] and the cells cp[a], cpp[a] on either side of the edge v[a] - w[a]
+// (counter-clockwise around v[a]).
+struct T2Cand {
+  int c, id;
+  int v[3], nb[3], w[3], cp[3], cpp[3];
+};
+
+// The T2 area test: twice the signed area of the triangle, each product and
+// the difference rounded separately, below twice the threshold.
+bool t2_small(const Net& g, int c, double t2_area) {
+  const int v0 = g.cv[c * kR], v1 = g.cv[c * kR + 1], v2 = g.cv[c * kR + 2];
+  volatile double px1 = mimg(g.hx[v1] - g.hx[v0], g.Lx), py1 = mimg(g.hy[v1] - g.hy[v0], g.Ly);
+  volatile double px2 = mimg(g.hx[v2] - g.hx[v0], g.Lx), py2 = mimg(g.hy[v2] - g.hy[v0], g.Ly);
+  volatile double a = px1 * py2;
+  volatile double b = px2 * py1;
+  volatile double d = a - b;
+  return d < 2.0 * t2_area;
+}
+
+// Cell other than c that has both vertices va and vb, or -1.
+int across(const Net& g, int c, int va, int vb) {
+  for (int s = 0; s < 3; ++s) {
+    const int x = g.vc[3 * va + s];
+    if (x != c && x >= 0 && (x == g.vc[3 * vb] || x == g.vc[3 * vb + 1] || x == g.vc[3 * vb + 2])) return x;
+  }
+  return -1;
+}
+
+// Fills a T2 candidate for the triangular cell c; false when the removal is
+// not allowed (a neighbour with 3 vertices, neighbours or outer vertices not
+// distinct); -1 in *broken for an inconsistent network.
+bool t2_candidate(const Net& g, int c, T2Cand& t, int* broken) {
+  t.c = c;
+  t.id = 3 * g.V + c;
+  for (int a = 0; a < 3; ++a) t.v[a] = g.cv[c * kR + a];
+  for (int a = 0; a < 3; ++a) {
+    const int va = t.v[a];
+    const int s = slot_of(g.vc, va, c);
+    if (s < 0) {
+      *broken = 1;
+      return false;
+    }
+    t.w[a] = g.vn[3 * va + (s + 1) % 3];
+    t.cp[a] = g.vc[3 * va + (s + 1) % 3];
+    t.cpp[a] = g.vc[3 * va + (s + 2) % 3];
+    t.nb[a] = across(g, c, va, t.v[(a + 1) % 3]);
+    if (t.nb[a] < 0) {
+      *broken = 1;
+      return false;
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    if (g.cc[t.nb[a]] <= 3) return false;
+    for (int b2 = a + 1; b2 < 3; ++b2)
+      if (t.nb[a] == t.nb[b2] || t.w[a] == t.w[b2]) return false;
+    for (int b2 = 0; b2 < 3; ++b2)
+      if (t.w[a] == t.v[b2]) return false;
+  }
+  return true;
+}
+
+// Replaces v0, v1, v2 by vk in cell x's list and drops the repeat this makes
+// (the cell shared one edge with the removed triangle).
+void merge_in_cell(Net& g, int x, const int* v, int vk) {
+  const int m = g.cc[x];
+  std::vector<int> out;
+  for (int a = 0; a < m; ++a) {
+    int e = g.cv[x * kR + a];
+    if (e == v[0] || e == v[1] || e == v[2]) e = vk;
+    if (!out.empty() && e == vk && out.back() == vk) continue;
+    out.push_back(e);
+  }
+  if (out.size() > 1 && out.front() == vk && out.back() == vk) out.pop_back();
+  for (int a = 0; a < kR; ++a) g.cv[x * kR + a] = a < (int)out.size() ? out[a] : -1;
+  g.cc[x] = (int)out.size();
+}
+
+// Applies a T2; -1 on an inconsistent network.
+int apply_t2(Net& g, const T2Cand& t) {
+  const int vk = std::min(t.v[0], std::min(t.v[1], t.v[2]));
+  // centroid relative to the first vertex of the list
+  const int u0 = t.v[0], u1 = t.v[1], u2 = t.v[2];
+  const double dx1 = mimg(g.hx[u1] - g.hx[u0], g.Lx), dy1 = mimg(g.hy[u1] - g.hy[u0], g.Ly);
+  const double dx2 = mimg(g.hx[u2] - g.hx[u0], g.Lx), dy2 = mimg(g.hy[u2] - g.hy[u0], g.Ly);
+  const double cx = wrapL(g.hx[u0] + (dx1 + dx2) / 3.0, g.Lx);
+  const double cy = wrapL(g.hy[u0] + (dy1 + dy2) / 3.0, g.Ly);
+  // the kept vertex: outer edges in the order a0 = 0, then the one whose
+  // first cell is the previous edge's second cell
+  int ord[3] = {0, -1, -1};
+  for (int q = 1; q < 3; ++q)
+    for (int a = 0; a < 3; ++a)
+      if (t.cp[a] == t.cpp[ord[q - 1]] && a != ord[0] && (q < 2 || a != ord[1])) ord[q] = a;
+  if (ord[1] < 0 || ord[2] < 0 || t.cpp[ord[2]] != t.cp[ord[0]]) return -1;
+  for (int a = 0; a < 3; ++a) {
+    const int s = slot_of(g.vn, t.w[a], t.v[a]);
+    if (s < 0) return -1;
+    g.vn[3 * t.w[a] + s] = vk;
+  }
+  for (int a = 0; a < 3; ++a) merge_in_cell(g, t.nb[a], t.v, vk);
+  for (int q = 0; q < 3; ++q) {
+    g.vc[3 * vk + q] = t.cp[ord[q]];
+    g.vn[3 * vk + q] = t.w[ord[q]];
+  }
+  g.hx[vk] = cx;
+  g.hy[vk] = cy;
+  for (int a = 0; a < 3; ++a) {
+    if (t.v[a] == vk) continue;
+    for (int q = 0; q < 3; ++q) g.vc[3 * t.v[a] + q] = g.vn[3 * t.v[a] + q] = -1;
+  }
+  for (int a = 0; a < kR; ++a) g.cv[t.c * kR + a] = -1;
+  g.cc[t.c] = 0;
+  return 0;
+}
+
+// One pass of topological transitions (T1 and, with t2_area > 0, T2);
+// returns the number applied (T1s in *n_t1, T2s in *n_t2) or -1 on a broken
+// network; *remaining = candidates proposed.
+int topo_pass(Net& g, double thr, double newlen, double t2_area, int* remaining, int* n_t1, int* n_t2) {
   std::vector<Cand> cands;
+  std::vector<T2Cand> t2s;
   const double thr2 = thr * thr;
   for (int v = 0; v < g.V; ++v) {
+    if (vertex_free(g, v)) continue;
     for (int s = 0; s < 3; ++s) {
       int w = g.vn[3 * v + s];
       if (w <= v) continue;
@@ -168,11 +312,23 @@ int t1_pass(Net& g, double thr, double newlen, int* remaining) {
       cands.push_back(Cand{v, s, w, i, j, k, l, 3 * v + s});
     }
   }
-  *remaining = (int)cands.size();
-  if (cands.empty()) return 0;
+  if (t2_area > 0.0) {
+    for (int c = 0; c < g.N; ++c) {
+      if (g.cc[c] != 3 || !t2_small(g, c, t2_area)) continue;
+      T2Cand t;
+      int broken = 0;
+      if (t2_candidate(g, c, t, &broken)) t2s.push_back(t);
+      if (broken) return -1;
+    }
+  }
+  *remaining = (int)(cands.size() + t2s.size());
+  *n_t1 = *n_t2 = 0;
+  if (*remaining == 0) return 0;
   std::vector<int> lock(g.N, INT_MAX);
   for (const Cand& c : cands)
     for (int cell : {c.i, c.j, c.k, c.l}) lock[cell] = std::min(lock[cell], c.id);
+  for (const T2Cand& t : t2s)
+    for (int cell : {t.c, t.nb[0], t.nb[1], t.nb[2]}) lock[cell] = std::min(lock[cell], t.id);
   int applied = 0;
   for (const Cand& c : cands) {
     if (lock[c.i] != c.id || lock[c.j] != c.id || lock[c.k] != c.id || lock[c.l] != c.id) continue;
@@ -209,6 +365,13 @@ int t1_pass(Net& g, double thr, double newlen, int* remaining) {
     insert_after(g, c.j, v1, v2);
     insert_after(g, c.l, v2, v1);
     ++applied;
+    ++*n_t1;
+  }
+  for (const T2Cand& t : t2s) {
+    if (lock[t.c] != t.id || lock[t.nb[0]] != t.id || lock[t.nb[1]] != t.id || lock[t.nb[2]] != t.id) continue;
+    if (apply_t2(g, t) < 0) return -1;
+    ++applied;
+    ++*n_t2;
   }
   return applied;
 }
@@ -293,54 +456,59 @@ int cgo_avm_build(int n, double Lx, double Ly, const double* x, const double* y,
 }
 
 int cgo_avm_forces(int n, int V, double Lx, double Ly, double* hx, double* hy, int32_t* vc, int32_t* vn,
-                   int32_t* cc, int32_t* cv, const double* p0, const double* mech, double* Fx, double* Fy, double* A,
-                   double* P, double* E) {
+                   int32_t* cc, int32_t* cv, const double* p0, const double* a0, const double* mech, double* Fx,
+                   double* Fy, double* A, double* P, double* E) {
   Net g{n, V, Lx, Ly, hx, hy, vc, vn, cc, cv};
-  vertex_forces(g, p0, mech[0], mech[1], mech[2], Fx, Fy, A, P, E);
+  vertex_forces(g, p0, a0, mech[0], mech[1], Fx, Fy, A, P, E);
   return 0;
 }
 
-// T1 passes until a pass finds no eligible candidate (at most cap passes);
-// *applied = transitions made.  Returns -8 when candidates remain after cap.
+// Transition passes (T1, and T2 when t2_area > 0) until a pass proposes no
+// candidate (at most cap passes with transitions); applied[0] = T1s,
+// applied[1] = T2s made.  Returns -8 when candidates remain after cap.
 int cgo_avm_t1(int n, int V, double Lx, double Ly, double* hx, double* hy, int32_t* vc, int32_t* vn, int32_t* cc,
-               int32_t* cv, double thr, double newlen, int cap, int32_t* applied) {
+               int32_t* cv, double thr, double newlen, double t2_area, int cap, int32_t* applied) {
   Net g{n, V, Lx, Ly, hx, hy, vc, vn, cc, cv};
-  int total = 0;
+  int tot1 = 0, tot2 = 0;
   for (int r = 0; r <= cap; ++r) {
-    int rem = 0;
-    int a = (r < cap) ? t1_pass(g, thr, newlen, &rem) : 0;
+    int rem = 0, a1 = 0, a2 = 0;
+    int a = (r < cap) ? topo_pass(g, thr, newlen, t2_area, &rem, &a1, &a2) : 0;
     if (r == cap) {  // count what is left without applying
       Net h = g;
       std::vector<double> sx(hx, hx + V), sy(hy, hy + V);
       std::vector<int32_t> svc(vc, vc + 3 * V), svn(vn, vn + 3 * V), scc(cc, cc + n), scv(cv, cv + n * kR);
       h.hx = sx.data(); h.hy = sy.data(); h.vc = svc.data(); h.vn = svn.data(); h.cc = scc.data(); h.cv = scv.data();
-      t1_pass(h, thr, newlen, &rem);
-      *applied = total;
+      topo_pass(h, thr, newlen, t2_area, &rem, &a1, &a2);
+      applied[0] = tot1;
+      applied[1] = tot2;
       return rem ? -8 : 0;
     }
     if (a < 0) return -22;
-    total += a;
+    tot1 += a1;
+    tot2 += a2;
     if (rem == 0) break;
   }
-  *applied = total;
+  applied[0] = tot1;
+  applied[1] = tot2;
   return 0;
 }
 
-// One AVM step: vertex move (Eq. 4), director rotation, T1 passes.
-// par = {A0, KA, KP, mu, Dr, dt, thr, newlen}; v0 per cell.
+// One AVM step: vertex move (Eq. 4), director rotation, transition passes.
+// par = {KA, KP, mu, Dr, dt, thr, newlen, t2_area}; p0, v0, a0 per cell.
 int cgo_avm_step(int n, int V, double Lx, double Ly, double* hx, double* hy, double* theta, int32_t* vc, int32_t* vn,
-                 int32_t* cc, int32_t* cv, const double* p0, const double* v0, const double* par, uint64_t seed,
-                 int64_t step, int cap, int32_t* applied) {
+                 int32_t* cc, int32_t* cv, const double* p0, const double* v0, const double* a0, const double* par,
+                 uint64_t seed, int64_t step, int cap, int32_t* applied) {
   Net g{n, V, Lx, Ly, hx, hy, vc, vn, cc, cv};
   std::vector<double> Fx(V), Fy(V), A(n), P(n);
-  vertex_forces(g, p0, par[0], par[1], par[2], Fx.data(), Fy.data(), A.data(), P.data(), nullptr);
-  const double mu = par[3], Dr = par[4], dt = par[5];
+  vertex_forces(g, p0, a0, par[0], par[1], Fx.data(), Fy.data(), A.data(), P.data(), nullptr);
+  const double mu = par[2], Dr = par[3], dt = par[4];
   std::vector<double> nx(n), ny(n);
   for (int c = 0; c < n; ++c) {
     nx[c] = v0[c] * std::cos(theta[c]);
     ny[c] = v0[c] * std::sin(theta[c]);
   }
   for (int v = 0; v < V; ++v) {
+    if (vertex_free(g, v)) continue;  // removed by a T2: stays where it is
     // Eq. 4 with n = 3 cells per vertex (per-cell speeds v0_c)
     double ax = (nx[vc[3 * v]] + nx[vc[3 * v + 1]] + nx[vc[3 * v + 2]]) / 3.0;
     double ay = (ny[vc[3 * v]] + ny[vc[3 * v + 1]] + ny[vc[3 * v + 2]]) / 3.0;
@@ -349,7 +517,7 @@ int cgo_avm_step(int n, int V, double Lx, double Ly, double* hx, double* hy, dou
   }
   const double s = std::sqrt(2.0 * Dr * dt);
   for (int c = 0; c < n; ++c) theta[c] = theta[c] + s * cgo_director_noise(seed, c, step);
-  return cgo_avm_t1(n, V, Lx, Ly, hx, hy, vc, vn, cc, cv, par[6], par[7], cap, applied);
+  return cgo_avm_t1(n, V, Lx, Ly, hx, hy, vc, vn, cc, cv, par[5], par[6], par[7], cap, applied);
 }
 
 }  // extern "C"
