@@ -310,6 +310,22 @@ int cg_triangulate_noalloc(int32_t n, double Lx, double Ly, const double* d_x, c
  * about its midpoint to length t1_length and i, k lose the edge to j, l.
  * After t1_cap passes with transitions a last pass only counts candidates:
  * any left set CG_ET1_CAP.
+ *
+ * T2 rule (cell removal; Sec. 2.A names T2 transitions, the paper's code has
+ * only T1s): with t2_area > 0, a cell with exactly 3 vertices (v0, v1, v2 its
+ * list) and d < 2 t2_area, d = px1 py2 - px2 py1 with p the minimum-image
+ * offsets from v0 (each product and the difference rounded separately), is a
+ * candidate with id 3V + c in the same passes as the T1s; its cells are c and
+ * the three across its edges, which must be distinct with more than 3
+ * vertices each (the three outer vertices distinct too); the same lock rule.
+ * It keeps the smallest of the three vertex ids at v0 + (p1 + p2)/3 (wrapped),
+ * joined to the three outer vertices; the other two are freed (their vc, vn
+ * entries -1, positions left as they were) and the cell is emptied (cc = 0,
+ * cv = -1).  Freed vertices and empty cells take no part in forces, moves or
+ * transitions (an empty cell's A, P are 0; its director still turns).  The
+ * preferred perimeter of cell c is P0_c = p0_c sqrt(A0_c) with per-cell
+ * preferred areas A0_c (cg_avm_set_a0; all A0 at creation): a cell set to
+ * die gets a small A0_c.
  * ------------------------------------------------------------------------ */
 typedef struct cg_avm_ctx cg_avm_ctx;
 
@@ -324,6 +340,7 @@ typedef struct cg_avm_params {
   uint64_t seed;        /* Philox key of the director noise */
   int32_t t1_cap;       /* T1 passes with transitions per step; 0 = 16 */
   int32_t reserved;
+  double t2_area;       /* triangular cells with area below this are removed (T2); 0: none */
 } cg_avm_params;
 
 /* Workspace size for an N-cell network in an Lx x Ly box. */
@@ -368,8 +385,12 @@ int cg_avm_t1(cg_avm_ctx* ctx);
 /* Per-cell shape index and speed, N doubles (host or device).  Synchronizes. */
 int cg_avm_set_p0(cg_avm_ctx* ctx, const double* p0);
 int cg_avm_set_v0(cg_avm_ctx* ctx, const double* v0);
-/* Counters: steps, repaired_total = T1 transitions made, last_rounds = T1
- * passes that ran (both since creation), status. */
+/* Per-cell preferred areas A0_c >= 0 (Eq. 1), N doubles (host or device);
+ * a negative or non-finite entry returns CG_EINVAL.  Synchronizes. */
+int cg_avm_set_a0(cg_avm_ctx* ctx, const double* a0);
+/* Counters: steps, repaired_total = T1 transitions made, flagged_total = T2
+ * transitions made, last_rounds = transition passes that ran (all since
+ * creation), status. */
 int cg_avm_get_counters(cg_avm_ctx* ctx, cg_counters* host_out);
 /* Releases the host context (the workspace stays the caller's). */
 int cg_avm_destroy(cg_avm_ctx* ctx);

@@ -54,7 +54,7 @@ class cg_avm_params(C.Structure):
     _fields_ = [("A0", C.c_double), ("KA", C.c_double), ("KP", C.c_double), ("mu", C.c_double),
                 ("Dr", C.c_double), ("dt", C.c_double), ("t1_threshold", C.c_double),
                 ("t1_length", C.c_double), ("seed", C.c_uint64), ("t1_cap", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("t2_area", C.c_double)]
 
 
 class cg_counters(C.Structure):
@@ -131,13 +131,14 @@ def lib():
         L.cg_avm_t1.argtypes = [vp]
         L.cg_avm_set_p0.argtypes = [vp, vp]
         L.cg_avm_set_v0.argtypes = [vp, vp]
+        L.cg_avm_set_a0.argtypes = [vp, vp]
         L.cg_avm_get_counters.argtypes = [vp, C.POINTER(cg_counters)]
         L.cg_avm_destroy.argtypes = [vp]
         L.cg_avm_last_error.argtypes = [vp]
         L.cg_avm_last_error.restype = C.c_char_p
         for name in ("cg_avm_workspace_bytes", "cg_avm_create", "cg_avm_step", "cg_avm_sync", "cg_avm_get_state",
                      "cg_avm_get_topology", "cg_avm_set_state", "cg_avm_get_geometry", "cg_avm_get_forces",
-                     "cg_avm_t1", "cg_avm_set_p0", "cg_avm_set_v0", "cg_avm_get_counters", "cg_avm_destroy",
+                     "cg_avm_t1", "cg_avm_set_p0", "cg_avm_set_v0", "cg_avm_set_a0", "cg_avm_get_counters", "cg_avm_destroy",
                      "cg_avm_profile_step"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -595,11 +596,15 @@ def cg_avm_set_v0(ctx, v0):
     _check_avm(lib().cg_avm_set_v0(ctx, _ptr(v0)), ctx)
 
 
+def cg_avm_set_a0(ctx, a0):
+    _check_avm(lib().cg_avm_set_a0(ctx, _ptr(a0)), ctx)
+
+
 def cg_avm_get_counters(ctx):
     c = cg_counters()
     _check_avm(lib().cg_avm_get_counters(ctx, C.byref(c)), ctx)
-    return {"steps": c.steps, "t1_total": c.repaired_total, "t1_passes": c.last_rounds, "status": c.status,
-            "loop_total": c.loop_total}
+    return {"steps": c.steps, "t1_total": c.repaired_total, "t2_total": c.flagged_total, "t1_passes": c.last_rounds,
+            "status": c.status, "loop_total": c.loop_total}
 
 
 def cg_avm_destroy(ctx):
@@ -612,12 +617,13 @@ class AVM:
     seed positions x, y (numpy, or torch tensors on any device)."""
 
     def __init__(self, n, Lx, Ly, x, y, theta, p0=3.8, v0=0.1, A0=1.0, KA=1.0, KP=1.0, mu=1.0, Dr=1.0, dt=0.01,
-                 t1_threshold=0.04, t1_length=0.0, seed=0, t1_cap=16, device="cuda"):
+                 t1_threshold=0.04, t1_length=0.0, seed=0, t1_cap=16, t2_area=0.0, device="cuda"):
         import torch
         self.torch = torch
         self.device = torch.device(device)
         self.n, self.V = int(n), 2 * int(n)
-        self.params = cg_avm_params(A0, KA, KP, mu, Dr, dt, t1_threshold, t1_length, int(seed), int(t1_cap), 0)
+        self.params = cg_avm_params(A0, KA, KP, mu, Dr, dt, t1_threshold, t1_length, int(seed), int(t1_cap), 0,
+                                    float(t2_area))
         nbytes = cg_avm_workspace_bytes(n, Lx, Ly)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.stream = torch.cuda.current_stream(self.device).cuda_stream
@@ -680,6 +686,11 @@ class AVM:
 
     def set_v0(self, v0):
         cg_avm_set_v0(self.ctx, self._as_input(v0))
+
+    def set_a0(self, a0):
+        """Per-cell preferred areas (a cell given a small A0 shrinks and,
+        with t2_area > 0, is removed once it is a small triangle)."""
+        cg_avm_set_a0(self.ctx, self._as_input(a0))
 
     def counters(self):
         return cg_avm_get_counters(self.ctx)

@@ -26,7 +26,8 @@ struct Lay {
 
 struct AvmOff {
   size_t spv, spv_bytes;
-  size_t hx, hy, hf, vc, vn, cc, cv, theta, p0, v0, A, P, ka, kp, energy, act, Fx, Fy, lock, cand_e, cand, done;
+  size_t hx, hy, hf, vc, vn, cc, cv, theta, p0, v0, a0, P0, A, P, ka, kp, energy, act, Fx, Fy, lock, cand_e, cand,
+      done;
   size_t owned, base_local, base_partial, xs, ys, cnt, nbr, scalar, ctl, dir_tab;
   size_t total;
 };
@@ -48,6 +49,8 @@ AvmOff avm_layout(int64_t n, size_t spv_bytes) {
   o.theta = L.take(n * d);
   o.p0 = L.take(n * d);
   o.v0 = L.take(n * d);
+  o.a0 = L.take(n * d);
+  o.P0 = L.take(n * d);
   o.A = L.take(n * d);
   o.P = L.take(n * d);
   o.ka = L.take(n * d);
@@ -57,8 +60,8 @@ AvmOff avm_layout(int64_t n, size_t spv_bytes) {
   o.Fx = L.take(V * d);
   o.Fy = L.take(V * d);
   o.lock = L.take(n * sizeof(unsigned long long));
-  o.cand_e = L.take((3 * V / 2 + 1) * i4);  // at most one entry per edge
-  o.cand = L.take((3 * V / 2 + 1) * sizeof(int4));
+  o.cand_e = L.take((3 * V / 2 + n + 1) * i4);  // at most one entry per edge and per cell
+  o.cand = L.take((3 * V / 2 + n + 1) * sizeof(int4));
   o.done = L.take(2 * sizeof(unsigned int));
   o.owned = L.take(n * i4);
   o.base_local = L.take((n + 1) * i4);
@@ -155,8 +158,8 @@ AvmArgs avm_args(cg_avm_ctx* c) {
   a.theta = c->at<double>(c->off.theta);
   a.p0 = c->at<double>(c->off.p0);
   a.v0 = c->at<double>(c->off.v0);
-  a.A0 = c->par.A0;
-  a.sqrtA0 = std::sqrt(c->par.A0);
+  a.a0 = c->at<double>(c->off.a0);
+  a.P0 = c->at<double>(c->off.P0);
   a.KA = c->par.KA;
   a.KP = c->par.KP;
   a.mu = c->par.mu;
@@ -175,6 +178,7 @@ AvmArgs avm_args(cg_avm_ctx* c) {
   a.move = 1;
   a.thr2 = c->par.t1_threshold * c->par.t1_threshold;
   a.t1_len = c->par.t1_length > 0 ? c->par.t1_length : 1.5 * c->par.t1_threshold;
+  a.t2_twice = 2.0 * c->par.t2_area;
   t1_bounds(c->par.t1_threshold, std::fmax(c->Lx, c->Ly), a.t2lo, a.t2hi);
   a.hf = c->at<float2>(c->off.hf);
   a.t1_cap = cap_of(c);
@@ -277,8 +281,9 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
   if (!out) return CG_EINVAL;
   *out = nullptr;
   if (!par || !x || !y || !theta || !d_ws || ((uintptr_t)d_ws & 255) || n < 16) return CG_EINVAL;
-  if (!(par->dt > 0) || !(par->A0 > 0) || !(par->t1_threshold >= 0)) return CG_EINVAL;
-  for (double v : {par->A0, par->KA, par->KP, par->mu, par->Dr, par->dt, par->t1_threshold, par->t1_length, p0, v0})
+  if (!(par->dt > 0) || !(par->A0 > 0) || !(par->t1_threshold >= 0) || !(par->t2_area >= 0)) return CG_EINVAL;
+  for (double v : {par->A0, par->KA, par->KP, par->mu, par->Dr, par->dt, par->t1_threshold, par->t1_length,
+                   par->t2_area, p0, v0})
     if (!std::isfinite(v)) return CG_EINVAL;
   size_t need = 0;
   int rc = cg_avm_workspace_bytes(n, Lx, Ly, &need);
@@ -349,6 +354,8 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
     launch_check_finite(n, c->at<double>(c->off.theta), c->ctl(), st);
     launch_init_dir_tables(c->at<double2>(c->off.dir_tab), st);
     launch_fill_d(n, p0, c->at<double>(c->off.p0), st);
+    launch_fill_d(n, c->par.A0, c->at<double>(c->off.a0), st);
+    launch_avm_p0s(avm_args(c), st);
     launch_fill_d(n, v0, c->at<double>(c->off.v0), st);
     launch_fill_u64(n, ~0ull, c->at<unsigned long long>(c->off.lock), st);
     if (cudaMemsetAsync(c->at<unsigned int>(c->off.done), 0, 2 * sizeof(unsigned int), st) != cudaSuccess) {
@@ -500,6 +507,14 @@ int cg_avm_set_p0(cg_avm_ctx* c, const double* p0) {
   int rc = copy_in(c, c->at<double>(c->off.p0), p0, c->n * sizeof(double));
   if (rc) return rc;
   launch_check_finite(c->n, c->at<double>(c->off.p0), c->ctl(), c->stream);
+  launch_avm_p0s(avm_args(c), c->stream);
+  return avm_status(c);
+}
+int cg_avm_set_a0(cg_avm_ctx* c, const double* a0) {
+  if (!c || !a0) return CG_EINVAL;
+  int rc = copy_in(c, c->at<double>(c->off.a0), a0, c->n * sizeof(double));
+  if (rc) return rc;
+  launch_avm_p0s(avm_args(c), c->stream);  // also refuses a negative or non-finite A0
   return avm_status(c);
 }
 
@@ -517,7 +532,7 @@ int cg_avm_get_counters(cg_avm_ctx* c, cg_counters* out) {
   Ctl h;
   AV_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
   out->steps = h.step;
-  out->flagged_total = 0;
+  out->flagged_total = h.flagged_total;    // T2 transitions
   out->repaired_total = h.repaired_total;  // T1 transitions
   out->last_flagged = 0;
   out->last_rounds = h.round_count;        // T1 passes

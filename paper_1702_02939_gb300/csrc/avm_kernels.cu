@@ -165,6 +165,18 @@ __global__ void k_avm_cells(AvmArgs g) {
   const double* hx = g.hx + cur * V;
   const double* hy = g.hy + cur * V;
   const int m = g.cc[c];
+  if (m == 0) {  // removed by a T2: no geometry, no force; the director still turns
+    g.A[c] = 0.0;
+    g.P[c] = 0.0;
+    g.ka[c] = 0.0;
+    g.kp[c] = 0.0;
+    if (g.energy) g.energy[c] = 0.0;
+    if (g.move) {
+      g.act[c] = make_double2(0.0, 0.0);
+      g.theta[c] = g.theta[c] + g.noise_amp * director_noise(g.seed, c, g.ctl->step, g.tab);
+    }
+    return;
+  }
   if (m < 3 || m > CG_RING) {
     raise_status(g.ctl, kETOPO);
     return;
@@ -193,7 +205,7 @@ __global__ void k_avm_cells(AvmArgs g) {
   const double A = 0.5 * area, P = per;
   g.A[c] = A;
   g.P[c] = P;
-  const double dA = A - g.A0, dP = P - g.p0[c] * g.sqrtA0;
+  const double dA = A - g.a0[c], dP = P - g.P0[c];
   g.ka[c] = 2.0 * g.KA * dA;
   g.kp[c] = 2.0 * g.KP * dP;
   if (g.energy) g.energy[c] = g.KA * dA * dA + g.KP * dP * dP;
@@ -215,6 +227,15 @@ __global__ void k_avm_force_move(AvmArgs g) {
   const size_t V = (size_t)g.V;
   const int cur = g.ctl->cur;
   bool ok = v < g.V;
+  if (ok && g.vc[3 * v] < 0) {  // freed by a T2: stays where it is
+    ok = false;
+    g.Fx[v] = 0.0;
+    g.Fy[v] = 0.0;
+    if (g.move) {
+      g.hx[(cur ^ 1) * V + v] = g.hx[cur * V + v];
+      g.hy[(cur ^ 1) * V + v] = g.hy[cur * V + v];
+    }
+  }
   if (ok)
     for (int k = 0; k < 3; ++k)
       if ((unsigned)g.vn[3 * v + k] >= (unsigned)g.V || (unsigned)g.vc[3 * v + k] >= (unsigned)g.n) {
@@ -304,6 +325,80 @@ __device__ __forceinline__ float t1_len2_f(const AvmArgs& g, float2 pv, float2 p
   return __fadd_rn(__fmul_rn(fx, fx), __fmul_rn(fy, fy));
 }
 
+__device__ __forceinline__ int slot3(const int* a, int v, int val) {
+  for (int s = 0; s < 3; ++s)
+    if (a[3 * v + s] == val) return s;
+  return -1;
+}
+
+// Cell other than c that has both vertices va and vb, or -1.
+__device__ __forceinline__ int cell_across(const int* __restrict__ vc, int c, int va, int vb) {
+  int r = -1;
+#pragma unroll
+  for (int s = 2; s >= 0; --s) {
+    const int x = vc[3 * va + s];
+    if (x != c && x >= 0 && (x == vc[3 * vb] || x == vc[3 * vb + 1] || x == vc[3 * vb + 2])) r = x;
+  }
+  return r;
+}
+
+// T2 proposal for the triangular cell c: twice its signed area (each product
+// and the difference rounded separately, offsets from its first vertex)
+// below twice the threshold; the cells across its three edges must be
+// distinct with more than 3 vertices and the outer vertices distinct.  The
+// candidate id is 3V + c; its cells are c and the three across its edges.
+__device__ void t2_propose(const AvmArgs& g, int c, int stamp) {
+  const size_t V = (size_t)g.V;
+  const int cur = g.ctl->cur;
+  const double* hx = g.hx + cur * V;
+  const double* hy = g.hy + cur * V;
+  const int* row = g.cv + (size_t)c * CG_RING;
+  int v[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    v[a] = row[a];
+    if ((unsigned)v[a] >= (unsigned)g.V) {
+      raise_status(g.ctl, kETOPO);
+      return;
+    }
+  }
+  const double px1 = mimg_a(hx[v[1]] - hx[v[0]], g.ax), py1 = mimg_a(hy[v[1]] - hy[v[0]], g.ay);
+  const double px2 = mimg_a(hx[v[2]] - hx[v[0]], g.ax), py2 = mimg_a(hy[v[2]] - hy[v[0]], g.ay);
+  const double d = __dsub_rn(__dmul_rn(px1, py2), __dmul_rn(px2, py1));
+  if (!(d < g.t2_twice)) return;
+  int nb[3], w[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int s = slot3(g.vc, v[a], c);
+    nb[a] = cell_across(g.vc, c, v[a], v[(a + 1) % 3]);
+    if (s < 0 || nb[a] < 0) {
+      raise_status(g.ctl, kETOPO);
+      return;
+    }
+    w[a] = g.vn[3 * v[a] + (s + 1) % 3];
+  }
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    ok &= g.cc[nb[a]] > 3;
+    ok &= nb[a] != nb[(a + 1) % 3] && w[a] != w[(a + 1) % 3];
+    ok &= w[a] != v[0] && w[a] != v[1] && w[a] != v[2];
+  }
+  if (!ok) {  // a later transition may allow it
+    g.ctl->t1_more = 1;
+    return;
+  }
+  const int e = 3 * g.V + c;
+  const unsigned long long key = lock_key(stamp, e);
+  atomicMin(&g.lock[c], key);
+  atomicMin(&g.lock[nb[0]], key);
+  atomicMin(&g.lock[nb[1]], key);
+  atomicMin(&g.lock[nb[2]], key);
+  const int slot = atomicAdd(&g.ctl->count[1], 1);
+  g.cand_e[slot] = e;
+  g.cand[slot] = make_int4(c, nb[0], nb[1], nb[2]);
+}
+
 // One thread per vertex v, its edges (v, w) with w > v.  The squared length
 // is first bounded in FP32 from the float copies of the positions; only edges
 // within the error band of the threshold are decided in FP64 in the fixed
@@ -314,10 +409,11 @@ __global__ void k_t1_propose(AvmArgs g) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   // stop the loop unless the closing kernel of this pass asks for another
   if (v == 0 && g.loop) cudaGraphSetConditional(g.loop, 0);
+  const int stamp = g.ctl->round_count;
+  if (g.t2_twice > 0.0 && v < g.n && g.cc[v] == 3) t2_propose(g, v, stamp);
   if (v >= g.V) return;
   const size_t V = (size_t)g.V;
   const float2 pv = g.hf[v];
-  const int stamp = g.ctl->round_count;
   for (int s = 0; s < 3; ++s) {
     const int e = 3 * v + s;
     const int w = g.vn[e];
@@ -360,11 +456,6 @@ __global__ void k_t1_propose(AvmArgs g) {
   }
 }
 
-__device__ __forceinline__ int slot3(const int* a, int v, int val) {
-  for (int s = 0; s < 3; ++s)
-    if (a[3 * v + s] == val) return s;
-  return -1;
-}
 
 __device__ void remove_from_cell(int* cc, int* cv, int c, int v) {
   const int m = cc[c];
@@ -535,11 +626,106 @@ __device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd) {
     insert_in_cell(g.cc, g.cv, j, v1, v2);
     insert_in_cell(g.cc, g.cv, l, v2, v1);
   }
+  // i or k left as a triangle may be removed by a T2 in the next pass
+  if (g.t2_twice > 0.0 && (g.cc[i] == 3 || g.cc[k] == 3)) ctl->t1_more = 1;
   atomicAdd((unsigned long long*)&ctl->repaired_total, 1ull);
 }
 
-// Applies the listed candidates that hold all four locks (passes 0 ..
-// t1_cap-1; pass t1_cap only counts).  The last block closes the pass:
+// Cell x's vertex list with v[0..2] replaced by vk and the repeat this makes
+// dropped (x shares one edge with the removed triangle: one vertex fewer).
+__device__ void merge_in_cell(int* cc, int* cv, int x, const int* v, int vk) {
+  const int m = cc[x];
+  int* row = cv + (size_t)x * CG_RING;
+  int out = 0;
+  for (int a = 0; a < m; ++a) {
+    int e = row[a];
+    if (e == v[0] || e == v[1] || e == v[2]) e = vk;
+    if (out > 0 && e == vk && row[out - 1] == vk) continue;
+    row[out++] = e;
+  }
+  if (out > 1 && row[0] == vk && row[out - 1] == vk) --out;
+  for (int a = out; a < CG_RING; ++a) row[a] = -1;
+  cc[x] = out;
+}
+
+// T2: the triangle c (cells across its edges cd.y, cd.z, cd.w) shrinks to
+// its centroid.  The smallest of its three vertex ids stays, joined to the
+// three outer vertices in their order around the triangle; the other two are
+// freed (vc, vn = -1) and the cell is emptied (cc = 0, cv = -1).
+__device__ void apply_t2(const AvmArgs& g, int c, int4 cd) {
+  Ctl* ctl = g.ctl;
+  const size_t V = (size_t)g.V;
+  double* hx = g.hx + ctl->cur * V;
+  double* hy = g.hy + ctl->cur * V;
+  int* row = g.cv + (size_t)c * CG_RING;
+  int v[3], w[3], cp[3], cpp[3];
+  const int nb[3] = {cd.y, cd.z, cd.w};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) v[a] = row[a];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int s = slot3(g.vc, v[a], c);
+    if (s < 0) {
+      raise_status(ctl, kETOPO);
+      return;
+    }
+    w[a] = g.vn[3 * v[a] + (s + 1) % 3];
+    cp[a] = g.vc[3 * v[a] + (s + 1) % 3];
+    cpp[a] = g.vc[3 * v[a] + (s + 2) % 3];
+  }
+  const int vk = min(v[0], min(v[1], v[2]));
+  // centroid relative to the first vertex of the list
+  const double dx1 = mimg_a(hx[v[1]] - hx[v[0]], g.ax), dy1 = mimg_a(hy[v[1]] - hy[v[0]], g.ay);
+  const double dx2 = mimg_a(hx[v[2]] - hx[v[0]], g.ax), dy2 = mimg_a(hy[v[2]] - hy[v[0]], g.ay);
+  const double cx = wrap_a(hx[v[0]] + (dx1 + dx2) / 3.0, g.ax);
+  const double cy = wrap_a(hy[v[0]] + (dy1 + dy2) / 3.0, g.ay);
+  // outer edges around the kept vertex: from a = 0, each next one starts in
+  // the cell where the previous one ends
+  int ord[3] = {0, -1, -1};
+#pragma unroll
+  for (int q = 1; q < 3; ++q)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (cp[a] == cpp[ord[q - 1]] && a != ord[0] && (q < 2 || a != ord[1])) ord[q] = a;
+  if (ord[1] < 0 || ord[2] < 0 || cpp[ord[2]] != cp[ord[0]]) {
+    raise_status(ctl, kETOPO);
+    return;
+  }
+  int so[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    so[a] = slot3(g.vn, w[a], v[a]);
+    if (so[a] < 0) {
+      raise_status(ctl, kETOPO);
+      return;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) g.vn[3 * w[a] + so[a]] = vk;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) merge_in_cell(g.cc, g.cv, nb[a], v, vk);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    g.vc[3 * vk + q] = cp[ord[q]];
+    g.vn[3 * vk + q] = w[ord[q]];
+  }
+  hx[vk] = cx;
+  hy[vk] = cy;
+  g.hf[vk] = make_float2((float)cx, (float)cy);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (v[a] != vk)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) g.vc[3 * v[a] + q] = g.vn[3 * v[a] + q] = -1;
+#pragma unroll
+  for (int a = 0; a < CG_RING; ++a) row[a] = -1;
+  g.cc[c] = 0;
+  ctl->t1_more = 1;  // the merged vertex's edges and the neighbours' counts changed
+  atomicAdd((unsigned long long*)&ctl->flagged_total, 1ull);
+}
+
+// Applies the listed candidates (T1 edges, T2 cells) that hold all four
+// locks (passes 0 .. t1_cap-1; pass t1_cap only counts).  The last block closes the pass:
 // another pass runs while this one may have left work (a candidate that lost
 // a lock, an edge at a moved vertex within the FP32 bound of the threshold,
 // or a short edge its cells kept from flipping) and the cap is not reached;
@@ -559,7 +745,8 @@ __global__ void k_t1_apply(AvmArgs g) {
         ctl->t1_more = 1;
         continue;
       }
-      apply_t1(g, e / 3, e % 3, cd);
+      if (e >= 3 * g.V) apply_t2(g, e - 3 * g.V, cd);
+      else apply_t1(g, e / 3, e % 3, cd);
     }
   }
   if (last_block(g.done + 1) && threadIdx.x == 0) {
@@ -589,16 +776,28 @@ __global__ void k_avm_shadow(AvmArgs g) {
 __global__ void k_avm_validate(AvmArgs g) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   bool bad = false;
-  if (t < g.V)
+  if (t < g.V) {
+    const bool freed = g.vc[3 * t] < 0;  // freed by a T2: all six entries -1
     for (int k = 0; k < 3; ++k)
-      bad |= (unsigned)g.vc[3 * t + k] >= (unsigned)g.n || (unsigned)g.vn[3 * t + k] >= (unsigned)g.V;
+      bad |= freed ? (g.vc[3 * t + k] != -1 || g.vn[3 * t + k] != -1)
+                   : ((unsigned)g.vc[3 * t + k] >= (unsigned)g.n || (unsigned)g.vn[3 * t + k] >= (unsigned)g.V);
+  }
   if (t < g.n) {
-    const int m = g.cc[t];
-    if (m < 3 || m > CG_RING) bad = true;
+    const int m = g.cc[t];  // 0: removed by a T2
+    if (m != 0 && (m < 3 || m > CG_RING)) bad = true;
     else
       for (int a = 0; a < m; ++a) bad |= (unsigned)g.cv[(size_t)t * CG_RING + a] >= (unsigned)g.V;
   }
   if (bad) raise_status(g.ctl, kEINVAL);
+}
+
+// Preferred perimeters P0_c = p0_c sqrt(A0_c); A0_c must be finite and >= 0.
+__global__ void k_avm_p0s(AvmArgs g) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.n) return;
+  const double a0 = g.a0[c];
+  if (!(a0 >= 0.0) || !isfinite(a0)) raise_status(g.ctl, kEINVAL);
+  g.P0[c] = g.p0[c] * sqrt(a0);
 }
 
 __global__ void k_fill_d(int n, double v, double* out) {
@@ -641,6 +840,9 @@ void launch_avm_forces(const AvmArgs& a, cudaStream_t st) {
   f.move = 0;
   k_avm_cells<<<cell_blocks_of(a.n), kAvmCellThreads, 0, st>>>(f);
   k_avm_force_move<<<vertex_blocks_of(a.V), kAvmVertexThreads, 0, st>>>(f);
+}
+void launch_avm_p0s(const AvmArgs& a, cudaStream_t st) {
+  k_avm_p0s<<<blocks_of(a.n), kAvmThreads, 0, st>>>(a);
 }
 void launch_avm_validate(const AvmArgs& a, cudaStream_t st) {
   k_avm_validate<<<blocks_of(a.V), kAvmThreads, 0, st>>>(a);

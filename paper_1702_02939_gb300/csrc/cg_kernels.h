@@ -251,7 +251,9 @@ struct AvmArgs {
   int *vc, *vn, *cc, *cv;
   double* theta;
   const double *p0, *v0;
-  double A0, sqrtA0, KA, KP, mu, dt, noise_amp;
+  const double* a0;        // [n] preferred areas A0_c
+  double* P0;              // [n] preferred perimeters p0_c sqrt(A0_c)
+  double KA, KP, mu, dt, noise_amp;
   unsigned long long seed;
   const double2* tab;      // director table (dir_math.cuh)
   double *A, *P, *ka, *kp, *energy;
@@ -259,12 +261,13 @@ struct AvmArgs {
   double *Fx, *Fy;
   int move;
   double thr2, t1_len;
+  double t2_twice;           // T2: twice the area threshold (0: no T2)
   float t2lo, t2hi;          // FP32 squared lengths certainly below / above thr2
   float2* hf;                // [V] float copies of the current positions
   int t1_cap, apply_blocks;
   unsigned long long* lock;  // [n] pass-stamped T1 locks
-  int* cand_e;               // [3V/2] proposed edges (ids), compacted
-  int4* cand;                // [3V/2] their cells (i, j, k, l)
+  int* cand_e;               // [3V/2 + n] proposed edge ids 3v+s, or 3V + c for a T2 of cell c
+  int4* cand;                // [3V/2 + n] their cells (i, j, k, l), or (c, and the three across its edges)
   unsigned int* done;        // [2] last-block counters (force/move, T1 apply)
   cudaGraphConditionalHandle loop;  // while-node handle of the T1 passes
 };
@@ -275,6 +278,8 @@ void launch_avm_begin_t1(Ctl* ctl, cudaStream_t st);
 void launch_avm_t1_pass(const AvmArgs& a, cudaStream_t st);
 void launch_avm_forces(const AvmArgs& a, cudaStream_t st);
 void launch_avm_validate(const AvmArgs& a, cudaStream_t st);
+// P0[c] = p0[c] sqrt(a0[c]) after p0 or A0 change
+void launch_avm_p0s(const AvmArgs& a, cudaStream_t st);
 void launch_avm_shadow(const AvmArgs& a, cudaStream_t st);
 void launch_fill_d(int n, double v, double* out, cudaStream_t st);
 void launch_fill_u64(int n, unsigned long long v, unsigned long long* out, cudaStream_t st);

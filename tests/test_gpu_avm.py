@@ -229,21 +229,30 @@ def test_profiled_steps_equal_graph_steps():
 
 def check_network_valid(sim, Lx, Ly, p0):
     """Properties that hold at any size: degree 3, symmetric neighbour lists,
-    cell lists consistent with vertex lists, areas positive and tiling the box."""
+    cell lists consistent with vertex lists, areas positive and tiling the box;
+    vertices freed and cells emptied by T2s (vc, vn = -1; cc = 0, A = 0) excluded,
+    two vertices per remaining cell."""
     g, _ = gpu_net(sim, Lx, Ly)
     V, n = g.V, g.n
     vc, vn = g.vc.reshape(V, 3), g.vn.reshape(V, 3)
-    assert np.all(np.bincount(g.vn, minlength=V) == 3)
+    free = vc[:, 0] < 0
+    assert np.all(vc[free] == -1) and np.all(vn[free] == -1)
+    alive = g.cc > 0
+    assert int((~free).sum()) == 2 * int(alive.sum())
+    live = np.nonzero(~free)[0]
+    assert np.all(np.bincount(vn[live].ravel(), minlength=V)[live] == 3)
     for s in range(3):
-        w = vn[:, s]
-        assert np.all((vn[w] == np.arange(V)[:, None]).any(1))
-    assert int(g.cc.sum()) == 3 * V
+        w = vn[live, s]
+        assert np.all(w >= 0) and not np.any(free[w])
+        assert np.all((vn[w] == live[:, None]).any(1))
+        assert np.all(alive[vc[live, s]])
+    assert int(g.cc.sum()) == 3 * len(live)
     cv = g.cv.reshape(n, R)
     for c in range(0, n, max(1, n // 300)):
         for a in range(g.cc[c]):
             assert c in vc[cv[c, a]]
     A, P = (t.cpu().numpy() for t in sim.geometry())
-    assert np.all(A > 0)
+    assert np.all(A[alive] > 0) and np.all(A[~alive] == 0.0)
     assert abs(A.sum() - Lx * Ly) <= 1e-9 * Lx * Ly
     return g
 
@@ -350,4 +359,69 @@ def test_rectangular_box():
     g, gth = gpu_net(sim, Lx, Ly)
     o, oth, _ = oracle.avm_step(net, th, 3.8, 0.1, seed=3, step=0, thr=0.1)
     assert_same_network(g, o)
+    sim.close()
+
+
+def test_t2_dying_cells_match_oracle():
+    """Cells given A0 = 0 shrink, become triangles through T1s and are removed
+    by T2s: every step (move, directors, T1 and T2 passes) equals the oracle's
+    step from the same state (network exact, positions within 1e-12 L)."""
+    n, p0, v0, thr, t2 = 400, 3.8, 0.05, 0.04, 0.01
+    sim, xs, ys, th, Lx, Ly = make(n, 21, p0=p0, v0=v0, t1_threshold=thr, t2_area=t2, seed=4)
+    net = oracle.avm_build(xs, ys, Lx, Ly)
+    rng = np.random.default_rng(1)
+    a0 = np.ones(n)
+    dying = rng.choice(n, 8, replace=False)
+    a0[dying] = 0.0
+    sim.set_a0(a0)
+    load(sim, net, th)
+    o, oth = net, th
+    total_t1 = total_t2 = 0
+    for k in range(160):
+        sim.step(1)
+        g, gth = gpu_net(sim, Lx, Ly)
+        o, oth, k1, k2 = oracle.avm_step(o, oth, p0, v0, seed=4, step=k, A0=a0, thr=thr, t2_area=t2, counts=True)
+        assert_same_network(g, o)
+        np.testing.assert_allclose(gth, oth, rtol=0, atol=1e-13)
+        total_t1 += k1
+        total_t2 += k2
+        load(sim, o, oth)  # the next step from the oracle's state
+    assert total_t2 >= 4
+    assert set(np.nonzero(o.cc == 0)[0].tolist()) <= set(dying.tolist())
+    c = sim.counters()
+    assert c["t2_total"] == total_t2 and c["t1_total"] == total_t1
+    Fx, Fy, _ = sim.forces()
+    oFx, oFy, *_ = oracle.avm_forces(o, p0, A0=a0)
+    scale = max(np.abs(oFx).max(), np.abs(oFy).max())
+    assert np.abs(Fx.cpu().numpy() - oFx).max() <= F_TOL * scale
+    sim.close()
+
+
+def test_per_cell_a0_is_checked():
+    sim, *_ = make(400, 22)
+    bad = np.ones(400)
+    bad[3] = -1.0
+    with pytest.raises(cg.CellgbError) as e:
+        sim.set_a0(bad)
+    assert e.value.code == -1
+    sim.close()
+
+
+def test_full_size_with_cell_death():
+    """N = 65536 with 1% of the cells set to die: after 400 graph steps every
+    dying cell that was removed is one of them, the counters agree with the
+    emptied cells, and the network is still a valid tiling."""
+    n, p0, v0, thr = 65536, 3.8, 0.1, 0.04
+    sim, xs, ys, th, Lx, Ly = make(n, 1, p0=p0, v0=v0, t1_threshold=thr, t2_area=0.01, seed=1)
+    rng = np.random.default_rng(7)
+    a0 = np.ones(n)
+    dying = rng.choice(n, n // 100, replace=False)
+    a0[dying] = 0.0
+    sim.set_a0(a0)
+    sim.step(400)
+    sim.sync()
+    g = check_network_valid(sim, Lx, Ly, p0)
+    removed = set(np.nonzero(g.cc == 0)[0].tolist())
+    assert len(removed) > n // 200 and removed <= set(dying.tolist())
+    assert sim.counters()["t2_total"] == len(removed)
     sim.close()
