@@ -445,7 +445,52 @@ def avm_throughput(args, device):
                                   "t1_passes": ph["t1_ms"] / prof_steps,
                                   "t1_passes_count": ph["t1_passes"] / prof_steps},
             "cpu_oracle": {"value": V * steps / el, "unit": "vertex-steps/s", "cores": 1, "kind": "oracle",
-                           "sample": f"{steps} oracle AVM steps of the same N={n} network, {el:.1f} s"}}
+                           "sample": f"{steps} oracle AVM steps of the same N={n} network, {el:.1f} s"},
+            "cell_death": avm_death_throughput(args, device)}
+
+
+def avm_death_throughput(args, device):
+    """The AVM workload with T2 transitions: 1% of the cells get A0 = 0 and
+    are removed once they are triangles of area below 0.01 (T2 passes share
+    the T1 passes).  After the same warm-up, each step is timed alone with
+    CUDA events (L2 flushed in between) while the dying cells are removed."""
+    import numpy as np
+    import torch
+
+    import paper_1702_02939_gb300 as cg
+    import workloads
+
+    if args.avm_steps == 0:  # profiled steps only
+        return None
+    n, thr, p0, v0 = 65536, 0.04, 3.8, 0.1
+    x, y, th, L = workloads.spv_uniform(n, 21)
+    sim = cg.AVM(n, L, L, x, y, th, p0=p0, v0=v0, dt=DT, t1_threshold=thr, t2_area=0.01, seed=21, device=device)
+    sim.step(args.avm_warmup)
+    a0 = np.ones(n)
+    a0[np.random.default_rng(5).choice(n, n // 100, replace=False)] = 0.0
+    sim.set_a0(a0)
+    sim.sync()
+    c0 = sim.counters()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    K = args.avm_steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record(stream)
+        sim.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    sim.sync()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    c1 = sim.counters()
+    removed = int((sim.topology()[2] == 0).sum())
+    sim.close()
+    return {"workload": "avm_N65536_L256_p0_3.8_v0_0.1_thr0.04_t2area0.01_dying1pct_fp64", "unit": "vertex-steps/s",
+            "vertex_steps_per_s": 2 * n * K / (ms * 1e-3), "ms_per_step": ms / K, "steps": K,
+            "t2_per_step": (c1["t2_total"] - c0["t2_total"]) / K, "t1_per_step": (c1["t1_total"] - c0["t1_total"]) / K,
+            "cells_removed": removed, "dying": n // 100}
 
 
 def sweep(args):
