@@ -339,12 +339,17 @@ typedef struct cg_avm_params {
   double t1_length;     /* length of the rotated edge; 0 = 1.5 t1_threshold */
   uint64_t seed;        /* Philox key of the director noise */
   int32_t t1_cap;       /* T1 passes with transitions per step; 0 = 16 */
-  int32_t reserved;
+  int32_t cell_capacity; /* cell slots, >= N (0: N); divisions fill slots N, N+1, ...
+                            and vertex slots 2N, 2N+1, ... */
   double t2_area;       /* triangular cells with area below this are removed (T2); 0: none */
 } cg_avm_params;
 
 /* Workspace size for an N-cell network in an Lx x Ly box. */
 int cg_avm_workspace_bytes(int32_t n, double Lx, double Ly, size_t* bytes);
+/* The same with room for `capacity` cells (N <= capacity <= 2^26): every
+ * per-cell array then has `capacity` entries and every per-vertex array
+ * 2 capacity (slots past the network: empty cells, free vertices). */
+int cg_avm_workspace_bytes_capacity(int32_t n, int32_t capacity, double Lx, double Ly, size_t* bytes);
 /* Builds the Voronoi network of the seeds x, y (n doubles each, host or
  * device, in [-L, 2L), snapped to the position grid as cg_create does) with
  * directors theta, per-cell shape index p0 and speed v0.  d_ws: device,

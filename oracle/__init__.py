@@ -66,7 +66,9 @@ def _declare(L):
                              C.c_double, C.c_double, C.c_int, _ip]
     L.cgo_avm_step.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _ip, _ip, _ip, _ip, _dp, _dp,
                                _dp, _dp, C.c_uint64, C.c_int64, C.c_int, _ip]
-    for name in ("cgo_avm_build", "cgo_avm_forces", "cgo_avm_t1", "cgo_avm_step"):
+    L.cgo_avm_divide.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _ip, _ip, _ip, _ip, _dp, _dp,
+                                 _dp, _dp, C.c_int, _ip, _dp, _ip, _ip, _ip]
+    for name in ("cgo_avm_build", "cgo_avm_forces", "cgo_avm_t1", "cgo_avm_step", "cgo_avm_divide"):
         getattr(L, name).restype = C.c_int
     for extra in ("_declare_avm", "_declare_adjoint"):
         fn = globals().get(extra)
@@ -336,6 +338,18 @@ class AvmNet:
         return (self.n, self.V, self.Lx, self.Ly, _d(self.hx), _d(self.hy), _i(self.vc), _i(self.vn), _i(self.cc),
                 _i(self.cv))
 
+    def with_capacity(self, cap):
+        """The network with `cap` cell slots (2 cap vertex slots): slots past
+        the network are empty cells (cc 0, cv -1) and free vertices (-1)."""
+        n, V = self.n, self.V
+        hx, hy = np.zeros(2 * cap), np.zeros(2 * cap)
+        hx[:V], hy[:V] = self.hx, self.hy
+        vc, vn = np.full(6 * cap, -1, np.int32), np.full(6 * cap, -1, np.int32)
+        vc[:3 * V], vn[:3 * V] = self.vc, self.vn
+        cc, cv = np.zeros(cap, np.int32), np.full(cap * MAX_RING, -1, np.int32)
+        cc[:n], cv[:n * MAX_RING] = self.cc, self.cv
+        return AvmNet(cap, self.Lx, self.Ly, hx, hy, vc, vn, cc, cv)
+
 
 def avm_build(x, y, Lx, Ly):
     """Voronoi tessellation of the seed positions as a vertex network."""
@@ -375,6 +389,20 @@ def avm_transitions(net, thr, newlen=None, t2_area=0.0, cap=16, allow_cap=False)
     if not (allow_cap and rc == -8):
         _check(rc, "avm_t1")
     return net, int(applied[0]), int(applied[1])
+
+
+def avm_divide(net, cells, dirs, next_cell, next_vertex, theta, p0, v0, a0):
+    """Divisions of cells[k] along dirs[k] = (ux, uy), in order, on copies.
+    Returns (network, theta, p0, v0, a0, next_cell, next_vertex, made)."""
+    net = net.copy()
+    theta, p0, v0, a0 = (np.array(a, np.float64, copy=True) for a in (theta, p0, v0, a0))
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1)
+    nc, nv = np.array([next_cell], np.int32), np.array([next_vertex], np.int32)
+    made = np.zeros(len(cells), np.int32)
+    _check(lib().cgo_avm_divide(*net._args(), _d(theta), _d(p0), _d(v0), _d(a0), len(cells), _i(cells), _d(dirs),
+                                _i(nc), _i(nv), _i(made)), "avm_divide")
+    return net, theta, p0, v0, a0, int(nc[0]), int(nv[0]), made
 
 
 def avm_t1(net, thr, newlen=None, cap=16, allow_cap=False):

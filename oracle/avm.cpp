@@ -46,7 +46,21 @@
 //    the cell is emptied (cc = 0, cv = -1); around the kept vertex the
 //    outer edges keep their order; each neighbour cell loses one vertex;
 //  * free vertices and empty cells take no part in forces, moves or
-//    transitions (their positions stay); P0_c = p0_c sqrt(A0_c).
+//    transitions (their positions stay); P0_c = p0_c sqrt(A0_c);
+//  * division of cell c along direction u (cell division, named in Sec. 2.A
+//    as a feature of vertex models; the paper's code has none): with p the
+//    minimum-image offsets of its vertices from its first vertex, m their
+//    mean (sum in list order, then / count), q = p - m and s_a = u x q_a, an
+//    edge a -> a+1 is cut where s changes sign (s > 0 against s <= 0) at
+//    X = q_a + t (q_{a+1} - q_a), t = s_a / (s_a - s_{a+1}) clamped to
+//    [1/16, 15/16]; of the cuts, the one with the smallest u.X > 0 (new
+//    vertex A, edge a1) and the one with the largest u.X < 0 (new vertex B,
+//    edge a2) are taken (every product, sum and quotient rounded on its own);
+//    c keeps A, v_{a1+1} .. v_{a2}, B and the new cell B, v_{a2+1} ..
+//    v_{a1}, A; the cells across the cut edges gain A and B; the new cell
+//    copies c's director, p0, v0 and A0.  Refused (no change) when a cut is
+//    missing, a daughter would exceed 16 vertices or a neighbour could not
+//    take the new vertex.
 #include "internal.h"
 
 #include <climits>
@@ -376,6 +390,114 @@ int topo_pass(Net& g, double thr, double newlen, double t2_area, int* remaining,
   return applied;
 }
 
+// Division of cell c along (ux, uy) into c and newc, new vertices va (A) and
+// vb (B); per-cell arrays copied to newc.  0 made, 1 refused, -1 broken.
+int divide_cell(Net& g, int c, double ux, double uy, int newc, int va, int vb, double* theta, double* p0,
+                double* v0, double* a0) {
+  const int m = g.cc[c];
+  if (m < 3) return 1;
+  std::vector<int> v(m);
+  for (int a = 0; a < m; ++a) v[a] = g.cv[c * kR + a];
+  std::vector<double> qx(m), qy(m), sd(m);
+  volatile double sx = 0.0, sy = 0.0;
+  std::vector<double> px(m), py(m);
+  for (int a = 0; a < m; ++a) {
+    px[a] = mimg(g.hx[v[a]] - g.hx[v[0]], g.Lx);
+    py[a] = mimg(g.hy[v[a]] - g.hy[v[0]], g.Ly);
+  }
+  for (int a = 1; a < m; ++a) {
+    sx = sx + px[a];
+    sy = sy + py[a];
+  }
+  const double mx = sx / (double)m, my = sy / (double)m;
+  for (int a = 0; a < m; ++a) {
+    qx[a] = px[a] - mx;
+    qy[a] = py[a] - my;
+    volatile double t1 = ux * qy[a];
+    volatile double t2 = uy * qx[a];
+    sd[a] = t1 - t2;
+  }
+  int a1 = -1, a2 = -1;
+  double l1 = 0.0, l2 = 0.0, X1x = 0.0, X1y = 0.0, X2x = 0.0, X2y = 0.0;
+  for (int a = 0; a < m; ++a) {
+    const int b = (a + 1) % m;
+    if ((sd[a] > 0.0) == (sd[b] > 0.0)) continue;
+    volatile double den = sd[a] - sd[b];
+    double t = sd[a] / den;
+    if (t < 0.0625) t = 0.0625;
+    if (t > 0.9375) t = 0.9375;
+    volatile double dx = qx[b] - qx[a], dy = qy[b] - qy[a];
+    volatile double tx = t * dx, ty = t * dy;
+    volatile double Xx = qx[a] + tx, Xy = qy[a] + ty;
+    volatile double lx = ux * Xx, ly = uy * Xy;
+    const double lam = lx + ly;
+    if (lam > 0.0 && (a1 < 0 || lam < l1)) { a1 = a; l1 = lam; X1x = Xx; X1y = Xy; }
+    if (lam < 0.0 && (a2 < 0 || lam > l2)) { a2 = a; l2 = lam; X2x = Xx; X2y = Xy; }
+  }
+  if (a1 < 0 || a2 < 0) return 1;
+  const int n1 = (a2 - a1 + m) % m + 2, n2 = (a1 - a2 + m) % m + 2;
+  if (n1 > kR || n2 > kR) return 1;
+  const int p1 = v[a1], p1n = v[(a1 + 1) % m], p2 = v[a2], p2n = v[(a2 + 1) % m];
+  int x1 = -1, x2 = -1;
+  for (int s = 0; s < 3; ++s) {
+    const int y1 = g.vc[3 * p1 + s], y2 = g.vc[3 * p2 + s];
+    if (y1 != c && (y1 == g.vc[3 * p1n] || y1 == g.vc[3 * p1n + 1] || y1 == g.vc[3 * p1n + 2])) x1 = y1;
+    if (y2 != c && (y2 == g.vc[3 * p2n] || y2 == g.vc[3 * p2n + 1] || y2 == g.vc[3 * p2n + 2])) x2 = y2;
+  }
+  if (x1 < 0 || x2 < 0) return -1;
+  if (g.cc[x1] + (x1 == x2 ? 2 : 1) > kR) return 1;
+  if (x1 != x2 && g.cc[x2] + 1 > kR) return 1;
+  // positions
+  volatile double ax = mx + X1x, ay = my + X1y, bx = mx + X2x, by = my + X2y;
+  const double x0 = g.hx[v[0]], y0 = g.hy[v[0]];
+  // vertex neighbours along the cut edges
+  const int s1 = slot_of(g.vn, p1, p1n), s1n = slot_of(g.vn, p1n, p1);
+  const int s2 = slot_of(g.vn, p2, p2n), s2n = slot_of(g.vn, p2n, p2);
+  if (s1 < 0 || s1n < 0 || s2 < 0 || s2n < 0) return -1;
+  g.vn[3 * p1 + s1] = va;
+  g.vn[3 * p1n + s1n] = va;
+  g.vn[3 * p2 + s2] = vb;
+  g.vn[3 * p2n + s2n] = vb;
+  // the vertices of the new cell move from c to newc
+  std::vector<int> d1, d2;
+  d1.push_back(va);
+  for (int a = (a1 + 1) % m;; a = (a + 1) % m) {
+    d1.push_back(v[a]);
+    if (a == a2) break;
+  }
+  d1.push_back(vb);
+  d2.push_back(vb);
+  for (int a = (a2 + 1) % m;; a = (a + 1) % m) {
+    d2.push_back(v[a]);
+    const int s = slot_of(g.vc, v[a], c);
+    if (s < 0) return -1;
+    g.vc[3 * v[a] + s] = newc;
+    if (a == a1) break;
+  }
+  d2.push_back(va);
+  for (int a = 0; a < kR; ++a) {
+    g.cv[c * kR + a] = a < (int)d1.size() ? d1[a] : -1;
+    g.cv[newc * kR + a] = a < (int)d2.size() ? d2[a] : -1;
+  }
+  g.cc[c] = (int)d1.size();
+  g.cc[newc] = (int)d2.size();
+  insert_after(g, x1, p1n, va);
+  insert_after(g, x2, p2n, vb);
+  g.vc[3 * va] = x1; g.vc[3 * va + 1] = c; g.vc[3 * va + 2] = newc;
+  g.vn[3 * va] = p1n; g.vn[3 * va + 1] = vb; g.vn[3 * va + 2] = p1;
+  g.vc[3 * vb] = x2; g.vc[3 * vb + 1] = newc; g.vc[3 * vb + 2] = c;
+  g.vn[3 * vb] = p2n; g.vn[3 * vb + 1] = va; g.vn[3 * vb + 2] = p2;
+  g.hx[va] = wrapL(x0 + ax, g.Lx);
+  g.hy[va] = wrapL(y0 + ay, g.Ly);
+  g.hx[vb] = wrapL(x0 + bx, g.Lx);
+  g.hy[vb] = wrapL(y0 + by, g.Ly);
+  theta[newc] = theta[c];
+  p0[newc] = p0[c];
+  v0[newc] = v0[c];
+  a0[newc] = a0[c];
+  return 0;
+}
+
 }  // namespace
 }  // namespace cgo
 
@@ -518,6 +640,30 @@ int cgo_avm_step(int n, int V, double Lx, double Ly, double* hx, double* hy, dou
   const double s = std::sqrt(2.0 * Dr * dt);
   for (int c = 0; c < n; ++c) theta[c] = theta[c] + s * cgo_director_noise(seed, c, step);
   return cgo_avm_t1(n, V, Lx, Ly, hx, hy, vc, vn, cc, cv, par[5], par[6], par[7], cap, applied);
+}
+
+// Divisions of cells[k] along dirs[2k], dirs[2k+1], in order; each made one
+// takes cell slot *next_cell and vertex slots *next_vertex, +1 (advanced).
+// made[k] = 1 when division k was made.  Returns -22 on a broken network,
+// -1 when the slots run out.
+int cgo_avm_divide(int n, int V, double Lx, double Ly, double* hx, double* hy, int32_t* vc, int32_t* vn,
+                   int32_t* cc, int32_t* cv, double* theta, double* p0, double* v0, double* a0, int count,
+                   const int32_t* cells, const double* dirs, int32_t* next_cell, int32_t* next_vertex,
+                   int32_t* made) {
+  Net g{n, V, Lx, Ly, hx, hy, vc, vn, cc, cv};
+  for (int k = 0; k < count; ++k) {
+    made[k] = 0;
+    if (*next_cell >= n || *next_vertex + 2 > V) return -1;
+    const int r = divide_cell(g, cells[k], dirs[2 * k], dirs[2 * k + 1], *next_cell, *next_vertex,
+                              *next_vertex + 1, theta, p0, v0, a0);
+    if (r < 0) return -22;
+    if (r == 0) {
+      made[k] = 1;
+      *next_cell += 1;
+      *next_vertex += 2;
+    }
+  }
+  return 0;
 }
 
 }  // extern "C"

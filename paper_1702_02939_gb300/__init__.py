@@ -54,7 +54,7 @@ class cg_avm_params(C.Structure):
     _fields_ = [("A0", C.c_double), ("KA", C.c_double), ("KP", C.c_double), ("mu", C.c_double),
                 ("Dr", C.c_double), ("dt", C.c_double), ("t1_threshold", C.c_double),
                 ("t1_length", C.c_double), ("seed", C.c_uint64), ("t1_cap", C.c_int32),
-                ("reserved", C.c_int32), ("t2_area", C.c_double)]
+                ("cell_capacity", C.c_int32), ("t2_area", C.c_double)]
 
 
 class cg_counters(C.Structure):
@@ -118,6 +118,7 @@ def lib():
             getattr(L, name).restype = C.c_int
         # active vertex model
         L.cg_avm_workspace_bytes.argtypes = [i32, C.c_double, C.c_double, C.POINTER(C.c_size_t)]
+        L.cg_avm_workspace_bytes_capacity.argtypes = [i32, i32, C.c_double, C.c_double, C.POINTER(C.c_size_t)]
         L.cg_avm_create.argtypes = [i32, C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(cg_avm_params),
                                     vp, vp, vp, vp, C.c_size_t, vp, C.POINTER(vp)]
         L.cg_avm_step.argtypes = [vp, i64]
@@ -136,7 +137,7 @@ def lib():
         L.cg_avm_destroy.argtypes = [vp]
         L.cg_avm_last_error.argtypes = [vp]
         L.cg_avm_last_error.restype = C.c_char_p
-        for name in ("cg_avm_workspace_bytes", "cg_avm_create", "cg_avm_step", "cg_avm_sync", "cg_avm_get_state",
+        for name in ("cg_avm_workspace_bytes", "cg_avm_workspace_bytes_capacity", "cg_avm_create", "cg_avm_step", "cg_avm_sync", "cg_avm_get_state",
                      "cg_avm_get_topology", "cg_avm_set_state", "cg_avm_get_geometry", "cg_avm_get_forces",
                      "cg_avm_t1", "cg_avm_set_p0", "cg_avm_set_v0", "cg_avm_set_a0", "cg_avm_get_counters", "cg_avm_destroy",
                      "cg_avm_profile_step"):
@@ -539,6 +540,12 @@ def cg_avm_workspace_bytes(n, Lx, Ly):
     return out.value
 
 
+def cg_avm_workspace_bytes_capacity(n, capacity, Lx, Ly):
+    out = C.c_size_t(0)
+    _check_avm(lib().cg_avm_workspace_bytes_capacity(int(n), int(capacity), float(Lx), float(Ly), C.byref(out)))
+    return out.value
+
+
 def cg_avm_create(n, Lx, Ly, p0, v0, params, x, y, theta, workspace, stream):
     ctx = C.c_void_p()
     _check_avm(lib().cg_avm_create(int(n), float(Lx), float(Ly), float(p0), float(v0), C.byref(params), _ptr(x),
@@ -617,14 +624,18 @@ class AVM:
     seed positions x, y (numpy, or torch tensors on any device)."""
 
     def __init__(self, n, Lx, Ly, x, y, theta, p0=3.8, v0=0.1, A0=1.0, KA=1.0, KP=1.0, mu=1.0, Dr=1.0, dt=0.01,
-                 t1_threshold=0.04, t1_length=0.0, seed=0, t1_cap=16, t2_area=0.0, device="cuda"):
+                 t1_threshold=0.04, t1_length=0.0, seed=0, t1_cap=16, t2_area=0.0, capacity=None, device="cuda"):
+        """n seeds; `capacity` cell slots (default n) leave room for divisions:
+        per-cell outputs then have `capacity` entries, per-vertex ones 2x."""
         import torch
         self.torch = torch
         self.device = torch.device(device)
-        self.n, self.V = int(n), 2 * int(n)
-        self.params = cg_avm_params(A0, KA, KP, mu, Dr, dt, t1_threshold, t1_length, int(seed), int(t1_cap), 0,
+        cap = int(n) if capacity is None else int(capacity)
+        self.n_seed = int(n)
+        self.n, self.V = cap, 2 * cap
+        self.params = cg_avm_params(A0, KA, KP, mu, Dr, dt, t1_threshold, t1_length, int(seed), int(t1_cap), cap,
                                     float(t2_area))
-        nbytes = cg_avm_workspace_bytes(n, Lx, Ly)
+        nbytes = cg_avm_workspace_bytes_capacity(n, cap, Lx, Ly)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.stream = torch.cuda.current_stream(self.device).cuda_stream
         xs, ys, ts = (self._as_input(v) for v in (x, y, theta))

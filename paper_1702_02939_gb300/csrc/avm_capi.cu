@@ -80,7 +80,9 @@ AvmOff avm_layout(int64_t n, size_t spv_bytes) {
 }  // namespace
 
 struct cg_avm_ctx {
-  int n = 0, V = 0;
+  int n = 0, V = 0;        // cell slots (the capacity) and vertex slots (2n)
+  int n_seed = 0;          // cells of the initial network (slots 0 .. n_seed-1)
+  int next_cell = 0, next_vertex = 0;  // first slots never used (divisions take them in order)
   double Lx = 0, Ly = 0;
   cg_avm_params par{};
   char* ws = nullptr;
@@ -267,12 +269,16 @@ int copy_out(cg_avm_ctx* c, void* dst, const void* src, size_t bytes) {
 extern "C" {
 
 int cg_avm_workspace_bytes(int32_t n, double Lx, double Ly, size_t* bytes) {
-  if (!bytes || n < 16) return CG_EINVAL;
+  return cg_avm_workspace_bytes_capacity(n, n, Lx, Ly, bytes);
+}
+
+int cg_avm_workspace_bytes_capacity(int32_t n, int32_t capacity, double Lx, double Ly, size_t* bytes) {
+  if (!bytes || n < 16 || capacity < n || capacity > (1 << 26)) return CG_EINVAL;
   cg_replica r{n, Lx, Ly, 3.8, 0.0};
   size_t spv = 0;
   int rc = cg_workspace_bytes(1, &r, &spv);
   if (rc) return rc;
-  *bytes = avm_layout(n, spv).total;
+  *bytes = avm_layout(capacity, spv).total;
   return CG_OK;
 }
 
@@ -285,21 +291,25 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
   for (double v : {par->A0, par->KA, par->KP, par->mu, par->Dr, par->dt, par->t1_threshold, par->t1_length,
                    par->t2_area, p0, v0})
     if (!std::isfinite(v)) return CG_EINVAL;
+  const int ncap = par->cell_capacity > 0 ? par->cell_capacity : n;
   size_t need = 0;
-  int rc = cg_avm_workspace_bytes(n, Lx, Ly, &need);
+  int rc = cg_avm_workspace_bytes_capacity(n, ncap, Lx, Ly, &need);
   if (rc) return rc;
   if (ws_bytes < need) return CG_EINVAL;
   cg_avm_ctx* c = new (std::nothrow) cg_avm_ctx();
   if (!c) return CG_EINVAL;
-  c->n = n;
-  c->V = 2 * n;
+  c->n = ncap;
+  c->V = 2 * ncap;
+  c->n_seed = n;
+  c->next_cell = n;
+  c->next_vertex = 2 * n;
   c->par = *par;
   c->ws = static_cast<char*>(d_ws);
   c->stream = static_cast<cudaStream_t>(stream);
   cg_replica r{n, Lx, Ly, p0, v0};
   size_t spv_bytes = 0;
   cg_workspace_bytes(1, &r, &spv_bytes);
-  c->off = avm_layout(n, spv_bytes);
+  c->off = avm_layout(ncap, spv_bytes);
   do {
     if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) { rc = CG_ECUDA; break; }
     int dev = 0;
@@ -328,6 +338,18 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
     Ctl h;
     std::memset(&h, 0, sizeof(h));
     if (cudaMemcpyAsync(c->ctl(), &h, sizeof(Ctl), cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = CG_ECUDA; break; }
+    // slots past the initial network: empty cells and free vertices
+    const size_t Vc = (size_t)c->V;
+    if (cudaMemsetAsync(c->at<int>(c->off.cc), 0, (size_t)ncap * sizeof(int), st) != cudaSuccess ||
+        cudaMemsetAsync(c->at<int>(c->off.cv), 0xff, (size_t)ncap * CG_RING * sizeof(int), st) != cudaSuccess ||
+        cudaMemsetAsync(c->at<int>(c->off.vc), 0xff, 3 * Vc * sizeof(int), st) != cudaSuccess ||
+        cudaMemsetAsync(c->at<int>(c->off.vn), 0xff, 3 * Vc * sizeof(int), st) != cudaSuccess ||
+        cudaMemsetAsync(c->at<double>(c->off.hx), 0, 2 * Vc * sizeof(double), st) != cudaSuccess ||
+        cudaMemsetAsync(c->at<double>(c->off.hy), 0, 2 * Vc * sizeof(double), st) != cudaSuccess ||
+        cudaMemsetAsync(c->at<double>(c->off.theta), 0, (size_t)ncap * sizeof(double), st) != cudaSuccess) {
+      rc = CG_ECUDA;
+      break;
+    }
     AvmBuildArgs b{};  // every field starts zero or null
     b.n = n;
     b.ctl = c->ctl();
@@ -353,11 +375,11 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
     if (rc) break;
     launch_check_finite(n, c->at<double>(c->off.theta), c->ctl(), st);
     launch_init_dir_tables(c->at<double2>(c->off.dir_tab), st);
-    launch_fill_d(n, p0, c->at<double>(c->off.p0), st);
-    launch_fill_d(n, c->par.A0, c->at<double>(c->off.a0), st);
+    launch_fill_d(ncap, p0, c->at<double>(c->off.p0), st);
+    launch_fill_d(ncap, c->par.A0, c->at<double>(c->off.a0), st);
     launch_avm_p0s(avm_args(c), st);
-    launch_fill_d(n, v0, c->at<double>(c->off.v0), st);
-    launch_fill_u64(n, ~0ull, c->at<unsigned long long>(c->off.lock), st);
+    launch_fill_d(ncap, v0, c->at<double>(c->off.v0), st);
+    launch_fill_u64(ncap, ~0ull, c->at<unsigned long long>(c->off.lock), st);
     if (cudaMemsetAsync(c->at<unsigned int>(c->off.done), 0, 2 * sizeof(unsigned int), st) != cudaSuccess) {
       rc = CG_ECUDA;
       break;
