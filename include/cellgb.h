@@ -390,6 +390,27 @@ int cg_avm_t1(cg_avm_ctx* ctx);
 /* Per-cell shape index and speed, N doubles (host or device).  Synchronizes. */
 int cg_avm_set_p0(cg_avm_ctx* ctx, const double* p0);
 int cg_avm_set_v0(cg_avm_ctx* ctx, const double* v0);
+/* Cell divisions (Sec. 2.A lists division among the features vertex models
+ * add; the paper's code has none), made one after the other: division k cuts
+ * cell cells[k] along the direction (dirs[2k], dirs[2k+1]) through the mean
+ * of its vertices.  With p the minimum-image offsets of its vertices from
+ * the first one, m their mean (sum in list order, then / count), q = p - m
+ * and s = u x q, an edge a -> a+1 is cut where s changes sign (s > 0 against
+ * s <= 0) at X = q_a + t (q_{a+1} - q_a), t = s_a / (s_a - s_{a+1}) clamped
+ * to [1/16, 15/16]; the cut with the smallest u.X > 0 gives new vertex A
+ * (edge a1), the one with the largest u.X < 0 new vertex B (edge a2); every
+ * product, sum and quotient is rounded on its own.  The cell keeps A,
+ * v_{a1+1} .. v_{a2}, B; the next free cell slot takes B, v_{a2+1} .. v_{a1},
+ * A and copies the cell's director, p0, v0 and A0; A and B take the next two
+ * free vertex slots; the cells across the cut edges gain them.  A division
+ * with a missing cut, or that would give a cell more than CG_MAX_RING
+ * vertices, is not made (made[k] = 0).  cells [count] int32 and dirs
+ * [2 count] doubles: host or device; made [count] (NULL to skip) and
+ * *n_made (host, may be NULL) receive the outcome.  CG_EINVAL when fewer
+ * than count cell slots (2 count vertex slots) are free, a cell index is
+ * out of range or a direction is not finite.  Synchronizes. */
+int cg_avm_divide(cg_avm_ctx* ctx, int32_t count, const int32_t* cells, const double* dirs, int32_t* made,
+                  int32_t* n_made);
 /* Per-cell preferred areas A0_c >= 0 (Eq. 1), N doubles (host or device);
  * a negative or non-finite entry returns CG_EINVAL.  Synchronizes. */
 int cg_avm_set_a0(cg_avm_ctx* ctx, const double* a0);

@@ -133,13 +133,14 @@ def lib():
         L.cg_avm_set_p0.argtypes = [vp, vp]
         L.cg_avm_set_v0.argtypes = [vp, vp]
         L.cg_avm_set_a0.argtypes = [vp, vp]
+        L.cg_avm_divide.argtypes = [vp, i32, vp, vp, vp, C.POINTER(i32)]
         L.cg_avm_get_counters.argtypes = [vp, C.POINTER(cg_counters)]
         L.cg_avm_destroy.argtypes = [vp]
         L.cg_avm_last_error.argtypes = [vp]
         L.cg_avm_last_error.restype = C.c_char_p
         for name in ("cg_avm_workspace_bytes", "cg_avm_workspace_bytes_capacity", "cg_avm_create", "cg_avm_step", "cg_avm_sync", "cg_avm_get_state",
                      "cg_avm_get_topology", "cg_avm_set_state", "cg_avm_get_geometry", "cg_avm_get_forces",
-                     "cg_avm_t1", "cg_avm_set_p0", "cg_avm_set_v0", "cg_avm_set_a0", "cg_avm_get_counters", "cg_avm_destroy",
+                     "cg_avm_t1", "cg_avm_set_p0", "cg_avm_set_v0", "cg_avm_set_a0", "cg_avm_divide", "cg_avm_get_counters", "cg_avm_destroy",
                      "cg_avm_profile_step"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -607,6 +608,12 @@ def cg_avm_set_a0(ctx, a0):
     _check_avm(lib().cg_avm_set_a0(ctx, _ptr(a0)), ctx)
 
 
+def cg_avm_divide(ctx, count, cells, dirs, made):
+    n_made = C.c_int32(0)
+    _check_avm(lib().cg_avm_divide(ctx, int(count), _ptr(cells), _ptr(dirs), _ptr(made), C.byref(n_made)), ctx)
+    return n_made.value
+
+
 def cg_avm_get_counters(ctx):
     c = cg_counters()
     _check_avm(lib().cg_avm_get_counters(ctx, C.byref(c)), ctx)
@@ -697,6 +704,18 @@ class AVM:
 
     def set_v0(self, v0):
         cg_avm_set_v0(self.ctx, self._as_input(v0))
+
+    def divide(self, cells, dirs):
+        """Divides cells[k] along dirs[k] = (ux, uy), in order; returns the
+        int32 array made[k] (1 when division k was made).  The new cells take
+        the next free slots (see `capacity`)."""
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1)
+        if dirs.size != 2 * cells.size:
+            raise ValueError("one direction (ux, uy) per cell")
+        made = np.zeros(cells.size, np.int32)
+        cg_avm_divide(self.ctx, cells.size, cells, dirs, made)
+        return made
 
     def set_a0(self, a0):
         """Per-cell preferred areas (a cell given a small A0 shrinks and,

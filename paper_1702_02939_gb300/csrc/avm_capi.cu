@@ -29,6 +29,7 @@ struct AvmOff {
   size_t hx, hy, hf, vc, vn, cc, cv, theta, p0, v0, a0, P0, A, P, ka, kp, energy, act, Fx, Fy, lock, cand_e, cand,
       done;
   size_t owned, base_local, base_partial, xs, ys, cnt, nbr, scalar, ctl, dir_tab;
+  size_t div_cells, div_dirs, div_made, div_next;  // staging of cg_avm_divide
   size_t total;
 };
 
@@ -73,6 +74,10 @@ AvmOff avm_layout(int64_t n, size_t spv_bytes) {
   o.scalar = L.take(4 * d);
   o.ctl = L.take(sizeof(Ctl));
   o.dir_tab = L.take(kDirTabEntries * sizeof(double2));
+  o.div_cells = L.take(n * i4);
+  o.div_dirs = L.take(2 * n * d);
+  o.div_made = L.take(n * i4);
+  o.div_next = L.take(2 * i4);
   o.total = L.total;
   return o;
 }
@@ -532,6 +537,41 @@ int cg_avm_set_p0(cg_avm_ctx* c, const double* p0) {
   launch_avm_p0s(avm_args(c), c->stream);
   return avm_status(c);
 }
+int cg_avm_divide(cg_avm_ctx* c, int32_t count, const int32_t* cells, const double* dirs, int32_t* made,
+                  int32_t* n_made) {
+  if (!c || count < 0) return CG_EINVAL;
+  if (count == 0) {
+    if (n_made) *n_made = 0;
+    return CG_OK;
+  }
+  if (!cells || !dirs) return CG_EINVAL;
+  if (c->next_cell + count > c->n || c->next_vertex + 2 * count > c->V)
+    return afail(c, CG_EINVAL, "not enough free cell slots for the divisions");
+  int rc = avm_status(c);
+  if (rc) return rc;
+  int* dc = c->at<int>(c->off.div_cells);
+  double* dd = c->at<double>(c->off.div_dirs);
+  int* dm = c->at<int>(c->off.div_made);
+  int* dn = c->at<int>(c->off.div_next);
+  const int next[2] = {c->next_cell, c->next_vertex};
+  if ((rc = copy_in(c, dc, cells, (size_t)count * sizeof(int)))) return rc;
+  if ((rc = copy_in(c, dd, dirs, 2 * (size_t)count * sizeof(double)))) return rc;
+  AV_CUDA(c, cudaMemcpyAsync(dn, next, sizeof(next), cudaMemcpyHostToDevice, c->stream));
+  launch_check_finite(2 * count, dd, c->ctl(), c->stream);
+  launch_avm_divide(avm_args(c), count, dc, dd, dn, dm, c->stream);
+  AV_CUDA(c, cudaGetLastError());
+  int after[2];
+  AV_CUDA(c, cudaMemcpyAsync(after, dn, sizeof(after), cudaMemcpyDeviceToHost, c->stream));
+  if (made && (rc = copy_out(c, made, dm, (size_t)count * sizeof(int)))) return rc;
+  AV_CUDA(c, cudaStreamSynchronize(c->stream));
+  rc = avm_status(c);
+  if (rc) return rc;
+  if (n_made) *n_made = after[0] - c->next_cell;
+  c->next_cell = after[0];
+  c->next_vertex = after[1];
+  return CG_OK;
+}
+
 int cg_avm_set_a0(cg_avm_ctx* c, const double* a0) {
   if (!c || !a0) return CG_EINVAL;
   int rc = copy_in(c, c->at<double>(c->off.a0), a0, c->n * sizeof(double));

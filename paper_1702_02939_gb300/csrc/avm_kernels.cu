@@ -791,6 +791,146 @@ __global__ void k_avm_validate(AvmArgs g) {
   if (bad) raise_status(g.ctl, kEINVAL);
 }
 
+// Division of cell c along (ux, uy) into c and newc with new vertices va (A)
+// and vb (B), the per-cell values copied to newc.  With p the minimum-image
+// offsets of the vertices from the first one, m their mean (sum in list
+// order, then / count), q = p - m and s = u x q, an edge is cut where s
+// changes sign (s > 0 against s <= 0) at X = q_a + t (q_b - q_a),
+// t = s_a / (s_a - s_b) clamped to [1/16, 15/16]; the cut with the smallest
+// u.X > 0 gives A, the one with the largest u.X < 0 gives B.  Every product,
+// sum and quotient is rounded on its own, so the host reference decides the
+// same.  c keeps A, v_{a1+1} .. v_{a2}, B; newc gets B, v_{a2+1} .. v_{a1}, A.
+// Returns 0 made, 1 refused (a missing cut, a daughter or a neighbour over 16
+// vertices), -1 for an inconsistent network.
+__device__ int divide_cell(const AvmArgs& g, int c, double ux, double uy, int newc, int va, int vb) {
+  const size_t V = (size_t)g.V;
+  double* hx = g.hx + g.ctl->cur * V;
+  double* hy = g.hy + g.ctl->cur * V;
+  const int m = g.cc[c];
+  if (m < 3 || m > CG_RING) return 1;
+  int v[CG_RING];
+  double px[CG_RING], py[CG_RING], sd[CG_RING];
+  for (int a = 0; a < m; ++a) v[a] = g.cv[(size_t)c * CG_RING + a];
+  for (int a = 0; a < m; ++a) {
+    px[a] = mimg_a(hx[v[a]] - hx[v[0]], g.ax);
+    py[a] = mimg_a(hy[v[a]] - hy[v[0]], g.ay);
+  }
+  double sx = 0.0, sy = 0.0;
+  for (int a = 1; a < m; ++a) {
+    sx = __dadd_rn(sx, px[a]);
+    sy = __dadd_rn(sy, py[a]);
+  }
+  const double mx = __ddiv_rn(sx, (double)m), my = __ddiv_rn(sy, (double)m);
+  for (int a = 0; a < m; ++a) {
+    px[a] = __dsub_rn(px[a], mx);  // q
+    py[a] = __dsub_rn(py[a], my);
+    sd[a] = __dsub_rn(__dmul_rn(ux, py[a]), __dmul_rn(uy, px[a]));
+  }
+  int a1 = -1, a2 = -1;
+  double l1 = 0.0, l2 = 0.0, X1x = 0.0, X1y = 0.0, X2x = 0.0, X2y = 0.0;
+  for (int a = 0; a < m; ++a) {
+    const int b = (a + 1 == m) ? 0 : a + 1;
+    if ((sd[a] > 0.0) == (sd[b] > 0.0)) continue;
+    double t = __ddiv_rn(sd[a], __dsub_rn(sd[a], sd[b]));
+    if (t < 0.0625) t = 0.0625;
+    if (t > 0.9375) t = 0.9375;
+    const double Xx = __dadd_rn(px[a], __dmul_rn(t, __dsub_rn(px[b], px[a])));
+    const double Xy = __dadd_rn(py[a], __dmul_rn(t, __dsub_rn(py[b], py[a])));
+    const double lam = __dadd_rn(__dmul_rn(ux, Xx), __dmul_rn(uy, Xy));
+    if (lam > 0.0 && (a1 < 0 || lam < l1)) { a1 = a; l1 = lam; X1x = Xx; X1y = Xy; }
+    if (lam < 0.0 && (a2 < 0 || lam > l2)) { a2 = a; l2 = lam; X2x = Xx; X2y = Xy; }
+  }
+  if (a1 < 0 || a2 < 0) return 1;
+  const int n1 = (a2 - a1 + m) % m + 2, n2 = (a1 - a2 + m) % m + 2;
+  if (n1 > CG_RING || n2 > CG_RING) return 1;
+  const int p1 = v[a1], p1n = v[(a1 + 1) % m], p2 = v[a2], p2n = v[(a2 + 1) % m];
+  int x1 = -1, x2 = -1;
+  for (int s = 0; s < 3; ++s) {
+    const int y1 = g.vc[3 * p1 + s], y2 = g.vc[3 * p2 + s];
+    if (y1 != c && (y1 == g.vc[3 * p1n] || y1 == g.vc[3 * p1n + 1] || y1 == g.vc[3 * p1n + 2])) x1 = y1;
+    if (y2 != c && (y2 == g.vc[3 * p2n] || y2 == g.vc[3 * p2n + 1] || y2 == g.vc[3 * p2n + 2])) x2 = y2;
+  }
+  if (x1 < 0 || x2 < 0) return -1;
+  if (g.cc[x1] + (x1 == x2 ? 2 : 1) > CG_RING) return 1;
+  if (x1 != x2 && g.cc[x2] + 1 > CG_RING) return 1;
+  const double ax = __dadd_rn(mx, X1x), ay = __dadd_rn(my, X1y);
+  const double bx = __dadd_rn(mx, X2x), by = __dadd_rn(my, X2y);
+  const double x0 = hx[v[0]], y0 = hy[v[0]];
+  const int s1 = slot3(g.vn, p1, p1n), s1n = slot3(g.vn, p1n, p1);
+  const int s2 = slot3(g.vn, p2, p2n), s2n = slot3(g.vn, p2n, p2);
+  if (s1 < 0 || s1n < 0 || s2 < 0 || s2n < 0) return -1;
+  g.vn[3 * p1 + s1] = va;
+  g.vn[3 * p1n + s1n] = va;
+  g.vn[3 * p2 + s2] = vb;
+  g.vn[3 * p2n + s2n] = vb;
+  int d1[CG_RING], d2[CG_RING], k1 = 0, k2 = 0;
+  d1[k1++] = va;
+  for (int a = (a1 + 1) % m;; a = (a + 1) % m) {
+    d1[k1++] = v[a];
+    if (a == a2) break;
+  }
+  d1[k1++] = vb;
+  d2[k2++] = vb;
+  for (int a = (a2 + 1) % m;; a = (a + 1) % m) {
+    d2[k2++] = v[a];
+    const int s = slot3(g.vc, v[a], c);
+    if (s < 0) return -1;
+    g.vc[3 * v[a] + s] = newc;
+    if (a == a1) break;
+  }
+  d2[k2++] = va;
+  for (int a = 0; a < CG_RING; ++a) {
+    g.cv[(size_t)c * CG_RING + a] = a < k1 ? d1[a] : -1;
+    g.cv[(size_t)newc * CG_RING + a] = a < k2 ? d2[a] : -1;
+  }
+  g.cc[c] = k1;
+  g.cc[newc] = k2;
+  insert_in_cell(g.cc, g.cv, x1, p1n, va);
+  insert_in_cell(g.cc, g.cv, x2, p2n, vb);
+  g.vc[3 * va] = x1; g.vc[3 * va + 1] = c; g.vc[3 * va + 2] = newc;
+  g.vn[3 * va] = p1n; g.vn[3 * va + 1] = vb; g.vn[3 * va + 2] = p1;
+  g.vc[3 * vb] = x2; g.vc[3 * vb + 1] = newc; g.vc[3 * vb + 2] = c;
+  g.vn[3 * vb] = p2n; g.vn[3 * vb + 1] = va; g.vn[3 * vb + 2] = p2;
+  const double hax = wrap_a(__dadd_rn(x0, ax), g.ax), hay = wrap_a(__dadd_rn(y0, ay), g.ay);
+  const double hbx = wrap_a(__dadd_rn(x0, bx), g.ax), hby = wrap_a(__dadd_rn(y0, by), g.ay);
+  hx[va] = hax; hy[va] = hay;
+  hx[vb] = hbx; hy[vb] = hby;
+  g.hf[va] = make_float2((float)hax, (float)hay);
+  g.hf[vb] = make_float2((float)hbx, (float)hby);
+  g.theta[newc] = g.theta[c];
+  g.p0[newc] = g.p0[c];
+  g.v0[newc] = g.v0[c];
+  g.a0[newc] = g.a0[c];
+  g.P0[newc] = g.P0[c];
+  return 0;
+}
+
+// The divisions of a call, one after the other (one thread: each sees the
+// network the previous ones left).  next[0], next[1]: first free cell and
+// vertex slots, advanced by each division made; made[k] = 1 when division k
+// was made.
+__global__ void k_avm_divide(AvmArgs g, int count, const int* cells, const double* dirs, int* next, int* made) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int k = 0; k < count; ++k) {
+    made[k] = 0;
+    const int c = cells[k];
+    if ((unsigned)c >= (unsigned)g.n || next[0] >= g.n || next[1] + 2 > g.V) {
+      raise_status(g.ctl, kEINVAL);
+      return;
+    }
+    const int r = divide_cell(g, c, dirs[2 * k], dirs[2 * k + 1], next[0], next[1], next[1] + 1);
+    if (r < 0) {
+      raise_status(g.ctl, kETOPO);
+      return;
+    }
+    if (r == 0) {
+      made[k] = 1;
+      next[0] += 1;
+      next[1] += 2;
+    }
+  }
+}
+
 // Preferred perimeters P0_c = p0_c sqrt(A0_c); A0_c must be finite and >= 0.
 __global__ void k_avm_p0s(AvmArgs g) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -840,6 +980,10 @@ void launch_avm_forces(const AvmArgs& a, cudaStream_t st) {
   f.move = 0;
   k_avm_cells<<<cell_blocks_of(a.n), kAvmCellThreads, 0, st>>>(f);
   k_avm_force_move<<<vertex_blocks_of(a.V), kAvmVertexThreads, 0, st>>>(f);
+}
+void launch_avm_divide(const AvmArgs& a, int count, const int* cells, const double* dirs, int* next, int* made,
+                       cudaStream_t st) {
+  if (count > 0) k_avm_divide<<<1, 32, 0, st>>>(a, count, cells, dirs, next, made);
 }
 void launch_avm_p0s(const AvmArgs& a, cudaStream_t st) {
   k_avm_p0s<<<blocks_of(a.n), kAvmThreads, 0, st>>>(a);

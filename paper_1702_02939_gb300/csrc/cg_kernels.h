@@ -250,8 +250,8 @@ struct AvmArgs {
   double *hx, *hy;         // [2][V]
   int *vc, *vn, *cc, *cv;
   double* theta;
-  const double *p0, *v0;
-  const double* a0;        // [n] preferred areas A0_c
+  double *p0, *v0;         // [n] (written only by divisions)
+  double* a0;              // [n] preferred areas A0_c
   double* P0;              // [n] preferred perimeters p0_c sqrt(A0_c)
   double KA, KP, mu, dt, noise_amp;
   unsigned long long seed;
@@ -280,6 +280,10 @@ void launch_avm_forces(const AvmArgs& a, cudaStream_t st);
 void launch_avm_validate(const AvmArgs& a, cudaStream_t st);
 // P0[c] = p0[c] sqrt(a0[c]) after p0 or A0 change
 void launch_avm_p0s(const AvmArgs& a, cudaStream_t st);
+// count divisions (cells[k], direction dirs[2k], dirs[2k+1]) in order, one
+// thread; next = {first free cell slot, first free vertex slot}, advanced
+void launch_avm_divide(const AvmArgs& a, int count, const int* cells, const double* dirs, int* next, int* made,
+                       cudaStream_t st);
 void launch_avm_shadow(const AvmArgs& a, cudaStream_t st);
 void launch_fill_d(int n, double v, double* out, cudaStream_t st);
 void launch_fill_u64(int n, unsigned long long v, unsigned long long* out, cudaStream_t st);

@@ -425,3 +425,71 @@ def test_full_size_with_cell_death():
     assert len(removed) > n // 200 and removed <= set(dying.tolist())
     assert sim.counters()["t2_total"] == len(removed)
     sim.close()
+
+
+def test_divisions_match_oracle():
+    """Divisions along given directions give the oracle's network (topology
+    exact, new vertex positions within 1e-12 L), and the grown network then
+    steps like the oracle's (T1 and T2 passes, new cells' directors)."""
+    n, cap, p0, v0, thr = 100, 150, 3.8, 0.05, 0.04
+    sim, xs, ys, th, Lx, Ly = make(n, 31, p0=p0, v0=v0, t1_threshold=thr, t2_area=0.01, seed=6, capacity=cap)
+    assert sim.n == cap and sim.V == 2 * cap
+    net = oracle.avm_build(xs, ys, Lx, Ly).with_capacity(cap)
+    theta = np.concatenate([th, np.zeros(cap - n)])
+    pa, va, aa = np.full(cap, p0), np.full(cap, v0), np.ones(cap)
+    g, gth = gpu_net(sim, Lx, Ly)
+    assert_same_network(g, net)
+    rng = np.random.default_rng(3)
+    cells = rng.choice(n, 30, replace=False)
+    ang = rng.uniform(0.0, np.pi, 30)
+    dirs = np.stack([np.cos(ang), np.sin(ang)], 1)
+    made = sim.divide(cells, dirs)
+    o, theta, pa, va, aa, nc, nv, omade = oracle.avm_divide(net, cells, dirs, n, 2 * n, theta, pa, va, aa)
+    np.testing.assert_array_equal(made, omade)
+    g, gth = gpu_net(sim, Lx, Ly)
+    assert_same_network(g, o)
+    np.testing.assert_array_equal(gth, theta)
+    # a few of the new cells die
+    aa[n:n + 3] = 0.0
+    sim.set_a0(aa)
+    for k in range(120):
+        sim.step(1)
+        g, gth = gpu_net(sim, Lx, Ly)
+        o, theta, _, _ = oracle.avm_step(o, theta, pa, va, seed=6, step=k, A0=aa, thr=thr, t2_area=0.01, counts=True)
+        assert_same_network(g, o)
+        np.testing.assert_allclose(gth, theta, rtol=0, atol=1e-13)
+        load(sim, o, theta)
+    check_network_valid(sim, Lx, Ly, p0)
+    assert int((g.cc == 0).sum()) >= 1
+    sim.close()
+
+
+def test_division_slots_are_checked():
+    n = 64
+    sim, *_ = make(n, 32, capacity=n + 1)
+    with pytest.raises(cg.CellgbError) as e:
+        sim.divide([3, 4], [[1.0, 0.0], [0.0, 1.0]])
+    assert e.value.code == -1
+    assert sim.divide([3], [[1.0, 0.0]])[0] == 1
+    with pytest.raises(cg.CellgbError):
+        sim.divide([5], [[0.0, 1.0]])
+    sim.close()
+
+
+def test_full_size_growth():
+    """N = 65536 seeds with room for 4096 more cells: 4000 divisions, then 200
+    graph steps with T1 and T2 passes keep a valid tiling, one cell per
+    division made and none but those the T2s removed."""
+    n, cap = 65536, 65536 + 4096
+    sim, xs, ys, th, Lx, Ly = make(n, 1, p0=3.8, v0=0.1, t1_threshold=0.04, t2_area=0.01, seed=1, capacity=cap)
+    rng = np.random.default_rng(9)
+    cells = rng.choice(n, 4000, replace=False)
+    ang = rng.uniform(0.0, np.pi, 4000)
+    made = sim.divide(cells, np.stack([np.cos(ang), np.sin(ang)], 1))
+    assert made.sum() >= 3990
+    sim.step(200)
+    sim.sync()
+    g = check_network_valid(sim, Lx, Ly, 3.8)
+    # a daughter that is a small triangle may be removed by a T2 meanwhile
+    assert int((g.cc > 0).sum()) == n + int(made.sum()) - sim.counters()["t2_total"]
+    sim.close()
