@@ -464,9 +464,11 @@ def avm_death_throughput(args, device):
         return None
     n, thr, p0, v0 = 65536, 0.04, 3.8, 0.1
     x, y, th, L = workloads.spv_uniform(n, 21)
-    sim = cg.AVM(n, L, L, x, y, th, p0=p0, v0=v0, dt=DT, t1_threshold=thr, t2_area=0.01, seed=21, device=device)
+    cap = n + n // 50
+    sim = cg.AVM(n, L, L, x, y, th, p0=p0, v0=v0, dt=DT, t1_threshold=thr, t2_area=0.01, seed=21, capacity=cap,
+                 device=device)
     sim.step(args.avm_warmup)
-    a0 = np.ones(n)
+    a0 = np.ones(cap)
     a0[np.random.default_rng(5).choice(n, n // 100, replace=False)] = 0.0
     sim.set_a0(a0)
     sim.sync()
@@ -485,12 +487,37 @@ def avm_death_throughput(args, device):
     sim.sync()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     c1 = sim.counters()
-    removed = int((sim.topology()[2] == 0).sum())
+    removed = int((sim.topology()[2][:n] == 0).sum())
+    # divisions: 1% of the cells along random directions in one call (host
+    # arrays in, outcome back; the call synchronizes), then the grown tissue steps
+    rng = np.random.default_rng(6)
+    alive = np.nonzero(sim.topology()[2].cpu().numpy() > 0)[0]
+    cells = rng.choice(alive, n // 100, replace=False)
+    ang = rng.uniform(0.0, np.pi, cells.size)
+    dirs = np.stack([np.cos(ang), np.sin(ang)], 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    made = sim.divide(cells, dirs)
+    div_s = time.perf_counter() - t0
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        flush.zero_()
+        ev2[k][0].record(stream)
+        sim.step(1)
+        ev2[k][1].record(stream)
+    torch.cuda.synchronize()
+    sim.sync()
+    ms2 = sum(a.elapsed_time(b) for a, b in ev2)
+    alive_after = int((sim.topology()[2] > 0).sum())
     sim.close()
     return {"workload": "avm_N65536_L256_p0_3.8_v0_0.1_thr0.04_t2area0.01_dying1pct_fp64", "unit": "vertex-steps/s",
             "vertex_steps_per_s": 2 * n * K / (ms * 1e-3), "ms_per_step": ms / K, "steps": K,
             "t2_per_step": (c1["t2_total"] - c0["t2_total"]) / K, "t1_per_step": (c1["t1_total"] - c0["t1_total"]) / K,
-            "cells_removed": removed, "dying": n // 100}
+            "cells_removed": removed, "dying": n // 100,
+            "divisions": {"requested": int(cells.size), "made": int(made.sum()), "call_ms": 1e3 * div_s,
+                          "divisions_per_s": int(made.sum()) / div_s,
+                          "ms_per_step_after": ms2 / K, "cells_alive_after": alive_after,
+                          "cell_slots": cap}}
 
 
 def sweep(args):
