@@ -377,6 +377,7 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
         }
         if (!p.err) {
           int slot = nbuf + incl - count;
+          bool same = false;  // another cell on exactly this grid point
           for (int t = 0; t < count; ++t) {
             const int j = g.ids[start + t];
             if (j == i) {
@@ -386,6 +387,7 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
               s_Y[wib][slot] = 0;
             } else {
               const long long dX = min_image_i(X[j] - Xi, R.LX), dY = min_image_i(Y[j] - Yi, R.LY);
+              same |= (dX == 0 && dY == 0);
               const float dx = i2f_scaled(dX, sc), dy = i2f_scaled(dY, sc);
               s_d2[wib][slot] = dx * dx + dy * dy;
               s_id[wib][slot] = j;
@@ -395,6 +397,7 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
             ++slot;
           }
           nbuf += tot;
+          if (__any_sync(0xffffffffu, same)) p.err = kEDEGEN;  // no bisector between them
         }
         __syncwarp();
       }

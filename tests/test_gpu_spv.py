@@ -615,3 +615,55 @@ def test_run_io_refuses_a_non_finite_v0():
         sim.run_io(2, v0=bad)
     assert e.value.code == -1  # CG_EINVAL
     sim.close()
+
+
+def test_coincident_cells_are_refused():
+    """Two cells at exactly the same position have no Voronoi polygon between
+    them: the triangulation refuses the state with CG_EDEGENERATE."""
+    n = 400
+    x, y, th, L = workloads.spv_uniform(n, 61)
+    Lx, Ly, q = oracle.box(L)
+    xs, ys = oracle.snap_positions(x, y, Lx, Ly)
+    xs, ys = xs.copy(), ys.copy()
+    xs[7], ys[7] = xs[123], ys[123]
+    with pytest.raises(cg.CellgbError) as e:
+        cg.SPV([dict(n=n, Lx=L, Ly=L, p0=3.8, v0=0.05)], xs, ys, th)
+    assert e.value.code == -8
+
+
+def test_million_cells_sampled_against_local_triangulations():
+    """N = 1048576 (the largest size of the timing sweep), 20 fluid steps:
+    ring symmetry and 6N ring entries over all cells, areas tiling the box,
+    and the rings of the cells inside three windows equal to the exact
+    Delaunay triangulation of the window's points computed by the oracle."""
+    n = 1 << 20
+    sim, xs, ys, th, Lx, Ly = make(n, 71, p0=3.85, v0=0.1, seed=5, dt=0.01)
+    sim.step(20)
+    cnt, nbr = (t.cpu().numpy() for t in sim.neighbors())
+    assert int(cnt.sum()) == 6 * n
+    rows = np.repeat(np.arange(n, dtype=np.int64), cnt)
+    cols = nbr[nbr >= 0].astype(np.int64)
+    # j in ring(i) <=> i in ring(j): the directed edges equal their reverses
+    np.testing.assert_array_equal(np.sort(rows * n + cols), np.sort(cols * n + rows))
+    A, P = (t.cpu().numpy() for t in sim.geometry())
+    assert abs(A.sum() - Lx * Ly) <= 1e-9 * Lx * Ly
+    gx, gy, _ = (t.cpu().numpy() for t in sim.state())
+    q = oracle.grid_exponent(Lx, Ly)
+    X = np.rint(np.ldexp(gx, q)).astype(np.int64)
+    Y = np.rint(np.ldexp(gy, q)).astype(np.int64)
+    rng = np.random.default_rng(8)
+    for _ in range(3):
+        cx, cy = rng.uniform(0.25 * Lx, 0.75 * Lx), rng.uniform(0.25 * Ly, 0.75 * Ly)
+        hw, margin = 20.0, 8.0
+        inside = np.nonzero((np.abs(gx - cx) < hw + margin) & (np.abs(gy - cy) < hw + margin))[0]
+        core = set(np.nonzero((np.abs(gx - cx) < hw) & (np.abs(gy - cy) < hw))[0].tolist())
+        wcnt, wnbr = oracle.delaunay_plain(X[inside], Y[inside])
+        checked = 0
+        for k, i in enumerate(inside):
+            if int(i) not in core:
+                continue
+            ring = {int(inside[j]) for j in wnbr[k, :wcnt[k]]}
+            assert ring == set(nbr[i, :cnt[i]].tolist()), i
+            checked += 1
+        assert checked > 1000
+    sim.close()
