@@ -829,10 +829,12 @@ int cg_run_io(cg_ctx* c, int64_t nsteps, const double* v0, int64_t v0_stride, do
       CG_CUDA(c, cudaMemcpyAsync(in, v0 + k * v0_stride, N * sizeof(double), cudaMemcpyDefault, c->h2d));
       CG_CUDA(c, cudaEventRecord(c->in_ready[b], c->h2d));
       CG_CUDA(c, cudaStreamWaitEvent(st, c->in_ready[b], 0));
-      launch_scatter_d(n, tag, in, c->at<double>(c->off.v0), st);
+      // this step's v0 into storage order and the pending move redone with it
+      // (as cg_set_v0), in one kernel
+      ForceArgs f = force_args(c, 2);
+      f.v0_user = in;
+      run_force(c, f, st);
       CG_CUDA(c, cudaEventRecord(c->in_free[b], st));
-      launch_check_finite(n, c->at<double>(c->off.v0), c->ctl(), st);
-      run_force(c, force_args(c, 2), st);  // the pending move with this step's v0 (as cg_set_v0)
     }
     if (c->par.sort_every > 0 && c->host_step > 0 && c->host_step % c->par.sort_every == 0) {
       launch_sort(sort_args(c), st);

@@ -49,7 +49,10 @@ struct ForceArgs {
   double *x, *y;       // [2][n]
   long long *X, *Y;    // [2][n]
   double* theta;
-  const double* v0;
+  double* v0;
+  // integrate 2 only: new speeds in user order (or nullptr), stored into v0
+  // (through tag) before the move, a non-finite one raising CG_EINVAL
+  const double* v0_user;
   double mu, dt, noise_amp;
   unsigned long long seed;
   const double2* nrm;  // (cos, sin) of each cell's director, from k_dir

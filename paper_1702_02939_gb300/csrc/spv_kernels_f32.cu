@@ -222,7 +222,14 @@ __global__ void __launch_bounds__(kForceThreads) k_force_f32(ForceArgs g) {
   const Rep R = g.reps[g.rep[i]];
   const double xi = g.x[(size_t)cur * N + i], yi = g.y[(size_t)cur * N + i];
   const double2 nd = g.nrm[i];  // (cos theta, sin theta), from k_dir_f32
-  const double v0 = g.v0[i];
+  double v0;
+  if (g.v0_user) {  // integrate 2 with new speeds: take them over first
+    v0 = g.v0_user[g.tag[i]];
+    if (!isfinite(v0)) raise_status(g.ctl, kEINVAL);
+    g.v0[i] = v0;
+  } else {
+    v0 = g.v0[i];
+  }
   const double vx = g.mu * (double)fx + v0 * nd.x, vy = g.mu * (double)fy + v0 * nd.y;
   const double xn = xi + g.dt * vx, yn = yi + g.dt * vy;
   long long Xn, Yn;
