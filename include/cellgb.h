@@ -291,7 +291,9 @@ int cg_triangulate_noalloc(int32_t n, double Lx, double Ly, const double* d_x, c
  * theta_c += sqrt(2 D_r dt) xi (Philox4x32-10, counter (c, step)), then T1
  * passes (Fig. 1) until no edge is shorter than the threshold.
  *
- * Layout (all int32 / double, vertex v, cell c):
+ * Layout (all int32 / double, vertex v, cell c; N = the cell slots, i.e.
+ * cell_capacity when one is given, V = 2N vertex slots; slots past the
+ * network, and those T2s free, hold empty cells and free vertices):
  *   hx, hy [V]        vertex positions in [0, L)
  *   vc [3V], vn [3V]  cells and neighbours of v, counter-clockwise: the edge
  *                     v - vn[3v+k] separates cells vc[3v+k] and vc[3v+k+1]
@@ -385,7 +387,8 @@ int cg_avm_get_geometry(cg_avm_ctx* ctx, double* A, double* P);
 /* Vertex forces [V] and, if energy != NULL, the total energy of Eq. 1.
  * Synchronizes. */
 int cg_avm_get_forces(cg_avm_ctx* ctx, double* Fx, double* Fy, double* energy);
-/* T1 passes on the current state, without a move.  Synchronizes. */
+/* Transition passes (T1, and T2 when t2_area > 0) on the current state,
+ * without a move.  Synchronizes. */
 int cg_avm_t1(cg_avm_ctx* ctx);
 /* Per-cell shape index and speed, N doubles (host or device).  Synchronizes. */
 int cg_avm_set_p0(cg_avm_ctx* ctx, const double* p0);
