@@ -9,7 +9,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcellgb.so")
 SOURCES = ["capi.cu", "spv_kernels.cu", "spv_kernels_f32.cu", "topo_kernels.cu", "sort_kernels.cu",
            "adjoint_kernels.cu", "noalloc.cu", "avm_kernels.cu", "avm_capi.cu"]
-HEADERS = ["cg_device.cuh", "cg_kernels.h", "cg_graph.h"]
+HEADERS = ["cg_device.cuh", "cg_kernels.h", "cg_graph.h", "dir_math.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
