@@ -250,40 +250,46 @@ __device__ __forceinline__ void clip(Poly& p, long long jX, long long jY, int ji
   p.R2 = warp_max(lane < m2 ? p.r2 : 0.0f);
 }
 
-// Sort the warp's candidate buffer by squared distance (bitonic, 64 entries)
-// and clip with every candidate that can still reach the polygon.
-__device__ void process_candidates(Poly& p, int nbuf, int* s_id, long long* s_X, long long* s_Y, float* s_d2,
-                                   float* s_key, int* s_val, const int* tag, int ikey, float sc, double inv_scale,
+// Sort the warp's candidate buffer by squared distance and clip with every
+// candidate that can still reach the polygon.  The 64 keys live in registers,
+// two per lane (entries lane and lane + 32), and are sorted by a bitonic
+// network of register shuffles; the clips then take the entries in order.
+__device__ void process_candidates(Poly& p, int nbuf, const int* s_id, const long long* s_X, const long long* s_Y,
+                                   const float* s_d2, const int* tag, int ikey, float sc, double inv_scale,
                                    int lane) {
+  static_assert(kCand == 64, "two keys per lane");
   if (nbuf == 0) return;
-  for (int q = lane; q < kCand; q += 32) {
-    s_key[q] = (q < nbuf) ? s_d2[q] : kPadKey;
-    s_val[q] = q;
-  }
-  __syncwarp();
-  for (int k = 2; k <= kCand; k <<= 1) {
-    for (int jj = k >> 1; jj > 0; jj >>= 1) {
-      for (int q = lane; q < kCand; q += 32) {
-        const int partner = q ^ jj;
-        if (partner > q) {
-          const bool up = (q & k) == 0;
-          const float a = s_key[q], b = s_key[partner];
-          if ((a > b) == up) {
-            s_key[q] = b; s_key[partner] = a;
-            const int t = s_val[q]; s_val[q] = s_val[partner]; s_val[partner] = t;
-          }
+  float k0 = (lane < nbuf) ? s_d2[lane] : kPadKey, k1 = (lane + 32 < nbuf) ? s_d2[lane + 32] : kPadKey;
+  int v0 = lane, v1 = lane + 32;
+#pragma unroll
+  for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j == 32) {  // entries lane and lane + 32, ascending (k = 64)
+        if (k0 > k1) {
+          const float tk = k0; k0 = k1; k1 = tk;
+          const int tv = v0; v0 = v1; v1 = tv;
         }
+      } else {
+        const bool lower = (lane & j) == 0;
+        // entry q = lane (+ 32): ascending block when (q & k) == 0
+        const bool up0 = (lane & k) == 0, up1 = ((lane + 32) & k) == 0;
+        const float p0 = __shfl_xor_sync(0xffffffffu, k0, j), p1 = __shfl_xor_sync(0xffffffffu, k1, j);
+        const int w0 = __shfl_xor_sync(0xffffffffu, v0, j), w1 = __shfl_xor_sync(0xffffffffu, v1, j);
+        // the lower entry of a pair keeps the minimum in an ascending block
+        if (lower == up0 ? p0 < k0 : p0 > k0) { k0 = p0; v0 = w0; }
+        if (lower == up1 ? p1 < k1 : p1 > k1) { k1 = p1; v1 = w1; }
       }
-      __syncwarp();
     }
   }
   for (int c = 0; c < nbuf; ++c) {
-    const float d2 = s_key[c];
+    const int src = c & 31;
+    const float d2 = __shfl_sync(0xffffffffu, c < 32 ? k0 : k1, src);
+    const int e = __shfl_sync(0xffffffffu, c < 32 ? v0 : v1, src);
     if (d2 >= kSelfKey) break;  // the cell itself and padding sort last
     // a cell can cut the polygon only if it is nearer than twice its circumradius
     // (d2 carries a relative error below 1e-6; the margin is 1e-3)
     if (d2 > 4.0f * p.R2 * (1.0f + 1e-3f)) break;
-    const int e = s_val[c];
     const int jid = s_id[e];
     clip(p, s_X[e], s_Y[e], jid, tag[jid], ikey, sc, inv_scale, lane);
     if (p.err) break;
@@ -295,8 +301,6 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
   __shared__ int s_id[kRepairWarps][kCand];
   __shared__ long long s_X[kRepairWarps][kCand], s_Y[kRepairWarps][kCand];
   __shared__ float s_d2[kRepairWarps][kCand];
-  __shared__ float s_key[kRepairWarps][kCand];
-  __shared__ int s_val[kRepairWarps][kCand];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gw = blockIdx.x * kRepairWarps + wib, nw = gridDim.x * kRepairWarps;
   // stop the round loop unless this round's check asks for another
@@ -347,14 +351,20 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
     const int kmax = min((R.nbx - 1) / 2, (R.nby - 1) / 2);
     int nbuf = 0;
     bool done = false;
+    // rings 0..2 (25 bins) are gathered in one pass, one bin per lane, unless
+    // they hold more candidates than the buffer; then ring by ring
+    bool batch = kmax >= 2;
     for (int k = 0; k <= kmax && !done && !p.err; ++k) {
-      const int nring = (k == 0) ? 1 : 8 * k;
+      const bool first = batch && k == 0;
+      const int nring = first ? 25 : ((k == 0) ? 1 : 8 * k);
+      bool retry = false;
       for (int base = 0; base < nring && !p.err; base += 32) {
         const int idx = base + lane;
         int start = 0, count = 0;
         if (idx < nring) {
           int dx, dy;
-          ring_bin(k, idx, dx, dy);
+          if (first) ring_bin(idx == 0 ? 0 : (idx <= 8 ? 1 : 2), idx == 0 ? 0 : (idx <= 8 ? idx - 1 : idx - 9), dx, dy);
+          else ring_bin(k, idx, dx, dy);
           int bx = bxi + dx, by = byi + dy;
           bx += (bx < 0) ? R.nbx : (bx >= R.nbx ? -R.nbx : 0);
           by += (by < 0) ? R.nby : (by >= R.nby ? -R.nby : 0);
@@ -369,8 +379,12 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
           if (lane >= o) incl += t;
         }
         const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (first && tot > kCand) {
+          retry = true;
+          break;
+        }
         if (nbuf + tot > kCand) {
-          process_candidates(p, nbuf, s_id[wib], s_X[wib], s_Y[wib], s_d2[wib], s_key[wib], s_val[wib], g.tag,
+          process_candidates(p, nbuf, s_id[wib], s_X[wib], s_Y[wib], s_d2[wib], g.tag,
                              ikey, sc, R.inv_scale, lane);
           nbuf = 0;
           if (tot > kCand) p.err = kECAND;
@@ -401,10 +415,16 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
         }
         __syncwarp();
       }
+      if (retry) {  // the ring-by-ring gathering from ring 0
+        batch = false;
+        k = -1;
+        continue;
+      }
       if (p.err) break;
+      if (first) k = 2;  // rings 1 and 2 are in the batch
       // rings 0..2 are gathered into one batch before clipping
       if (k < 2 && k < kmax) continue;
-      process_candidates(p, nbuf, s_id[wib], s_X[wib], s_Y[wib], s_d2[wib], s_key[wib], s_val[wib], g.tag, ikey,
+      process_candidates(p, nbuf, s_id[wib], s_X[wib], s_Y[wib], s_d2[wib], g.tag, ikey,
                          sc, R.inv_scale, lane);
       nbuf = 0;
       // every unvisited cell is farther than k*bs from cell i
