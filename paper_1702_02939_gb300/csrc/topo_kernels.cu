@@ -231,10 +231,15 @@ __device__ __forceinline__ void clip(Poly& p, long long jX, long long jY, int ji
   const unsigned smask = __ballot_sync(0xffffffffu, lane < m && rem && !prevrem);
   if (__popc(smask) != 1) { p.err = kEDEGEN; return; }
   const int s = __ffs(smask) - 1;
-  const int e = (s + r - 1) % m;
+  int e = s + r - 1;  // (s + r - 1) mod m, with s, r - 1 < m
+  if (e >= m) e -= m;
   const int m2 = m - r + 2;
   if (m2 > 32) { p.err = kERING; return; }
-  const int src = (lane + e + 1) % m;
+  // (lane + e + 1) mod m for the lanes that keep a generator (lane < m2 <= m + 1,
+  // so lane + e + 1 <= 2m); other lanes read any lane
+  int src = lane + e + 1;
+  if (src >= m) src -= m;
+  if (src >= m) src -= m;
   long long ngX = __shfl_sync(0xffffffffu, p.gX, src);
   long long ngY = __shfl_sync(0xffffffffu, p.gY, src);
   int ngid = __shfl_sync(0xffffffffu, p.gid, src);
@@ -255,7 +260,7 @@ __device__ __forceinline__ void clip(Poly& p, long long jX, long long jY, int ji
 // two per lane (entries lane and lane + 32), and are sorted by a bitonic
 // network of register shuffles; the clips then take the entries in order.
 __device__ void process_candidates(Poly& p, int nbuf, const int* s_id, const long long* s_X, const long long* s_Y,
-                                   const float* s_d2, const int* tag, int ikey, float sc, double inv_scale,
+                                   const float* s_d2, const int* s_tag, int ikey, float sc, double inv_scale,
                                    int lane) {
   static_assert(kCand == 64, "two keys per lane");
   if (nbuf == 0) return;
@@ -290,8 +295,7 @@ __device__ void process_candidates(Poly& p, int nbuf, const int* s_id, const lon
     // a cell can cut the polygon only if it is nearer than twice its circumradius
     // (d2 carries a relative error below 1e-6; the margin is 1e-3)
     if (d2 > 4.0f * p.R2 * (1.0f + 1e-3f)) break;
-    const int jid = s_id[e];
-    clip(p, s_X[e], s_Y[e], jid, tag[jid], ikey, sc, inv_scale, lane);
+    clip(p, s_X[e], s_Y[e], s_id[e], s_tag[e], ikey, sc, inv_scale, lane);
     if (p.err) break;
   }
   __syncwarp();
@@ -301,6 +305,7 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
   __shared__ int s_id[kRepairWarps][kCand];
   __shared__ long long s_X[kRepairWarps][kCand], s_Y[kRepairWarps][kCand];
   __shared__ float s_d2[kRepairWarps][kCand];
+  __shared__ int s_tag[kRepairWarps][kCand];  // perturbation keys, loaded with the positions
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gw = blockIdx.x * kRepairWarps + wib, nw = gridDim.x * kRepairWarps;
   // stop the round loop unless this round's check asks for another
@@ -384,7 +389,7 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
           break;
         }
         if (nbuf + tot > kCand) {
-          process_candidates(p, nbuf, s_id[wib], s_X[wib], s_Y[wib], s_d2[wib], g.tag,
+          process_candidates(p, nbuf, s_id[wib], s_X[wib], s_Y[wib], s_d2[wib], s_tag[wib],
                              ikey, sc, R.inv_scale, lane);
           nbuf = 0;
           if (tot > kCand) p.err = kECAND;
@@ -394,6 +399,7 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
           bool same = false;  // another cell on exactly this grid point
           for (int t = 0; t < count; ++t) {
             const int j = g.ids[start + t];
+            s_tag[wib][slot] = g.tag[j];
             if (j == i) {
               s_d2[wib][slot] = kSelfKey;  // never clips
               s_id[wib][slot] = j;
@@ -424,7 +430,7 @@ __global__ void __launch_bounds__(kRepairWarps * 32) k_repair(RepairArgs g) {
       if (first) k = 2;  // rings 1 and 2 are in the batch
       // rings 0..2 are gathered into one batch before clipping
       if (k < 2 && k < kmax) continue;
-      process_candidates(p, nbuf, s_id[wib], s_X[wib], s_Y[wib], s_d2[wib], g.tag, ikey,
+      process_candidates(p, nbuf, s_id[wib], s_X[wib], s_Y[wib], s_d2[wib], s_tag[wib], ikey,
                          sc, R.inv_scale, lane);
       nbuf = 0;
       // every unvisited cell is farther than k*bs from cell i
