@@ -493,3 +493,17 @@ def test_full_size_growth():
     # a daughter that is a small triangle may be removed by a T2 meanwhile
     assert int((g.cc > 0).sum()) == n + int(made.sum()) - sim.counters()["t2_total"]
     sim.close()
+
+
+def test_full_size_five_thousand_steps():
+    """The AVM workload's length: N = 65536, 5000 graph steps with T1 passes;
+    the network is still a valid tiling and the T1 count is in line with the
+    per-step rate of the benchmark (about 16 per step)."""
+    n = 65536
+    sim, xs, ys, th, Lx, Ly = make(n, 1, p0=3.8, v0=0.1, t1_threshold=0.04, seed=1)
+    sim.step(5000)
+    sim.sync()
+    check_network_valid(sim, Lx, Ly, 3.8)
+    c = sim.counters()
+    assert c["steps"] == 5000 and 5 * 5000 < c["t1_total"] < 50 * 5000
+    sim.close()

@@ -667,3 +667,18 @@ def test_million_cells_sampled_against_local_triangulations():
             checked += 1
         assert checked > 1000
     sim.close()
+
+
+def test_full_size_thousand_steps_stay_exact():
+    """The benchmark workload's length: N = 262144, 100 + 1000 graph steps in
+    the fluid regime; the maintained topology then equals the oracle's exact
+    triangulation of the final positions, and the areas tile the box."""
+    n = 262144
+    sim, xs, ys, th, Lx, Ly = make(n, 1, p0=3.85, v0=0.1, seed=1, dt=0.01)
+    sim.step(1100)
+    gx, gy, _ = (t.cpu().numpy() for t in sim.state())
+    check_topology(sim, gx, gy, Lx, Ly)
+    A, P = (t.cpu().numpy() for t in sim.geometry())
+    assert abs(A.sum() - Lx * Ly) <= 1e-9 * Lx * Ly
+    assert sim.counters()["status"] == 0
+    sim.close()
