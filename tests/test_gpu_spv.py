@@ -682,3 +682,36 @@ def test_full_size_thousand_steps_stay_exact():
     assert abs(A.sum() - Lx * Ly) <= 1e-9 * Lx * Ly
     assert sim.counters()["status"] == 0
     sim.close()
+
+
+def test_full_size_batched_replicas_stay_exact():
+    """The batched workload at full size: 512 replicas (N_r log-uniform on
+    [256, 16384], per-replica p0, v0 and box) in one context, 2000 steps; then
+    the rings of six sampled replicas equal the oracle's exact triangulation
+    of each replica's final positions, and every replica's areas tile its box."""
+    R = 512
+    sizes = workloads.replica_sizes(R, 7)
+    p0s, v0s = workloads.replica_params(R, 7)
+    reps, xs, ys, ths, boxes = [], [], [], [], []
+    for r in range(R):
+        x, y, th, L = workloads.spv_uniform(int(sizes[r]), 1000 + r)
+        reps.append(dict(n=int(sizes[r]), Lx=L, Ly=L, p0=float(p0s[r]), v0=float(v0s[r])))
+        xs.append(x); ys.append(y); ths.append(th); boxes.append(oracle.box(L)[:2])
+    sim = cg.SPV(reps, np.concatenate(xs), np.concatenate(ys), np.concatenate(ths), dt=0.01, seed=7)
+    sim.step(2000)
+    gx, gy, _ = (t.cpu().numpy() for t in sim.state())
+    cnt, nbr = (t.cpu().numpy() for t in sim.neighbors())
+    A, _ = (t.cpu().numpy() for t in sim.geometry())
+    assert sim.counters()["status"] == 0
+    starts = np.concatenate([[0], np.cumsum(sizes)])
+    for r in range(R):
+        a, b = starts[r], starts[r + 1]
+        Lx, Ly = boxes[r]
+        assert abs(A[a:b].sum() - Lx * Ly) <= 1e-9 * Lx * Ly
+    for r in np.random.default_rng(3).choice(R, 6, replace=False):
+        a, b = starts[r], starts[r + 1]
+        Lx, Ly = boxes[r]
+        topo = oracle.triangulate(gx[a:b], gy[a:b], Lx, Ly)
+        np.testing.assert_array_equal(cnt[a:b], topo.cnt)
+        np.testing.assert_array_equal(nbr[a:b] - np.where(nbr[a:b] >= 0, a, 0), topo.nbr)
+    sim.close()
