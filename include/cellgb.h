@@ -341,8 +341,8 @@ typedef struct cg_avm_params {
   double t1_length;     /* length of the rotated edge; 0 = 1.5 t1_threshold */
   uint64_t seed;        /* Philox key of the director noise */
   int32_t t1_cap;       /* T1 passes with transitions per step; 0 = 16 */
-  int32_t cell_capacity; /* cell slots, >= N (0: N); divisions fill slots N, N+1, ...
-                            and vertex slots 2N, 2N+1, ... */
+  int32_t cell_capacity; /* cell slots, >= N (0: N); divisions fill empty cell
+                            slots and free vertex slots, lowest first */
   double t2_area;       /* triangular cells with area below this are removed (T2); 0: none */
 } cg_avm_params;
 
@@ -379,9 +379,17 @@ int cg_avm_get_state(cg_avm_ctx* ctx, double* hx, double* hy, double* theta);
 /* Network (layout above); any pointer may be NULL.  Synchronizes. */
 int cg_avm_get_topology(cg_avm_ctx* ctx, int32_t* vc, int32_t* vn, int32_t* cc, int32_t* cv);
 /* Replaces positions (required) and, where not NULL, directors and network
- * arrays, which must describe a valid network of the same N.  Synchronizes. */
+ * arrays, which must describe a valid network of the same N (cell slots).
+ * Synchronizes. */
 int cg_avm_set_state(cg_avm_ctx* ctx, const double* hx, const double* hy, const double* theta, const int32_t* vc,
                      const int32_t* vn, const int32_t* cc, const int32_t* cv);
+/* Per-cell p0, v0 and A0 [N] as they stand (divisions copy them to the new
+ * cells); any pointer may be NULL.  Host or device pointers.  Synchronizes. */
+int cg_avm_get_cell_params(cg_avm_ctx* ctx, double* p0, double* v0, double* a0);
+/* Sets the Philox step counter (the director noise of the next step uses it);
+ * with cg_avm_get_state/_topology/_cell_params it resumes a run.
+ * Synchronizes. */
+int cg_avm_set_step(cg_avm_ctx* ctx, int64_t step);
 /* Polygon areas and perimeters [N] of the current state.  Synchronizes. */
 int cg_avm_get_geometry(cg_avm_ctx* ctx, double* A, double* P);
 /* Vertex forces [V] and, if energy != NULL, the total energy of Eq. 1.
@@ -403,9 +411,10 @@ int cg_avm_set_v0(cg_avm_ctx* ctx, const double* v0);
  * to [1/16, 15/16]; the cut with the smallest u.X > 0 gives new vertex A
  * (edge a1), the one with the largest u.X < 0 new vertex B (edge a2); every
  * product, sum and quotient is rounded on its own.  The cell keeps A,
- * v_{a1+1} .. v_{a2}, B; the next free cell slot takes B, v_{a2+1} .. v_{a1},
- * A and copies the cell's director, p0, v0 and A0; A and B take the next two
- * free vertex slots; the cells across the cut edges gain them.  A division
+ * v_{a1+1} .. v_{a2}, B; the lowest empty cell slot (cc = 0: never used, or
+ * emptied by a T2) takes B, v_{a2+1} .. v_{a1}, A and copies the cell's
+ * director, p0, v0 and A0; A and B take the two lowest free vertex slots
+ * (vc = -1); the cells across the cut edges gain them.  A division
  * with a missing cut, or that would give a cell more than CG_MAX_RING
  * vertices, is not made (made[k] = 0).  cells [count] int32 and dirs
  * [2 count] doubles: host or device; made [count] (NULL to skip) and

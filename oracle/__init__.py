@@ -67,7 +67,7 @@ def _declare(L):
     L.cgo_avm_step.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _ip, _ip, _ip, _ip, _dp, _dp,
                                _dp, _dp, C.c_uint64, C.c_int64, C.c_int, _ip]
     L.cgo_avm_divide.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _ip, _ip, _ip, _ip, _dp, _dp,
-                                 _dp, _dp, C.c_int, _ip, _dp, _ip, _ip, _ip]
+                                 _dp, _dp, C.c_int, _ip, _dp, _ip]
     for name in ("cgo_avm_build", "cgo_avm_forces", "cgo_avm_t1", "cgo_avm_step", "cgo_avm_divide"):
         getattr(L, name).restype = C.c_int
     for extra in ("_declare_avm", "_declare_adjoint"):
@@ -391,18 +391,18 @@ def avm_transitions(net, thr, newlen=None, t2_area=0.0, cap=16, allow_cap=False)
     return net, int(applied[0]), int(applied[1])
 
 
-def avm_divide(net, cells, dirs, next_cell, next_vertex, theta, p0, v0, a0):
-    """Divisions of cells[k] along dirs[k] = (ux, uy), in order, on copies.
-    Returns (network, theta, p0, v0, a0, next_cell, next_vertex, made)."""
+def avm_divide(net, cells, dirs, theta, p0, v0, a0):
+    """Divisions of cells[k] along dirs[k] = (ux, uy), in order, on copies; each
+    one made takes the lowest empty cell slot and the two lowest free vertex
+    slots.  Returns (network, theta, p0, v0, a0, made)."""
     net = net.copy()
     theta, p0, v0, a0 = (np.array(a, np.float64, copy=True) for a in (theta, p0, v0, a0))
     cells = np.ascontiguousarray(cells, dtype=np.int32)
     dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1)
-    nc, nv = np.array([next_cell], np.int32), np.array([next_vertex], np.int32)
     made = np.zeros(len(cells), np.int32)
     _check(lib().cgo_avm_divide(*net._args(), _d(theta), _d(p0), _d(v0), _d(a0), len(cells), _i(cells), _d(dirs),
-                                _i(nc), _i(nv), _i(made)), "avm_divide")
-    return net, theta, p0, v0, a0, int(nc[0]), int(nv[0]), made
+                                _i(made)), "avm_divide")
+    return net, theta, p0, v0, a0, made
 
 
 def avm_t1(net, thr, newlen=None, cap=16, allow_cap=False):

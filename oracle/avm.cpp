@@ -57,7 +57,8 @@
 //    vertex A, edge a1) and the one with the largest u.X < 0 (new vertex B,
 //    edge a2) are taken (every product, sum and quotient rounded on its own);
 //    c keeps A, v_{a1+1} .. v_{a2}, B and the new cell B, v_{a2+1} ..
-//    v_{a1}, A; the cells across the cut edges gain A and B; the new cell
+//    v_{a1}, A (the lowest empty cell slot; A, B the two lowest free vertex
+//    slots); the cells across the cut edges gain A and B; the new cell
 //    copies c's director, p0, v0 and A0.  Refused (no change) when a cut is
 //    missing, a daughter would exceed 16 vertices or a neighbour could not
 //    take the new vertex.
@@ -642,26 +643,25 @@ int cgo_avm_step(int n, int V, double Lx, double Ly, double* hx, double* hy, dou
   return cgo_avm_t1(n, V, Lx, Ly, hx, hy, vc, vn, cc, cv, par[5], par[6], par[7], cap, applied);
 }
 
-// Divisions of cells[k] along dirs[2k], dirs[2k+1], in order; each made one
-// takes cell slot *next_cell and vertex slots *next_vertex, +1 (advanced).
-// made[k] = 1 when division k was made.  Returns -22 on a broken network,
-// -1 when the slots run out.
+// Divisions of cells[k] along dirs[2k], dirs[2k+1], in order; each one made
+// takes the lowest empty cell slot (cc = 0) and the two lowest free vertex
+// slots (vc = -1) left.  made[k] = 1 when division k was made.  Returns -22
+// on a broken network, -1 when the slots run out.
 int cgo_avm_divide(int n, int V, double Lx, double Ly, double* hx, double* hy, int32_t* vc, int32_t* vn,
                    int32_t* cc, int32_t* cv, double* theta, double* p0, double* v0, double* a0, int count,
-                   const int32_t* cells, const double* dirs, int32_t* next_cell, int32_t* next_vertex,
-                   int32_t* made) {
+                   const int32_t* cells, const double* dirs, int32_t* made) {
   Net g{n, V, Lx, Ly, hx, hy, vc, vn, cc, cv};
+  int fc = 0, fv = 0;  // search cursors: a call only fills slots
   for (int k = 0; k < count; ++k) {
     made[k] = 0;
-    if (*next_cell >= n || *next_vertex + 2 > V) return -1;
-    const int r = divide_cell(g, cells[k], dirs[2 * k], dirs[2 * k + 1], *next_cell, *next_vertex,
-                              *next_vertex + 1, theta, p0, v0, a0);
+    while (fc < n && cc[fc] != 0) ++fc;
+    while (fv < V && vc[3 * fv] >= 0) ++fv;
+    int fv2 = fv + 1;
+    while (fv2 < V && vc[3 * fv2] >= 0) ++fv2;
+    if (fc >= n || fv2 >= V) return -1;
+    const int r = divide_cell(g, cells[k], dirs[2 * k], dirs[2 * k + 1], fc, fv, fv2, theta, p0, v0, a0);
     if (r < 0) return -22;
-    if (r == 0) {
-      made[k] = 1;
-      *next_cell += 1;
-      *next_vertex += 2;
-    }
+    if (r == 0) made[k] = 1;
   }
   return 0;
 }

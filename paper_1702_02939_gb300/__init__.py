@@ -133,6 +133,8 @@ def lib():
         L.cg_avm_set_p0.argtypes = [vp, vp]
         L.cg_avm_set_v0.argtypes = [vp, vp]
         L.cg_avm_set_a0.argtypes = [vp, vp]
+        L.cg_avm_set_step.argtypes = [vp, i64]
+        L.cg_avm_get_cell_params.argtypes = [vp, vp, vp, vp]
         L.cg_avm_divide.argtypes = [vp, i32, vp, vp, vp, C.POINTER(i32)]
         L.cg_avm_get_counters.argtypes = [vp, C.POINTER(cg_counters)]
         L.cg_avm_destroy.argtypes = [vp]
@@ -140,7 +142,7 @@ def lib():
         L.cg_avm_last_error.restype = C.c_char_p
         for name in ("cg_avm_workspace_bytes", "cg_avm_workspace_bytes_capacity", "cg_avm_create", "cg_avm_step", "cg_avm_sync", "cg_avm_get_state",
                      "cg_avm_get_topology", "cg_avm_set_state", "cg_avm_get_geometry", "cg_avm_get_forces",
-                     "cg_avm_t1", "cg_avm_set_p0", "cg_avm_set_v0", "cg_avm_set_a0", "cg_avm_divide", "cg_avm_get_counters", "cg_avm_destroy",
+                     "cg_avm_t1", "cg_avm_set_p0", "cg_avm_set_v0", "cg_avm_set_a0", "cg_avm_divide", "cg_avm_set_step", "cg_avm_get_cell_params", "cg_avm_get_counters", "cg_avm_destroy",
                      "cg_avm_profile_step"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -608,6 +610,14 @@ def cg_avm_set_a0(ctx, a0):
     _check_avm(lib().cg_avm_set_a0(ctx, _ptr(a0)), ctx)
 
 
+def cg_avm_set_step(ctx, step):
+    _check_avm(lib().cg_avm_set_step(ctx, int(step)), ctx)
+
+
+def cg_avm_get_cell_params(ctx, p0, v0, a0):
+    _check_avm(lib().cg_avm_get_cell_params(ctx, _ptr(p0), _ptr(v0), _ptr(a0)), ctx)
+
+
 def cg_avm_divide(ctx, count, cells, dirs, made):
     n_made = C.c_int32(0)
     _check_avm(lib().cg_avm_divide(ctx, int(count), _ptr(cells), _ptr(dirs), _ptr(made), C.byref(n_made)), ctx)
@@ -716,6 +726,16 @@ class AVM:
         made = np.zeros(cells.size, np.int32)
         cg_avm_divide(self.ctx, cells.size, cells, dirs, made)
         return made
+
+    def cell_params(self):
+        """(p0, v0, A0) per cell slot as they stand (divisions copy them)."""
+        p0, v0, a0 = self._out(self.n), self._out(self.n), self._out(self.n)
+        cg_avm_get_cell_params(self.ctx, p0, v0, a0)
+        return p0, v0, a0
+
+    def set_step(self, step):
+        """Sets the step counter that keys the director noise (to resume a run)."""
+        cg_avm_set_step(self.ctx, step)
 
     def set_a0(self, a0):
         """Per-cell preferred areas (a cell given a small A0 shrinks and,

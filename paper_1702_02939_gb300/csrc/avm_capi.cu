@@ -29,7 +29,7 @@ struct AvmOff {
   size_t hx, hy, hf, vc, vn, cc, cv, theta, p0, v0, a0, P0, A, P, ka, kp, energy, act, Fx, Fy, lock, cand_e, cand,
       done;
   size_t owned, base_local, base_partial, xs, ys, cnt, nbr, scalar, ctl, dir_tab;
-  size_t div_cells, div_dirs, div_made, div_next;  // staging of cg_avm_divide
+  size_t div_cells, div_dirs, div_made, div_cslots, div_vslots;  // staging of cg_avm_divide
   size_t total;
 };
 
@@ -77,7 +77,8 @@ AvmOff avm_layout(int64_t n, size_t spv_bytes) {
   o.div_cells = L.take(n * i4);
   o.div_dirs = L.take(2 * n * d);
   o.div_made = L.take(n * i4);
-  o.div_next = L.take(2 * i4);
+  o.div_cslots = L.take(n * i4);
+  o.div_vslots = L.take(2 * n * i4);
   o.total = L.total;
   return o;
 }
@@ -87,7 +88,6 @@ AvmOff avm_layout(int64_t n, size_t spv_bytes) {
 struct cg_avm_ctx {
   int n = 0, V = 0;        // cell slots (the capacity) and vertex slots (2n)
   int n_seed = 0;          // cells of the initial network (slots 0 .. n_seed-1)
-  int next_cell = 0, next_vertex = 0;  // first slots never used (divisions take them in order)
   double Lx = 0, Ly = 0;
   cg_avm_params par{};
   char* ws = nullptr;
@@ -306,8 +306,6 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
   c->n = ncap;
   c->V = 2 * ncap;
   c->n_seed = n;
-  c->next_cell = n;
-  c->next_vertex = 2 * n;
   c->par = *par;
   c->ws = static_cast<char*>(d_ws);
   c->stream = static_cast<cudaStream_t>(stream);
@@ -496,6 +494,28 @@ int cg_avm_set_state(cg_avm_ctx* c, const double* hx, const double* hy, const do
   return avm_status(c);
 }
 
+int cg_avm_get_cell_params(cg_avm_ctx* c, double* p0, double* v0, double* a0) {
+  if (!c) return CG_EINVAL;
+  int rc = avm_status(c);
+  if (rc) return rc;
+  const size_t b = (size_t)c->n * sizeof(double);
+  if ((rc = copy_out(c, p0, c->at<double>(c->off.p0), b))) return rc;
+  if ((rc = copy_out(c, v0, c->at<double>(c->off.v0), b))) return rc;
+  if ((rc = copy_out(c, a0, c->at<double>(c->off.a0), b))) return rc;
+  return avm_status(c);
+}
+
+int cg_avm_set_step(cg_avm_ctx* c, int64_t step) {
+  if (!c || step < 0) return CG_EINVAL;
+  int rc = avm_status(c);
+  if (rc) return rc;
+  Ctl h;
+  AV_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
+  h.step = step;
+  AV_CUDA(c, cudaMemcpy(c->ctl(), &h, sizeof(Ctl), cudaMemcpyHostToDevice));
+  return CG_OK;
+}
+
 int cg_avm_get_geometry(cg_avm_ctx* c, double* A, double* P) {
   if (!c) return CG_EINVAL;
   launch_avm_forces(avm_args(c), c->stream);
@@ -544,31 +564,43 @@ int cg_avm_divide(cg_avm_ctx* c, int32_t count, const int32_t* cells, const doub
     if (n_made) *n_made = 0;
     return CG_OK;
   }
-  if (!cells || !dirs) return CG_EINVAL;
-  if (c->next_cell + count > c->n || c->next_vertex + 2 * count > c->V)
-    return afail(c, CG_EINVAL, "not enough free cell slots for the divisions");
+  if (!cells || !dirs || count > c->n) return CG_EINVAL;
   int rc = avm_status(c);
   if (rc) return rc;
+  // the slots the divisions may take, in order: the lowest empty cells and
+  // the lowest free vertices (a call only fills slots)
+  std::vector<int> hcc(c->n), hvc(3 * (size_t)c->V), cs, vs;
+  AV_CUDA(c, cudaMemcpy(hcc.data(), c->at<int>(c->off.cc), hcc.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  AV_CUDA(c, cudaMemcpy(hvc.data(), c->at<int>(c->off.vc), hvc.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < c->n && (int)cs.size() < count; ++k)
+    if (hcc[k] == 0) cs.push_back(k);
+  for (int v = 0; v < c->V && (int)vs.size() < 2 * count; ++v)
+    if (hvc[3 * (size_t)v] < 0) vs.push_back(v);
+  if ((int)cs.size() < count || (int)vs.size() < 2 * count)
+    return afail(c, CG_EINVAL, "not enough free cell slots for the divisions");
   int* dc = c->at<int>(c->off.div_cells);
   double* dd = c->at<double>(c->off.div_dirs);
   int* dm = c->at<int>(c->off.div_made);
-  int* dn = c->at<int>(c->off.div_next);
-  const int next[2] = {c->next_cell, c->next_vertex};
+  int* dcs = c->at<int>(c->off.div_cslots);
+  int* dvs = c->at<int>(c->off.div_vslots);
   if ((rc = copy_in(c, dc, cells, (size_t)count * sizeof(int)))) return rc;
   if ((rc = copy_in(c, dd, dirs, 2 * (size_t)count * sizeof(double)))) return rc;
-  AV_CUDA(c, cudaMemcpyAsync(dn, next, sizeof(next), cudaMemcpyHostToDevice, c->stream));
+  AV_CUDA(c, cudaMemcpyAsync(dcs, cs.data(), cs.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  AV_CUDA(c, cudaMemcpyAsync(dvs, vs.data(), vs.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   launch_check_finite(2 * count, dd, c->ctl(), c->stream);
-  launch_avm_divide(avm_args(c), count, dc, dd, dn, dm, c->stream);
+  launch_avm_divide(avm_args(c), count, dc, dd, dcs, dvs, dm, c->stream);
   AV_CUDA(c, cudaGetLastError());
-  int after[2];
-  AV_CUDA(c, cudaMemcpyAsync(after, dn, sizeof(after), cudaMemcpyDeviceToHost, c->stream));
-  if (made && (rc = copy_out(c, made, dm, (size_t)count * sizeof(int)))) return rc;
+  std::vector<int> hm(count);
+  AV_CUDA(c, cudaMemcpyAsync(hm.data(), dm, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   AV_CUDA(c, cudaStreamSynchronize(c->stream));
   rc = avm_status(c);
   if (rc) return rc;
-  if (n_made) *n_made = after[0] - c->next_cell;
-  c->next_cell = after[0];
-  c->next_vertex = after[1];
+  if (made) AV_CUDA(c, cudaMemcpy(made, hm.data(), (size_t)count * sizeof(int), cudaMemcpyDefault));
+  if (n_made) {
+    int t = 0;
+    for (int v : hm) t += v;
+    *n_made = t;
+  }
   return CG_OK;
 }
 

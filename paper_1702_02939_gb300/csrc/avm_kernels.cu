@@ -906,27 +906,28 @@ __device__ int divide_cell(const AvmArgs& g, int c, double ux, double uy, int ne
 }
 
 // The divisions of a call, one after the other (one thread: each sees the
-// network the previous ones left).  next[0], next[1]: first free cell and
-// vertex slots, advanced by each division made; made[k] = 1 when division k
-// was made.
-__global__ void k_avm_divide(AvmArgs g, int count, const int* cells, const double* dirs, int* next, int* made) {
+// network the previous ones left).  Division k, if made, takes the next
+// unused entries of cslots (cell slot) and vslots (two vertex slots), the
+// empty slots in increasing order; made[k] = 1 when division k was made.
+__global__ void k_avm_divide(AvmArgs g, int count, const int* cells, const double* dirs, const int* cslots,
+                             const int* vslots, int* made) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int m = 0;
   for (int k = 0; k < count; ++k) {
     made[k] = 0;
     const int c = cells[k];
-    if ((unsigned)c >= (unsigned)g.n || next[0] >= g.n || next[1] + 2 > g.V) {
+    if ((unsigned)c >= (unsigned)g.n) {
       raise_status(g.ctl, kEINVAL);
       return;
     }
-    const int r = divide_cell(g, c, dirs[2 * k], dirs[2 * k + 1], next[0], next[1], next[1] + 1);
+    const int r = divide_cell(g, c, dirs[2 * k], dirs[2 * k + 1], cslots[m], vslots[2 * m], vslots[2 * m + 1]);
     if (r < 0) {
       raise_status(g.ctl, kETOPO);
       return;
     }
     if (r == 0) {
       made[k] = 1;
-      next[0] += 1;
-      next[1] += 2;
+      ++m;
     }
   }
 }
@@ -981,9 +982,9 @@ void launch_avm_forces(const AvmArgs& a, cudaStream_t st) {
   k_avm_cells<<<cell_blocks_of(a.n), kAvmCellThreads, 0, st>>>(f);
   k_avm_force_move<<<vertex_blocks_of(a.V), kAvmVertexThreads, 0, st>>>(f);
 }
-void launch_avm_divide(const AvmArgs& a, int count, const int* cells, const double* dirs, int* next, int* made,
-                       cudaStream_t st) {
-  if (count > 0) k_avm_divide<<<1, 32, 0, st>>>(a, count, cells, dirs, next, made);
+void launch_avm_divide(const AvmArgs& a, int count, const int* cells, const double* dirs, const int* cslots,
+                       const int* vslots, int* made, cudaStream_t st) {
+  if (count > 0) k_avm_divide<<<1, 32, 0, st>>>(a, count, cells, dirs, cslots, vslots, made);
 }
 void launch_avm_p0s(const AvmArgs& a, cudaStream_t st) {
   k_avm_p0s<<<blocks_of(a.n), kAvmThreads, 0, st>>>(a);

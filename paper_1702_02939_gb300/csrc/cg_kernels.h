@@ -284,9 +284,9 @@ void launch_avm_validate(const AvmArgs& a, cudaStream_t st);
 // P0[c] = p0[c] sqrt(a0[c]) after p0 or A0 change
 void launch_avm_p0s(const AvmArgs& a, cudaStream_t st);
 // count divisions (cells[k], direction dirs[2k], dirs[2k+1]) in order, one
-// thread; next = {first free cell slot, first free vertex slot}, advanced
-void launch_avm_divide(const AvmArgs& a, int count, const int* cells, const double* dirs, int* next, int* made,
-                       cudaStream_t st);
+// thread; the divisions made take cslots[0, 1, ...] and vslots[0, 1, ...] in turn
+void launch_avm_divide(const AvmArgs& a, int count, const int* cells, const double* dirs, const int* cslots,
+                       const int* vslots, int* made, cudaStream_t st);
 void launch_avm_shadow(const AvmArgs& a, cudaStream_t st);
 void launch_fill_d(int n, double v, double* out, cudaStream_t st);
 void launch_fill_u64(int n, unsigned long long v, unsigned long long* out, cudaStream_t st);

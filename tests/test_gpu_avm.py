@@ -444,7 +444,7 @@ def test_divisions_match_oracle():
     ang = rng.uniform(0.0, np.pi, 30)
     dirs = np.stack([np.cos(ang), np.sin(ang)], 1)
     made = sim.divide(cells, dirs)
-    o, theta, pa, va, aa, nc, nv, omade = oracle.avm_divide(net, cells, dirs, n, 2 * n, theta, pa, va, aa)
+    o, theta, pa, va, aa, omade = oracle.avm_divide(net, cells, dirs, theta, pa, va, aa)
     np.testing.assert_array_equal(made, omade)
     g, gth = gpu_net(sim, Lx, Ly)
     assert_same_network(g, o)
@@ -506,4 +506,78 @@ def test_full_size_five_thousand_steps():
     check_network_valid(sim, Lx, Ly, 3.8)
     c = sim.counters()
     assert c["steps"] == 5000 and 5 * 5000 < c["t1_total"] < 50 * 5000
+    sim.close()
+
+
+def test_resume_after_deaths_and_divisions_is_bit_identical():
+    """A run with dying cells and divisions, saved (positions, directors,
+    network, step counter) and resumed in a fresh context, continues bit for
+    bit like the original (divisions take the same slots)."""
+    n, cap = 400, 440
+    kw = dict(p0=3.8, v0=0.1, t1_threshold=0.04, t2_area=0.01, seed=12, capacity=cap)
+    a, xs, ys, th, Lx, Ly = make(n, 41, **kw)
+    a0 = np.ones(cap)
+    rng = np.random.default_rng(4)
+    dying = rng.choice(n, 6, replace=False)
+    a0[dying] = 0.0
+    a.set_a0(a0)
+    live = np.setdiff1d(np.arange(n), dying)
+    c1, c2 = rng.choice(live, 8, replace=False), rng.choice(live, 8, replace=False)
+    d1, d2 = rng.normal(size=(8, 2)), rng.normal(size=(8, 2))
+    a.step(60)
+    a.divide(c1, d1)
+    a.step(20)
+    hx, hy, theta = (t.clone() for t in a.state())
+    topo = [t.clone() for t in a.topology()]
+    p0s, v0s, a0s = a.cell_params()  # divisions may have put new cells in emptied slots
+    step = a.counters()["steps"]
+    a.divide(c2, d2)
+    a.step(40)
+    b, *_ = make(n, 42, **kw)  # other seeds: everything comes from the saved state
+    b.set_p0(p0s)
+    b.set_v0(v0s)
+    b.set_a0(a0s)
+    b.set_state(hx, hy, theta, *topo)
+    b.set_step(step)
+    b.divide(c2, d2)
+    b.step(40)
+    for ta, tb in zip(a.state(), b.state()):
+        assert torch.equal(ta, tb)
+    for ta, tb in zip(a.topology(), b.topology()):
+        assert torch.equal(ta, tb)
+    assert a.counters()["t2_total"] > 0
+    a.close()
+    b.close()
+
+
+def test_divisions_after_deaths_match_oracle():
+    """Dying cells removed by T2s free their slots; later divisions take the
+    lowest empty and free slots, as in the oracle."""
+    n, cap, p0, v0, thr = 100, 120, 3.8, 0.05, 0.04
+    sim, xs, ys, th, Lx, Ly = make(n, 33, p0=p0, v0=v0, t1_threshold=thr, t2_area=0.01, seed=8, capacity=cap)
+    net = oracle.avm_build(xs, ys, Lx, Ly).with_capacity(cap)
+    theta = np.concatenate([th, np.zeros(cap - n)])
+    pa, va, aa = np.full(cap, p0), np.full(cap, v0), np.ones(cap)
+    rng = np.random.default_rng(2)
+    dying = rng.choice(n, 4, replace=False)
+    aa[dying] = 0.0
+    sim.set_a0(aa)
+    o = net
+    for k in range(150):
+        sim.step(1)
+        o, theta, _, _ = oracle.avm_step(o, theta, pa, va, seed=8, step=k, A0=aa, thr=thr, t2_area=0.01, counts=True)
+        g, gth = gpu_net(sim, Lx, Ly)
+        assert_same_network(g, o)
+        load(sim, o, theta)
+    removed = np.nonzero(o.cc[:n] == 0)[0]
+    assert len(removed) >= 2
+    live = np.nonzero(o.cc > 0)[0]
+    cells = rng.choice(live, 10, replace=False)
+    dirs = rng.normal(size=(10, 2))
+    made = sim.divide(cells, dirs)
+    o, theta, pa, va, aa, omade = oracle.avm_divide(o, cells, dirs, theta, pa, va, aa)
+    np.testing.assert_array_equal(made, omade)
+    g, gth = gpu_net(sim, Lx, Ly)
+    assert_same_network(g, o)
+    assert np.all(o.cc[removed] > 0)  # the emptied slots are taken first
     sim.close()

@@ -569,15 +569,16 @@ def test_director_terms_match_libm_and_oracle():
     sim.close()
 
 
-@pytest.mark.parametrize("precision", ["f64", "f32"])
-def test_run_io_is_bit_identical_to_set_step_get(precision):
+@pytest.mark.parametrize("precision,sort_every", [("f64", 0), ("f32", 0), ("f64", 3)])
+def test_run_io_is_bit_identical_to_set_step_get(precision, sort_every):
     """cg_run_io (uploads overlapped with the steps, double-buffered staging)
     gives the same positions, bit for bit, as cg_set_v0, cg_step(1),
     cg_get_state per step; with a per-step v0 and per-step outputs, and with
     v0 kept and one output buffer reused."""
     n, K = 1000, 7
-    a, *_ = make(n, 51, p0=3.85, v0=0.1, seed=8, dt=0.01, precision=precision)
-    b, *_ = make(n, 51, p0=3.85, v0=0.1, seed=8, dt=0.01, precision=precision)
+    kw = dict(p0=3.85, v0=0.1, seed=8, dt=0.01, precision=precision, sort_every=sort_every)
+    a, *_ = make(n, 51, **kw)
+    b, *_ = make(n, 51, **kw)
     rng = np.random.default_rng(5)
     v0 = rng.uniform(0.0, 0.3, (K, n))
     ref_x, ref_y = [], []

@@ -46,8 +46,11 @@ def test_divisions_split_cells_exactly(seed):
     ang = rng.uniform(0.0, np.pi, 30)
     dirs = np.stack([np.cos(ang), np.sin(ang)], 1)
     _, _, A0, P0, _ = oracle.avm_forces(net, p0, A0=a0)
-    g, th2, p02, v02, a02, nc, nv, made = oracle.avm_divide(net, cells, dirs, n, 2 * n, th, p0, v0, a0)
-    assert made.sum() == 30 and nc == n + 30 and nv == 2 * n + 60
+    g, th2, p02, v02, a02, made = oracle.avm_divide(net, cells, dirs, th, p0, v0, a0)
+    # no cell has died: the new cells fill slots n, n+1, ... and the new vertices 2n, 2n+1, ...
+    assert made.sum() == 30
+    assert np.all(g.cc[n:n + 30] > 0) and np.all(g.cc[n + 30:] == 0)
+    assert np.all(g.vc[3 * 2 * n:3 * (2 * n + 60)] >= 0) and np.all(g.vc[3 * (2 * n + 60):] == -1)
     check_alive_network(g, p0=p02, a0=a02)
     _, _, A1, P1, _ = oracle.avm_forces(g, p02, A0=a02)
     # divisions in order: cell k's daughter is slot n + k
@@ -62,14 +65,14 @@ def test_divisions_split_cells_exactly(seed):
             continue
         assert abs(A1[c] - A0[c]) <= 1e-12
     # each division (checked against the state just before it, one at a time)
-    cur, tcur, pcur, vcur, acur, ncur, vnext = net, th, p0, v0, a0, n, 2 * n
+    cur, tcur, pcur, vcur, acur, ncur, vnext = net, th, p0, v0, a0, n, 2 * n  # the slots each division takes
     for k, c in enumerate(cells):
         c = int(c)
         _, _, Ab, Pb, _ = oracle.avm_forces(cur, pcur, A0=acur)
         vs, pts, (x0, y0) = polygon(cur, c)
         mean = pts.mean(0)
-        nxt, tcur, pcur, vcur, acur, ncur2, vnext2, mk = oracle.avm_divide(cur, [c], dirs[k][None], ncur, vnext, tcur,
-                                                                         pcur, vcur, acur)
+        nxt, tcur, pcur, vcur, acur, mk = oracle.avm_divide(cur, [c], dirs[k][None], tcur, pcur, vcur, acur)
+        ncur2, vnext2 = ncur + 1, vnext + 2
         assert mk[0] == 1
         _, _, Aa, Pa, _ = oracle.avm_forces(nxt, pcur, A0=acur)
         d = ncur
@@ -100,17 +103,20 @@ def test_grown_network_keeps_stepping():
     n, cap = 100, 160
     net, th, p0, v0, a0 = grown(n, 4, cap)
     rng = np.random.default_rng(4)
-    nc, nv, births = n, 2 * n, 0
+    births = deaths = 0
     for k in range(300):
         if k % 50 == 0:
             alive = np.nonzero(net.cc > 0)[0]
             cells = rng.choice(alive, 8, replace=False)
             ang = rng.uniform(0.0, np.pi, 8)
-            net, th, p0, v0, a0, nc, nv, made = oracle.avm_divide(net, cells, np.stack([np.cos(ang), np.sin(ang)], 1),
-                                                                  nc, nv, th, p0, v0, a0)
+            net, th, p0, v0, a0, made = oracle.avm_divide(net, cells, np.stack([np.cos(ang), np.sin(ang)], 1),
+                                                          th, p0, v0, a0)
             births += int(made.sum())
-        net, th, _, _ = oracle.avm_step(net, th, p0, v0, seed=4, step=k, A0=a0, thr=0.04, t2_area=0.01, counts=True)
-    assert births == 48 and nc == n + births
+        net, th, _, t2 = oracle.avm_step(net, th, p0, v0, seed=4, step=k, A0=a0, thr=0.04, t2_area=0.01, counts=True)
+        deaths += t2
+    assert births == 48
+    # deaths free slots that later divisions take again
+    assert int((net.cc > 0).sum()) == n + births - deaths
     check_alive_network(net, p0=p0, a0=a0)
 
 
@@ -118,4 +124,25 @@ def test_slots_running_out_is_an_error():
     n = 64
     net, th, p0, v0, a0 = grown(n, 5, n + 1)
     with pytest.raises(RuntimeError):
-        oracle.avm_divide(net, [3, 4], [[1.0, 0.0], [0.0, 1.0]], n, 2 * n, th, p0, v0, a0)
+        oracle.avm_divide(net, [3, 4], [[1.0, 0.0], [0.0, 1.0]], th, p0, v0, a0)
+
+
+def test_division_reuses_the_slots_a_death_freed():
+    """Divisions take the lowest empty cell slot and the two lowest free vertex
+    slots: after a T2 removal those are the slots it freed."""
+    n, cap = 64, 80
+    net, th, p0, v0, a0 = grown(n, 11, cap)
+    a0[9] = 0.0
+    for k in range(400):
+        net, th, _, t2 = oracle.avm_step(net, th, p0, v0, seed=5, step=k, A0=a0, thr=0.04, t2_area=0.01, counts=True)
+        if t2:
+            break
+    assert net.cc[9] == 0
+    freed = sorted(np.nonzero(net.vc.reshape(-1, 3)[:2 * n, 0] < 0)[0].tolist())
+    assert len(freed) == 2
+    a0[9] = 1.0
+    g, th2, p02, v02, a02, made = oracle.avm_divide(net, [20], [[1.0, 0.3]], th, p0, v0, a0)
+    assert made[0] == 1 and g.cc[9] > 0 and np.all(g.cc[n:] == 0)
+    assert all(g.vc[3 * v] >= 0 for v in freed)
+    assert th2[9] == th2[20] and a02[9] == a0[20]
+    check_alive_network(g, p0=p02, a0=a02)
