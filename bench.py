@@ -56,7 +56,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # Dominant-kernel DRAM traffic per launch (dram__bytes_read.sum +
 # dram__bytes_write.sum) from the committed ncu capture of the current k_geom
 # (profiles/k_geom_spv_N262144.md); set back to None whenever k_geom changes.
-GEOM_DRAM_BYTES_PER_LAUNCH = None
+GEOM_DRAM_BYTES_PER_LAUNCH = 56.95e6
 
 
 def parse():
