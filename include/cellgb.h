@@ -115,6 +115,9 @@ typedef struct cg_launch {
                                     0 = one thread per cell (default) */
   int32_t test_blocks_per_sm;    /* grid of the circumcircle test = SMs x this (default 8), a
                                     grid-stride loop over cells; 0 = one thread per cell */
+  int32_t dir_beside_geom;       /* 1: the director terms on a branch of their own, beside the
+                                    geometry pass (both FP64; one fills the other's idle FP64
+                                    cycles); 0: before it on the same branch (default 0) */
 } cg_launch;
 
 /* Workspace size for R replicas. */

@@ -182,12 +182,12 @@ struct cg_ctx {
   Offsets off{};
   cudaStream_t stream = nullptr;    // user stream
   cudaStream_t capture = nullptr;   // private stream used for graph capture
-  cudaStream_t side[2] = {nullptr, nullptr};  // branches of the captured step
-  cudaEvent_t fork = nullptr, join_dir = nullptr, join_list = nullptr;
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};  // branches of the captured step
+  cudaEvent_t fork = nullptr, join_dir = nullptr, join_list = nullptr, join_terms = nullptr;
   // cg_run_io: copy streams and the events that order the double-buffered staging
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t in_ready[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_free[2] = {};
-  cg_launch launch{4, 4, 2, 1, 0, 8};          // launch shapes of the step graph
+  cg_launch launch{4, 4, 2, 1, 0, 8, 0};       // launch shapes of the step graph
   std::vector<cg_replica> user_reps;           // as passed to cg_create
   cudaGraphExec_t step_exec = nullptr;
   int graph_steps = 0;
@@ -453,12 +453,20 @@ int check_grid_all(const cg_ctx* c) { return (int)((c->N + 255) / 256); }
 // new noise) followed by the geometry and force sets of the new positions,
 // which overlaps the latency-bound repair rounds (rings rewritten meanwhile
 // are recomputed by the fix-up after the rounds) — and ends with the forces
-// and the next pending move, while the force sets are still in L2.
+// and the next pending move, while the force sets are still in L2.  With
+// dir_beside_geom the director terms take a fourth branch and run beside the
+// geometry instead of before it.
 void enqueue_step_prefix(cg_ctx* c, cudaStream_t st) {
   launch_begin_topology(c->ctl(), 1, st);
   cudaEventRecord(c->fork, st);
   cudaStreamWaitEvent(c->side[0], c->fork, 0);
-  run_dir(c, dir_args_step(c), c->side[0], dir_grid(c));
+  if (c->launch.dir_beside_geom) {
+    cudaStreamWaitEvent(c->side[2], c->fork, 0);
+    run_dir(c, dir_args_step(c), c->side[2], dir_grid(c));
+    cudaEventRecord(c->join_terms, c->side[2]);
+  } else {
+    run_dir(c, dir_args_step(c), c->side[0], dir_grid(c));
+  }
   GeomArgs g = geom_args(c);
   g.tolerant = 1;
   run_geom(c, g, c->side[0], geom_grid(c));
@@ -479,6 +487,7 @@ void enqueue_step_suffix(cg_ctx* c, cudaStream_t st) {
   g.list_count = &c->ctl()->dirty_count;
   g.list_bits = c->at<unsigned>(c->off.dirty_bits);
   run_geom(c, g, st, sm_count() * 2);
+  if (c->launch.dir_beside_geom) cudaStreamWaitEvent(st, c->join_terms, 0);
   run_force(c, force_args(c, 1), st);
 }
 
@@ -738,9 +747,11 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->capture, cudaStreamNonBlocking, hi);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side[0], cudaStreamNonBlocking, lo);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side[1], cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side[2], cudaStreamNonBlocking, lo);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_dir, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_list, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_terms, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->h2d, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking);
     for (int b = 0; b < 2; ++b)
@@ -1090,7 +1101,8 @@ int cg_set_launch(cg_ctx* c, const cg_launch* l) {
   if (l->repair_blocks_per_sm < 1 || l->repair_blocks_per_sm > 64 || l->check_blocks_per_sm < 1 ||
       l->check_blocks_per_sm > 64 || l->dir_blocks_per_sm < 0 || l->dir_blocks_per_sm > 64 ||
       (l->dir_low_priority != 0 && l->dir_low_priority != 1) || l->geom_blocks_per_sm < 0 ||
-      l->geom_blocks_per_sm > 64 || l->test_blocks_per_sm < 0 || l->test_blocks_per_sm > 64)
+      l->geom_blocks_per_sm > 64 || l->test_blocks_per_sm < 0 || l->test_blocks_per_sm > 64 ||
+      (l->dir_beside_geom != 0 && l->dir_beside_geom != 1))
     return CG_EINVAL;
   int rc = read_status(c);
   if (rc) return rc;
@@ -1174,20 +1186,23 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
   static const int prio_opts[] = {0, 1};
   static const int geom_opts[] = {0, 4, 8, 16};
   static const int test_opts[] = {0, 2, 4, 8};
+  static const int beside_opts[] = {0, 1};
   const cg_launch start = c->launch;
   cg_launch cur = start;
   double cur_ms = 0.0;
   rc = trial(cur, steps_per_trial, cur_ms);
   for (int sweep = 0; sweep < 2 && !rc; ++sweep) {
-    for (int field = 0; field < 6 && !rc; ++field) {
+    for (int field = 0; field < 7 && !rc; ++field) {
       const int* opts = field == 0 ? repair_opts : field == 1 ? check_opts : field == 2 ? dir_opts
-                      : field == 3 ? prio_opts : field == 4 ? geom_opts : test_opts;
-      const int nopt = field == 0 ? 4 : field == 1 ? 4 : field == 2 ? 5 : field == 3 ? 2 : 4;
+                      : field == 3 ? prio_opts : field == 4 ? geom_opts : field == 5 ? test_opts : beside_opts;
+      const int nopt = field == 0 ? 4 : field == 1 ? 4 : field == 2 ? 5 : field == 3 ? 2 : field == 5 ? 4
+                     : field == 6 ? 2 : 4;
       for (int k = 0; k < nopt && !rc; ++k) {
         cg_launch cand = cur;
         int* slot = field == 0 ? &cand.repair_blocks_per_sm : field == 1 ? &cand.check_blocks_per_sm
                   : field == 2 ? &cand.dir_blocks_per_sm : field == 3 ? &cand.dir_low_priority
-                  : field == 4 ? &cand.geom_blocks_per_sm : &cand.test_blocks_per_sm;
+                  : field == 4 ? &cand.geom_blocks_per_sm : field == 5 ? &cand.test_blocks_per_sm
+                  : &cand.dir_beside_geom;
         if (*slot == opts[k]) continue;
         *slot = opts[k];
         double ms = 0.0;
@@ -1391,7 +1406,7 @@ int cg_destroy(cg_ctx* c) {
   if (c->capture) cudaStreamDestroy(c->capture);
   for (cudaStream_t sd : c->side)
     if (sd) cudaStreamDestroy(sd);
-  for (cudaEvent_t ev : {c->fork, c->join_dir, c->join_list})
+  for (cudaEvent_t ev : {c->fork, c->join_dir, c->join_list, c->join_terms})
     if (ev) cudaEventDestroy(ev);
   for (cudaStream_t sc : {c->h2d, c->d2h})
     if (sc) cudaStreamDestroy(sc);

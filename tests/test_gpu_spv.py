@@ -346,12 +346,18 @@ def test_launch_shapes_do_not_change_results():
     b.set_launch(repair_blocks_per_sm=8, check_blocks_per_sm=4, dir_blocks_per_sm=1, dir_low_priority=1,
                  geom_blocks_per_sm=2, test_blocks_per_sm=2)
     assert b.launch["dir_blocks_per_sm"] == 1
+    c, *_ = make(n, 33, p0=3.85, v0=0.1, seed=3)
+    c.set_launch(dir_beside_geom=1, dir_low_priority=0, dir_blocks_per_sm=0)
+    assert c.launch["dir_beside_geom"] == 1
     a.step(20)
     b.step(20)
-    for ta, tb in zip(a.state() + a.neighbors(), b.state() + b.neighbors()):
-        assert torch.equal(ta, tb)
-    a.close()
-    b.close()
+    c.step(20)
+    for ta, tb, tc in zip(a.state() + a.neighbors(), b.state() + b.neighbors(), c.state() + c.neighbors()):
+        assert torch.equal(ta, tb) and torch.equal(ta, tc)
+    with pytest.raises(RuntimeError):
+        c.set_launch(dir_beside_geom=2)
+    for s in (a, b, c):
+        s.close()
 
 
 def test_autotune_takes_no_step_and_keeps_results():
@@ -365,7 +371,8 @@ def test_autotune_takes_no_step_and_keeps_results():
     before = a.state()
     best, ms = a.autotune(3)
     assert ms > 0 and set(best) == {"repair_blocks_per_sm", "check_blocks_per_sm", "dir_blocks_per_sm",
-                                    "dir_low_priority", "geom_blocks_per_sm", "test_blocks_per_sm"}
+                                    "dir_low_priority", "geom_blocks_per_sm", "test_blocks_per_sm",
+                                    "dir_beside_geom"}
     assert a.launch == best
     for t0, t1 in zip(before, a.state()):
         assert torch.equal(t0, t1)
