@@ -197,8 +197,9 @@ __global__ void k_avm_cells(AvmArgs g) {
       qx = mimg_a(hx[v] - x0, g.ax);
       qy = mimg_a(hy[v] - y0, g.ay);
     }
-    area += px * qy - qx * py;
-    per += sqrt((qx - px) * (qx - px) + (qy - py) * (qy - py));
+    area = fma(-qx, py, fma(px, qy, area));
+    const double l2 = (qx - px) * (qx - px) + (qy - py) * (qy - py);
+    per = (__double_as_longlong(l2) > 0) ? fma(l2, fast_rsqrt(l2), per) : per;  // sqrt(l2)
     px = qx;
     py = qy;
   }
@@ -213,7 +214,9 @@ __global__ void k_avm_cells(AvmArgs g) {
     const double th = g.theta[c];
     double sn, cs;
     dm_sincos(th, g.tab, sn, cs);
-    g.act[c] = make_double2(g.v0[c] * cs, g.v0[c] * sn);
+    // (v0/3) n(theta): each of the cell's vertices takes a third (Eq. 4, n = 3)
+    const double v3 = g.v0[c] * (1.0 / 3.0);
+    g.act[c] = make_double2(v3 * cs, v3 * sn);
     g.theta[c] = th + g.noise_amp * director_noise(g.seed, c, g.ctl->step, g.tab);
   }
 }
@@ -253,7 +256,7 @@ __global__ void k_avm_force_move(AvmArgs g) {
       const int w = g.vn[3 * v + k];
       ux[k] = mimg_a(hx[w] - xv, g.ax);
       uy[k] = mimg_a(hy[w] - yv, g.ay);
-      const double il = rsqrt(ux[k] * ux[k] + uy[k] * uy[k]);
+      const double il = fast_rsqrt(ux[k] * ux[k] + uy[k] * uy[k]);
       nx[k] = ux[k] * il;
       ny[k] = uy[k] * il;
     }
@@ -277,7 +280,7 @@ __global__ void k_avm_force_move(AvmArgs g) {
     g.Fy[v] = fy;
     if (g.move) {
       const int nxt = cur ^ 1;
-      const double mx = xv + g.dt * (g.mu * fx + ax / 3.0), my = yv + g.dt * (g.mu * fy + ay / 3.0);
+      const double mx = xv + g.dt * (g.mu * fx + ax), my = yv + g.dt * (g.mu * fy + ay);
       if (!isfinite(mx) || !isfinite(my)) raise_status(g.ctl, kENONFINITE);
       const double wx = wrap_a(mx, g.ax), wy = wrap_a(my, g.ay);
       g.hx[nxt * V + v] = wx;

@@ -20,28 +20,6 @@
 
 namespace cgk {
 
-// 1/d to ~1 ulp: hardware reciprocal approximation r = (1 - e)/d refined by
-// one third-order step r (1 + e + e^2), e = 1 - d r (the geometric series of
-// 1/(1 - e) to e^2; the error left is e^3 plus rounding): 3 FP64 FMAs
-// instead of an IEEE division.
-__device__ __forceinline__ double fast_rcp(double d) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  const double e = fma(-d, r, 1.0);
-  return fma(r, fma(e, e, e), r);
-}
-
-// 1/sqrt(x) for a positive normal x: hardware approximation y refined by one
-// third-order step y (1 + e/2 + 3 e^2/8), e = 1 - x y^2 (the binomial series
-// of (1 - e)^(-1/2) to e^2; the error left is about (5/16) e^3 plus
-// rounding): 5 FP64 operations.
-__device__ __forceinline__ double fast_rsqrt(double x) {
-  double y;
-  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  const double e = fma(-x, y * y, 1.0);
-  return fma(y * e, fma(e, 0.375, 0.5), y);
-}
-
 // One thread per cell.  Writes A, P, force sets fs[a][i] = dE_i/dh_a, and the
 // per-slot Jacobian factors s[a][i] = u_a / det_a and w[a][i].
 //
