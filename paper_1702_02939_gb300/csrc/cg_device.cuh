@@ -139,6 +139,28 @@ __device__ __forceinline__ double unit53(unsigned hi, unsigned lo) {
   return (double)(k + 1ull) * 0x1.0p-53;
 }
 
+// 1/d to ~1 ulp: hardware reciprocal approximation r = (1 - e)/d refined by
+// one third-order step r (1 + e + e^2), e = 1 - d r (the geometric series of
+// 1/(1 - e) to e^2; the error left is e^3 plus rounding): 3 FP64 FMAs
+// instead of an IEEE division.
+__device__ __forceinline__ double fast_rcp(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  const double e = fma(-d, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+}
+
+// 1/sqrt(x) for a positive normal x: hardware approximation y refined by one
+// third-order step y (1 + e/2 + 3 e^2/8), e = 1 - x y^2 (the binomial series
+// of (1 - e)^(-1/2) to e^2; the error left is about (5/16) e^3 plus
+// rounding): 5 FP64 operations.
+__device__ __forceinline__ double fast_rsqrt(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-x, y * y, 1.0);
+  return fma(y * e, fma(e, 0.375, 0.5), y);
+}
+
 // Standard normal for (seed, cell tag, step), cosine branch of Box-Muller,
 // with the table-driven ln and cos(pi .) of dir_math.cuh (tab: the 512-entry
 // director table).
@@ -148,8 +170,11 @@ __device__ __forceinline__ double director_noise(unsigned long long seed, int ta
                                  (unsigned)((unsigned long long)step >> 32), 0u),
                       make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
   double u1 = unit53(r.x, r.y), u2 = unit53(r.z, r.w);
+  // sqrt(x) as x / sqrt(x) (within 2 ulp; u1 = 1 gives x = -0 and R = 0);
   // cos(2 pi u2) as cos(pi t), t = 2 u2 exact
-  return sqrt(-2.0 * dm_log(u1, tab)) * dm_cospi(2.0 * u2, tab);
+  const double x = -2.0 * dm_log(u1, tab);
+  const double R = (__double_as_longlong(x) > 0) ? x * fast_rsqrt(x) : 0.0;
+  return R * dm_cospi(2.0 * u2, tab);
 }
 
 // ----------------------------------------------------------------------------
@@ -343,28 +368,6 @@ __device__ __forceinline__ long long wrap_to_grid(double v, double L, double sca
   if (X < 0) X += LI;
   else if (X >= LI) X -= LI;
   return X;
-}
-
-// 1/d to ~1 ulp: hardware reciprocal approximation r = (1 - e)/d refined by
-// one third-order step r (1 + e + e^2), e = 1 - d r (the geometric series of
-// 1/(1 - e) to e^2; the error left is e^3 plus rounding): 3 FP64 FMAs
-// instead of an IEEE division.
-__device__ __forceinline__ double fast_rcp(double d) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  const double e = fma(-d, r, 1.0);
-  return fma(r, fma(e, e, e), r);
-}
-
-// 1/sqrt(x) for a positive normal x: hardware approximation y refined by one
-// third-order step y (1 + e/2 + 3 e^2/8), e = 1 - x y^2 (the binomial series
-// of (1 - e)^(-1/2) to e^2; the error left is about (5/16) e^3 plus
-// rounding): 5 FP64 operations.
-__device__ __forceinline__ double fast_rsqrt(double x) {
-  double y;
-  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  const double e = fma(-x, y * y, 1.0);
-  return fma(y * e, fma(e, 0.375, 0.5), y);
 }
 
 // Exact int64 -> double for |v| < 2^51: v added to the bit pattern of 1.5 * 2^52
