@@ -54,3 +54,35 @@ def test_workspace_size_is_host_only():
     assert 0 < b1 < b2
     with pytest.raises(cg.CellgbError):
         cg.cg_workspace_bytes([dict(n=4, Lx=2, Ly=2, p0=3.8, v0=0.05)])
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets that
+    a C compiler gives the header's struct of the same name."""
+    import shutil
+    import subprocess
+
+    import paper_1702_02939_gb300 as cg
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [cg.cg_replica, cg.cg_params, cg.cg_launch, cg.cg_avm_params, cg.cg_counters]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "cellgb.h"', "int main(void) {"]
+    for s in structs:
+        name = s.__name__
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in s._fields_:
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                        text=True).stdout.splitlines())
+    for s in structs:
+        name = s.__name__
+        assert int(got[name]) == ctypes.sizeof(s), name
+        for f, _ in s._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(s, f).offset, (name, f)
