@@ -207,7 +207,7 @@ __global__ void k_avm_cells(AvmArgs g) {
   g.A[c] = A;
   g.P[c] = P;
   const double dA = A - g.a0[c], dP = P - g.P0[c];
-  g.ka[c] = 2.0 * g.KA * dA;
+  g.ka[c] = g.KA * dA;  // half of dE/dA = 2 K_A (A - A0): dA/dh carries a 1/2
   g.kp[c] = 2.0 * g.KP * dP;
   if (g.energy) g.energy[c] = g.KA * dA * dA + g.KP * dP * dP;
   if (g.move) {
@@ -265,11 +265,12 @@ __global__ void k_avm_force_move(AvmArgs g) {
     for (int k = 0; k < 3; ++k) {
       const int km = (k + 2) % 3;
       const int c = g.vc[3 * v + k];
-      const double ka = g.ka[c], kp = g.kp[c];
+      const double kh = g.ka[c], kp = g.kp[c];
       const double dx = ux[km] - ux[k], dy = uy[km] - uy[k];
-      // dE_c/dh = ka/2 perp(h_next - h_prev) + kp (t^_in - t^_out), perp(d) = (d_y, -d_x)
-      fx -= 0.5 * ka * dy - kp * (nx[k] + nx[km]);
-      fy -= -0.5 * ka * dx - kp * (ny[k] + ny[km]);
+      // dE_c/dh = kh perp(h_next - h_prev) + kp (t^_in - t^_out), perp(d) = (d_y, -d_x),
+      // kh = K_A (A_c - A0_c); F = -dE/dh accumulated in two FMAs per component
+      fx = fma(-kh, dy, fma(kp, nx[k] + nx[km], fx));
+      fy = fma(kh, dx, fma(kp, ny[k] + ny[km], fy));
       if (g.move) {
         const double2 a = g.act[c];
         ax += a.x;

@@ -259,8 +259,9 @@ struct AvmArgs {
   double KA, KP, mu, dt, noise_amp;
   unsigned long long seed;
   const double2* tab;      // director table (dir_math.cuh)
-  double *A, *P, *ka, *kp, *energy;
-  double2* act;            // [n] v0 n(theta) of the step's directors
+  double *A, *P, *energy;
+  double *ka, *kp;         // [n] K_A (A - A0) and 2 K_P (P - P0) of each cell
+  double2* act;            // [n] (v0/3) n(theta) of the step's directors
   double *Fx, *Fy;
   int move;
   double thr2, t1_len;
