@@ -538,15 +538,19 @@ __device__ __forceinline__ int row_insert(Row& w, int m, int after, int v) {
   return m + 1;
 }
 
-__device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd) {
+__device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd, unsigned long long key) {
   Ctl* ctl = g.ctl;
   const size_t V = (size_t)g.V;
   double* hx = g.hx + ctl->cur * V;
   double* hy = g.hy + ctl->cur * V;
   const int e = 3 * v1 + a;
   const int i = cd.x, j = cd.y, k = cd.z, l = cd.w;
-  // independent loads first: the lists of v1 and of the four cells
-  const int v2 = g.vn[e];
+  // independent loads first: the lists of v1 and of the four cells.  They
+  // run before the lock check, while other flips of the pass edit the
+  // network: a T2 that won a shared cell may have freed v2 (vn = -1), so the
+  // loads take v1 in its place (the flip then loses a lock and returns)
+  const int v2r = g.vn[e];
+  const int v2 = ((unsigned)v2r < (unsigned)g.V) ? v2r : v1;
   const int Aul = g.vn[3 * v1 + (a + 1) % 3], All = g.vn[3 * v1 + (a + 2) % 3];
   const bool distinct = i != j && i != k && i != l && j != k && j != l && k != l;
   Row ri, rk, rj, rl;
@@ -562,6 +566,13 @@ __device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd) {
     c2[t] = g.vc[3 * v2 + t];
   }
   const double x1 = hx[v1], y1 = hy[v1], x2 = hx[v2], y2 = hy[v2];
+  // the four locks, read beside the loads above (all depend only on the
+  // candidate; a flip that holds its locks sees none of that data change in
+  // this pass, and one that does not discards it)
+  if (g.lock[i] != key || g.lock[j] != key || g.lock[k] != key || g.lock[l] != key) {
+    ctl->t1_more = 1;
+    return;
+  }
   int b = -1;
 #pragma unroll
   for (int t = 2; t >= 0; --t)
@@ -745,12 +756,15 @@ __global__ void k_t1_apply(AvmArgs g) {
       const int e = g.cand_e[t];
       const int4 cd = g.cand[t];
       const unsigned long long key = lock_key(stamp, e);
+      if (e < 3 * g.V) {
+        apply_t1(g, e / 3, e % 3, cd, key);  // checks the locks itself
+        continue;
+      }
       if (g.lock[cd.x] != key || g.lock[cd.y] != key || g.lock[cd.z] != key || g.lock[cd.w] != key) {
         ctl->t1_more = 1;
         continue;
       }
-      if (e >= 3 * g.V) apply_t2(g, e - 3 * g.V, cd);
-      else apply_t1(g, e / 3, e % 3, cd);
+      apply_t2(g, e - 3 * g.V, cd);
     }
   }
   if (last_block(g.done + 1) && threadIdx.x == 0) {
