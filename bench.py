@@ -4,10 +4,12 @@
 Workload (Sussman, arXiv 1702.02939, SPV model of Sec. 2.C, fluid regime of
 Fig. 3): N = 262144 cells at unit density in a periodic box L = 512, uniform
 random positions and directors, p0 = 3.85, v0 = 0.1, A0 = K_A = K_P = mu =
-D_r = 1, dt = 0.01, FP64.  Warm-up steps double as equilibration; every timed
-step runs the whole hot path (geometry, force sets, net force, move, exact
-circumcircle test, local repair) and is timed alone with CUDA events, with L2
-flushed in between.
+D_r = 1, dt = 0.01, FP64.  The workload's 100 equilibration steps always run
+first (--warmup adds untimed steps on top); every timed step runs the whole
+hot path (geometry, force sets, net force, move, exact circumcircle test,
+local repair) and is timed alone with CUDA events, with L2 flushed in
+between.  The end-to-end figure replays the same timed steps from the same
+state through the public API with host buffers.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -38,6 +40,9 @@ UNIT = "cell-steps/s"
 WORKLOAD = "spv_fluid_N262144_L512_p0_3.85_v0_0.1_dt0.01_fp64"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FLUSH_BYTES = 256 * 1024 * 1024  # written between timed steps: more than the 126 MB L2
+# The workload runs 100 equilibration steps before its timed steps, whatever
+# the number of warm-up steps asked for.
+EQUIL_STEPS = 100
 
 # Algorithmic FP64 floating-point operations per cell-step of each kernel
 # (fma = 2, add/mul/div/sqrt/rsqrt = 1, transcendental = 1), for the mean ring
@@ -54,8 +59,8 @@ BYTES_PER_CELL_STEP = 84.0
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # Dominant-kernel DRAM traffic per launch (dram__bytes_read.sum +
-# dram__bytes_write.sum) from the committed ncu capture of the current k_geom
-# (profiles/k_geom_spv_N262144.md); set back to None whenever k_geom changes.
+# dram__bytes_write.sum) from one ncu capture of the current k_geom at
+# N = 262144; None whenever the kernel has changed since the capture.
 GEOM_DRAM_BYTES_PER_LAUNCH = 56.95e6
 
 
@@ -71,8 +76,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--batched-steps", type=int, default=40)
-    ap.add_argument("--batched-warmup", type=int, default=50)
+    ap.add_argument("--batched-steps", type=int, default=2000, help="length of the batched run")
+    ap.add_argument("--batched-window", type=int, default=10, help="steps of the per-replica loop timed")
     ap.add_argument("--bwd-steps", type=int, default=1000)
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-avm", action="store_true")
@@ -205,7 +210,8 @@ def host_cpu():
 
 def cpu_baseline(x, y, th, L, seconds):
     """The oracle as it stands: full periodic steps (retriangulation from
-    scratch, forces, update) of the same workload, single thread."""
+    scratch, forces, update) of the same workload from the state the timed
+    region starts from, single thread."""
     import oracle
 
     Lx, Ly, q = oracle.box(L)
@@ -225,9 +231,14 @@ def cpu_baseline(x, y, th, L, seconds):
 
 def batched_comparison(args, device):
     """512 independent replicas (N_r log-uniform on [256, 16384], p0 ~
-    U[3.6, 4.0], v0 ~ U[0.01, 0.5], L_r = sqrt(N_r)): all replicas in one
-    context (one graph launch per step for all of them) versus one context per
-    replica stepped in a loop (one graph launch per replica per step)."""
+    U[3.6, 4.0], v0 ~ U[0.01, 0.5], L_r = sqrt(N_r)), 2000 steps: all
+    replicas in one context (one graph launch per step for all of them)
+    versus one context per replica stepped in a loop (one graph launch per
+    replica per step).  Both arms run the same first EQUIL_STEPS steps
+    untimed; the fused arm then times every step of the rest of the 2000-step
+    run (CUDA events around each step; 2 M cells hold ~2 GB of state, far
+    more than L2) and the loop arm a window of steps right after the
+    equilibration.  fused_over_loop compares the two on that same window."""
     import numpy as np
     import torch
 
@@ -235,6 +246,7 @@ def batched_comparison(args, device):
     import workloads
 
     R = 512
+    total_steps = args.batched_steps
     sizes = workloads.replica_sizes(R, 7)
     p0s, v0s = workloads.replica_params(R, 7)
     reps, xs, ys, ths = [], [], [], []
@@ -244,41 +256,51 @@ def batched_comparison(args, device):
         xs.append(x); ys.append(y); ths.append(th)
     total = int(sizes.sum())
     stream = torch.cuda.current_stream()
-
-    def timed(step_fn, steps):
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            step_fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1)
+    window = args.batched_window
 
     fused = cg.SPV(reps, np.concatenate(xs), np.concatenate(ys), np.concatenate(ths), dt=DT, seed=7,
                    device=device)
-    # equilibration: the random initial state relaxes large forces first
-    fused.step(args.batched_warmup)
+    fused.step(EQUIL_STEPS)
     launch, _ = fused.autotune(5) if not args.no_autotune else (fused.launch, None)
-    ms_f = timed(lambda: fused.step(1), args.batched_steps)
+    timed = total_steps - EQUIL_STEPS
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(timed)]
+    torch.cuda.synchronize()
+    for k in range(timed):
+        ev[k][0].record(stream)
+        fused.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
     fused.sync()
+    per_step = [a.elapsed_time(b) for a, b in ev]
     fused.close()
     del fused
     singles = [cg.SPV([reps[r]], xs[r], ys[r], ths[r], dt=DT, seed=7, device=device) for r in range(R)]
     for sim in singles:
-        sim.step(args.batched_warmup)
-    steps_loop = max(3, args.batched_steps // 4)
-    ms_l = timed(lambda: [sim.step(1) for sim in singles], steps_loop)
+        sim.step(EQUIL_STEPS)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(window):
+        for sim in singles:
+            sim.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_l = e0.elapsed_time(e1)
     for sim in singles:
         sim.sync()
         sim.close()
-    v_f = total * args.batched_steps / (ms_f * 1e-3)
-    v_l = total * steps_loop / (ms_l * 1e-3)
+    ms_fw = sum(per_step[:window])
+    ms_f = sum(per_step)
+    v_fw = total * window / (ms_fw * 1e-3)
+    v_l = total * window / (ms_l * 1e-3)
     return {"workload": "spv_batched_R512_N256-16384_loguniform", "replicas": R, "cells": total,
-            "fused_cell_steps_per_s": v_f, "per_replica_loop_cell_steps_per_s": v_l, "fused_over_loop": v_f / v_l,
-            "fused_ms_per_step": ms_f / args.batched_steps, "loop_ms_per_step": ms_l / steps_loop,
-            "steps": [args.batched_steps, steps_loop], "warmup": args.batched_warmup,
+            "run_steps": total_steps, "equilibration_steps": EQUIL_STEPS,
+            "fused_cell_steps_per_s": total * timed / (ms_f * 1e-3), "fused_ms_per_step": ms_f / timed,
+            "fused_timed_steps": [EQUIL_STEPS + 1, total_steps],
+            "window_steps": [EQUIL_STEPS + 1, EQUIL_STEPS + window],
+            "fused_window_cell_steps_per_s": v_fw, "per_replica_loop_cell_steps_per_s": v_l,
+            "fused_over_loop": v_fw / v_l,
+            "fused_window_ms_per_step": ms_fw / window, "loop_ms_per_step": ms_l / window,
             "fused_launch_shapes": launch}
 
 
@@ -325,9 +347,10 @@ def backward_cost(args, device):
 def fp32_throughput(args, device):
     """The same SPV workload with single-precision physics (cg_params.precision
     = 1: FP32 geometry, forces and director terms; positions on the exact grid
-    and exact topology): 100 FP64 warm-up steps (the random initial state's
-    largest forces overflow FP32), 10 FP32 steps, autotuned launch shapes, then
-    each graph step timed alone with CUDA events, L2 flushed in between."""
+    and exact topology): the 100 equilibration steps (and any extra warm-up)
+    in FP64 (the random initial state's largest forces overflow FP32), 10 FP32
+    steps, autotuned launch shapes, then each graph step timed alone with
+    CUDA events, L2 flushed in between."""
     import torch
 
     import paper_1702_02939_gb300 as cg
@@ -336,13 +359,13 @@ def fp32_throughput(args, device):
     # overflow FP32; it is relaxed with FP64 steps first
     x, y, th, L = workload(args.n, 1)
     relax = cg.SPV([dict(n=args.n, Lx=L, Ly=L, p0=P0, v0=V0)], x, y, th, dt=DT, seed=1, device=device)
-    relax.step(args.warmup)
+    relax.step(EQUIL_STEPS + args.warmup)
     x, y, th = relax.state()
     relax.close()
     del relax
     sim = cg.SPV([dict(n=args.n, Lx=L, Ly=L, p0=P0, v0=V0)], x, y, th, dt=DT, seed=1, precision="f32",
                  device=device)
-    sim.set_step(args.warmup)
+    sim.set_step(EQUIL_STEPS + args.warmup)
     sim.step(10)
     sim.sync()
     launch, _ = sim.autotune(10, flush_bytes=FLUSH_BYTES) if not args.no_autotune else (sim.launch, None)
@@ -362,7 +385,8 @@ def fp32_throughput(args, device):
     ph = sim.profile(20)
     sim.close()
     return {"workload": WORKLOAD.replace("fp64", "fp32"), "unit": UNIT, "dtype": "f32 physics, int64 grid, exact topology",
-            "cell_steps_per_s": args.n / (ms * 1e-3), "ms_per_step": ms, "steps": K, "warmup": args.warmup,
+            "cell_steps_per_s": args.n / (ms * 1e-3), "ms_per_step": ms, "steps": K,
+            "equilibration_steps": EQUIL_STEPS + args.warmup,
             "launch_shapes": launch, "phase_ms_per_step": {k: v / 20 for k, v in ph.items()}}
 
 
@@ -377,7 +401,7 @@ def avm_roofline(n, ph, prof_steps):
     achieved = flops / (ms * 1e-3) / 1e12
     return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "note": "FP64 pipe 78-80% busy (profiles/avm_step_N65536.md): sqrt, sincos, log, cos count one flop "
+            "note": "FP64 pipe 78-80% busy under ncu: sqrt, sincos, log, cos count one flop "
                     "each but take many FP64 instructions"}
 
 
@@ -721,17 +745,22 @@ def run_ours(args):
                  repair_cap=repair_cap, device=f"cuda:{local}")
     stream = torch.cuda.current_stream()
     advance = sim.profile if args.eager else sim.step
-    # warm-up = equilibration steps; then the launch shapes are tuned on a
-    # temporary copy of the equilibrated state (the simulation takes no step)
+    # the workload's equilibration, then the extra warm-up steps asked for;
+    # then the launch shapes are tuned on a temporary copy of the state (the
+    # simulation itself takes no step)
+    advance(EQUIL_STEPS)
     advance(args.warmup)
     sim.sync()
     # tuned under the timing conditions of the timed region (L2 evicted before each step)
     launch, tune_ms = (sim.autotune(10, flush_bytes=FLUSH_BYTES) if not args.no_autotune else (sim.launch, None))
+    # the state the timed region starts from: the end-to-end run replays the same steps from it
+    x0, y0, th0 = sim.state()
+    step0 = sim.counters()["steps"]
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
-    loops0 = sim.counters()["loop_total"]
+    c_start = sim.counters()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -750,6 +779,14 @@ def run_ours(args):
     ms = max_over_ranks(sum(ev_s[k].elapsed_time(ev_e[k]) for k in range(args.steps)), world, "cuda")
     counters = sim.counters()
     value = weak_scaling_value(world, args.n, args.steps, ms)
+    Kd = max(args.steps, 1)
+    timed_state = {
+        "equilibration_steps": EQUIL_STEPS, "extra_warmup_steps": args.warmup,
+        "first_timed_step": step0 + 1, "last_timed_step": counters["steps"],
+        "flagged_cells_per_step": (counters["flagged_total"] - c_start["flagged_total"]) / Kd,
+        "repaired_cells_per_step": (counters["repaired_total"] - c_start["repaired_total"]) / Kd,
+        "repair_rounds_per_step": (counters["loop_total"] - c_start["loop_total"]) / Kd,
+        "last_flagged": counters["last_flagged"]}
 
     # per-kernel device times (eager launches, CUDA events on the same stream)
     prof_steps = max(1, args.avm_profile_steps)
@@ -768,27 +805,51 @@ def run_ours(args):
            "frac": BYTES_PER_CELL_STEP * args.n / step_s / 1e9 / hbm_gbs, "source": hbm_src,
            "bytes_per_cell_step": BYTES_PER_CELL_STEP}
 
-    # end to end through the public API with pinned host buffers: every step
-    # uploads that step's per-cell v0 and reads back the positions
+    # end to end through the public API with pinned host buffers, over the
+    # same steps from the same state as the timed region: every step uploads
+    # that step's per-cell v0 and reads back the positions.  Each step is one
+    # cg_run_io call after the same L2 flush as the timed region (host clock,
+    # flush excluded); the pipelined figure runs the steps in one call, the
+    # copies of one step overlapping the kernels of the next (L2 not flushed).
     e2e = None
     if not args.no_e2e:
         hv0 = torch.full((args.n,), V0, dtype=torch.float64).pin_memory()
         hx = torch.empty(args.n, dtype=torch.float64).pin_memory()
         hy = torch.empty(args.n, dtype=torch.float64).pin_memory()
+
+        def restore():
+            sim.set_state(x0, y0, th0)
+            sim.set_step(step0)
+            sim.sync()
+
+        restore()
+        el = 0.0
+        for k in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.run_io(1, v0=hv0, x=hx, y=hy)
+            el += time.perf_counter() - t0
+        el = max_over_ranks(el, world, "cuda")
+        same = sim.counters()["steps"] == counters["steps"]
+        restore()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        # every step uploads its v0 and downloads its positions (strides 0:
-        # the same pinned buffers each step); the copies overlap the kernels
-        sim.run_io(args.e2e_steps, v0=hv0, x=hx, y=hy)
-        el = max_over_ranks(time.perf_counter() - t0, world, "cuda")
-        e2e = {"value": weak_scaling_value(world, args.n, args.e2e_steps, 1e3 * el), "unit": UNIT,
+        sim.run_io(args.steps, v0=hv0, x=hx, y=hy)
+        elp = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+        e2e = {"value": weak_scaling_value(world, args.n, args.steps, 1e3 * el), "unit": UNIT,
                "h2d_bytes_per_step": 8 * args.n, "d2h_bytes_per_step": 16 * args.n,
-               "api": "cg_run_io: per-step v0 upload and position download on copy streams, overlapped "
-                      "with the step kernels", "steps": args.e2e_steps}
+               "api": "cg_run_io, one call per step (v0 uploaded from pinned host memory, positions downloaded "
+                      "to pinned host memory), host clock",
+               "steps": args.steps, "same_steps_as_timed_region": bool(same),
+               "l2": "flushed before every step, as the timed region (flush not timed)",
+               "pipelined": {"value": weak_scaling_value(world, args.n, args.steps, 1e3 * elp), "unit": UNIT,
+                             "api": "cg_run_io, all steps in one call: copies on two copy streams overlap the "
+                                    "kernels of neighbouring steps", "l2": "not flushed"}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(x, y, th, L, args.cpu_seconds)
+        cpu = cpu_baseline(x0.cpu().numpy(), y0.cpu().numpy(), th0.cpu().numpy(), L, args.cpu_seconds)
     sim.close()
     batched = None
     if rank == 0 and world == 1 and not args.no_batched:
@@ -808,12 +869,14 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n_cells": args.n, "box": L, "p0": P0, "v0": V0, "dt": DT,
+                           "equilibration_steps": EQUIL_STEPS,
                            "replicas_per_gpu": 1, "l2": "flushed between timed steps (256 MB write)",
                            "repair_cap": repair_cap, "launch": "eager" if args.eager else "graph",
                            "launch_shapes": launch, "autotune_ms_per_step": tune_ms},
                 "clocks": clk, "e2e": e2e,
                 "gpu_launches": (kernels_launched(args.steps, args.steps * repair_cap, eager=True) if args.eager
-                                 else kernels_launched(args.steps, counters["loop_total"] - loops0)),
+                                 else kernels_launched(args.steps, counters["loop_total"] - c_start["loop_total"])),
+                "timed_state": timed_state,
                 "roofline": roofline, "hbm_roofline": hbm, "cpu_baseline": cpu,
                 "phase_ms_per_step": {k: v / prof_steps for k, v in ph.items()},
                 "counters": counters, "batched": batched, "backward": backward, "avm": avm, "fp32": fp32}

@@ -265,9 +265,11 @@ int cg_autotune(cg_ctx* ctx, int32_t steps_per_trial, size_t flush_bytes, void* 
  * The paper has no counterpart: this is a deployment variant of the
  * from-scratch triangulation that cg_create performs.
  *   n, Lx, Ly   : 16 <= n <= CG_NOALLOC_MAX_CELLS cells in a periodic box;
- *                 n > CG_NOALLOC_MAX_CELLS (or a box needing more than
- *                 2*CG_NOALLOC_MAX_CELLS cell-list bins) returns CG_EINVAL.
- *   d_x, d_y    : device, n doubles each, positions in [-L, 2L).
+ *                 any other n, or a box needing more than
+ *                 4*CG_NOALLOC_MAX_CELLS cell-list bins (a very elongated
+ *                 box), returns CG_EINVAL before any GPU work.
+ *   d_x, d_y    : device, n doubles each, positions in [-L, 2L); a position
+ *                 outside that range returns CG_EINVAL.
  *   d_cnt, d_nbr: device outputs, n and n*CG_MAX_RING int32: the Delaunay
  *                 neighbours of every cell exactly as cg_get_neighbors()
  *                 returns them for the same positions.
@@ -276,8 +278,10 @@ int cg_autotune(cg_ctx* ctx, int32_t steps_per_trial, size_t flush_bytes, void* 
  * by every GPU that loads the library until the process exits); the call
  * makes no device allocation.  All calls share that array: calls whose GPU
  * work overlaps race.  The first call on each device looks the array's address
- * up and should come before any stream capture.  Returns CG_OK or a status
- * code (the outputs are undefined on error). */
+ * up and should come before any stream capture.  That address is kept for the
+ * life of the process: after a cudaDeviceReset() of a device, do not call
+ * this function on that device again.  Returns CG_OK or a status code (the
+ * outputs are undefined on error). */
 #define CG_NOALLOC_MAX_CELLS 16384
 int cg_triangulate_noalloc(int32_t n, double Lx, double Ly, const double* d_x, const double* d_y,
                            int32_t* d_cnt, int32_t* d_nbr, void* stream);

@@ -49,6 +49,8 @@ def _declare(L):
                              _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.cgo_integrate.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
                                 C.c_uint64, C.c_int64]
+    L.cgo_integrate_tagged.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                       C.c_uint64, C.c_int64, C.c_int64]
     L.cgo_spv_run.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp,
                               C.c_uint64, C.c_int64, C.c_int64, _dp, _dp, _dp, _dp]
     L.cgo_spv_window_step.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp, _dp,
@@ -57,7 +59,7 @@ def _declare(L):
     L.cgo_spv_window_step.restype = C.c_int
     for name in ("cgo_snap_positions", "cgo_orient2d", "cgo_incircle", "cgo_incircle_sos",
                  "cgo_delaunay_plain", "cgo_triangulate", "cgo_geometry", "cgo_forces",
-                 "cgo_integrate", "cgo_spv_run"):
+                 "cgo_integrate", "cgo_integrate_tagged", "cgo_spv_run"):
         getattr(L, name).restype = C.c_int
     L.cgo_avm_build.argtypes = [C.c_int, C.c_double, C.c_double, _dp, _dp, _dp, _dp, _ip, _ip, _ip, _ip]
     L.cgo_avm_forces.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, _ip, _ip, _ip, _ip, _dp, _dp,
@@ -211,7 +213,10 @@ def energy(x, y, Lx, Ly, topo, p0, A0=1.0, KA=1.0, KP=1.0):
     return forces(x, y, Lx, Ly, topo, p0, A0, KA, KP)[4]
 
 
-def integrate(x, y, theta, Fx, Fy, Lx, Ly, v0, mu, Dr, dt, seed, step):
+def integrate(x, y, theta, Fx, Fy, Lx, Ly, v0, mu, Dr, dt, seed, step, tag0=0):
+    """Eq. 3 for one step from the given forces; the director noise of cell i
+    is drawn with counter tag0 + i (tag0 > 0: a system whose cells follow
+    others in a larger numbering, as a replica in a batch)."""
     n = len(x)
     x = np.array(x, np.float64, copy=True)
     y = np.array(y, np.float64, copy=True)
@@ -220,8 +225,8 @@ def integrate(x, y, theta, Fx, Fy, Lx, Ly, v0, mu, Dr, dt, seed, step):
     Fy = np.ascontiguousarray(Fy, dtype=np.float64)
     v0 = np.ascontiguousarray(np.broadcast_to(np.asarray(v0, np.float64), (n,)))
     par = np.array([mu, Dr, dt], np.float64)
-    _check(lib().cgo_integrate(n, Lx, Ly, _d(x), _d(y), _d(theta), _d(Fx), _d(Fy), _d(v0),
-                               _d(par), int(seed), int(step)), "integrate")
+    _check(lib().cgo_integrate_tagged(n, Lx, Ly, _d(x), _d(y), _d(theta), _d(Fx), _d(Fy), _d(v0),
+                                      _d(par), int(seed), int(step), int(tag0)), "integrate")
     return x, y, theta
 
 

@@ -13,7 +13,9 @@ LIB = os.path.join(HERE, "libcgo.so")
 
 def build(force: bool = False) -> str:
     srcs = [os.path.join(HERE, s) for s in SOURCES if os.path.exists(os.path.join(HERE, s))]
-    deps = srcs + [os.path.join(HERE, "internal.h")]
+    # every header of the oracle (internal.h, spv_core.h, ...) is a dependency
+    hdrs = sorted(os.path.join(HERE, h) for h in os.listdir(HERE) if h.endswith(".h"))
+    deps = srcs + hdrs
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in deps):

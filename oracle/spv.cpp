@@ -204,9 +204,12 @@ int cgo_forces(int n, double Lx, double Ly, const double* x, const double* y, co
 
 // One Euler-Maruyama update (Eq. 3) from given forces; positions snapped/wrapped.
 // par = {mu, Dr, dt}
-int cgo_integrate(int n, double Lx, double Ly, double* x, double* y, double* theta,
-                  const double* Fx, const double* Fy, const double* v0, const double* par,
-                  uint64_t seed, int64_t step) {
+// The same update for cells whose noise counters are tag0 + i: the cells of
+// one system placed from index tag0 on in a larger numbering (the tag is the
+// cell's index in the Philox counter of the director noise).
+int cgo_integrate_tagged(int n, double Lx, double Ly, double* x, double* y, double* theta,
+                         const double* Fx, const double* Fy, const double* v0, const double* par,
+                         uint64_t seed, int64_t step, int64_t tag0) {
   int q = grid_exponent(Lx, Ly);
   double mu = par[0], Dr = par[1], dt = par[2];
   double s = std::sqrt(2.0 * Dr * dt);
@@ -215,9 +218,15 @@ int cgo_integrate(int n, double Lx, double Ly, double* x, double* y, double* the
     double vy = mu * Fy[i] + v0[i] * std::sin(theta[i]);
     double xn = x[i] + dt * vx, yn = y[i] + dt * vy;
     if (!snap_wrap_ok(xn, Lx, q, x[i]) || !snap_wrap_ok(yn, Ly, q, y[i])) return -6;  // non-finite move
-    theta[i] = theta[i] + s * director_noise(seed, i, step);
+    theta[i] = theta[i] + s * director_noise(seed, (int)(tag0 + i), step);
   }
   return 0;
+}
+
+int cgo_integrate(int n, double Lx, double Ly, double* x, double* y, double* theta,
+                  const double* Fx, const double* Fy, const double* v0, const double* par,
+                  uint64_t seed, int64_t step) {
+  return cgo_integrate_tagged(n, Lx, Ly, x, y, theta, Fx, Fy, v0, par, seed, step, 0);
 }
 
 // nsteps full oracle steps: triangulate from scratch, forces, update.

@@ -17,7 +17,8 @@
 //    different host threads on one device) race on the array;
 //  * the first call on a device looks up the array's device address with
 //    cudaGetSymbolAddress and caches it; that first call should therefore
-//    come before any stream capture;
+//    come before any stream capture, and a cudaDeviceReset() of the device
+//    (which reloads the module elsewhere) ends the use of this function on it;
 //  * no cudaMalloc, cudaFree or allocating library routine is called.
 #include "../../include/cellgb.h"
 #include "cg_device.cuh"
@@ -227,8 +228,9 @@ extern "C" int cg_triangulate_noalloc(int32_t n, double Lx, double Ly, const dou
 
   launch_gather_ring(n, tag, cnt, nbr, d_cnt, d_nbr, st);
   if (cudaGetLastError() != cudaSuccess) return CG_ECUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return CG_ECUDA;
+  // the status word read on the caller's stream, behind the kernels above
   int status = 0;
-  if (cudaMemcpy(&status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CG_ECUDA;
+  if (cudaMemcpyAsync(&status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return CG_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return CG_ECUDA;
   return status;
 }

@@ -240,10 +240,13 @@ def test_batched_replicas_match_per_replica_oracle():
         scale = max(np.abs(oFx).max(), np.abs(oFy).max())
         assert np.abs(Fx[sl] - oFx).max() <= F_TOL * scale
         assert np.abs(Fy[sl] - oFy).max() <= F_TOL * scale
-        # noise counters use the global cell index of the concatenated system
+        # noise counters use the global cell index of the concatenated
+        # system: replica k's cells are tags off ... off + n - 1
         ox, oy, oth = oracle.integrate(xs_all[k], ys_all[k], th_all[k], oFx, oFy, Lx, Ly, v0, 1.0, 1.0, 0.01,
-                                       9, 0)
+                                       9, 0, tag0=off)
         assert np.abs(wrapdiff(gx[sl], ox, Lx)).max() <= X_TOL * Lx
+        assert np.abs(wrapdiff(gy[sl], oy, Ly)).max() <= X_TOL * Ly
+        np.testing.assert_allclose(gth[sl], oth, rtol=0, atol=1e-12)
         off += n
     sim.close()
 

@@ -141,6 +141,22 @@ def test_single_step_update_formula():
     np.testing.assert_allclose(th1, th + math.sqrt(2 * 1.0 * 0.01) * xi, rtol=0, atol=1e-15)
 
 
+def test_update_with_a_tag_offset():
+    """Eq. 3 for a system whose cells carry noise counters tag0 + i (a
+    replica placed after others in a batch): positions as without the offset,
+    directors rotated by the noise of counters tag0 + i."""
+    x, y, th, Lx, Ly = state(64, 7)
+    topo = oracle.triangulate(x, y, Lx, Ly)
+    Fx, Fy, *_ = oracle.forces(x, y, Lx, Ly, topo, 3.8)
+    x0, y0, th0 = oracle.integrate(x, y, th, Fx, Fy, Lx, Ly, 0.1, 1.0, 1.0, 0.01, 5, 3)
+    x1, y1, th1 = oracle.integrate(x, y, th, Fx, Fy, Lx, Ly, 0.1, 1.0, 1.0, 0.01, 5, 3, tag0=1000)
+    np.testing.assert_array_equal(x1, x0)
+    np.testing.assert_array_equal(y1, y0)
+    xi = np.array([oracle.director_noise(5, 1000 + i, 3) for i in range(64)])
+    np.testing.assert_allclose(th1, th + math.sqrt(2 * 1.0 * 0.01) * xi, rtol=0, atol=1e-15)
+    assert np.abs(th1 - th0).max() > 1e-3
+
+
 def test_window_step_equals_full_step():
     """The spatial-window step used to time bounded samples of a large
     workload reproduces the full periodic step exactly for its interior cells."""
