@@ -108,7 +108,8 @@ typedef struct cg_counters {
 typedef struct cg_launch {
   int32_t repair_blocks_per_sm;  /* repair-round grid = SMs x this (1..64, default 4) */
   int32_t check_blocks_per_sm;   /* consistency-check grid = SMs x this (1..64, default 4) */
-  int32_t dir_blocks_per_sm;     /* director branch grid = SMs x this; 0 = one thread per cell (default 2) */
+  int32_t dir_blocks_per_sm;     /* director branch grid = SMs x this; 0 = one thread per cell
+                                    (default 4 in FP64, 2 in FP32) */
   int32_t dir_low_priority;      /* 1: the low-priority branch (directors, next geometry) at the lowest
                                     stream priority, the rest at the highest (default 1) */
   int32_t geom_blocks_per_sm;    /* grid of the geometry pass beside the repair rounds = SMs x this;
@@ -117,7 +118,12 @@ typedef struct cg_launch {
                                     grid-stride loop over cells; 0 = one thread per cell */
   int32_t dir_beside_geom;       /* 1: the director terms on a branch of their own, beside the
                                     geometry pass (both FP64; one fills the other's idle FP64
-                                    cycles); 0: before it on the same branch (default 0) */
+                                    cycles); 0: before it on the same branch (default 1 in FP64,
+                                    0 in FP32) */
+  int32_t ring_order;            /* bit 0: the geometry pass, bit 1: the force pass takes the cells
+                                    regrouped by ring size within chunks of 1024 cells, so that the
+                                    lanes of a warp run the same number of ring slots (default 1 in
+                                    FP64, 0 in FP32) */
 } cg_launch;
 
 /* Workspace size for R replicas. */
@@ -217,6 +223,44 @@ int cg_backward_bytes(const cg_ctx* ctx, int64_t nsteps, int32_t ckpt_every, siz
 int cg_set_moduli(cg_ctx* ctx, double KA, double KP);
 /* Sets the Philox step counter (the noise of the next step uses it). */
 int cg_set_step(cg_ctx* ctx, int64_t step);
+
+/* ------------------------------------------------------------------------
+ * Domain decomposition of one large periodic system (Sec. 4 of the paper
+ * names it as the way to larger systems; forces reach the next-nearest
+ * neighbours, App. A.2 after Eq. A7, so a domain needs a halo of cells around
+ * the cells it owns).  A domain is a context of one replica whose box is a
+ * frame of the larger box (a strip plus its halo); the host owns the
+ * partition, the exchange and the migration of cells between domains.  With
+ * the calls below a domain's own cells evolve exactly (bit for bit) as in the
+ * undivided system, provided its cells are passed in increasing global index
+ * (the order that breaks ties and starts rings) and its halo is wide enough.
+ * ------------------------------------------------------------------------ */
+/* Noise counters of the cells: ids (host or device, n int32 >= 0, user order)
+ * replace the user index as the cell's Philox counter of Eq. 3's director
+ * noise (a domain passes its cells' indices in the undivided system).
+ * Recomputes the pending move.  Synchronizes. */
+int cg_set_noise_ids(cg_ctx* ctx, const int32_t* ids);
+/* Makes replica's box (Lx, Ly of cg_create) the frame with origin (x0, y0) of
+ * a larger periodic box (Lx_outer, Ly_outer): positions stay in frame
+ * coordinates, and the move of Eq. 3 is formed and rounded in the larger
+ * box's coordinates (x0 + x, reduced into [0, Lx_outer)), as the undivided
+ * system rounds it.  The larger box must have the same position grid
+ * (ceil(log2(max side)) equal), the origin must be a grid point inside it
+ * and the frame must fit in it; otherwise CG_EINVAL.  A cell whose move
+ * leaves the frame is wrapped into it (only halo cells can; their positions
+ * are replaced by the halo exchange).  Recomputes the pending move.
+ * Synchronizes. */
+int cg_set_frame(cg_ctx* ctx, int32_t replica, double x0, double y0, double Lx_outer, double Ly_outer);
+/* Halo exchange, asynchronous on the context's stream.  The values exchanged
+ * are the pending positions (where the next step starts) as int64 grid
+ * coordinates (units of 2^-q) of the larger box of a framed replica (of the
+ * replica's own box otherwise).  d_slot: device, n int32 in user order, the
+ * cell's place in the message or -1.  cg_halo_pack writes the listed cells to
+ * d_out[2 slot], d_out[2 slot + 1]; cg_halo_unpack replaces the listed cells'
+ * pending positions with d_in[2 slot], d_in[2 slot + 1] (a value outside the
+ * frame sets the device status to CG_EINVAL and leaves the cell unchanged). */
+int cg_halo_pack(cg_ctx* ctx, const int32_t* d_slot, int64_t* d_out);
+int cg_halo_unpack(cg_ctx* ctx, const int32_t* d_slot, const int64_t* d_in);
 /* nsteps steps from the current state, saving checkpoints into d_bw
  * (device, >= cg_backward_bytes, 256-byte aligned).  Synchronizes. */
 int cg_run_checkpointed(cg_ctx* ctx, int64_t nsteps, int32_t ckpt_every, void* d_bw, size_t bytes);

@@ -48,7 +48,7 @@ class cg_launch(C.Structure):
     _fields_ = [("repair_blocks_per_sm", C.c_int32), ("check_blocks_per_sm", C.c_int32),
                 ("dir_blocks_per_sm", C.c_int32), ("dir_low_priority", C.c_int32),
                 ("geom_blocks_per_sm", C.c_int32), ("test_blocks_per_sm", C.c_int32),
-                ("dir_beside_geom", C.c_int32)]
+                ("dir_beside_geom", C.c_int32), ("ring_order", C.c_int32)]
 
 
 class cg_avm_params(C.Structure):
@@ -97,6 +97,12 @@ def lib():
         L.cg_hvp.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, C.c_size_t]
         for name in ("cg_backward_bytes", "cg_set_moduli", "cg_set_step", "cg_run_checkpointed", "cg_backward",
                      "cg_hvp"):
+            getattr(L, name).restype = C.c_int
+        L.cg_set_noise_ids.argtypes = [vp, vp]
+        L.cg_set_frame.argtypes = [vp, i32, C.c_double, C.c_double, C.c_double, C.c_double]
+        L.cg_halo_pack.argtypes = [vp, vp, vp]
+        L.cg_halo_unpack.argtypes = [vp, vp, vp]
+        for name in ("cg_set_noise_ids", "cg_set_frame", "cg_halo_pack", "cg_halo_unpack"):
             getattr(L, name).restype = C.c_int
         L.cg_triangulate_noalloc.argtypes = [i32, C.c_double, C.c_double, vp, vp, vp, vp, vp]
         L.cg_triangulate_noalloc.restype = C.c_int
@@ -266,6 +272,22 @@ def cg_set_step(ctx, step):
     _check(lib().cg_set_step(ctx, int(step)), ctx)
 
 
+def cg_set_noise_ids(ctx, ids):
+    _check(lib().cg_set_noise_ids(ctx, _ptr(ids)), ctx)
+
+
+def cg_set_frame(ctx, replica, x0, y0, Lx_outer, Ly_outer):
+    _check(lib().cg_set_frame(ctx, int(replica), float(x0), float(y0), float(Lx_outer), float(Ly_outer)), ctx)
+
+
+def cg_halo_pack(ctx, slot, out):
+    _check(lib().cg_halo_pack(ctx, _ptr(slot), _ptr(out)), ctx)
+
+
+def cg_halo_unpack(ctx, slot, inp):
+    _check(lib().cg_halo_unpack(ctx, _ptr(slot), _ptr(inp)), ctx)
+
+
 def cg_run_checkpointed(ctx, nsteps, ckpt_every, bw):
     _check(lib().cg_run_checkpointed(ctx, int(nsteps), int(ckpt_every), _ptr(bw), bw.numel()), ctx)
 
@@ -330,6 +352,46 @@ def cg_destroy(ctx):
 # ---------------------------------------------------------------------------
 # Convenience object
 # ---------------------------------------------------------------------------
+# ---------------------------------------------------------------------------
+# Persisted launch shapes: the autotuner's choice per GPU model and problem
+# class, so that a run can reuse a tuning instead of repeating it.
+# ---------------------------------------------------------------------------
+LAUNCH_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "launch_cache.json")
+
+
+def launch_cache_key(gpu_name, n, replicas, precision, flush_bytes):
+    """GPU model | precision | replica count bucket | cell count bucket (the
+    nearest power of two) | whether the L2 is evicted before each step."""
+    import math
+
+    name = str(gpu_name).replace("|", "/")
+    rb = 1 if replicas <= 1 else 2 ** int(round(math.log2(replicas)))
+    nb = 2 ** int(round(math.log2(max(int(n), 1))))
+    return f"{name}|{'f32' if precision == 1 else 'f64'}|R~{rb}|N~{nb}|l2{'cold' if flush_bytes else 'warm'}"
+
+
+def _read_launch_cache(path):
+    import json
+
+    try:
+        with open(path) as f:
+            data = json.load(f)
+        return data if isinstance(data, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def _write_launch_cache(path, key, launch):
+    import json
+
+    data = _read_launch_cache(path)
+    data[key] = {k: int(v) for k, v in launch.items()}
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 class SPV:
     """One or more independent periodic SPV systems advanced together.
 
@@ -438,14 +500,30 @@ class SPV:
         cur.update(launch)
         cg_set_launch(self.ctx, cur)
 
-    def autotune(self, steps_per_trial=10, flush_bytes=0):
+    def autotune(self, steps_per_trial=10, flush_bytes=0, cache=None):
         """Times candidate launch shapes on a temporary copy of the current
         state and keeps the fastest; the simulation itself takes no step.
-        flush_bytes > 0 times every step after an L2-evicting write."""
+        flush_bytes > 0 times every step after an L2-evicting write.
+
+        cache: path of a JSON file of tuned shapes (see `launch_cache_key`).
+        A stored entry for this GPU and problem class is applied without
+        timing (ms is then None); otherwise the tuned shapes are stored.
+        Launch shapes change timing only, never results."""
+        key = None
+        if cache is not None:
+            key = launch_cache_key(self.torch.cuda.get_device_name(self.device), self.n, len(self.replicas),
+                                   self.params.precision, flush_bytes)
+            hit = _read_launch_cache(cache).get(key)
+            if hit is not None:
+                known = {f for f, _ in cg_launch._fields_}
+                self.set_launch(**{k: v for k, v in hit.items() if k in known})
+                return self.launch, None
         t = self.torch
         scratch = t.empty(cg_autotune_bytes(self.ctx, flush_bytes), dtype=t.uint8, device=self.device)
         best, ms = cg_autotune(self.ctx, steps_per_trial, flush_bytes, scratch)
         del scratch
+        if key is not None:
+            _write_launch_cache(cache, key, best)
         return best, ms
 
     def set_moduli(self, KA, KP):
@@ -453,6 +531,29 @@ class SPV:
 
     def set_step(self, step):
         cg_set_step(self.ctx, step)
+
+    def set_noise_ids(self, ids):
+        """Philox counters of the cells' director noise (user order), in place
+        of their user indices."""
+        t = self.torch
+        ids = t.as_tensor(ids, dtype=t.int32).contiguous()
+        cg_set_noise_ids(self.ctx, ids)
+
+    def set_frame(self, x0, y0, Lx_outer, Ly_outer, replica=0):
+        """Makes the replica's box the frame at (x0, y0) of a larger periodic
+        box: moves are rounded in the larger box's coordinates."""
+        cg_set_frame(self.ctx, replica, x0, y0, Lx_outer, Ly_outer)
+
+    def halo_pack(self, slot, out):
+        """Pending positions (int64 grid coordinates of the larger box) of the
+        cells with slot[u] >= 0 into out[2 slot:2 slot + 2] (device tensors;
+        asynchronous on the context's stream)."""
+        cg_halo_pack(self.ctx, slot, out)
+
+    def halo_unpack(self, slot, inp):
+        """Replaces the pending positions of the cells with slot[u] >= 0 by
+        inp[2 slot:2 slot + 2] (device tensors; asynchronous)."""
+        cg_halo_unpack(self.ctx, slot, inp)
 
     def _bwd_buffer(self, nsteps, ckpt_every):
         nbytes = cg_backward_bytes(self.ctx, nsteps, ckpt_every)

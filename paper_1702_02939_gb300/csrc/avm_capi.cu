@@ -26,10 +26,10 @@ struct Lay {
 
 struct AvmOff {
   size_t spv, spv_bytes;
-  size_t hx, hy, hf, vc, vn, cc, cv, theta, p0, v0, a0, P0, A, P, ka, kp, energy, act, Fx, Fy, lock, cand_e, cand,
+  size_t hx, hy, hf, vc, vn, cc, cv, theta, thn, p0, v0, a0, P0, A, P, ka, kp, energy, act, Fx, Fy, lock, cand_e, cand,
       done;
   size_t owned, base_local, base_partial, xs, ys, cnt, nbr, scalar, ctl, dir_tab;
-  size_t div_cells, div_dirs, div_made, div_cslots, div_vslots;  // staging of cg_avm_divide
+  size_t div_cells, div_dirs, div_made, div_cslots, div_vslots, div_lock;  // staging of cg_avm_divide
   size_t total;
 };
 
@@ -48,6 +48,7 @@ AvmOff avm_layout(int64_t n, size_t spv_bytes) {
   o.cc = L.take(n * i4);
   o.cv = L.take(n * CG_RING * i4);
   o.theta = L.take(n * d);
+  o.thn = L.take(n * d);
   o.p0 = L.take(n * d);
   o.v0 = L.take(n * d);
   o.a0 = L.take(n * d);
@@ -79,6 +80,7 @@ AvmOff avm_layout(int64_t n, size_t spv_bytes) {
   o.div_made = L.take(n * i4);
   o.div_cslots = L.take(n * i4);
   o.div_vslots = L.take(2 * n * i4);
+  o.div_lock = L.take(n * sizeof(unsigned long long));
   o.total = L.total;
   return o;
 }
@@ -93,6 +95,8 @@ struct cg_avm_ctx {
   char* ws = nullptr;
   AvmOff off{};
   cudaStream_t stream = nullptr, capture = nullptr;
+  cudaStream_t side = nullptr;                     // the director branch of the step graph
+  cudaEvent_t fork = nullptr, join = nullptr;
   cudaGraphExec_t exec = nullptr;     // one step
   cudaGraphExec_t t1_exec = nullptr;  // T1 passes alone
   int sms = 0;
@@ -180,6 +184,7 @@ AvmArgs avm_args(cg_avm_ctx* c) {
   a.kp = c->at<double>(c->off.kp);
   a.energy = nullptr;
   a.act = c->at<double2>(c->off.act);
+  a.thn = c->at<double>(c->off.thn);
   a.Fx = c->at<double>(c->off.Fx);
   a.Fy = c->at<double>(c->off.Fy);
   a.move = 1;
@@ -212,8 +217,8 @@ int avm_status(cg_avm_ctx* c) {
 // A graph of `prefix` (captured) followed by a while node whose body is one
 // T1 pass (the pass's first kernel clears the handle, its closing block sets
 // it again when another pass is due).
-template <class Prefix>
-int loop_graph(cg_avm_ctx* c, Prefix prefix, cudaGraphExec_t* out) {
+template <class Prefix, class Suffix>
+int loop_graph(cg_avm_ctx* c, Prefix prefix, Suffix suffix, cudaGraphExec_t* out) {
   if (*out) {
     cudaGraphExecDestroy(*out);
     *out = nullptr;
@@ -229,7 +234,7 @@ int loop_graph(cg_avm_ctx* c, Prefix prefix, cudaGraphExec_t* out) {
         a.loop = h;
         launch_avm_t1_pass(a, st);
       },
-      [](cudaStream_t) {}, out);
+      suffix, out);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return afail(c, CG_ECUDA, std::string("building the T1 loop graph: ") + cudaGetErrorString(e));
@@ -240,13 +245,20 @@ int loop_graph(cg_avm_ctx* c, Prefix prefix, cudaGraphExec_t* out) {
 // The first T1 pass of a step runs as plain graph nodes before the while
 // node (every step has one); the node then runs only the further passes.
 int avm_graphs(cg_avm_ctx* c) {
+  // the step: geometry, vertex forces and move; then the T1 passes beside the
+  // director terms of the next step (FP64 work on a branch of its own, joined
+  // at the end of the step)
   int rc = loop_graph(
       c,
-      [](const AvmArgs& a, cudaStream_t st) {
+      [c](const AvmArgs& a, cudaStream_t st) {
         launch_avm_move(a, st);
+        cudaEventRecord(c->fork, st);
+        cudaStreamWaitEvent(c->side, c->fork, 0);
+        launch_avm_dir(a, c->side);
+        cudaEventRecord(c->join, c->side);
         launch_avm_t1_pass(a, st);
       },
-      &c->exec);
+      [c](cudaStream_t st) { cudaStreamWaitEvent(st, c->join, 0); }, &c->exec);
   if (rc) return rc;
   return loop_graph(
       c,
@@ -254,7 +266,7 @@ int avm_graphs(cg_avm_ctx* c) {
         launch_avm_begin_t1(a.ctl, st);
         launch_avm_t1_pass(a, st);
       },
-      &c->t1_exec);
+      [](cudaStream_t) {}, &c->t1_exec);
 }
 
 int copy_in(cg_avm_ctx* c, void* dst, const void* src, size_t bytes) {
@@ -314,7 +326,10 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
   cg_workspace_bytes(1, &r, &spv_bytes);
   c->off = avm_layout(ncap, spv_bytes);
   do {
-    if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) { rc = CG_ECUDA; break; }
+    if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) { rc = CG_ECUDA; break; }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) { rc = CG_ECUDA; break; }
@@ -387,6 +402,7 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
       rc = CG_ECUDA;
       break;
     }
+    launch_avm_dir(avm_args(c), st);
     rc = avm_status(c);
     if (rc) break;
     rc = avm_graphs(c);
@@ -427,6 +443,14 @@ int cg_avm_profile_step(cg_avm_ctx* c, int64_t nsteps, double* ms_out, int32_t n
     ms_out[0] += ms;
     cudaEventElapsedTime(&ms, ev[1], ev[2]);
     ms_out[1] += ms;
+    // the director terms of the next step (beside the T1 passes in the
+    // graph), counted with the per-cell phase
+    cudaEventRecord(ev[0], st);
+    launch_avm_dir(a, st);
+    cudaEventRecord(ev[1], st);
+    if (cudaEventSynchronize(ev[1]) != cudaSuccess) { rc = afail(c, CG_ECUDA, "profile sync"); break; }
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    ms_out[0] += ms;
     for (int pass = 0; pass <= cap_of(c) + 1; ++pass) {
       cudaEventRecord(ev[0], st);
       launch_avm_t1_pass(a, st);
@@ -491,6 +515,7 @@ int cg_avm_set_state(cg_avm_ctx* c, const double* hx, const double* hy, const do
   if ((rc = copy_in(c, c->at<int>(c->off.cv), cv, c->n * CG_RING * sizeof(int)))) return rc;
   launch_avm_validate(avm_args(c), c->stream);
   launch_avm_shadow(avm_args(c), c->stream);
+  launch_avm_dir(avm_args(c), c->stream);  // director terms of the next step
   return avm_status(c);
 }
 
@@ -513,7 +538,8 @@ int cg_avm_set_step(cg_avm_ctx* c, int64_t step) {
   AV_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
   h.step = step;
   AV_CUDA(c, cudaMemcpy(c->ctl(), &h, sizeof(Ctl), cudaMemcpyHostToDevice));
-  return CG_OK;
+  launch_avm_dir(avm_args(c), c->stream);  // the next step's noise depends on the counter
+  return avm_status(c);
 }
 
 int cg_avm_get_geometry(cg_avm_ctx* c, double* A, double* P) {
@@ -588,7 +614,9 @@ int cg_avm_divide(cg_avm_ctx* c, int32_t count, const int32_t* cells, const doub
   AV_CUDA(c, cudaMemcpyAsync(dcs, cs.data(), cs.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   AV_CUDA(c, cudaMemcpyAsync(dvs, vs.data(), vs.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   launch_check_finite(2 * count, dd, c->ctl(), c->stream);
-  launch_avm_divide(avm_args(c), count, dc, dd, dcs, dvs, dm, c->stream);
+  launch_avm_divide(avm_args(c), count, dc, dd, dcs, dvs, dm, c->at<unsigned long long>(c->off.div_lock),
+                    c->stream);
+  launch_avm_dir(avm_args(c), c->stream);  // the daughters' director terms
   AV_CUDA(c, cudaGetLastError());
   std::vector<int> hm(count);
   AV_CUDA(c, cudaMemcpyAsync(hm.data(), dm, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -617,6 +645,7 @@ int cg_avm_set_v0(cg_avm_ctx* c, const double* v0) {
   int rc = copy_in(c, c->at<double>(c->off.v0), v0, c->n * sizeof(double));
   if (rc) return rc;
   launch_check_finite(c->n, c->at<double>(c->off.v0), c->ctl(), c->stream);
+  launch_avm_dir(avm_args(c), c->stream);  // the activity of the next step
   return avm_status(c);
 }
 
@@ -641,6 +670,9 @@ int cg_avm_destroy(cg_avm_ctx* c) {
   if (c->exec) cudaGraphExecDestroy(c->exec);
   if (c->t1_exec) cudaGraphExecDestroy(c->t1_exec);
   if (c->capture) cudaStreamDestroy(c->capture);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->fork) cudaEventDestroy(c->fork);
+  if (c->join) cudaEventDestroy(c->join);
   delete c;
   return CG_OK;
 }

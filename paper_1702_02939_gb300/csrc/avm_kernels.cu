@@ -152,11 +152,26 @@ void launch_avm_build(const AvmBuildArgs& a, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // Step kernels.
 // ---------------------------------------------------------------------------
-// Per cell: area and perimeter of the polygon, the force coefficients
-// ka = 2 K_A (A - A0) and kp = 2 K_P (P - P0), and, when stepping, the
-// self-propulsion v0 n(theta) of the current director followed by the
-// director update theta <- theta + sqrt(2 D_r dt) xi (Philox, counter
-// (cell, step)).
+// Director terms of the next step (launch_avm_dir): the self-propulsion
+// (v0/3) n(theta) of the current director (each of a cell's vertices takes a
+// third, Eq. 4 with n = 3) and the director after the next step's rotation,
+// theta + sqrt(2 D_r dt) xi (Philox, counter (cell, step) with the step
+// counter of the next step).  Cells removed by a T2 turn as well.
+__global__ void k_avm_dir(AvmArgs g) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.n) return;
+  const double th = g.theta[c];
+  double sn, cs;
+  dm_sincos(th, g.tab, sn, cs);
+  const double v3 = g.v0[c] * (1.0 / 3.0);
+  g.act[c] = make_double2(v3 * cs, v3 * sn);
+  g.thn[c] = th + g.noise_amp * director_noise(g.seed, c, g.ctl->step, g.tab);
+}
+
+// Per cell: area and perimeter of the polygon and the force coefficients
+// ka = 2 K_A (A - A0) and kp = 2 K_P (P - P0); when stepping, the director
+// takes its rotated value thn (k_avm_dir computed it, with the activity act
+// of the current director, before the step).
 __global__ void k_avm_cells(AvmArgs g) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.n) return;
@@ -165,16 +180,13 @@ __global__ void k_avm_cells(AvmArgs g) {
   const double* hx = g.hx + cur * V;
   const double* hy = g.hy + cur * V;
   const int m = g.cc[c];
+  if (g.move) g.theta[c] = g.thn[c];
   if (m == 0) {  // removed by a T2: no geometry, no force; the director still turns
     g.A[c] = 0.0;
     g.P[c] = 0.0;
     g.ka[c] = 0.0;
     g.kp[c] = 0.0;
     if (g.energy) g.energy[c] = 0.0;
-    if (g.move) {
-      g.act[c] = make_double2(0.0, 0.0);
-      g.theta[c] = g.theta[c] + g.noise_amp * director_noise(g.seed, c, g.ctl->step, g.tab);
-    }
     return;
   }
   if (m < 3 || m > CG_RING) {
@@ -210,15 +222,6 @@ __global__ void k_avm_cells(AvmArgs g) {
   g.ka[c] = g.KA * dA;  // half of dE/dA = 2 K_A (A - A0): dA/dh carries a 1/2
   g.kp[c] = 2.0 * g.KP * dP;
   if (g.energy) g.energy[c] = g.KA * dA * dA + g.KP * dP * dP;
-  if (g.move) {
-    const double th = g.theta[c];
-    double sn, cs;
-    dm_sincos(th, g.tab, sn, cs);
-    // (v0/3) n(theta): each of the cell's vertices takes a third (Eq. 4, n = 3)
-    const double v3 = g.v0[c] * (1.0 / 3.0);
-    g.act[c] = make_double2(v3 * cs, v3 * sn);
-    g.theta[c] = th + g.noise_amp * director_noise(g.seed, c, g.ctl->step, g.tab);
-  }
 }
 
 // Per vertex: F_v = -sum_k [ka_k 1/2 perp(u_{k-1} - u_k) - kp_k (u^_k + u^_{k-1})]
@@ -820,7 +823,8 @@ __global__ void k_avm_validate(AvmArgs g) {
 // same.  c keeps A, v_{a1+1} .. v_{a2}, B; newc gets B, v_{a2+1} .. v_{a1}, A.
 // Returns 0 made, 1 refused (a missing cut, a daughter or a neighbour over 16
 // vertices), -1 for an inconsistent network.
-__device__ int divide_cell(const AvmArgs& g, int c, double ux, double uy, int newc, int va, int vb) {
+__device__ int divide_cell(const AvmArgs& g, int c, double ux, double uy, int newc, int va, int vb,
+                           bool commit = true) {
   const size_t V = (size_t)g.V;
   double* hx = g.hx + g.ctl->cur * V;
   double* hy = g.hy + g.ctl->cur * V;
@@ -877,6 +881,7 @@ __device__ int divide_cell(const AvmArgs& g, int c, double ux, double uy, int ne
   const int s1 = slot3(g.vn, p1, p1n), s1n = slot3(g.vn, p1n, p1);
   const int s2 = slot3(g.vn, p2, p2n), s2n = slot3(g.vn, p2n, p2);
   if (s1 < 0 || s1n < 0 || s2 < 0 || s2n < 0) return -1;
+  if (!commit) return 0;  // the division would be made (nothing written)
   g.vn[3 * p1 + s1] = va;
   g.vn[3 * p1n + s1n] = va;
   g.vn[3 * p2 + s2] = vb;
@@ -923,10 +928,127 @@ __device__ int divide_cell(const AvmArgs& g, int c, double ux, double uy, int ne
   return 0;
 }
 
+// The divisions of a call, with the result of doing them one after the other
+// in request order (each seeing the network the previous ones left), in
+// rounds of one block.  Division k reads and writes only the cells of its
+// mother's 1-ring (the mother, the cells across its edges) and the vertices
+// between them, plus fresh slots; divisions whose 1-rings are disjoint
+// therefore commute.  Each round, the pending divisions of a window take a
+// 64-bit atomic minimum of (round stamp, request index) on every cell of their
+// 1-ring (the stamp makes this round's keys smaller than any earlier one's, so
+// the locks are never cleared within a call); the longest prefix of the window
+// whose divisions all hold their locks is mutually disjoint and disjoint from
+// every division after it.  Its divisions are tried without writing
+// (made or not), a block scan of the outcome gives each made one its slots in
+// request order (the next unused entries of cslots and of vslots, two each),
+// and they are applied together.  A division of a cell slot without a polygon
+// (empty: an earlier division of the call may fill it) waits until it is the
+// first pending one.  The first pending division always holds its locks, so
+// every round makes progress.  made[k] = 1 when division k was made.
+constexpr int kDivThreads = 256;
+__global__ void __launch_bounds__(kDivThreads) k_avm_divide_rounds(AvmArgs g, int count, const int* cells,
+                                                                   const double* dirs, const int* cslots,
+                                                                   const int* vslots, int* made,
+                                                                   unsigned long long* dlock) {
+  __shared__ int s_start, s_end, s_used, s_stop;
+  __shared__ int s_scan[kDivThreads];
+  const int t = threadIdx.x;
+  if (t == 0) {
+    s_start = 0;
+    s_used = 0;
+    s_stop = 0;
+  }
+  __syncthreads();
+  const unsigned V = (unsigned)g.V, n = (unsigned)g.n;
+  for (unsigned round = 0;; ++round) {
+    const int start = s_start;
+    if (start >= count || s_stop) break;
+    const int wend = min(count, start + kDivThreads);
+    const int k = start + t;
+    const bool mine = k < wend;
+    const unsigned long long key = ((unsigned long long)(0xffffffffu - round) << 32) | (unsigned)k;
+    const int c = mine ? cells[k] : -1;
+    const bool valid = mine && (unsigned)c < n;
+    const int m = valid ? g.cc[c] : 0;
+    const bool poly = m >= 3 && m <= CG_RING;
+    if (valid) {
+      atomicMin(&dlock[c], key);
+      if (poly)
+        for (int a = 0; a < m; ++a) {
+          const int v = g.cv[(size_t)c * CG_RING + a];
+          if ((unsigned)v < V)
+            for (int q = 0; q < 3; ++q) {
+              const int x = g.vc[3 * v + q];
+              if ((unsigned)x < n) atomicMin(&dlock[x], key);
+            }
+        }
+    }
+    if (t == 0) s_end = wend;
+    __syncthreads();
+    // a mother without a polygon (an empty slot, which an earlier division
+    // of the call may fill) waits until it is the first pending division
+    bool ok = valid && dlock[c] == key && (poly || k == start);
+    if (valid && poly)
+      for (int a = 0; a < m && ok; ++a) {
+        const int v = g.cv[(size_t)c * CG_RING + a];
+        if ((unsigned)v < V)
+          for (int q = 0; q < 3; ++q) {
+            const int x = g.vc[3 * v + q];
+            if ((unsigned)x < n && dlock[x] != key) ok = false;
+          }
+      }
+    if (mine && !ok) atomicMin(&s_end, k);
+    __syncthreads();
+    const int end = s_end;
+    if (end == start) {  // the first pending division can only fail by an invalid cell index
+      if (t == 0) {
+        raise_status(g.ctl, kEINVAL);
+        s_stop = 1;
+      }
+      __syncthreads();
+      break;
+    }
+    int flag = 0;
+    if (k < end) {
+      const int r = divide_cell(g, c, dirs[2 * k], dirs[2 * k + 1], 0, 0, 0, false);
+      if (r < 0) {
+        raise_status(g.ctl, kETOPO);
+        s_stop = 1;
+      }
+      flag = (r == 0);
+    }
+    s_scan[t] = flag;
+    __syncthreads();
+    for (int off = 1; off < kDivThreads; off <<= 1) {  // inclusive scan
+      const int add = t >= off ? s_scan[t - off] : 0;
+      __syncthreads();
+      s_scan[t] += add;
+      __syncthreads();
+    }
+    const int slot = s_used + s_scan[t] - flag;
+    if (k < end && !s_stop) {
+      made[k] = flag;
+      if (flag && divide_cell(g, c, dirs[2 * k], dirs[2 * k + 1], cslots[slot], vslots[2 * slot],
+                              vslots[2 * slot + 1]) != 0) {
+        raise_status(g.ctl, kETOPO);
+        s_stop = 1;
+      }
+    }
+    __syncthreads();
+    if (t == 0) {
+      s_used += s_scan[kDivThreads - 1];
+      s_start = end;
+    }
+    __syncthreads();
+  }
+}
+
 // The divisions of a call, one after the other (one thread: each sees the
 // network the previous ones left).  Division k, if made, takes the next
 // unused entries of cslots (cell slot) and vslots (two vertex slots), the
 // empty slots in increasing order; made[k] = 1 when division k was made.
+// Kept as the plain statement of the rule (cg_avm_divide runs the rounds
+// above, which give the same result).
 __global__ void k_avm_divide(AvmArgs g, int count, const int* cells, const double* dirs, const int* cslots,
                              const int* vslots, int* made) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
@@ -986,6 +1108,9 @@ void launch_avm_move(const AvmArgs& a, cudaStream_t st, int part) {
   if (part != 2) k_avm_cells<<<cell_blocks_of(a.n), kAvmCellThreads, 0, st>>>(m);
   if (part != 1) k_avm_force_move<<<vertex_blocks_of(a.V), kAvmVertexThreads, 0, st>>>(m);
 }
+void launch_avm_dir(const AvmArgs& a, cudaStream_t st) {
+  k_avm_dir<<<cell_blocks_of(a.n), kAvmCellThreads, 0, st>>>(a);
+}
 void launch_avm_begin_t1(Ctl* ctl, cudaStream_t st) { k_avm_begin_t1<<<1, 1, 0, st>>>(ctl); }
 void launch_avm_t1_pass(const AvmArgs& a, cudaStream_t st) {
   k_t1_propose<<<blocks_of(a.V), kAvmThreads, 0, st>>>(a);
@@ -1001,8 +1126,14 @@ void launch_avm_forces(const AvmArgs& a, cudaStream_t st) {
   k_avm_force_move<<<vertex_blocks_of(a.V), kAvmVertexThreads, 0, st>>>(f);
 }
 void launch_avm_divide(const AvmArgs& a, int count, const int* cells, const double* dirs, const int* cslots,
-                       const int* vslots, int* made, cudaStream_t st) {
-  if (count > 0) k_avm_divide<<<1, 32, 0, st>>>(a, count, cells, dirs, cslots, vslots, made);
+                       const int* vslots, int* made, unsigned long long* dlock, cudaStream_t st) {
+  if (count <= 0) return;
+  if (dlock) {
+    cudaMemsetAsync(dlock, 0xff, (size_t)a.n * sizeof(unsigned long long), st);
+    k_avm_divide_rounds<<<1, kDivThreads, 0, st>>>(a, count, cells, dirs, cslots, vslots, made, dlock);
+  } else {
+    k_avm_divide<<<1, 32, 0, st>>>(a, count, cells, dirs, cslots, vslots, made);
+  }
 }
 void launch_avm_p0s(const AvmArgs& a, cudaStream_t st) {
   k_avm_p0s<<<blocks_of(a.n), kAvmThreads, 0, st>>>(a);

@@ -29,8 +29,8 @@ struct Offsets {
   size_t key, rank, perm, key_count, key_start, key_partials, theta_alt, p0_alt, v0_alt, tag_alt, rep_alt,
       cnt_alt, nbr_alt;
   size_t x, y, X, Y, theta, p0, v0, A, P, Fx, Fy, ecell, tmp, tmp2, scalar, nrm, xi;
-  size_t tag, rep, cnt, nbr, old_cnt, old_nbr;
-  size_t fs, s, w;
+  size_t tag, nid, nid_alt, rep, cnt, nbr, old_cnt, old_nbr;
+  size_t fs, s, w, order;
   size_t flags, list0, list1, dirty_list, dirty_bits;
   size_t bin_count, bin_start, partials, cell_bin, cell_rank, ids;
   size_t reps, ctl, dir_tab;
@@ -75,6 +75,8 @@ Offsets layout(int64_t N, int64_t NB, int64_t NK, int R) {
   o.nrm = L.take(N * sizeof(double2));
   o.xi = L.take(N * d);
   o.tag = L.take(N * i4);
+  o.nid = L.take(N * i4);
+  o.nid_alt = L.take(N * i4);
   o.rep = L.take(N * i4);
   o.cnt = L.take(N * i4);
   o.nbr = L.take(N * CG_RING * i4);
@@ -83,6 +85,7 @@ Offsets layout(int64_t N, int64_t NB, int64_t NK, int R) {
   o.fs = L.take(N * CG_RING * sizeof(double2));
   o.s = L.take(N * CG_RING * sizeof(double2));
   o.w = L.take(N * CG_RING * sizeof(double2));
+  o.order = L.take(N * i4);
   o.flags = L.take(((N + 31) / 32) * 4);
   o.list0 = L.take(N * i4);
   o.list1 = L.take(N * i4);
@@ -187,7 +190,7 @@ struct cg_ctx {
   // cg_run_io: copy streams and the events that order the double-buffered staging
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t in_ready[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_free[2] = {};
-  cg_launch launch{4, 4, 2, 1, 0, 8, 0};       // launch shapes of the step graph
+  cg_launch launch{4, 4, 4, 1, 0, 8, 1, 1};    // launch shapes of the step graph
   std::vector<cg_replica> user_reps;           // as passed to cg_create
   cudaGraphExec_t step_exec = nullptr;
   int graph_steps = 0;
@@ -237,6 +240,7 @@ GeomArgs geom_args(cg_ctx* c) {
   g.list_count = nullptr;
   g.list_bits = nullptr;
   g.tolerant = 0;
+  g.order = (c->launch.ring_order & 1) ? c->at<int>(c->off.order) : nullptr;
   return g;
 }
 
@@ -267,7 +271,14 @@ ForceArgs force_args(cg_ctx* c, int integrate) {
   f.seed = c->par.seed;
   f.nrm = c->at<double2>(c->off.nrm);
   f.xi = c->at<double>(c->off.xi);
+  f.order = (c->launch.ring_order & 2) ? c->at<int>(c->off.order) : nullptr;
   return f;
+}
+
+// Ring-size grouping of the cells for the geometry and force kernels (always
+// a permutation of the cells, so a stale one is only slower, never wrong).
+void run_order(cg_ctx* c, cudaStream_t st) {
+  launch_order((int)c->N, c->at<int>(c->off.cnt), c->at<int>(c->off.order), st);
 }
 
 DirArgs dir_args(cg_ctx* c) {
@@ -275,7 +286,7 @@ DirArgs dir_args(cg_ctx* c) {
   d.n = (int)c->N;
   d.ctl = c->ctl();
   d.theta = c->at<double>(c->off.theta);
-  d.tag = c->at<int>(c->off.tag);
+  d.tag = c->at<int>(c->off.nid);  // the noise counter of each cell
   d.seed = c->par.seed;
   d.nrm = c->at<double2>(c->off.nrm);
   d.xi = c->at<double>(c->off.xi);
@@ -424,6 +435,8 @@ SortArgs sort_args(cg_ctx* c) {
   a.rep_alt = c->at<int>(c->off.rep_alt);
   a.cnt_alt = c->at<int>(c->off.cnt_alt);
   a.nbr_alt = c->at<int>(c->off.nbr_alt);
+  a.nid = c->at<int>(c->off.nid);
+  a.nid_alt = c->at<int>(c->off.nid_alt);
   return a;
 }
 
@@ -460,6 +473,10 @@ void enqueue_step_prefix(cg_ctx* c, cudaStream_t st) {
   launch_begin_topology(c->ctl(), 1, st);
   cudaEventRecord(c->fork, st);
   cudaStreamWaitEvent(c->side[0], c->fork, 0);
+  cudaStreamWaitEvent(c->side[1], c->fork, 0);
+  // the ring-size grouping from the rings of the previous step, first on the
+  // geometry branch (before any repair round can rewrite a ring)
+  if (c->launch.ring_order) run_order(c, c->side[0]);
   if (c->launch.dir_beside_geom) {
     cudaStreamWaitEvent(c->side[2], c->fork, 0);
     run_dir(c, dir_args_step(c), c->side[2], dir_grid(c));
@@ -471,7 +488,6 @@ void enqueue_step_prefix(cg_ctx* c, cudaStream_t st) {
   g.tolerant = 1;
   run_geom(c, g, c->side[0], geom_grid(c));
   cudaEventRecord(c->join_dir, c->side[0]);
-  cudaStreamWaitEvent(c->side[1], c->fork, 0);
   launch_cell_list(cell_list_args(c, 0), c->side[1]);
   cudaEventRecord(c->join_list, c->side[1]);
   launch_test(test_args(c), st, test_grid(c));
@@ -496,6 +512,7 @@ void enqueue_step_suffix(cg_ctx* c, cudaStream_t st) {
 // positions, directors, step counter, storage order, p0, v0 or the moduli).
 enum : int { kPrimeDir = 1, kPrimeGeom = 2, kPrimeMove = 4, kPrimeAll = 7 };
 void prime(cg_ctx* c, int what = kPrimeAll) {
+  run_order(c, c->stream);
   if (what & kPrimeDir) run_dir(c, dir_args(c), c->stream);
   if (what & kPrimeGeom) run_geom(c, geom_args(c), c->stream);
   if (what & kPrimeMove) run_force(c, force_args(c, 1), c->stream);
@@ -730,6 +747,16 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
     delete c;
     return CG_EINVAL;
   }
+  // FP64 defaults (measured at N = 262144): the geometry pass in ring-size
+  // groups (it is bound by the FP64 pipe, where idle lanes cost most) with the
+  // director terms on a branch of their own beside it.  The FP32 kernels gain
+  // more from the plain (coalesced) order and keep the director terms first
+  // on the geometry branch.
+  if (c->par.precision == 1) {
+    c->launch.ring_order = 0;
+    c->launch.dir_beside_geom = 0;
+    c->launch.dir_blocks_per_sm = 2;
+  }
   c->off = layout(c->N, c->NB, c->NK, R);
   if (ws_bytes < c->off.total) {
     delete c;
@@ -775,6 +802,8 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
 #define TRY(call) do { cudaError_t e2 = (call); if (e2 != cudaSuccess) { rc = fail(c, CG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e2)); } } while (0)
     TRY(cudaMemcpyAsync(c->at<Rep>(c->off.reps), c->reps.data(), R * sizeof(Rep), cudaMemcpyHostToDevice, st));
     TRY(cudaMemcpyAsync(c->at<int>(c->off.tag), tag.data(), c->N * sizeof(int), cudaMemcpyHostToDevice, st));
+    // noise counters: the cell's index in user order (cg_set_noise_ids may replace them)
+    TRY(cudaMemcpyAsync(c->at<int>(c->off.nid), tag.data(), c->N * sizeof(int), cudaMemcpyHostToDevice, st));
     TRY(cudaMemcpyAsync(c->at<int>(c->off.rep), rep.data(), c->N * sizeof(int), cudaMemcpyHostToDevice, st));
     TRY(cudaMemcpyAsync(c->at<double>(c->off.p0), p0.data(), c->N * sizeof(double), cudaMemcpyHostToDevice, st));
     TRY(cudaMemcpyAsync(c->at<double>(c->off.v0), v0.data(), c->N * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -896,6 +925,7 @@ int cg_profile_step(cg_ctx* c, int64_t nsteps, double* ms_out, int32_t n_out) {
     cudaEventRecord(ev[3], st);
     run_dir(c, dir_args_step(c), st, dir_grid(c));
     cudaEventRecord(ev[4], st);
+    if (c->launch.ring_order) run_order(c, st);
     run_geom(c, geom_args(c), st);
     cudaEventRecord(ev[5], st);
     run_force(c, force_args(c, 1), st);
@@ -1102,7 +1132,7 @@ int cg_set_launch(cg_ctx* c, const cg_launch* l) {
       l->check_blocks_per_sm > 64 || l->dir_blocks_per_sm < 0 || l->dir_blocks_per_sm > 64 ||
       (l->dir_low_priority != 0 && l->dir_low_priority != 1) || l->geom_blocks_per_sm < 0 ||
       l->geom_blocks_per_sm > 64 || l->test_blocks_per_sm < 0 || l->test_blocks_per_sm > 64 ||
-      (l->dir_beside_geom != 0 && l->dir_beside_geom != 1))
+      (l->dir_beside_geom != 0 && l->dir_beside_geom != 1) || l->ring_order < 0 || l->ring_order > 3)
     return CG_EINVAL;
   int rc = read_status(c);
   if (rc) return rc;
@@ -1187,24 +1217,27 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
   static const int geom_opts[] = {0, 4, 8, 16};
   static const int test_opts[] = {0, 2, 4, 8};
   static const int beside_opts[] = {0, 1};
+  static const int order_opts[] = {0, 1, 2, 3};
   const cg_launch start = c->launch;
   cg_launch cur = start;
   double cur_ms = 0.0;
   rc = trial(cur, steps_per_trial, cur_ms);
+  struct Field {
+    int32_t cg_launch::*member;
+    const int* opts;
+    int nopt;
+  };
+  static const Field fields[] = {
+      {&cg_launch::repair_blocks_per_sm, repair_opts, 4}, {&cg_launch::check_blocks_per_sm, check_opts, 4},
+      {&cg_launch::dir_blocks_per_sm, dir_opts, 5},       {&cg_launch::dir_low_priority, prio_opts, 2},
+      {&cg_launch::geom_blocks_per_sm, geom_opts, 4},     {&cg_launch::test_blocks_per_sm, test_opts, 4},
+      {&cg_launch::dir_beside_geom, beside_opts, 2},      {&cg_launch::ring_order, order_opts, 4}};
   for (int sweep = 0; sweep < 2 && !rc; ++sweep) {
-    for (int field = 0; field < 7 && !rc; ++field) {
-      const int* opts = field == 0 ? repair_opts : field == 1 ? check_opts : field == 2 ? dir_opts
-                      : field == 3 ? prio_opts : field == 4 ? geom_opts : field == 5 ? test_opts : beside_opts;
-      const int nopt = field == 0 ? 4 : field == 1 ? 4 : field == 2 ? 5 : field == 3 ? 2 : field == 5 ? 4
-                     : field == 6 ? 2 : 4;
-      for (int k = 0; k < nopt && !rc; ++k) {
+    for (const Field& f : fields) {
+      for (int k = 0; k < f.nopt && !rc; ++k) {
         cg_launch cand = cur;
-        int* slot = field == 0 ? &cand.repair_blocks_per_sm : field == 1 ? &cand.check_blocks_per_sm
-                  : field == 2 ? &cand.dir_blocks_per_sm : field == 3 ? &cand.dir_low_priority
-                  : field == 4 ? &cand.geom_blocks_per_sm : field == 5 ? &cand.test_blocks_per_sm
-                  : &cand.dir_beside_geom;
-        if (*slot == opts[k]) continue;
-        *slot = opts[k];
+        if (cand.*f.member == f.opts[k]) continue;
+        cand.*f.member = f.opts[k];
         double ms = 0.0;
         rc = trial(cand, steps_per_trial, ms);
         if (!rc && ms < cur_ms) {
@@ -1212,8 +1245,10 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
           cur_ms = ms;
         }
       }
+      if (rc) break;
     }
   }
+
   // short trials are noisy: the winner must beat the starting shapes again in
   // two longer, interleaved trials each (best of two)
   if (!rc && std::memcmp(&cur, &start, sizeof(cg_launch)) != 0) {
@@ -1243,6 +1278,76 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
   if (rc) return rc;
   if (best) *best = cur;
   if (best_ms) *best_ms = cur_ms;
+  return CG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Domain decomposition of one large system (strips with halos): the pieces a
+// domain's context needs so that its cells evolve exactly as in the
+// undivided system.
+// ---------------------------------------------------------------------------
+int cg_set_noise_ids(cg_ctx* c, const int32_t* ids) {
+  if (!c || !ids) return CG_EINVAL;
+  int rc = read_status(c);
+  if (rc) return rc;
+  std::vector<int32_t> h(c->N);
+  CG_CUDA(c, cudaMemcpy(h.data(), ids, c->N * sizeof(int32_t), cudaMemcpyDefault));
+  for (int32_t v : h)
+    if (v < 0) return fail(c, CG_EINVAL, "noise ids must be non-negative");
+  int* tmp = c->at<int>(c->off.tmp);  // staging (user order)
+  CG_CUDA(c, cudaMemcpyAsync(tmp, h.data(), c->N * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  launch_scatter_i((int)c->N, c->at<int>(c->off.tag), tmp, c->at<int>(c->off.nid), c->stream);
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  prime(c, kPrimeDir | kPrimeMove);  // the noise of the pending move depends on the ids
+  return read_status(c);
+}
+
+int cg_set_frame(cg_ctx* c, int32_t replica, double x0, double y0, double Lx_outer, double Ly_outer) {
+  if (!c || replica < 0 || replica >= c->R) return CG_EINVAL;
+  Rep& R = c->reps[replica];
+  if (!(Lx_outer > 0) || !(Ly_outer > 0) || !std::isfinite(Lx_outer) || !std::isfinite(Ly_outer))
+    return fail(c, CG_EINVAL, "cg_set_frame: the outer box needs positive finite sides");
+  if (ceil_log2(std::fmax(Lx_outer, Ly_outer)) != 50 - R.q)
+    return fail(c, CG_EINVAL, "cg_set_frame: the outer box must have the same position grid (same ceil(log2(max side)))");
+  const long long LXg = (long long)std::rint(std::ldexp(Lx_outer, R.q));
+  const long long LYg = (long long)std::rint(std::ldexp(Ly_outer, R.q));
+  const double X0d = std::ldexp(x0, R.q), Y0d = std::ldexp(y0, R.q);
+  if (!(X0d >= 0 && X0d < (double)LXg && Y0d >= 0 && Y0d < (double)LYg) || X0d != std::rint(X0d) ||
+      Y0d != std::rint(Y0d))
+    return fail(c, CG_EINVAL, "cg_set_frame: the origin must be a grid point inside the outer box");
+  if (R.LX > LXg || R.LY > LYg) return fail(c, CG_EINVAL, "cg_set_frame: the frame must fit in the outer box");
+  int rc = read_status(c);
+  if (rc) return rc;
+  R.framed = 1;
+  R.X0 = (long long)X0d;
+  R.Y0 = (long long)Y0d;
+  R.LXg = LXg;
+  R.LYg = LYg;
+  R.x0 = std::ldexp((double)R.X0, -R.q);
+  R.y0 = std::ldexp((double)R.Y0, -R.q);
+  R.Lxg = std::ldexp((double)LXg, -R.q);
+  R.Lyg = std::ldexp((double)LYg, -R.q);
+  CG_CUDA(c, cudaMemcpyAsync(c->at<Rep>(c->off.reps) + replica, &R, sizeof(Rep), cudaMemcpyHostToDevice, c->stream));
+  CG_CUDA(c, cudaStreamSynchronize(c->stream));
+  prime(c, kPrimeMove);  // the pending move is rounded in the outer box's coordinates
+  return read_status(c);
+}
+
+int cg_halo_pack(cg_ctx* c, const int32_t* d_slot, int64_t* d_out) {
+  if (!c || !d_slot || !d_out) return CG_EINVAL;
+  launch_halo_pack((int)c->N, c->at<int>(c->off.tag), d_slot, c->at<Rep>(c->off.reps), c->at<int>(c->off.rep),
+                   c->ctl(), c->at<long long>(c->off.X), c->at<long long>(c->off.Y),
+                   reinterpret_cast<long long*>(d_out), c->stream);
+  CG_CUDA(c, cudaGetLastError());
+  return CG_OK;
+}
+
+int cg_halo_unpack(cg_ctx* c, const int32_t* d_slot, const int64_t* d_in) {
+  if (!c || !d_slot || !d_in) return CG_EINVAL;
+  launch_halo_unpack((int)c->N, c->at<int>(c->off.tag), d_slot, c->at<Rep>(c->off.reps), c->at<int>(c->off.rep),
+                     c->ctl(), reinterpret_cast<const long long*>(d_in), c->at<double>(c->off.x),
+                     c->at<double>(c->off.y), c->at<long long>(c->off.X), c->at<long long>(c->off.Y), c->stream);
+  CG_CUDA(c, cudaGetLastError());
   return CG_OK;
 }
 

@@ -54,6 +54,14 @@ struct Rep {
   int hkey0;                // first sort key of the replica
   int bshift;               // cell-list bin width = 2^bshift grid units
   int hshift;               // Hilbert grid cell = 2^hshift grid units
+  // Frame of a sub-box of a larger periodic box (a domain of a decomposed
+  // system, cg_set_frame): the move of Eq. 3 is evaluated in the larger box's
+  // coordinates (origin X0, Y0 and sides LXg, LYg in grid units, Lxg, Lyg in
+  // box units) so that it rounds exactly as there.  framed = 0: the box is
+  // the whole system.
+  int framed;
+  long long X0, Y0, LXg, LYg;
+  double x0, y0, Lxg, Lyg;
 };
 
 // Cell-list bin of a position in grid units (integer only: every bin is
@@ -370,11 +378,41 @@ __device__ __forceinline__ long long wrap_to_grid(double v, double L, double sca
   return X;
 }
 
+// Position update of Eq. 3 on one axis in a framed box (a domain of a
+// larger periodic box, Rep::framed): x + dt v is formed in the larger box's
+// coordinates, x = xi + x0 reduced into [0, Lg) (both exact on the grid), so
+// that it rounds exactly as in the undivided system; the grid value is then
+// brought back into the frame (a cell that left the frame is wrapped into
+// it: only halo cells can, and their positions are replaced).
+__device__ __forceinline__ long long move_framed(double xi, double dt, double v, double x0, double Lg, double scale,
+                                                 long long X0, long long LG, long long LI) {
+  double x = xi + x0;
+  if (x >= Lg) x -= Lg;
+  long long X = wrap_to_grid(fma(dt, v, x), Lg, scale, LG) - X0;
+  if (X < 0) X += LG;
+  if (X >= LI) X %= LI;
+  return X;
+}
+
 // Exact int64 -> double for |v| < 2^51: v added to the bit pattern of 1.5 * 2^52
 // (integer pipe) lands in [2^52, 2^53) where doubles are spaced by one; one
 // FP64 subtraction removes the offset.
 __device__ __forceinline__ double i2d_exact(long long v) {
   return __longlong_as_double(0x4338000000000000LL + v) - 0x1.8p52;
+}
+
+// Exact v * 2^k as a double for |v| < 2^53 (and a result in the normal
+// range), built on the integer pipes alone: sign, leading-zero count, the
+// leading one shifted to bit 52, the exponent field added on top (the leading
+// one carries into it).  No FP64 instruction: in the geometry kernels the FP64
+// pipe is the bottleneck while the integer pipes are mostly idle.
+__device__ __forceinline__ double i2d_int(long long v, int k = 0) {
+  const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
+  const unsigned long long a = (v < 0) ? (0ull - (unsigned long long)v) : (unsigned long long)v;
+  const int lz = __clzll((long long)a);  // 11 <= lz for |v| < 2^53; 64 for v = 0
+  const unsigned long long m = a << (lz - 11);
+  const unsigned long long e = (unsigned long long)(1022 + 63 - lz + k) << 52;
+  return a ? __longlong_as_double((long long)(sgn | (e + m))) : 0.0;
 }
 
 // Position of cell i in the ring of cell j, or -1.

@@ -35,6 +35,9 @@ struct GeomArgs {
   // out-of-range entries are skipped and no status is raised; every cell whose
   // ring changes is processed again afterwards.
   int tolerant;
+  // Processing order of all cells (a permutation of 0..n-1, cells of equal
+  // ring size grouped; see launch_order), or null for 0..n-1.  Unused with list.
+  const int* order;
 };
 
 struct ForceArgs {
@@ -57,7 +60,16 @@ struct ForceArgs {
   unsigned long long seed;
   const double2* nrm;  // (cos, sin) of each cell's director, from k_dir
   const double* xi;    // the step's director noise, from k_dir
+  const int* order;    // processing order of the cells (as GeomArgs), or null
 };
+
+// Cells of each chunk of kOrderChunk consecutive cells regrouped by ring size:
+// a warp of the geometry and force kernels then runs cells with (mostly) the
+// same number of ring slots, so its lanes stay active through the slot loop.
+// order becomes a permutation of 0..n-1 whatever the ring sizes read (rings
+// may be rewritten concurrently; each cell is placed exactly once).
+constexpr int kOrderChunk = 1024;
+void launch_order(int n, const int* cnt, int* order, cudaStream_t st);
 
 // Director terms of the next move, computed off the critical path: n(theta)
 // and the Philox/Box-Muller noise of the step held in the control word.
@@ -171,6 +183,14 @@ void launch_snap(int n, const Rep* reps, const int* rep, const double* xin, cons
 void launch_gather_d(int n, const int* tag, const double* src, double* dst_user, cudaStream_t st);
 void launch_check_finite(int n, const double* v, Ctl* ctl, cudaStream_t st);
 void launch_scatter_d(int n, const int* tag, const double* src_user, double* dst, cudaStream_t st);
+void launch_scatter_i(int n, const int* tag, const int* src_user, int* dst, cudaStream_t st);
+// Halo exchange of a decomposed system: pending positions of the cells with
+// slot[user index] >= 0 to/from out/in[2 slot], [2 slot + 1] as grid
+// coordinates of the larger box (topo_kernels.cu).
+void launch_halo_pack(int n, const int* tag, const int* slot, const Rep* reps, const int* rep, const Ctl* ctl,
+                      const long long* X2, const long long* Y2, long long* out, cudaStream_t st);
+void launch_halo_unpack(int n, const int* tag, const int* slot, const Rep* reps, const int* rep, Ctl* ctl,
+                        const long long* in, double* x2, double* y2, long long* X2, long long* Y2, cudaStream_t st);
 // current positions (x2, y2: [2][n], buffer ctl->cur) into user order
 void launch_gather_cur_xy(int n, const int* tag, const double* x2, const double* y2, const Ctl* ctl,
                           double* dst_x, double* dst_y, cudaStream_t st);
@@ -192,6 +212,7 @@ struct SortArgs {
   int *key_count, *key_start, *key_partials;
   double *theta_alt, *p0_alt, *v0_alt;
   int *tag_alt, *rep_alt, *cnt_alt, *nbr_alt;
+  int *nid, *nid_alt;  // noise counters of the cells
 };
 void launch_sort(const SortArgs& a, cudaStream_t st);
 
@@ -262,6 +283,7 @@ struct AvmArgs {
   double *A, *P, *energy;
   double *ka, *kp;         // [n] K_A (A - A0) and 2 K_P (P - P0) of each cell
   double2* act;            // [n] (v0/3) n(theta) of the step's directors
+  double* thn;             // [n] the directors after the step's rotation (k_avm_dir)
   double *Fx, *Fy;
   int move;
   double thr2, t1_len;
@@ -278,16 +300,22 @@ struct AvmArgs {
 void launch_avm_build(const AvmBuildArgs& a, cudaStream_t st);
 // part: 0 both kernels, 1 the per-cell kernel only, 2 the per-vertex kernel only
 void launch_avm_move(const AvmArgs& a, cudaStream_t st, int part = 0);
+// Director terms of the next step, act = (v0/3) n(theta) and the rotated
+// directors thn = theta + sqrt(2 D_r dt) xi (noise counter of ctl->step); in
+// the step graph beside the T1 passes, which leave the FP64 pipe idle
+void launch_avm_dir(const AvmArgs& a, cudaStream_t st);
 void launch_avm_begin_t1(Ctl* ctl, cudaStream_t st);
 void launch_avm_t1_pass(const AvmArgs& a, cudaStream_t st);
 void launch_avm_forces(const AvmArgs& a, cudaStream_t st);
 void launch_avm_validate(const AvmArgs& a, cudaStream_t st);
 // P0[c] = p0[c] sqrt(a0[c]) after p0 or A0 change
 void launch_avm_p0s(const AvmArgs& a, cudaStream_t st);
-// count divisions (cells[k], direction dirs[2k], dirs[2k+1]) in order, one
-// thread; the divisions made take cslots[0, 1, ...] and vslots[0, 1, ...] in turn
+// count divisions (cells[k], direction dirs[2k], dirs[2k+1]) with the result
+// of doing them in order; the divisions made take cslots[0, 1, ...] and
+// vslots[0, 1, ...] in turn.  dlock ([n] scratch): conflict-free rounds in
+// one block; null: one thread, one division after the other
 void launch_avm_divide(const AvmArgs& a, int count, const int* cells, const double* dirs, const int* cslots,
-                       const int* vslots, int* made, cudaStream_t st);
+                       const int* vslots, int* made, unsigned long long* dlock, cudaStream_t st);
 void launch_avm_shadow(const AvmArgs& a, cudaStream_t st);
 void launch_fill_d(int n, double v, double* out, cudaStream_t st);
 void launch_fill_u64(int n, unsigned long long v, unsigned long long* out, cudaStream_t st);

@@ -72,6 +72,7 @@ __global__ void k_sort_move(SortArgs g) {
   g.p0_alt[j] = g.p0[i];
   g.v0_alt[j] = g.v0[i];
   g.tag_alt[j] = g.tag[i];
+  g.nid_alt[j] = g.nid[i];
   g.rep_alt[j] = g.rep[i];
   const int m = g.cnt[i];
   g.cnt_alt[j] = m;
@@ -104,6 +105,7 @@ void launch_sort(const SortArgs& a, cudaStream_t st) {
   cudaMemcpyAsync(a.p0, a.p0_alt, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(a.v0, a.v0_alt, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(a.tag, a.tag_alt, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(a.nid, a.nid_alt, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(a.rep, a.rep_alt, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(a.cnt, a.cnt_alt, N * sizeof(int), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(a.nbr, a.nbr_alt, N * CG_RING * sizeof(int), cudaMemcpyDeviceToDevice, st);

@@ -21,12 +21,17 @@
 namespace cgk {
 
 // One thread per cell.  Writes A, P, force sets fs[a][i] = dE_i/dh_a, and the
-// per-slot Jacobian factors s[a][i] = u_a / det_a and w[a][i].
+// per-slot Jacobian factor s[a][i] = 2 u_a / det_a (the other factor, w_a / 2,
+// is rebuilt exactly from the integer positions by k_force).
 //
 // The geometry runs in grid units (coordinates x 2^q): relative positions come
 // exactly from the int64 grid coordinates, and the powers of two cancel in the
 // force (u/det scales as 2^q, w as 2^-q) or fold into one factor per cell
-// (A x 2^-2q, P x 2^-q, dA/dh x 2^-q).
+// (A x 2^-2q, P x 2^-q, dA/dh x 2^-q).  The circumcentres are kept doubled,
+// g_a = 2 h_a = num / det: every use is homogeneous in h, so the factor 2
+// (exact) folds into the per-cell constants (A x 1/4, P x 1/2, dA/dh x 1/2,
+// s x 2 against w / 2) and the results equal those of h itself bit for bit.
+// Integer-to-double conversions run on the integer pipes (i2d_int).
 __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
   __shared__ double sh_hx[CG_RING][kGeomThreads];
   __shared__ double sh_hy[CG_RING][kGeomThreads];
@@ -39,7 +44,7 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
   const long long* __restrict__ Y = g.Y + (size_t)cur * N;
   const int total = g.list ? *g.list_count : g.n;
   for (int item = blockIdx.x * kGeomThreads + t; item < total; item += gridDim.x * kGeomThreads) {
-    const int i = g.list ? g.list[item] : item;
+    const int i = g.list ? g.list[item] : (g.order ? g.order[item] : item);
     if (g.list_bits) atomicAnd(&g.list_bits[i >> 5], ~(1u << (i & 31)));
     const Rep R = g.reps[g.rep[i]];
     const long long Xi = X[i], Yi = Y[i];
@@ -57,8 +62,8 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
     };
 
     const int j0 = nb(0);
-    const double d0x = i2d_exact(min_image_i(X[j0] - Xi, R.LX));
-    const double d0y = i2d_exact(min_image_i(Y[j0] - Yi, R.LY));
+    const double d0x = i2d_int(min_image_i(X[j0] - Xi, R.LX));
+    const double d0y = i2d_int(min_image_i(Y[j0] - Yi, R.LY));
     const double l0 = d0x * d0x + d0y * d0y;
     double ax = d0x, ay = d0y, la = l0;
     double hpx = 0.0, hpy = 0.0, h0x = 0.0, h0y = 0.0;
@@ -67,20 +72,18 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
       double bx, by, lb;
       if (a + 1 < m) {
         const int j = nb(a + 1);
-        bx = i2d_exact(min_image_i(X[j] - Xi, R.LX));
-        by = i2d_exact(min_image_i(Y[j] - Yi, R.LY));
+        bx = i2d_int(min_image_i(X[j] - Xi, R.LX));
+        by = i2d_int(min_image_i(Y[j] - Yi, R.LY));
         lb = bx * bx + by * by;
       } else {
         bx = d0x; by = d0y; lb = l0;
       }
       const double det = ax * by - ay * bx;  // (r_j - r_i) x (r_k - r_i)
       const double r = fast_rcp(det);
-      const double hr = 0.5 * r;
-      // circumcentre relative to r_i
-      const double hx = (by * la - ay * lb) * hr;
-      const double hy = (ax * lb - bx * la) * hr;
+      // doubled circumcentre relative to r_i
+      const double hx = (by * la - ay * lb) * r;
+      const double hy = (ax * lb - bx * la) * r;
       g.s[a * N + i] = make_double2(hx * r, hy * r);
-      g.w[a * N + i] = make_double2(by - ay, ax - bx);
       sh_hx[a][t] = hx;
       sh_hy[a][t] = hy;
       if (a == 0) {
@@ -107,14 +110,14 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
       sh_ey[0][t] = ey * il;
     }
     const double sc = R.inv_scale;
-    const double A = 0.5 * area * sc * sc, P = per * sc;
+    const double A = 0.125 * area * sc * sc, P = 0.5 * per * sc;
     g.A[i] = A;
     g.P[i] = P;
     const double dA = A - g.A0, dP = P - g.p0[i] * g.sqrtA0;
     if (g.energy_out) g.energy_out[i] = g.KA * dA * dA + g.KP * dP * dP;
-    // dA/dh = 1/2 perp(h_next - h_prev) (the 1/2 and the grid scale fold into ka);
-    // dP/dh = e_in - e_out (unit edge vectors)
-    const double ka = g.KA * dA * sc, kp = 2.0 * g.KP * dP;
+    // dA/dh = 1/2 perp(h_next - h_prev) (the 1/2, the doubling of g and the
+    // grid scale fold into ka); dP/dh = e_in - e_out (unit edge vectors)
+    const double ka = g.KA * dA * (0.5 * sc), kp = 2.0 * g.KP * dP;
     for (int a = 0; a < m; ++a) {
       const int ap = (a == 0) ? m - 1 : a - 1;
       const int an = (a + 1 == m) ? 0 : a + 1;
@@ -126,8 +129,10 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
 }
 
 // Net force on cell i: G_t = sum over the triangle's three cells of their
-// force sets, F_i = -sum_t s_t (w_t . G_t).  False (status raised) for a
-// malformed ring.
+// force sets, F_i = -sum_t s_t (w_t . G_t), with s_t = 2 u_t / det_t from
+// k_geom and w_t / 2 = perp(r_k - r_j) / 2 rebuilt exactly from the integer
+// grid offsets (an exact difference, converted on the integer pipes).  False
+// (status raised) for a malformed ring.
 __device__ __forceinline__ bool net_force(const ForceArgs& g, int i, double& fx_out, double& fy_out) {
   const size_t N = (size_t)g.n;
   const int m = g.cnt[i];
@@ -135,21 +140,33 @@ __device__ __forceinline__ bool net_force(const ForceArgs& g, int i, double& fx_
     raise_status(g.ctl, kETOPO);
     return false;
   }
+  const int cur = g.ctl->cur;
+  const long long* __restrict__ X = g.X + (size_t)cur * N;
+  const long long* __restrict__ Y = g.Y + (size_t)cur * N;
+  const Rep R = g.reps[g.rep[i]];
+  const long long Xi = X[i], Yi = Y[i];
   const int* ring = g.nbr + (size_t)i * CG_RING;
   int jfirst = ring[0];
   int pfirst = ring_pos(g.nbr, g.cnt, jfirst, i);
   int j = jfirst, pj = pfirst;
+  const long long fX = min_image_i(X[jfirst] - Xi, R.LX), fY = min_image_i(Y[jfirst] - Yi, R.LY);
+  long long aX = fX, aY = fY;
   double fx = 0.0, fy = 0.0;
   bool bad = pfirst < 0;
   for (int a = 0; a < m; ++a) {
     int k, pk;
+    long long bX, bY;
     if (a + 1 < m) {
       k = ring[a + 1];
       pk = ring_pos(g.nbr, g.cnt, k, i);
       bad |= pk < 0;
+      bX = min_image_i(X[k] - Xi, R.LX);
+      bY = min_image_i(Y[k] - Yi, R.LY);
     } else {
       k = jfirst;
       pk = pfirst;
+      bX = fX;
+      bY = fY;
     }
     // triangle (i, j, k) is slot pj-1 around j and slot pk around k
     const int mj = g.cnt[j];
@@ -158,12 +175,15 @@ __device__ __forceinline__ bool net_force(const ForceArgs& g, int i, double& fx_
     const double2 f1 = g.fs[(size_t)bj * N + j];
     const double2 f2 = g.fs[(size_t)(pk < 0 ? 0 : pk) * N + k];
     const double Gx = f0.x + f1.x + f2.x, Gy = f0.y + f1.y + f2.y;
-    const double2 s = g.s[a * N + i], w = g.w[a * N + i];
-    const double c = w.x * Gx + w.y * Gy;
+    const double2 s = g.s[a * N + i];
+    const double wx = i2d_int(bY - aY, -1), wy = i2d_int(aX - bX, -1);
+    const double c = wx * Gx + wy * Gy;
     fx -= s.x * c;
     fy -= s.y * c;
     j = k;
     pj = pk;
+    aX = bX;
+    aY = bY;
   }
   if (bad) raise_status(g.ctl, kETOPO);
   fx_out = fx;
@@ -175,8 +195,9 @@ __device__ __forceinline__ bool net_force(const ForceArgs& g, int i, double& fx_
 // Eq. 3 (integrate 1), or the update alone from the stored forces of the
 // current positions (integrate 2: after a change of v0).
 __global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
-  const int i = blockIdx.x * kForceThreads + threadIdx.x;
-  if (i >= g.n) return;
+  const int item = blockIdx.x * kForceThreads + threadIdx.x;
+  if (item >= g.n) return;
+  const int i = g.order ? g.order[item] : item;
   const size_t N = (size_t)g.n;
   double fx, fy;
   if (g.integrate == 2) {
@@ -206,19 +227,24 @@ __global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
     v0 = g.v0[i];
   }
   const double vx = g.mu * fx + v0 * nd.x, vy = g.mu * fy + v0 * nd.y;
-  const double xn = xi + g.dt * vx, yn = yi + g.dt * vy;
+  const double xn = fma(g.dt, vx, xi), yn = fma(g.dt, vy, yi);
   long long X, Y;
   if (isfinite(xn) && isfinite(yn)) {
-    X = wrap_to_grid(xn, R.Lx, R.scale, R.LX);
-    Y = wrap_to_grid(yn, R.Ly, R.scale, R.LY);
+    if (!R.framed) {
+      X = wrap_to_grid(xn, R.Lx, R.scale, R.LX);
+      Y = wrap_to_grid(yn, R.Ly, R.scale, R.LY);
+    } else {
+      X = move_framed(xi, g.dt, vx, R.x0, R.Lxg, R.scale, R.X0, R.LXg, R.LX);
+      Y = move_framed(yi, g.dt, vy, R.y0, R.Lyg, R.scale, R.Y0, R.LYg, R.LY);
+    }
   } else {
     raise_status(g.ctl, kENONFINITE);
     X = (long long)rint(xi * R.scale);
     Y = (long long)rint(yi * R.scale);
   }
   const int nxt = cur ^ 1;
-  g.x[(size_t)nxt * N + i] = i2d_exact(X) * R.inv_scale;
-  g.y[(size_t)nxt * N + i] = i2d_exact(Y) * R.inv_scale;
+  g.x[(size_t)nxt * N + i] = i2d_int(X, -R.q);
+  g.y[(size_t)nxt * N + i] = i2d_int(Y, -R.q);
   g.X[(size_t)nxt * N + i] = X;
   g.Y[(size_t)nxt * N + i] = Y;
 }
@@ -374,9 +400,51 @@ __global__ void __launch_bounds__(kTestThreads) k_test(TestArgs g) {
   for (int i = blockIdx.x * kTestThreads + threadIdx.x; i < g.n; i += gridDim.x * kTestThreads) test_cell(g, i, X, Y);
 }
 
+// Ring-size grouping of each chunk of kOrderChunk cells (see launch_order):
+// a counting sort by min(cnt, CG_RING) in shared memory.  Ranks within a
+// size come from shared atomics (their order does not matter: every cell's
+// results are computed independently of which thread computes them).
+__global__ void __launch_bounds__(256) k_order(int n, const int* __restrict__ cnt, int* __restrict__ order) {
+  __shared__ int hist[CG_RING + 1], base[CG_RING + 1];
+  const int c0 = blockIdx.x * kOrderChunk;
+  const int len = min(kOrderChunk, n - c0);
+  if (threadIdx.x <= CG_RING) hist[threadIdx.x] = 0;
+  __syncthreads();
+  int msz[kOrderChunk / 256];
+#pragma unroll
+  for (int k = 0; k < kOrderChunk / 256; ++k) {
+    const int c = k * 256 + threadIdx.x;
+    int m = -1;
+    if (c < len) {
+      m = cnt[c0 + c];
+      m = m < 0 ? 0 : (m > CG_RING ? CG_RING : m);
+      atomicAdd(&hist[m], 1);
+    }
+    msz[k] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = 0; b <= CG_RING; ++b) {
+      base[b] = acc;
+      acc += hist[b];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kOrderChunk / 256; ++k) {
+    const int c = k * 256 + threadIdx.x;
+    if (msz[k] >= 0) order[c0 + atomicAdd(&base[msz[k]], 1)] = c0 + c;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
+void launch_order(int n, const int* cnt, int* order, cudaStream_t st) {
+  if (n <= 0) return;
+  k_order<<<(n + kOrderChunk - 1) / kOrderChunk, 256, 0, st>>>(n, cnt, order);
+}
 void launch_geom(const GeomArgs& a, cudaStream_t st, int blocks) {
   if (a.n <= 0) return;
   const int full = (a.n + kGeomThreads - 1) / kGeomThreads;

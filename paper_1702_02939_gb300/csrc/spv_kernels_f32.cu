@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom_f32(GeomArgs g) {
   float2* wv = as_f2(g.w);
   const int total = g.list ? *g.list_count : g.n;
   for (int item = blockIdx.x * kGeomThreads + t; item < total; item += gridDim.x * kGeomThreads) {
-    const int i = g.list ? g.list[item] : item;
+    const int i = g.list ? g.list[item] : (g.order ? g.order[item] : item);
     if (g.list_bits) atomicAnd(&g.list_bits[i >> 5], ~(1u << (i & 31)));
     const Rep R = g.reps[g.rep[i]];
     const float sc = (float)R.inv_scale;
@@ -204,8 +204,9 @@ __device__ __forceinline__ bool net_force_f32(const ForceArgs& g, int i, float& 
 // accumulated in FP64 and rounded to the grid (integrate 2: the move alone
 // from the stored forces, which hold the FP32 values exactly).
 __global__ void __launch_bounds__(kForceThreads) k_force_f32(ForceArgs g) {
-  const int i = blockIdx.x * kForceThreads + threadIdx.x;
-  if (i >= g.n) return;
+  const int item = blockIdx.x * kForceThreads + threadIdx.x;
+  if (item >= g.n) return;
+  const int i = g.order ? g.order[item] : item;
   const size_t N = (size_t)g.n;
   float fx, fy;
   if (g.integrate == 2) {
@@ -231,11 +232,16 @@ __global__ void __launch_bounds__(kForceThreads) k_force_f32(ForceArgs g) {
     v0 = g.v0[i];
   }
   const double vx = g.mu * (double)fx + v0 * nd.x, vy = g.mu * (double)fy + v0 * nd.y;
-  const double xn = xi + g.dt * vx, yn = yi + g.dt * vy;
+  const double xn = fma(g.dt, vx, xi), yn = fma(g.dt, vy, yi);
   long long Xn, Yn;
   if (isfinite(xn) && isfinite(yn)) {
-    Xn = wrap_to_grid(xn, R.Lx, R.scale, R.LX);
-    Yn = wrap_to_grid(yn, R.Ly, R.scale, R.LY);
+    if (!R.framed) {
+      Xn = wrap_to_grid(xn, R.Lx, R.scale, R.LX);
+      Yn = wrap_to_grid(yn, R.Ly, R.scale, R.LY);
+    } else {
+      Xn = move_framed(xi, g.dt, vx, R.x0, R.Lxg, R.scale, R.X0, R.LXg, R.LX);
+      Yn = move_framed(yi, g.dt, vy, R.y0, R.Lyg, R.scale, R.Y0, R.LYg, R.LY);
+    }
   } else {
     raise_status(g.ctl, kENONFINITE);
     Xn = (long long)rint(xi * R.scale);

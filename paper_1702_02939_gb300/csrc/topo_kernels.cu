@@ -652,6 +652,81 @@ void launch_gather_cur_xy(int n, const int* tag, const double* x2, const double*
 void launch_scatter_d(int n, const int* tag, const double* src_user, double* dst, cudaStream_t st) {
   if (n > 0) k_scatter_d<<<(n + 255) / 256, 256, 0, st>>>(n, tag, src_user, dst);
 }
+
+__global__ void k_scatter_i(int n, const int* tag, const int* src, int* dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[tag[i]];
+}
+void launch_scatter_i(int n, const int* tag, const int* src_user, int* dst, cudaStream_t st) {
+  if (n > 0) k_scatter_i<<<(n + 255) / 256, 256, 0, st>>>(n, tag, src_user, dst);
+}
+
+// Halo exchange of a decomposed system.  The exchanged values are the
+// pending positions (position buffer cur ^ 1: where the next step starts),
+// as grid coordinates of the larger box a framed replica belongs to, so a
+// cell's position crosses from one domain's frame to another's exactly.
+// slot[u] (user order) is the cell's place in the message, or -1.
+__global__ void k_halo_pack(int n, const int* tag, const int* slot, const Rep* reps, const int* rep, const Ctl* ctl,
+                            const long long* X2, const long long* Y2, long long* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int s = slot[tag[i]];
+  if (s < 0) return;
+  const size_t nxt = (size_t)(ctl->cur ^ 1) * n + i;
+  const Rep R = reps[rep[i]];
+  long long X = X2[nxt], Y = Y2[nxt];
+  if (R.framed) {
+    X += R.X0;
+    if (X >= R.LXg) X -= R.LXg;
+    Y += R.Y0;
+    if (Y >= R.LYg) Y -= R.LYg;
+  }
+  out[2 * (size_t)s] = X;
+  out[2 * (size_t)s + 1] = Y;
+}
+
+// The received positions replace the pending positions of the listed cells;
+// a position that does not fall inside the replica's frame (a halo cell that
+// drifted out of the domain's box: the halo must be re-partitioned) raises
+// CG_EINVAL and leaves the cell unchanged.
+__global__ void k_halo_unpack(int n, const int* tag, const int* slot, const Rep* reps, const int* rep, Ctl* ctl,
+                              const long long* in, double* x2, double* y2, long long* X2, long long* Y2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int s = slot[tag[i]];
+  if (s < 0) return;
+  const Rep R = reps[rep[i]];
+  long long X = in[2 * (size_t)s], Y = in[2 * (size_t)s + 1];
+  const long long LXo = R.framed ? R.LXg : R.LX, LYo = R.framed ? R.LYg : R.LY;
+  if (X < 0 || X >= LXo || Y < 0 || Y >= LYo) {
+    raise_status(ctl, kEINVAL);
+    return;
+  }
+  if (R.framed) {
+    X -= R.X0;
+    if (X < 0) X += R.LXg;
+    Y -= R.Y0;
+    if (Y < 0) Y += R.LYg;
+  }
+  if (X >= R.LX || Y >= R.LY) {
+    raise_status(ctl, kEINVAL);
+    return;
+  }
+  const size_t nxt = (size_t)(ctl->cur ^ 1) * n + i;
+  X2[nxt] = X;
+  Y2[nxt] = Y;
+  x2[nxt] = i2d_int(X, -R.q);
+  y2[nxt] = i2d_int(Y, -R.q);
+}
+
+void launch_halo_pack(int n, const int* tag, const int* slot, const Rep* reps, const int* rep, const Ctl* ctl,
+                      const long long* X2, const long long* Y2, long long* out, cudaStream_t st) {
+  if (n > 0) k_halo_pack<<<(n + 255) / 256, 256, 0, st>>>(n, tag, slot, reps, rep, ctl, X2, Y2, out);
+}
+void launch_halo_unpack(int n, const int* tag, const int* slot, const Rep* reps, const int* rep, Ctl* ctl,
+                        const long long* in, double* x2, double* y2, long long* X2, long long* Y2, cudaStream_t st) {
+  if (n > 0) k_halo_unpack<<<(n + 255) / 256, 256, 0, st>>>(n, tag, slot, reps, rep, ctl, in, x2, y2, X2, Y2);
+}
 void launch_gather_ring(int n, const int* tag, const int* cnt, const int* nbr, int* cnt_user, int* nbr_user,
                         cudaStream_t st) {
   if (n > 0) k_gather_ring<<<(n + 255) / 256, 256, 0, st>>>(n, tag, cnt, nbr, cnt_user, nbr_user);

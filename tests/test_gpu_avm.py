@@ -464,6 +464,43 @@ def test_divisions_match_oracle():
     sim.close()
 
 
+def test_divisions_in_conflict_match_oracle():
+    """Divisions that touch one another within one call -- the same cell
+    twice, neighbouring cells, the empty slot an earlier division of the call
+    fills -- give the network of doing them one after the other, as the
+    oracle does; and a large call (many cells, few conflicts) as well."""
+    n, cap, p0, v0 = 400, 520, 3.8, 0.05
+    sim, xs, ys, th, Lx, Ly = make(n, 35, p0=p0, v0=v0, t1_threshold=0.04, seed=9, capacity=cap)
+    net = oracle.avm_build(xs, ys, Lx, Ly).with_capacity(cap)
+    theta = np.concatenate([th, np.zeros(cap - n)])
+    pa, va, aa = np.full(cap, p0), np.full(cap, v0), np.ones(cap)
+    g, _ = gpu_net(sim, Lx, Ly)
+    v7 = int(g.cv[7 * R])  # a vertex of cell 7; its other cells are neighbours of 7
+    nb7 = [int(c) for c in g.vc[3 * v7:3 * v7 + 3] if c != 7][0]
+    cells = np.array([7, 7, nb7, n, 7, n, 11, 12, 13, 14, 200, 201, n + 1])
+    rng = np.random.default_rng(4)
+    ang = rng.uniform(0.0, np.pi, len(cells))
+    dirs = np.stack([np.cos(ang), np.sin(ang)], 1)
+    made = sim.divide(cells, dirs)
+    o, theta, pa, va, aa, omade = oracle.avm_divide(net, cells, dirs, theta, pa, va, aa)
+    np.testing.assert_array_equal(made, omade)
+    assert made[3] == 1  # slot n, filled by the first division, was divided in the same call
+    g, gth = gpu_net(sim, Lx, Ly)
+    assert_same_network(g, o)
+    np.testing.assert_array_equal(gth, theta)
+    live = np.nonzero(o.cc > 0)[0]
+    cells = rng.choice(live, 100, replace=False)
+    ang = rng.uniform(0.0, np.pi, 100)
+    dirs = np.stack([np.cos(ang), np.sin(ang)], 1)
+    made = sim.divide(cells, dirs)
+    o, theta, pa, va, aa, omade = oracle.avm_divide(o, cells, dirs, theta, pa, va, aa)
+    np.testing.assert_array_equal(made, omade)
+    g, gth = gpu_net(sim, Lx, Ly)
+    assert_same_network(g, o)
+    check_network_valid(sim, Lx, Ly, p0)
+    sim.close()
+
+
 def test_division_slots_are_checked():
     n = 64
     sim, *_ = make(n, 32, capacity=n + 1)

@@ -341,25 +341,33 @@ def test_repair_cap_status():
 
 
 def test_launch_shapes_do_not_change_results():
-    """Grids of the repair, check and director kernels and the node priorities
-    change timing only: 20 steps agree bit for bit."""
+    """Grids of the repair, check and director kernels, the node priorities
+    and the ring-size grouping of the geometry and force passes change timing
+    only: 20 steps agree bit for bit."""
     n = 4096
     a, *_ = make(n, 33, p0=3.85, v0=0.1, seed=3)
+    assert a.launch["ring_order"] == 1
     b, *_ = make(n, 33, p0=3.85, v0=0.1, seed=3)
     b.set_launch(repair_blocks_per_sm=8, check_blocks_per_sm=4, dir_blocks_per_sm=1, dir_low_priority=1,
-                 geom_blocks_per_sm=2, test_blocks_per_sm=2)
+                 geom_blocks_per_sm=2, test_blocks_per_sm=2, ring_order=0, dir_beside_geom=0)
     assert b.launch["dir_blocks_per_sm"] == 1
     c, *_ = make(n, 33, p0=3.85, v0=0.1, seed=3)
-    c.set_launch(dir_beside_geom=1, dir_low_priority=0, dir_blocks_per_sm=0)
+    c.set_launch(dir_beside_geom=1, dir_low_priority=0, dir_blocks_per_sm=0, ring_order=3)
     assert c.launch["dir_beside_geom"] == 1
+    d, *_ = make(n, 33, p0=3.85, v0=0.1, seed=3)
+    d.set_launch(ring_order=2)
     a.step(20)
     b.step(20)
     c.step(20)
-    for ta, tb, tc in zip(a.state() + a.neighbors(), b.state() + b.neighbors(), c.state() + c.neighbors()):
-        assert torch.equal(ta, tb) and torch.equal(ta, tc)
+    d.step(20)
+    for ta, tb, tc, td in zip(a.state() + a.neighbors() + a.forces()[:2], b.state() + b.neighbors() + b.forces()[:2],
+                              c.state() + c.neighbors() + c.forces()[:2], d.state() + d.neighbors() + d.forces()[:2]):
+        assert torch.equal(ta, tb) and torch.equal(ta, tc) and torch.equal(ta, td)
     with pytest.raises(RuntimeError):
         c.set_launch(dir_beside_geom=2)
-    for s in (a, b, c):
+    with pytest.raises(RuntimeError):
+        c.set_launch(ring_order=4)
+    for s in (a, b, c, d):
         s.close()
 
 
@@ -375,7 +383,7 @@ def test_autotune_takes_no_step_and_keeps_results():
     best, ms = a.autotune(3)
     assert ms > 0 and set(best) == {"repair_blocks_per_sm", "check_blocks_per_sm", "dir_blocks_per_sm",
                                     "dir_low_priority", "geom_blocks_per_sm", "test_blocks_per_sm",
-                                    "dir_beside_geom"}
+                                    "dir_beside_geom", "ring_order"}
     assert a.launch == best
     for t0, t1 in zip(before, a.state()):
         assert torch.equal(t0, t1)
@@ -386,6 +394,27 @@ def test_autotune_takes_no_step_and_keeps_results():
         assert torch.equal(ta, tb)
     a.close()
     b.close()
+
+
+def test_autotune_cache_reuses_a_tuning(tmp_path):
+    """A tuning stored in a cache file is applied by the next context of the
+    same problem class without timing; results stay those of any shapes."""
+    path = str(tmp_path / "launch.json")
+    n = 4096
+    a, *_ = make(n, 36, p0=3.85, v0=0.1, seed=5)
+    best, ms = a.autotune(2, cache=path)
+    assert ms is not None
+    b, *_ = make(n, 36, p0=3.85, v0=0.1, seed=5)
+    again, ms2 = b.autotune(2, cache=path)
+    assert ms2 is None and again == best and b.launch == best
+    c, *_ = make(n, 36, p0=3.85, v0=0.1, seed=5)
+    a.step(5)
+    b.step(5)
+    c.step(5)
+    for ta, tb, tc in zip(a.state(), b.state(), c.state()):
+        assert torch.equal(ta, tb) and torch.equal(ta, tc)
+    for s in (a, b, c):
+        s.close()
 
 
 # FP32 mode (single-precision physics, exact topology).  Bounds from the
