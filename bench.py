@@ -46,8 +46,11 @@ EQUIL_STEPS = 100
 
 # Algorithmic FP64 floating-point operations per cell-step of each kernel
 # (fma = 2, add/mul/div/sqrt/rsqrt = 1, transcendental = 1), for the mean ring
-# size of 6 of a random Voronoi tessellation.  Derivation in the design notes.
-FLOPS_PER_CELL = {"geometry": 342.0, "force_move": 93.0}
+# size of 6 of a random Voronoi tessellation.  Geometry counts each Delaunay
+# circumcentre once (2 triangles per cell x 24, plus 6 ring slots x 36 for
+# the Jacobian factors, area, edges and force sets, plus 13 per cell), not
+# the three times the kernel evaluates it.
+FLOPS_PER_CELL = {"geometry": 277.0, "force_move": 93.0}
 # AVM: per cell of k_avm_cells (12 per polygon vertex x 6: offsets, shoelace
 # term, edge, sqrt, sum; 12 for A, P and the coefficients; 11 for the
 # director terms with sincos, log, sqrt, cos counted as 1 each) and per vertex
@@ -61,7 +64,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # Dominant-kernel DRAM traffic per launch (dram__bytes_read.sum +
 # dram__bytes_write.sum) from one ncu capture of the current k_geom at
 # N = 262144; None whenever the kernel has changed since the capture.
-GEOM_DRAM_BYTES_PER_LAUNCH = 56.95e6
+GEOM_DRAM_BYTES_PER_LAUNCH = 42.54e6
 
 
 def parse():

@@ -141,11 +141,17 @@ __device__ __forceinline__ uint4 philox_10(uint4 c, uint2 k) {
   return c;
 }
 
-// (53 high bits of hi:lo, plus one) * 2^-53, in (0, 1].
-__device__ __forceinline__ double unit53(unsigned hi, unsigned lo) {
-  unsigned long long k = ((((unsigned long long)hi) << 32) | lo) >> 11;
-  return (double)(k + 1ull) * 0x1.0p-53;
+// The 53 high bits of hi:lo, plus one: the uniform (k + 1) 2^-53 in (0, 1]
+// as an integer k + 1 in [1, 2^53].
+__device__ __forceinline__ unsigned long long bits53p1(unsigned hi, unsigned lo) {
+  return (((((unsigned long long)hi) << 32) | lo) >> 11) + 1ull;
 }
+// (k + 1) 2^-53 exactly, on the integer pipes.
+__device__ __forceinline__ double unit53_of(unsigned long long kp1) {
+  return kp1 == (1ull << 53) ? 1.0 : i2d_int((long long)kp1, -53);
+}
+// (53 high bits of hi:lo, plus one) * 2^-53, in (0, 1].
+__device__ __forceinline__ double unit53(unsigned hi, unsigned lo) { return unit53_of(bits53p1(hi, lo)); }
 
 // 1/d to ~1 ulp: hardware reciprocal approximation r = (1 - e)/d refined by
 // one third-order step r (1 + e + e^2), e = 1 - d r (the geometric series of
@@ -177,12 +183,13 @@ __device__ __forceinline__ double director_noise(unsigned long long seed, int ta
   uint4 r = philox_10(make_uint4((unsigned)tag, (unsigned)(unsigned long long)step,
                                  (unsigned)((unsigned long long)step >> 32), 0u),
                       make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
-  double u1 = unit53(r.x, r.y), u2 = unit53(r.z, r.w);
+  const double u1 = unit53(r.x, r.y);
+  const unsigned long long k2 = bits53p1(r.z, r.w);  // u2 = k2 2^-53
   // sqrt(x) as x / sqrt(x) (within 2 ulp; u1 = 1 gives x = -0 and R = 0);
   // cos(2 pi u2) as cos(pi t), t = 2 u2 exact
   const double x = -2.0 * dm_log(u1, tab);
   const double R = (__double_as_longlong(x) > 0) ? x * fast_rsqrt(x) : 0.0;
-  return R * dm_cospi(2.0 * u2, tab);
+  return R * dm_cospi_grid52(k2, tab);  // cos(2 pi u2) = cos(pi k2 2^-52)
 }
 
 // ----------------------------------------------------------------------------
@@ -399,20 +406,6 @@ __device__ __forceinline__ long long move_framed(double xi, double dt, double v,
 // FP64 subtraction removes the offset.
 __device__ __forceinline__ double i2d_exact(long long v) {
   return __longlong_as_double(0x4338000000000000LL + v) - 0x1.8p52;
-}
-
-// Exact v * 2^k as a double for |v| < 2^53 (and a result in the normal
-// range), built on the integer pipes alone: sign, leading-zero count, the
-// leading one shifted to bit 52, the exponent field added on top (the leading
-// one carries into it).  No FP64 instruction: in the geometry kernels the FP64
-// pipe is the bottleneck while the integer pipes are mostly idle.
-__device__ __forceinline__ double i2d_int(long long v, int k = 0) {
-  const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
-  const unsigned long long a = (v < 0) ? (0ull - (unsigned long long)v) : (unsigned long long)v;
-  const int lz = __clzll((long long)a);  // 11 <= lz for |v| < 2^53; 64 for v = 0
-  const unsigned long long m = a << (lz - 11);
-  const unsigned long long e = (unsigned long long)(1022 + 63 - lz + k) << 52;
-  return a ? __longlong_as_double((long long)(sgn | (e + m))) : 0.0;
 }
 
 // Position of cell i in the ring of cell j, or -1.

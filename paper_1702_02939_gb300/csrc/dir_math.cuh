@@ -33,9 +33,21 @@ constexpr int kDirTabEntries = 512;
 constexpr long long kLogOff = 0x3FE6A80000000000LL;
 constexpr int kLogOne = 149;
 
-__device__ __forceinline__ double dm_i2d(long long v) {  // exact for |v| < 2^51
-  return __longlong_as_double(0x4338000000000000LL + v) - 0x1.8p52;
+// Exact v * 2^k as a double for |v| < 2^53 (and a result in the normal
+// range), built on the integer pipes alone: sign, leading-zero count, the
+// leading one shifted to bit 52, the exponent field added on top (the leading
+// one carries into it).  No FP64 instruction: in the geometry kernels the FP64
+// pipe is the bottleneck while the integer pipes are mostly idle.
+__device__ __forceinline__ double i2d_int(long long v, int k = 0) {
+  const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
+  const unsigned long long a = (v < 0) ? (0ull - (unsigned long long)v) : (unsigned long long)v;
+  const int lz = __clzll((long long)a);  // 11 <= lz for |v| < 2^53; 64 for v = 0
+  const unsigned long long m = a << (lz - 11);
+  const unsigned long long e = (unsigned long long)(1022 + 63 - lz + k) << 52;
+  return a ? __longlong_as_double((long long)(sgn | (e + m))) : 0.0;
 }
+
+__device__ __forceinline__ double dm_i2d(long long v) { return i2d_int(v); }  // exact for |v| < 2^53
 
 // sin(r) - r and cos(r) - 1 for |r| <= 0.0125 (Taylor to r^7 and r^6; the
 // first omitted terms are below 2^-70).
@@ -80,6 +92,24 @@ __device__ __forceinline__ double dm_cospi(double t, const double2* __restrict__
   const int j = __double2loint(jm) & 255;
   const double rr = fma(-jd, 0x1p-7, t);   // exact
   const double r = rr * 0x1.921fb54442d18p+1;  // pi
+  double sr, cm;
+  dm_small(r, sr, cm);
+  sr += r;
+  const double2 tt = __ldg(&tab[j]);
+  return tt.y + fma(-tt.x, sr, tt.y * cm);
+}
+
+// cos(pi t) for t = v 2^-52, v in [1, 2^53] (t in (0, 2]) given as the
+// integer v: the reduction t = j/128 + r is done on the integer pipes
+// (j = v / 2^45 rounded to nearest, ties to even, as the FP64 reduction of
+// dm_cospi rounds; r = (v - j 2^45) 2^-52 exactly), then as dm_cospi.
+__device__ __forceinline__ double dm_cospi_grid52(unsigned long long v, const double2* __restrict__ tab) {
+  const unsigned long long half = 1ull << 44;
+  const unsigned long long q = v >> 45, rem = v & ((1ull << 45) - 1);
+  const unsigned long long jr = q + ((rem > half || (rem == half && (q & 1))) ? 1ull : 0ull);
+  const int j = (int)(jr & 255);
+  const double rr = i2d_int((long long)v - (long long)(jr << 45), -52);  // exact, |rr| <= 2^-8
+  const double r = rr * 0x1.921fb54442d18p+1;                            // pi
   double sr, cm;
   dm_small(r, sr, cm);
   sr += r;
