@@ -189,11 +189,12 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def kernels_launched(steps, loop_iterations, eager=False):
-    # per step: force+move, begin-topology, test, 4 cell-list kernels,
-    # directors, geometry of the new state, and (graph only) the geometry
-    # fix-up of repaired cells; per repair round: repair + check
-    return (9 if eager else 10) * steps + 2 * loop_iterations
+def kernels_launched(steps, loop_iterations, eager=False, ring_order=1):
+    # per step: begin-topology, test, 4 cell-list kernels, directors, the
+    # ring-size grouping (if on), geometry of the new state, force + move;
+    # graph only: the geometry fix-up of rewritten rings; per repair round:
+    # repair + check
+    return (9 + (1 if ring_order else 0) + (0 if eager else 1)) * steps + 2 * loop_iterations
 
 
 def host_cpu():
@@ -877,8 +878,10 @@ def run_ours(args):
                            "repair_cap": repair_cap, "launch": "eager" if args.eager else "graph",
                            "launch_shapes": launch, "autotune_ms_per_step": tune_ms},
                 "clocks": clk, "e2e": e2e,
-                "gpu_launches": (kernels_launched(args.steps, args.steps * repair_cap, eager=True) if args.eager
-                                 else kernels_launched(args.steps, counters["loop_total"] - c_start["loop_total"])),
+                "gpu_launches": (kernels_launched(args.steps, args.steps * repair_cap, True, launch["ring_order"])
+                                 if args.eager else
+                                 kernels_launched(args.steps, counters["loop_total"] - c_start["loop_total"], False,
+                                                  launch["ring_order"])),
                 "timed_state": timed_state,
                 "roofline": roofline, "hbm_roofline": hbm, "cpu_baseline": cpu,
                 "phase_ms_per_step": {k: v / prof_steps for k, v in ph.items()},
