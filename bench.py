@@ -405,8 +405,9 @@ def avm_roofline(n, ph, prof_steps):
     achieved = flops / (ms * 1e-3) / 1e12
     return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "note": "FP64 pipe 78-80% busy under ncu: sqrt, sincos, log, cos count one flop "
-                    "each but take many FP64 instructions"}
+            "note": "the per-cell phase is the polygon geometry plus the next step's director terms "
+                    "(beside the T1 passes in the step graph); sqrt, sincos, log, cos count one flop "
+                    "each but take many FP64 instructions; at N = 65536 the passes are latency bound"}
 
 
 def avm_throughput(args, device):
