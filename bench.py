@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--bwd-steps", type=int, default=1000)
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-avm", action="store_true")
+    ap.add_argument("--domains", type=int, default=2, help="strip domains of the decomposed-run section (0: skip)")
+    ap.add_argument("--domain-steps", type=int, default=200)
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--fp32-steps", type=int, default=500)
     ap.add_argument("--avm-steps", type=int, default=500)
@@ -408,6 +410,48 @@ def avm_roofline(n, ph, prof_steps):
             "note": "the per-cell phase is the polygon geometry plus the next step's director terms "
                     "(beside the T1 passes in the step graph); sqrt, sincos, log, cos count one flop "
                     "each but take many FP64 instructions; at N = 65536 the passes are latency bound"}
+
+
+def decomposed_throughput(args, device):
+    """One SPV system advanced as D strip domains in one process on this GPU
+    (the domain decomposition's host protocol with its halo exchange after
+    every step and a re-partition every 50 steps), against one context over
+    the whole box from the same equilibrated state: cell-steps/s of both and
+    whether their states agree bit for bit.  Timed on the host clock around
+    synchronised runs (L2 not flushed)."""
+    import numpy as np
+    import torch
+
+    import paper_1702_02939_gb300 as cg
+    from paper_1702_02939_gb300 import domains
+
+    n, D, steps = args.n, args.domains, args.domain_steps
+    x, y, th, L = workload(n, 1)
+    ref = cg.SPV([dict(n=n, Lx=L, Ly=L, p0=P0, v0=V0)], x, y, th, dt=DT, seed=1, device=device)
+    ref.step(EQUIL_STEPS)
+    x0, y0, t0 = (t.cpu().numpy() for t in ref.state())
+    torch.cuda.synchronize()
+    h0 = time.perf_counter()
+    ref.step(steps)
+    ref.sync()
+    ms_ref = 1e3 * (time.perf_counter() - h0)
+    rx, ry, rt = (t.cpu().numpy() for t in ref.state())
+    ref.close()
+    dd = domains.DecomposedSPV(x0, y0, t0, L, L, D, halo=8.0, p0=P0, v0=V0, repartition_every=50,
+                               step0=EQUIL_STEPS, dt=DT, seed=1, device=device)
+    torch.cuda.synchronize()
+    h0 = time.perf_counter()
+    dd.step(steps)
+    gx, gy, gt = dd.state()
+    ms_dd = 1e3 * (time.perf_counter() - h0)
+    halo = sum(len(p["ids"]) for p in dd.plans) - n
+    dd.close()
+    same = bool(np.array_equal(gx, rx) and np.array_equal(gy, ry) and np.array_equal(gt, rt))
+    return {"workload": WORKLOAD, "domains": D, "steps": steps, "transport": "one process, one GPU",
+            "halo_cells": int(halo), "undivided_cell_steps_per_s": n * steps / (ms_ref * 1e-3),
+            "decomposed_cell_steps_per_s": n * steps / (ms_dd * 1e-3),
+            "decomposed_ms_per_step": ms_dd / steps, "undivided_ms_per_step": ms_ref / steps,
+            "bit_identical_to_undivided": same}
 
 
 def avm_throughput(args, device):
@@ -862,6 +906,9 @@ def run_ours(args):
     backward = None
     if rank == 0 and world == 1 and not args.no_backward:
         backward = backward_cost(args, f"cuda:{local}")
+    decomposed = None
+    if rank == 0 and world == 1 and args.domains >= 2:
+        decomposed = decomposed_throughput(args, f"cuda:{local}")
     avm = None
     if rank == 0 and world == 1 and not args.no_avm:
         avm = avm_throughput(args, f"cuda:{local}")
@@ -886,7 +933,8 @@ def run_ours(args):
                 "timed_state": timed_state,
                 "roofline": roofline, "hbm_roofline": hbm, "cpu_baseline": cpu,
                 "phase_ms_per_step": {k: v / prof_steps for k, v in ph.items()},
-                "counters": counters, "batched": batched, "backward": backward, "avm": avm, "fp32": fp32}
+                "counters": counters, "batched": batched, "backward": backward, "avm": avm, "fp32": fp32,
+                "decomposed": decomposed}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -11,19 +11,31 @@
 // values.  Every coefficient is a Taylor coefficient (1/k!, 1/k); the split of
 // pi/128 and the other constants are derived from pi and ln 2.
 //
-// Accuracy (checked against CUDA's sincos/log/cospi in the tests):
-//   dm_sincos  absolute error <= 4 * 2^-53 for |theta| < 2^20 (CUDA's sincos
-//              beyond, and for non-finite theta);
-//   dm_cospi   absolute error <= 4 * 2^-53 on [0, 2];
-//   dm_log     relative error <= 4 * 2^-53 on (0, 1] (normal numbers).
+// The argument reductions run in FP64 (or, for the Box-Muller cosine, on the
+// integer pipes); the polynomials and the combination with the table run in
+// 64-bit fixed point (Q1.62: value x 2^62 in a signed 64-bit integer; products
+// by the 128-bit integer multiply), rounded to double once at the end.  The
+// integer pipes are mostly idle in the FP64-bound step kernels, and a
+// fixed-point polynomial carries ~2^-60 absolute error against ~2^-53 per
+// FP64 operation.
+//
+// Accuracy (the tests allow 4 units of 2^-53 against numpy and the oracle;
+// an exact-arithmetic check of the same formulas found at most 1 unit for
+// sin/cos, absolute, and 2 units for ln(1 + r), relative):
+//   dm_sincos        for |theta| < 2^20 (CUDA's sincos beyond, and for
+//                    non-finite theta);
+//   dm_cospi_grid52  on (0, 2];
+//   dm_log           on (0, 1] (normal numbers).
 #pragma once
 #include <cuda_runtime.h>
 
 namespace cgk {
 
 // Table layout: 256 entries (sin(j pi/128), cos(j pi/128)), then 256 entries
-// (1/c_j, -ln(1/c_j)) for the logarithm's reduction intervals.
-constexpr int kDirTabEntries = 512;
+// (1/c_j, -ln(1/c_j)) for the logarithm's reduction intervals, then the 256
+// (sin, cos)(j pi/128) again as Q1.62 integers (the doubles times 2^62, exact).
+constexpr int kDirTabEntries = 768;
+constexpr int kDirTabQ = 512;
 
 // The logarithm reduces u = 2^k m with m in [M0, 2 M0), M0 = 0.708 (bit
 // pattern kLogOff), so that ln m never cancels against k ln 2; the octave is
@@ -49,19 +61,61 @@ __device__ __forceinline__ double i2d_int(long long v, int k = 0) {
 
 __device__ __forceinline__ double dm_i2d(long long v) { return i2d_int(v); }  // exact for |v| < 2^53
 
-// sin(r) - r and cos(r) - 1 for |r| <= 0.0125 (Taylor to r^7 and r^6; the
-// first omitted terms are below 2^-70).
-__device__ __forceinline__ void dm_small(double r, double& s_minus_r, double& c_minus_1) {
-  const double r2 = r * r;
-  const double ps = fma(r2, fma(r2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0);
-  s_minus_r = (r * r2) * ps;
-  const double pc = fma(r2, fma(r2, -1.0 / 720.0, 1.0 / 24.0), -0.5);
-  c_minus_1 = r2 * pc;
+// ---- 64-bit fixed point, Q1.62 ----
+constexpr long long kQOne = 1LL << 62;
+// round(2^62 / d)
+__host__ __device__ constexpr long long qdiv(long long d) { return (kQOne + d / 2) / d; }
+// a b in Q1.62 (|a b| < 2), the product truncated toward minus infinity
+__device__ __forceinline__ long long mulq(long long a, long long b) {
+  return (long long)(((__int128)a * (__int128)b) >> 62);
+}
+// x 2^62 for |x| < 2, truncated toward zero, on the integer pipes
+__device__ __forceinline__ long long d2q(double x) {
+  const long long b = __double_as_longlong(x);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  if (ef == 0) return 0;  // zero (or subnormal, below 2^-1022)
+  const long long m = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+  const int sh = ef - 1023 + 10;  // m 2^(e - 52) 2^62
+  const long long v = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0);
+  return b < 0 ? -v : v;
+}
+// v 2^k rounded to the nearest double (ties to even), any int64 v, on the
+// integer pipes: the leading bits kept, the dropped ones rounded (a carry out
+// of the mantissa lands in the exponent field)
+__device__ __forceinline__ double q2d(long long v, int k) {
+  const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ull;
+  const unsigned long long a = (v < 0) ? (0ull - (unsigned long long)v) : (unsigned long long)v;
+  if (!a) return 0.0;
+  const int lz = __clzll((long long)a);
+  const int nb = 64 - lz;  // significant bits
+  unsigned long long m;
+  if (nb <= 53) {
+    m = a << (53 - nb);
+  } else {
+    const int sh = nb - 53;
+    m = a >> sh;
+    const unsigned long long rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m & 1))) m += 1;
+  }
+  const unsigned long long e = (unsigned long long)(1022 + nb - 1 + k) << 52;
+  return __longlong_as_double((long long)(sgn | (e + m)));
+}
+
+// sin(r) and cos(r) - 1 in Q1.62 for r (Q1.62) with |r| <= 0.0125 (Taylor to
+// r^7 and r^6; the first omitted terms are below 2^-70).
+__device__ __forceinline__ void dm_small_q(long long r, long long& s, long long& c_minus_1) {
+  const long long r2 = mulq(r, r);
+  const long long ps = -qdiv(6) + mulq(r2, qdiv(120) - mulq(r2, qdiv(5040)));
+  s = r + mulq(mulq(r2, r), ps);
+  const long long pc = -(kQOne / 2) + mulq(r2, qdiv(24) - mulq(r2, qdiv(720)));
+  c_minus_1 = mulq(r2, pc);
 }
 
 // (sin theta, cos theta).  theta = j pi/128 + r with j = rint(128 theta / pi)
-// and r by a three-term Cody-Waite reduction (the first two parts of pi/128
-// carry 27 significant bits, so j * part is exact for |j| < 2^26).
+// and r by a three-term Cody-Waite reduction in FP64 (the first two parts of
+// pi/128 carry 27 significant bits, so j * part is exact for |j| < 2^26);
+// sin r, cos r - 1 and the combination with the table in fixed point:
+// sin(a + r) = S + S (cos r - 1) + C sin r, cos(a + r) = C + C (cos r - 1) - S sin r.
 __device__ __forceinline__ void dm_sincos(double th, const double2* __restrict__ tab, double& s, double& c) {
   if (!((__double_as_longlong(th) & 0x7FFFFFFFFFFFFFFFLL) < 0x4130000000000000LL)) {  // |theta| >= 2^20 or NaN
     sincos(th, &s, &c);
@@ -74,52 +128,36 @@ __device__ __forceinline__ void dm_sincos(double th, const double2* __restrict__
   double r = fma(-jd, 0x1.921fb54000000p-6, th);  // pi/128, part 1
   r = fma(-jd, 0x1.10b4610000000p-36, r);          // part 2
   r = fma(-jd, 0x1.a62633145c06ep-64, r);          // part 3
-  double sr, cm;
-  dm_small(r, sr, cm);
-  sr += r;
-  const double2 t = __ldg(&tab[j]);  // (S, C) = (sin, cos)(j pi/128)
-  // sin(a + r) = S + (S (cos r - 1) + C sin r), cos(a + r) = C + (C (cos r - 1) - S sin r)
-  s = t.x + fma(t.y, sr, t.x * cm);
-  c = t.y + fma(-t.x, sr, t.y * cm);
-}
-
-// cos(pi t) for t in [0, 2]: t = j/128 + r exactly (t is a multiple of
-// 2^-52), then the angle pi r.
-__device__ __forceinline__ double dm_cospi(double t, const double2* __restrict__ tab) {
-  const double kMagic = 0x1.8p52;
-  const double jm = fma(t, 128.0, kMagic);
-  const double jd = jm - kMagic;
-  const int j = __double2loint(jm) & 255;
-  const double rr = fma(-jd, 0x1p-7, t);   // exact
-  const double r = rr * 0x1.921fb54442d18p+1;  // pi
-  double sr, cm;
-  dm_small(r, sr, cm);
-  sr += r;
-  const double2 tt = __ldg(&tab[j]);
-  return tt.y + fma(-tt.x, sr, tt.y * cm);
+  long long sr, cm;
+  dm_small_q(d2q(r), sr, cm);
+  const longlong2 t = __ldg(reinterpret_cast<const longlong2*>(tab + kDirTabQ) + j);  // (S, C) in Q1.62
+  s = q2d(t.x + mulq(t.x, cm) + mulq(t.y, sr), -62);
+  c = q2d(t.y + mulq(t.y, cm) - mulq(t.x, sr), -62);
 }
 
 // cos(pi t) for t = v 2^-52, v in [1, 2^53] (t in (0, 2]) given as the
-// integer v: the reduction t = j/128 + r is done on the integer pipes
-// (j = v / 2^45 rounded to nearest, ties to even, as the FP64 reduction of
-// dm_cospi rounds; r = (v - j 2^45) 2^-52 exactly), then as dm_cospi.
+// integer v, on the integer pipes: t = j/128 + r with j = v / 2^45 rounded to
+// nearest (ties to even) and r = (v - j 2^45) 2^-52 exactly, |r| <= 2^-8;
+// the angle pi r in Q1.62 from pi in Q2.61; then as dm_sincos.
 __device__ __forceinline__ double dm_cospi_grid52(unsigned long long v, const double2* __restrict__ tab) {
   const unsigned long long half = 1ull << 44;
   const unsigned long long q = v >> 45, rem = v & ((1ull << 45) - 1);
   const unsigned long long jr = q + ((rem > half || (rem == half && (q & 1))) ? 1ull : 0ull);
   const int j = (int)(jr & 255);
-  const double rr = i2d_int((long long)v - (long long)(jr << 45), -52);  // exact, |rr| <= 2^-8
-  const double r = rr * 0x1.921fb54442d18p+1;                            // pi
-  double sr, cm;
-  dm_small(r, sr, cm);
-  sr += r;
-  const double2 tt = __ldg(&tab[j]);
-  return tt.y + fma(-tt.x, sr, tt.y * cm);
+  const long long rr = (long long)v - (long long)(jr << 45);  // r 2^52, |rr| <= 2^44
+  const long long kPiQ61 = 0x6487ED5110B4611ALL;             // round(pi 2^61)
+  const long long rq = (long long)(((__int128)rr * kPiQ61) >> 51);  // pi r 2^62
+  long long sr, cm;
+  dm_small_q(rq, sr, cm);
+  const longlong2 tt = __ldg(reinterpret_cast<const longlong2*>(tab + kDirTabQ) + j);
+  return q2d(tt.y + mulq(tt.y, cm) - mulq(tt.x, sr), -62);
 }
 
 // ln u for a positive normal u: u = 2^k m, m in [M0, 2 M0).  With c_j the
 // centre of m's interval, ln m = -ln(1/c_j) + ln(1 + r) where r = m (1/c_j) - 1
-// is formed in one rounding (|r| <= 2^-9); ln(1 + r) by Taylor to r^7.
+// is formed in one FP64 rounding (|r| <= 2^-9); ln(1 + r) = r P(r) with
+// P(r) = 1 - r/2 + r^2/3 - ... + r^6/7 (Taylor to r^7) in fixed point, so that
+// r P keeps full relative precision when u is near 1 (r tiny, c_j = 1).
 __device__ __forceinline__ double dm_log(double u, const double2* __restrict__ tab) {
   const long long b = __double_as_longlong(u);
   const long long d = b - kLogOff;
@@ -128,12 +166,15 @@ __device__ __forceinline__ double dm_log(double u, const double2* __restrict__ t
   const double m = __longlong_as_double(b - (k << 52));
   const double2 t = __ldg(&tab[256 + j]);  // (1/c_j, -ln(1/c_j))
   const double r = fma(m, t.x, -1.0);
-  double q = fma(r, 1.0 / 7.0, -1.0 / 6.0);
-  q = fma(r, q, 1.0 / 5.0);
-  q = fma(r, q, -0.25);
-  q = fma(r, q, 1.0 / 3.0);
-  q = fma(r, q, -0.5);
-  const double l1p = fma(r * r, q, r);
+  const long long rq = d2q(r);
+  long long p = qdiv(7);
+  p = -qdiv(6) + mulq(rq, p);
+  p = qdiv(5) + mulq(rq, p);
+  p = -(kQOne / 4) + mulq(rq, p);
+  p = qdiv(3) + mulq(rq, p);
+  p = -(kQOne / 2) + mulq(rq, p);
+  p = kQOne + mulq(rq, p);
+  const double l1p = r * q2d(p, -62);
   return fma(dm_i2d(k), 0x1.62e42fefa39efp-1, t.y + l1p);  // + k ln 2
 }
 

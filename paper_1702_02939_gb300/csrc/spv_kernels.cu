@@ -281,7 +281,11 @@ __global__ void k_init_dir_tables(double2* tab) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < 256) {
     tab[j] = make_double2(sinpi(j / 128.0), cospi(j / 128.0));
-  } else if (j < kDirTabEntries) {
+  } else if (j >= kDirTabQ && j < kDirTabQ + 256) {
+    // the same values in Q1.62 (exact: every nonzero entry is above 2^-10)
+    const double sn = sinpi((j - kDirTabQ) / 128.0), cs = cospi((j - kDirTabQ) / 128.0);
+    reinterpret_cast<longlong2*>(tab)[j] = make_longlong2(__double2ll_rn(sn * 0x1p62), __double2ll_rn(cs * 0x1p62));
+  } else if (j < kDirTabQ) {
     const int i = j - 256;
     const double inv =
         (i == kLogOne) ? 1.0 : 1.0 / __longlong_as_double(kLogOff + ((long long)i << 44) + (1LL << 43));
