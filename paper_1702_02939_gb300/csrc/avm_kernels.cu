@@ -211,7 +211,7 @@ __global__ void k_avm_cells(AvmArgs g) {
     }
     area = fma(-qx, py, fma(px, qy, area));
     const double l2 = (qx - px) * (qx - px) + (qy - py) * (qy - py);
-    per = (__double_as_longlong(l2) > 0) ? fma(l2, fast_rsqrt(l2), per) : per;  // sqrt(l2)
+    per = (__double_as_longlong(l2) > 0) ? fma(l2, fx_rsqrt(l2), per) : per;  // sqrt(l2)
     px = qx;
     py = qy;
   }
@@ -259,7 +259,7 @@ __global__ void k_avm_force_move(AvmArgs g) {
       const int w = g.vn[3 * v + k];
       ux[k] = mimg_a(hx[w] - xv, g.ax);
       uy[k] = mimg_a(hy[w] - yv, g.ay);
-      const double il = fast_rsqrt(ux[k] * ux[k] + uy[k] * uy[k]);
+      const double il = fx_rsqrt(ux[k] * ux[k] + uy[k] * uy[k]);
       nx[k] = ux[k] * il;
       ny[k] = uy[k] * il;
     }

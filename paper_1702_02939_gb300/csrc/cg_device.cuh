@@ -175,6 +175,51 @@ __device__ __forceinline__ double fast_rsqrt(double x) {
   return fma(y * e, fma(e, 0.375, 0.5), y);
 }
 
+// 1/d and 1/sqrt(x) with the refinement on the integer pipes: the mantissa
+// (53 bits) in fixed point, an FP32 hardware seed (rcp/rsqrt.approx of the
+// mantissa's top 23 bits, relative error ~2^-22), one third-order step in
+// Q1.62 (r (1 + e + e^2) with e = 1 - m r; y (1 + e/2 + 3 e^2/8) with
+// e = 1 - m y^2; the error left is ~e^3 ~ 2^-66), and one rounding to double
+// with the exponent put back: within 1 ulp, like fast_rcp / fast_rsqrt, with
+// no FP64 instruction.  Zero, subnormal, infinite and NaN inputs take the
+// FP64 functions.
+__device__ __forceinline__ long long seed_q62(float yf) {  // yf in (0.5, 1]: yf 2^62
+  const int b = __float_as_int(yf);
+  const long long mant = (long long)((b & 0x7fffff) | 0x800000);
+  return mant << (39 + ((b >> 23) & 0xff) - 127);  // 62 - 23 + exponent (0 or -1)
+}
+__device__ __forceinline__ double fx_rcp(double d) {
+  const long long b = __double_as_longlong(d);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  if (ef == 0 || ef == 0x7ff) return fast_rcp(d);
+  const long long m = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;  // mantissa in [1, 2) times 2^52
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff))));
+  long long y = seed_q62(yf);
+  const long long e = kQOne - mulq(m << 10, y);  // 1 - m y
+  y += mulq(y, e + mulq(e, e));
+  const double r = q2d(y, -62 - (ef - 1023));
+  return b < 0 ? -r : r;
+}
+__device__ __forceinline__ double fx_rsqrt(double x) {
+  const long long b = __double_as_longlong(x);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  if (ef == 0 || ef == 0x7ff || b < 0) return fast_rsqrt(x);
+  const int E = ef - 1023, odd = E & 1;
+  const long long m = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+  // x = m' 2^(E - odd) with m' = m 2^(odd - 52) in [1, 4), held as m' 2^61
+  const long long mq61 = m << (9 + odd);
+  float yf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;"
+      : "=f"(yf)
+      : "f"(__int_as_float((odd ? 0x40000000 : 0x3f800000) | (int)((b >> 29) & 0x7fffff))));
+  long long y = seed_q62(yf);
+  const long long my2 = (long long)(((__int128)mq61 * mulq(y, y)) >> 61);  // m' y^2 in Q1.62
+  const long long e = kQOne - my2;
+  y += mulq(y, mulq(e, (kQOne >> 1) + mulq(e, 3 * (kQOne >> 3))));
+  return q2d(y, -62 - (E - odd) / 2);
+}
+
 // Standard normal for (seed, cell tag, step), cosine branch of Box-Muller,
 // with the table-driven ln and cos(pi .) of dir_math.cuh (tab: the 512-entry
 // director table).

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
         bx = d0x; by = d0y; lb = l0;
       }
       const double det = ax * by - ay * bx;  // (r_j - r_i) x (r_k - r_i)
-      const double r = fast_rcp(det);
+      const double r = fx_rcp(det);
       // doubled circumcentre relative to r_i
       const double hx = (by * la - ay * lb) * r;
       const double hy = (ax * lb - bx * la) * r;
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
         area = fma(-hx, hpy, fma(hpx, hy, area));  // shoelace term, two FMAs
         const double ex = hx - hpx, ey = hy - hpy;
         const double l2 = ex * ex + ey * ey;
-        const double il = (__double_as_longlong(l2) > 0) ? fast_rsqrt(l2) : 0.0;  // zero-length edge: no direction
+        const double il = (__double_as_longlong(l2) > 0) ? fx_rsqrt(l2) : 0.0;  // zero-length edge: no direction
         per += l2 * il;
         sh_ex[a][t] = ex * il;
         sh_ey[a][t] = ey * il;
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
       area = fma(-h0x, hpy, fma(hpx, h0y, area));
       const double ex = h0x - hpx, ey = h0y - hpy;
       const double l2 = ex * ex + ey * ey;
-      const double il = (__double_as_longlong(l2) > 0) ? fast_rsqrt(l2) : 0.0;  // zero-length edge: no direction
+      const double il = (__double_as_longlong(l2) > 0) ? fx_rsqrt(l2) : 0.0;  // zero-length edge: no direction
       per += l2 * il;
       sh_ex[0][t] = ex * il;
       sh_ey[0][t] = ey * il;
