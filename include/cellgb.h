@@ -120,10 +120,10 @@ typedef struct cg_launch {
                                     geometry pass (both FP64; one fills the other's idle FP64
                                     cycles); 0: before it on the same branch (default 1 in FP64,
                                     0 in FP32) */
-  int32_t ring_order;            /* bit 0: the geometry pass, bit 1: the force pass takes the cells
-                                    regrouped by ring size within chunks of 1024 cells, so that the
-                                    lanes of a warp run the same number of ring slots (default 1 in
-                                    FP64, 0 in FP32) */
+  int32_t ring_order;            /* bit 0: the geometry pass, bit 1: the force pass, bit 2: the
+                                    circumcircle test takes the cells regrouped by ring size within
+                                    chunks of 1024 cells, so that the lanes of a warp run the same
+                                    number of ring slots (0..7; default 5 in FP64, 0 in FP32) */
 } cg_launch;
 
 /* Workspace size for R replicas. */

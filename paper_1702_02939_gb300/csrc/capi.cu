@@ -190,7 +190,7 @@ struct cg_ctx {
   // cg_run_io: copy streams and the events that order the double-buffered staging
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t in_ready[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_free[2] = {};
-  cg_launch launch{4, 4, 4, 1, 0, 8, 1, 1};    // launch shapes of the step graph
+  cg_launch launch{4, 4, 4, 1, 0, 8, 1, 5};    // launch shapes of the step graph
   std::vector<cg_replica> user_reps;           // as passed to cg_create
   cudaGraphExec_t step_exec = nullptr;
   int graph_steps = 0;
@@ -331,6 +331,7 @@ TestArgs test_args(cg_ctx* c) {
   t.tag = c->at<int>(c->off.tag);
   t.flags = c->at<unsigned>(c->off.flags);
   t.list = c->at<int>(c->off.list0);
+  t.order = (c->launch.ring_order & 4) ? c->at<int>(c->off.order) : nullptr;
   return t;
 }
 
@@ -474,9 +475,6 @@ void enqueue_step_prefix(cg_ctx* c, cudaStream_t st) {
   cudaEventRecord(c->fork, st);
   cudaStreamWaitEvent(c->side[0], c->fork, 0);
   cudaStreamWaitEvent(c->side[1], c->fork, 0);
-  // the ring-size grouping from the rings of the previous step, first on the
-  // geometry branch (before any repair round can rewrite a ring)
-  if (c->launch.ring_order) run_order(c, c->side[0]);
   if (c->launch.dir_beside_geom) {
     cudaStreamWaitEvent(c->side[2], c->fork, 0);
     run_dir(c, dir_args_step(c), c->side[2], dir_grid(c));
@@ -502,9 +500,20 @@ void enqueue_step_suffix(cg_ctx* c, cudaStream_t st) {
   g.list = c->at<int>(c->off.dirty_list);
   g.list_count = &c->ctl()->dirty_count;
   g.list_bits = c->at<unsigned>(c->off.dirty_bits);
-  run_geom(c, g, st, sm_count() * 2);
+  // one warp per rewritten ring (about 1% of the cells per step): every cell
+  // of the list at once rather than a few per warp one after another
+  run_geom(c, g, st, sm_count() * 16);
   if (c->launch.dir_beside_geom) cudaStreamWaitEvent(st, c->join_terms, 0);
+  if (c->launch.ring_order) {
+    // the ring-size grouping of the next step, from the rings this step
+    // leaves, beside the force pass (both only read the rings)
+    cudaEventRecord(c->fork, st);
+    cudaStreamWaitEvent(c->side[0], c->fork, 0);
+    run_order(c, c->side[0]);
+    cudaEventRecord(c->join_dir, c->side[0]);
+  }
   run_force(c, force_args(c, 1), st);
+  if (c->launch.ring_order) cudaStreamWaitEvent(st, c->join_dir, 0);
 }
 
 // Director terms, geometry, force sets and the pending move of the current
@@ -747,9 +756,10 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
     delete c;
     return CG_EINVAL;
   }
-  // FP64 defaults (measured at N = 262144): the geometry pass in ring-size
-  // groups (it is bound by the FP64 pipe, where idle lanes cost most) with the
-  // director terms on a branch of their own beside it.  The FP32 kernels gain
+  // FP64 defaults (measured at N = 262144): the geometry pass and the
+  // circumcircle test in ring-size groups (the geometry pass is bound by the
+  // FP64 pipe, where idle lanes cost most) with the director terms on a
+  // branch of their own beside the geometry.  The FP32 kernels gain
   // more from the plain (coalesced) order and keep the director terms first
   // on the geometry branch.
   if (c->par.precision == 1) {
@@ -1132,7 +1142,7 @@ int cg_set_launch(cg_ctx* c, const cg_launch* l) {
       l->check_blocks_per_sm > 64 || l->dir_blocks_per_sm < 0 || l->dir_blocks_per_sm > 64 ||
       (l->dir_low_priority != 0 && l->dir_low_priority != 1) || l->geom_blocks_per_sm < 0 ||
       l->geom_blocks_per_sm > 64 || l->test_blocks_per_sm < 0 || l->test_blocks_per_sm > 64 ||
-      (l->dir_beside_geom != 0 && l->dir_beside_geom != 1) || l->ring_order < 0 || l->ring_order > 3)
+      (l->dir_beside_geom != 0 && l->dir_beside_geom != 1) || l->ring_order < 0 || l->ring_order > 7)
     return CG_EINVAL;
   int rc = read_status(c);
   if (rc) return rc;
@@ -1217,7 +1227,7 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
   static const int geom_opts[] = {0, 4, 8, 16};
   static const int test_opts[] = {0, 2, 4, 8};
   static const int beside_opts[] = {0, 1};
-  static const int order_opts[] = {0, 1, 2, 3};
+  static const int order_opts[] = {0, 1, 4, 5};
   const cg_launch start = c->launch;
   cg_launch cur = start;
   double cur_ms = 0.0;

@@ -175,6 +175,38 @@ __device__ __forceinline__ double fast_rsqrt(double x) {
   return fma(y * e, fma(e, 0.375, 0.5), y);
 }
 
+// A 128-bit integer rounded to the nearest double (ties to even), on the
+// integer pipes: the magnitude shifted so that its leading one is bit 127,
+// its top 64 bits rounded to 53 with a sticky bit for the rest (a carry out
+// of the mantissa lands in the exponent field).
+__device__ __forceinline__ double i128_to_double(__int128 v) {
+  const bool neg = v < 0;
+  const unsigned __int128 a = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+  const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+  int nb;  // significant bits
+  unsigned long long top;
+  bool sticky;
+  if (hi) {
+    const int lz = __clzll((long long)hi);
+    nb = 128 - lz;
+    const unsigned __int128 sh = a << lz;
+    top = (unsigned long long)(sh >> 64);
+    sticky = (unsigned long long)sh != 0;
+  } else if (lo) {
+    const int lz = __clzll((long long)lo);
+    nb = 64 - lz;
+    top = lo << lz;
+    sticky = false;
+  } else {
+    return 0.0;
+  }
+  unsigned long long m = top >> 11;
+  const unsigned long long rem = top & 0x7ff;
+  if (rem > 0x400 || (rem == 0x400 && (sticky || (m & 1)))) m += 1;
+  const unsigned long long bits = ((unsigned long long)(nb + 1021) << 52) + m;
+  return __longlong_as_double((long long)(bits | (neg ? 0x8000000000000000ull : 0ull)));
+}
+
 // 1/d and 1/sqrt(x) with the refinement on the integer pipes: the mantissa
 // (53 bits) in fixed point, an FP32 hardware seed (rcp/rsqrt.approx of the
 // mantissa's top 23 bits, relative error ~2^-22), one third-order step in

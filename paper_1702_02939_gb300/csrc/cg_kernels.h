@@ -105,6 +105,7 @@ struct TestArgs {
   const int *cnt, *nbr, *tag;
   unsigned* flags;
   int* list;  // list 0
+  const int* order;  // processing order of the cells (as GeomArgs), or null
 };
 
 struct CellListArgs {

@@ -61,24 +61,32 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
       return ((unsigned)j < (unsigned)g.n) ? j : i;
     };
 
+    // squared lengths and the triangle determinants exactly in 128-bit
+    // integers from the grid offsets, each rounded to double once
     const int j0 = nb(0);
-    const double d0x = i2d_int(min_image_i(X[j0] - Xi, R.LX));
-    const double d0y = i2d_int(min_image_i(Y[j0] - Yi, R.LY));
-    const double l0 = d0x * d0x + d0y * d0y;
+    const long long D0X = min_image_i(X[j0] - Xi, R.LX), D0Y = min_image_i(Y[j0] - Yi, R.LY);
+    const double d0x = i2d_int(D0X), d0y = i2d_int(D0Y);
+    const double l0 = i128_to_double((__int128)D0X * D0X + (__int128)D0Y * D0Y);
     double ax = d0x, ay = d0y, la = l0;
+    long long AX = D0X, AY = D0Y;
     double hpx = 0.0, hpy = 0.0, h0x = 0.0, h0y = 0.0;
     double area = 0.0, per = 0.0;
     for (int a = 0; a < m; ++a) {
       double bx, by, lb;
+      long long BX, BY;
       if (a + 1 < m) {
         const int j = nb(a + 1);
-        bx = i2d_int(min_image_i(X[j] - Xi, R.LX));
-        by = i2d_int(min_image_i(Y[j] - Yi, R.LY));
-        lb = bx * bx + by * by;
+        BX = min_image_i(X[j] - Xi, R.LX);
+        BY = min_image_i(Y[j] - Yi, R.LY);
+        bx = i2d_int(BX);
+        by = i2d_int(BY);
+        lb = i128_to_double((__int128)BX * BX + (__int128)BY * BY);
       } else {
+        BX = D0X; BY = D0Y;
         bx = d0x; by = d0y; lb = l0;
       }
-      const double det = ax * by - ay * bx;  // (r_j - r_i) x (r_k - r_i)
+      // (r_j - r_i) x (r_k - r_i)
+      const double det = i128_to_double((__int128)AX * BY - (__int128)AY * BX);
       const double r = fx_rcp(det);
       // doubled circumcentre relative to r_i
       const double hx = (by * la - ay * lb) * r;
@@ -99,6 +107,7 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
       }
       hpx = hx; hpy = hy;
       ax = bx; ay = by; la = lb;
+      AX = BX; AY = BY;
     }
     {  // closing edge h_{m-1} -> h_0 is the incoming edge of vertex 0
       area = fma(-h0x, hpy, fma(hpx, h0y, area));
@@ -401,7 +410,8 @@ __global__ void __launch_bounds__(kTestThreads) k_test(TestArgs g) {
   const int cur = g.ctl->cur;
   const long long* __restrict__ X = g.X + (size_t)cur * N;
   const long long* __restrict__ Y = g.Y + (size_t)cur * N;
-  for (int i = blockIdx.x * kTestThreads + threadIdx.x; i < g.n; i += gridDim.x * kTestThreads) test_cell(g, i, X, Y);
+  for (int item = blockIdx.x * kTestThreads + threadIdx.x; item < g.n; item += gridDim.x * kTestThreads)
+    test_cell(g, g.order ? g.order[item] : item, X, Y);
 }
 
 // Ring-size grouping of each chunk of kOrderChunk cells (see launch_order):
