@@ -64,7 +64,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # Dominant-kernel DRAM traffic per launch (dram__bytes_read.sum +
 # dram__bytes_write.sum) from one ncu capture of the current k_geom at
 # N = 262144; None whenever the kernel has changed since the capture.
-GEOM_DRAM_BYTES_PER_LAUNCH = None
+GEOM_DRAM_BYTES_PER_LAUNCH = 42.66e6
 
 
 def parse():
@@ -92,6 +92,8 @@ def parse():
     ap.add_argument("--avm-warmup", type=int, default=100)
     ap.add_argument("--avm-profile-steps", type=int, default=20)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--retune", action="store_true",
+                    help="tune the launch shapes afresh instead of taking the stored ones")
     ap.add_argument("--eager", action="store_true",
                     help="launch every kernel of the step eagerly instead of replaying the step graph "
                          "(same kernels and results; for kernel-level profilers)")
@@ -101,6 +103,16 @@ def parse():
     ap.add_argument("--avm-only", action="store_true",
                     help="run only the AVM section and print its JSON object (a diagnostic, not the bench line)")
     return ap.parse_args()
+
+
+def launch_cache(args):
+    """The persisted launch shapes (tuned per GPU model and problem class)
+    unless --retune asks for a fresh tuning pass (which does not write)."""
+    if args.retune:
+        return None
+    import paper_1702_02939_gb300 as cg
+
+    return cg.LAUNCH_CACHE
 
 
 def dist_env():
@@ -267,7 +279,7 @@ def batched_comparison(args, device):
     fused = cg.SPV(reps, np.concatenate(xs), np.concatenate(ys), np.concatenate(ths), dt=DT, seed=7,
                    device=device)
     fused.step(EQUIL_STEPS)
-    launch, _ = fused.autotune(5) if not args.no_autotune else (fused.launch, None)
+    launch, _ = fused.autotune(5, cache=launch_cache(args)) if not args.no_autotune else (fused.launch, None)
     timed = total_steps - EQUIL_STEPS
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(timed)]
     torch.cuda.synchronize()
@@ -374,7 +386,8 @@ def fp32_throughput(args, device):
     sim.set_step(EQUIL_STEPS + args.warmup)
     sim.step(10)
     sim.sync()
-    launch, _ = sim.autotune(10, flush_bytes=FLUSH_BYTES) if not args.no_autotune else (sim.launch, None)
+    launch, _ = (sim.autotune(10, flush_bytes=FLUSH_BYTES, cache=launch_cache(args)) if not args.no_autotune
+                 else (sim.launch, None))
     stream = torch.cuda.current_stream()
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
     K = args.fp32_steps
@@ -801,7 +814,9 @@ def run_ours(args):
     advance(args.warmup)
     sim.sync()
     # tuned under the timing conditions of the timed region (L2 evicted before each step)
-    launch, tune_ms = (sim.autotune(10, flush_bytes=FLUSH_BYTES) if not args.no_autotune else (sim.launch, None))
+    launch, tune_ms = (sim.autotune(10, flush_bytes=FLUSH_BYTES, cache=launch_cache(args)) if not args.no_autotune
+                       else (sim.launch, None))
+    launch_source = "default" if args.no_autotune else ("stored" if tune_ms is None else "tuned")
     # the state the timed region starts from: the end-to-end run replays the same steps from it
     x0, y0, th0 = sim.state()
     step0 = sim.counters()["steps"]
@@ -924,7 +939,8 @@ def run_ours(args):
                            "equilibration_steps": EQUIL_STEPS,
                            "replicas_per_gpu": 1, "l2": "flushed between timed steps (256 MB write)",
                            "repair_cap": repair_cap, "launch": "eager" if args.eager else "graph",
-                           "launch_shapes": launch, "autotune_ms_per_step": tune_ms},
+                           "launch_shapes": launch, "launch_source": launch_source,
+                           "autotune_ms_per_step": tune_ms},
                 "clocks": clk, "e2e": e2e,
                 "gpu_launches": (kernels_launched(args.steps, args.steps * repair_cap, True, launch["ring_order"])
                                  if args.eager else

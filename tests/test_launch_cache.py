@@ -28,3 +28,23 @@ def test_cache_file_round_trip(tmp_path):
     with open(path, "w") as f:
         json.dump([1, 2], f)
     assert cg._read_launch_cache(path) == {}
+
+
+def test_shipped_cache_holds_complete_valid_shapes():
+    """Every stored entry names each launch field once, within the ranges
+    cg_set_launch accepts, under a well-formed key."""
+    data = cg._read_launch_cache(cg.LAUNCH_CACHE)
+    assert data, "the package ships tuned shapes"
+    fields = {f for f, _ in cg.cg_launch._fields_}
+    for key, shape in data.items():
+        gpu, prec, rb, nb, l2 = key.split("|")
+        assert gpu and prec in ("f32", "f64") and l2 in ("l2cold", "l2warm")
+        assert rb.startswith("R~") and nb.startswith("N~")
+        for b in (int(rb[2:]), int(nb[2:])):
+            assert b >= 1 and b & (b - 1) == 0
+        assert set(shape) == fields
+        assert 1 <= shape["repair_blocks_per_sm"] <= 64 and 1 <= shape["check_blocks_per_sm"] <= 64
+        for f in ("dir_blocks_per_sm", "geom_blocks_per_sm", "test_blocks_per_sm"):
+            assert 0 <= shape[f] <= 64
+        assert shape["dir_low_priority"] in (0, 1) and shape["dir_beside_geom"] in (0, 1)
+        assert 0 <= shape["ring_order"] <= 7
