@@ -395,6 +395,8 @@ typedef struct cg_avm_params {
   int32_t cell_capacity; /* cell slots, >= N (0: N); divisions fill empty cell
                             slots and free vertex slots, lowest first */
   double t2_area;       /* triangular cells with area below this are removed (T2); 0: none */
+  int32_t sort_every;   /* Hilbert re-sort of the vertex and cell storage at creation and every
+                           sort_every steps (Sec. 2.B); 0: never.  Results are the same either way */
 } cg_avm_params;
 
 /* Workspace size for an N-cell network in an Lx x Ly box. */
@@ -484,6 +486,22 @@ int cg_avm_get_counters(cg_avm_ctx* ctx, cg_counters* host_out);
 /* Releases the host context (the workspace stays the caller's). */
 int cg_avm_destroy(cg_avm_ctx* ctx);
 const char* cg_avm_last_error(const cg_avm_ctx* ctx);
+/* Storage order (Sec. 2.B: spatially close vertices and cells close in
+ * memory).  The ids of this API (vertex and cell ids, the entries of vc, vn,
+ * cv, the order of every per-vertex and per-cell array, the cells of
+ * cg_avm_divide) are tags fixed when a vertex or cell slot comes into being;
+ * where each one is stored is the context's business.  Every rule above that
+ * depends on ids (T1 and T2 priorities, the end a T1 edge is taken from, the
+ * vertex a T2 keeps, the director noise counter, the slots divisions fill)
+ * uses the tags, so results do not depend on the storage order.
+ * cg_avm_sort re-sorts now: vertices along a Hilbert curve of their
+ * positions, cells along one of their first vertices', freed vertices and
+ * empty cells last.  Enqueued on the context's stream; synchronizes. */
+int cg_avm_sort(cg_avm_ctx* ctx);
+/* The tag held by each vertex slot [V] and cell slot [N] (host or device
+ * pointers, either may be NULL): a diagnostic of the storage order.
+ * Synchronizes. */
+int cg_avm_get_tags(cg_avm_ctx* ctx, int32_t* vtag, int32_t* ctag);
 
 /* Releases the host context (the workspace stays the caller's). */
 int cg_destroy(cg_ctx* ctx);

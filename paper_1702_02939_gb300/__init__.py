@@ -55,7 +55,7 @@ class cg_avm_params(C.Structure):
     _fields_ = [("A0", C.c_double), ("KA", C.c_double), ("KP", C.c_double), ("mu", C.c_double),
                 ("Dr", C.c_double), ("dt", C.c_double), ("t1_threshold", C.c_double),
                 ("t1_length", C.c_double), ("seed", C.c_uint64), ("t1_cap", C.c_int32),
-                ("cell_capacity", C.c_int32), ("t2_area", C.c_double)]
+                ("cell_capacity", C.c_int32), ("t2_area", C.c_double), ("sort_every", C.c_int32)]
 
 
 class cg_counters(C.Structure):
@@ -144,6 +144,8 @@ def lib():
         L.cg_avm_get_cell_params.argtypes = [vp, vp, vp, vp]
         L.cg_avm_divide.argtypes = [vp, i32, vp, vp, vp, C.POINTER(i32)]
         L.cg_avm_get_counters.argtypes = [vp, C.POINTER(cg_counters)]
+        L.cg_avm_sort.argtypes = [vp]
+        L.cg_avm_get_tags.argtypes = [vp, vp, vp]
         L.cg_avm_destroy.argtypes = [vp]
         L.cg_avm_last_error.argtypes = [vp]
         L.cg_avm_last_error.restype = C.c_char_p
@@ -733,6 +735,14 @@ def cg_avm_get_counters(ctx):
             "status": c.status, "loop_total": c.loop_total}
 
 
+def cg_avm_sort(ctx):
+    _check_avm(lib().cg_avm_sort(ctx), ctx)
+
+
+def cg_avm_get_tags(ctx, vtag, ctag):
+    _check_avm(lib().cg_avm_get_tags(ctx, _ptr(vtag), _ptr(ctag)), ctx)
+
+
 def cg_avm_destroy(ctx):
     if ctx:
         lib().cg_avm_destroy(ctx)
@@ -743,9 +753,12 @@ class AVM:
     seed positions x, y (numpy, or torch tensors on any device)."""
 
     def __init__(self, n, Lx, Ly, x, y, theta, p0=3.8, v0=0.1, A0=1.0, KA=1.0, KP=1.0, mu=1.0, Dr=1.0, dt=0.01,
-                 t1_threshold=0.04, t1_length=0.0, seed=0, t1_cap=16, t2_area=0.0, capacity=None, device="cuda"):
+                 t1_threshold=0.04, t1_length=0.0, seed=0, t1_cap=16, t2_area=0.0, capacity=None, sort_every=0,
+                 device="cuda"):
         """n seeds; `capacity` cell slots (default n) leave room for divisions:
-        per-cell outputs then have `capacity` entries, per-vertex ones 2x."""
+        per-cell outputs then have `capacity` entries, per-vertex ones 2x.
+        sort_every > 0: Hilbert re-sort of the storage at creation and every
+        sort_every steps (results unchanged; ids stay those of the API)."""
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -753,7 +766,7 @@ class AVM:
         self.n_seed = int(n)
         self.n, self.V = cap, 2 * cap
         self.params = cg_avm_params(A0, KA, KP, mu, Dr, dt, t1_threshold, t1_length, int(seed), int(t1_cap), cap,
-                                    float(t2_area))
+                                    float(t2_area), int(sort_every))
         nbytes = cg_avm_workspace_bytes_capacity(n, cap, Lx, Ly)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.stream = torch.cuda.current_stream(self.device).cuda_stream
@@ -783,6 +796,17 @@ class AVM:
         hx, hy, th = self._out(self.V), self._out(self.V), self._out(self.n)
         cg_avm_get_state(self.ctx, hx, hy, th)
         return hx, hy, th
+
+    def sort(self):
+        """Hilbert re-sort of the storage now (ids and results unchanged)."""
+        cg_avm_sort(self.ctx)
+
+    def storage_tags(self):
+        """(vertex tags [V], cell tags [N]) by storage slot (int32 tensors)."""
+        t = self.torch
+        vt, ct = self._out(self.V, t.int32), self._out(self.n, t.int32)
+        cg_avm_get_tags(self.ctx, vt, ct)
+        return vt, ct
 
     def topology(self):
         """(vc [V,3], vn [V,3], cc [N], cv [N, MAX_RING]) as int32 tensors."""

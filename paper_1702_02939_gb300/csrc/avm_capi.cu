@@ -30,6 +30,12 @@ struct AvmOff {
       done;
   size_t owned, base_local, base_partial, xs, ys, cnt, nbr, scalar, ctl, dir_tab;
   size_t div_cells, div_dirs, div_made, div_cslots, div_vslots, div_lock;  // staging of cg_avm_divide
+  // storage order: tags of the slots, slots of the tags, candidate priorities
+  size_t vtag, ctag, vslot, cslot, cand_k;
+  // re-sort scratch (keys, ranks, new places, key counts, permuted copies);
+  // between re-sorts the copies stage the API's tag-ordered transfers
+  size_t vkey, vrank, vperm, ckey, crank, cperm, kcount_v, kstart_v, kpart_v, kcount_c, kstart_c, kpart_c;
+  size_t vc_s, vn_s, cc_s, cv_s, vtag_s, ctag_s, theta_s, p0_s, v0_s, a0_s, P0_s;
   size_t total;
 };
 
@@ -81,6 +87,35 @@ AvmOff avm_layout(int64_t n, size_t spv_bytes) {
   o.div_cslots = L.take(n * i4);
   o.div_vslots = L.take(2 * n * i4);
   o.div_lock = L.take(n * sizeof(unsigned long long));
+  o.vtag = L.take(V * i4);
+  o.ctag = L.take(n * i4);
+  o.vslot = L.take(V * i4);
+  o.cslot = L.take(n * i4);
+  o.cand_k = L.take((3 * V / 2 + n + 1) * i4);
+  o.vkey = L.take(V * i4);
+  o.vrank = L.take(V * i4);
+  o.vperm = L.take(V * i4);
+  o.ckey = L.take(n * i4);
+  o.crank = L.take(n * i4);
+  o.cperm = L.take(n * i4);
+  // key counts: at most V + 1 (Hilbert keys <= V plus the last key, or V tags)
+  o.kcount_v = L.take((V + 2) * i4);
+  o.kstart_v = L.take((V + 2) * i4);
+  o.kpart_v = L.take(((V + 2) / kScanChunk + 2) * i4);
+  o.kcount_c = L.take((n + 2) * i4);
+  o.kstart_c = L.take((n + 2) * i4);
+  o.kpart_c = L.take(((n + 2) / kScanChunk + 2) * i4);
+  o.vc_s = L.take(3 * V * i4);
+  o.vn_s = L.take(3 * V * i4);
+  o.cc_s = L.take(n * i4);
+  o.cv_s = L.take(n * CG_RING * i4);
+  o.vtag_s = L.take(V * i4);
+  o.ctag_s = L.take(n * i4);
+  o.theta_s = L.take(n * d);
+  o.p0_s = L.take(n * d);
+  o.v0_s = L.take(n * d);
+  o.a0_s = L.take(n * d);
+  o.P0_s = L.take(n * d);
   o.total = L.total;
   return o;
 }
@@ -100,6 +135,9 @@ struct cg_avm_ctx {
   cudaGraphExec_t exec = nullptr;     // one step
   cudaGraphExec_t t1_exec = nullptr;  // T1 passes alone
   int sms = 0;
+  int hord_v = 0, hord_c = 0;  // Hilbert grids of the re-sort
+  int since_sort = 0;          // steps since the last re-sort
+  bool permuted = false;       // slots differ from tags (a re-sort ran)
   bool broken = false;  // a device status was seen: no further steps
   std::string last_error;
   template <class T>
@@ -198,6 +236,9 @@ AvmArgs avm_args(cg_avm_ctx* c) {
   a.lock = c->at<unsigned long long>(c->off.lock);
   a.cand_e = c->at<int>(c->off.cand_e);
   a.cand = c->at<int4>(c->off.cand);
+  a.cand_k = c->at<int>(c->off.cand_k);
+  a.vtag = c->at<int>(c->off.vtag);
+  a.ctag = c->at<int>(c->off.ctag);
   a.done = c->at<unsigned int>(c->off.done);
   a.loop = 0;
   return a;
@@ -211,6 +252,104 @@ int avm_status(cg_avm_ctx* c) {
     c->broken = true;
     return afail(c, h.status, std::string("device status: ") + cg_status_string(h.status));
   }
+  return CG_OK;
+}
+
+int copy_in(cg_avm_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (!src) return CG_OK;
+  AV_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+  return CG_OK;
+}
+
+int copy_out(cg_avm_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (!dst) return CG_OK;
+  AV_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+  return CG_OK;
+}
+
+AvmSortArgs sort_args(cg_avm_ctx* c, int by_tag) {
+  AvmSortArgs a{};
+  a.n = c->n;
+  a.V = c->V;
+  a.ctl = c->ctl();
+  a.Lx = c->Lx;
+  a.Ly = c->Ly;
+  a.hord_v = c->hord_v;
+  a.hord_c = c->hord_c;
+  a.by_tag = by_tag;
+  a.hx = a.hx_w = c->at<double>(c->off.hx);
+  a.hy = a.hy_w = c->at<double>(c->off.hy);
+  a.vc = c->at<int>(c->off.vc);
+  a.vn = c->at<int>(c->off.vn);
+  a.cc = c->at<int>(c->off.cc);
+  a.cv = c->at<int>(c->off.cv);
+  a.theta = c->at<double>(c->off.theta);
+  a.p0 = c->at<double>(c->off.p0);
+  a.v0 = c->at<double>(c->off.v0);
+  a.a0 = c->at<double>(c->off.a0);
+  a.P0 = c->at<double>(c->off.P0);
+  a.vtag = c->at<int>(c->off.vtag);
+  a.ctag = c->at<int>(c->off.ctag);
+  a.vslot = c->at<int>(c->off.vslot);
+  a.cslot = c->at<int>(c->off.cslot);
+  a.vkey = c->at<int>(c->off.vkey);
+  a.vrank = c->at<int>(c->off.vrank);
+  a.vperm = c->at<int>(c->off.vperm);
+  a.ckey = c->at<int>(c->off.ckey);
+  a.crank = c->at<int>(c->off.crank);
+  a.cperm = c->at<int>(c->off.cperm);
+  a.kcount_v = c->at<int>(c->off.kcount_v);
+  a.kstart_v = c->at<int>(c->off.kstart_v);
+  a.kpart_v = c->at<int>(c->off.kpart_v);
+  a.kcount_c = c->at<int>(c->off.kcount_c);
+  a.kstart_c = c->at<int>(c->off.kstart_c);
+  a.kpart_c = c->at<int>(c->off.kpart_c);
+  a.vc_s = c->at<int>(c->off.vc_s);
+  a.vn_s = c->at<int>(c->off.vn_s);
+  a.cc_s = c->at<int>(c->off.cc_s);
+  a.cv_s = c->at<int>(c->off.cv_s);
+  a.vtag_s = c->at<int>(c->off.vtag_s);
+  a.ctag_s = c->at<int>(c->off.ctag_s);
+  a.theta_s = c->at<double>(c->off.theta_s);
+  a.p0_s = c->at<double>(c->off.p0_s);
+  a.v0_s = c->at<double>(c->off.v0_s);
+  a.a0_s = c->at<double>(c->off.a0_s);
+  a.P0_s = c->at<double>(c->off.P0_s);
+  return a;
+}
+
+// Re-sort (by_tag 0: along the Hilbert curves; 1: back to the order as
+// built), then the float copies, the locks and the next step's director
+// terms of the moved state (the same values: they depend on tags only).
+int enqueue_sort(cg_avm_ctx* c, int by_tag) {
+  cudaStream_t st = c->stream;
+  launch_avm_sort(sort_args(c, by_tag), st);
+  const AvmArgs a = avm_args(c);
+  launch_avm_shadow(a, st);
+  launch_fill_u64(c->n, ~0ull, a.lock, st);
+  launch_avm_dir(a, st);
+  AV_CUDA(c, cudaGetLastError());
+  c->permuted = !by_tag;
+  c->since_sort = 0;
+  return CG_OK;
+}
+
+// A per-slot double array in tag order: straight copy when slots are tags,
+// else through a staging array (device) of the context.
+int out_by_tag(cg_avm_ctx* c, double* dst, const double* src, int count, const int* tags, double* stage) {
+  if (!dst) return CG_OK;
+  if (!c->permuted) return copy_out(c, dst, src, (size_t)count * sizeof(double));
+  launch_gather_d(count, tags, src, stage, c->stream);
+  return copy_out(c, dst, stage, (size_t)count * sizeof(double));
+}
+
+// A tag-ordered double array into the per-slot array dst.
+int in_by_tag(cg_avm_ctx* c, double* dst, const double* src, int count, const int* tags, double* stage) {
+  if (!src) return CG_OK;
+  if (!c->permuted) return copy_in(c, dst, src, (size_t)count * sizeof(double));
+  int rc = copy_in(c, stage, src, (size_t)count * sizeof(double));
+  if (rc) return rc;
+  launch_scatter_d(count, tags, stage, dst, c->stream);
   return CG_OK;
 }
 
@@ -269,18 +408,6 @@ int avm_graphs(cg_avm_ctx* c) {
       [](cudaStream_t) {}, &c->t1_exec);
 }
 
-int copy_in(cg_avm_ctx* c, void* dst, const void* src, size_t bytes) {
-  if (!src) return CG_OK;
-  AV_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
-  return CG_OK;
-}
-
-int copy_out(cg_avm_ctx* c, void* dst, const void* src, size_t bytes) {
-  if (!dst) return CG_OK;
-  AV_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
-  return CG_OK;
-}
-
 }  // namespace
 
 extern "C" {
@@ -304,7 +431,8 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
   if (!out) return CG_EINVAL;
   *out = nullptr;
   if (!par || !x || !y || !theta || !d_ws || ((uintptr_t)d_ws & 255) || n < 16) return CG_EINVAL;
-  if (!(par->dt > 0) || !(par->A0 > 0) || !(par->t1_threshold >= 0) || !(par->t2_area >= 0)) return CG_EINVAL;
+  if (!(par->dt > 0) || !(par->A0 > 0) || !(par->t1_threshold >= 0) || !(par->t2_area >= 0) || par->sort_every < 0)
+    return CG_EINVAL;
   for (double v : {par->A0, par->KA, par->KP, par->mu, par->Dr, par->dt, par->t1_threshold, par->t1_length,
                    par->t2_area, p0, v0})
     if (!std::isfinite(v)) return CG_EINVAL;
@@ -325,6 +453,9 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
   size_t spv_bytes = 0;
   cg_workspace_bytes(1, &r, &spv_bytes);
   c->off = avm_layout(ncap, spv_bytes);
+  // Hilbert grids with at most V (n) keys: about two vertices (one cell) each
+  while (c->hord_v < 15 && (int64_t(1) << (2 * (c->hord_v + 1))) <= c->V) ++c->hord_v;
+  while (c->hord_c < 15 && (int64_t(1) << (2 * (c->hord_c + 1))) <= c->n) ++c->hord_c;
   do {
     if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
@@ -364,10 +495,15 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
         cudaMemsetAsync(c->at<int>(c->off.vn), 0xff, 3 * Vc * sizeof(int), st) != cudaSuccess ||
         cudaMemsetAsync(c->at<double>(c->off.hx), 0, 2 * Vc * sizeof(double), st) != cudaSuccess ||
         cudaMemsetAsync(c->at<double>(c->off.hy), 0, 2 * Vc * sizeof(double), st) != cudaSuccess ||
-        cudaMemsetAsync(c->at<double>(c->off.theta), 0, (size_t)ncap * sizeof(double), st) != cudaSuccess) {
+        cudaMemsetAsync(c->at<double>(c->off.theta), 0, (size_t)ncap * sizeof(double), st) != cudaSuccess ||
+        cudaMemsetAsync(c->at<int>(c->off.kcount_v), 0, ((size_t)c->V + 2) * sizeof(int), st) != cudaSuccess ||
+        cudaMemsetAsync(c->at<int>(c->off.kcount_c), 0, ((size_t)ncap + 2) * sizeof(int), st) != cudaSuccess) {
       rc = CG_ECUDA;
       break;
     }
+    // slots in the order as built: tag = slot
+    launch_iota2(c->V, c->at<int>(c->off.vtag), c->at<int>(c->off.vslot), st);
+    launch_iota2(ncap, c->at<int>(c->off.ctag), c->at<int>(c->off.cslot), st);
     AvmBuildArgs b{};  // every field starts zero or null
     b.n = n;
     b.ctl = c->ctl();
@@ -405,6 +541,7 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
     launch_avm_dir(avm_args(c), st);
     rc = avm_status(c);
     if (rc) break;
+    if (c->par.sort_every > 0 && (rc = enqueue_sort(c, 0))) break;
     rc = avm_graphs(c);
   } while (0);
   if (rc) {
@@ -418,7 +555,13 @@ int cg_avm_create(int32_t n, double Lx, double Ly, double p0, double v0, const c
 int cg_avm_step(cg_avm_ctx* c, int64_t nsteps) {
   if (!c || nsteps < 0) return CG_EINVAL;
   if (c->broken) return afail(c, CG_EINVAL, "context holds a device error: " + c->last_error);
-  for (int64_t s = 0; s < nsteps; ++s) AV_CUDA(c, cudaGraphLaunch(c->exec, c->stream));
+  for (int64_t s = 0; s < nsteps; ++s) {
+    AV_CUDA(c, cudaGraphLaunch(c->exec, c->stream));
+    if (c->par.sort_every > 0 && ++c->since_sort >= c->par.sort_every) {
+      const int rc = enqueue_sort(c, 0);
+      if (rc) return rc;
+    }
+  }
   return CG_OK;
 }
 
@@ -478,9 +621,14 @@ int cg_avm_get_state(cg_avm_ctx* c, double* hx, double* hy, double* theta) {
   Ctl h;
   AV_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
   const size_t V = c->V;
-  if ((rc = copy_out(c, hx, c->at<double>(c->off.hx) + h.cur * V, V * sizeof(double)))) return rc;
-  if ((rc = copy_out(c, hy, c->at<double>(c->off.hy) + h.cur * V, V * sizeof(double)))) return rc;
-  if ((rc = copy_out(c, theta, c->at<double>(c->off.theta), c->n * sizeof(double)))) return rc;
+  const int* vtag = c->at<int>(c->off.vtag);
+  const int* ctag = c->at<int>(c->off.ctag);
+  // staging: the permuted-copy arrays of the re-sort (3V ints >= V doubles)
+  if ((rc = out_by_tag(c, hx, c->at<double>(c->off.hx) + h.cur * V, c->V, vtag, c->at<double>(c->off.vc_s))))
+    return rc;
+  if ((rc = out_by_tag(c, hy, c->at<double>(c->off.hy) + h.cur * V, c->V, vtag, c->at<double>(c->off.vn_s))))
+    return rc;
+  if ((rc = out_by_tag(c, theta, c->at<double>(c->off.theta), c->n, ctag, c->at<double>(c->off.theta_s)))) return rc;
   return avm_status(c);
 }
 
@@ -488,10 +636,21 @@ int cg_avm_get_topology(cg_avm_ctx* c, int32_t* vc, int32_t* vn, int32_t* cc, in
   if (!c) return CG_EINVAL;
   int rc = avm_status(c);
   if (rc) return rc;
-  if ((rc = copy_out(c, vc, c->at<int>(c->off.vc), 3 * (size_t)c->V * sizeof(int)))) return rc;
-  if ((rc = copy_out(c, vn, c->at<int>(c->off.vn), 3 * (size_t)c->V * sizeof(int)))) return rc;
-  if ((rc = copy_out(c, cc, c->at<int>(c->off.cc), (size_t)c->n * sizeof(int)))) return rc;
-  if ((rc = copy_out(c, cv, c->at<int>(c->off.cv), (size_t)c->n * CG_RING * sizeof(int)))) return rc;
+  const int *svc = c->at<int>(c->off.vc), *svn = c->at<int>(c->off.vn);
+  const int *scc = c->at<int>(c->off.cc), *scv = c->at<int>(c->off.cv);
+  if (c->permuted) {  // in tag order, entries renamed to tags
+    launch_avm_topology_by_tag(avm_args(c), c->at<int>(c->off.vslot), c->at<int>(c->off.cslot),
+                               c->at<int>(c->off.vc_s), c->at<int>(c->off.vn_s), c->at<int>(c->off.cc_s),
+                               c->at<int>(c->off.cv_s), c->stream);
+    svc = c->at<int>(c->off.vc_s);
+    svn = c->at<int>(c->off.vn_s);
+    scc = c->at<int>(c->off.cc_s);
+    scv = c->at<int>(c->off.cv_s);
+  }
+  if ((rc = copy_out(c, vc, svc, 3 * (size_t)c->V * sizeof(int)))) return rc;
+  if ((rc = copy_out(c, vn, svn, 3 * (size_t)c->V * sizeof(int)))) return rc;
+  if ((rc = copy_out(c, cc, scc, (size_t)c->n * sizeof(int)))) return rc;
+  if ((rc = copy_out(c, cv, scv, (size_t)c->n * CG_RING * sizeof(int)))) return rc;
   return avm_status(c);
 }
 
@@ -500,6 +659,9 @@ int cg_avm_set_state(cg_avm_ctx* c, const double* hx, const double* hy, const do
   if (!c || !hx || !hy) return CG_EINVAL;
   int rc = avm_status(c);
   if (rc) return rc;
+  // arrays in tag order: slots back to tags first (the next re-sort is due
+  // sort_every steps later)
+  if (c->permuted && (rc = enqueue_sort(c, 1))) return rc;
   Ctl h;
   AV_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
   const size_t V = c->V;
@@ -523,10 +685,10 @@ int cg_avm_get_cell_params(cg_avm_ctx* c, double* p0, double* v0, double* a0) {
   if (!c) return CG_EINVAL;
   int rc = avm_status(c);
   if (rc) return rc;
-  const size_t b = (size_t)c->n * sizeof(double);
-  if ((rc = copy_out(c, p0, c->at<double>(c->off.p0), b))) return rc;
-  if ((rc = copy_out(c, v0, c->at<double>(c->off.v0), b))) return rc;
-  if ((rc = copy_out(c, a0, c->at<double>(c->off.a0), b))) return rc;
+  const int* ctag = c->at<int>(c->off.ctag);
+  if ((rc = out_by_tag(c, p0, c->at<double>(c->off.p0), c->n, ctag, c->at<double>(c->off.p0_s)))) return rc;
+  if ((rc = out_by_tag(c, v0, c->at<double>(c->off.v0), c->n, ctag, c->at<double>(c->off.v0_s)))) return rc;
+  if ((rc = out_by_tag(c, a0, c->at<double>(c->off.a0), c->n, ctag, c->at<double>(c->off.a0_s)))) return rc;
   return avm_status(c);
 }
 
@@ -546,8 +708,9 @@ int cg_avm_get_geometry(cg_avm_ctx* c, double* A, double* P) {
   if (!c) return CG_EINVAL;
   launch_avm_forces(avm_args(c), c->stream);
   int rc;
-  if ((rc = copy_out(c, A, c->at<double>(c->off.A), c->n * sizeof(double)))) return rc;
-  if ((rc = copy_out(c, P, c->at<double>(c->off.P), c->n * sizeof(double)))) return rc;
+  const int* ctag = c->at<int>(c->off.ctag);
+  if ((rc = out_by_tag(c, A, c->at<double>(c->off.A), c->n, ctag, c->at<double>(c->off.p0_s)))) return rc;
+  if ((rc = out_by_tag(c, P, c->at<double>(c->off.P), c->n, ctag, c->at<double>(c->off.v0_s)))) return rc;
   return avm_status(c);
 }
 
@@ -557,10 +720,16 @@ int cg_avm_get_forces(cg_avm_ctx* c, double* Fx, double* Fy, double* energy) {
   a.energy = c->at<double>(c->off.energy);
   launch_avm_forces(a, c->stream);
   int rc;
-  if ((rc = copy_out(c, Fx, c->at<double>(c->off.Fx), c->V * sizeof(double)))) return rc;
-  if ((rc = copy_out(c, Fy, c->at<double>(c->off.Fy), c->V * sizeof(double)))) return rc;
+  const int* vtag = c->at<int>(c->off.vtag);
+  if ((rc = out_by_tag(c, Fx, c->at<double>(c->off.Fx), c->V, vtag, c->at<double>(c->off.vc_s)))) return rc;
+  if ((rc = out_by_tag(c, Fy, c->at<double>(c->off.Fy), c->V, vtag, c->at<double>(c->off.vn_s)))) return rc;
   if (energy) {
-    launch_reduce_sum(c->n, a.energy, c->at<double>(c->off.scalar), c->stream);
+    const double* e = a.energy;
+    if (c->permuted) {  // summed in tag order, as without a re-sort
+      launch_gather_d(c->n, c->at<int>(c->off.ctag), a.energy, c->at<double>(c->off.theta_s), c->stream);
+      e = c->at<double>(c->off.theta_s);
+    }
+    launch_reduce_sum(c->n, e, c->at<double>(c->off.scalar), c->stream);
     AV_CUDA(c, cudaMemcpyAsync(energy, c->at<double>(c->off.scalar), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   }
   return avm_status(c);
@@ -577,7 +746,7 @@ int cg_avm_t1(cg_avm_ctx* c) {
 
 int cg_avm_set_p0(cg_avm_ctx* c, const double* p0) {
   if (!c || !p0) return CG_EINVAL;
-  int rc = copy_in(c, c->at<double>(c->off.p0), p0, c->n * sizeof(double));
+  int rc = in_by_tag(c, c->at<double>(c->off.p0), p0, c->n, c->at<int>(c->off.ctag), c->at<double>(c->off.p0_s));
   if (rc) return rc;
   launch_check_finite(c->n, c->at<double>(c->off.p0), c->ctl(), c->stream);
   launch_avm_p0s(avm_args(c), c->stream);
@@ -593,23 +762,31 @@ int cg_avm_divide(cg_avm_ctx* c, int32_t count, const int32_t* cells, const doub
   if (!cells || !dirs || count > c->n) return CG_EINVAL;
   int rc = avm_status(c);
   if (rc) return rc;
-  // the slots the divisions may take, in order: the lowest empty cells and
-  // the lowest free vertices (a call only fills slots)
-  std::vector<int> hcc(c->n), hvc(3 * (size_t)c->V), cs, vs;
+  // the slots the divisions may take, in order: the empty cells and the free
+  // vertices of lowest tag (a call only fills slots)
+  std::vector<int> hcc(c->n), hvc(3 * (size_t)c->V), hcs(c->n), hvs(c->V), cs, vs;
   AV_CUDA(c, cudaMemcpy(hcc.data(), c->at<int>(c->off.cc), hcc.size() * sizeof(int), cudaMemcpyDeviceToHost));
   AV_CUDA(c, cudaMemcpy(hvc.data(), c->at<int>(c->off.vc), hvc.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  AV_CUDA(c, cudaMemcpy(hcs.data(), c->at<int>(c->off.cslot), hcs.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  AV_CUDA(c, cudaMemcpy(hvs.data(), c->at<int>(c->off.vslot), hvs.size() * sizeof(int), cudaMemcpyDeviceToHost));
   for (int k = 0; k < c->n && (int)cs.size() < count; ++k)
-    if (hcc[k] == 0) cs.push_back(k);
+    if (hcc[hcs[k]] == 0) cs.push_back(hcs[k]);
   for (int v = 0; v < c->V && (int)vs.size() < 2 * count; ++v)
-    if (hvc[3 * (size_t)v] < 0) vs.push_back(v);
+    if (hvc[3 * (size_t)hvs[v]] < 0) vs.push_back(hvs[v]);
   if ((int)cs.size() < count || (int)vs.size() < 2 * count)
     return afail(c, CG_EINVAL, "not enough free cell slots for the divisions");
+  // the cells named by tag, in slots (an index out of range stays so and is
+  // refused by the kernel)
+  std::vector<int> hcells(count);
+  AV_CUDA(c, cudaMemcpy(hcells.data(), cells, (size_t)count * sizeof(int), cudaMemcpyDefault));
+  for (int& x : hcells)
+    if ((unsigned)x < (unsigned)c->n) x = hcs[x];
   int* dc = c->at<int>(c->off.div_cells);
   double* dd = c->at<double>(c->off.div_dirs);
   int* dm = c->at<int>(c->off.div_made);
   int* dcs = c->at<int>(c->off.div_cslots);
   int* dvs = c->at<int>(c->off.div_vslots);
-  if ((rc = copy_in(c, dc, cells, (size_t)count * sizeof(int)))) return rc;
+  if ((rc = copy_in(c, dc, hcells.data(), (size_t)count * sizeof(int)))) return rc;
   if ((rc = copy_in(c, dd, dirs, 2 * (size_t)count * sizeof(double)))) return rc;
   AV_CUDA(c, cudaMemcpyAsync(dcs, cs.data(), cs.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   AV_CUDA(c, cudaMemcpyAsync(dvs, vs.data(), vs.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
@@ -634,7 +811,7 @@ int cg_avm_divide(cg_avm_ctx* c, int32_t count, const int32_t* cells, const doub
 
 int cg_avm_set_a0(cg_avm_ctx* c, const double* a0) {
   if (!c || !a0) return CG_EINVAL;
-  int rc = copy_in(c, c->at<double>(c->off.a0), a0, c->n * sizeof(double));
+  int rc = in_by_tag(c, c->at<double>(c->off.a0), a0, c->n, c->at<int>(c->off.ctag), c->at<double>(c->off.a0_s));
   if (rc) return rc;
   launch_avm_p0s(avm_args(c), c->stream);  // also refuses a negative or non-finite A0
   return avm_status(c);
@@ -642,7 +819,7 @@ int cg_avm_set_a0(cg_avm_ctx* c, const double* a0) {
 
 int cg_avm_set_v0(cg_avm_ctx* c, const double* v0) {
   if (!c || !v0) return CG_EINVAL;
-  int rc = copy_in(c, c->at<double>(c->off.v0), v0, c->n * sizeof(double));
+  int rc = in_by_tag(c, c->at<double>(c->off.v0), v0, c->n, c->at<int>(c->off.ctag), c->at<double>(c->off.v0_s));
   if (rc) return rc;
   launch_check_finite(c->n, c->at<double>(c->off.v0), c->ctl(), c->stream);
   launch_avm_dir(avm_args(c), c->stream);  // the activity of the next step
@@ -663,6 +840,23 @@ int cg_avm_get_counters(cg_avm_ctx* c, cg_counters* out) {
   out->reserved = 0;
   out->loop_total = h.loop_total;
   return CG_OK;
+}
+
+int cg_avm_sort(cg_avm_ctx* c) {
+  if (!c) return CG_EINVAL;
+  int rc = avm_status(c);
+  if (rc) return rc;
+  if ((rc = enqueue_sort(c, 0))) return rc;
+  return avm_status(c);
+}
+
+int cg_avm_get_tags(cg_avm_ctx* c, int32_t* vtag, int32_t* ctag) {
+  if (!c) return CG_EINVAL;
+  int rc = avm_status(c);
+  if (rc) return rc;
+  if ((rc = copy_out(c, vtag, c->at<int>(c->off.vtag), (size_t)c->V * sizeof(int)))) return rc;
+  if ((rc = copy_out(c, ctag, c->at<int>(c->off.ctag), (size_t)c->n * sizeof(int)))) return rc;
+  return avm_status(c);
 }
 
 int cg_avm_destroy(cg_avm_ctx* c) {

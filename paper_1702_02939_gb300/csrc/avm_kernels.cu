@@ -10,6 +10,13 @@
 // a transition and take an atomic-min lock (edge id) on their four cells;
 // an edge whose id holds all four locks rotates by 90 degrees about its
 // midpoint and exchanges neighbours; passes repeat until none is proposed.
+//
+// Storage order: every vertex and cell slot carries a tag, its id in the
+// network as built (the id the API speaks in).  Every rule that depends on
+// ids takes tags: the T1 and T2 priorities, the end an edge is oriented from,
+// the vertex a T2 keeps, the director noise counter and the slots divisions
+// fill.  Results therefore do not depend on the storage order, which the
+// Hilbert re-sort below changes (Sec. 2.B).
 #include "cg_device.cuh"
 #include "cg_kernels.h"
 
@@ -156,7 +163,8 @@ void launch_avm_build(const AvmBuildArgs& a, cudaStream_t st) {
 // (v0/3) n(theta) of the current director (each of a cell's vertices takes a
 // third, Eq. 4 with n = 3) and the director after the next step's rotation,
 // theta + sqrt(2 D_r dt) xi (Philox, counter (cell, step) with the step
-// counter of the next step).  Cells removed by a T2 turn as well.
+// counter of the next step, cell id = tag).  Cells removed by a T2 turn as
+// well.
 __global__ void k_avm_dir(AvmArgs g) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.n) return;
@@ -165,7 +173,7 @@ __global__ void k_avm_dir(AvmArgs g) {
   dm_sincos(th, g.tab, sn, cs);
   const double v3 = g.v0[c] * (1.0 / 3.0);
   g.act[c] = make_double2(v3 * cs, v3 * sn);
-  g.thn[c] = th + g.noise_amp * director_noise(g.seed, c, g.ctl->step, g.tab);
+  g.thn[c] = th + g.noise_amp * director_noise(g.seed, g.ctag[c], g.ctl->step, g.tab);
 }
 
 // Per cell: area and perimeter of the polygon and the force coefficients
@@ -353,7 +361,7 @@ __device__ __forceinline__ int cell_across(const int* __restrict__ vc, int c, in
 // and the difference rounded separately, offsets from its first vertex)
 // below twice the threshold; the cells across its three edges must be
 // distinct with more than 3 vertices and the outer vertices distinct.  The
-// candidate id is 3V + c; its cells are c and the three across its edges.
+// candidate id is 3V + tag(c); its cells are c and the three across its edges.
 __device__ void t2_propose(const AvmArgs& g, int c, int stamp) {
   const size_t V = (size_t)g.V;
   const int cur = g.ctl->cur;
@@ -395,23 +403,27 @@ __device__ void t2_propose(const AvmArgs& g, int c, int stamp) {
     g.ctl->t1_more = 1;
     return;
   }
-  const int e = 3 * g.V + c;
-  const unsigned long long key = lock_key(stamp, e);
+  const int ek = 3 * g.V + g.ctag[c];  // priority: the id in tags
+  const unsigned long long key = lock_key(stamp, ek);
   atomicMin(&g.lock[c], key);
   atomicMin(&g.lock[nb[0]], key);
   atomicMin(&g.lock[nb[1]], key);
   atomicMin(&g.lock[nb[2]], key);
   const int slot = atomicAdd(&g.ctl->count[1], 1);
-  g.cand_e[slot] = e;
+  g.cand_e[slot] = 3 * g.V + c;
+  g.cand_k[slot] = ek;
   g.cand[slot] = make_int4(c, nb[0], nb[1], nb[2]);
 }
 
-// One thread per vertex v, its edges (v, w) with w > v.  The squared length
-// is first bounded in FP32 from the float copies of the positions; only edges
-// within the error band of the threshold are decided in FP64 in the fixed
-// rounding order.  Candidates go to a compact list.  A short edge that its
-// cells' vertex counts keep from flipping marks the pass as possibly leaving
-// work (another flip may change those counts).
+// One thread per vertex slot v, its edges (v, w) with slot w > v.  The
+// squared length is first bounded in FP32 from the float copies of the
+// positions; only edges within the error band of the threshold are decided in
+// FP64 in the fixed rounding order (both bounds are symmetric in the two
+// ends).  A short edge is then oriented from its end of smaller tag, v1 (the
+// edge is slot a of v1's lists), and takes the id 3 tag(v1) + a.  Candidates
+// go to a compact list.  A short edge that its cells' vertex counts keep from
+// flipping marks the pass as possibly leaving work (another flip may change
+// those counts).
 __global__ void k_t1_propose(AvmArgs g) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   // stop the loop unless the closing kernel of this pass asks for another
@@ -438,10 +450,18 @@ __global__ void k_t1_propose(AvmArgs g) {
       const double dx = mimg_a(hx[w] - hx[v], g.ax), dy = mimg_a(hy[w] - hy[v], g.ay);
       if (!(len2_rn(dx, dy) < g.thr2)) continue;
     }
-    const int i = g.vc[e], k = g.vc[3 * v + (s + 1) % 3], j = g.vc[3 * v + (s + 2) % 3];
+    // orientation by tags: v1 the end of smaller tag, the edge slot a of v1
+    const int tv = g.vtag[v], tw = g.vtag[w];
+    const int v1 = tv < tw ? v : w, v2 = tv < tw ? w : v;
+    const int a = tv < tw ? s : slot3(g.vn, w, v);
+    if (a < 0) {
+      raise_status(g.ctl, kETOPO);
+      continue;
+    }
+    const int i = g.vc[3 * v1 + a], k = g.vc[3 * v1 + (a + 1) % 3], j = g.vc[3 * v1 + (a + 2) % 3];
     int l = -1;
     for (int t = 0; t < 3; ++t) {
-      const int c = g.vc[3 * w + t];
+      const int c = g.vc[3 * v2 + t];
       if (c != i && c != k) l = c;
     }
     if (l < 0) {
@@ -452,13 +472,15 @@ __global__ void k_t1_propose(AvmArgs g) {
       g.ctl->t1_more = 1;
       continue;
     }
-    const unsigned long long key = lock_key(stamp, e);
+    const int ek = 3 * min(tv, tw) + a;  // priority: the id in tags
+    const unsigned long long key = lock_key(stamp, ek);
     atomicMin(&g.lock[i], key);
     atomicMin(&g.lock[j], key);
     atomicMin(&g.lock[k], key);
     atomicMin(&g.lock[l], key);
     const int slot = atomicAdd(&g.ctl->count[1], 1);
-    g.cand_e[slot] = e;
+    g.cand_e[slot] = 3 * v1 + a;
+    g.cand_k[slot] = ek;
     g.cand[slot] = make_int4(i, j, k, l);
   }
 }
@@ -606,20 +628,15 @@ __device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd, unsigned long
   // moves a vertex adjacent to them (it would need one of this flip's locked
   // cells), so the edges at v1 and v2 are the only ones whose length changed.
   // If none of them passes the proposal's FP32 bound, the next pass finds no
-  // new candidate here.
+  // new candidate here.  (The bound is symmetric in the two ends: the float
+  // difference and its minimum image change sign exactly.)
   {
-    const int a1[3] = {All, Alr, v2}, a2[2] = {Aul, Aur};
-    bool near = false;
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      const int w = a1[t];
-      near |= (w == v2) ? t1_len2_f(g, v1 < v2 ? f1 : f2, v1 < v2 ? f2 : f1) <= g.t2hi
-                        : t1_len2_f(g, v1 < w ? f1 : g.hf[w], v1 < w ? g.hf[w] : f1) <= g.t2hi;
-    }
+    const int a1[2] = {All, Alr}, a2[2] = {Aul, Aur};
+    bool near = t1_len2_f(g, f1, f2) <= g.t2hi;
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
-      const int w = a2[t];
-      near |= t1_len2_f(g, v2 < w ? f2 : g.hf[w], v2 < w ? g.hf[w] : f2) <= g.t2hi;
+      near |= t1_len2_f(g, f1, g.hf[a1[t]]) <= g.t2hi;
+      near |= t1_len2_f(g, f2, g.hf[a2[t]]) <= g.t2hi;
     }
     // (a degenerate network, with a cell on both sides of an edge, takes the
     // next pass regardless)
@@ -667,7 +684,7 @@ __device__ void merge_in_cell(int* cc, int* cv, int x, const int* v, int vk) {
 }
 
 // T2: the triangle c (cells across its edges cd.y, cd.z, cd.w) shrinks to
-// its centroid.  The smallest of its three vertex ids stays, joined to the
+// its centroid.  The vertex of smallest tag among its three stays, joined to the
 // three outer vertices in their order around the triangle; the other two are
 // freed (vc, vn = -1) and the cell is emptied (cc = 0, cv = -1).
 __device__ void apply_t2(const AvmArgs& g, int c, int4 cd) {
@@ -691,7 +708,8 @@ __device__ void apply_t2(const AvmArgs& g, int c, int4 cd) {
     cp[a] = g.vc[3 * v[a] + (s + 1) % 3];
     cpp[a] = g.vc[3 * v[a] + (s + 2) % 3];
   }
-  const int vk = min(v[0], min(v[1], v[2]));
+  const int t0 = g.vtag[v[0]], t1 = g.vtag[v[1]], t2 = g.vtag[v[2]];
+  const int vk = (t0 < t1) ? (t0 < t2 ? v[0] : v[2]) : (t1 < t2 ? v[1] : v[2]);
   // centroid relative to the first vertex of the list
   const double dx1 = mimg_a(hx[v[1]] - hx[v[0]], g.ax), dy1 = mimg_a(hy[v[1]] - hy[v[0]], g.ay);
   const double dx2 = mimg_a(hx[v[2]] - hx[v[0]], g.ax), dy2 = mimg_a(hy[v[2]] - hy[v[0]], g.ay);
@@ -758,7 +776,7 @@ __global__ void k_t1_apply(AvmArgs g) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < proposed; t += gridDim.x * blockDim.x) {
       const int e = g.cand_e[t];
       const int4 cd = g.cand[t];
-      const unsigned long long key = lock_key(stamp, e);
+      const unsigned long long key = lock_key(stamp, g.cand_k[t]);
       if (e < 3 * g.V) {
         apply_t1(g, e / 3, e % 3, cd, key);  // checks the locks itself
         continue;
@@ -1091,6 +1109,135 @@ __global__ void k_fill_u64(int n, unsigned long long v, unsigned long long* out)
 }
 
 // ---------------------------------------------------------------------------
+// Storage order: Hilbert re-sort of the vertex and cell slots (Sec. 2.B).
+// A vertex's key is the Hilbert index of its position on a 2^hord_v grid, a
+// cell's that of its first vertex on a 2^hord_c grid; freed vertices and
+// empty cells take the last key.  A counting sort gives each slot its new
+// place (within a key, in the order of the atomic ranks: the storage order is
+// not deterministic, the results are); one kernel per kind moves every
+// per-slot array and renames the entries.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned grid_coord(double x, double L, unsigned side) {
+  const double u = x / L * (double)side;
+  const unsigned g = u > 0.0 ? (unsigned)u : 0u;
+  return g >= side ? side - 1 : g;
+}
+
+__global__ void k_avm_sort_keys(AvmSortArgs g) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cur = g.ctl->cur;
+  const double* hx = g.hx + (size_t)cur * g.V;
+  const double* hy = g.hy + (size_t)cur * g.V;
+  if (t < g.V) {
+    const unsigned side = 1u << g.hord_v;
+    int key = (int)(side * side);  // freed
+    if (g.by_tag)
+      key = g.vtag[t];
+    else if (g.vc[3 * t] >= 0)
+      key = (int)hilbert_index(g.hord_v, grid_coord(hx[t], g.Lx, side), grid_coord(hy[t], g.Ly, side));
+    g.vkey[t] = key;
+    g.vrank[t] = atomicAdd(&g.kcount_v[key], 1);
+  }
+  if (t < g.n) {
+    const unsigned side = 1u << g.hord_c;
+    int key = (int)(side * side);  // empty
+    const int v0 = g.cv[(size_t)t * CG_RING];
+    if (g.by_tag)
+      key = g.ctag[t];
+    else if (g.cc[t] > 0 && (unsigned)v0 < (unsigned)g.V)
+      key = (int)hilbert_index(g.hord_c, grid_coord(hx[v0], g.Lx, side), grid_coord(hy[v0], g.Ly, side));
+    g.ckey[t] = key;
+    g.crank[t] = atomicAdd(&g.kcount_c[key], 1);
+  }
+}
+
+__global__ void k_avm_sort_perm(AvmSortArgs g) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < g.V) g.vperm[t] = bin_begin(g.kstart_v, g.kpart_v, g.vkey[t]) + g.vrank[t];
+  if (t < g.n) g.cperm[t] = bin_begin(g.kstart_c, g.kpart_c, g.ckey[t]) + g.crank[t];
+}
+
+__global__ void k_avm_sort_move(AvmSortArgs g) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t V = (size_t)g.V;
+  const int cur = g.ctl->cur, alt = cur ^ 1;
+  if (t < g.V) {
+    const int j = g.vperm[t];
+    g.hx_w[alt * V + j] = g.hx[cur * V + t];
+    g.hy_w[alt * V + j] = g.hy[cur * V + t];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int c = g.vc[3 * t + k], w = g.vn[3 * t + k];
+      g.vc_s[3 * j + k] = (unsigned)c < (unsigned)g.n ? g.cperm[c] : -1;
+      g.vn_s[3 * j + k] = (unsigned)w < (unsigned)g.V ? g.vperm[w] : -1;
+    }
+    g.vtag_s[j] = g.vtag[t];
+  }
+  if (t < g.n) {
+    const int j = g.cperm[t];
+    const int m = g.cc[t];
+    g.cc_s[j] = m;
+    for (int a = 0; a < CG_RING; ++a) {
+      const int v = g.cv[(size_t)t * CG_RING + a];
+      g.cv_s[(size_t)j * CG_RING + a] = (a < m && (unsigned)v < (unsigned)g.V) ? g.vperm[v] : -1;
+    }
+    g.theta_s[j] = g.theta[t];
+    g.p0_s[j] = g.p0[t];
+    g.v0_s[j] = g.v0[t];
+    g.a0_s[j] = g.a0[t];
+    g.P0_s[j] = g.P0[t];
+    g.ctag_s[j] = g.ctag[t];
+  }
+}
+
+__global__ void k_avm_sort_finish(AvmSortArgs g) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < g.V) {
+    g.vslot[g.vtag[t]] = t;
+    g.kcount_v[g.vkey[t]] = 0;
+  }
+  if (t < g.n) {
+    g.cslot[g.ctag[t]] = t;
+    g.kcount_c[g.ckey[t]] = 0;
+  }
+  if (t == 0) g.ctl->cur ^= 1;
+}
+
+__global__ void k_iota2(int n, int* a, int* b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = b[i] = i;
+}
+__global__ void k_invert_tags(int n, const int* tags, int* slots) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) slots[tags[i]] = i;
+}
+
+// The network in tag order with its entries renamed to tags.
+__global__ void k_avm_topology_by_tag(AvmArgs g, const int* vslot, const int* cslot, int* vc_out, int* vn_out,
+                                      int* cc_out, int* cv_out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < g.V) {
+    const int v = vslot[t];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int c = g.vc[3 * v + k], w = g.vn[3 * v + k];
+      if (vc_out) vc_out[3 * t + k] = (unsigned)c < (unsigned)g.n ? g.ctag[c] : -1;
+      if (vn_out) vn_out[3 * t + k] = (unsigned)w < (unsigned)g.V ? g.vtag[w] : -1;
+    }
+  }
+  if (t < g.n) {
+    const int c = cslot[t];
+    const int m = g.cc[c];
+    if (cc_out) cc_out[t] = m;
+    if (cv_out)
+      for (int a = 0; a < CG_RING; ++a) {
+        const int v = g.cv[(size_t)c * CG_RING + a];
+        cv_out[(size_t)t * CG_RING + a] = (a < m && (unsigned)v < (unsigned)g.V) ? g.vtag[v] : -1;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
 constexpr int kAvmThreads = 128;
@@ -1134,6 +1281,49 @@ void launch_avm_divide(const AvmArgs& a, int count, const int* cells, const doub
   } else {
     k_avm_divide<<<1, 32, 0, st>>>(a, count, cells, dirs, cslots, vslots, made);
   }
+}
+void launch_avm_sort(const AvmSortArgs& a, cudaStream_t st) {
+  const int blocks = blocks_of(a.V);  // V = 2n covers the cells too
+  k_avm_sort_keys<<<blocks, kAvmThreads, 0, st>>>(a);
+  CellListArgs sc{};
+  sc.ctl = a.ctl;
+  sc.n = a.V;
+  sc.nbins = a.by_tag ? a.V : (1 << (2 * a.hord_v)) + 1;
+  sc.bin_count = a.kcount_v;
+  sc.bin_start = a.kstart_v;
+  sc.scan_partials = a.kpart_v;
+  launch_scan(sc, st);
+  sc.n = a.n;
+  sc.nbins = a.by_tag ? a.n : (1 << (2 * a.hord_c)) + 1;
+  sc.bin_count = a.kcount_c;
+  sc.bin_start = a.kstart_c;
+  sc.scan_partials = a.kpart_c;
+  launch_scan(sc, st);
+  k_avm_sort_perm<<<blocks, kAvmThreads, 0, st>>>(a);
+  k_avm_sort_move<<<blocks, kAvmThreads, 0, st>>>(a);
+  const size_t V = (size_t)a.V, n = (size_t)a.n;
+  cudaMemcpyAsync(a.vc, a.vc_s, 3 * V * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(a.vn, a.vn_s, 3 * V * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(a.vtag, a.vtag_s, V * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(a.cc, a.cc_s, n * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(a.cv, a.cv_s, n * CG_RING * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(a.ctag, a.ctag_s, n * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(a.theta, a.theta_s, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(a.p0, a.p0_s, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(a.v0, a.v0_s, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(a.a0, a.a0_s, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(a.P0, a.P0_s, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  k_avm_sort_finish<<<blocks, kAvmThreads, 0, st>>>(a);
+}
+void launch_iota2(int n, int* tags, int* slots, cudaStream_t st) {
+  if (n > 0) k_iota2<<<(n + 255) / 256, 256, 0, st>>>(n, tags, slots);
+}
+void launch_invert_tags(int n, const int* tags, int* slots, cudaStream_t st) {
+  if (n > 0) k_invert_tags<<<(n + 255) / 256, 256, 0, st>>>(n, tags, slots);
+}
+void launch_avm_topology_by_tag(const AvmArgs& a, const int* vslot, const int* cslot, int* vc_out, int* vn_out,
+                                int* cc_out, int* cv_out, cudaStream_t st) {
+  k_avm_topology_by_tag<<<blocks_of(a.V), kAvmThreads, 0, st>>>(a, vslot, cslot, vc_out, vn_out, cc_out, cv_out);
 }
 void launch_avm_p0s(const AvmArgs& a, cudaStream_t st) {
   k_avm_p0s<<<blocks_of(a.n), kAvmThreads, 0, st>>>(a);

@@ -113,6 +113,31 @@ __device__ __forceinline__ int bin_begin(const int* local, const int* partial, i
   return local[b] + partial[b / kScanChunk];
 }
 
+// Position of grid cell (x, y) along the Hilbert curve of side 2^order:
+// at each level the quadrant fixes two digits of the index, and the
+// coordinates inside the quadrant are rotated/reflected so that the curve
+// enters every sub-square at its start.
+__device__ __forceinline__ unsigned hilbert_index(int order, unsigned x, unsigned y) {
+  unsigned d = 0;
+  for (int lev = order - 1; lev >= 0; --lev) {
+    const unsigned s = 1u << lev;
+    const unsigned rx = (x >> lev) & 1u, ry = (y >> lev) & 1u;
+    d += s * s * ((3u * rx) ^ ry);
+    x &= s - 1u;
+    y &= s - 1u;
+    if (ry == 0) {
+      if (rx == 1) {
+        x = s - 1u - x;
+        y = s - 1u - y;
+      }
+      const unsigned t = x;
+      x = y;
+      y = t;
+    }
+  }
+  return d;
+}
+
 __device__ __forceinline__ void raise_status(Ctl* ctl, int code) {
   atomicCAS(&ctl->status, 0, code);
 }

@@ -10,6 +10,8 @@ struct Rep;
 struct Ctl;
 
 constexpr int kGeomThreads = 32;   // one warp: finer blocks than 64 cut k_geom by ~4% at N = 262144
+constexpr int kGeomSh = 10;        // ring slots of k_geom held in shared memory (longer rings: local)
+constexpr int kGeomMinBlocks = 20;  // resident one-warp blocks per SM that k_geom is compiled for
 constexpr int kForceThreads = 128;
 constexpr int kTestThreads = 128;
 constexpr int kRepairWarps = 4;  // warps per repair block
@@ -293,8 +295,10 @@ struct AvmArgs {
   float2* hf;                // [V] float copies of the current positions
   int t1_cap, apply_blocks;
   unsigned long long* lock;  // [n] pass-stamped T1 locks
-  int* cand_e;               // [3V/2 + n] proposed edge ids 3v+s, or 3V + c for a T2 of cell c
+  int* cand_e;               // [3V/2 + n] proposed edges 3v+s (slots), or 3V + c for a T2 of cell slot c
+  int* cand_k;               // [3V/2 + n] their priorities: the same ids in tags
   int4* cand;                // [3V/2 + n] their cells (i, j, k, l), or (c, and the three across its edges)
+  const int *vtag, *ctag;    // [V], [n] the tag (API id) of each vertex and cell slot
   unsigned int* done;        // [2] last-block counters (force/move, T1 apply)
   cudaGraphConditionalHandle loop;  // while-node handle of the T1 passes
 };
@@ -318,6 +322,39 @@ void launch_avm_p0s(const AvmArgs& a, cudaStream_t st);
 void launch_avm_divide(const AvmArgs& a, int count, const int* cells, const double* dirs, const int* cslots,
                        const int* vslots, int* made, unsigned long long* dlock, cudaStream_t st);
 void launch_avm_shadow(const AvmArgs& a, cudaStream_t st);
+// Storage order of the AVM (Hilbert re-sort of the vertex and cell slots).
+// Every slot carries a tag, its id in the network as built (and as the API
+// speaks of it); vslot/cslot map tags back to slots.  The *_s arrays receive
+// the permuted copies before they are copied back.
+struct AvmSortArgs {
+  int n, V;
+  Ctl* ctl;
+  double Lx, Ly;
+  int hord_v, hord_c;             // Hilbert grid of side 2^hord for vertices and cells
+  int by_tag;                     // 1: key = tag (back to the order as built)
+  const double *hx, *hy;          // [2][V]
+  double *hx_w, *hy_w;            // the same buffers (written: the permuted copy into the other half)
+  int *vc, *vn, *cc, *cv;
+  double *theta, *p0, *v0, *a0, *P0;
+  int *vtag, *ctag, *vslot, *cslot;
+  int *vkey, *vrank, *vperm, *ckey, *crank, *cperm;
+  int *kcount_v, *kstart_v, *kpart_v, *kcount_c, *kstart_c, *kpart_c;
+  int *vc_s, *vn_s, *cc_s, *cv_s, *vtag_s, *ctag_s;
+  double *theta_s, *p0_s, *v0_s, *a0_s, *P0_s;
+};
+// Re-sorts vertices and cells along Hilbert curves (keys: vertex position;
+// a cell's first vertex; freed vertices and empty cells last), or by tag
+// (by_tag: every slot back to its tag).  Leaves the positions in the other
+// buffer and flips ctl->cur.  Key counts: kcount/kstart [max(keys, V) + 2]
+void launch_avm_sort(const AvmSortArgs& a, cudaStream_t st);
+// Identity tags (tags[i] = slots[i] = i)
+void launch_iota2(int n, int* tags, int* slots, cudaStream_t st);
+// slots[tags[i]] = i
+void launch_invert_tags(int n, const int* tags, int* slots, cudaStream_t st);
+// Network in tag order (for the API): dst arrays indexed by tag, entries
+// renamed to tags (-1 kept)
+void launch_avm_topology_by_tag(const AvmArgs& a, const int* vslot, const int* cslot, int* vc_out, int* vn_out,
+                                int* cc_out, int* cv_out, cudaStream_t st);
 void launch_fill_d(int n, double v, double* out, cudaStream_t st);
 void launch_fill_u64(int n, unsigned long long v, unsigned long long* out, cudaStream_t st);
 

@@ -32,12 +32,26 @@ namespace cgk {
 // (exact) folds into the per-cell constants (A x 1/4, P x 1/2, dA/dh x 1/2,
 // s x 2 against w / 2) and the results equal those of h itself bit for bit.
 // Integer-to-double conversions run on the integer pipes (i2d_int).
-__global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
-  __shared__ double sh_hx[CG_RING][kGeomThreads];
-  __shared__ double sh_hy[CG_RING][kGeomThreads];
-  __shared__ double sh_ex[CG_RING][kGeomThreads];  // unit vector of the edge ending at vertex a
-  __shared__ double sh_ey[CG_RING][kGeomThreads];
+//
+// Per ring slot the kernel keeps the circumcentre and the unit vector of the
+// edge ending there for the force-set pass: the first kGeomSh slots in shared
+// memory (10 KB per one-warp block, so that 20 blocks fit on an SM), the
+// slots of longer rings (rare) in local memory.
+__global__ void __launch_bounds__(kGeomThreads, kGeomMinBlocks) k_geom(GeomArgs g) {
+  __shared__ double sh_hx[kGeomSh][kGeomThreads];
+  __shared__ double sh_hy[kGeomSh][kGeomThreads];
+  __shared__ double sh_ex[kGeomSh][kGeomThreads];  // unit vector of the edge ending at vertex a
+  __shared__ double sh_ey[kGeomSh][kGeomThreads];
+  constexpr int kLo = (CG_RING > kGeomSh) ? CG_RING - kGeomSh : 1;
+  double lo_hx[kLo], lo_hy[kLo], lo_ex[kLo], lo_ey[kLo];
   const int t = threadIdx.x;
+  auto put = [&](double (&sh)[kGeomSh][kGeomThreads], double* lo, int a, double v) {
+    if (a < kGeomSh) sh[a][t] = v;
+    else lo[a - kGeomSh] = v;
+  };
+  auto get = [&](const double (&sh)[kGeomSh][kGeomThreads], const double* lo, int a) -> double {
+    return (a < kGeomSh) ? sh[a][t] : lo[a - kGeomSh];
+  };
   const size_t N = (size_t)g.n;
   const int cur = g.ctl->cur;
   const long long* __restrict__ X = g.X + (size_t)cur * N;
@@ -92,8 +106,8 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
       const double hx = (by * la - ay * lb) * r;
       const double hy = (ax * lb - bx * la) * r;
       g.s[a * N + i] = make_double2(hx * r, hy * r);
-      sh_hx[a][t] = hx;
-      sh_hy[a][t] = hy;
+      put(sh_hx, lo_hx, a, hx);
+      put(sh_hy, lo_hy, a, hy);
       if (a == 0) {
         h0x = hx; h0y = hy;
       } else {
@@ -102,8 +116,8 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
         const double l2 = ex * ex + ey * ey;
         const double il = (__double_as_longlong(l2) > 0) ? fx_rsqrt(l2) : 0.0;  // zero-length edge: no direction
         per += l2 * il;
-        sh_ex[a][t] = ex * il;
-        sh_ey[a][t] = ey * il;
+        put(sh_ex, lo_ex, a, ex * il);
+        put(sh_ey, lo_ey, a, ey * il);
       }
       hpx = hx; hpy = hy;
       ax = bx; ay = by; la = lb;
@@ -130,8 +144,10 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom(GeomArgs g) {
     for (int a = 0; a < m; ++a) {
       const int ap = (a == 0) ? m - 1 : a - 1;
       const int an = (a + 1 == m) ? 0 : a + 1;
-      const double gx = sh_hy[an][t] - sh_hy[ap][t], gy = sh_hx[ap][t] - sh_hx[an][t];
-      const double dPx = sh_ex[a][t] - sh_ex[an][t], dPy = sh_ey[a][t] - sh_ey[an][t];
+      const double gx = get(sh_hy, lo_hy, an) - get(sh_hy, lo_hy, ap);
+      const double gy = get(sh_hx, lo_hx, ap) - get(sh_hx, lo_hx, an);
+      const double dPx = get(sh_ex, lo_ex, a) - get(sh_ex, lo_ex, an);
+      const double dPy = get(sh_ey, lo_ey, a) - get(sh_ey, lo_ey, an);
       g.fs[a * N + i] = make_double2(fma(ka, gx, kp * dPx), fma(ka, gy, kp * dPy));
     }
   }
