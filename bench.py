@@ -57,6 +57,9 @@ FLOPS_PER_CELL = {"geometry": 277.0, "force_move": 93.0}
 # of k_avm_force_move (3 edges x (offset, length, rsqrt, unit vector) + 3 force
 # terms x 8 + activity and move).
 AVM_FLOPS = {"cells_per_cell": 95.0, "vertices_per_vertex": 62.0}
+# AVM storage order: Hilbert re-sort of the vertex and cell slots at creation
+# and every this many steps (Sec. 2.B; results are the same either way).
+AVM_SORT_EVERY = 100
 # Algorithmic bytes per cell-step of the whole step (state read + written once).
 BYTES_PER_CELL_STEP = 84.0
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
@@ -64,7 +67,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # Dominant-kernel DRAM traffic per launch (dram__bytes_read.sum +
 # dram__bytes_write.sum) from one ncu capture of the current k_geom at
 # N = 262144; None whenever the kernel has changed since the capture.
-GEOM_DRAM_BYTES_PER_LAUNCH = 42.66e6
+GEOM_DRAM_BYTES_PER_LAUNCH = None
 
 
 def parse():
@@ -484,7 +487,8 @@ def avm_throughput(args, device):
 
     n, thr, p0, v0 = 65536, 0.04, 3.8, 0.1
     x, y, th, L = workloads.spv_uniform(n, 21)
-    sim = cg.AVM(n, L, L, x, y, th, p0=p0, v0=v0, dt=DT, t1_threshold=thr, seed=21, device=device)
+    sim = cg.AVM(n, L, L, x, y, th, p0=p0, v0=v0, dt=DT, t1_threshold=thr, seed=21, sort_every=AVM_SORT_EVERY,
+                 device=device)
     sim.step(args.avm_warmup)
     sim.sync()
     c0 = sim.counters()
@@ -523,6 +527,7 @@ def avm_throughput(args, device):
             "vertex_steps_per_s": V * K / (ms * 1e-3) if K else None,
             "cell_steps_per_s": n * K / (ms * 1e-3) if K else None,
             "ms_per_step": ms / Kd if K else None, "steps": K, "warmup": args.avm_warmup, "l2": "flushed between timed steps",
+            "sort_every": AVM_SORT_EVERY,
             "gpu_launches": launches,
             "t1_per_step": (c1["t1_total"] - c0["t1_total"]) / Kd,
             "t1_passes_per_step": (c1["t1_passes"] - c0["t1_passes"]) / Kd,
@@ -552,7 +557,7 @@ def avm_death_throughput(args, device):
     x, y, th, L = workloads.spv_uniform(n, 21)
     cap = n + n // 50
     sim = cg.AVM(n, L, L, x, y, th, p0=p0, v0=v0, dt=DT, t1_threshold=thr, t2_area=0.01, seed=21, capacity=cap,
-                 device=device)
+                 sort_every=AVM_SORT_EVERY, device=device)
     sim.step(args.avm_warmup)
     a0 = np.ones(cap)
     a0[np.random.default_rng(5).choice(n, n // 100, replace=False)] = 0.0
@@ -688,17 +693,19 @@ def sweep(args):
     avm_rows = []
     for n in (4096, 16384, 65536, 262144, 1048576):
         x, y, th, L = workloads.spv_uniform(n, 7)
-        sim = cg.AVM(n, L, L, x, y, th, p0=3.8, v0=0.1, dt=0.01, t1_threshold=0.04, seed=7)
-        sim.step(50)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        sim.step(200)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        sim.sync()
-        sim.close()
-        gms = e0.elapsed_time(e1) / 200
+        gms = {}
+        for every in (0, AVM_SORT_EVERY):  # without and with the re-sort
+            sim = cg.AVM(n, L, L, x, y, th, p0=3.8, v0=0.1, dt=0.01, t1_threshold=0.04, seed=7, sort_every=every)
+            sim.step(50)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sim.step(200)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sim.sync()
+            sim.close()
+            gms[every] = e0.elapsed_time(e1) / 200
         cms = None
         if n <= 262144:
             Lx, Ly, q = oracle.box(L)
@@ -712,8 +719,9 @@ def sweep(args):
                 if el > 2.0 or k >= 50:
                     break
             cms = 1e3 * el / k
-        avm_rows.append({"n": n, "vertices": 2 * n, "gpu_ms_per_step": gms, "cpu_oracle_ms_per_step": cms,
-                         "ratio": (cms / gms) if cms else None})
+        avm_rows.append({"n": n, "vertices": 2 * n, "gpu_ms_per_step": gms[AVM_SORT_EVERY],
+                         "gpu_ms_per_step_unsorted": gms[0], "sort_every": AVM_SORT_EVERY,
+                         "cpu_oracle_ms_per_step": cms, "ratio": (cms / gms[AVM_SORT_EVERY]) if cms else None})
     print(json.dumps({"study": "SPV time per step vs N and p0, Hilbert re-sort period, AVM vs N (GB300, FP64)",
                       "rows": rows, "sort_rows": sort_rows, "avm_rows": avm_rows}), flush=True)
 

@@ -30,6 +30,7 @@ struct AvmOff {
       done;
   size_t owned, base_local, base_partial, xs, ys, cnt, nbr, scalar, ctl, dir_tab;
   size_t div_cells, div_dirs, div_made, div_cslots, div_vslots, div_lock;  // staging of cg_avm_divide
+  size_t div_flag, div_pos, div_ctl;                                       // its rounds
   // storage order: tags of the slots, slots of the tags, candidate priorities
   size_t vtag, ctag, vslot, cslot, cand_k;
   // re-sort scratch (keys, ranks, new places, key counts, permuted copies);
@@ -87,6 +88,9 @@ AvmOff avm_layout(int64_t n, size_t spv_bytes) {
   o.div_cslots = L.take(n * i4);
   o.div_vslots = L.take(2 * n * i4);
   o.div_lock = L.take(n * sizeof(unsigned long long));
+  o.div_flag = L.take(kDivWindow * i4);
+  o.div_pos = L.take(kDivWindow * i4);
+  o.div_ctl = L.take(sizeof(DivCtl));
   o.vtag = L.take(V * i4);
   o.ctag = L.take(n * i4);
   o.vslot = L.take(V * i4);
@@ -134,6 +138,7 @@ struct cg_avm_ctx {
   cudaEvent_t fork = nullptr, join = nullptr;
   cudaGraphExec_t exec = nullptr;     // one step
   cudaGraphExec_t t1_exec = nullptr;  // T1 passes alone
+  cudaGraphExec_t div_exec = nullptr;  // the division rounds of cg_avm_divide
   int sms = 0;
   int hord_v = 0, hord_c = 0;  // Hilbert grids of the re-sort
   int since_sort = 0;          // steps since the last re-sort
@@ -399,13 +404,46 @@ int avm_graphs(cg_avm_ctx* c) {
       },
       [c](cudaStream_t st) { cudaStreamWaitEvent(st, c->join, 0); }, &c->exec);
   if (rc) return rc;
-  return loop_graph(
+  rc = loop_graph(
       c,
       [](const AvmArgs& a, cudaStream_t st) {
         launch_avm_begin_t1(a.ctl, st);
         launch_avm_t1_pass(a, st);
       },
       [](cudaStream_t) {}, &c->t1_exec);
+  if (rc) return rc;
+  // division rounds: locks, prefix, dry runs, slots, application, advance
+  DivArgs d{};
+  d.g = avm_args(c);
+  d.cells = c->at<int>(c->off.div_cells);
+  d.dirs = c->at<double>(c->off.div_dirs);
+  d.cslots = c->at<int>(c->off.div_cslots);
+  d.vslots = c->at<int>(c->off.div_vslots);
+  d.made = c->at<int>(c->off.div_made);
+  d.dlock = c->at<unsigned long long>(c->off.div_lock);
+  d.flag = c->at<int>(c->off.div_flag);
+  d.pos = c->at<int>(c->off.div_pos);
+  d.dc = c->at<DivCtl>(c->off.div_ctl);
+  if (c->div_exec) {
+    cudaGraphExecDestroy(c->div_exec);
+    c->div_exec = nullptr;
+  }
+  cudaError_t e = build_loop_graph(
+      c->capture,
+      [&](cudaGraphConditionalHandle h, cudaStream_t st) {
+        d.loop = h;
+        launch_avm_divide_begin(d, st);
+      },
+      [&](cudaGraphConditionalHandle h, cudaStream_t st) {
+        d.loop = h;
+        launch_avm_divide_round(d, st);
+      },
+      [](cudaStream_t) {}, &c->div_exec);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return afail(c, CG_ECUDA, std::string("building the division graph: ") + cudaGetErrorString(e));
+  }
+  return CG_OK;
 }
 
 }  // namespace
@@ -762,37 +800,37 @@ int cg_avm_divide(cg_avm_ctx* c, int32_t count, const int32_t* cells, const doub
   if (!cells || !dirs || count > c->n) return CG_EINVAL;
   int rc = avm_status(c);
   if (rc) return rc;
-  // the slots the divisions may take, in order: the empty cells and the free
-  // vertices of lowest tag (a call only fills slots)
-  std::vector<int> hcc(c->n), hvc(3 * (size_t)c->V), hcs(c->n), hvs(c->V), cs, vs;
-  AV_CUDA(c, cudaMemcpy(hcc.data(), c->at<int>(c->off.cc), hcc.size() * sizeof(int), cudaMemcpyDeviceToHost));
-  AV_CUDA(c, cudaMemcpy(hvc.data(), c->at<int>(c->off.vc), hvc.size() * sizeof(int), cudaMemcpyDeviceToHost));
-  AV_CUDA(c, cudaMemcpy(hcs.data(), c->at<int>(c->off.cslot), hcs.size() * sizeof(int), cudaMemcpyDeviceToHost));
-  AV_CUDA(c, cudaMemcpy(hvs.data(), c->at<int>(c->off.vslot), hvs.size() * sizeof(int), cudaMemcpyDeviceToHost));
-  for (int k = 0; k < c->n && (int)cs.size() < count; ++k)
-    if (hcc[hcs[k]] == 0) cs.push_back(hcs[k]);
-  for (int v = 0; v < c->V && (int)vs.size() < 2 * count; ++v)
-    if (hvc[3 * (size_t)hvs[v]] < 0) vs.push_back(hvs[v]);
-  if ((int)cs.size() < count || (int)vs.size() < 2 * count)
-    return afail(c, CG_EINVAL, "not enough free cell slots for the divisions");
-  // the cells named by tag, in slots (an index out of range stays so and is
-  // refused by the kernel)
-  std::vector<int> hcells(count);
-  AV_CUDA(c, cudaMemcpy(hcells.data(), cells, (size_t)count * sizeof(int), cudaMemcpyDefault));
-  for (int& x : hcells)
-    if ((unsigned)x < (unsigned)c->n) x = hcs[x];
+  // staged: the cells (tags) and directions; on the device the cells are
+  // mapped to slots and the slots the divisions may take listed in order
+  // (the empty cells and the free vertices of lowest tag: a call only fills
+  // slots); the host reads back how many there are
+  DivCtl* dctl = c->at<DivCtl>(c->off.div_ctl);
   int* dc = c->at<int>(c->off.div_cells);
   double* dd = c->at<double>(c->off.div_dirs);
   int* dm = c->at<int>(c->off.div_made);
-  int* dcs = c->at<int>(c->off.div_cslots);
-  int* dvs = c->at<int>(c->off.div_vslots);
-  if ((rc = copy_in(c, dc, hcells.data(), (size_t)count * sizeof(int)))) return rc;
+  if ((rc = copy_in(c, dc, cells, (size_t)count * sizeof(int)))) return rc;
   if ((rc = copy_in(c, dd, dirs, 2 * (size_t)count * sizeof(double)))) return rc;
-  AV_CUDA(c, cudaMemcpyAsync(dcs, cs.data(), cs.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-  AV_CUDA(c, cudaMemcpyAsync(dvs, vs.data(), vs.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  AV_CUDA(c, cudaMemcpyAsync(&dctl->count, &count, sizeof(int), cudaMemcpyHostToDevice, c->stream));
   launch_check_finite(2 * count, dd, c->ctl(), c->stream);
-  launch_avm_divide(avm_args(c), count, dc, dd, dcs, dvs, dm, c->at<unsigned long long>(c->off.div_lock),
-                    c->stream);
+  DivArgs d{};
+  d.g = avm_args(c);
+  d.cells = dc;
+  d.cslots = c->at<int>(c->off.div_cslots);
+  d.vslots = c->at<int>(c->off.div_vslots);
+  d.dc = dctl;
+  launch_avm_divide_slots(d, c->at<int>(c->off.cslot), c->at<int>(c->off.vslot), c->at<int>(c->off.kcount_c),
+                          c->at<int>(c->off.kstart_c), c->at<int>(c->off.kpart_c), c->at<int>(c->off.kcount_v),
+                          c->at<int>(c->off.kstart_v), c->at<int>(c->off.kpart_v), c->stream);
+  // the re-sort's key counts served as scan input: cleared again
+  AV_CUDA(c, cudaMemsetAsync(c->at<int>(c->off.kcount_c), 0, ((size_t)c->n + 2) * sizeof(int), c->stream));
+  AV_CUDA(c, cudaMemsetAsync(c->at<int>(c->off.kcount_v), 0, ((size_t)c->V + 2) * sizeof(int), c->stream));
+  int freec[2] = {0, 0};
+  AV_CUDA(c, cudaMemcpyAsync(freec, &dctl->free_c, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  rc = avm_status(c);  // synchronizes
+  if (rc) return rc;
+  if (freec[0] < count || freec[1] < 2 * count)
+    return afail(c, CG_EINVAL, "not enough free cell slots for the divisions");
+  AV_CUDA(c, cudaGraphLaunch(c->div_exec, c->stream));
   launch_avm_dir(avm_args(c), c->stream);  // the daughters' director terms
   AV_CUDA(c, cudaGetLastError());
   std::vector<int> hm(count);
@@ -863,6 +901,7 @@ int cg_avm_destroy(cg_avm_ctx* c) {
   if (!c) return CG_EINVAL;
   if (c->exec) cudaGraphExecDestroy(c->exec);
   if (c->t1_exec) cudaGraphExecDestroy(c->t1_exec);
+  if (c->div_exec) cudaGraphExecDestroy(c->div_exec);
   if (c->capture) cudaStreamDestroy(c->capture);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->fork) cudaEventDestroy(c->fork);

@@ -948,146 +948,188 @@ __device__ int divide_cell(const AvmArgs& g, int c, double ux, double uy, int ne
 
 // The divisions of a call, with the result of doing them one after the other
 // in request order (each seeing the network the previous ones left), in
-// rounds of one block.  Division k reads and writes only the cells of its
-// mother's 1-ring (the mother, the cells across its edges) and the vertices
-// between them, plus fresh slots; divisions whose 1-rings are disjoint
-// therefore commute.  Each round, the pending divisions of a window take a
-// 64-bit atomic minimum of (round stamp, request index) on every cell of their
-// 1-ring (the stamp makes this round's keys smaller than any earlier one's, so
-// the locks are never cleared within a call); the longest prefix of the window
-// whose divisions all hold their locks is mutually disjoint and disjoint from
-// every division after it.  Its divisions are tried without writing
-// (made or not), a block scan of the outcome gives each made one its slots in
-// request order (the next unused entries of cslots and of vslots, two each),
-// and they are applied together.  A division of a cell slot without a polygon
-// (empty: an earlier division of the call may fill it) waits until it is the
-// first pending one.  The first pending division always holds its locks, so
-// every round makes progress.  made[k] = 1 when division k was made.
-constexpr int kDivThreads = 256;
-__global__ void __launch_bounds__(kDivThreads) k_avm_divide_rounds(AvmArgs g, int count, const int* cells,
-                                                                   const double* dirs, const int* cslots,
-                                                                   const int* vslots, int* made,
-                                                                   unsigned long long* dlock) {
-  __shared__ int s_start, s_end, s_used, s_stop;
-  __shared__ int s_scan[kDivThreads];
-  const int t = threadIdx.x;
-  if (t == 0) {
-    s_start = 0;
-    s_used = 0;
-    s_stop = 0;
-  }
-  __syncthreads();
-  const unsigned V = (unsigned)g.V, n = (unsigned)g.n;
-  for (unsigned round = 0;; ++round) {
-    const int start = s_start;
-    if (start >= count || s_stop) break;
-    const int wend = min(count, start + kDivThreads);
-    const int k = start + t;
-    const bool mine = k < wend;
-    const unsigned long long key = ((unsigned long long)(0xffffffffu - round) << 32) | (unsigned)k;
-    const int c = mine ? cells[k] : -1;
-    const bool valid = mine && (unsigned)c < n;
-    const int m = valid ? g.cc[c] : 0;
-    const bool poly = m >= 3 && m <= CG_RING;
-    if (valid) {
-      atomicMin(&dlock[c], key);
-      if (poly)
-        for (int a = 0; a < m; ++a) {
-          const int v = g.cv[(size_t)c * CG_RING + a];
-          if ((unsigned)v < V)
-            for (int q = 0; q < 3; ++q) {
-              const int x = g.vc[3 * v + q];
-              if ((unsigned)x < n) atomicMin(&dlock[x], key);
-            }
-        }
-    }
-    if (t == 0) s_end = wend;
-    __syncthreads();
-    // a mother without a polygon (an empty slot, which an earlier division
-    // of the call may fill) waits until it is the first pending division
-    bool ok = valid && dlock[c] == key && (poly || k == start);
-    if (valid && poly)
-      for (int a = 0; a < m && ok; ++a) {
-        const int v = g.cv[(size_t)c * CG_RING + a];
-        if ((unsigned)v < V)
-          for (int q = 0; q < 3; ++q) {
-            const int x = g.vc[3 * v + q];
-            if ((unsigned)x < n && dlock[x] != key) ok = false;
-          }
+// rounds: the body of a conditional while node (launch_avm_divide_round).
+// Division k reads and writes only the cells of its mother's 1-ring (the
+// mother, the cells across its edges) and the vertices between them, plus
+// fresh slots; divisions whose 1-rings are disjoint therefore commute.  Each
+// round, the pending divisions of a window of kDivWindow take a 64-bit atomic
+// minimum of (round stamp, request index) on every cell of their 1-ring (the
+// stamp makes this round's keys smaller than any earlier one's, so the locks
+// are never cleared within a call); the longest prefix of the window whose
+// divisions all hold their locks is mutually disjoint and disjoint from every
+// division after it.  Its divisions are tried without writing (made or not),
+// one per block so that their FP64 work spreads over the SMs; a block scan of
+// the outcomes gives each made one its slots in request order (the next
+// unused entries of cslots and of vslots, two each); they are then applied
+// together.  A division of a cell slot without a polygon (empty: an earlier
+// division of the call may fill it) waits until it is the first pending one.
+// The first pending division always holds its locks, so every round makes
+// progress.  made[k] = 1 when division k was made.
+constexpr int kDivLockThreads = 128;
+
+__device__ __forceinline__ unsigned long long div_key(int round, int k) {
+  return ((unsigned long long)(0xffffffffu - (unsigned)round) << 32) | (unsigned)k;
+}
+
+// Visits the cells of the 1-ring of c (c itself, then the cells of each of
+// its vertices; repeats included).
+template <class F>
+__device__ __forceinline__ void for_ring_cells(const AvmArgs& g, int c, int m, F f) {
+  f(c);
+  for (int a = 0; a < m; ++a) {
+    const int v = g.cv[(size_t)c * CG_RING + a];
+    if ((unsigned)v < (unsigned)g.V)
+      for (int q = 0; q < 3; ++q) {
+        const int x = g.vc[3 * v + q];
+        if ((unsigned)x < (unsigned)g.n) f(x);
       }
-    if (mine && !ok) atomicMin(&s_end, k);
-    __syncthreads();
-    const int end = s_end;
-    if (end == start) {  // the first pending division can only fail by an invalid cell index
-      if (t == 0) {
-        raise_status(g.ctl, kEINVAL);
-        s_stop = 1;
-      }
-      __syncthreads();
-      break;
-    }
-    int flag = 0;
-    if (k < end) {
-      const int r = divide_cell(g, c, dirs[2 * k], dirs[2 * k + 1], 0, 0, 0, false);
-      if (r < 0) {
-        raise_status(g.ctl, kETOPO);
-        s_stop = 1;
-      }
-      flag = (r == 0);
-    }
-    s_scan[t] = flag;
-    __syncthreads();
-    for (int off = 1; off < kDivThreads; off <<= 1) {  // inclusive scan
-      const int add = t >= off ? s_scan[t - off] : 0;
-      __syncthreads();
-      s_scan[t] += add;
-      __syncthreads();
-    }
-    const int slot = s_used + s_scan[t] - flag;
-    if (k < end && !s_stop) {
-      made[k] = flag;
-      if (flag && divide_cell(g, c, dirs[2 * k], dirs[2 * k + 1], cslots[slot], vslots[2 * slot],
-                              vslots[2 * slot + 1]) != 0) {
-        raise_status(g.ctl, kETOPO);
-        s_stop = 1;
-      }
-    }
-    __syncthreads();
-    if (t == 0) {
-      s_used += s_scan[kDivThreads - 1];
-      s_start = end;
-    }
-    __syncthreads();
   }
 }
 
-// The divisions of a call, one after the other (one thread: each sees the
-// network the previous ones left).  Division k, if made, takes the next
-// unused entries of cslots (cell slot) and vslots (two vertex slots), the
-// empty slots in increasing order; made[k] = 1 when division k was made.
-// Kept as the plain statement of the rule (cg_avm_divide runs the rounds
-// above, which give the same result).
-__global__ void k_avm_divide(AvmArgs g, int count, const int* cells, const double* dirs, const int* cslots,
-                             const int* vslots, int* made) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  int m = 0;
-  for (int k = 0; k < count; ++k) {
-    made[k] = 0;
-    const int c = cells[k];
-    if ((unsigned)c >= (unsigned)g.n) {
-      raise_status(g.ctl, kEINVAL);
-      return;
+// The free slots a call's divisions may take, in increasing tag order: empty
+// cells (cc = 0) and free vertices (vc = -1), compacted on the device (flags,
+// the counting-sort scan, a scatter); the cells the call names (tags) mapped
+// to their slots.
+__global__ void k_div_free_flags(AvmArgs g, const int* cslot, const int* vslot, int* fc, int* fv) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < g.n) fc[t] = g.cc[cslot[t]] == 0;
+  if (t < g.V) fv[t] = g.vc[3 * vslot[t]] < 0;
+}
+
+__global__ void k_div_free_list(DivArgs d, const int* cslot, const int* vslot, const int* fc, const int* sc,
+                                const int* scp, const int* fv, const int* sv, const int* svp) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = d.g.n, V = d.g.V, want = d.dc->count;
+  if (t < n) {
+    if (fc[t]) {
+      const int p = bin_begin(sc, scp, t);
+      if (p < want) d.cslots[p] = cslot[t];
     }
-    const int r = divide_cell(g, c, dirs[2 * k], dirs[2 * k + 1], cslots[m], vslots[2 * m], vslots[2 * m + 1]);
-    if (r < 0) {
-      raise_status(g.ctl, kETOPO);
-      return;
-    }
-    if (r == 0) {
-      made[k] = 1;
-      ++m;
+    const int k = t;  // the named cells, tags -> slots
+    if (k < want) {
+      const int c = d.cells[k];
+      if ((unsigned)c < (unsigned)n) d.cells[k] = cslot[c];
     }
   }
+  if (t < V && fv[t]) {
+    const int p = bin_begin(sv, svp, t);
+    if (p < 2 * want) d.vslots[p] = vslot[t];
+  }
+  if (t == 0) {
+    d.dc->free_c = bin_begin(sc, scp, n);
+    d.dc->free_v = bin_begin(sv, svp, V);
+  }
+}
+
+__global__ void k_div_begin(DivArgs d) {
+  DivCtl* dc = d.dc;
+  dc->start = 0;
+  dc->used = 0;
+  dc->round = 0;
+  dc->stop = 0;
+}
+
+__global__ void __launch_bounds__(kDivLockThreads) k_div_lock(DivArgs d) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  // stop the loop unless the closing kernel of this round asks for another
+  if (t == 0 && d.loop) cudaGraphSetConditional(d.loop, 0);
+  DivCtl* dc = d.dc;
+  const int start = dc->start, wend = min(dc->count, start + kDivWindow);
+  if (t == 0) dc->end = wend;
+  const int k = start + t;
+  if (k >= wend || dc->stop) return;
+  const int c = d.cells[k];
+  if ((unsigned)c >= (unsigned)d.g.n) return;
+  const int m = d.g.cc[c];
+  const unsigned long long key = div_key(dc->round, k);
+  for_ring_cells(d.g, c, (m >= 3 && m <= CG_RING) ? m : 0, [&](int x) { atomicMin(&d.dlock[x], key); });
+}
+
+__global__ void __launch_bounds__(kDivLockThreads) k_div_check(DivArgs d) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  DivCtl* dc = d.dc;
+  const int start = dc->start, wend = min(dc->count, start + kDivWindow);
+  const int k = start + t;
+  if (k >= wend || dc->stop) return;
+  const int c = d.cells[k];
+  bool ok = (unsigned)c < (unsigned)d.g.n;
+  if (ok) {
+    const int m = d.g.cc[c];
+    const bool poly = m >= 3 && m <= CG_RING;
+    // a mother without a polygon waits until it is the first pending division
+    ok = poly || k == start;
+    const unsigned long long key = div_key(dc->round, k);
+    for_ring_cells(d.g, c, poly ? m : 0, [&](int x) { ok = ok && d.dlock[x] == key; });
+  }
+  if (!ok) atomicMin(&dc->end, k);
+}
+
+// One block per division of the round's prefix (lane 0 works): the dry run.
+__global__ void k_div_dry(DivArgs d) {
+  if (threadIdx.x != 0) return;
+  DivCtl* dc = d.dc;
+  const int b = blockIdx.x, start = dc->start, end = dc->end;
+  const int k = start + b;
+  int flag = 0;
+  if (b == 0 && end == start && start < dc->count && !dc->stop) {
+    // the first pending division can only fail by an invalid cell index
+    raise_status(d.g.ctl, kEINVAL);
+    dc->stop = 1;
+  }
+  if (k < end && !dc->stop) {
+    const int r = divide_cell(d.g, d.cells[k], d.dirs[2 * k], d.dirs[2 * k + 1], 0, 0, 0, false);
+    if (r < 0) {
+      raise_status(d.g.ctl, kETOPO);
+      dc->stop = 1;
+    }
+    flag = (r == 0);
+  }
+  d.flag[b] = flag;
+}
+
+// The slots of the made divisions of the round (one block of kDivWindow).
+__global__ void __launch_bounds__(kDivWindow) k_div_scan(DivArgs d) {
+  __shared__ int warp_tot[kDivWindow / 32];
+  DivCtl* dc = d.dc;
+  const int t = threadIdx.x, start = dc->start, nr = dc->end - start, used = dc->used;
+  const int f = t < nr ? d.flag[t] : 0;
+  const int lane = t & 31, wid = t >> 5;
+  int incl = f;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  int woff = 0;
+  for (int w = 0; w < wid; ++w) woff += warp_tot[w];
+  d.pos[t] = used + woff + incl - f;
+  if (t < nr) d.made[start + t] = f;
+  __syncthreads();
+  if (t == kDivWindow - 1) dc->used = used + woff + incl;
+}
+
+// One block per division of the round's prefix (lane 0 works): applied.
+__global__ void k_div_commit(DivArgs d) {
+  if (threadIdx.x != 0) return;
+  DivCtl* dc = d.dc;
+  const int b = blockIdx.x, k = dc->start + b;
+  if (k >= dc->end || !d.flag[b] || dc->stop) return;
+  const int p = d.pos[b];
+  if (divide_cell(d.g, d.cells[k], d.dirs[2 * k], d.dirs[2 * k + 1], d.cslots[p], d.vslots[2 * p],
+                  d.vslots[2 * p + 1]) != 0) {
+    raise_status(d.g.ctl, kETOPO);
+    dc->stop = 1;
+  }
+}
+
+__global__ void k_div_advance(DivArgs d) {
+  DivCtl* dc = d.dc;
+  dc->start = dc->end;
+  dc->round += 1;
+  const int more = dc->start < dc->count && !dc->stop && d.g.ctl->status == 0;
+  if (more && d.loop) cudaGraphSetConditional(d.loop, 1);
 }
 
 // Preferred perimeters P0_c = p0_c sqrt(A0_c); A0_c must be finite and >= 0.
@@ -1272,15 +1314,38 @@ void launch_avm_forces(const AvmArgs& a, cudaStream_t st) {
   k_avm_cells<<<cell_blocks_of(a.n), kAvmCellThreads, 0, st>>>(f);
   k_avm_force_move<<<vertex_blocks_of(a.V), kAvmVertexThreads, 0, st>>>(f);
 }
-void launch_avm_divide(const AvmArgs& a, int count, const int* cells, const double* dirs, const int* cslots,
-                       const int* vslots, int* made, unsigned long long* dlock, cudaStream_t st) {
-  if (count <= 0) return;
-  if (dlock) {
-    cudaMemsetAsync(dlock, 0xff, (size_t)a.n * sizeof(unsigned long long), st);
-    k_avm_divide_rounds<<<1, kDivThreads, 0, st>>>(a, count, cells, dirs, cslots, vslots, made, dlock);
-  } else {
-    k_avm_divide<<<1, 32, 0, st>>>(a, count, cells, dirs, cslots, vslots, made);
-  }
+void launch_avm_divide_slots(const DivArgs& d, const int* cslot, const int* vslot, int* fc, int* sc, int* scp,
+                             int* fv, int* sv, int* svp, cudaStream_t st) {
+  const int blocks = blocks_of(d.g.V);  // V = 2n covers the cells too
+  k_div_free_flags<<<blocks, kAvmThreads, 0, st>>>(d.g, cslot, vslot, fc, fv);
+  CellListArgs sc_args{};
+  sc_args.ctl = d.g.ctl;
+  sc_args.n = d.g.n;
+  sc_args.nbins = d.g.n;
+  sc_args.bin_count = fc;
+  sc_args.bin_start = sc;
+  sc_args.scan_partials = scp;
+  launch_scan(sc_args, st);
+  sc_args.n = d.g.V;
+  sc_args.nbins = d.g.V;
+  sc_args.bin_count = fv;
+  sc_args.bin_start = sv;
+  sc_args.scan_partials = svp;
+  launch_scan(sc_args, st);
+  k_div_free_list<<<blocks, kAvmThreads, 0, st>>>(d, cslot, vslot, fc, sc, scp, fv, sv, svp);
+}
+void launch_avm_divide_begin(const DivArgs& d, cudaStream_t st) {
+  cudaMemsetAsync(d.dlock, 0xff, (size_t)d.g.n * sizeof(unsigned long long), st);
+  cudaMemsetAsync(d.made, 0, (size_t)d.g.n * sizeof(int), st);
+  k_div_begin<<<1, 1, 0, st>>>(d);
+}
+void launch_avm_divide_round(const DivArgs& d, cudaStream_t st) {
+  k_div_lock<<<kDivWindow / kDivLockThreads, kDivLockThreads, 0, st>>>(d);
+  k_div_check<<<kDivWindow / kDivLockThreads, kDivLockThreads, 0, st>>>(d);
+  k_div_dry<<<kDivWindow, 32, 0, st>>>(d);
+  k_div_scan<<<1, kDivWindow, 0, st>>>(d);
+  k_div_commit<<<kDivWindow, 32, 0, st>>>(d);
+  k_div_advance<<<1, 1, 0, st>>>(d);
 }
 void launch_avm_sort(const AvmSortArgs& a, cudaStream_t st) {
   const int blocks = blocks_of(a.V);  // V = 2n covers the cells too

@@ -315,12 +315,41 @@ void launch_avm_forces(const AvmArgs& a, cudaStream_t st);
 void launch_avm_validate(const AvmArgs& a, cudaStream_t st);
 // P0[c] = p0[c] sqrt(a0[c]) after p0 or A0 change
 void launch_avm_p0s(const AvmArgs& a, cudaStream_t st);
-// count divisions (cells[k], direction dirs[2k], dirs[2k+1]) with the result
-// of doing them in order; the divisions made take cslots[0, 1, ...] and
-// vslots[0, 1, ...] in turn.  dlock ([n] scratch): conflict-free rounds in
-// one block; null: one thread, one division after the other
-void launch_avm_divide(const AvmArgs& a, int count, const int* cells, const double* dirs, const int* cslots,
-                       const int* vslots, int* made, unsigned long long* dlock, cudaStream_t st);
+// Divisions of a call (cells[k], direction dirs[2k], dirs[2k+1]) with the
+// result of doing them in order; the divisions made take cslots[0, 1, ...]
+// and vslots[0, 1, ...] in turn.  Conflict-free rounds: launch_avm_divide_begin
+// once, then launch_avm_divide_round as the body of a while node (its first
+// kernel clears the node's handle, its last sets it while divisions remain).
+constexpr int kDivWindow = 1024;  // divisions tried per round
+struct DivCtl {
+  int count;  // divisions of the call (set by the host)
+  int start;  // first pending division
+  int end;    // end of the round's prefix of lock holders
+  int used;   // divisions made so far (slots taken)
+  int round;
+  int stop;   // a status was raised
+  int free_c, free_v;  // free cell and vertex slots before the call
+};
+struct DivArgs {
+  AvmArgs g;
+  int* cells;  // the named cells (staged as tags, mapped to slots)
+  const double* dirs;
+  int *cslots, *vslots;
+  int* made;
+  unsigned long long* dlock;  // [n] round-stamped locks
+  int *flag, *pos;            // [kDivWindow] outcome and slot index of the round's divisions
+  DivCtl* dc;
+  cudaGraphConditionalHandle loop;
+};
+// Before the rounds: the named cells (tags) to slots in place, and the first
+// count empty cells and 2 count free vertices in increasing tag order into
+// cslots and vslots (dc->free_c, free_v: how many there are).  fc/sc/scp and
+// fv/sv/svp: scan scratch for n and V flags (bins and partials), left to be
+// cleared by the caller.
+void launch_avm_divide_slots(const DivArgs& d, const int* cslot, const int* vslot, int* fc, int* sc, int* scp,
+                             int* fv, int* sv, int* svp, cudaStream_t st);
+void launch_avm_divide_begin(const DivArgs& d, cudaStream_t st);
+void launch_avm_divide_round(const DivArgs& d, cudaStream_t st);
 void launch_avm_shadow(const AvmArgs& a, cudaStream_t st);
 // Storage order of the AVM (Hilbert re-sort of the vertex and cell slots).
 // Every slot carries a tag, its id in the network as built (and as the API
