@@ -869,7 +869,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tflops / FP64_PEAK_TFLOPS,
                 "traffic": GEOM_DRAM_BYTES_PER_LAUNCH if dominant == "geometry" else None,
-                "kernel": {"geometry": "k_geom", "force_move": "k_force"}[dominant],
+                "kernel": {"geometry": "k_geom", "force_move": "k_force"}[dominant], "duration_ms": dom_ms,
                 "peak_source": "FP64 nominal from unit counts x 2.07 GHz (FP64 units, not tensor)"}
     hbm_gbs, hbm_src = hbm_peak()
     step_s = ms * 1e-3 / args.steps

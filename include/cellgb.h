@@ -168,9 +168,11 @@ int cg_run_io(cg_ctx* ctx, int64_t nsteps, const double* v0, int64_t v0_stride, 
  *   0 geometry + force sets, 1 net force + move, 2 circumcircle test,
  *   3 cell-list build, 4 repair rounds (repair + consistency check),
  *   5 director terms of the next step (n(theta) and the noise; in the step
- *     graph this runs beside phases 2-4).
+ *     graph this runs beside phases 2-4),
+ *   6 ring-size grouping of the cells for the geometry pass (in the step
+ *     graph this runs at the end of the previous step, beside the forces).
  * The steps advance the state exactly like cg_step(). */
-#define CG_NUM_PHASES 6
+#define CG_NUM_PHASES 7
 int cg_profile_step(cg_ctx* ctx, int64_t nsteps, double* ms_out, int32_t n_out);
 
 /* Waits for the stream and returns the device status word. */

@@ -202,7 +202,7 @@ def cg_step(ctx, nsteps):
     _check(lib().cg_step(ctx, int(nsteps)), ctx)
 
 
-PHASES = ("geometry", "force_move", "test", "cell_list", "repair", "directors")
+PHASES = ("geometry", "force_move", "test", "cell_list", "repair", "directors", "ring_order")
 
 
 def cg_profile_step(ctx, nsteps):

@@ -920,7 +920,7 @@ int cg_profile_step(cg_ctx* c, int64_t nsteps, double* ms_out, int32_t n_out) {
   int rc = CG_OK;
   // the order of the graph step: the pending move becomes current, then the
   // test, cell list, rounds, director terms, geometry, and the next move
-  static const int kPhaseOfInterval[CG_NUM_PHASES] = {2, 3, 4, 5, 0, 1};
+  static const int kPhaseOfInterval[CG_NUM_PHASES] = {2, 3, 4, 5, 6, 0, 1};
   for (int64_t s = 0; s < nsteps && !rc; ++s) {
     cudaEventRecord(ev[0], st);
     launch_begin_topology(c->ctl(), 1, st);
@@ -936,11 +936,12 @@ int cg_profile_step(cg_ctx* c, int64_t nsteps, double* ms_out, int32_t n_out) {
     run_dir(c, dir_args_step(c), st, dir_grid(c));
     cudaEventRecord(ev[4], st);
     if (c->launch.ring_order) run_order(c, st);
-    run_geom(c, geom_args(c), st);
     cudaEventRecord(ev[5], st);
-    run_force(c, force_args(c, 1), st);
+    run_geom(c, geom_args(c), st);
     cudaEventRecord(ev[6], st);
-    if (cudaEventSynchronize(ev[6]) != cudaSuccess) { rc = fail(c, CG_ECUDA, "profile sync"); break; }
+    run_force(c, force_args(c, 1), st);
+    cudaEventRecord(ev[7], st);
+    if (cudaEventSynchronize(ev[7]) != cudaSuccess) { rc = fail(c, CG_ECUDA, "profile sync"); break; }
     for (int k = 0; k < CG_NUM_PHASES; ++k) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);

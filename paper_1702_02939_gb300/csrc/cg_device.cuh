@@ -203,8 +203,8 @@ __device__ __forceinline__ double fast_rsqrt(double x) {
 // A 128-bit integer rounded to the nearest double (ties to even), on the
 // integer pipes: the magnitude shifted so that its leading one is bit 127,
 // its top 64 bits rounded to 53 with a sticky bit for the rest (a carry out
-// of the mantissa lands in the exponent field).
-__device__ __forceinline__ double i128_to_double(__int128 v) {
+// of the mantissa lands in the exponent field); times 2^e2 (exact).
+__device__ __forceinline__ double i128_to_double(__int128 v, int e2 = 0) {
   const bool neg = v < 0;
   const unsigned __int128 a = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
   const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
@@ -228,8 +228,14 @@ __device__ __forceinline__ double i128_to_double(__int128 v) {
   unsigned long long m = top >> 11;
   const unsigned long long rem = top & 0x7ff;
   if (rem > 0x400 || (rem == 0x400 && (sticky || (m & 1)))) m += 1;
-  const unsigned long long bits = ((unsigned long long)(nb + 1021) << 52) + m;
+  const unsigned long long bits = ((unsigned long long)(nb + 1021 + e2) << 52) + m;
   return __longlong_as_double((long long)(bits | (neg ? 0x8000000000000000ull : 0ull)));
+}
+
+// Significant bits of a 128-bit magnitude (0 for 0).
+__device__ __forceinline__ int u128_bits(unsigned __int128 v) {
+  const unsigned long long hi = (unsigned long long)(v >> 64), lo = (unsigned long long)v;
+  return hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
 }
 
 // 1/d and 1/sqrt(x) with the refinement on the integer pipes: the mantissa

@@ -76,35 +76,37 @@ __global__ void __launch_bounds__(kGeomThreads, kGeomMinBlocks) k_geom(GeomArgs 
     };
 
     // squared lengths and the triangle determinants exactly in 128-bit
-    // integers from the grid offsets, each rounded to double once
+    // integers from the grid offsets; the doubled circumcentre g = num / det
+    // with num = (b_y |a|^2 - a_y |b|^2, a_x |b|^2 - b_x |a|^2) in 128-bit
+    // integers too, from |a|^2 and |b|^2 cut to 62 significant bits by a
+    // shift common to the triangle (at least as accurate as FP64 products
+    // of the rounded squares), each rounded to double once
     const int j0 = nb(0);
     const long long D0X = min_image_i(X[j0] - Xi, R.LX), D0Y = min_image_i(Y[j0] - Yi, R.LY);
-    const double d0x = i2d_int(D0X), d0y = i2d_int(D0Y);
-    const double l0 = i128_to_double((__int128)D0X * D0X + (__int128)D0Y * D0Y);
-    double ax = d0x, ay = d0y, la = l0;
+    const unsigned __int128 L0 = (unsigned __int128)((__int128)D0X * D0X + (__int128)D0Y * D0Y);
+    unsigned __int128 LA = L0;
     long long AX = D0X, AY = D0Y;
     double hpx = 0.0, hpy = 0.0, h0x = 0.0, h0y = 0.0;
     double area = 0.0, per = 0.0;
     for (int a = 0; a < m; ++a) {
-      double bx, by, lb;
       long long BX, BY;
+      unsigned __int128 LB;
       if (a + 1 < m) {
         const int j = nb(a + 1);
         BX = min_image_i(X[j] - Xi, R.LX);
         BY = min_image_i(Y[j] - Yi, R.LY);
-        bx = i2d_int(BX);
-        by = i2d_int(BY);
-        lb = i128_to_double((__int128)BX * BX + (__int128)BY * BY);
+        LB = (unsigned __int128)((__int128)BX * BX + (__int128)BY * BY);
       } else {
-        BX = D0X; BY = D0Y;
-        bx = d0x; by = d0y; lb = l0;
+        BX = D0X; BY = D0Y; LB = L0;
       }
       // (r_j - r_i) x (r_k - r_i)
       const double det = i128_to_double((__int128)AX * BY - (__int128)AY * BX);
       const double r = fx_rcp(det);
-      // doubled circumcentre relative to r_i
-      const double hx = (by * la - ay * lb) * r;
-      const double hy = (ax * lb - bx * la) * r;
+      // |offsets| < 2^49 and the cut squares < 2^62: the numerators fit in 113 bits
+      const int S = max(u128_bits(LA > LB ? LA : LB) - 62, 0);
+      const long long la = (long long)(LA >> S), lb = (long long)(LB >> S);
+      const double hx = i128_to_double((__int128)BY * la - (__int128)AY * lb, S) * r;
+      const double hy = i128_to_double((__int128)AX * lb - (__int128)BX * la, S) * r;
       g.s[a * N + i] = make_double2(hx * r, hy * r);
       put(sh_hx, lo_hx, a, hx);
       put(sh_hy, lo_hy, a, hy);
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(kGeomThreads, kGeomMinBlocks) k_geom(GeomArgs 
         put(sh_ey, lo_ey, a, ey * il);
       }
       hpx = hx; hpy = hy;
-      ax = bx; ay = by; la = lb;
+      LA = LB;
       AX = BX; AY = BY;
     }
     {  // closing edge h_{m-1} -> h_0 is the incoming edge of vertex 0
