@@ -67,7 +67,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # Dominant-kernel DRAM traffic per launch (dram__bytes_read.sum +
 # dram__bytes_write.sum) from one ncu capture of the current k_geom at
 # N = 262144; None whenever the kernel has changed since the capture.
-GEOM_DRAM_BYTES_PER_LAUNCH = None
+GEOM_DRAM_BYTES_PER_LAUNCH = 43.99e6
 
 
 def parse():
