@@ -52,11 +52,10 @@ EQUIL_STEPS = 100
 # the three times the kernel evaluates it.
 FLOPS_PER_CELL = {"geometry": 277.0, "force_move": 93.0}
 # AVM: per cell of k_avm_cells (12 per polygon vertex x 6: offsets, shoelace
-# term, edge, sqrt, sum; 12 for A, P and the coefficients; 11 for the
-# director terms with sincos, log, sqrt, cos counted as 1 each) and per vertex
-# of k_avm_force_move (3 edges x (offset, length, rsqrt, unit vector) + 3 force
+# term, edge, sqrt, sum; 12 for A, P and the coefficients) and per vertex of
+# k_avm_force_move (3 edges x (offset, length, rsqrt, unit vector) + 3 force
 # terms x 8 + activity and move).
-AVM_FLOPS = {"cells_per_cell": 95.0, "vertices_per_vertex": 62.0}
+AVM_FLOPS = {"cells_per_cell": 84.0, "vertices_per_vertex": 62.0}
 # AVM storage order: Hilbert re-sort of the vertex and cell slots at creation
 # and every this many steps (Sec. 2.B; results are the same either way).
 AVM_SORT_EVERY = 100
@@ -423,9 +422,9 @@ def avm_roofline(n, ph, prof_steps):
     achieved = flops / (ms * 1e-3) / 1e12
     return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "note": "the per-cell phase is the polygon geometry plus the next step's director terms "
-                    "(beside the T1 passes in the step graph); sqrt, sincos, log, cos count one flop "
-                    "each but take many FP64 instructions; at N = 65536 the passes are latency bound"}
+            "duration_ms": ms,
+            "note": "the kernel's own event-timed duration (eager launches); sqrt counts one flop but takes "
+                    "an integer-pipe refinement; at N = 65536 the passes are latency bound"}
 
 
 def decomposed_throughput(args, device):
@@ -533,6 +532,7 @@ def avm_throughput(args, device):
             "t1_passes_per_step": (c1["t1_passes"] - c0["t1_passes"]) / Kd,
             "roofline": avm_roofline(n, ph, prof_steps),
             "phase_ms_per_step": {"cells": ph["cells_ms"] / prof_steps, "vertices": ph["vertices_ms"] / prof_steps,
+                                  "directors": ph["dir_ms"] / prof_steps,
                                   "t1_passes": ph["t1_ms"] / prof_steps,
                                   "t1_passes_count": ph["t1_passes"] / prof_steps},
             "cpu_oracle": {"value": V * steps / el, "unit": "vertex-steps/s", "cores": 1, "kind": "oracle",

@@ -420,11 +420,12 @@ int cg_avm_step(cg_avm_ctx* ctx, int64_t nsteps);
 /* Device time of nsteps ordinary steps run eagerly (not as a graph), timed
  * with CUDA events on the context's stream; the T1 pass control is read back
  * by the host after each pass.  ms_out (n_out >= CG_AVM_NUM_PHASES) receives:
- *   [0] summed ms of the per-cell kernel (geometry, activity, directors),
+ *   [0] summed ms of the per-cell kernel (geometry, force coefficients),
  *   [1] of the per-vertex kernel (forces, move), [2] of the T1 passes,
- *   [3] the number of T1 passes run.
+ *   [3] the number of T1 passes run, [4] ms of the next step's director
+ *   terms (activity and rotation; beside the T1 passes in the step graph).
  * The steps advance the state exactly like cg_avm_step(). */
-#define CG_AVM_NUM_PHASES 4
+#define CG_AVM_NUM_PHASES 5
 int cg_avm_profile_step(cg_avm_ctx* ctx, int64_t nsteps, double* ms_out, int32_t n_out);
 /* Waits for the stream and returns the device status. */
 int cg_avm_sync(cg_avm_ctx* ctx);

@@ -666,9 +666,9 @@ def cg_avm_step(ctx, nsteps):
 
 
 def cg_avm_profile_step(ctx, nsteps):
-    out = (C.c_double * 4)()
-    _check_avm(lib().cg_avm_profile_step(ctx, int(nsteps), out, 4), ctx)
-    return {"cells_ms": out[0], "vertices_ms": out[1], "t1_ms": out[2], "t1_passes": out[3]}
+    out = (C.c_double * 5)()
+    _check_avm(lib().cg_avm_profile_step(ctx, int(nsteps), out, 5), ctx)
+    return {"cells_ms": out[0], "vertices_ms": out[1], "t1_ms": out[2], "t1_passes": out[3], "dir_ms": out[4]}
 
 
 def cg_avm_sync(ctx):

@@ -624,14 +624,13 @@ int cg_avm_profile_step(cg_avm_ctx* c, int64_t nsteps, double* ms_out, int32_t n
     ms_out[0] += ms;
     cudaEventElapsedTime(&ms, ev[1], ev[2]);
     ms_out[1] += ms;
-    // the director terms of the next step (beside the T1 passes in the
-    // graph), counted with the per-cell phase
+    // the director terms of the next step (beside the T1 passes in the graph)
     cudaEventRecord(ev[0], st);
     launch_avm_dir(a, st);
     cudaEventRecord(ev[1], st);
     if (cudaEventSynchronize(ev[1]) != cudaSuccess) { rc = afail(c, CG_ECUDA, "profile sync"); break; }
     cudaEventElapsedTime(&ms, ev[0], ev[1]);
-    ms_out[0] += ms;
+    ms_out[4] += ms;
     for (int pass = 0; pass <= cap_of(c) + 1; ++pass) {
       cudaEventRecord(ev[0], st);
       launch_avm_t1_pass(a, st);

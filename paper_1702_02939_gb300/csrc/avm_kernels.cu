@@ -261,32 +261,34 @@ __global__ void k_avm_force_move(AvmArgs g) {
     const double* hx = g.hx + cur * V;
     const double* hy = g.hy + cur * V;
     const double xv = hx[v], yv = hy[v];
-    double ux[3], uy[3], nx[3], ny[3];
+    double ux[3], uy[3], il[3], kh[3], kp[3];
+    double ax = 0.0, ay = 0.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const int w = g.vn[3 * v + k];
       ux[k] = mimg_a(hx[w] - xv, g.ax);
       uy[k] = mimg_a(hy[w] - yv, g.ay);
-      const double il = fx_rsqrt(ux[k] * ux[k] + uy[k] * uy[k]);
-      nx[k] = ux[k] * il;
-      ny[k] = uy[k] * il;
-    }
-    double fx = 0.0, fy = 0.0, ax = 0.0, ay = 0.0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int km = (k + 2) % 3;
+      il[k] = fx_rsqrt(ux[k] * ux[k] + uy[k] * uy[k]);
       const int c = g.vc[3 * v + k];
-      const double kh = g.ka[c], kp = g.kp[c];
-      const double dx = ux[km] - ux[k], dy = uy[km] - uy[k];
-      // dE_c/dh = kh perp(h_next - h_prev) + kp (t^_in - t^_out), perp(d) = (d_y, -d_x),
-      // kh = K_A (A_c - A0_c); F = -dE/dh accumulated in two FMAs per component
-      fx = fma(-kh, dy, fma(kp, nx[k] + nx[km], fx));
-      fy = fma(kh, dx, fma(kp, ny[k] + ny[km], fy));
+      kh[k] = g.ka[c];
+      kp[k] = g.kp[c];
       if (g.move) {
         const double2 a = g.act[c];
         ax += a.x;
         ay += a.y;
       }
+    }
+    // dE_c/dh = kh perp(h_next - h_prev) + kp (t^_in - t^_out) summed over the
+    // three cells and regrouped by edge: edge k (to vn[k], between cells k and
+    // k+1) carries u_k (kh_k - kh_{k+1}) rotated and u^_k (kp_k + kp_{k+1});
+    // F = -dE/dh, kh = K_A (A - A0) stored halved
+    double fx = 0.0, fy = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int kn = (k + 1) % 3;
+      const double dkh = kh[k] - kh[kn], skp = (kp[k] + kp[kn]) * il[k];
+      fx = fma(uy[k], dkh, fma(ux[k], skp, fx));
+      fy = fma(-ux[k], dkh, fma(uy[k], skp, fy));
     }
     g.Fx[v] = fx;
     g.Fy[v] = fy;
