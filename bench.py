@@ -90,7 +90,8 @@ def parse():
     ap.add_argument("--domain-steps", type=int, default=200)
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--fp32-steps", type=int, default=500)
-    ap.add_argument("--avm-steps", type=int, default=500)
+    ap.add_argument("--avm-steps", type=int, default=4900,
+                    help="timed AVM steps after --avm-warmup (default: a 5000-step run)")
     ap.add_argument("--avm-warmup", type=int, default=100)
     ap.add_argument("--avm-profile-steps", type=int, default=20)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
