@@ -206,12 +206,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def kernels_launched(steps, loop_iterations, eager=False, ring_order=1):
+def kernels_launched(steps, loop_iterations, eager=False, ring_order=1, force_beside=0):
     # per step: begin-topology, test, 4 cell-list kernels, directors, the
     # ring-size grouping (if on), geometry of the new state, force + move;
-    # graph only: the geometry fix-up of rewritten rings; per repair round:
-    # repair + check
-    return (9 + (1 if ring_order else 0) + (0 if eager else 1)) * steps + 2 * loop_iterations
+    # graph only: the geometry fix-up of rewritten rings and, with the force
+    # pass beside the rounds, the fix-up list and the force fix-up; per
+    # repair round: repair + check
+    graph_extra = 0 if eager else 1 + (2 if force_beside else 0)
+    return (9 + (1 if ring_order else 0) + graph_extra) * steps + 2 * loop_iterations
 
 
 def host_cpu():
@@ -954,7 +956,7 @@ def run_ours(args):
                 "gpu_launches": (kernels_launched(args.steps, args.steps * repair_cap, True, launch["ring_order"])
                                  if args.eager else
                                  kernels_launched(args.steps, counters["loop_total"] - c_start["loop_total"], False,
-                                                  launch["ring_order"])),
+                                                  launch["ring_order"], launch.get("force_beside", 0))),
                 "timed_state": timed_state,
                 "roofline": roofline, "hbm_roofline": hbm, "cpu_baseline": cpu,
                 "phase_ms_per_step": {k: v / prof_steps for k, v in ph.items()},

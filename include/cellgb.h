@@ -124,6 +124,11 @@ typedef struct cg_launch {
                                     circumcircle test takes the cells regrouped by ring size within
                                     chunks of 1024 cells, so that the lanes of a warp run the same
                                     number of ring slots (0..7; default 5 in FP64, 0 in FP32) */
+  int32_t force_beside;          /* 1: the force pass and the pending move run on the geometry
+                                    branch beside the repair rounds, and after the rounds only the
+                                    cells around rewritten rings are done again (FP64 only;
+                                    results unchanged); 0: after the rounds, all cells (default:
+                                    the geometry branch is already as long as the rounds) */
 } cg_launch;
 
 /* Workspace size for R replicas. */

@@ -48,7 +48,7 @@ class cg_launch(C.Structure):
     _fields_ = [("repair_blocks_per_sm", C.c_int32), ("check_blocks_per_sm", C.c_int32),
                 ("dir_blocks_per_sm", C.c_int32), ("dir_low_priority", C.c_int32),
                 ("geom_blocks_per_sm", C.c_int32), ("test_blocks_per_sm", C.c_int32),
-                ("dir_beside_geom", C.c_int32), ("ring_order", C.c_int32)]
+                ("dir_beside_geom", C.c_int32), ("ring_order", C.c_int32), ("force_beside", C.c_int32)]
 
 
 class cg_avm_params(C.Structure):

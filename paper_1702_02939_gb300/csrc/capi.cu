@@ -31,7 +31,7 @@ struct Offsets {
   size_t x, y, X, Y, theta, p0, v0, A, P, Fx, Fy, ecell, tmp, tmp2, scalar, nrm, xi;
   size_t tag, nid, nid_alt, rep, cnt, nbr, old_cnt, old_nbr;
   size_t fs, s, w, order;
-  size_t flags, list0, list1, dirty_list, dirty_bits;
+  size_t flags, list0, list1, dirty_list, dirty_bits, fix_list, fix_bits;
   size_t bin_count, bin_start, partials, cell_bin, cell_rank, ids;
   size_t reps, ctl, dir_tab;
   size_t io_v0, io_xy;  // staging of cg_run_io: [2][n] v0, [2][2][n] positions
@@ -91,6 +91,8 @@ Offsets layout(int64_t N, int64_t NB, int64_t NK, int R) {
   o.list1 = L.take(N * i4);
   o.dirty_list = L.take(N * i4);
   o.dirty_bits = L.take(((N + 31) / 32) * 4);
+  o.fix_list = L.take(N * i4);
+  o.fix_bits = L.take(((N + 31) / 32) * 4);
   o.bin_count = L.take(NB * i4);
   o.bin_start = L.take((NB + 1) * i4);
   o.partials = L.take(((NB + 1 + kScanChunkHost - 1) / kScanChunkHost + 1) * i4);
@@ -190,7 +192,7 @@ struct cg_ctx {
   // cg_run_io: copy streams and the events that order the double-buffered staging
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t in_ready[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_free[2] = {};
-  cg_launch launch{4, 4, 4, 1, 0, 8, 1, 5};    // launch shapes of the step graph
+  cg_launch launch{4, 4, 4, 1, 0, 8, 1, 5, 0};    // launch shapes of the step graph
   std::vector<cg_replica> user_reps;           // as passed to cg_create
   cudaGraphExec_t step_exec = nullptr;
   int graph_steps = 0;
@@ -308,9 +310,9 @@ void run_geom(const cg_ctx* c, const GeomArgs& a, cudaStream_t st, int blocks = 
   if (fp32(c)) launch_geom_f32(a, st, blocks);
   else launch_geom(a, st, blocks);
 }
-void run_force(const cg_ctx* c, const ForceArgs& a, cudaStream_t st) {
+void run_force(const cg_ctx* c, const ForceArgs& a, cudaStream_t st, int blocks = 0) {
   if (fp32(c)) launch_force_f32(a, st);
-  else launch_force(a, st);
+  else launch_force(a, st, blocks);
 }
 void run_dir(const cg_ctx* c, const DirArgs& a, cudaStream_t st, int blocks = 0) {
   if (fp32(c)) launch_dir_f32(a, st, blocks);
@@ -485,6 +487,16 @@ void enqueue_step_prefix(cg_ctx* c, cudaStream_t st) {
   GeomArgs g = geom_args(c);
   g.tolerant = 1;
   run_geom(c, g, c->side[0], geom_grid(c));
+  if (c->launch.force_beside) {
+    // the forces and the pending move of every cell, beside the rounds; the
+    // cells around rings the rounds rewrite are done again afterwards
+    if (c->launch.dir_beside_geom) cudaStreamWaitEvent(c->side[0], c->join_terms, 0);
+    ForceArgs f = force_args(c, 1);
+    f.tolerant = 1;
+    f.fix_list = c->at<int>(c->off.fix_list);
+    f.fix_bits = c->at<unsigned>(c->off.fix_bits);
+    run_force(c, f, c->side[0]);
+  }
   cudaEventRecord(c->join_dir, c->side[0]);
   launch_cell_list(cell_list_args(c, 0), c->side[1]);
   cudaEventRecord(c->join_list, c->side[1]);
@@ -493,9 +505,23 @@ void enqueue_step_prefix(cg_ctx* c, cudaStream_t st) {
 }
 
 // After the repair rounds and the concurrent geometry: the geometry of every
-// cell whose ring a round rewrote, then the forces and the next pending move.
+// cell whose ring a round rewrote, then the forces and the next pending move
+// (with force_beside only of the cells around those rings and of the cells
+// the pass beside the rounds could not decide).
 void enqueue_step_suffix(cg_ctx* c, cudaStream_t st) {
   cudaStreamWaitEvent(st, c->join_dir, 0);
+  if (c->launch.force_beside) {
+    ForceFixArgs x{};
+    x.n = (int)c->N;
+    x.cnt = c->at<int>(c->off.cnt);
+    x.nbr = c->at<int>(c->off.nbr);
+    x.dirty_list = c->at<int>(c->off.dirty_list);
+    x.dirty_count = &c->ctl()->dirty_count;
+    x.fix_list = c->at<int>(c->off.fix_list);
+    x.fix_bits = c->at<unsigned>(c->off.fix_bits);
+    x.ctl = c->ctl();
+    launch_force_fix_list(x, sm_count() * 4, st);
+  }
   GeomArgs g = geom_args(c);
   g.list = c->at<int>(c->off.dirty_list);
   g.list_count = &c->ctl()->dirty_count;
@@ -512,7 +538,15 @@ void enqueue_step_suffix(cg_ctx* c, cudaStream_t st) {
     run_order(c, c->side[0]);
     cudaEventRecord(c->join_dir, c->side[0]);
   }
-  run_force(c, force_args(c, 1), st);
+  if (c->launch.force_beside) {
+    ForceArgs f = force_args(c, 1);
+    f.list = c->at<int>(c->off.fix_list);
+    f.list_count = &c->ctl()->force_count;
+    f.list_bits = c->at<unsigned>(c->off.fix_bits);
+    run_force(c, f, st, sm_count() * 8);
+  } else {
+    run_force(c, force_args(c, 1), st);
+  }
   if (c->launch.ring_order) cudaStreamWaitEvent(st, c->join_dir, 0);
 }
 
@@ -766,6 +800,7 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
     c->launch.ring_order = 0;
     c->launch.dir_beside_geom = 0;
     c->launch.dir_blocks_per_sm = 2;
+    c->launch.force_beside = 0;  // the FP32 kernels have no tolerant force pass
   }
   c->off = layout(c->N, c->NB, c->NK, R);
   if (ws_bytes < c->off.total) {
@@ -829,7 +864,8 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
     rc = load_positions(c, x, y);
     if (rc) break;
     launch_sort(sort_args(c), st);  // spatial order before the first triangulation
-    if (cudaMemsetAsync(c->at<unsigned>(c->off.dirty_bits), 0, ((c->N + 31) / 32) * 4, st) != cudaSuccess) {
+    if (cudaMemsetAsync(c->at<unsigned>(c->off.dirty_bits), 0, ((c->N + 31) / 32) * 4, st) != cudaSuccess ||
+        cudaMemsetAsync(c->at<unsigned>(c->off.fix_bits), 0, ((c->N + 31) / 32) * 4, st) != cudaSuccess) {
       rc = fail(c, CG_ECUDA, "clearing the dirty bitmap");
       break;
     }
@@ -1143,7 +1179,8 @@ int cg_set_launch(cg_ctx* c, const cg_launch* l) {
       l->check_blocks_per_sm > 64 || l->dir_blocks_per_sm < 0 || l->dir_blocks_per_sm > 64 ||
       (l->dir_low_priority != 0 && l->dir_low_priority != 1) || l->geom_blocks_per_sm < 0 ||
       l->geom_blocks_per_sm > 64 || l->test_blocks_per_sm < 0 || l->test_blocks_per_sm > 64 ||
-      (l->dir_beside_geom != 0 && l->dir_beside_geom != 1) || l->ring_order < 0 || l->ring_order > 7)
+      (l->dir_beside_geom != 0 && l->dir_beside_geom != 1) || l->ring_order < 0 || l->ring_order > 7 ||
+      (l->force_beside != 0 && l->force_beside != 1) || (l->force_beside && fp32(c)))
     return CG_EINVAL;
   int rc = read_status(c);
   if (rc) return rc;
@@ -1229,6 +1266,8 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
   static const int test_opts[] = {0, 2, 4, 8};
   static const int beside_opts[] = {0, 1};
   static const int order_opts[] = {0, 1, 4, 5};
+  static const int fb_opts[] = {0, 1};
+  const int n_fb = fp32(c) ? 1 : 2;  // FP32: force_beside stays 0
   const cg_launch start = c->launch;
   cg_launch cur = start;
   double cur_ms = 0.0;
@@ -1238,11 +1277,12 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
     const int* opts;
     int nopt;
   };
-  static const Field fields[] = {
+  const Field fields[] = {
       {&cg_launch::repair_blocks_per_sm, repair_opts, 4}, {&cg_launch::check_blocks_per_sm, check_opts, 4},
       {&cg_launch::dir_blocks_per_sm, dir_opts, 5},       {&cg_launch::dir_low_priority, prio_opts, 2},
       {&cg_launch::geom_blocks_per_sm, geom_opts, 4},     {&cg_launch::test_blocks_per_sm, test_opts, 4},
-      {&cg_launch::dir_beside_geom, beside_opts, 2},      {&cg_launch::ring_order, order_opts, 4}};
+      {&cg_launch::dir_beside_geom, beside_opts, 2},      {&cg_launch::ring_order, order_opts, 4},
+      {&cg_launch::force_beside, fb_opts, n_fb}};
   for (int sweep = 0; sweep < 2 && !rc; ++sweep) {
     for (const Field& f : fields) {
       for (int k = 0; k < f.nopt && !rc; ++k) {

@@ -87,6 +87,7 @@ struct Ctl {
   int dirty_count;    // cells whose ring a repair round rewrote in this step
   long long loop_total;  // iterations of the repair-round (or T1-pass) loop node
   int t1_more;        // the current T1 pass may leave work for another (AVM)
+  int force_count;    // cells whose force the step recomputes after the repair rounds
 };
 
 // True in exactly one block of the grid: the last one to get here.  Every

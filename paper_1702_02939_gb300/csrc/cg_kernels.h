@@ -63,7 +63,30 @@ struct ForceArgs {
   const double2* nrm;  // (cos, sin) of each cell's director, from k_dir
   const double* xi;    // the step's director noise, from k_dir
   const int* order;    // processing order of the cells (as GeomArgs), or null
+  // Beside the repair rounds (tolerant): rings may be rewritten meanwhile; a
+  // cell whose ring, neighbours or move look wrong raises nothing and is
+  // put on the fix-up list (fix_list, fix_bits, ctl->force_count) instead.
+  int tolerant;
+  int* fix_list;
+  unsigned* fix_bits;
+  // Fix-up: only the cells of list[0 .. *list_count), clearing their bits
+  const int* list;
+  const int* list_count;
+  unsigned* list_bits;
 };
+// The cells whose force the step recomputes after the repair rounds: every
+// cell whose ring a round rewrote and every cell of its new ring, added once
+// each to the fix-up list (beside the cells the tolerant pass put there).
+struct ForceFixArgs {
+  int n;
+  const int *cnt, *nbr;
+  const int* dirty_list;
+  const int* dirty_count;
+  int* fix_list;
+  unsigned* fix_bits;
+  Ctl* ctl;
+};
+void launch_force_fix_list(const ForceFixArgs& a, int blocks, cudaStream_t st);
 
 // Cells of each chunk of kOrderChunk consecutive cells regrouped by ring size:
 // a warp of the geometry and force kernels then runs cells with (mostly) the
@@ -171,7 +194,8 @@ void launch_geom(const GeomArgs& a, cudaStream_t st, int blocks = 0);
 void launch_geom_f32(const GeomArgs& a, cudaStream_t st, int blocks = 0);
 void launch_force_f32(const ForceArgs& a, cudaStream_t st);
 void launch_dir_f32(const DirArgs& a, cudaStream_t st, int blocks = 0);
-void launch_force(const ForceArgs& a, cudaStream_t st);
+// blocks > 0: a grid-stride launch of that many blocks (list mode)
+void launch_force(const ForceArgs& a, cudaStream_t st, int blocks = 0);
 void launch_begin_topology(Ctl* ctl, int flip, cudaStream_t st);
 void launch_test(const TestArgs& a, cudaStream_t st, int blocks = 0);
 void launch_cell_list(const CellListArgs& a, cudaStream_t st);

@@ -164,7 +164,7 @@ __device__ __forceinline__ bool net_force(const ForceArgs& g, int i, double& fx_
   const size_t N = (size_t)g.n;
   const int m = g.cnt[i];
   if (m < 3 || m > CG_RING) {
-    raise_status(g.ctl, kETOPO);
+    if (!g.tolerant) raise_status(g.ctl, kETOPO);
     return false;
   }
   const int cur = g.ctl->cur;
@@ -173,18 +173,27 @@ __device__ __forceinline__ bool net_force(const ForceArgs& g, int i, double& fx_
   const Rep R = g.reps[g.rep[i]];
   const long long Xi = X[i], Yi = Y[i];
   const int* ring = g.nbr + (size_t)i * CG_RING;
-  int jfirst = ring[0];
+  bool bad = false;
+  // a ring being rewritten meanwhile (tolerant pass) may hold -1 entries:
+  // the cell itself is read there and the result marked bad
+  auto nb = [&](int a) {
+    const int j = ring[a];
+    const bool ok = (unsigned)j < (unsigned)g.n;
+    bad |= !ok;
+    return ok ? j : i;
+  };
+  int jfirst = nb(0);
   int pfirst = ring_pos(g.nbr, g.cnt, jfirst, i);
   int j = jfirst, pj = pfirst;
   const long long fX = min_image_i(X[jfirst] - Xi, R.LX), fY = min_image_i(Y[jfirst] - Yi, R.LY);
   long long aX = fX, aY = fY;
   double fx = 0.0, fy = 0.0;
-  bool bad = pfirst < 0;
+  bad |= pfirst < 0;
   for (int a = 0; a < m; ++a) {
     int k, pk;
     long long bX, bY;
     if (a + 1 < m) {
-      k = ring[a + 1];
+      k = nb(a + 1);
       pk = ring_pos(g.nbr, g.cnt, k, i);
       bad |= pk < 0;
       bX = min_image_i(X[k] - Xi, R.LX);
@@ -212,26 +221,35 @@ __device__ __forceinline__ bool net_force(const ForceArgs& g, int i, double& fx_
     aX = bX;
     aY = bY;
   }
-  if (bad) raise_status(g.ctl, kETOPO);
+  if (bad) {
+    if (g.tolerant) return false;
+    raise_status(g.ctl, kETOPO);
+  }
   fx_out = fx;
   fy_out = fy;
   return true;
 }
 
-// One thread per cell: the net force (integrate 0 or 1) and the update of
-// Eq. 3 (integrate 1), or the update alone from the stored forces of the
-// current positions (integrate 2: after a change of v0).
-__global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
-  const int item = blockIdx.x * kForceThreads + threadIdx.x;
-  if (item >= g.n) return;
-  const int i = g.order ? g.order[item] : item;
+// Puts cell i on the fix-up list of the step, once.
+__device__ __forceinline__ void claim_fix(unsigned* bits, int* list, int* count, int i) {
+  const unsigned bit = 1u << (i & 31);
+  if (!(atomicOr(&bits[i >> 5], bit) & bit)) list[atomicAdd(count, 1)] = i;
+}
+
+// Cell i's net force (integrate 0 or 1) and update of Eq. 3 (integrate 1),
+// or the update alone from the stored forces of the current positions
+// (integrate 2: after a change of v0).
+__device__ __forceinline__ void force_cell(const ForceArgs& g, int i) {
   const size_t N = (size_t)g.n;
   double fx, fy;
   if (g.integrate == 2) {
     fx = g.Fx[i];
     fy = g.Fy[i];
   } else {
-    if (!net_force(g, i, fx, fy)) return;
+    if (!net_force(g, i, fx, fy)) {
+      if (g.tolerant) claim_fix(g.fix_bits, g.fix_list, &g.ctl->force_count, i);
+      return;
+    }
     g.Fx[i] = fx;
     g.Fy[i] = fy;
     if (!g.integrate) return;
@@ -265,6 +283,10 @@ __global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
       Y = move_framed(yi, g.dt, vy, R.y0, R.Lyg, R.scale, R.Y0, R.LYg, R.LY);
     }
   } else {
+    if (g.tolerant) {  // decided again, strictly, after the repair rounds
+      claim_fix(g.fix_bits, g.fix_list, &g.ctl->force_count, i);
+      return;
+    }
     raise_status(g.ctl, kENONFINITE);
     X = (long long)rint(xi * R.scale);
     Y = (long long)rint(yi * R.scale);
@@ -274,6 +296,35 @@ __global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
   g.y[(size_t)nxt * N + i] = i2d_int(Y, -R.q);
   g.X[(size_t)nxt * N + i] = X;
   g.Y[(size_t)nxt * N + i] = Y;
+}
+
+// One thread per cell: the net force (integrate 0 or 1) and the update of
+// Eq. 3 (integrate 1), or the update alone from the stored forces of the
+// current positions (integrate 2: after a change of v0); with a list, the
+// cells of the list (grid-stride), their list bits cleared.
+__global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs g) {
+  const int total = g.list ? *g.list_count : g.n;
+  for (int item = blockIdx.x * kForceThreads + threadIdx.x; item < total; item += gridDim.x * kForceThreads) {
+    const int i = g.list ? g.list[item] : (g.order ? g.order[item] : item);
+    if (g.list_bits) atomicAnd(&g.list_bits[i >> 5], ~(1u << (i & 31)));
+    force_cell(g, i);
+  }
+}
+
+// The fix-up list of the force pass: each rewritten ring's cell and the
+// cells of its new ring (their force sets or ring positions changed).
+__global__ void k_force_fix_list(ForceFixArgs g) {
+  const int total = *g.dirty_count;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int d = g.dirty_list[t];
+    if ((unsigned)d >= (unsigned)g.n) continue;
+    claim_fix(g.fix_bits, g.fix_list, &g.ctl->force_count, d);
+    const int m = min(g.cnt[d], CG_RING);
+    for (int a = 0; a < m; ++a) {
+      const int j = g.nbr[(size_t)d * CG_RING + a];
+      if ((unsigned)j < (unsigned)g.n) claim_fix(g.fix_bits, g.fix_list, &g.ctl->force_count, j);
+    }
+  }
 }
 
 // Director terms of a step: with `advance`, first the rotation of the
@@ -350,6 +401,7 @@ __global__ void k_begin_topology(Ctl* ctl, int flip) {
   ctl->count[1] = 0;
   ctl->round_count = 0;
   ctl->dirty_count = 0;
+  ctl->force_count = 0;
 }
 
 __device__ __forceinline__ void flag_cell(unsigned* flags, int* list, int* count, int c) {
@@ -482,9 +534,13 @@ void launch_geom(const GeomArgs& a, cudaStream_t st, int blocks) {
   const int full = (a.n + kGeomThreads - 1) / kGeomThreads;
   k_geom<<<(blocks > 0 && blocks < full) ? blocks : full, kGeomThreads, 0, st>>>(a);
 }
-void launch_force(const ForceArgs& a, cudaStream_t st) {
+void launch_force(const ForceArgs& a, cudaStream_t st, int blocks) {
   if (a.n <= 0) return;
-  k_force<<<(a.n + kForceThreads - 1) / kForceThreads, kForceThreads, 0, st>>>(a);
+  const int full = (a.n + kForceThreads - 1) / kForceThreads;
+  k_force<<<(blocks > 0 && blocks < full) ? blocks : full, kForceThreads, 0, st>>>(a);
+}
+void launch_force_fix_list(const ForceFixArgs& a, int blocks, cudaStream_t st) {
+  if (a.n > 0) k_force_fix_list<<<blocks, 128, 0, st>>>(a);
 }
 void launch_begin_topology(Ctl* ctl, int flip, cudaStream_t st) { k_begin_topology<<<1, 1, 0, st>>>(ctl, flip); }
 void launch_test(const TestArgs& a, cudaStream_t st, int blocks) {

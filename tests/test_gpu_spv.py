@@ -346,16 +346,16 @@ def test_launch_shapes_do_not_change_results():
     only: 20 steps agree bit for bit."""
     n = 4096
     a, *_ = make(n, 33, p0=3.85, v0=0.1, seed=3)
-    assert a.launch["ring_order"] == 5
+    assert a.launch["ring_order"] == 5 and a.launch["force_beside"] == 0
     b, *_ = make(n, 33, p0=3.85, v0=0.1, seed=3)
     b.set_launch(repair_blocks_per_sm=8, check_blocks_per_sm=4, dir_blocks_per_sm=1, dir_low_priority=1,
-                 geom_blocks_per_sm=2, test_blocks_per_sm=2, ring_order=0, dir_beside_geom=0)
+                 geom_blocks_per_sm=2, test_blocks_per_sm=2, ring_order=0, dir_beside_geom=0, force_beside=0)
     assert b.launch["dir_blocks_per_sm"] == 1
     c, *_ = make(n, 33, p0=3.85, v0=0.1, seed=3)
     c.set_launch(dir_beside_geom=1, dir_low_priority=0, dir_blocks_per_sm=0, ring_order=3)
     assert c.launch["dir_beside_geom"] == 1
     d, *_ = make(n, 33, p0=3.85, v0=0.1, seed=3)
-    d.set_launch(ring_order=6)
+    d.set_launch(ring_order=6, force_beside=1)
     a.step(20)
     b.step(20)
     c.step(20)
@@ -367,8 +367,30 @@ def test_launch_shapes_do_not_change_results():
         c.set_launch(dir_beside_geom=2)
     with pytest.raises(RuntimeError):
         c.set_launch(ring_order=8)
+    with pytest.raises(RuntimeError):
+        c.set_launch(force_beside=2)
     for s in (a, b, c, d):
         s.close()
+
+
+def test_force_pass_beside_the_rounds_keeps_results():
+    """The force pass run beside the repair rounds, with the cells around
+    rewritten rings (and any it could not decide) done again afterwards,
+    gives bit for bit the state of the force pass after the rounds, in a
+    regime that rewrites many rings every step (and in a batch of replicas)."""
+    n = 16384
+    a, *_ = make(n, 35, p0=3.95, v0=0.5, seed=5)
+    b, *_ = make(n, 35, p0=3.95, v0=0.5, seed=5)
+    a.set_launch(force_beside=1)
+    assert b.launch["force_beside"] == 0
+    a.step(60)
+    b.step(60)
+    ca, cb = a.counters(), b.counters()
+    assert ca["repaired_total"] > 60 * 20 and ca == cb
+    for ta, tb in zip(a.state() + a.neighbors() + a.forces()[:2], b.state() + b.neighbors() + b.forces()[:2]):
+        assert torch.equal(ta, tb)
+    a.close()
+    b.close()
 
 
 def test_autotune_takes_no_step_and_keeps_results():
@@ -383,7 +405,7 @@ def test_autotune_takes_no_step_and_keeps_results():
     best, ms = a.autotune(3)
     assert ms > 0 and set(best) == {"repair_blocks_per_sm", "check_blocks_per_sm", "dir_blocks_per_sm",
                                     "dir_low_priority", "geom_blocks_per_sm", "test_blocks_per_sm",
-                                    "dir_beside_geom", "ring_order"}
+                                    "dir_beside_geom", "ring_order", "force_beside"}
     assert a.launch == best
     for t0, t1 in zip(before, a.state()):
         assert torch.equal(t0, t1)
@@ -485,6 +507,10 @@ def test_fp32_mode_refuses_the_backward_pass():
     with pytest.raises(cg.CellgbError) as e:
         sim.hvp(np.zeros(400), np.zeros(400))
     assert e.value.code == -1
+    # nor does it take the force pass beside the repair rounds
+    assert sim.launch["force_beside"] == 0
+    with pytest.raises(RuntimeError):
+        sim.set_launch(force_beside=1)
     sim.close()
 
 
