@@ -196,6 +196,7 @@ struct cg_ctx {
   std::vector<cg_replica> user_reps;           // as passed to cg_create
   cudaGraphExec_t step_exec = nullptr;
   int graph_steps = 0;
+  int seen_status = 0;  // a device status read back earlier (the context then stays refused)
   std::string last_error;
 
   template <class T>
@@ -599,9 +600,13 @@ int triangulate_all(cg_ctx* c) {
 
 int read_status(cg_ctx* c) {
   Ctl h;
+  // the control word read on the context's stream (ordered after its work)
+  CG_CUDA(c, cudaMemcpyAsync(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
   CG_CUDA(c, cudaStreamSynchronize(c->stream));
-  CG_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
-  if (h.status != 0) return fail(c, h.status, std::string("device status: ") + cg_status_string(h.status));
+  if (h.status != 0) {
+    c->seen_status = h.status;
+    return fail(c, h.status, std::string("device status: ") + cg_status_string(h.status));
+  }
   return CG_OK;
 }
 
@@ -900,8 +905,11 @@ int cg_step(cg_ctx* c, int64_t nsteps) {
 int cg_run_io(cg_ctx* c, int64_t nsteps, const double* v0, int64_t v0_stride, double* x, double* y,
               int64_t out_stride) {
   if (!c || nsteps < 0 || v0_stride < 0 || out_stride < 0) return CG_EINVAL;
-  int rc = read_status(c);
-  if (rc) return rc;
+  // no synchronisation on entry: a status raised by earlier work is returned
+  // at the end (the status word keeps the first one); one already read back
+  // refuses the call
+  if (c->seen_status)
+    return fail(c, c->seen_status, std::string("device status: ") + cg_status_string(c->seen_status));
   const size_t N = (size_t)c->N;
   const int n = (int)c->N;
   cudaStream_t st = c->stream;
