@@ -442,9 +442,12 @@ __device__ __forceinline__ int incircle_sign(long long px, long long py, long lo
 // det3(q, r, s) = -det3(0 - s, q - s, r - s).  The filter bound is the one of
 // incircle_sign; an inconclusive filter defers to incircle_sign itself, so
 // every decision (ties included) is the same.
+// The tags of the four cells (for the symbolic perturbation of the exact
+// fallback) are read only when the filter cannot decide.
 __device__ __forceinline__ int incircle0_sign(float fqx, float fqy, float frx, float fry, float fsx, float fsy,
                                               long long qx, long long qy, long long rx, long long ry, long long sx,
-                                              long long sy, int kp, int kq, int kr, int ks, float sc) {
+                                              long long sy, const int* __restrict__ tag, int ip, int iq, int ir,
+                                              int is, float sc) {
   float la = fqx * fqx + fqy * fqy, lb = frx * frx + fry * fry, lc = fsx * fsx + fsy * fsy;
   float t1 = frx * fsy, t2 = fry * fsx, t3 = fsx * fqy, t4 = fsy * fqx, t5 = fqx * fry, t6 = fqy * frx;
   float det = la * (t1 - t2) + lb * (t3 - t4) + lc * (t5 - t6);
@@ -454,7 +457,7 @@ __device__ __forceinline__ int incircle0_sign(float fqx, float fqy, float frx, f
     if (det > bound) return -1;
     if (det < -bound) return 1;
   }
-  return incircle_sign(0, 0, qx, qy, rx, ry, sx, sy, kp, kq, kr, ks, sc);
+  return incircle_sign(0, 0, qx, qy, rx, ry, sx, sy, tag[ip], tag[iq], tag[ir], tag[is], sc);
 }
 
 // orient_sign(a, b) with the float values of a and b converted by the caller.

@@ -425,7 +425,6 @@ __device__ __forceinline__ void test_cell(const TestArgs& g, int i, const long l
     return;
   }
   const int* ring = g.nbr + (size_t)i * CG_RING;
-  const int ti = g.tag[i];
   // sliding window over (j_{a-1}, j_a, j_{a+1}): grid offsets (exact) and
   // their float values, each converted once
   int jp = ring[m - 1], ja = ring[0];
@@ -436,7 +435,6 @@ __device__ __forceinline__ void test_cell(const TestArgs& g, int i, const long l
   const long long fX = aX, fY = aY;
   const float ffx = fax, ffy = fay;
   const int jfirst = ja;
-  int tp = g.tag[jp], ta = g.tag[ja];
   for (int a = 0; a < m; ++a) {
     int jn;
     long long nX, nY;
@@ -450,10 +448,9 @@ __device__ __forceinline__ void test_cell(const TestArgs& g, int i, const long l
     } else {
       jn = jfirst; nX = fX; nY = fY; fnx = ffx; fny = ffy;
     }
-    const int tn = g.tag[jn];
     if (i < ja) {
       // triangle (i, j_{a-1}, j_a) CCW; j_{a+1} must be outside its circle
-      int s = incircle0_sign(fpx, fpy, fax, fay, fnx, fny, pX, pY, aX, aY, nX, nY, ti, tp, ta, tn, sc);
+      int s = incircle0_sign(fpx, fpy, fax, fay, fnx, fny, pX, pY, aX, aY, nX, nY, g.tag, i, jp, ja, jn, sc);
       if (s > 0) {
         flag_cell(g.flags, g.list, &g.ctl->count[0], i);
         flag_cell(g.flags, g.list, &g.ctl->count[0], jp);
@@ -468,8 +465,8 @@ __device__ __forceinline__ void test_cell(const TestArgs& g, int i, const long l
         flag_cell(g.flags, g.list, &g.ctl->count[0], jn);
       }
     }
-    jp = ja; pX = aX; pY = aY; tp = ta; fpx = fax; fpy = fay;
-    ja = jn; aX = nX; aY = nY; ta = tn; fax = fnx; fay = fny;
+    jp = ja; pX = aX; pY = aY; fpx = fax; fpy = fay;
+    ja = jn; aX = nX; aY = nY; fax = fnx; fay = fny;
   }
 }
 
