@@ -56,6 +56,10 @@ FLOPS_PER_CELL = {"geometry": 277.0, "force_move": 93.0}
 # k_avm_force_move (3 edges x (offset, length, rsqrt, unit vector) + 3 force
 # terms x 8 + activity and move).
 AVM_FLOPS = {"cells_per_cell": 84.0, "vertices_per_vertex": 62.0}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the AVM kernels at N = 65536 from one ncu capture of the current kernels
+# (caches flushed before the kernel); None whenever a kernel has changed.
+AVM_DRAM_BYTES_PER_LAUNCH = {"k_avm_cells": 8.14e6, "k_avm_force_move": 7.37e6}
 # AVM storage order: Hilbert re-sort of the vertex and cell slots at creation
 # and every this many steps (Sec. 2.B; results are the same either way).
 AVM_SORT_EVERY = 100
@@ -424,7 +428,7 @@ def avm_roofline(n, ph, prof_steps):
         kernel, flops, ms = "k_avm_force_move", AVM_FLOPS["vertices_per_vertex"] * 2 * n, verts_ms
     achieved = flops / (ms * 1e-3) / 1e12
     return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": AVM_DRAM_BYTES_PER_LAUNCH.get(kernel),
             "duration_ms": ms,
             "note": "the kernel's own event-timed duration (eager launches); sqrt counts one flop but takes "
                     "an integer-pipe refinement; at N = 65536 the passes are latency bound"}

@@ -681,6 +681,26 @@ def test_run_io_refuses_a_non_finite_v0():
     with pytest.raises(cg.CellgbError) as e:
         sim.run_io(2, v0=bad)
     assert e.value.code == -1  # CG_EINVAL
+    # the status read back stays: the next call is refused before any work
+    steps = sim.counters()["steps"]
+    with pytest.raises(cg.CellgbError) as e:
+        sim.run_io(1)
+    assert e.value.code == -1 and sim.counters()["steps"] == steps
+    sim.close()
+
+
+def test_run_io_returns_a_status_raised_before_it():
+    """cg_run_io does not synchronise on entry: a status raised by earlier,
+    still unread work (a step that runs out of repair rounds) is returned
+    when the call ends, and the context refuses further I/O steps."""
+    sim, *_ = make(4096, 32, p0=3.85, v0=0.1, repair_cap=1)
+    sim.step(1)  # enqueued only; its status is not read here
+    with pytest.raises(cg.CellgbError) as e:
+        sim.run_io(1)
+    assert e.value.code == -4
+    with pytest.raises(cg.CellgbError) as e:
+        sim.run_io(1)
+    assert e.value.code == -4
     sim.close()
 
 
