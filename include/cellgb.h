@@ -126,9 +126,10 @@ typedef struct cg_launch {
                                     number of ring slots (0..7; default 5 in FP64, 0 in FP32) */
   int32_t force_beside;          /* 1: the force pass and the pending move run on the geometry
                                     branch beside the repair rounds, and after the rounds only the
-                                    cells around rewritten rings are done again (FP64 only;
-                                    results unchanged); 0: after the rounds, all cells (default:
-                                    the geometry branch is already as long as the rounds) */
+                                    cells around rewritten rings are done again (results
+                                    unchanged); 0: after the rounds, all cells (default: the
+                                    fix-up after the rounds costs more than the overlap gains,
+                                    in FP64 and in FP32 at N = 262144) */
 } cg_launch;
 
 /* Workspace size for R replicas. */

@@ -312,7 +312,7 @@ void run_geom(const cg_ctx* c, const GeomArgs& a, cudaStream_t st, int blocks = 
   else launch_geom(a, st, blocks);
 }
 void run_force(const cg_ctx* c, const ForceArgs& a, cudaStream_t st, int blocks = 0) {
-  if (fp32(c)) launch_force_f32(a, st);
+  if (fp32(c)) launch_force_f32(a, st, blocks);
   else launch_force(a, st, blocks);
 }
 void run_dir(const cg_ctx* c, const DirArgs& a, cudaStream_t st, int blocks = 0) {
@@ -805,7 +805,6 @@ int cg_create(int32_t R, const cg_replica* reps, const cg_params* params, const 
     c->launch.ring_order = 0;
     c->launch.dir_beside_geom = 0;
     c->launch.dir_blocks_per_sm = 2;
-    c->launch.force_beside = 0;  // the FP32 kernels have no tolerant force pass
   }
   c->off = layout(c->N, c->NB, c->NK, R);
   if (ws_bytes < c->off.total) {
@@ -1188,7 +1187,7 @@ int cg_set_launch(cg_ctx* c, const cg_launch* l) {
       (l->dir_low_priority != 0 && l->dir_low_priority != 1) || l->geom_blocks_per_sm < 0 ||
       l->geom_blocks_per_sm > 64 || l->test_blocks_per_sm < 0 || l->test_blocks_per_sm > 64 ||
       (l->dir_beside_geom != 0 && l->dir_beside_geom != 1) || l->ring_order < 0 || l->ring_order > 7 ||
-      (l->force_beside != 0 && l->force_beside != 1) || (l->force_beside && fp32(c)))
+      (l->force_beside != 0 && l->force_beside != 1))
     return CG_EINVAL;
   int rc = read_status(c);
   if (rc) return rc;
@@ -1275,7 +1274,6 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
   static const int beside_opts[] = {0, 1};
   static const int order_opts[] = {0, 1, 4, 5};
   static const int fb_opts[] = {0, 1};
-  const int n_fb = fp32(c) ? 1 : 2;  // FP32: force_beside stays 0
   const cg_launch start = c->launch;
   cg_launch cur = start;
   double cur_ms = 0.0;
@@ -1290,7 +1288,7 @@ int cg_autotune(cg_ctx* c, int32_t steps_per_trial, size_t flush_bytes, void* d_
       {&cg_launch::dir_blocks_per_sm, dir_opts, 5},       {&cg_launch::dir_low_priority, prio_opts, 2},
       {&cg_launch::geom_blocks_per_sm, geom_opts, 4},     {&cg_launch::test_blocks_per_sm, test_opts, 4},
       {&cg_launch::dir_beside_geom, beside_opts, 2},      {&cg_launch::ring_order, order_opts, 4},
-      {&cg_launch::force_beside, fb_opts, n_fb}};
+      {&cg_launch::force_beside, fb_opts, 2}};
   for (int sweep = 0; sweep < 2 && !rc; ++sweep) {
     for (const Field& f : fields) {
       for (int k = 0; k < f.nopt && !rc; ++k) {

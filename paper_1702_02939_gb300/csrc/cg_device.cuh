@@ -233,6 +233,13 @@ __device__ __forceinline__ double i128_to_double(__int128 v, int e2 = 0) {
   return __longlong_as_double((long long)(bits | (neg ? 0x8000000000000000ull : 0ull)));
 }
 
+// Puts cell i on a list once per use of the bitmap: the caller that sets
+// its bit appends it (the force pass's fix-up list of a step).
+__device__ __forceinline__ void claim_fix(unsigned* bits, int* list, int* count, int i) {
+  const unsigned bit = 1u << (i & 31);
+  if (!(atomicOr(&bits[i >> 5], bit) & bit)) list[atomicAdd(count, 1)] = i;
+}
+
 // Significant bits of a 128-bit magnitude (0 for 0).
 __device__ __forceinline__ int u128_bits(unsigned __int128 v) {
   const unsigned long long hi = (unsigned long long)(v >> 64), lo = (unsigned long long)v;

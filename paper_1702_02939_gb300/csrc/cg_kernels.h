@@ -192,7 +192,7 @@ struct CheckArgs {
 void launch_geom(const GeomArgs& a, cudaStream_t st, int blocks = 0);
 // Single-precision variants (spv_kernels_f32.cu); same arguments.
 void launch_geom_f32(const GeomArgs& a, cudaStream_t st, int blocks = 0);
-void launch_force_f32(const ForceArgs& a, cudaStream_t st);
+void launch_force_f32(const ForceArgs& a, cudaStream_t st, int blocks = 0);
 void launch_dir_f32(const DirArgs& a, cudaStream_t st, int blocks = 0);
 // blocks > 0: a grid-stride launch of that many blocks (list mode)
 void launch_force(const ForceArgs& a, cudaStream_t st, int blocks = 0);

@@ -230,11 +230,6 @@ __device__ __forceinline__ bool net_force(const ForceArgs& g, int i, double& fx_
   return true;
 }
 
-// Puts cell i on the fix-up list of the step, once.
-__device__ __forceinline__ void claim_fix(unsigned* bits, int* list, int* count, int i) {
-  const unsigned bit = 1u << (i & 31);
-  if (!(atomicOr(&bits[i >> 5], bit) & bit)) list[atomicAdd(count, 1)] = i;
-}
 
 // Cell i's net force (integrate 0 or 1) and update of Eq. 3 (integrate 1),
 // or the update alone from the stored forces of the current positions

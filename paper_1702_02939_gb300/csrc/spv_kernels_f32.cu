@@ -153,8 +153,9 @@ __global__ void __launch_bounds__(kGeomThreads) k_geom_f32(GeomArgs g) {
   }
 }
 
-// Net force on cell i in FP32 from the float force sets (false, status
-// raised, for a malformed ring).
+// Net force on cell i in FP32 from the float force sets (false for a
+// malformed ring: status raised, or, in the tolerant pass beside the repair
+// rounds, nothing raised and the cell left to the fix-up).
 __device__ __forceinline__ bool net_force_f32(const ForceArgs& g, int i, float& fx_out, float& fy_out) {
   const size_t N = (size_t)g.n;
   const float2* fs = as_f2(g.fs);
@@ -162,19 +163,26 @@ __device__ __forceinline__ bool net_force_f32(const ForceArgs& g, int i, float& 
   const float2* wv = as_f2(g.w);
   const int m = g.cnt[i];
   if (m < 3 || m > CG_RING) {
-    raise_status(g.ctl, kETOPO);
+    if (!g.tolerant) raise_status(g.ctl, kETOPO);
     return false;
   }
   const int* ring = g.nbr + (size_t)i * CG_RING;
-  int jfirst = ring[0];
+  bool bad = false;
+  auto nb = [&](int a) {  // a ring being rewritten may hold -1 entries
+    const int j = ring[a];
+    const bool ok = (unsigned)j < (unsigned)g.n;
+    bad |= !ok;
+    return ok ? j : i;
+  };
+  int jfirst = nb(0);
   int pfirst = ring_pos(g.nbr, g.cnt, jfirst, i);
   int j = jfirst, pj = pfirst;
   float fx = 0.f, fy = 0.f;
-  bool bad = pfirst < 0;
+  bad |= pfirst < 0;
   for (int a = 0; a < m; ++a) {
     int k, pk;
     if (a + 1 < m) {
-      k = ring[a + 1];
+      k = nb(a + 1);
       pk = ring_pos(g.nbr, g.cnt, k, i);
       bad |= pk < 0;
     } else {
@@ -194,26 +202,29 @@ __device__ __forceinline__ bool net_force_f32(const ForceArgs& g, int i, float& 
     j = k;
     pj = pk;
   }
-  if (bad) raise_status(g.ctl, kETOPO);
+  if (bad) {
+    if (g.tolerant) return false;
+    raise_status(g.ctl, kETOPO);
+  }
   fx_out = fx;
   fy_out = fy;
   return true;
 }
 
-// One thread per cell: the net force and, as in k_force, the move of Eq. 3
-// accumulated in FP64 and rounded to the grid (integrate 2: the move alone
-// from the stored forces, which hold the FP32 values exactly).
-__global__ void __launch_bounds__(kForceThreads) k_force_f32(ForceArgs g) {
-  const int item = blockIdx.x * kForceThreads + threadIdx.x;
-  if (item >= g.n) return;
-  const int i = g.order ? g.order[item] : item;
+// Cell i's net force and, as in k_force, the move of Eq. 3 accumulated in
+// FP64 and rounded to the grid (integrate 2: the move alone from the stored
+// forces, which hold the FP32 values exactly).
+__device__ __forceinline__ void force_cell_f32(const ForceArgs& g, int i) {
   const size_t N = (size_t)g.n;
   float fx, fy;
   if (g.integrate == 2) {
     fx = (float)g.Fx[i];
     fy = (float)g.Fy[i];
   } else {
-    if (!net_force_f32(g, i, fx, fy)) return;
+    if (!net_force_f32(g, i, fx, fy)) {
+      if (g.tolerant) claim_fix(g.fix_bits, g.fix_list, &g.ctl->force_count, i);
+      return;
+    }
     g.Fx[i] = fx;
     g.Fy[i] = fy;
     if (!g.integrate) return;
@@ -243,6 +254,10 @@ __global__ void __launch_bounds__(kForceThreads) k_force_f32(ForceArgs g) {
       Yn = move_framed(yi, g.dt, vy, R.y0, R.Lyg, R.scale, R.Y0, R.LYg, R.LY);
     }
   } else {
+    if (g.tolerant) {  // decided again, strictly, after the repair rounds
+      claim_fix(g.fix_bits, g.fix_list, &g.ctl->force_count, i);
+      return;
+    }
     raise_status(g.ctl, kENONFINITE);
     Xn = (long long)rint(xi * R.scale);
     Yn = (long long)rint(yi * R.scale);
@@ -252,6 +267,16 @@ __global__ void __launch_bounds__(kForceThreads) k_force_f32(ForceArgs g) {
   g.y[(size_t)nxt * N + i] = i2d_exact(Yn) * R.inv_scale;
   g.X[(size_t)nxt * N + i] = Xn;
   g.Y[(size_t)nxt * N + i] = Yn;
+}
+
+// One thread per cell, or grid-stride over a list (bits cleared), as k_force.
+__global__ void __launch_bounds__(kForceThreads) k_force_f32(ForceArgs g) {
+  const int total = g.list ? *g.list_count : g.n;
+  for (int item = blockIdx.x * kForceThreads + threadIdx.x; item < total; item += gridDim.x * kForceThreads) {
+    const int i = g.list ? g.list[item] : (g.order ? g.order[item] : item);
+    if (g.list_bits) atomicAnd(&g.list_bits[i >> 5], ~(1u << (i & 31)));
+    force_cell_f32(g, i);
+  }
 }
 
 // Director terms in FP32: n(theta) of the float director, and the noise from
@@ -283,8 +308,10 @@ void launch_geom_f32(const GeomArgs& a, cudaStream_t st, int blocks) {
   const int full = (a.n + kGeomThreads - 1) / kGeomThreads;
   k_geom_f32<<<(blocks > 0 && blocks < full) ? blocks : full, kGeomThreads, 0, st>>>(a);
 }
-void launch_force_f32(const ForceArgs& a, cudaStream_t st) {
-  if (a.n > 0) k_force_f32<<<(a.n + kForceThreads - 1) / kForceThreads, kForceThreads, 0, st>>>(a);
+void launch_force_f32(const ForceArgs& a, cudaStream_t st, int blocks) {
+  if (a.n <= 0) return;
+  const int full = (a.n + kForceThreads - 1) / kForceThreads;
+  k_force_f32<<<(blocks > 0 && blocks < full) ? blocks : full, kForceThreads, 0, st>>>(a);
 }
 void launch_dir_f32(const DirArgs& a, cudaStream_t st, int blocks) {
   if (a.n <= 0) return;

@@ -373,16 +373,17 @@ def test_launch_shapes_do_not_change_results():
         s.close()
 
 
-def test_force_pass_beside_the_rounds_keeps_results():
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_force_pass_beside_the_rounds_keeps_results(precision):
     """The force pass run beside the repair rounds, with the cells around
     rewritten rings (and any it could not decide) done again afterwards,
     gives bit for bit the state of the force pass after the rounds, in a
-    regime that rewrites many rings every step (and in a batch of replicas)."""
+    regime that rewrites many rings every step, in FP64 and FP32 mode."""
     n = 16384
-    a, *_ = make(n, 35, p0=3.95, v0=0.5, seed=5)
-    b, *_ = make(n, 35, p0=3.95, v0=0.5, seed=5)
+    a, *_ = make(n, 35, p0=3.95, v0=0.5, seed=5, precision=precision)
+    b, *_ = make(n, 35, p0=3.95, v0=0.5, seed=5, precision=precision)
     a.set_launch(force_beside=1)
-    assert b.launch["force_beside"] == 0
+    b.set_launch(force_beside=0)
     a.step(60)
     b.step(60)
     ca, cb = a.counters(), b.counters()
@@ -507,10 +508,6 @@ def test_fp32_mode_refuses_the_backward_pass():
     with pytest.raises(cg.CellgbError) as e:
         sim.hvp(np.zeros(400), np.zeros(400))
     assert e.value.code == -1
-    # nor does it take the force pass beside the repair rounds
-    assert sim.launch["force_beside"] == 0
-    with pytest.raises(RuntimeError):
-        sim.set_launch(force_beside=1)
     sim.close()
 
 
