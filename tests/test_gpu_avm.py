@@ -501,6 +501,30 @@ def test_divisions_in_conflict_match_oracle():
     sim.close()
 
 
+def test_divisions_beyond_one_window_match_oracle():
+    """A call with more divisions than one round's window (1024), some of them
+    on neighbouring cells, on a re-sorted storage: the network of doing them
+    one after the other, as the oracle does."""
+    n, cap, p0, v0 = 4096, 5400, 3.8, 0.05
+    sim, xs, ys, th, Lx, Ly = make(n, 36, p0=p0, v0=v0, t1_threshold=0.04, seed=10, capacity=cap, sort_every=50)
+    net = oracle.avm_build(xs, ys, Lx, Ly).with_capacity(cap)
+    theta = np.concatenate([th, np.zeros(cap - n)])
+    pa, va, aa = np.full(cap, p0), np.full(cap, v0), np.ones(cap)
+    rng = np.random.default_rng(7)
+    cells = rng.choice(n, 1200, replace=False)
+    ang = rng.uniform(0.0, np.pi, cells.size)
+    dirs = np.stack([np.cos(ang), np.sin(ang)], 1)
+    made = sim.divide(cells, dirs)
+    o, theta, pa, va, aa, omade = oracle.avm_divide(net, cells, dirs, theta, pa, va, aa)
+    np.testing.assert_array_equal(made, omade)
+    assert made.sum() > 1100
+    g, gth = gpu_net(sim, Lx, Ly)
+    assert_same_network(g, o)
+    np.testing.assert_array_equal(gth, theta)
+    check_network_valid(sim, Lx, Ly, p0)
+    sim.close()
+
+
 def test_division_slots_are_checked():
     n = 64
     sim, *_ = make(n, 32, capacity=n + 1)
