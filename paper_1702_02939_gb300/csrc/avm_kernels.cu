@@ -1251,10 +1251,6 @@ __global__ void k_iota2(int n, int* a, int* b) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] = b[i] = i;
 }
-__global__ void k_invert_tags(int n, const int* tags, int* slots) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) slots[tags[i]] = i;
-}
 
 // The network in tag order with its entries renamed to tags.
 __global__ void k_avm_topology_by_tag(AvmArgs g, const int* vslot, const int* cslot, int* vc_out, int* vn_out,
@@ -1384,9 +1380,6 @@ void launch_avm_sort(const AvmSortArgs& a, cudaStream_t st) {
 }
 void launch_iota2(int n, int* tags, int* slots, cudaStream_t st) {
   if (n > 0) k_iota2<<<(n + 255) / 256, 256, 0, st>>>(n, tags, slots);
-}
-void launch_invert_tags(int n, const int* tags, int* slots, cudaStream_t st) {
-  if (n > 0) k_invert_tags<<<(n + 255) / 256, 256, 0, st>>>(n, tags, slots);
 }
 void launch_avm_topology_by_tag(const AvmArgs& a, const int* vslot, const int* cslot, int* vc_out, int* vn_out,
                                 int* cc_out, int* cv_out, cudaStream_t st) {

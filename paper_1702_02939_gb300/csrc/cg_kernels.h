@@ -402,8 +402,6 @@ struct AvmSortArgs {
 void launch_avm_sort(const AvmSortArgs& a, cudaStream_t st);
 // Identity tags (tags[i] = slots[i] = i)
 void launch_iota2(int n, int* tags, int* slots, cudaStream_t st);
-// slots[tags[i]] = i
-void launch_invert_tags(int n, const int* tags, int* slots, cudaStream_t st);
 // Network in tag order (for the API): dst arrays indexed by tag, entries
 // renamed to tags (-1 kept)
 void launch_avm_topology_by_tag(const AvmArgs& a, const int* vslot, const int* cslot, int* vc_out, int* vn_out,
