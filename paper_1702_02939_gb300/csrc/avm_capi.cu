@@ -250,9 +250,9 @@ AvmArgs avm_args(cg_avm_ctx* c) {
 }
 
 int avm_status(cg_avm_ctx* c) {
+  Ctl h;  // read on the context's stream, after its work
+  AV_CUDA(c, cudaMemcpyAsync(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
   AV_CUDA(c, cudaStreamSynchronize(c->stream));
-  Ctl h;
-  AV_CUDA(c, cudaMemcpy(&h, c->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
   if (h.status) {
     c->broken = true;
     return afail(c, h.status, std::string("device status: ") + cg_status_string(h.status));
@@ -797,12 +797,13 @@ int cg_avm_divide(cg_avm_ctx* c, int32_t count, const int32_t* cells, const doub
     return CG_OK;
   }
   if (!cells || !dirs || count > c->n) return CG_EINVAL;
-  int rc = avm_status(c);
-  if (rc) return rc;
+  if (c->broken) return afail(c, CG_EINVAL, "context holds a device error: " + c->last_error);
+  int rc = CG_OK;
   // staged: the cells (tags) and directions; on the device the cells are
   // mapped to slots and the slots the divisions may take listed in order
   // (the empty cells and the free vertices of lowest tag: a call only fills
-  // slots); the host reads back how many there are
+  // slots); with too few of them the rounds do nothing.  One synchronisation,
+  // at the end.
   DivCtl* dctl = c->at<DivCtl>(c->off.div_ctl);
   int* dc = c->at<int>(c->off.div_cells);
   double* dd = c->at<double>(c->off.div_dirs);
@@ -823,20 +824,16 @@ int cg_avm_divide(cg_avm_ctx* c, int32_t count, const int32_t* cells, const doub
   // the re-sort's key counts served as scan input: cleared again
   AV_CUDA(c, cudaMemsetAsync(c->at<int>(c->off.kcount_c), 0, ((size_t)c->n + 2) * sizeof(int), c->stream));
   AV_CUDA(c, cudaMemsetAsync(c->at<int>(c->off.kcount_v), 0, ((size_t)c->V + 2) * sizeof(int), c->stream));
-  int freec[2] = {0, 0};
-  AV_CUDA(c, cudaMemcpyAsync(freec, &dctl->free_c, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  rc = avm_status(c);  // synchronizes
-  if (rc) return rc;
-  if (freec[0] < count || freec[1] < 2 * count)
-    return afail(c, CG_EINVAL, "not enough free cell slots for the divisions");
   AV_CUDA(c, cudaGraphLaunch(c->div_exec, c->stream));
   launch_avm_dir(avm_args(c), c->stream);  // the daughters' director terms
   AV_CUDA(c, cudaGetLastError());
   std::vector<int> hm(count);
+  DivCtl hd;
   AV_CUDA(c, cudaMemcpyAsync(hm.data(), dm, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  AV_CUDA(c, cudaStreamSynchronize(c->stream));
-  rc = avm_status(c);
+  AV_CUDA(c, cudaMemcpyAsync(&hd, dctl, sizeof(DivCtl), cudaMemcpyDeviceToHost, c->stream));
+  rc = avm_status(c);  // synchronizes
   if (rc) return rc;
+  if (hd.stop == 2) return afail(c, CG_EINVAL, "not enough free cell slots for the divisions");
   if (made) AV_CUDA(c, cudaMemcpy(made, hm.data(), (size_t)count * sizeof(int), cudaMemcpyDefault));
   if (n_made) {
     int t = 0;

@@ -1023,12 +1023,14 @@ __global__ void k_div_free_list(DivArgs d, const int* cslot, const int* vslot, c
   }
 }
 
+// A call with fewer free slots than it may need makes no division and
+// raises nothing (stop = 2; the host refuses the call).
 __global__ void k_div_begin(DivArgs d) {
   DivCtl* dc = d.dc;
   dc->start = 0;
   dc->used = 0;
   dc->round = 0;
-  dc->stop = 0;
+  dc->stop = (dc->free_c < dc->count || dc->free_v < 2 * dc->count) ? 2 : 0;
 }
 
 __global__ void __launch_bounds__(kDivLockThreads) k_div_lock(DivArgs d) {

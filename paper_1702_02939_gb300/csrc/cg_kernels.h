@@ -351,7 +351,7 @@ struct DivCtl {
   int end;    // end of the round's prefix of lock holders
   int used;   // divisions made so far (slots taken)
   int round;
-  int stop;   // a status was raised
+  int stop;   // 1: a status was raised; 2: too few free slots (nothing done)
   int free_c, free_v;  // free cell and vertex slots before the call
 };
 struct DivArgs {
