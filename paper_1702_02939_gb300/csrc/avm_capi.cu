@@ -30,7 +30,7 @@ struct AvmOff {
       done;
   size_t owned, base_local, base_partial, xs, ys, cnt, nbr, scalar, ctl, dir_tab;
   size_t div_cells, div_dirs, div_made, div_cslots, div_vslots, div_lock;  // staging of cg_avm_divide
-  size_t div_flag, div_pos, div_ctl;                                       // its rounds
+  size_t div_flag, div_ctl;                                                // its rounds
   // storage order: tags of the slots, slots of the tags, candidate priorities
   size_t vtag, ctag, vslot, cslot, cand_k;
   // re-sort scratch (keys, ranks, new places, key counts, permuted copies);
@@ -89,7 +89,6 @@ AvmOff avm_layout(int64_t n, size_t spv_bytes) {
   o.div_vslots = L.take(2 * n * i4);
   o.div_lock = L.take(n * sizeof(unsigned long long));
   o.div_flag = L.take(kDivWindow * i4);
-  o.div_pos = L.take(kDivWindow * i4);
   o.div_ctl = L.take(sizeof(DivCtl));
   o.vtag = L.take(V * i4);
   o.ctag = L.take(n * i4);
@@ -422,7 +421,6 @@ int avm_graphs(cg_avm_ctx* c) {
   d.made = c->at<int>(c->off.div_made);
   d.dlock = c->at<unsigned long long>(c->off.div_lock);
   d.flag = c->at<int>(c->off.div_flag);
-  d.pos = c->at<int>(c->off.div_pos);
   d.dc = c->at<DivCtl>(c->off.div_ctl);
   if (c->div_exec) {
     cudaGraphExecDestroy(c->div_exec);

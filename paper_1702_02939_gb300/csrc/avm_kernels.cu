@@ -960,10 +960,11 @@ __device__ int divide_cell(const AvmArgs& g, int c, double ux, double uy, int ne
 // are never cleared within a call); the longest prefix of the window whose
 // divisions all hold their locks is mutually disjoint and disjoint from every
 // division after it.  Its divisions are tried without writing (made or not),
-// one per block so that their FP64 work spreads over the SMs; a block scan of
-// the outcomes gives each made one its slots in request order (the next
-// unused entries of cslots and of vslots, two each); they are then applied
-// together.  A division of a cell slot without a polygon (empty: an earlier
+// one per block so that their FP64 work spreads over the SMs; each made one
+// then takes its slots in request order (the next unused entries of cslots
+// and of vslots, two each, after the made ones before it) and they are
+// applied together.  Three kernels a round: locks, check and dry run,
+// application (whose last block closes the round).  A division of a cell slot without a polygon (empty: an earlier
 // division of the call may fill it) waits until it is the first pending one.
 // The first pending division always holds its locks, so every round makes
 // progress.  made[k] = 1 when division k was made.
@@ -1031,6 +1032,7 @@ __global__ void k_div_begin(DivArgs d) {
   dc->used = 0;
   dc->round = 0;
   dc->stop = (dc->free_c < dc->count || dc->free_v < 2 * dc->count) ? 2 : 0;
+  dc->done = 0u;
 }
 
 __global__ void __launch_bounds__(kDivLockThreads) k_div_lock(DivArgs d) {
@@ -1049,91 +1051,79 @@ __global__ void __launch_bounds__(kDivLockThreads) k_div_lock(DivArgs d) {
   for_ring_cells(d.g, c, (m >= 3 && m <= CG_RING) ? m : 0, [&](int x) { atomicMin(&d.dlock[x], key); });
 }
 
-__global__ void __launch_bounds__(kDivLockThreads) k_div_check(DivArgs d) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  DivCtl* dc = d.dc;
-  const int start = dc->start, wend = min(dc->count, start + kDivWindow);
-  const int k = start + t;
-  if (k >= wend || dc->stop) return;
-  const int c = d.cells[k];
-  bool ok = (unsigned)c < (unsigned)d.g.n;
-  if (ok) {
-    const int m = d.g.cc[c];
-    const bool poly = m >= 3 && m <= CG_RING;
-    // a mother without a polygon waits until it is the first pending division
-    ok = poly || k == start;
-    const unsigned long long key = div_key(dc->round, k);
-    for_ring_cells(d.g, c, poly ? m : 0, [&](int x) { ok = ok && d.dlock[x] == key; });
-  }
-  if (!ok) atomicMin(&dc->end, k);
-}
-
-// One block per division of the round's prefix (lane 0 works): the dry run.
-__global__ void k_div_dry(DivArgs d) {
+// One block per division of the window (lane 0 works, so that the divisions'
+// FP64 work spreads over the SMs): whether it holds every lock of its 1-ring
+// (the first non-holder ends the round's prefix) and, if it does, the dry run
+// (made or not).  A holder beyond the prefix is tried too, harmlessly: it
+// reads only its own 1-ring, which no division of the prefix touches.
+__global__ void k_div_check_dry(DivArgs d) {
   if (threadIdx.x != 0) return;
   DivCtl* dc = d.dc;
-  const int b = blockIdx.x, start = dc->start, end = dc->end;
+  const int b = blockIdx.x, start = dc->start, wend = min(dc->count, start + kDivWindow);
   const int k = start + b;
   int flag = 0;
-  if (b == 0 && end == start && start < dc->count && !dc->stop) {
-    // the first pending division can only fail by an invalid cell index
-    raise_status(d.g.ctl, kEINVAL);
-    dc->stop = 1;
-  }
-  if (k < end && !dc->stop) {
-    const int r = divide_cell(d.g, d.cells[k], d.dirs[2 * k], d.dirs[2 * k + 1], 0, 0, 0, false);
-    if (r < 0) {
-      raise_status(d.g.ctl, kETOPO);
-      dc->stop = 1;
+  if (k < wend && !dc->stop) {
+    const int c = d.cells[k];
+    bool ok = (unsigned)c < (unsigned)d.g.n;
+    if (ok) {
+      const int m = d.g.cc[c];
+      const bool poly = m >= 3 && m <= CG_RING;
+      // a mother without a polygon waits until it is the first pending division
+      ok = poly || k == start;
+      const unsigned long long key = div_key(dc->round, k);
+      for_ring_cells(d.g, c, poly ? m : 0, [&](int x) { ok = ok && d.dlock[x] == key; });
     }
-    flag = (r == 0);
+    if (!ok) {
+      atomicMin(&dc->end, k);
+    } else {
+      const int r = divide_cell(d.g, c, d.dirs[2 * k], d.dirs[2 * k + 1], 0, 0, 0, false);
+      if (r < 0) {
+        raise_status(d.g.ctl, kETOPO);
+        dc->stop = 1;
+      }
+      flag = (r == 0);
+    }
   }
   d.flag[b] = flag;
 }
 
-// The slots of the made divisions of the round (one block of kDivWindow).
-__global__ void __launch_bounds__(kDivWindow) k_div_scan(DivArgs d) {
-  __shared__ int warp_tot[kDivWindow / 32];
-  DivCtl* dc = d.dc;
-  const int t = threadIdx.x, start = dc->start, nr = dc->end - start, used = dc->used;
-  const int f = t < nr ? d.flag[t] : 0;
-  const int lane = t & 31, wid = t >> 5;
-  int incl = f;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) warp_tot[wid] = incl;
-  __syncthreads();
-  int woff = 0;
-  for (int w = 0; w < wid; ++w) woff += warp_tot[w];
-  d.pos[t] = used + woff + incl - f;
-  if (t < nr) d.made[start + t] = f;
-  __syncthreads();
-  if (t == kDivWindow - 1) dc->used = used + woff + incl;
-}
-
-// One block per division of the round's prefix (lane 0 works): applied.
+// One block per division of the prefix [start, end): its slots (the made
+// divisions before it in the prefix, counted by lane 0), the division
+// applied, its outcome recorded.  The last block to finish closes the round:
+// slots used, the next window's start, another round while divisions remain.
 __global__ void k_div_commit(DivArgs d) {
-  if (threadIdx.x != 0) return;
   DivCtl* dc = d.dc;
-  const int b = blockIdx.x, k = dc->start + b;
-  if (k >= dc->end || !d.flag[b] || dc->stop) return;
-  const int p = d.pos[b];
-  if (divide_cell(d.g, d.cells[k], d.dirs[2 * k], d.dirs[2 * k + 1], d.cslots[p], d.vslots[2 * p],
-                  d.vslots[2 * p + 1]) != 0) {
-    raise_status(d.g.ctl, kETOPO);
-    dc->stop = 1;
+  const int b = blockIdx.x, start = dc->start, end = dc->end;
+  if (threadIdx.x == 0) {
+    if (b == 0 && end == start && start < dc->count && !dc->stop) {
+      // the first pending division can only fail by an invalid cell index
+      raise_status(d.g.ctl, kEINVAL);
+      dc->stop = 1;
+    }
+    const int k = start + b;
+    if (k < end) {
+      const int f = d.flag[b];
+      d.made[k] = f;
+      if (f && !dc->stop) {
+        int p = dc->used;
+        for (int t = 0; t < b; ++t) p += d.flag[t];
+        if (divide_cell(d.g, d.cells[k], d.dirs[2 * k], d.dirs[2 * k + 1], d.cslots[p], d.vslots[2 * p],
+                        d.vslots[2 * p + 1]) != 0) {
+          raise_status(d.g.ctl, kETOPO);
+          dc->stop = 1;
+        }
+      }
+    }
   }
-}
-
-__global__ void k_div_advance(DivArgs d) {
-  DivCtl* dc = d.dc;
-  dc->start = dc->end;
-  dc->round += 1;
-  const int more = dc->start < dc->count && !dc->stop && d.g.ctl->status == 0;
-  if (more && d.loop) cudaGraphSetConditional(d.loop, 1);
+  if (last_block(&dc->done) && threadIdx.x == 0) {
+    int made = 0;
+    for (int t = 0; t < end - start; ++t) made += d.flag[t];
+    dc->used += made;
+    dc->start = end;
+    dc->round += 1;
+    const int more = end < dc->count && !dc->stop && d.g.ctl->status == 0;
+    if (more && d.loop) cudaGraphSetConditional(d.loop, 1);
+  }
 }
 
 // Preferred perimeters P0_c = p0_c sqrt(A0_c); A0_c must be finite and >= 0.
@@ -1341,11 +1331,8 @@ void launch_avm_divide_begin(const DivArgs& d, cudaStream_t st) {
 }
 void launch_avm_divide_round(const DivArgs& d, cudaStream_t st) {
   k_div_lock<<<kDivWindow / kDivLockThreads, kDivLockThreads, 0, st>>>(d);
-  k_div_check<<<kDivWindow / kDivLockThreads, kDivLockThreads, 0, st>>>(d);
-  k_div_dry<<<kDivWindow, 32, 0, st>>>(d);
-  k_div_scan<<<1, kDivWindow, 0, st>>>(d);
+  k_div_check_dry<<<kDivWindow, 32, 0, st>>>(d);
   k_div_commit<<<kDivWindow, 32, 0, st>>>(d);
-  k_div_advance<<<1, 1, 0, st>>>(d);
 }
 void launch_avm_sort(const AvmSortArgs& a, cudaStream_t st) {
   const int blocks = blocks_of(a.V);  // V = 2n covers the cells too

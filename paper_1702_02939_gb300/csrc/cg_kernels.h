@@ -353,6 +353,7 @@ struct DivCtl {
   int round;
   int stop;   // 1: a status was raised; 2: too few free slots (nothing done)
   int free_c, free_v;  // free cell and vertex slots before the call
+  unsigned int done;   // last-block counter of the commit kernel
 };
 struct DivArgs {
   AvmArgs g;
@@ -361,7 +362,7 @@ struct DivArgs {
   int *cslots, *vslots;
   int* made;
   unsigned long long* dlock;  // [n] round-stamped locks
-  int *flag, *pos;            // [kDivWindow] outcome and slot index of the round's divisions
+  int* flag;                  // [kDivWindow] outcome of the round's dry runs
   DivCtl* dc;
   cudaGraphConditionalHandle loop;
 };
