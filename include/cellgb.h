@@ -298,7 +298,7 @@ int cg_set_launch(cg_ctx* ctx, const cg_launch* launch);
  * optional L2-flush region of flush_bytes. */
 int cg_autotune_bytes(const cg_ctx* ctx, size_t flush_bytes, size_t* bytes);
 /* Picks the launch shapes by timing candidates (coordinate descent over the
- * six fields, two sweeps; the winner is confirmed against the starting shapes
+ * fields of cg_launch, two sweeps; the winner is confirmed against the starting shapes
  * in longer trials) on a temporary copy of the context built in d_ws2
  * (device, >= cg_autotune_bytes(ctx, flush_bytes), 256-byte aligned) from the
  * current state, directors, step counter, p0 and v0: each trial restores that
