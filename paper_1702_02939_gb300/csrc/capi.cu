@@ -913,15 +913,22 @@ int cg_run_io(cg_ctx* c, int64_t nsteps, const double* v0, int64_t v0_stride, do
   const int n = (int)c->N;
   cudaStream_t st = c->stream;
   const int* tag = c->at<int>(c->off.tag);
+  // several steps: the copies on streams of their own, overlapping the
+  // neighbouring steps' kernels; one step: everything on the context's
+  // stream (nothing to overlap with), one synchronisation
+  const bool sep = nsteps > 1;
+  cudaStream_t sin = sep ? c->h2d : st, sout = sep ? c->d2h : st;
   for (int64_t k = 0; k < nsteps; ++k) {
     const int b = (int)(k & 1);
     if (v0) {
       // H2D into staging b once the scatter that last read it is done
       double* in = c->at<double>(c->off.io_v0) + b * N;
-      CG_CUDA(c, cudaStreamWaitEvent(c->h2d, c->in_free[b], 0));
-      CG_CUDA(c, cudaMemcpyAsync(in, v0 + k * v0_stride, N * sizeof(double), cudaMemcpyDefault, c->h2d));
-      CG_CUDA(c, cudaEventRecord(c->in_ready[b], c->h2d));
-      CG_CUDA(c, cudaStreamWaitEvent(st, c->in_ready[b], 0));
+      if (sep) CG_CUDA(c, cudaStreamWaitEvent(sin, c->in_free[b], 0));
+      CG_CUDA(c, cudaMemcpyAsync(in, v0 + k * v0_stride, N * sizeof(double), cudaMemcpyDefault, sin));
+      if (sep) {
+        CG_CUDA(c, cudaEventRecord(c->in_ready[b], sin));
+        CG_CUDA(c, cudaStreamWaitEvent(st, c->in_ready[b], 0));
+      }
       // this step's v0 into storage order and the pending move redone with it
       // (as cg_set_v0), in one kernel
       ForceArgs f = force_args(c, 2);
@@ -940,15 +947,19 @@ int cg_run_io(cg_ctx* c, int64_t nsteps, const double* v0, int64_t v0_stride, do
       double* out = c->at<double>(c->off.io_xy) + 2 * b * N;
       CG_CUDA(c, cudaStreamWaitEvent(st, c->out_free[b], 0));
       launch_gather_cur_xy(n, tag, c->at<double>(c->off.x), c->at<double>(c->off.y), c->ctl(), out, out + N, st);
-      CG_CUDA(c, cudaEventRecord(c->out_ready[b], st));
-      CG_CUDA(c, cudaStreamWaitEvent(c->d2h, c->out_ready[b], 0));
-      if (x) CG_CUDA(c, cudaMemcpyAsync(x + k * out_stride, out, N * sizeof(double), cudaMemcpyDefault, c->d2h));
-      if (y) CG_CUDA(c, cudaMemcpyAsync(y + k * out_stride, out + N, N * sizeof(double), cudaMemcpyDefault, c->d2h));
-      CG_CUDA(c, cudaEventRecord(c->out_free[b], c->d2h));
+      if (sep) {
+        CG_CUDA(c, cudaEventRecord(c->out_ready[b], st));
+        CG_CUDA(c, cudaStreamWaitEvent(sout, c->out_ready[b], 0));
+      }
+      if (x) CG_CUDA(c, cudaMemcpyAsync(x + k * out_stride, out, N * sizeof(double), cudaMemcpyDefault, sout));
+      if (y) CG_CUDA(c, cudaMemcpyAsync(y + k * out_stride, out + N, N * sizeof(double), cudaMemcpyDefault, sout));
+      CG_CUDA(c, cudaEventRecord(c->out_free[b], sout));
     }
   }
-  CG_CUDA(c, cudaStreamSynchronize(c->h2d));
-  CG_CUDA(c, cudaStreamSynchronize(c->d2h));
+  if (sep) {
+    CG_CUDA(c, cudaStreamSynchronize(c->h2d));
+    CG_CUDA(c, cudaStreamSynchronize(c->d2h));
+  }
   return read_status(c);
 }
 
