@@ -158,13 +158,14 @@ int cg_step(cg_ctx* ctx, int64_t nsteps);
  * as cg_set_v0 would set it; after step k the positions are written to
  * x + k*out_stride and y + k*out_stride (n_total doubles each, user order;
  * NULL skips).  Strides count doubles; 0 reuses one buffer for every step.
- * Pointers may be host (page-locked, for the copies to overlap) or device.
- * The copies run on two private streams through double-buffered staging in
- * the workspace, so step k's upload and step k-1's download overlap the
- * kernels; the results are bit-identical to cg_set_v0, cg_step(1),
- * cg_get_state per step.  Synchronizes before returning and returns the
- * device status (a non-finite v0 sets CG_EINVAL; the steps after it still
- * run). */
+ * Pointers may be host or device.  Device buffers are read and written by
+ * the step's kernels in place; host buffers (page-locked for overlap) go
+ * through double-buffered staging in the workspace, copied on two private
+ * streams (one call of several steps) so that step k's upload and step
+ * k-1's download overlap the kernels.  The results are bit-identical to
+ * cg_set_v0, cg_step(1), cg_get_state per step.  Synchronizes before
+ * returning and returns the device status (a non-finite v0 sets CG_EINVAL;
+ * the steps after it still run). */
 int cg_run_io(cg_ctx* ctx, int64_t nsteps, const double* v0, int64_t v0_stride, double* x, double* y,
               int64_t out_stride);
 

@@ -918,9 +918,30 @@ int cg_run_io(cg_ctx* c, int64_t nsteps, const double* v0, int64_t v0_stride, do
   // stream (nothing to overlap with), one synchronisation
   const bool sep = nsteps > 1;
   cudaStream_t sin = sep ? c->h2d : st, sout = sep ? c->d2h : st;
+  // device buffers are read and written by the kernels in place (no staging
+  // copy); host buffers, page-locked or not, go through staging and the copy
+  // engines, which move them faster than the kernels' own loads and stores
+  // across the host link
+  auto addressable = [](const void* p) -> const void* {
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return a.type == cudaMemoryTypeDevice ? p : nullptr;
+  };
+  const double* dv0 = static_cast<const double*>(addressable(v0));
+  double* dx = static_cast<double*>(const_cast<void*>(addressable(x)));
+  double* dy = static_cast<double*>(const_cast<void*>(addressable(y)));
+  const bool direct_out = (!x || dx) && (!y || dy);
   for (int64_t k = 0; k < nsteps; ++k) {
     const int b = (int)(k & 1);
-    if (v0) {
+    if (v0 && dv0) {
+      // this step's v0 read in place, the pending move redone with it
+      ForceArgs f = force_args(c, 2);
+      f.v0_user = dv0 + k * v0_stride;
+      run_force(c, f, st);
+    } else if (v0) {
       // H2D into staging b once the scatter that last read it is done
       double* in = c->at<double>(c->off.io_v0) + b * N;
       if (sep) CG_CUDA(c, cudaStreamWaitEvent(sin, c->in_free[b], 0));
@@ -942,7 +963,10 @@ int cg_run_io(cg_ctx* c, int64_t nsteps, const double* v0, int64_t v0_stride, do
     }
     CG_CUDA(c, cudaGraphLaunch(c->step_exec, st));
     ++c->host_step;
-    if (x || y) {
+    if ((x || y) && direct_out) {
+      launch_gather_cur_xy(n, tag, c->at<double>(c->off.x), c->at<double>(c->off.y), c->ctl(),
+                           dx ? dx + k * out_stride : nullptr, dy ? dy + k * out_stride : nullptr, st);
+    } else if (x || y) {
       // positions of this step into staging b once its previous D2H is done
       double* out = c->at<double>(c->off.io_xy) + 2 * b * N;
       CG_CUDA(c, cudaStreamWaitEvent(st, c->out_free[b], 0));

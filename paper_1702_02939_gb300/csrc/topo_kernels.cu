@@ -612,8 +612,8 @@ __global__ void k_gather_cur_xy(int n, const int* tag, const double* x2, const d
   if (i >= n) return;
   const size_t off = (size_t)ctl->cur * n + i;
   const int u = tag[i];
-  dst_x[u] = x2[off];
-  dst_y[u] = y2[off];
+  if (dst_x) dst_x[u] = x2[off];
+  if (dst_y) dst_y[u] = y2[off];
 }
 __global__ void k_scatter_d(int n, const int* tag, const double* src, double* dst) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -665,6 +665,24 @@ def test_run_io_is_bit_identical_to_set_step_get(precision, sort_every):
     b.run_io(3, x=dx, y=dy)
     x, y, th = a.state()
     assert torch.equal(dx, x) and torch.equal(dy, y)
+    # a per-step v0 read in place from device memory, one step and several
+    for k in (1, 3):
+        for j in range(k):
+            a.set_v0(v0[j])
+            a.step(1)
+        dv0 = torch.from_numpy(v0[:k].ravel().copy()).cuda()
+        b.run_io(k, v0=dv0, x=dx, y=dy, v0_stride=n)
+        x, y, th = a.state()
+        assert torch.equal(dx, x) and torch.equal(dy, y)
+    # pageable host buffers (staged copies), one step and several
+    for k in (1, 2):
+        a.set_v0(v0[k])
+        a.step(k)
+        px, py = np.empty(k * n), np.empty(k * n)
+        b.run_io(k, v0=np.tile(v0[k], k), x=px, y=py, v0_stride=n, out_stride=n)
+        x, y, _ = a.state()
+        np.testing.assert_array_equal(px[(k - 1) * n:], x.cpu().numpy())
+        np.testing.assert_array_equal(py[(k - 1) * n:], y.cpu().numpy())
     for t0, t1 in zip(a.state(), b.state()):
         assert torch.equal(t0, t1)
     a.close()
