@@ -160,9 +160,11 @@ int cg_step(cg_ctx* ctx, int64_t nsteps);
  * NULL skips).  Strides count doubles; 0 reuses one buffer for every step.
  * Pointers may be host or device.  Device buffers are read and written by
  * the step's kernels in place; host buffers (page-locked for overlap) go
- * through double-buffered staging in the workspace, copied on two private
- * streams (one call of several steps) so that step k's upload and step
- * k-1's download overlap the kernels.  The results are bit-identical to
+ * through double-buffered staging in the workspace.  The positions after
+ * step k are known before step k's kernels start (they are its pending
+ * move), so their download runs on a private stream beside step k; in a
+ * call of several steps the upload of step k's v0 runs on another private
+ * stream beside step k-1.  The results are bit-identical to
  * cg_set_v0, cg_step(1), cg_get_state per step.  Synchronizes before
  * returning and returns the device status (a non-finite v0 sets CG_EINVAL;
  * the steps after it still run). */

@@ -913,11 +913,14 @@ int cg_run_io(cg_ctx* c, int64_t nsteps, const double* v0, int64_t v0_stride, do
   const int n = (int)c->N;
   cudaStream_t st = c->stream;
   const int* tag = c->at<int>(c->off.tag);
-  // several steps: the copies on streams of their own, overlapping the
-  // neighbouring steps' kernels; one step: everything on the context's
-  // stream (nothing to overlap with), one synchronisation
+  // several steps: the uploads on a stream of their own, overlapping the
+  // previous step's kernels; one step: the upload on the context's stream
+  // (the step needs it first).  The downloads always take a stream of their
+  // own: the positions after a step are its pending move, complete before
+  // the step starts, so they are gathered then and downloaded while the
+  // step's kernels run
   const bool sep = nsteps > 1;
-  cudaStream_t sin = sep ? c->h2d : st, sout = sep ? c->d2h : st;
+  cudaStream_t sin = sep ? c->h2d : st, sout = c->d2h;
   // device buffers are read and written by the kernels in place (no staging
   // copy); host buffers, page-locked or not, go through staging and the copy
   // engines, which move them faster than the kernels' own loads and stores
@@ -961,30 +964,31 @@ int cg_run_io(cg_ctx* c, int64_t nsteps, const double* v0, int64_t v0_stride, do
       launch_sort(sort_args(c), st);
       prime(c);
     }
-    CG_CUDA(c, cudaGraphLaunch(c->step_exec, st));
-    ++c->host_step;
+    // the positions after this step: the pending move, now final
+    const double* x2 = c->at<double>(c->off.x);
+    const double* y2 = c->at<double>(c->off.y);
     if ((x || y) && direct_out) {
-      launch_gather_cur_xy(n, tag, c->at<double>(c->off.x), c->at<double>(c->off.y), c->ctl(),
-                           dx ? dx + k * out_stride : nullptr, dy ? dy + k * out_stride : nullptr, st);
+      launch_gather_cur_xy(n, tag, x2, y2, c->ctl(), 1, dx ? dx + k * out_stride : nullptr,
+                           dy ? dy + k * out_stride : nullptr, st);
     } else if (x || y) {
-      // positions of this step into staging b once its previous D2H is done
+      // into staging b once its previous D2H is done, then downloaded beside
+      // the step
       double* out = c->at<double>(c->off.io_xy) + 2 * b * N;
       CG_CUDA(c, cudaStreamWaitEvent(st, c->out_free[b], 0));
-      launch_gather_cur_xy(n, tag, c->at<double>(c->off.x), c->at<double>(c->off.y), c->ctl(), out, out + N, st);
-      if (sep) {
-        CG_CUDA(c, cudaEventRecord(c->out_ready[b], st));
-        CG_CUDA(c, cudaStreamWaitEvent(sout, c->out_ready[b], 0));
-      }
+      launch_gather_cur_xy(n, tag, x2, y2, c->ctl(), 1, out, out + N, st);
+      CG_CUDA(c, cudaEventRecord(c->out_ready[b], st));
+      CG_CUDA(c, cudaStreamWaitEvent(sout, c->out_ready[b], 0));
       if (x) CG_CUDA(c, cudaMemcpyAsync(x + k * out_stride, out, N * sizeof(double), cudaMemcpyDefault, sout));
       if (y) CG_CUDA(c, cudaMemcpyAsync(y + k * out_stride, out + N, N * sizeof(double), cudaMemcpyDefault, sout));
       CG_CUDA(c, cudaEventRecord(c->out_free[b], sout));
     }
+    CG_CUDA(c, cudaGraphLaunch(c->step_exec, st));
+    ++c->host_step;
   }
-  if (sep) {
-    CG_CUDA(c, cudaStreamSynchronize(c->h2d));
-    CG_CUDA(c, cudaStreamSynchronize(c->d2h));
-  }
-  return read_status(c);
+  const int rc = read_status(c);
+  if (sep) CG_CUDA(c, cudaStreamSynchronize(c->h2d));
+  CG_CUDA(c, cudaStreamSynchronize(c->d2h));
+  return rc;
 }
 
 int cg_profile_step(cg_ctx* c, int64_t nsteps, double* ms_out, int32_t n_out) {

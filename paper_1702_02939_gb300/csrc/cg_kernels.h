@@ -218,8 +218,10 @@ void launch_halo_pack(int n, const int* tag, const int* slot, const Rep* reps, c
                       const long long* X2, const long long* Y2, long long* out, cudaStream_t st);
 void launch_halo_unpack(int n, const int* tag, const int* slot, const Rep* reps, const int* rep, Ctl* ctl,
                         const long long* in, double* x2, double* y2, long long* X2, long long* Y2, cudaStream_t st);
-// current positions (x2, y2: [2][n], buffer ctl->cur) into user order
-void launch_gather_cur_xy(int n, const int* tag, const double* x2, const double* y2, const Ctl* ctl,
+// positions (x2, y2: [2][n]) of buffer ctl->cur (pending 0) or of the
+// pending move, buffer ctl->cur ^ 1 (pending 1), into user order; a null
+// destination is skipped
+void launch_gather_cur_xy(int n, const int* tag, const double* x2, const double* y2, const Ctl* ctl, int pending,
                           double* dst_x, double* dst_y, cudaStream_t st);
 void launch_gather_ring(int n, const int* tag, const int* cnt, const int* nbr, int* cnt_user, int* nbr_user,
                         cudaStream_t st);

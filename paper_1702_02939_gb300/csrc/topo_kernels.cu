@@ -607,10 +607,10 @@ __global__ void k_gather_d(int n, const int* tag, const double* src, double* dst
 }
 // Current positions (buffer ctl->cur of x2, y2, each [2][n]) in user order.
 __global__ void k_gather_cur_xy(int n, const int* tag, const double* x2, const double* y2, const Ctl* ctl,
-                                double* dst_x, double* dst_y) {
+                                int pending, double* dst_x, double* dst_y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const size_t off = (size_t)ctl->cur * n + i;
+  const size_t off = (size_t)(ctl->cur ^ pending) * n + i;
   const int u = tag[i];
   if (dst_x) dst_x[u] = x2[off];
   if (dst_y) dst_y[u] = y2[off];
@@ -645,9 +645,9 @@ __global__ void __launch_bounds__(1024) k_reduce_sum(int n, const double* v, dou
 void launch_gather_d(int n, const int* tag, const double* src, double* dst_user, cudaStream_t st) {
   if (n > 0) k_gather_d<<<(n + 255) / 256, 256, 0, st>>>(n, tag, src, dst_user);
 }
-void launch_gather_cur_xy(int n, const int* tag, const double* x2, const double* y2, const Ctl* ctl,
+void launch_gather_cur_xy(int n, const int* tag, const double* x2, const double* y2, const Ctl* ctl, int pending,
                           double* dst_x, double* dst_y, cudaStream_t st) {
-  if (n > 0) k_gather_cur_xy<<<(n + 255) / 256, 256, 0, st>>>(n, tag, x2, y2, ctl, dst_x, dst_y);
+  if (n > 0) k_gather_cur_xy<<<(n + 255) / 256, 256, 0, st>>>(n, tag, x2, y2, ctl, pending, dst_x, dst_y);
 }
 void launch_scatter_d(int n, const int* tag, const double* src_user, double* dst, cudaStream_t st) {
   if (n > 0) k_scatter_d<<<(n + 255) / 256, 256, 0, st>>>(n, tag, src_user, dst);
