@@ -512,7 +512,10 @@ def avm_throughput(args, device):
     sim.sync()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     c1 = sim.counters()
-    launches = 2 * K + 2 * (c1["loop_total"] - c0["loop_total"])
+    # per step: cell pass, vertex pass, director terms, one kernel per T1
+    # pass; per re-sort (after every AVM_SORT_EVERY-th step): 11 kernels
+    sorts = (args.avm_warmup + K) // AVM_SORT_EVERY - args.avm_warmup // AVM_SORT_EVERY
+    launches = 3 * K + (c1["loop_total"] - c0["loop_total"]) + 11 * sorts
     prof_steps = max(1, args.avm_profile_steps)
     ph = sim.profile(prof_steps)
     # oracle on the same kind of state (its own network build), a few steps

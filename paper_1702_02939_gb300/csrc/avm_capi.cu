@@ -33,6 +33,7 @@ struct AvmOff {
   size_t div_flag, div_ctl;                                                // its rounds
   // storage order: tags of the slots, slots of the tags, candidate priorities
   size_t vtag, ctag, vslot, cslot, cand_k;
+  size_t cand_v, cand_w;  // a T1 candidate's other end and outer neighbours
   // re-sort scratch (keys, ranks, new places, key counts, permuted copies);
   // between re-sorts the copies stage the API's tag-ordered transfers
   size_t vkey, vrank, vperm, ckey, crank, cperm, kcount_v, kstart_v, kpart_v, kcount_c, kstart_c, kpart_c;
@@ -95,6 +96,8 @@ AvmOff avm_layout(int64_t n, size_t spv_bytes) {
   o.vslot = L.take(V * i4);
   o.cslot = L.take(n * i4);
   o.cand_k = L.take((3 * V / 2 + n + 1) * i4);
+  o.cand_v = L.take((3 * V / 2 + n + 1) * sizeof(int4));
+  o.cand_w = L.take((3 * V / 2 + n + 1) * i4);
   o.vkey = L.take(V * i4);
   o.vrank = L.take(V * i4);
   o.vperm = L.take(V * i4);
@@ -241,6 +244,8 @@ AvmArgs avm_args(cg_avm_ctx* c) {
   a.cand_e = c->at<int>(c->off.cand_e);
   a.cand = c->at<int4>(c->off.cand);
   a.cand_k = c->at<int>(c->off.cand_k);
+  a.cand_v = c->at<int4>(c->off.cand_v);
+  a.cand_w = c->at<int>(c->off.cand_w);
   a.vtag = c->at<int>(c->off.vtag);
   a.ctag = c->at<int>(c->off.ctag);
   a.done = c->at<unsigned int>(c->off.done);

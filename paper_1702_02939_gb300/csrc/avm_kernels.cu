@@ -453,13 +453,24 @@ __global__ void k_t1_propose(AvmArgs g) {
       if (!(len2_rn(dx, dy) < g.thr2)) continue;
     }
     // orientation by tags: v1 the end of smaller tag, the edge slot a of v1
+    // and slot b of v2; both ends' neighbour lists give the flip's four outer
+    // vertices, recorded with the candidate so that the flip loads nothing
+    // whose address waits on another load
     const int tv = g.vtag[v], tw = g.vtag[w];
-    const int v1 = tv < tw ? v : w, v2 = tv < tw ? w : v;
-    const int a = tv < tw ? s : slot3(g.vn, w, v);
-    if (a < 0) {
+    const int rv0 = g.vn[3 * v], rv1 = g.vn[3 * v + 1], rv2 = g.vn[3 * v + 2];
+    const int rw0 = g.vn[3 * w], rw1 = g.vn[3 * w + 1], rw2 = g.vn[3 * w + 2];
+    const int sw = rw0 == v ? 0 : rw1 == v ? 1 : rw2 == v ? 2 : -1;  // slot of v in w's list
+    if (sw < 0) {
       raise_status(g.ctl, kETOPO);
       continue;
     }
+    const bool vfirst = tv < tw;
+    const int v1 = vfirst ? v : w, v2 = vfirst ? w : v;
+    const int a = vfirst ? s : sw, b = vfirst ? sw : s;
+    const int p0 = vfirst ? rv0 : rw0, p1 = vfirst ? rv1 : rw1, p2 = vfirst ? rv2 : rw2;  // v1's list
+    const int q0 = vfirst ? rw0 : rv0, q1 = vfirst ? rw1 : rv1, q2 = vfirst ? rw2 : rv2;  // v2's list
+    const int Aul = a == 0 ? p1 : a == 1 ? p2 : p0, All = a == 0 ? p2 : a == 1 ? p0 : p1;
+    const int Alr = b == 0 ? q1 : b == 1 ? q2 : q0, Aur = b == 0 ? q2 : b == 1 ? q0 : q1;
     const int i = g.vc[3 * v1 + a], k = g.vc[3 * v1 + (a + 1) % 3], j = g.vc[3 * v1 + (a + 2) % 3];
     int l = -1;
     for (int t = 0; t < 3; ++t) {
@@ -484,6 +495,8 @@ __global__ void k_t1_propose(AvmArgs g) {
     g.cand_e[slot] = 3 * v1 + a;
     g.cand_k[slot] = ek;
     g.cand[slot] = make_int4(i, j, k, l);
+    g.cand_v[slot] = make_int4(v2, Aul, All, Alr);
+    g.cand_w[slot] = Aur;
   }
 }
 
@@ -531,8 +544,15 @@ __device__ __forceinline__ void store_row(int* cv, int c, const Row& w) {
   for (int q = 0; q < CG_RING / 4; ++q)
     p[q] = make_int4(w.r[4 * q], w.r[4 * q + 1], w.r[4 * q + 2], w.r[4 * q + 3]);
 }
+// Bit a set where entry a < m equals v: every compare at once, no chain.
+__device__ __forceinline__ unsigned row_match(const Row& w, int m, int v) {
+  unsigned hit = 0u;
+#pragma unroll
+  for (int a = 0; a < CG_RING; ++a) hit |= (a < m && w.r[a] == v) ? (1u << a) : 0u;
+  return hit;
+}
 // Removes every occurrence of v among the first m entries; returns the count.
-__device__ __forceinline__ int row_remove(Row& w, int m, int v) {
+__device__ __forceinline__ int row_remove_all(Row& w, int m, int v) {
   Row o;
   int n = 0;
 #pragma unroll
@@ -548,13 +568,27 @@ __device__ __forceinline__ int row_remove(Row& w, int m, int v) {
   w = o;
   return n;
 }
+// The same for the usual case of at most one occurrence (a cell lists a
+// vertex once): one shift selected per slot.
+__device__ __forceinline__ int row_remove(Row& w, int m, int v) {
+  const unsigned hit = row_match(w, m, v);
+  if (__popc(hit) > 1) return row_remove_all(w, m, v);
+  const int n = max(0, min(m, CG_RING)) - (hit ? 1 : 0);
+  const int p = hit ? __ffs(hit) - 1 : CG_RING;
+  Row o;
+#pragma unroll
+  for (int a = 0; a < CG_RING; ++a) {
+    const int next = a + 1 < CG_RING ? w.r[a + 1] : -1;
+    o.r[a] = a >= n ? -1 : a < p ? w.r[a] : next;
+  }
+  w = o;
+  return n;
+}
 // Inserts v after the last occurrence of `after` among the first m entries
 // (at the front if absent); returns the new count.
 __device__ __forceinline__ int row_insert(Row& w, int m, int after, int v) {
-  int p = -1;
-#pragma unroll
-  for (int a = 0; a < CG_RING; ++a)
-    if (a < m && w.r[a] == after) p = a;
+  const unsigned hit = row_match(w, m, after);
+  const int p = hit ? 31 - __clz(hit) : -1;
   Row o;
 #pragma unroll
   for (int a = 0; a < CG_RING; ++a) {
@@ -565,20 +599,25 @@ __device__ __forceinline__ int row_insert(Row& w, int m, int after, int v) {
   return m + 1;
 }
 
-__device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd, unsigned long long key) {
+__device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd, int4 nv, int Aur, unsigned long long key) {
   Ctl* ctl = g.ctl;
   const size_t V = (size_t)g.V;
   double* hx = g.hx + ctl->cur * V;
   double* hy = g.hy + ctl->cur * V;
   const int e = 3 * v1 + a;
   const int i = cd.x, j = cd.y, k = cd.z, l = cd.w;
-  // independent loads first: the lists of v1 and of the four cells.  They
-  // run before the lock check, while other flips of the pass edit the
-  // network: a T2 that won a shared cell may have freed v2 (vn = -1), so the
-  // loads take v1 in its place (the flip then loses a lock and returns)
-  const int v2r = g.vn[e];
-  const int v2 = ((unsigned)v2r < (unsigned)g.V) ? v2r : v1;
-  const int Aul = g.vn[3 * v1 + (a + 1) % 3], All = g.vn[3 * v1 + (a + 2) % 3];
+  const int v2 = nv.x, Aul = nv.y, All = nv.z, Alr = nv.w;
+  if ((unsigned)v2 >= (unsigned)g.V || (unsigned)Aul >= (unsigned)g.V || (unsigned)All >= (unsigned)g.V ||
+      (unsigned)Alr >= (unsigned)g.V || (unsigned)Aur >= (unsigned)g.V) {
+    raise_status(ctl, kETOPO);
+    return;
+  }
+  // Every load of the flip at once (the proposal recorded the vertices it
+  // touches, so no address waits on another load), before the lock check,
+  // while other flips of the pass edit the network.  A flip that holds its
+  // four locks sees none of this data change: a vertex has three cells, two
+  // of them this flip's, so no other winner edits these lists or positions;
+  // one that does not hold them discards it.
   const bool distinct = i != j && i != k && i != l && j != k && j != l && k != l;
   Row ri, rk, rj, rl;
   int mi = 0, mk = 0, mj = 0, ml = 0;
@@ -586,30 +625,32 @@ __device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd, unsigned long
     ri = load_row(g.cv, i); rk = load_row(g.cv, k); rj = load_row(g.cv, j); rl = load_row(g.cv, l);
     mi = g.cc[i]; mk = g.cc[k]; mj = g.cc[j]; ml = g.cc[l];
   }
-  int n2[3], c2[3];
+  const int v2r = g.vn[e], Aul_r = g.vn[3 * v1 + (a == 2 ? 0 : a + 1)], All_r = g.vn[3 * v1 + (a == 0 ? 2 : a - 1)];
+  int n2[3], c2[3], nu[3], nl[3];
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
     n2[t] = g.vn[3 * v2 + t];
     c2[t] = g.vc[3 * v2 + t];
+    nu[t] = g.vn[3 * Aul + t];
+    nl[t] = g.vn[3 * Alr + t];
   }
   const double x1 = hx[v1], y1 = hy[v1], x2 = hx[v2], y2 = hy[v2];
-  // the four locks, read beside the loads above (all depend only on the
-  // candidate; a flip that holds its locks sees none of that data change in
-  // this pass, and one that does not discards it)
+  const float2 fAll = g.hf[All], fAlr = g.hf[Alr], fAul = g.hf[Aul], fAur = g.hf[Aur];
   if (g.lock[i] != key || g.lock[j] != key || g.lock[k] != key || g.lock[l] != key) {
     ctl->t1_more = 1;
     return;
   }
-  int b = -1;
-#pragma unroll
-  for (int t = 2; t >= 0; --t)
-    if (n2[t] == v1) b = t;
-  if (b < 0 || c2[b] != k || c2[(b + 1) % 3] != i) {
+  // the network as the proposal saw it (always so for a lock holder); the
+  // slot b of v1 in v2's lists picks by selects (no indexed local array)
+  const int b = n2[0] == v1 ? 0 : n2[1] == v1 ? 1 : n2[2] == v1 ? 2 : -1;
+  const int c2b = b == 0 ? c2[0] : b == 1 ? c2[1] : c2[2], c2b1 = b == 0 ? c2[1] : b == 1 ? c2[2] : c2[0];
+  const int n2b1 = b == 0 ? n2[1] : b == 1 ? n2[2] : n2[0], n2b2 = b == 0 ? n2[2] : b == 1 ? n2[0] : n2[1];
+  if (v2r != v2 || Aul_r != Aul || All_r != All || b < 0 || c2b != k || c2b1 != i || n2b1 != Alr || n2b2 != Aur) {
     raise_status(ctl, kETOPO);
     return;
   }
-  const int Alr = n2[(b + 1) % 3], Aur = n2[(b + 2) % 3];
-  const int su = slot3(g.vn, Aul, v1), sl = slot3(g.vn, Alr, v2);
+  const int su = nu[0] == v1 ? 0 : nu[1] == v1 ? 1 : nu[2] == v1 ? 2 : -1;  // v1 in Aul's list
+  const int sl = nl[0] == v2 ? 0 : nl[1] == v2 ? 1 : nl[2] == v2 ? 2 : -1;  // v2 in Alr's list
   if (su < 0 || sl < 0) {
     raise_status(ctl, kETOPO);
     return;
@@ -617,8 +658,10 @@ __device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd, unsigned long
   // rotate the edge by 90 degrees about its midpoint, new length t1_len
   const double ex = mimg_a(x2 - x1, g.ax), ey = mimg_a(y2 - y1, g.ay);
   const double mx = x1 + 0.5 * ex, my = y1 + 0.5 * ey;
-  const double len = sqrt(ex * ex + ey * ey);
-  const double px = -ey / len * 0.5 * g.t1_len, py = ex / len * 0.5 * g.t1_len;
+  // half the new length over the old one, from the refined inverse square
+  // root (a short dependent chain; FP64 square root and division are long)
+  const double h = fx_rsqrt(ex * ex + ey * ey) * (0.5 * g.t1_len);
+  const double px = -ey * h, py = ex * h;
   const double nx1 = wrap_a(mx - px, g.ax), ny1 = wrap_a(my - py, g.ay);
   const double nx2 = wrap_a(mx + px, g.ax), ny2 = wrap_a(my + py, g.ay);
   hx[v1] = nx1; hy[v1] = ny1;
@@ -633,13 +676,12 @@ __device__ void apply_t1(const AvmArgs& g, int v1, int a, int4 cd, unsigned long
   // new candidate here.  (The bound is symmetric in the two ends: the float
   // difference and its minimum image change sign exactly.)
   {
-    const int a1[2] = {All, Alr}, a2[2] = {Aul, Aur};
-    bool near = t1_len2_f(g, f1, f2) <= g.t2hi;
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      near |= t1_len2_f(g, f1, g.hf[a1[t]]) <= g.t2hi;
-      near |= t1_len2_f(g, f2, g.hf[a2[t]]) <= g.t2hi;
-    }
+    // the outer vertices' float positions as loaded, or v1's and v2's new
+    // ones where a degenerate network names v1 or v2 among them
+    auto now = [&](int u, float2 f) { return u == v1 ? f1 : u == v2 ? f2 : f; };
+    const bool near = t1_len2_f(g, f1, f2) <= g.t2hi || t1_len2_f(g, f1, now(All, fAll)) <= g.t2hi ||
+                      t1_len2_f(g, f1, now(Alr, fAlr)) <= g.t2hi || t1_len2_f(g, f2, now(Aul, fAul)) <= g.t2hi ||
+                      t1_len2_f(g, f2, now(Aur, fAur)) <= g.t2hi;
     // (a degenerate network, with a cell on both sides of an edge, takes the
     // next pass regardless)
     if (near || !distinct) ctl->t1_more = 1;
@@ -771,16 +813,23 @@ __device__ void apply_t2(const AvmArgs& g, int c, int4 cd) {
 // work the next pass would propose nothing, so it is skipped.
 __global__ void k_t1_apply(AvmArgs g) {
   Ctl* ctl = g.ctl;
+  // this thread's first candidate is loaded beside the pass's counters, before
+  // its count is known (the list always has room for the index)
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool room = t0 < 3 * g.V / 2 + g.n + 1;
+  const int e0 = room ? g.cand_e[t0] : 0, k0 = room ? g.cand_k[t0] : 0, w0 = room ? g.cand_w[t0] : 0;
+  const int4 cd0 = room ? g.cand[t0] : make_int4(0, 0, 0, 0), nv0 = room ? g.cand_v[t0] : make_int4(0, 0, 0, 0);
   const int pass = ctl->last_flagged;
   const int proposed = *(volatile int*)&ctl->count[1];
   if (pass < g.t1_cap) {
     const int stamp = ctl->round_count;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < proposed; t += gridDim.x * blockDim.x) {
-      const int e = g.cand_e[t];
-      const int4 cd = g.cand[t];
-      const unsigned long long key = lock_key(stamp, g.cand_k[t]);
+    for (int t = t0; t < proposed; t += gridDim.x * blockDim.x) {
+      const bool first = t == t0;
+      const int e = first ? e0 : g.cand_e[t];
+      const int4 cd = first ? cd0 : g.cand[t];
+      const unsigned long long key = lock_key(stamp, first ? k0 : g.cand_k[t]);
       if (e < 3 * g.V) {
-        apply_t1(g, e / 3, e % 3, cd, key);  // checks the locks itself
+        apply_t1(g, e / 3, e % 3, cd, first ? nv0 : g.cand_v[t], first ? w0 : g.cand_w[t], key);  // checks the locks itself
         continue;
       }
       if (g.lock[cd.x] != key || g.lock[cd.y] != key || g.lock[cd.z] != key || g.lock[cd.w] != key) {

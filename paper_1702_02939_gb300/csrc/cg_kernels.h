@@ -324,6 +324,9 @@ struct AvmArgs {
   int* cand_e;               // [3V/2 + n] proposed edges 3v+s (slots), or 3V + c for a T2 of cell slot c
   int* cand_k;               // [3V/2 + n] their priorities: the same ids in tags
   int4* cand;                // [3V/2 + n] their cells (i, j, k, l), or (c, and the three across its edges)
+  int4* cand_v;              // [3V/2 + n] of a T1 candidate: the other end v2 and v1's outer neighbours
+                             // (v2, Aul, All, Alr) (Fig. 1 naming)
+  int* cand_w;               // [3V/2 + n] and v2's other outer neighbour Aur
   const int *vtag, *ctag;    // [V], [n] the tag (API id) of each vertex and cell slot
   unsigned int* done;        // [2] last-block counters (force/move, T1 apply)
   cudaGraphConditionalHandle loop;  // while-node handle of the T1 passes
