@@ -239,6 +239,7 @@ AvmArgs avm_args(cg_avm_ctx* c) {
   t1_bounds(c->par.t1_threshold, std::fmax(c->Lx, c->Ly), a.t2lo, a.t2hi);
   a.hf = c->at<float2>(c->off.hf);
   a.t1_cap = cap_of(c);
+  a.apply_blocks = std::max(1, std::min((c->V + 127) / 128, std::max(c->sms / 2, 1)));
   a.lock = c->at<unsigned long long>(c->off.lock);
   a.cand_e = c->at<int>(c->off.cand_e);
   a.cand = c->at<int4>(c->off.cand);

@@ -805,29 +805,35 @@ __device__ void apply_t2(const AvmArgs& g, int c, int4 cd) {
 }
 
 // Applies the listed candidates (T1 edges, T2 cells) that hold all four
-// locks (passes 0 .. t1_cap-1; pass t1_cap only counts), in one block: a
-// pass has a handful of candidates once the tissue has relaxed (more only in
-// the first steps of a fresh network, taken kApplyThreads at a time), and
-// one block needs no count of finished blocks.  It then closes the pass:
+// locks (passes 0 .. t1_cap-1; pass t1_cap only counts) and closes the pass:
 // another pass runs while this one may have left work (a candidate that lost
 // a lock, an edge at a moved vertex within the FP32 bound of the threshold,
 // or a short edge its cells kept from flipping) and the cap is not reached;
 // candidates at the counting pass raise the T1-cap status.  Without such
-// work the next pass would propose nothing, so it is skipped.
+// work the next pass would propose nothing, so it is skipped.  A pass of at
+// most one block's worth of candidates (the usual case once the tissue has
+// relaxed) is applied by block 0 alone and closed after a block barrier; a
+// larger one (the first steps of a fresh network) by every block, closed by
+// the last block to finish.
 constexpr int kApplyThreads = 128;
 __global__ void k_t1_apply(AvmArgs g) {
   Ctl* ctl = g.ctl;
   // this thread's first candidate is loaded beside the pass's counters, before
-  // its count is known (the list always has room for the index)
-  const int t0 = threadIdx.x;
+  // their values are known (the list always has room for the index)
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
   const bool room = t0 < 3 * g.V / 2 + g.n + 1;
   const int e0 = room ? g.cand_e[t0] : 0, k0 = room ? g.cand_k[t0] : 0, w0 = room ? g.cand_w[t0] : 0;
   const int4 cd0 = room ? g.cand[t0] : make_int4(0, 0, 0, 0), nv0 = room ? g.cand_v[t0] : make_int4(0, 0, 0, 0);
   const int pass = ctl->last_flagged;
   const int proposed = *(volatile int*)&ctl->count[1];
+  // the same for every block (the count is cleared only by the closing
+  // block, after every block that uses it has read it)
+  const bool one_block = proposed <= (int)blockDim.x;
+  if (one_block && blockIdx.x != 0) return;
+  const int stride = one_block ? blockDim.x : gridDim.x * blockDim.x;
   if (pass < g.t1_cap) {
     const int stamp = ctl->round_count;
-    for (int t = t0; t < proposed; t += blockDim.x) {
+    for (int t = t0; t < proposed; t += stride) {
       const bool first = t == t0;
       const int e = first ? e0 : g.cand_e[t];
       const int4 cd = first ? cd0 : g.cand[t];
@@ -843,14 +849,20 @@ __global__ void k_t1_apply(AvmArgs g) {
       apply_t2(g, e - 3 * g.V, cd);
     }
   }
-  __syncthreads();  // every flip of the pass is done, its flags visible here
-  if (threadIdx.x == 0) {
+  bool closing;
+  if (one_block) {
+    __syncthreads();  // every flip of the pass is done, its flags visible here
+    closing = threadIdx.x == 0;
+  } else {
+    closing = last_block(g.done + 1) && threadIdx.x == 0;
+  }
+  if (closing) {
     ctl->count[1] = 0;
     ctl->round_count += 1;
     ctl->loop_total += 1;
     ctl->last_flagged = pass + 1;
     if (pass >= g.t1_cap && proposed > 0) atomicCAS(&ctl->status, 0, (int)kET1CAP);
-    const int more = proposed > 0 && ctl->t1_more && pass < g.t1_cap && ctl->status == 0;
+    const int more = proposed > 0 && *(volatile int*)&ctl->t1_more && pass < g.t1_cap && ctl->status == 0;
     ctl->t1_more = 0;
     ctl->pad = more;  // read by the host when the passes run outside a graph
     if (more && g.loop) cudaGraphSetConditional(g.loop, 1);
@@ -1347,7 +1359,7 @@ void launch_avm_dir(const AvmArgs& a, cudaStream_t st) {
 void launch_avm_begin_t1(Ctl* ctl, cudaStream_t st) { k_avm_begin_t1<<<1, 1, 0, st>>>(ctl); }
 void launch_avm_t1_pass(const AvmArgs& a, cudaStream_t st) {
   k_t1_propose<<<blocks_of(a.V), kAvmThreads, 0, st>>>(a);
-  k_t1_apply<<<1, kApplyThreads, 0, st>>>(a);
+  k_t1_apply<<<a.apply_blocks, kApplyThreads, 0, st>>>(a);
 }
 void launch_avm_shadow(const AvmArgs& a, cudaStream_t st) {
   k_avm_shadow<<<blocks_of(a.V), kAvmThreads, 0, st>>>(a);

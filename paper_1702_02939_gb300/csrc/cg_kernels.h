@@ -319,7 +319,7 @@ struct AvmArgs {
   double t2_twice;           // T2: twice the area threshold (0: no T2)
   float t2lo, t2hi;          // FP32 squared lengths certainly below / above thr2
   float2* hf;                // [V] float copies of the current positions
-  int t1_cap;
+  int t1_cap, apply_blocks;  // T1 pass cap; blocks of the apply kernel (of 128 threads)
   unsigned long long* lock;  // [n] pass-stamped T1 locks
   int* cand_e;               // [3V/2 + n] proposed edges 3v+s (slots), or 3V + c for a T2 of cell slot c
   int* cand_k;               // [3V/2 + n] their priorities: the same ids in tags
